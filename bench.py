@@ -1,0 +1,278 @@
+#!/usr/bin/env python
+"""Benchmark of the ternary D3Q19 LB + IBM step (one JSON line on stdout).
+
+Workload: the 128^3 D3Q19 capsule workload (walls in z, flat C1/C2
+interface at z = 64, icosphere level-4 capsule of radius 20 with Skalak and
+Helfrich membrane mechanics, FP32 storage), stepped with the library's CUDA
+kernels.  The state (about 1.1 GB) is far larger than L2, so no explicit L2
+flush is needed between steps.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+N > 1 runs independent replicas, one per rank (the method does not shard
+here): value = all ranks' cell updates / max-over-ranks time.
+`--impl reference` times the FP64 CPU oracle on the host cores instead.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "ternary D3Q19+IBM MLUPS & %HBM roofline; time-to-equilibrium learned vs plain"
+BYTES_PER_CELL = 480  # algorithmic bytes per cell update with FP32 storage
+
+
+def _peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return None
+
+
+def _src_hash():
+    h = hashlib.sha256()
+    d = os.path.join(ROOT, "paper_1906_03065_gb300", "csrc")
+    for f in sorted(os.listdir(d)):
+        h.update(open(os.path.join(d, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def _traffic(kernel: str):
+    """DRAM bytes per launch from a committed ncu summary, if it was taken
+    on the current kernel sources."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        t = json.load(open(p))
+        e = t[kernel]
+        if e.get("source_sha") != _src_hash():
+            return None
+        return e["dram_bytes_per_launch"]
+    except Exception:
+        return None
+
+
+class Clocks:
+    """nvidia-smi sampler (SM clock, max clock, throttle reasons)."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: str):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                                          "-lms", "100", "-i", self.index], stdout=subprocess.PIPE,
+                                         stderr=subprocess.DEVNULL, text=True)
+            self.th = threading.Thread(target=self._read, daemon=True)
+            self.th.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append((time.time(), line.strip()))
+
+    def stop(self):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self, t0=None, t1=None):
+        rows = []
+        for t, l in self.lines:
+            if t0 is not None and not (t0 <= t <= t1):
+                continue
+            f = [x.strip() for x in l.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                rows.append((float(f[1]), float(f[2]), f[5:9]))
+            except ValueError:
+                continue
+        if not rows:
+            return None
+        sm = sorted(r[0] for r in rows)
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            for n, v in zip(names, r[2]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        return {"sm_mhz": sm[len(sm) // 2], "sm_max_mhz": max(r[1] for r in rows),
+                "reasons": sorted(reasons), "samples": len(rows)}
+
+
+def _dist():
+    rank = int(os.environ.get("RANK", 0))
+    world = int(os.environ.get("WORLD_SIZE", 1))
+    local = int(os.environ.get("LOCAL_RANK", 0))
+    return rank, world, local
+
+
+def run_reference(args, wl):
+    rank, world, _ = _dist()
+    if rank != 0:
+        return
+    import oracle
+    oracle.build()
+    cores = oracle.set_threads(0)
+    o = oracle.Oracle(wl)  # initial state, untimed
+    n = min(args.steps, 2)
+    t0 = time.perf_counter()
+    o.step(n)
+    dt = time.perf_counter() - t0
+    N = wl.params.ncells
+    v = N * n / dt / 1e6
+    sample = f"{n} oracle step(s) of the full {wl.name} workload (of {args.steps} requested)"
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": v, "unit": "MLUPS", "n_gpus": args.gpus,
+        "steps": n, "warmup": 0, "ms_per_step": 1e3 * dt / n, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": wl.name, "cells": N, "markers": int(wl.membranes[0].X.shape[0])},
+        "cpu_baseline": {"value": v, "unit": "MLUPS", "cores": cores, "kind": "oracle", "sample": sample},
+        "e2e": {"value": v, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+
+    from paper_1906_03065_gb300 import workloads as W
+    wl = W.capsule_3d("f32")
+    if args.impl == "reference":
+        return run_reference(args, wl)
+
+    import numpy as np
+    import torch
+    rank, world, local = _dist()
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    dev = torch.device(f"cuda:{local}")
+    torch.cuda.set_device(dev)
+    from paper_1906_03065_gb300 import build
+    if rank == 0:
+        build.build()
+    if dist:
+        dist.barrier()
+    import paper_1906_03065_gb300 as T
+
+    sim = T.Simulation(wl, device=dev)
+    sim.init()
+    N = wl.params.ncells
+    stream = sim.stream
+    vis = os.environ.get("CUDA_VISIBLE_DEVICES")
+    clk = Clocks(vis.split(",")[local] if vis else str(local))
+    clk.start()
+    time.sleep(0.3)
+    with torch.cuda.stream(stream):
+        sim.step(args.warmup)
+        torch.cuda.synchronize(dev)
+        if dist:
+            dist.barrier()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        tw0 = time.time()
+        e0.record(stream)
+        sim.step(args.steps)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        tw1 = time.time()
+        launches = sim.launches()
+        if dist:
+            dist.barrier()
+    ms = e0.elapsed_time(e1)
+    ms_t = torch.tensor([ms], device=dev)
+    if dist:
+        dist.all_reduce(ms_t, op=dist.ReduceOp.MAX)
+    ms_max = float(ms_t.item())
+    clocks = clk.summary(tw0 - 0.05, tw1 + 0.05) or clk.summary()
+    clk.stop()
+    value = world * N * args.steps / (ms_max / 1e3) / 1e6
+
+    # per-phase device time (CUDA events on the library stream) for the roofline
+    nprof = max(20, min(200, args.steps))
+    pr = sim.profile(nprof)
+    t_coll = pr.ms_collide / nprof / 1e3
+    peaks = _peaks()
+    peak = peaks["hbm_gbs"] if peaks else 6800.0
+    achieved = BYTES_PER_CELL * N / t_coll / 1e9
+    step_eff = BYTES_PER_CELL * N * args.steps / (ms_max / 1e3) / 1e9
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "traffic": _traffic("k_collide"),
+                "kernel": "k_collide", "peak_source": "measured" if peaks else "fallback",
+                "bytes_per_launch": BYTES_PER_CELL * N,
+                "whole_step_frac": step_eff / peak,
+                "phase_ms_per_step": {"moments": pr.ms_moments / nprof, "ibm": pr.ms_ibm / nprof,
+                                      "collide": pr.ms_collide / nprof, "interp": pr.ms_interp / nprof}}
+
+    # end to end through the public API with host buffers: upload the initial
+    # fields, step, read back the C3 field and the markers
+    Ch = np.ascontiguousarray(np.stack([sim.field("C1"), sim.field("C2"), sim.field("C3")]))
+    Uh = np.ascontiguousarray(sim.field("u"))
+    Ke = args.steps
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    sim.init(Ch, Uh)
+    sim.step(Ke)
+    c3 = sim.field("C3")
+    X = sim.nodes(0)
+    t1 = time.perf_counter()
+    e2e_v = world * N * Ke / (t1 - t0) / 1e6
+    h2d = (Ch.nbytes + Uh.nbytes) / Ke
+    d2h = (c3.nbytes + X.nbytes) / Ke
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        import oracle
+        oracle.build()
+        cores = oracle.set_threads(0)
+        o = oracle.Oracle(wl)
+        tc = time.perf_counter()
+        o.step(1)
+        dtc = time.perf_counter() - tc
+        cpu = {"value": N / dtc / 1e6, "unit": "MLUPS", "cores": cores, "kind": "oracle",
+               "sample": f"1 FP64 oracle step of the full {wl.name} workload ({dtc:.1f} s)"}
+
+    if rank == 0:
+        print(json.dumps({
+            "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": wl.name, "cells": N, "markers": int(wl.membranes[0].X.shape[0]),
+                       "storage": "f32", "l2": "state 1.1 GB > L2, no flush needed",
+                       "parallelism": "replicas" if world > 1 else "single"},
+            "roofline": roofline, "cpu_baseline": cpu, "clocks": clocks,
+            "e2e": {"value": e2e_v, "unit": "MLUPS", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+            "gpu_launches": launches,
+        }))
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

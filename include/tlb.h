@@ -1,0 +1,191 @@
+/*
+ * tlb.h -- C ABI of the GB300 ternary lattice Boltzmann + immersed boundary
+ * library (libtlb.so).
+ *
+ * The library advances the method of "Modelling ternary fluids in contact
+ * with elastic membranes" (Pepona, Shek, Semprebon, Krueger, Kusumaatmaja):
+ * a three-component free-energy lattice Boltzmann fluid (populations f_i for
+ * the density rho, g_i for phi = C1 - C2 and h_i for psi = C3; Sec. 2.6 and
+ * Sec. 3.1, eqs. VariableTransform, LBE, EDF, MomentsDFs) coupled through the
+ * immersed boundary method (Sec. 3.3, eqs. Spreading, DiscreteDirac,
+ * Interpolation, UpdatedXl) to closed elastic membranes that enclose
+ * component 3 (Sec. 3.2, eqs. DiscreteSE, DiscreteBE, DiscreteCE,
+ * DiscreteCF).  Every step of the path runs in the library's own CUDA
+ * kernels for sm_103a.
+ *
+ * Conventions shared by every call:
+ *  - Units are lattice units, dx = dt = 1, cs^2 = 1/3 (Sec. 3.1).
+ *  - A lattice cell (x, y, z) has linear index (z*ny + y)*nx + x.  A 2D
+ *    lattice (dim = 2) is nx by ny with index y*nx + x (nz is ignored).
+ *  - Device memory is owned by the caller: one arena of tlb_state_bytes()
+ *    bytes, 256-byte aligned, passed to tlb_create() and kept alive until
+ *    tlb_destroy().  The library allocates no device memory itself.
+ *  - Host pointers are borrowed for the duration of the call only; the
+ *    library copies what it needs.
+ *  - Calls are ordered on the CUDA stream given to tlb_create().  tlb_step
+ *    returns once the work is enqueued; every tlb_read_* and
+ *    tlb_diagnostics call synchronises that stream before returning.
+ *  - Every call returns a tlb_status; on failure tlb_last_error() returns a
+ *    message (thread-local).  A context is not thread-safe.
+ */
+#ifndef TLB_H
+#define TLB_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  TLB_OK = 0,
+  TLB_ERR_ARG = 1,       /* invalid argument, size or state of the call     */
+  TLB_ERR_CUDA = 2,      /* a CUDA runtime call failed                       */
+  TLB_ERR_ALLOC = 3,     /* the arena is too small for the requested state   */
+  TLB_ERR_DIVERGED = 4,  /* NaN/Inf or a marker moved more than one cell     */
+  TLB_ERR_TIMEOUT = 5,   /* a bounded device-side wait gave up               */
+  TLB_ERR_STATE = 6      /* call out of order (e.g. step before init)        */
+} tlb_status;
+
+/* Population storage (Sec. 3.1 populations; compute precision follows):
+ * TLB_F64 -- double storage and arithmetic;
+ * TLB_F32 -- float storage of f_i - w_i (shifted by the rest-density
+ *            equilibrium) and of g_i, h_i; float arithmetic;
+ * TLB_F16 / TLB_BF16 -- binary16 / bfloat16 storage of f_i - w_i and of
+ *            g_i, h_i for i != 0, float storage of the rest populations
+ *            g_0, h_0 (they carry phi and psi themselves); float arithmetic. */
+enum { TLB_F64 = 0, TLB_F32 = 1, TLB_F16 = 2, TLB_BF16 = 3 };
+
+/* Membrane kinds: a closed ring of markers in 2D (stretching + bending,
+ * eqs. DiscreteSE, DiscreteBE) or a closed triangulated surface in 3D
+ * (Skalak shear + Helfrich bending). */
+enum { TLB_MEM_RING2D = 0, TLB_MEM_TRI3D = 1 };
+
+/* Fields for tlb_read_field (each ncells doubles, or 3*ncells for vectors
+ * laid out [component][cell]). */
+enum {
+  TLB_FIELD_RHO = 0, TLB_FIELD_PHI = 1, TLB_FIELD_PSI = 2,
+  TLB_FIELD_C1 = 3, TLB_FIELD_C2 = 4, TLB_FIELD_C3 = 5,
+  TLB_FIELD_U = 6,   /* bare velocity u = sum_i c_i f_i / rho (vector)     */
+  TLB_FIELD_I = 7    /* membrane profile I of the last step (eq. Iprofile) */
+};
+
+typedef struct {
+  int dim;            /* 2 (D2Q9, as printed in Sec. 3.1) or 3 (D3Q19)        */
+  int nx, ny, nz;     /* lattice size; nz ignored for dim = 2                 */
+  int wall_last;      /* 1: halfway bounce-back walls at both ends of the last
+                         axis (natural boundary conditions, eq. NaturalBCs);
+                         0: periodic                                         */
+  int storage;        /* TLB_F64 | TLB_F32 | TLB_F16 | TLB_BF16               */
+  double tau, tau_phi, tau_psi;     /* relaxation times (eq. RelaxationTimes) */
+  double gamma_phi, gamma_psi;      /* Gamma_phi, Gamma_psi (eq. EDF)         */
+  double alpha;                     /* interface width parameter (eq. CmProfile) */
+  double kappa[3];                  /* kappa_1..3 (eq. LandauFE)              */
+  double kappa_c;                   /* coupling strength (eq. CouplingE)      */
+  double dc;                        /* clamp of the signed distance in I     */
+  double u0[3];                     /* initial uniform velocity               */
+  double interface_pos;             /* default init: flat C1/C2 interface at
+                                       this coordinate of the last axis (C1
+                                       above); < 0: no interface (all C2)    */
+} tlb_params;
+
+typedef struct {
+  int kind;           /* TLB_MEM_RING2D | TLB_MEM_TRI3D                        */
+  int n_nodes;        /* markers                                               */
+  int n_elems;        /* triangles (3D); ignored for rings (segments l->l+1)   */
+  const double* X0;   /* host, n_nodes*3: initial positions (z ignored in 2D);
+                         also the reference (stress-free) shape               */
+  const int* elems;   /* host, n_elems*3 node indices, counter-clockwise seen
+                         from outside (3D only; NULL for rings)              */
+  double ks, kb;      /* 2D: stretching modulus kappa_s and bending modulus
+                         kappa_b (eqs. DiscreteSE, DiscreteBE); 3D: kb is the
+                         Helfrich bending modulus                            */
+  double skalak_G, skalak_C;  /* 3D Skalak shear modulus and area ratio       */
+} tlb_membrane_desc;
+
+typedef struct {
+  long step;          /* steps taken since init                                 */
+  double mass[3];     /* FP64 sums of rho, phi, psi over the lattice            */
+  double umax;        /* max |u|                                                */
+  int n_caps;         /* number of membranes                                    */
+  double area[8];     /* FP64 enclosed area (2D) / surface area (3D) per capsule */
+  double volume[8];   /* FP64 enclosed volume per capsule (3D; 0 in 2D)         */
+} tlb_diag;
+
+/* Arena size (bytes) for a lattice and its membranes.  params and mems are
+ * host pointers; n_mem membranes (at most 8).  Fails with TLB_ERR_ARG for
+ * invalid sizes (lattice dims < 4, dim not 2/3, wall not along the last axis,
+ * capsule larger than half the domain, ...). */
+tlb_status tlb_state_bytes(const tlb_params* params, const tlb_membrane_desc* mems, int n_mem,
+                           size_t* bytes);
+
+/* Create a context on the current CUDA device.  arena: device pointer to
+ * `bytes` bytes (at least tlb_state_bytes), owned by the caller.
+ * cuda_stream: a cudaStream_t (NULL = legacy default stream).  The
+ * membranes are uploaded here (their X0 is the reference shape).  The
+ * context is not usable for stepping until tlb_init_fields. */
+tlb_status tlb_create(const tlb_params* params, const tlb_membrane_desc* mems, int n_mem,
+                      void* arena, size_t bytes, void* cuda_stream, void** ctx_out);
+
+/* Initial state (the paper prints none; the reading is rho = 1, u = u0,
+ * psi = I(X0), a flat C1/C2 interface of tanh profile (eq. CmProfile) along
+ * the last axis, C1 = (1 - psi) s, C2 = (1 - psi)(1 - s), populations at
+ * equilibrium (eq. EDF) with the chemical potentials of these fields).
+ * C: host, 3*ncells doubles C1, C2, C3 (rho = C1+C2+C3, phi = C1-C2,
+ *    psi = C3), or NULL for the default fields above.
+ * u: host, 3*ncells doubles [component][cell] (z ignored in 2D), or NULL
+ *    for the uniform params->u0. */
+tlb_status tlb_init_fields(void* ctx, const double* C, const double* u);
+
+/* Advance n_steps time steps (Sec. 3: membrane forces at X(t), spreading,
+ * collision with exact-difference forcing, streaming, interpolation of
+ * v(t+dt) and marker advection).  Enqueued on the context stream. */
+tlb_status tlb_step(void* ctx, long n_steps);
+
+/* Read a field (see TLB_FIELD_*) into host memory as doubles; n_values is
+ * the capacity of dst in doubles (ncells, or 3*ncells for TLB_FIELD_U). */
+tlb_status tlb_read_field(void* ctx, int field, double* dst, size_t n_values);
+
+/* Marker positions of membrane `capsule` (n_nodes*3 doubles). */
+tlb_status tlb_read_nodes(void* ctx, int capsule, double* dst, size_t n_values);
+
+/* Overwrite the marker positions of membrane `capsule` (reference shape is
+ * unchanged). */
+tlb_status tlb_write_nodes(void* ctx, int capsule, const double* src, size_t n_values);
+
+/* Populations as doubles, layout [set f,g,h][i][cell] with the velocity
+ * ordering of the oracle/paper (D2Q9 as printed in Sec. 3.1; D3Q19: rest,
+ * +x,-x,+y,-y,+z,-z, then the edge velocities of the xy, xz, yz planes with
+ * sign pairs (+,+),(+,-),(-,+),(-,-)).  n_values = 3*Q*ncells.  Writing
+ * rounds to the storage format. */
+tlb_status tlb_read_populations(void* ctx, double* dst, size_t n_values);
+tlb_status tlb_write_populations(void* ctx, const double* src, size_t n_values);
+
+/* FP64 diagnostics of the current state (synchronises the stream). */
+tlb_status tlb_diagnostics(void* ctx, tlb_diag* out);
+
+/* Per-phase device time of n_steps steps, measured with CUDA events on the
+ * context stream around each phase (synchronises the stream).  Phases:
+ * moments (streamed-population moments), ibm (profile I, membrane and
+ * coupling forces, spreading), collide (force + collision + streaming),
+ * interp (interpolation and advection).  Times are totals in ms. */
+typedef struct {
+  long steps;
+  double ms_moments, ms_ibm, ms_collide, ms_interp;
+  long launches_per_step;
+} tlb_profile;
+tlb_status tlb_profile_steps(void* ctx, long n_steps, tlb_profile* out);
+
+/* Number of CUDA kernel launches enqueued by the last tlb_step call. */
+long tlb_last_launch_count(void* ctx);
+
+/* Release the context (the arena stays owned by the caller). */
+void tlb_destroy(void* ctx);
+
+/* Message of the last failed call on this thread ("" if none). */
+const char* tlb_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TLB_H */

@@ -669,6 +669,7 @@ bool cell_distance(const Sim& s, const Membrane& m, const Contig& cg, const int*
   for (int k = 0; k < s.dim; ++k) per[k] = is_wall_axis(s, k) ? 0 : 1;
   bool any = false;
   double best = 1e300, wsum = 0.0;
+  unsigned long long bestk = 0;
   int be = -1;
   double bb[3] = {0, 0, 0}, bP[3] = {0, 0, 0};
   std::vector<double> R(3 * m.nn);
@@ -694,7 +695,13 @@ bool cell_distance(const Sim& s, const Membrane& m, const Contig& cg, const int*
           else
             closest_tri(&R[3 * m.E[3 * e]], &R[3 * m.E[3 * e + 1]], &R[3 * m.E[3 * e + 2]], beta, P);
           double d = n3(P);
-          if (d < best) {
+          // nearest element, distances compared on a grid of 2^-34 lattice
+          // units and ties broken by the lowest element index (reading: the
+          // paper leaves ties open; exact mirror-symmetric ties would
+          // otherwise be decided by rounding)
+          unsigned long long kd = (unsigned long long)(d * 17179869184.0);
+          if (be < 0 || kd < bestk) {
+            bestk = kd;
             best = d;
             be = e;
             std::memcpy(bb, beta, sizeof(bb));

@@ -1,0 +1,219 @@
+"""GB300 ternary free-energy lattice Boltzmann + immersed boundary library.
+
+Python binding of the C ABI in ``include/tlb.h`` (``libtlb.so``).  It only
+marshals arguments: every step of the method runs in the library's CUDA
+kernels.  PyTorch supplies the device arena and the CUDA stream.
+
+The shared library is loaded on first use; if it is missing (not built) or
+no CUDA device is present the calls raise -- there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import workloads  # noqa: F401  (seeded input generators)
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libtlb.so")
+_lib = None
+
+TLB_OK = 0
+STORAGE = {"f64": 0, "f32": 1, "f16": 2, "bf16": 3}
+FIELD = {"rho": 0, "phi": 1, "psi": 2, "C1": 3, "C2": 4, "C3": 5, "u": 6, "I": 7}
+
+
+class TLBError(RuntimeError):
+    pass
+
+
+class _Params(C.Structure):
+    _fields_ = [("dim", C.c_int), ("nx", C.c_int), ("ny", C.c_int), ("nz", C.c_int),
+                ("wall_last", C.c_int), ("storage", C.c_int),
+                ("tau", C.c_double), ("tau_phi", C.c_double), ("tau_psi", C.c_double),
+                ("gamma_phi", C.c_double), ("gamma_psi", C.c_double), ("alpha", C.c_double),
+                ("kappa", C.c_double * 3), ("kappa_c", C.c_double), ("dc", C.c_double),
+                ("u0", C.c_double * 3), ("interface_pos", C.c_double)]
+
+
+class _Mem(C.Structure):
+    _fields_ = [("kind", C.c_int), ("n_nodes", C.c_int), ("n_elems", C.c_int),
+                ("X0", C.POINTER(C.c_double)), ("elems", C.POINTER(C.c_int)),
+                ("ks", C.c_double), ("kb", C.c_double),
+                ("skalak_G", C.c_double), ("skalak_C", C.c_double)]
+
+
+class Diag(C.Structure):
+    _fields_ = [("step", C.c_long), ("mass", C.c_double * 3), ("umax", C.c_double),
+                ("n_caps", C.c_int), ("area", C.c_double * 8), ("volume", C.c_double * 8)]
+
+
+class Profile(C.Structure):
+    _fields_ = [("steps", C.c_long), ("ms_moments", C.c_double), ("ms_ibm", C.c_double),
+                ("ms_collide", C.c_double), ("ms_interp", C.c_double), ("launches_per_step", C.c_long)]
+
+
+def lib():
+    """Load libtlb.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise TLBError(f"{LIB_PATH} is missing: run paper_1906_03065_gb300.build.build() first")
+        L = C.CDLL(LIB_PATH)
+        vp, dp, sz = C.c_void_p, C.POINTER(C.c_double), C.c_size_t
+        L.tlb_state_bytes.argtypes = [C.POINTER(_Params), C.POINTER(_Mem), C.c_int, C.POINTER(sz)]
+        L.tlb_create.argtypes = [C.POINTER(_Params), C.POINTER(_Mem), C.c_int, vp, sz, vp, C.POINTER(vp)]
+        L.tlb_init_fields.argtypes = [vp, dp, dp]
+        L.tlb_step.argtypes = [vp, C.c_long]
+        L.tlb_read_field.argtypes = [vp, C.c_int, dp, sz]
+        L.tlb_read_nodes.argtypes = [vp, C.c_int, dp, sz]
+        L.tlb_write_nodes.argtypes = [vp, C.c_int, dp, sz]
+        L.tlb_read_populations.argtypes = [vp, dp, sz]
+        L.tlb_write_populations.argtypes = [vp, dp, sz]
+        L.tlb_diagnostics.argtypes = [vp, C.POINTER(Diag)]
+        L.tlb_profile_steps.argtypes = [vp, C.c_long, C.POINTER(Profile)]
+        L.tlb_profile_steps.restype = C.c_int
+        L.tlb_last_launch_count.argtypes = [vp]
+        L.tlb_last_launch_count.restype = C.c_long
+        L.tlb_destroy.argtypes = [vp]
+        L.tlb_last_error.restype = C.c_char_p
+        for n in ("tlb_state_bytes", "tlb_create", "tlb_init_fields", "tlb_step", "tlb_read_field",
+                  "tlb_read_nodes", "tlb_write_nodes", "tlb_read_populations",
+                  "tlb_write_populations", "tlb_diagnostics"):
+            getattr(L, n).restype = C.c_int
+        _lib = L
+    return _lib
+
+
+def _check(st):
+    if st != TLB_OK:
+        msg = lib().tlb_last_error().decode()
+        raise TLBError(f"tlb status {st}: {msg}")
+
+
+def _dp(a):
+    return a.ctypes.data_as(C.POINTER(C.c_double))
+
+
+def make_params(p) -> _Params:
+    """``p`` is a ``workloads.Params``."""
+    cp = _Params()
+    cp.dim, cp.nx, cp.ny, cp.nz = p.dim, p.nx, p.ny, (p.nz if p.dim == 3 else 1)
+    cp.wall_last = p.wall_last
+    cp.storage = STORAGE[p.storage]
+    cp.tau, cp.tau_phi, cp.tau_psi = p.tau, p.tau_phi, p.tau_psi
+    cp.gamma_phi, cp.gamma_psi, cp.alpha = p.gamma_phi, p.gamma_psi, p.alpha
+    cp.kappa[0], cp.kappa[1], cp.kappa[2] = p.kappa1, p.kappa2, p.kappa3
+    cp.kappa_c, cp.dc = p.kappa_c, p.dc
+    for k in range(3):
+        cp.u0[k] = p.u0[k]
+    cp.interface_pos = p.interface_pos
+    return cp
+
+
+class Simulation:
+    """One lattice with its membranes on the current CUDA device.
+
+    ``wl`` is a ``workloads.Workload``.  The arena is a torch uint8 tensor on
+    ``device``; the stream is torch's current stream unless given.
+    """
+
+    def __init__(self, wl, device="cuda:0", stream=None):
+        import torch
+        L = lib()
+        self.wl = wl
+        p = wl.params
+        self.p = p
+        self._cp = make_params(p)
+        self._keep = []
+        mems = (_Mem * max(1, len(wl.membranes)))()
+        for i, m in enumerate(wl.membranes):
+            X = np.ascontiguousarray(m.X, dtype=np.float64)
+            E = np.ascontiguousarray(m.elems if m.elems is not None else np.zeros((1, 3)), dtype=np.int32)
+            self._keep += [X, E]
+            mems[i].kind = m.kind
+            mems[i].n_nodes = X.shape[0]
+            mems[i].n_elems = E.shape[0] if m.kind == 1 else 0
+            mems[i].X0 = _dp(X)
+            mems[i].elems = E.ctypes.data_as(C.POINTER(C.c_int)) if m.kind == 1 else None
+            mems[i].ks, mems[i].kb = m.ks, m.kb
+            mems[i].skalak_G, mems[i].skalak_C = m.G, m.C
+        self._mems = mems
+        self.n_mem = len(wl.membranes)
+        self.nn = [m.X.shape[0] for m in wl.membranes]
+        nbytes = C.c_size_t(0)
+        _check(L.tlb_state_bytes(C.byref(self._cp), mems, self.n_mem, C.byref(nbytes)))
+        self.nbytes = nbytes.value
+        self.device = torch.device(device)
+        with torch.cuda.device(self.device):
+            self.arena = torch.empty(self.nbytes + 256, dtype=torch.uint8, device=self.device)
+            self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+            base = self.arena.data_ptr()
+            aligned = (base + 255) // 256 * 256
+            h = C.c_void_p()
+            _check(L.tlb_create(C.byref(self._cp), mems, self.n_mem, C.c_void_p(aligned),
+                                C.c_size_t(self.nbytes), C.c_void_p(self.stream.cuda_stream), C.byref(h)))
+        self.h = h
+        self.N = p.nx * p.ny * (p.nz if p.dim == 3 else 1)
+        self.Q = 19 if p.dim == 3 else 9
+
+    def __del__(self):
+        try:
+            if getattr(self, "h", None) is not None and self.h.value:
+                lib().tlb_destroy(self.h)
+                self.h = None
+        except Exception:
+            pass
+
+    @property
+    def shape(self):
+        p = self.p
+        return (p.nz, p.ny, p.nx) if p.dim == 3 else (p.ny, p.nx)
+
+    def init(self, Cf=None, u=None):
+        cf = None if Cf is None else np.ascontiguousarray(Cf, dtype=np.float64)
+        uf = None if u is None else np.ascontiguousarray(u, dtype=np.float64)
+        _check(lib().tlb_init_fields(self.h, None if cf is None else _dp(cf), None if uf is None else _dp(uf)))
+        return self
+
+    def step(self, n: int = 1):
+        _check(lib().tlb_step(self.h, int(n)))
+
+    def launches(self) -> int:
+        return lib().tlb_last_launch_count(self.h)
+
+    def field(self, name: str) -> np.ndarray:
+        n = self.N * (3 if name == "u" else 1)
+        out = np.zeros(n)
+        _check(lib().tlb_read_field(self.h, FIELD[name], _dp(out), n))
+        return out.reshape(3, self.N) if name == "u" else out
+
+    def nodes(self, m: int = 0) -> np.ndarray:
+        out = np.zeros(3 * self.nn[m])
+        _check(lib().tlb_read_nodes(self.h, m, _dp(out), out.size))
+        return out.reshape(-1, 3)
+
+    def set_nodes(self, m: int, X):
+        X = np.ascontiguousarray(X, dtype=np.float64)
+        _check(lib().tlb_write_nodes(self.h, m, _dp(X), X.size))
+
+    def pops(self) -> np.ndarray:
+        out = np.zeros(3 * self.Q * self.N)
+        _check(lib().tlb_read_populations(self.h, _dp(out), out.size))
+        return out.reshape(3, self.Q, self.N)
+
+    def set_pops(self, P):
+        P = np.ascontiguousarray(P, dtype=np.float64).reshape(-1)
+        _check(lib().tlb_write_populations(self.h, _dp(P), P.size))
+
+    def profile(self, n: int) -> Profile:
+        pr = Profile()
+        _check(lib().tlb_profile_steps(self.h, int(n), C.byref(pr)))
+        return pr
+
+    def diagnostics(self) -> Diag:
+        d = Diag()
+        _check(lib().tlb_diagnostics(self.h, C.byref(d)))
+        return d

@@ -1,0 +1,188 @@
+// Shared device definitions of the GB300 ternary LB + IBM library.
+//
+// Internal geometry: every lattice is stored as nx * ny * nz cells with
+// linear index (z*ny + y)*nx + x.  A 2D lattice of the paper (D2Q9, Sec. 3.1)
+// is embedded as nx * 1 * ny: its y axis becomes the internal z axis, so the
+// same plane-sweep kernels serve both; markers of a 2D ring are stored as
+// (x, 0, y).  Walls, when present, bound the internal z axis.
+#pragma once
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/tlb.h"
+
+#define TLB_HD __host__ __device__ __forceinline__
+
+// ------------------------------------------------------------ velocity sets
+// D2Q9 in the order printed in Sec. 3.1, embedded in the internal (x, z) plane.
+struct D2Q9 {
+  static constexpr int Q = 9;
+  static constexpr int DIM = 2;
+  TLB_HD static constexpr int cx(int i) {
+    return i == 1 || i == 5 || i == 8 ? 1 : (i == 2 || i == 6 || i == 7 ? -1 : 0);
+  }
+  TLB_HD static constexpr int cy(int) { return 0; }
+  TLB_HD static constexpr int cz(int i) {
+    return i == 3 || i == 5 || i == 7 ? 1 : (i == 4 || i == 6 || i == 8 ? -1 : 0);
+  }
+  TLB_HD static constexpr double w(int i) {
+    return i == 0 ? 4.0 / 9.0 : (i < 5 ? 1.0 / 9.0 : 1.0 / 36.0);
+  }
+  TLB_HD static constexpr int opp(int i) {
+    return i == 0 ? 0 : (i == 1 ? 2 : i == 2 ? 1 : i == 3 ? 4 : i == 4 ? 3 : i == 5 ? 6 : i == 6 ? 5 : i == 7 ? 8 : 7);
+  }
+};
+
+// D3Q19: rest; +x,-x,+y,-y,+z,-z (w = 1/18); then the edge velocities of the
+// xy, xz and yz planes with sign pairs (+,+),(+,-),(-,+),(-,-) (w = 1/36).
+struct D3Q19 {
+  static constexpr int Q = 19;
+  static constexpr int DIM = 3;
+  TLB_HD static constexpr int comp(int i, int a) {
+    // axis velocities
+    return i == 0 ? 0
+         : i <= 6 ? ((i - 1) / 2 == a ? ((i - 1) % 2 == 0 ? 1 : -1) : 0)
+                  : edge(i - 7, a);
+  }
+  TLB_HD static constexpr int edge(int e, int a) {
+    // e = 4*plane + signs; planes (0,1), (0,2), (1,2)
+    return (a == pa(e / 4) ? ((e % 4) < 2 ? 1 : -1) : 0) + (a == pb(e / 4) ? ((e % 4) % 2 == 0 ? 1 : -1) : 0);
+  }
+  TLB_HD static constexpr int pa(int p) { return p == 2 ? 1 : 0; }
+  TLB_HD static constexpr int pb(int p) { return p == 0 ? 1 : 2; }
+  TLB_HD static constexpr int cx(int i) { return comp(i, 0); }
+  TLB_HD static constexpr int cy(int i) { return comp(i, 1); }
+  TLB_HD static constexpr int cz(int i) { return comp(i, 2); }
+  TLB_HD static constexpr double w(int i) { return i == 0 ? 1.0 / 3.0 : (i <= 6 ? 1.0 / 18.0 : 1.0 / 36.0); }
+  TLB_HD static constexpr int opp(int i) {
+    return i == 0 ? 0 : (i <= 6 ? (i % 2 == 1 ? i + 1 : i - 1) : 7 + 4 * ((i - 7) / 4) + (3 - (i - 7) % 4));
+  }
+};
+
+// ------------------------------------------------------------ precisions
+template <int MODE> struct Prec;
+template <> struct Prec<TLB_F64> { using Real = double; using Store = double; using Rest = double; };
+template <> struct Prec<TLB_F32> { using Real = float; using Store = float; using Rest = float; };
+template <> struct Prec<TLB_F16> { using Real = float; using Store = __half; using Rest = float; };
+template <> struct Prec<TLB_BF16> { using Real = float; using Store = __nv_bfloat16; using Rest = float; };
+
+TLB_HD double to_real(double v) { return v; }
+TLB_HD float to_real(float v) { return v; }
+__device__ __forceinline__ float to_real(__half v) { return __half2float(v); }
+__device__ __forceinline__ float to_real(__nv_bfloat16 v) { return __bfloat162float(v); }
+
+template <class S> __device__ __forceinline__ S from_real(double v);
+template <class S> __device__ __forceinline__ S from_real(float v);
+template <> __device__ __forceinline__ double from_real<double>(double v) { return v; }
+template <> __device__ __forceinline__ float from_real<float>(float v) { return v; }
+template <> __device__ __forceinline__ __half from_real<__half>(float v) { return __float2half_rn(v); }
+template <> __device__ __forceinline__ __nv_bfloat16 from_real<__nv_bfloat16>(float v) { return __float2bfloat16_rn(v); }
+
+// ------------------------------------------------------------ geometry
+struct Geo {
+  int nx, ny, nz;
+  int wall;        // walls at both ends of z
+  long long N;     // cells
+  long long P;     // plane stride of population / field arrays (>= N, padded)
+};
+
+TLB_HD int wrapc(int a, int n) { return a < 0 ? a + n : (a >= n ? a - n : a); }
+
+// Population layout: `lo` holds 3Q-2 planes of Store -- f_0..f_{Q-1} stored
+// as f_i - w_i, then g_1..g_{Q-1}, then h_1..h_{Q-1}; `rest` holds g_0, h_0 in
+// the Rest type.  Plane k of `lo` starts at lo + k*P.
+template <class L> TLB_HD int plane_f(int i) { return i; }
+template <class L> TLB_HD int plane_g(int i) { return L::Q + i - 1; }
+template <class L> TLB_HD int plane_h(int i) { return 2 * L::Q - 1 + i - 1; }
+
+template <class Real>
+struct CellMoments {
+  Real drho;     // rho - 1 (sum of the stored deviations)
+  Real j[3];     // sum_i c_i f_i
+  Real phi, psi;
+};
+
+// Pull of the populations arriving at cell (x, y, z): f_i(x) = f*_i(x - c_i);
+// across a wall, halfway bounce-back returns f*_{opp(i)}(x).  Both the moment
+// kernel and the collision kernel use this routine so they agree bit for bit.
+template <class L, int MODE>
+struct Pull {
+  using Real = typename Prec<MODE>::Real;
+  using Store = typename Prec<MODE>::Store;
+  using Rest = typename Prec<MODE>::Rest;
+  Real f[L::Q], g[L::Q], h[L::Q];  // f holds f_i - w_i
+
+  __device__ __forceinline__ void load(const Store* __restrict__ lo, const Rest* __restrict__ rest,
+                                       const Geo& G, int x, int y, int z) {
+    const long long self = ((long long)z * G.ny + y) * G.nx + x;
+#pragma unroll
+    for (int i = 0; i < L::Q; ++i) {
+      int sx = wrapc(x - L::cx(i), G.nx);
+      int sy = wrapc(y - L::cy(i), G.ny);
+      int szr = z - L::cz(i);
+      long long src;
+      int ii = i;
+      if (G.wall && (szr < 0 || szr >= G.nz)) {
+        src = self;
+        ii = L::opp(i);
+      } else {
+        src = ((long long)wrapc(szr, G.nz) * G.ny + sy) * G.nx + sx;
+      }
+      f[i] = to_real(__ldg(lo + (long long)plane_f<L>(ii) * G.P + src));
+      if (ii == 0) {
+        g[i] = to_real(__ldg(rest + src));
+        h[i] = to_real(__ldg(rest + G.P + src));
+      } else {
+        g[i] = to_real(__ldg(lo + (long long)plane_g<L>(ii) * G.P + src));
+        h[i] = to_real(__ldg(lo + (long long)plane_h<L>(ii) * G.P + src));
+      }
+    }
+  }
+
+  __device__ __forceinline__ CellMoments<Real> moments() const {
+    CellMoments<Real> m;
+    Real r = 0, jx = 0, jy = 0, jz = 0, p = 0, s = 0;
+#pragma unroll
+    for (int i = 0; i < L::Q; ++i) {
+      r += f[i];
+      if (L::cx(i)) jx += L::cx(i) > 0 ? f[i] : -f[i];
+      if (L::cy(i)) jy += L::cy(i) > 0 ? f[i] : -f[i];
+      if (L::cz(i)) jz += L::cz(i) > 0 ? f[i] : -f[i];
+      p += g[i];
+      s += h[i];
+    }
+    m.drho = r;
+    m.j[0] = jx;
+    m.j[1] = jy;
+    m.j[2] = jz;
+    m.phi = p;
+    m.psi = s;
+    return m;
+  }
+};
+
+// Chemical potentials of App. A (eq. AppA) without the ideal-gas part of
+// mu_rho; mu_psi' adds kappa_c (psi - I) (Sec. 3.1).
+template <class Real>
+struct FEParams {
+  Real k1, k2, k3, kc, a2;  // kappa_1..3, kappa_c, alpha^2
+};
+template <class Real>
+__device__ __forceinline__ void chem_potentials(const FEParams<Real>& fe, Real rho, Real phi, Real psi,
+                                                Real Lr, Real Lp, Real Ls, Real I, Real& mr,
+                                                Real& mp, Real& ms) {
+  Real A = rho + phi - psi, B = rho - phi - psi;
+  Real tA = fe.k1 * Real(0.125) * A * (A - Real(1)) * (A - Real(2));
+  Real tB = fe.k2 * Real(0.125) * B * (B - Real(1)) * (B - Real(2));
+  Real q = Real(0.25) * fe.a2;
+  Real kp = fe.k1 + fe.k2, km = fe.k2 - fe.k1;
+  mr = tA + tB + q * (kp * (Ls - Lr) + km * Lp);
+  mp = tA - tB + q * (km * (Lr - Ls) - kp * Lp);
+  ms = -tA - tB + q * (kp * Lr - km * Lp - (kp + Real(4) * fe.k3) * Ls) +
+       fe.k3 * psi * (psi - Real(1)) * (Real(2) * psi - Real(1)) + fe.kc * (psi - I);
+}
+
+// Status flags written by kernels (bitwise OR into a device word).
+enum { ST_NAN = 1, ST_MARKER_JUMP = 2, ST_TIMEOUT = 4, ST_OVERFLOW = 8 };

@@ -1,0 +1,105 @@
+// Host-side context of the library: the arena layout and the per-context
+// state.  The caller's arena is carved into fixed regions once, at
+// tlb_create; no other device memory is ever allocated.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/tlb.h"
+
+struct Ctx;
+
+struct ImplBase {
+  virtual ~ImplBase() {}
+  virtual tlb_status init_fields(Ctx* c, const double* C, const double* u) = 0;
+  virtual tlb_status step(Ctx* c, long n) = 0;
+  virtual tlb_status read_field(Ctx* c, int field, double* dst, size_t n) = 0;
+  virtual tlb_status read_pops(Ctx* c, double* dst) = 0;
+  virtual tlb_status write_pops(Ctx* c, const double* src) = 0;
+  virtual tlb_status diagnostics(Ctx* c, tlb_diag* out) = 0;
+};
+
+// CUDA events bracketing the phases of a step when profiling.
+struct PhaseEvents {
+  cudaEvent_t ev[5];
+  bool on = false;
+};
+
+// Sizes in bytes of the precision-dependent element types.
+struct TypeSizes {
+  size_t real, store, rest;
+};
+
+// One region of the arena.
+struct Region {
+  size_t off = 0, bytes = 0;
+};
+
+struct Layout {
+  // lattice
+  Region lo[2], rest[2];
+  Region rho, phi, psi, I, dsel, own, key, fib, ftot, mu, rb;
+  // membranes
+  Region X, E, ecap, ncap, cap_par, ds0, rprev, rnext, A0, G0i, inc_off, inc, adj, edges;
+  Region en, vn, esum, F, box;
+  Region bcnt, bprev, bcur, boff, blist, bact, ctr;
+  // misc
+  Region status, part, meas;
+  size_t total = 0;
+};
+
+struct HostMem {
+  int kind, nn, ne;
+  std::vector<double> X0;  // internal coordinates, unwrapped along edges
+  std::vector<int> E;
+  double ks, kb, G, C;
+};
+
+struct Ctx {
+  tlb_params p;
+  int Q = 0;
+  int nx = 0, ny = 0, nz = 0;  // internal sizes (2D: nx, 1, ny)
+  long long N = 0, P = 0;
+  TypeSizes ts{};
+  Layout L;
+  char* base = nullptr;
+  size_t bytes = 0;
+  cudaStream_t stream = nullptr;
+  int cur = 0;  // population buffer holding the current state
+  long t = 0;
+  bool initialised = false;
+  long launches = 0;
+  // membranes
+  std::vector<HostMem> mems;
+  int nn = 0, ne = 0, NV = 0, ncap = 0, nedge = 0;
+  int nbx = 0, nby = 0, nbz = 0, nbricks = 0;
+  int tiles_zc = 16;
+  PhaseEvents* prof = nullptr;  // non-null while tlb_profile_steps runs
+  double prof_ms[4] = {0, 0, 0, 0};
+  ImplBase* impl = nullptr;
+
+  template <class T> T* ptr(const Region& r) const { return reinterpret_cast<T*>(base + r.off); }
+};
+
+void set_error(const std::string& msg);
+tlb_status cuda_check(cudaError_t e, const char* what);
+#define TLB_CUDA(call)                                              \
+  do {                                                              \
+    tlb_status _s = cuda_check((call), #call);                      \
+    if (_s != TLB_OK) return _s;                                    \
+  } while (0)
+#define TLB_LAUNCHED(ctx, what)                                     \
+  do {                                                              \
+    (ctx)->launches++;                                              \
+    tlb_status _s = cuda_check(cudaGetLastError(), what);           \
+    if (_s != TLB_OK) return _s;                                    \
+  } while (0)
+
+ImplBase* make_impl_d2q9_f64();
+ImplBase* make_impl_d2q9_f32();
+ImplBase* make_impl_d3q19_f32();
+ImplBase* make_impl_d3q19_f16();
+ImplBase* make_impl_d3q19_bf16();

@@ -1,0 +1,952 @@
+// Immersed-boundary kernels: membrane profile I (eq. Iprofile), coupling
+// force (eqs. DiscreteCE, DiscreteCF), elastic forces (2D: eqs. DiscreteSE,
+// DiscreteBE; 3D: Skalak shear and Helfrich bending), spreading (eq.
+// Spreading with eq. DiscreteDirac), interpolation and advection (eqs.
+// Interpolation, UpdatedXl).
+#pragma once
+#include "tlb_common.cuh"
+
+constexpr unsigned long long KEY_NONE = ~0ull;
+constexpr int BRICK = 4;  // spreading bins are 4x4x4 cells (4x1x4 in 2D)
+
+template <class Real>
+struct IBArgs {
+  Geo G;
+  int dim, NV;  // dim 2: segments (NV = 2); dim 3: triangles (NV = 3)
+  int nn, ne;
+  double* X;             // [nn][3] unwrapped positions
+  const int* E;          // [ne][NV]
+  const int* ecap;       // element -> capsule
+  const int* ncap;       // node -> capsule
+  const double* ks;      // per capsule
+  const double* kb;
+  const double* sG;
+  const double* sC;
+  const double* ds0;     // 2D: rest length of segment e
+  const int* rprev;      // 2D: previous node on the ring
+  const int* rnext;      // 2D: next node on the ring
+  const double* A0;      // 3D: reference area per triangle
+  const double* G0i;     // 3D: inverse reference metric per triangle (3)
+  const int* inc_off;    // node -> incident elements (CSR, ascending)
+  const int* inc;
+  const int* adj;        // 3D: triangle across edge q (q: vertex q -> q+1)
+  int nedge;             // 3D: unique edges
+  const int* edges;      // 3D: [nedge][4] vertex a, vertex b, face left, face right
+  // per-step work
+  Real* en;              // [ne][3] unit outward normal
+  Real* vn;              // [nn][3] angle-weighted vertex pseudo-normal
+  unsigned long long* esum;  // [ne][NV][3] coupling contributions, fixed point (CPL_SCALE)
+  Real* F;               // [nn][3] node force
+  int* box;              // [6] lo xyz, hi xyz (unwrapped, inclusive)
+  unsigned long long* key;
+  int* own;
+  Real* I;
+  Real* dsel;
+  const Real* psi;
+  Real* fib;             // [3][P]
+  const Real* ftot;      // [3][P]
+  int* bcnt;             // bricks: count, previous count, cursor, offset
+  int* bprev;
+  int* bcur;
+  int* boff;
+  int* blist;
+  int* bact;             // active bricks (compacted list)
+  int* ctr;              // [0] active bricks, [1] list slots claimed
+  int nbx, nby, nbz, nbricks;
+  Real alpha, dc, kc;
+  unsigned* status;
+};
+
+// ------------------------------------------------------------ small vectors
+template <class T> struct V3 { T x, y, z; };
+template <class T> TLB_HD V3<T> mk(T a, T b, T c) { return {a, b, c}; }
+template <class T> TLB_HD V3<T> operator+(V3<T> a, V3<T> b) { return {a.x + b.x, a.y + b.y, a.z + b.z}; }
+template <class T> TLB_HD V3<T> operator-(V3<T> a, V3<T> b) { return {a.x - b.x, a.y - b.y, a.z - b.z}; }
+template <class T> TLB_HD V3<T> operator*(T s, V3<T> a) { return {s * a.x, s * a.y, s * a.z}; }
+template <class T> TLB_HD T dot(V3<T> a, V3<T> b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
+template <class T> TLB_HD V3<T> cross(V3<T> a, V3<T> b) {
+  return {a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x};
+}
+
+template <class Real>
+__device__ __forceinline__ V3<Real> node_rel(const double* X, int k, double ox, double oy, double oz) {
+  return mk<Real>((Real)(X[3 * k] - ox), (Real)(X[3 * k + 1] - oy), (Real)(X[3 * k + 2] - oz));
+}
+
+// Closest point of the origin on segment (a, b) or triangle (a, b, c)
+// (Voronoi-region classification).  Returns the barycentric weights and
+// the feature: 0 interior, 1..3 edge starting at vertex feat-1, 4..6 vertex feat-4.
+template <class Real>
+__device__ __forceinline__ V3<Real> closest_on_seg(V3<Real> a, V3<Real> b, Real* beta, int* feat) {
+  V3<Real> ab = b - a;
+  Real l2 = dot(ab, ab);
+  Real t = l2 > Real(0) ? -dot(a, ab) / l2 : Real(0);
+  if (t <= Real(0)) { t = 0; *feat = 4; }
+  else if (t >= Real(1)) { t = 1; *feat = 5; }
+  else *feat = 0;
+  beta[0] = Real(1) - t;
+  beta[1] = t;
+  beta[2] = 0;
+  return a + t * ab;
+}
+
+template <class Real>
+__device__ __forceinline__ V3<Real> closest_on_tri(V3<Real> a, V3<Real> b, V3<Real> c, Real* beta, int* feat) {
+  // p = origin
+  V3<Real> ab = b - a, ac = c - a;
+  V3<Real> ap = mk<Real>(-a.x, -a.y, -a.z);
+  Real d1 = dot(ab, ap), d2 = dot(ac, ap);
+  if (d1 <= 0 && d2 <= 0) { beta[0] = 1; beta[1] = 0; beta[2] = 0; *feat = 4; return a; }
+  V3<Real> bp = mk<Real>(-b.x, -b.y, -b.z);
+  Real d3 = dot(ab, bp), d4 = dot(ac, bp);
+  if (d3 >= 0 && d4 <= d3) { beta[0] = 0; beta[1] = 1; beta[2] = 0; *feat = 5; return b; }
+  Real vc = d1 * d4 - d3 * d2;
+  if (vc <= 0 && d1 >= 0 && d3 <= 0) {
+    Real v = d1 / (d1 - d3);
+    beta[0] = 1 - v; beta[1] = v; beta[2] = 0; *feat = 1;
+    return a + v * ab;
+  }
+  V3<Real> cp = mk<Real>(-c.x, -c.y, -c.z);
+  Real d5 = dot(ab, cp), d6 = dot(ac, cp);
+  if (d6 >= 0 && d5 <= d6) { beta[0] = 0; beta[1] = 0; beta[2] = 1; *feat = 6; return c; }
+  Real vb = d5 * d2 - d1 * d6;
+  if (vb <= 0 && d2 >= 0 && d6 <= 0) {
+    Real w = d2 / (d2 - d6);
+    beta[0] = 1 - w; beta[1] = 0; beta[2] = w; *feat = 3;  // edge c -> a
+    return a + w * ac;
+  }
+  Real va = d3 * d6 - d5 * d4;
+  if (va <= 0 && (d4 - d3) >= 0 && (d5 - d6) >= 0) {
+    Real w = (d4 - d3) / ((d4 - d3) + (d5 - d6));
+    beta[0] = 0; beta[1] = 1 - w; beta[2] = w; *feat = 2;  // edge b -> c
+    return b + w * (c - b);
+  }
+  Real den = Real(1) / (va + vb + vc);
+  Real v = vb * den, w = vc * den;
+  beta[0] = 1 - v - w; beta[1] = v; beta[2] = w; *feat = 0;
+  return a + v * ab + w * ac;
+}
+
+// Closest point of cell (cx, cy, cz) (unwrapped) on element e.
+template <class Real>
+__device__ __forceinline__ V3<Real> elem_closest(const IBArgs<Real>& a, int e, double cx, double cy, double cz,
+                                                 Real* beta, int* feat) {
+  if (a.NV == 2) {
+    V3<Real> p0 = node_rel<Real>(a.X, a.E[2 * e], cx, cy, cz);
+    V3<Real> p1 = node_rel<Real>(a.X, a.E[2 * e + 1], cx, cy, cz);
+    return closest_on_seg(p0, p1, beta, feat);
+  }
+  V3<Real> p0 = node_rel<Real>(a.X, a.E[3 * e], cx, cy, cz);
+  V3<Real> p1 = node_rel<Real>(a.X, a.E[3 * e + 1], cx, cy, cz);
+  V3<Real> p2 = node_rel<Real>(a.X, a.E[3 * e + 2], cx, cy, cz);
+  return closest_on_tri(p0, p1, p2, beta, feat);
+}
+
+// ------------------------------------------------------------ geometry pass
+// Unit outward element normals.  2D segments in the internal (x, z) plane:
+// tangent t = (tx, 0, tz), outward normal (tz, 0, -tx) for a counter-clockwise ring.
+template <class Real>
+__global__ void k_elem_normals(IBArgs<Real> a) {
+  int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= a.ne) return;
+  V3<Real> n;
+  if (a.NV == 2) {
+    int p = a.E[2 * e], q = a.E[2 * e + 1];
+    Real tx = (Real)(a.X[3 * q] - a.X[3 * p]), tz = (Real)(a.X[3 * q + 2] - a.X[3 * p + 2]);
+    Real l = sqrt(tx * tx + tz * tz);
+    n = mk<Real>(tz / l, Real(0), -tx / l);
+  } else {
+    int p = a.E[3 * e], q = a.E[3 * e + 1], r = a.E[3 * e + 2];
+    V3<Real> b = node_rel<Real>(a.X, q, a.X[3 * p], a.X[3 * p + 1], a.X[3 * p + 2]);
+    V3<Real> c = node_rel<Real>(a.X, r, a.X[3 * p], a.X[3 * p + 1], a.X[3 * p + 2]);
+    V3<Real> cr = cross(b, c);
+    Real l = sqrt(dot(cr, cr));
+    n = (Real(1) / l) * cr;
+  }
+  a.en[3 * e] = n.x;
+  a.en[3 * e + 1] = n.y;
+  a.en[3 * e + 2] = n.z;
+}
+
+// Vertex pseudo-normals: angle-weighted sum of the incident face normals
+// (Baerentzen and Aanaes 2005); in 2D the sum of the two segment normals.
+template <class Real>
+__global__ void k_vertex_normals(IBArgs<Real> a) {
+  int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= a.nn) return;
+  V3<Real> s = mk<Real>(0, 0, 0);
+  for (int j = a.inc_off[k]; j < a.inc_off[k + 1]; ++j) {
+    int e = a.inc[j];
+    V3<Real> n = mk<Real>(a.en[3 * e], a.en[3 * e + 1], a.en[3 * e + 2]);
+    Real wgt = 1;
+    if (a.NV == 3) {
+      int q0 = a.E[3 * e], q1 = a.E[3 * e + 1], q2 = a.E[3 * e + 2];
+      int u = q0 == k ? q1 : (q1 == k ? q2 : q0);
+      int v = q0 == k ? q2 : (q1 == k ? q0 : q1);
+      V3<Real> eu = node_rel<Real>(a.X, u, a.X[3 * k], a.X[3 * k + 1], a.X[3 * k + 2]);
+      V3<Real> ev = node_rel<Real>(a.X, v, a.X[3 * k], a.X[3 * k + 1], a.X[3 * k + 2]);
+      Real c = dot(eu, ev) / sqrt(dot(eu, eu) * dot(ev, ev));
+      wgt = acos(fmin(Real(1), fmax(Real(-1), c)));
+    }
+    s = s + wgt * n;
+  }
+  a.vn[3 * k] = s.x;
+  a.vn[3 * k + 1] = s.y;
+  a.vn[3 * k + 2] = s.z;
+}
+
+// Bounding box of all markers, widened by dc + 2 cells (unwrapped; walls clamp z).
+template <class Real>
+__global__ void k_box(IBArgs<Real> a) {
+  __shared__ double lo[3][256], hi[3][256];
+  double l[3] = {1e300, 1e300, 1e300}, h[3] = {-1e300, -1e300, -1e300};
+  for (int k = threadIdx.x; k < a.nn; k += blockDim.x)
+    for (int d = 0; d < 3; ++d) {
+      l[d] = fmin(l[d], a.X[3 * k + d]);
+      h[d] = fmax(h[d], a.X[3 * k + d]);
+    }
+  for (int d = 0; d < 3; ++d) { lo[d][threadIdx.x] = l[d]; hi[d][threadIdx.x] = h[d]; }
+  __syncthreads();
+  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+    if (threadIdx.x < s)
+      for (int d = 0; d < 3; ++d) {
+        lo[d][threadIdx.x] = fmin(lo[d][threadIdx.x], lo[d][threadIdx.x + s]);
+        hi[d][threadIdx.x] = fmax(hi[d][threadIdx.x], hi[d][threadIdx.x + s]);
+      }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    const int n[3] = {a.G.nx, a.G.ny, a.G.nz};
+    const int m = (int)ceil((double)a.dc) + 2;
+    for (int d = 0; d < 3; ++d) {
+      double fl = fmax(-1e8, fmin(1e8, lo[d][0])), fh = fmax(-1e8, fmin(1e8, hi[d][0]));
+      int bl = (int)floor(fl) - m, bh = (int)ceil(fh) + m;
+      if (d == 1 && a.dim == 2) { bl = 0; bh = 0; }
+      if (d == 2 && a.G.wall) { bl = max(bl, 0); bh = min(bh, n[2] - 1); }
+      if (bh - bl + 1 > n[d]) bh = bl + n[d] - 1;
+      if (bh < bl) bh = bl;
+      a.box[d] = bl;
+      a.box[3 + d] = bh;
+    }
+  }
+}
+
+template <class Real>
+__device__ __forceinline__ long long cell_of(const IBArgs<Real>& a, const int* pc) {
+  if (a.G.wall && (pc[2] < 0 || pc[2] >= a.G.nz)) return -1;
+  int x = ((pc[0] % a.G.nx) + a.G.nx) % a.G.nx;
+  int y = ((pc[1] % a.G.ny) + a.G.ny) % a.G.ny;
+  int z = ((pc[2] % a.G.nz) + a.G.nz) % a.G.nz;
+  return ((long long)z * a.G.ny + y) * a.G.nx + x;
+}
+
+// ------------------------------------------------------------ distance scatter
+// Every cell within dc of the membrane must receive the key (distance,
+// element) of its nearest element; keys are combined with atomicMin.  The
+// nearest point P of a cell x lies in the interior of a face, in the
+// interior of an edge or on a vertex, and x - P lies in the normal cone of
+// that feature: the face normal, the wedge of the two face normals of an
+// edge, the cone of the face normals around a vertex (in 2D: segment normal,
+// and the fan of the two segment normals at a marker).  Each feature sweeps
+// the cells x = P + t m, P on the feature, m in its cone (either sign),
+// |t| < dc, and offers every cell the exact distance to the faces that
+// contain the feature.  The sweep runs slice by slice along an axis k in
+// which all cone generators have a component of one sign; on slice x_k = c
+// the region lies in the convex hull of the points where the rays from the
+// feature's corners along the generators meet the slice, whose bounding box
+// is enumerated.  Distances are compared on a grid of 2^-34 lattice units,
+// ties going to the lowest element index.
+constexpr int MAXG = 12;  // generators (and faces) per feature
+constexpr int SCATTER_WARPS = 4;
+
+// Feature f: its corners, cone generators (unit normals) and the faces
+// containing it.  Returns the number of generators.
+template <class Real>
+__device__ __forceinline__ int feature_info(const IBArgs<Real>& a, int f, int* corners, int* nB, int* tri, int* nT) {
+  const int NV = a.NV;
+  *nT = 0;
+  if (f < a.ne) {  // face (3D) or segment (2D)
+    for (int q = 0; q < NV; ++q) corners[q] = a.E[NV * f + q];
+    *nB = NV;
+    tri[(*nT)++] = f;
+    return 1;
+  }
+  f -= a.ne;
+  if (NV == 3 && f < a.nedge) {  // edge
+    const int* ed = a.edges + 4 * f;
+    corners[0] = ed[0];
+    corners[1] = ed[1];
+    *nB = 2;
+    tri[(*nT)++] = ed[2];
+    tri[(*nT)++] = ed[3];
+    return 2;
+  }
+  if (NV == 3) f -= a.nedge;
+  corners[0] = f;  // vertex
+  *nB = 1;
+  for (int j = a.inc_off[f]; j < a.inc_off[f + 1] && *nT < MAXG; ++j) tri[(*nT)++] = a.inc[j];
+  return *nT;
+}
+
+// One warp per feature.  Geometry is in Real relative to an integer origin
+// (the lattice cell below the first corner), so the FP32 build does its
+// sweep in single precision without losing accuracy; slice boxes are widened
+// by 1e-3 cells to stay conservative under rounding.
+template <class Real>
+__global__ void __launch_bounds__(SCATTER_WARPS * 32) k_dist_scatter(IBArgs<Real> a) {
+  __shared__ Real sV[SCATTER_WARPS][MAXG][3][3];  // vertices of the feature's faces
+  __shared__ Real sG[SCATTER_WARPS][MAXG][3];     // cone generators
+  __shared__ Real sB[SCATTER_WARPS][3][3];        // feature corners
+  __shared__ int sT[SCATTER_WARPS][MAXG];
+  const int nfeat = a.ne + (a.NV == 3 ? a.nedge : 0) + a.nn;
+  const int w = threadIdx.x >> 5;
+  const int f = blockIdx.x * SCATTER_WARPS + w;
+  const int lane = threadIdx.x & 31;
+  if (f >= nfeat) return;
+  int corners[3], tri[MAXG], nB, nT;
+  const int nG = feature_info(a, f, corners, &nB, tri, &nT);
+  int o[3];
+  for (int d = 0; d < 3; ++d) o[d] = (int)floor(fmax(-1e8, fmin(1e8, a.X[3 * corners[0] + d])));
+  if (a.dim == 2) o[1] = 0;
+  // stage the feature in shared memory (positions relative to o)
+  for (int idx = lane; idx < nT * 9; idx += 32) {
+    int j = idx / 9, q = (idx / 3) % 3, d = idx % 3;
+    if (q < a.NV) sV[w][j][q][d] = (Real)(a.X[3 * a.E[a.NV * tri[j] + q] + d] - (double)o[d]);
+  }
+  for (int idx = lane; idx < nG * 3; idx += 32) sG[w][idx / 3][idx % 3] = a.en[3 * tri[idx / 3] + idx % 3];
+  for (int idx = lane; idx < nB * 3; idx += 32)
+    sB[w][idx / 3][idx % 3] = (Real)(a.X[3 * corners[idx / 3] + idx % 3] - (double)o[idx % 3]);
+  if (lane < nT) sT[w][lane] = tri[lane];
+  __syncwarp();
+  const Real dc = a.dc;
+  // slice axis: largest component of the generator sum, all generators of one sign
+  Real S[3] = {0, 0, 0};
+  bool finite = true;
+  for (int j = 0; j < nG; ++j)
+    for (int d = 0; d < 3; ++d) {
+      S[d] += sG[w][j][d];
+      finite &= fabs(sG[w][j][d]) <= Real(1.001);
+    }
+  for (int q = 0; q < nB; ++q)
+    for (int d = 0; d < 3; ++d) finite &= fabs(sB[w][q][d]) < Real(1e6);  // rejects NaN/Inf
+  if (!finite) {
+    if (lane == 0) atomicOr(a.status, (unsigned)ST_NAN);
+    return;
+  }
+  int k = 0;
+  if (a.dim == 3) {
+    if (fabs(S[1]) > fabs(S[k])) k = 1;
+    if (fabs(S[2]) > fabs(S[k])) k = 2;
+  } else {
+    k = fabs(S[2]) > fabs(S[0]) ? 2 : 0;
+  }
+  Real gmin = 1e30f;
+  for (int j = 0; j < nG; ++j) gmin = fmin(gmin, sG[w][j][k] * (S[k] >= 0 ? Real(1) : Real(-1)));
+  int oa, ob;
+  if (a.dim == 3) { oa = k == 0 ? 1 : 0; ob = k == 2 ? 1 : 2; }
+  else { oa = k == 0 ? 2 : 0; ob = 1; }
+  Real bmin = 1e30f, bmax = -1e30f;
+  for (int q = 0; q < nB; ++q) { bmin = fmin(bmin, sB[w][q][k]); bmax = fmax(bmax, sB[w][q][k]); }
+  const Real eps = Real(1e-3);
+  const int c0 = (int)ceil(bmin - dc - eps), c1 = (int)floor(bmax + dc + eps);
+  const bool wide = gmin < Real(0.25);  // a generator nearly parallel to the slices
+  for (int c = c0; c <= c1; ++c) {
+    Real lo0 = 1e30f, hi0 = -1e30f, lo1 = 1e30f, hi1 = -1e30f;
+    for (int q = 0; q < nB; ++q) {
+      if (!wide) {
+        for (int j = 0; j < nG; ++j) {
+          Real t = ((Real)c - sB[w][q][k]) / sG[w][j][k];
+          Real pa = sB[w][q][oa] + t * sG[w][j][oa], pb = sB[w][q][ob] + t * sG[w][j][ob];
+          lo0 = fmin(lo0, pa); hi0 = fmax(hi0, pa);
+          lo1 = fmin(lo1, pb); hi1 = fmax(hi1, pb);
+        }
+      } else {  // conservative: the feature's box widened by dc
+        lo0 = fmin(lo0, sB[w][q][oa] - dc); hi0 = fmax(hi0, sB[w][q][oa] + dc);
+        lo1 = fmin(lo1, sB[w][q][ob] - dc); hi1 = fmax(hi1, sB[w][q][ob] + dc);
+      }
+    }
+    const int a0 = (int)ceil(lo0 - eps), a1 = (int)floor(hi0 + eps);
+    int b0 = 0, b1 = 0;
+    if (a.dim == 3) { b0 = (int)ceil(lo1 - eps); b1 = (int)floor(hi1 + eps); }
+    const int wa = a1 - a0 + 1, wb = b1 - b0 + 1;
+    if (wa <= 0 || wb <= 0) continue;
+    if (wa > 1024 || wb > 1024) {  // bounded work even for a badly deformed mesh
+      if (lane == 0) atomicOr(a.status, (unsigned)ST_OVERFLOW);
+      continue;
+    }
+    for (int idx = lane; idx < wa * wb; idx += 32) {
+      int r[3];
+      r[k] = c;
+      r[oa] = a0 + idx % wa;
+      if (a.dim == 3) r[ob] = b0 + idx / wa; else r[1] = 0;
+      int pc[3] = {o[0] + r[0], o[1] + r[1], o[2] + r[2]};
+      long long cell = cell_of(a, pc);
+      if (cell < 0) continue;
+      const Real xr = (Real)r[0], yr = (Real)r[1], zr = (Real)r[2];
+      unsigned long long best = KEY_NONE;
+      for (int j = 0; j < nT; ++j) {
+        Real beta[3];
+        int feat;
+        V3<Real> p0 = mk<Real>(sV[w][j][0][0] - xr, sV[w][j][0][1] - yr, sV[w][j][0][2] - zr);
+        V3<Real> p1 = mk<Real>(sV[w][j][1][0] - xr, sV[w][j][1][1] - yr, sV[w][j][1][2] - zr);
+        V3<Real> P;
+        if (a.NV == 2) {
+          P = closest_on_seg(p0, p1, beta, &feat);
+        } else {
+          V3<Real> p2 = mk<Real>(sV[w][j][2][0] - xr, sV[w][j][2][1] - yr, sV[w][j][2][2] - zr);
+          P = closest_on_tri(p0, p1, p2, beta, &feat);
+        }
+        Real d = sqrt(dot(P, P));
+        if (!(d < dc)) continue;
+        unsigned long long key = ((unsigned long long)(d * Real(17179869184.0)) << 24) | (unsigned long long)sT[w][j];
+        best = key < best ? key : best;
+      }
+      if (best != KEY_NONE && best < a.key[cell]) atomicMin(a.key + cell, best);
+    }
+  }
+}
+
+// Sign of x - P relative to the membrane at the closest feature (interior:
+// element normal; edge: sum of the two adjacent normals; vertex: vertex
+// pseudo-normal): +1 inside (d > 0 in eq. Iprofile), -1 outside.
+template <class Real>
+__device__ __forceinline__ Real feature_sign(const IBArgs<Real>& a, int e, int feat, V3<Real> xmP) {
+  V3<Real> N;
+  if (feat == 0) {
+    N = mk<Real>(a.en[3 * e], a.en[3 * e + 1], a.en[3 * e + 2]);
+  } else if (a.NV == 3 && feat <= 3) {
+    int f = a.adj[3 * e + (feat - 1)];
+    N = mk<Real>(a.en[3 * e] + a.en[3 * f], a.en[3 * e + 1] + a.en[3 * f + 1], a.en[3 * e + 2] + a.en[3 * f + 2]);
+  } else {
+    int q = feat - 4;
+    int k = a.E[a.NV * e + q];
+    N = mk<Real>(a.vn[3 * k], a.vn[3 * k + 1], a.vn[3 * k + 2]);
+  }
+  // x - P points outward for a cell outside
+  return dot(xmP, N) > Real(0) ? Real(-1) : Real(1);
+}
+
+// Fixed-point scale of the coupling sums: integer additions make the
+// per-element totals independent of the order of the contributions.
+#define CPL_SCALE 1125899906842624.0  // 2^50
+
+// Band cells of the marker box (one thread per cell, x fastest): signed
+// distance from the nearest element, I = (1 + tanh(d/(2 alpha)))/2 (eq.
+// Iprofile), owner element, and the coupling force contributions (eq.
+// DiscreteCF from eq. DiscreteCE): node k of the owner receives
+//   kappa_c (psi - I) sech^2(d/(2 alpha))/(4 alpha) * (-s beta_k (x - P)/|x - P|),
+// summed per element in fixed point (lanes of a warp with the same element
+// are combined before one atomic).  Cells without a key are marked -1 for
+// the column fill; keys are cleared for the next step.
+template <class Real>
+__global__ void k_band(IBArgs<Real> a) {
+  const int bx0 = a.box[0], by0 = a.box[1], bz0 = a.box[2];
+  const int wx = a.box[3] - bx0 + 1, wy = a.box[4] - by0 + 1, wz = a.box[5] - bz0 + 1;
+  const long long total = (long long)wx * wy * wz;
+  const Real al = a.alpha;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long t0 = (long long)blockIdx.x * blockDim.x; t0 < total; t0 += stride) {
+    const long long t = t0 + threadIdx.x;
+    int e = -1;
+    Real acc[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+    if (t < total) {
+      int pc[3] = {bx0 + (int)(t % wx), by0 + (int)((t / wx) % wy), bz0 + (int)(t / ((long long)wx * wy))};
+      long long c = cell_of(a, pc);
+      if (c >= 0) {
+        unsigned long long key = a.key[c];
+        if (key == KEY_NONE) {
+          a.own[c] = -1;
+        } else {
+          e = (int)(key & 0xFFFFFF);
+          a.key[c] = KEY_NONE;
+          Real beta[3];
+          int feat;
+          V3<Real> P = elem_closest(a, e, (double)pc[0], (double)pc[1], (double)pc[2], beta, &feat);
+          V3<Real> xmP = mk<Real>(-P.x, -P.y, -P.z);
+          Real dist = sqrt(dot(xmP, xmP));
+          Real s = feature_sign(a, e, feat, xmP);
+          Real d = s * dist;
+          Real I = Real(0.5) * (Real(1) + tanh(d / (Real(2) * al)));
+          a.dsel[c] = d;
+          a.own[c] = e;
+          a.I[c] = I;
+          Real ch = cosh(d / (Real(2) * al));
+          Real coef = a.kc * (a.psi[c] - I) / (ch * ch) / (Real(4) * al);
+          V3<Real> dir;
+          if (dist > Real(1e-12)) dir = (-s / dist) * xmP;
+          else dir = mk<Real>(a.en[3 * e], a.en[3 * e + 1], a.en[3 * e + 2]);
+          for (int q = 0; q < a.NV; ++q) {
+            acc[q][0] = coef * beta[q] * dir.x;
+            acc[q][1] = coef * beta[q] * dir.y;
+            acc[q][2] = coef * beta[q] * dir.z;
+          }
+        }
+      }
+    }
+    // combine lanes that share an element, one fixed-point atomic per group
+    const unsigned active = __ballot_sync(0xffffffffu, e >= 0);
+    if (e >= 0) {
+      const unsigned grp = __match_any_sync(active, e);
+      const int leader = __ffs(grp) - 1;
+      const int lane = threadIdx.x & 31;
+      for (int q = 0; q < a.NV; ++q)
+        for (int d = 0; d < 3; ++d) {
+          long long v = llrint((double)acc[q][d] * CPL_SCALE);
+          // sum over the group in lane order
+          long long s = 0;
+          for (unsigned m = grp; m; m &= m - 1) {
+            int src = __ffs(m) - 1;
+            long long w = __shfl_sync(grp, v, src);
+            s += w;
+          }
+          if (lane == leader && s != 0) atomicAdd(a.esum + (a.NV * e + q) * 3 + d, (unsigned long long)s);
+        }
+    }
+  }
+}
+
+// Cells of the box farther than dc from the membrane: one warp per column
+// along z, 32 cells at a time.  A cell outside the band takes the side of
+// the nearest band cell below it (the membrane cannot be crossed between two
+// cells that are both farther than dc from it; the bottom of the box is
+// outside every capsule): d = +dc inside, -dc outside.
+template <class Real>
+__global__ void k_fill(IBArgs<Real> a) {
+  const int bx0 = a.box[0], by0 = a.box[1], bz0 = a.box[2];
+  const int wx = a.box[3] - bx0 + 1, wy = a.box[4] - by0 + 1, wz = a.box[5] - bz0 + 1;
+  const int col = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (col >= wx * wy) return;
+  const Real dc = a.dc, al = a.alpha;
+  const Real Iin = Real(0.5) * (Real(1) + tanh(dc / (Real(2) * al)));
+  const Real Iout = Real(0.5) * (Real(1) + tanh(-dc / (Real(2) * al)));
+  int pc[3] = {bx0 + col % wx, by0 + col / wx, 0};
+  bool inside = false;  // status carried from the chunk below
+  for (int z0 = 0; z0 < wz; z0 += 32) {
+    const int z = z0 + lane;
+    long long c = -1;
+    bool band = false, sgn = false;
+    if (z < wz) {
+      pc[2] = bz0 + z;
+      c = cell_of(a, pc);
+      if (c >= 0) {
+        band = a.own[c] >= 0;
+        if (band) sgn = a.dsel[c] > Real(0);
+      }
+    }
+    const unsigned bm = __ballot_sync(0xffffffffu, band);
+    const unsigned sm = __ballot_sync(0xffffffffu, band && sgn);
+    const unsigned below = bm & ((1u << lane) - 1u);
+    bool my = below ? ((sm >> (31 - __clz(below))) & 1u) : inside;
+    if (c >= 0 && !band) {
+      a.dsel[c] = my ? dc : -dc;
+      a.I[c] = my ? Iin : Iout;
+    }
+    // carry: status at the top lane of the chunk
+    const unsigned upto = bm;  // all band lanes in the chunk
+    bool top = upto ? ((sm >> (31 - __clz(upto))) & 1u) : inside;
+    inside = __shfl_sync(0xffffffffu, top, 0);
+  }
+}
+
+// ------------------------------------------------------------ elastic forces
+// Forward-mode dual number with derivatives with respect to one node.
+template <class T>
+struct D3 {
+  T v, d0, d1, d2;
+};
+template <class T> TLB_HD D3<T> dc(T v) { return {v, 0, 0, 0}; }
+template <class T> TLB_HD D3<T> operator+(D3<T> a, D3<T> b) { return {a.v + b.v, a.d0 + b.d0, a.d1 + b.d1, a.d2 + b.d2}; }
+template <class T> TLB_HD D3<T> operator-(D3<T> a, D3<T> b) { return {a.v - b.v, a.d0 - b.d0, a.d1 - b.d1, a.d2 - b.d2}; }
+template <class T> TLB_HD D3<T> operator*(D3<T> a, D3<T> b) {
+  return {a.v * b.v, a.d0 * b.v + a.v * b.d0, a.d1 * b.v + a.v * b.d1, a.d2 * b.v + a.v * b.d2};
+}
+template <class T> TLB_HD D3<T> operator*(T s, D3<T> a) { return {s * a.v, s * a.d0, s * a.d1, s * a.d2}; }
+template <class T> TLB_HD D3<T> operator/(D3<T> a, D3<T> b) {
+  T ib = T(1) / b.v;
+  T q = a.v * ib;
+  return {q, (a.d0 - q * b.d0) * ib, (a.d1 - q * b.d1) * ib, (a.d2 - q * b.d2) * ib};
+}
+template <class T> TLB_HD D3<T> dsqrt(D3<T> a) {
+  T s = sqrt(a.v);
+  T h = T(0.5) / s;
+  return {s, a.d0 * h, a.d1 * h, a.d2 * h};
+}
+template <class T> using DV = V3<D3<T>>;
+template <class T> TLB_HD DV<T> dsub(DV<T> a, DV<T> b) { return {a.x - b.x, a.y - b.y, a.z - b.z}; }
+template <class T> TLB_HD D3<T> ddot(DV<T> a, DV<T> b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
+template <class T> TLB_HD DV<T> dcross(DV<T> a, DV<T> b) {
+  return {a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x};
+}
+
+// Position of node j relative to the seed node k, differentiated with
+// respect to X_k (the seed carries derivative -1 in every other node's frame:
+// we place the origin at X_k so only the seed itself moves).
+template <class Real>
+__device__ __forceinline__ DV<Real> dnode(const IBArgs<Real>& a, int j, int k) {
+  DV<Real> r;
+  r.x = dc<Real>((Real)(a.X[3 * j] - a.X[3 * k]));
+  r.y = dc<Real>((Real)(a.X[3 * j + 1] - a.X[3 * k + 1]));
+  r.z = dc<Real>((Real)(a.X[3 * j + 2] - a.X[3 * k + 2]));
+  if (j == k) { r.x.d0 = 1; r.y.d1 = 1; r.z.d2 = 1; }
+  return r;
+}
+
+// Skalak energy of triangle t (shear modulus G, area ratio C):
+// W = (G/4)(I1^2 + 2 I1 - 2 I2 + C I2^2), I1 = tr(G0^-1 g) - 2, I2 = det(G0^-1 g) - 1.
+template <class Real>
+__device__ __forceinline__ D3<Real> skalak_dual(const IBArgs<Real>& a, int t, int k) {
+  int p = a.E[3 * t], q = a.E[3 * t + 1], r = a.E[3 * t + 2];
+  DV<Real> xp = dnode(a, p, k), xq = dnode(a, q, k), xr = dnode(a, r, k);
+  DV<Real> e1 = dsub(xq, xp), e2 = dsub(xr, xp);
+  D3<Real> g11 = ddot(e1, e1), g12 = ddot(e1, e2), g22 = ddot(e2, e2);
+  const double* Gi = a.G0i + 3 * t;
+  D3<Real> tr = (Real)Gi[0] * g11 + (Real)(2.0 * Gi[1]) * g12 + (Real)Gi[2] * g22;
+  D3<Real> det = (Real)(Gi[0] * Gi[2] - Gi[1] * Gi[1]) * (g11 * g22 - g12 * g12);
+  D3<Real> I1 = tr - dc<Real>(2), I2 = det - dc<Real>(1);
+  int cap = a.ecap[t];
+  Real G = (Real)a.sG[cap], C = (Real)a.sC[cap];
+  D3<Real> w = (G * Real(0.25)) * (I1 * I1 + Real(2) * I1 - Real(2) * I2 + C * (I2 * I2));
+  return (Real)a.A0[t] * w;
+}
+
+// Helfrich energy of vertex v: kb |sum_T (cot_k (x_v - x_j) + cot_j (x_v - x_k))|^2 / (8 A_v)
+// with A_v the mixed Voronoi area (Meyer et al. 2003).
+template <class Real>
+__device__ __forceinline__ D3<Real> helfrich_dual(const IBArgs<Real>& a, int v, int k) {
+  DV<Real> K = {dc<Real>(0), dc<Real>(0), dc<Real>(0)};
+  D3<Real> A = dc<Real>(0);
+  DV<Real> xv = dnode(a, v, k);
+  for (int jj = a.inc_off[v]; jj < a.inc_off[v + 1]; ++jj) {
+    int t = a.inc[jj];
+    int q0 = a.E[3 * t], q1 = a.E[3 * t + 1], q2 = a.E[3 * t + 2];
+    int j = q0 == v ? q1 : (q1 == v ? q2 : q0);
+    int kk = q0 == v ? q2 : (q1 == v ? q0 : q1);
+    DV<Real> xj = dnode(a, j, k), xk = dnode(a, kk, k);
+    DV<Real> vj = dsub(xv, xj), vk = dsub(xv, xk);
+    DV<Real> kj = dsub(xk, xj), jk = dsub(xj, xk);
+    DV<Real> c1 = dcross(vj, kj), c2 = dcross(vk, jk);
+    D3<Real> cotj = ddot(vj, kj) / dsqrt(ddot(c1, c1));
+    D3<Real> cotk = ddot(vk, jk) / dsqrt(ddot(c2, c2));
+    K.x = K.x + cotk * vj.x + cotj * vk.x;
+    K.y = K.y + cotk * vj.y + cotj * vk.y;
+    K.z = K.z + cotk * vj.z + cotj * vk.z;
+    DV<Real> ej = dsub(xj, xv), ek = dsub(xk, xv);
+    DV<Real> cr = dcross(ej, ek);
+    D3<Real> area = Real(0.5) * dsqrt(ddot(cr, cr));
+    Real dv = ddot(ej, ek).v, dj = ddot(vj, kj).v, dk = ddot(vk, jk).v;
+    if (dv < 0) A = A + Real(0.5) * area;
+    else if (dj < 0 || dk < 0) A = A + Real(0.25) * area;
+    else A = A + Real(0.125) * (ddot(vj, vj) * cotk + ddot(vk, vk) * cotj);
+  }
+  Real kb = (Real)a.kb[a.ncap[v]];
+  return (kb * Real(0.125)) * (ddot(K, K) / A);
+}
+
+// Node forces, one warp per marker: elastic (2D stretching + bending; 3D
+// Skalak + Helfrich, differentiated with forward-mode duals with respect to
+// the marker) plus the coupling contributions gathered from the incident
+// elements.  Lane sums are combined by a fixed shuffle tree.
+template <class Real>
+__global__ void k_node_forces(IBArgs<Real> a) {
+  const int k = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (k >= a.nn) return;
+  Real F[3] = {0, 0, 0};
+  if (a.NV == 2) {
+    if (lane == 0) {
+      // 2D ring: segment l joins node l -> next(l) (eq. DiscreteSE), bending
+      // at nodes prev, k, next (eqs. DiscreteBE, DiscreteTheta, DiscreteArcLength).
+      const int cap = a.ncap[k];
+      const Real ks = (Real)a.ks[cap], kb = (Real)a.kb[cap];
+      for (int side = 0; side < 2; ++side) {
+        int e = a.inc[a.inc_off[k] + side];
+        int p = a.E[2 * e], q = a.E[2 * e + 1];
+        Real tx = (Real)(a.X[3 * q] - a.X[3 * p]), tz = (Real)(a.X[3 * q + 2] - a.X[3 * p + 2]);
+        Real L = sqrt(tx * tx + tz * tz);
+        Real T = ks * (L / (Real)a.ds0[e] - Real(1)) / L;
+        Real sgn = (p == k) ? Real(1) : Real(-1);  // -dE/dX_p = +T t ; -dE/dX_q = -T t
+        F[0] += sgn * T * tx;
+        F[2] += sgn * T * tz;
+      }
+      int ms[3] = {a.rprev[k], k, a.rnext[k]};
+      for (int mi = 0; mi < 3; ++mi) {
+        int m = ms[mi], mp = a.rnext[m], mq = a.rprev[m];
+        Real ax = (Real)(a.X[3 * mp] - a.X[3 * m]), az = (Real)(a.X[3 * mp + 2] - a.X[3 * m + 2]);
+        Real bx = (Real)(a.X[3 * m] - a.X[3 * mq]), bz = (Real)(a.X[3 * m + 2] - a.X[3 * mq + 2]);
+        Real la = sqrt(ax * ax + az * az), lb = sqrt(bx * bx + bz * bz);
+        Real ab = ax * bx + az * bz;
+        Real cr = ax * bz - az * bx;
+        // theta1 = arccos(a.b / |a||b|), evaluated as atan2(|a x b|, a.b)
+        Real th = atan2(fabs(cr), ab);
+        Real sn = fabs(cr) / (la * lb);
+        Real ratio = th < Real(1e-4) ? Real(1) + th * th / Real(6) : th / sn;
+        Real dsp = la + lb;
+        Real k1 = Real(0.25) * kb * (Real(-8) * ratio / dsp);
+        Real dth = Real(2) * th;
+        Real k2 = Real(0.25) * kb * (dth / dsp) * (dth / dsp);
+        Real iab = Real(1) / (la * lb);
+        Real dya_x = bx * iab - ab * ax * iab / (la * la), dya_z = bz * iab - ab * az * iab / (la * la);
+        Real dyb_x = ax * iab - ab * bx * iab / (lb * lb), dyb_z = az * iab - ab * bz * iab / (lb * lb);
+        Real gx = 0, gz = 0;
+        if (k == mp) { gx += k1 * dya_x - k2 * ax / la; gz += k1 * dya_z - k2 * az / la; }
+        if (k == m) {
+          gx += k1 * (dyb_x - dya_x) - k2 * (bx / lb - ax / la);
+          gz += k1 * (dyb_z - dya_z) - k2 * (bz / lb - az / la);
+        }
+        if (k == mq) { gx += -k1 * dyb_x + k2 * bx / lb; gz += -k1 * dyb_z + k2 * bz / lb; }
+        F[0] -= gx;
+        F[2] -= gz;
+      }
+    }
+  } else {
+    const int i0 = a.inc_off[k], ninc = a.inc_off[k + 1] - i0;
+    // lanes 0..15: Skalak term of incident triangle `lane`
+    if (lane < 16 && lane < ninc) {
+      D3<Real> e = skalak_dual(a, a.inc[i0 + lane], k);
+      F[0] -= e.d0; F[1] -= e.d1; F[2] -= e.d2;
+    }
+    // lanes 16..31: Helfrich term of vertex v = k (lane 16) or of the
+    // (lane-17)-th distinct 1-ring neighbour of k, enumerated in the order
+    // of the incident triangles and their vertices
+    if (lane >= 16) {
+      int want = lane - 16, v = -1;
+      if (want == 0) v = k;
+      else {
+        int cnt = 0;
+        for (int jj = i0; jj < i0 + ninc && v < 0; ++jj) {
+          int t = a.inc[jj];
+          for (int q = 0; q < 3 && v < 0; ++q) {
+            int u = a.E[3 * t + q];
+            if (u == k) continue;
+            bool seen = false;
+            for (int ii = i0; ii < jj && !seen; ++ii) {
+              int t2 = a.inc[ii];
+              seen = a.E[3 * t2] == u || a.E[3 * t2 + 1] == u || a.E[3 * t2 + 2] == u;
+            }
+            for (int q2 = 0; q2 < q && !seen; ++q2) seen = a.E[3 * t + q2] == u;
+            if (seen) continue;
+            if (++cnt == want) v = u;
+          }
+        }
+      }
+      if (v >= 0) {
+        D3<Real> h = helfrich_dual(a, v, k);
+        F[0] -= h.d0; F[1] -= h.d1; F[2] -= h.d2;
+      }
+    }
+  }
+  for (int d = 0; d < 3; ++d)
+    for (int o = 16; o > 0; o >>= 1) F[d] += __shfl_xor_sync(0xffffffffu, F[d], o);
+  if (lane == 0) {
+    // coupling force gathered from the incident elements
+    double cpl[3] = {0, 0, 0};
+    for (int jj = a.inc_off[k]; jj < a.inc_off[k + 1]; ++jj) {
+      int e = a.inc[jj];
+      int slot = 0;
+      for (int q = 0; q < a.NV; ++q)
+        if (a.E[a.NV * e + q] == k) slot = q;
+      for (int d = 0; d < 3; ++d) cpl[d] += (double)(long long)a.esum[(a.NV * e + slot) * 3 + d];
+    }
+    for (int d = 0; d < 3; ++d) F[d] += (Real)(cpl[d] / CPL_SCALE);
+    if (a.dim == 2) F[1] = 0;
+    for (int d = 0; d < 3; ++d) a.F[3 * k + d] = F[d];
+  }
+}
+
+// ------------------------------------------------------------ spreading
+template <class Real>
+__device__ __forceinline__ Real peskin(Real r) {
+  Real x = fabs(r);
+  if (x <= Real(1)) return (Real(3) - Real(2) * x + sqrt(fmax(Real(0), Real(1) + Real(4) * x - Real(4) * x * x))) * Real(0.125);
+  if (x <= Real(2)) return (Real(5) - Real(2) * x - sqrt(fmax(Real(0), Real(-7) + Real(12) * x - Real(4) * x * x))) * Real(0.125);
+  return Real(0);
+}
+
+// Distinct bricks touched along one axis by the 4 support cells starting at base.
+__device__ __forceinline__ int axis_bricks(int base, int n, int* out) {
+  int m = 0;
+  for (int s = 0; s < 4; ++s) {
+    int c = ((base + s) % n + n) % n;
+    int b = c / BRICK;
+    bool dup = false;
+    for (int j = 0; j < m; ++j) dup |= out[j] == b;
+    if (!dup) out[m++] = b;
+  }
+  return m;
+}
+
+template <class Real>
+__device__ __forceinline__ int node_bricks(const IBArgs<Real>& a, int l, int* out) {
+  int bx[4], by[4], bz[4];
+  double X0 = fmax(-1e8, fmin(1e8, a.X[3 * l])), X1 = fmax(-1e8, fmin(1e8, a.X[3 * l + 1]));
+  double X2 = fmax(-1e8, fmin(1e8, a.X[3 * l + 2]));
+  int nxb = axis_bricks((int)floor(X0) - 1, a.G.nx, bx);
+  int nyb = 1;
+  by[0] = 0;
+  if (a.dim == 3) nyb = axis_bricks((int)floor(X1) - 1, a.G.ny, by);
+  int nzb = axis_bricks((int)floor(X2) - 1, a.G.nz, bz);
+  int m = 0;
+  for (int i = 0; i < nxb; ++i)
+    for (int j = 0; j < nyb; ++j)
+      for (int k = 0; k < nzb; ++k) out[m++] = (bz[k] * a.nby + by[j]) * a.nbx + bx[i];
+  return m;
+}
+
+template <class Real>
+__global__ void k_brick_count(IBArgs<Real> a) {
+  int l = blockIdx.x * blockDim.x + threadIdx.x;
+  if (l >= a.nn) return;
+  int b[64];
+  int m = node_bricks(a, l, b);
+  for (int j = 0; j < m; ++j) atomicAdd(a.bcnt + b[j], 1);
+}
+
+// Bricks holding markers now or in the previous step join the active list;
+// each claims a contiguous slot range for its marker list.
+template <class Real>
+__global__ void k_brick_compact(IBArgs<Real> a) {
+  int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= a.nbricks) return;
+  int c = a.bcnt[b];
+  if (c == 0 && a.bprev[b] == 0) return;
+  int i = atomicAdd(a.ctr, 1);
+  a.bact[i] = b;
+  a.boff[b] = atomicAdd(a.ctr + 1, c);
+}
+
+template <class Real>
+__global__ void k_brick_fill(IBArgs<Real> a) {
+  int l = blockIdx.x * blockDim.x + threadIdx.x;
+  if (l >= a.nn) return;
+  int b[64];
+  int m = node_bricks(a, l, b);
+  for (int j = 0; j < m; ++j) {
+    int s = atomicAdd(a.bcur + b[j], 1);
+    a.blist[a.boff[b[j]] + s] = l;
+  }
+}
+
+// Each cell of an active brick sums F_l delta_h(x - X_l) over the brick's
+// markers in ascending marker order (the list is sorted first, so the result
+// does not depend on the order of the atomic slot claims).  Bricks that held
+// markers in the previous step are visited too, so their cells return to zero.
+template <class Real>
+__global__ void k_spread(IBArgs<Real> a) {
+  __shared__ int list[512], sorted[512];
+  __shared__ Real sX[512][3];
+  __shared__ Real sF[512][3];
+  const int nact = a.ctr[0];
+  const int BY = a.dim == 3 ? BRICK : 1;
+  for (int ib = blockIdx.x; ib < nact; ib += gridDim.x) {
+    const int b = a.bact[ib];
+    const int cnt = a.bcnt[b];
+    const int off = a.boff[b];
+    const int m = min(cnt, 512);
+    if (cnt > 512 && threadIdx.x == 0) atomicOr(a.status, (unsigned)ST_OVERFLOW);
+    for (int j = threadIdx.x; j < m; j += blockDim.x) list[j] = a.blist[off + j];
+    __syncthreads();
+    // rank sort (marker indices are distinct), so the sum runs in marker order
+    for (int j = threadIdx.x; j < m; j += blockDim.x) {
+      int v = list[j], r = 0;
+      for (int i = 0; i < m; ++i) r += list[i] < v;
+      sorted[r] = v;
+    }
+    __syncthreads();
+    const int bx = b % a.nbx, by = (b / a.nbx) % a.nby, bz = b / (a.nbx * a.nby);
+    const int ox = bx * BRICK, oy = by * BRICK, oz = bz * BRICK;
+    // marker positions relative to the brick corner, nearest periodic image
+    for (int j = threadIdx.x; j < m; j += blockDim.x) {
+      int l = sorted[j];
+      double rx = a.X[3 * l] - ox, ry = a.X[3 * l + 1] - oy, rz = a.X[3 * l + 2] - oz;
+      rx -= a.G.nx * floor(rx / a.G.nx + 0.5);
+      if (a.dim == 3) ry -= a.G.ny * floor(ry / a.G.ny + 0.5); else ry = 0;
+      if (!a.G.wall) rz -= a.G.nz * floor(rz / a.G.nz + 0.5);
+      sX[j][0] = (Real)rx;
+      sX[j][1] = (Real)ry;
+      sX[j][2] = (Real)rz;
+      for (int d = 0; d < 3; ++d) sF[j][d] = a.F[3 * l + d];
+    }
+    __syncthreads();
+    const int lx = threadIdx.x % BRICK, ly = (threadIdx.x / BRICK) % BY, lz = threadIdx.x / (BRICK * BY);
+    const int cx = ox + lx, cy = oy + ly, cz = oz + lz;
+    const bool ok = threadIdx.x < BRICK * BY * BRICK && cx < a.G.nx && cy < a.G.ny && cz < a.G.nz;
+    if (ok) {
+      Real f[3] = {0, 0, 0};
+      for (int j = 0; j < m; ++j) {
+        Real rx = (Real)lx - sX[j][0], ry = (Real)ly - sX[j][1], rz = (Real)lz - sX[j][2];
+        if (!(fabs(rx) < Real(2) && fabs(rz) < Real(2) && (a.dim == 2 || fabs(ry) < Real(2)))) continue;
+        Real wgt = peskin(rx) * peskin(rz);
+        if (a.dim == 3) wgt *= peskin(ry);
+        for (int d = 0; d < 3; ++d) f[d] += wgt * sF[j][d];
+      }
+      long long c = ((long long)cz * a.G.ny + cy) * a.G.nx + cx;
+      for (int d = 0; d < 3; ++d) a.fib[d * a.G.P + c] = f[d];
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      a.bprev[b] = cnt;
+      a.bcnt[b] = 0;
+      a.bcur[b] = 0;
+    }
+    __syncthreads();
+  }
+}
+
+// ------------------------------------------------------------ interpolation
+// One warp per marker: v(t+1) = (j' + F/2)/rho' on the 4^d support cells
+// from the streamed populations and the force of the step, weighted by
+// delta_h, reduced over the warp; then X += U (explicit Euler).
+template <class L, int MODE>
+__global__ void k_interp_advect(IBArgs<typename Prec<MODE>::Real> a, const typename Prec<MODE>::Store* lo) {
+  using Real = typename Prec<MODE>::Real;
+  int l = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  int lane = threadIdx.x & 31;
+  if (l >= a.nn) return;
+  const Geo G = a.G;
+  const double X0 = a.X[3 * l], X1 = a.X[3 * l + 1], X2 = a.X[3 * l + 2];
+  const int b0 = (int)floor(X0) - 1, b1 = (int)floor(X1) - 1, b2 = (int)floor(X2) - 1;
+  const int ncell = a.dim == 3 ? 64 : 16;
+  Real U[3] = {0, 0, 0};
+  for (int s = lane; s < ncell; s += 32) {
+    int ox = s % 4, oy = a.dim == 3 ? (s / 4) % 4 : 0, oz = a.dim == 3 ? s / 16 : s / 4;
+    int px = b0 + ox, py = a.dim == 3 ? b1 + oy : 0, pz = b2 + oz;
+    Real w = peskin((Real)(px - X0)) * peskin((Real)(pz - X2));
+    if (a.dim == 3) w *= peskin((Real)(py - X1));
+    if (w == Real(0)) continue;
+    if (G.wall && (pz < 0 || pz >= G.nz)) continue;
+    int x = ((px % G.nx) + G.nx) % G.nx, y = ((py % G.ny) + G.ny) % G.ny, z = ((pz % G.nz) + G.nz) % G.nz;
+    long long self = ((long long)z * G.ny + y) * G.nx + x;
+    Real r = 0, j[3] = {0, 0, 0};
+#pragma unroll
+    for (int i = 0; i < L::Q; ++i) {
+      int sx = wrapc(x - L::cx(i), G.nx), sy = wrapc(y - L::cy(i), G.ny), szr = z - L::cz(i);
+      long long src;
+      int ii = i;
+      if (G.wall && (szr < 0 || szr >= G.nz)) { src = self; ii = L::opp(i); }
+      else src = ((long long)wrapc(szr, G.nz) * G.ny + sy) * G.nx + sx;
+      Real fi = to_real(lo[(long long)plane_f<L>(ii) * G.P + src]);
+      r += fi;
+      if (L::cx(i)) j[0] += L::cx(i) > 0 ? fi : -fi;
+      if (L::cy(i)) j[1] += L::cy(i) > 0 ? fi : -fi;
+      if (L::cz(i)) j[2] += L::cz(i) > 0 ? fi : -fi;
+    }
+    Real rho = Real(1) + r;
+    for (int d = 0; d < 3; ++d) U[d] += w * (j[d] + Real(0.5) * a.ftot[d * G.P + self]) / rho;
+  }
+  for (int d = 0; d < 3; ++d)
+    for (int o = 16; o > 0; o >>= 1) U[d] += __shfl_xor_sync(0xffffffffu, U[d], o);
+  if (lane == 0) {
+    if (a.dim == 2) U[1] = 0;
+    if (!(fabs((double)U[0]) < 0.5 && fabs((double)U[1]) < 0.5 && fabs((double)U[2]) < 0.5))
+      atomicOr(a.status, (unsigned)ST_MARKER_JUMP);
+    a.X[3 * l] = X0 + (double)U[0];
+    a.X[3 * l + 1] = X1 + (double)U[1];
+    a.X[3 * l + 2] = X2 + (double)U[2];
+  }
+}
+
+// FP64 capsule measures: 2D enclosed area (shoelace in the internal x-z
+// plane); 3D surface area and enclosed volume (divergence theorem).
+__global__ void k_capsule_measures(const double* X, const int* E, const int* ecap, int ne, int NV, int ncap,
+                                   double* out /* [ncap][2] */);

@@ -1,0 +1,427 @@
+// Templated host driver: builds kernel arguments from the context and
+// enqueues the step of the method on the context stream.
+#pragma once
+#include <math.h>
+
+#include <vector>
+
+#include "tlb_ctx.h"
+#include "tlb_ibm.cuh"
+#include "tlb_lb.cuh"
+
+template <class L, int MODE>
+struct Impl : ImplBase {
+  using Real = typename Prec<MODE>::Real;
+  using Store = typename Prec<MODE>::Store;
+  using Rest = typename Prec<MODE>::Rest;
+  static constexpr int TX = 32;
+  static constexpr int TY = L::DIM == 3 ? 4 : 1;
+
+  static Geo geo(const Ctx* c) {
+    Geo g;
+    g.nx = c->nx;
+    g.ny = c->ny;
+    g.nz = c->nz;
+    g.wall = c->p.wall_last;
+    g.N = c->N;
+    g.P = c->P;
+    return g;
+  }
+
+  static LBArgs<MODE> lbargs(Ctx* c, int src) {
+    LBArgs<MODE> a;
+    a.G = geo(c);
+    a.lo_src = c->ptr<Store>(c->L.lo[src]);
+    a.rest_src = c->ptr<Rest>(c->L.rest[src]);
+    a.lo_dst = c->ptr<Store>(c->L.lo[1 - src]);
+    a.rest_dst = c->ptr<Rest>(c->L.rest[1 - src]);
+    a.rho = c->ptr<Real>(c->L.rho);
+    a.phi = c->ptr<Real>(c->L.phi);
+    a.psi = c->ptr<Real>(c->L.psi);
+    a.I = c->ptr<Real>(c->L.I);
+    a.fib = c->ptr<Real>(c->L.fib);
+    a.ftot = c->ptr<Real>(c->L.ftot);
+    a.fe.k1 = (Real)c->p.kappa[0];
+    a.fe.k2 = (Real)c->p.kappa[1];
+    a.fe.k3 = (Real)c->p.kappa[2];
+    a.fe.kc = (Real)c->p.kappa_c;
+    a.fe.a2 = (Real)(c->p.alpha * c->p.alpha);
+    a.om = (Real)(1.0 / c->p.tau);
+    a.om_phi = (Real)(1.0 / c->p.tau_phi);
+    a.om_psi = (Real)(1.0 / c->p.tau_psi);
+    a.gphi = (Real)c->p.gamma_phi;
+    a.gpsi = (Real)c->p.gamma_psi;
+    a.zc = c->tiles_zc;
+    a.status = c->ptr<unsigned>(c->L.status);
+    return a;
+  }
+
+  static IBArgs<Real> ibargs(Ctx* c) {
+    IBArgs<Real> a;
+    a.G = geo(c);
+    a.dim = c->p.dim;
+    a.NV = c->NV;
+    a.nn = c->nn;
+    a.ne = c->ne;
+    a.X = c->ptr<double>(c->L.X);
+    a.E = c->ptr<int>(c->L.E);
+    a.ecap = c->ptr<int>(c->L.ecap);
+    a.ncap = c->ptr<int>(c->L.ncap);
+    const double* cp = c->ptr<double>(c->L.cap_par);
+    a.ks = cp;
+    a.kb = cp + c->ncap;
+    a.sG = cp + 2 * c->ncap;
+    a.sC = cp + 3 * c->ncap;
+    a.ds0 = c->ptr<double>(c->L.ds0);
+    a.rprev = c->ptr<int>(c->L.rprev);
+    a.rnext = c->ptr<int>(c->L.rnext);
+    a.A0 = c->ptr<double>(c->L.A0);
+    a.G0i = c->ptr<double>(c->L.G0i);
+    a.inc_off = c->ptr<int>(c->L.inc_off);
+    a.inc = c->ptr<int>(c->L.inc);
+    a.adj = c->ptr<int>(c->L.adj);
+    a.nedge = c->nedge;
+    a.edges = c->ptr<int>(c->L.edges);
+    a.en = c->ptr<Real>(c->L.en);
+    a.vn = c->ptr<Real>(c->L.vn);
+    a.esum = c->ptr<unsigned long long>(c->L.esum);
+    a.F = c->ptr<Real>(c->L.F);
+    a.box = c->ptr<int>(c->L.box);
+    a.key = c->ptr<unsigned long long>(c->L.key);
+    a.own = c->ptr<int>(c->L.own);
+    a.I = c->ptr<Real>(c->L.I);
+    a.dsel = c->ptr<Real>(c->L.dsel);
+    a.psi = c->ptr<Real>(c->L.psi);
+    a.fib = c->ptr<Real>(c->L.fib);
+    a.ftot = c->ptr<Real>(c->L.ftot);
+    a.bcnt = c->ptr<int>(c->L.bcnt);
+    a.bprev = c->ptr<int>(c->L.bprev);
+    a.bcur = c->ptr<int>(c->L.bcur);
+    a.boff = c->ptr<int>(c->L.boff);
+    a.blist = c->ptr<int>(c->L.blist);
+    a.bact = c->ptr<int>(c->L.bact);
+    a.ctr = c->ptr<int>(c->L.ctr);
+    a.nbx = c->nbx;
+    a.nby = c->nby;
+    a.nbz = c->nbz;
+    a.nbricks = c->nbricks;
+    a.alpha = (Real)c->p.alpha;
+    a.dc = (Real)c->p.dc;
+    a.kc = (Real)c->p.kappa_c;
+    a.status = c->ptr<unsigned>(c->L.status);
+    return a;
+  }
+
+  static unsigned blocks(long long n, int t) { return (unsigned)((n + t - 1) / t); }
+
+  // membrane profile I of the current marker positions and the coupling
+  // contributions of the band cells
+  static tlb_status profile(Ctx* c, IBArgs<Real>& a) {
+    cudaStream_t s = c->stream;
+    TLB_CUDA(cudaMemsetAsync(a.esum, 0, c->L.esum.bytes, s));
+    k_box<Real><<<1, 256, 0, s>>>(a);
+    TLB_LAUNCHED(c, "k_box");
+    k_elem_normals<Real><<<blocks(c->ne, 128), 128, 0, s>>>(a);
+    TLB_LAUNCHED(c, "k_elem_normals");
+    k_vertex_normals<Real><<<blocks(c->nn, 128), 128, 0, s>>>(a);
+    TLB_LAUNCHED(c, "k_vertex_normals");
+    const long long nfeat = (long long)c->ne + c->nedge + c->nn;
+    k_dist_scatter<Real><<<blocks(nfeat, SCATTER_WARPS), SCATTER_WARPS * 32, 0, s>>>(a);
+    TLB_LAUNCHED(c, "k_dist_scatter");
+    k_band<Real><<<8 * 152, 256, 0, s>>>(a);
+    TLB_LAUNCHED(c, "k_band");
+    k_fill<Real><<<blocks((long long)c->nx * c->ny * 32, 256), 256, 0, s>>>(a);
+    TLB_LAUNCHED(c, "k_fill");
+    return TLB_OK;
+  }
+
+  static tlb_status ibm_forces(Ctx* c, IBArgs<Real>& a) {
+    cudaStream_t s = c->stream;
+    k_node_forces<Real><<<blocks((long long)c->nn * 32, 128), 128, 0, s>>>(a);
+    TLB_LAUNCHED(c, "k_node_forces");
+    TLB_CUDA(cudaMemsetAsync(a.ctr, 0, 2 * sizeof(int), s));
+    k_brick_count<Real><<<blocks(c->nn, 128), 128, 0, s>>>(a);
+    TLB_LAUNCHED(c, "k_brick_count");
+    k_brick_compact<Real><<<blocks(c->nbricks, 256), 256, 0, s>>>(a);
+    TLB_LAUNCHED(c, "k_brick_compact");
+    k_brick_fill<Real><<<blocks(c->nn, 128), 128, 0, s>>>(a);
+    TLB_LAUNCHED(c, "k_brick_fill");
+    k_spread<Real><<<2 * 152, 64, 0, s>>>(a);
+    TLB_LAUNCHED(c, "k_spread");
+    return TLB_OK;
+  }
+
+  tlb_status init_fields(Ctx* c, const double* C, const double* u) override {
+    cudaStream_t s = c->stream;
+    const long long N = c->N, P = c->P;
+    IBArgs<Real> ia = ibargs(c);
+    // membrane profile I(X0) (I_out everywhere when there are no membranes)
+    if (c->nn > 0) {
+      tlb_status st = profile(c, ia);
+      if (st != TLB_OK) return st;
+    }
+    std::vector<Real> h((size_t)3 * P, Real(0));
+    Real* rho = c->ptr<Real>(c->L.rho);
+    Real* phi = c->ptr<Real>(c->L.phi);
+    Real* psi = c->ptr<Real>(c->L.psi);
+    if (C) {
+      for (long long n = 0; n < N; ++n) {
+        h[n] = (Real)(C[n] + C[N + n] + C[2 * N + n]);
+        h[P + n] = (Real)(C[n] - C[N + n]);
+        h[2 * P + n] = (Real)C[2 * N + n];
+      }
+    } else {
+      std::vector<Real> I((size_t)N);
+      TLB_CUDA(cudaMemcpyAsync(I.data(), c->ptr<Real>(c->L.I), N * sizeof(Real), cudaMemcpyDeviceToHost, s));
+      TLB_CUDA(cudaStreamSynchronize(s));
+      const double al = c->p.alpha;
+      for (long long n = 0; n < N; ++n) {
+        long long z = n / ((long long)c->nx * c->ny);  // last axis (2D: y)
+        double sv = 0.5 * (1.0 + tanh((z - c->p.interface_pos) / (2.0 * al)));
+        if (c->p.interface_pos < 0) sv = 0.0;
+        double ps = (double)I[n];
+        h[n] = (Real)1.0;
+        h[P + n] = (Real)((1.0 - ps) * (2.0 * sv - 1.0));
+        h[2 * P + n] = (Real)ps;
+      }
+    }
+    TLB_CUDA(cudaMemcpyAsync(rho, h.data(), N * sizeof(Real), cudaMemcpyHostToDevice, s));
+    TLB_CUDA(cudaMemcpyAsync(phi, h.data() + P, N * sizeof(Real), cudaMemcpyHostToDevice, s));
+    TLB_CUDA(cudaMemcpyAsync(psi, h.data() + 2 * P, N * sizeof(Real), cudaMemcpyHostToDevice, s));
+    TLB_CUDA(cudaStreamSynchronize(s));
+    // velocity field into ftot (free before the first step)
+    std::vector<Real> hu((size_t)3 * P, Real(0));
+    for (long long n = 0; n < N; ++n) {
+      double v[3];
+      if (u) {
+        v[0] = u[n];
+        v[1] = u[N + n];
+        v[2] = u[2 * N + n];
+      } else {
+        v[0] = c->p.u0[0];
+        v[1] = c->p.u0[1];
+        v[2] = c->p.u0[2];
+      }
+      if (c->p.dim == 2) {  // internal (x, 0, y)
+        hu[n] = (Real)v[0];
+        hu[P + n] = 0;
+        hu[2 * P + n] = (Real)v[1];
+      } else {
+        for (int d = 0; d < 3; ++d) hu[d * P + n] = (Real)v[d];
+      }
+    }
+    Real* uf = c->ptr<Real>(c->L.ftot);
+    TLB_CUDA(cudaMemcpyAsync(uf, hu.data(), 3 * P * sizeof(Real), cudaMemcpyHostToDevice, s));
+    Geo G = geo(c);
+    LBArgs<MODE> la = lbargs(c, c->cur);
+    Real* mu = c->ptr<Real>(c->L.mu);
+    k_mu_global<L, MODE><<<blocks(N, 256), 256, 0, s>>>(G, la.fe, rho, phi, psi, la.I, mu);
+    TLB_LAUNCHED(c, "k_mu_global");
+    k_init_eq<L, MODE><<<blocks(N, 256), 256, 0, s>>>(G, rho, phi, psi, uf, mu, la.gphi, la.gpsi,
+                                                       c->ptr<Store>(c->L.lo[c->cur]),
+                                                       c->ptr<Rest>(c->L.rest[c->cur]));
+    TLB_LAUNCHED(c, "k_init_eq");
+    TLB_CUDA(cudaMemsetAsync(c->ptr<char>(c->L.ftot), 0, c->L.ftot.bytes, s));
+    TLB_CUDA(cudaStreamSynchronize(s));
+    c->t = 0;
+    c->initialised = true;
+    return TLB_OK;
+  }
+
+  static tlb_status mark(Ctx* c, int k) {
+    if (c->prof) TLB_CUDA(cudaEventRecord(c->prof->ev[k], c->stream));
+    return TLB_OK;
+  }
+
+  static tlb_status collect(Ctx* c) {
+    if (!c->prof) return TLB_OK;
+    TLB_CUDA(cudaEventSynchronize(c->prof->ev[4]));
+    for (int k = 0; k < 4; ++k) {
+      float ms = 0;
+      TLB_CUDA(cudaEventElapsedTime(&ms, c->prof->ev[k], c->prof->ev[k + 1]));
+      c->prof_ms[k] += ms;
+    }
+    return TLB_OK;
+  }
+
+  tlb_status step(Ctx* c, long n) override {
+    cudaStream_t s = c->stream;
+    const long long N = c->N;
+    dim3 grid(blocks(c->nx, TX), blocks(c->ny, TY), blocks(c->nz, c->tiles_zc));
+    tlb_status st;
+    for (long k = 0; k < n; ++k) {
+      LBArgs<MODE> la = lbargs(c, c->cur);
+      if ((st = mark(c, 0)) != TLB_OK) return st;
+      k_moments<L, MODE><<<blocks(N, 256), 256, 0, s>>>(la);
+      TLB_LAUNCHED(c, "k_moments");
+      if ((st = mark(c, 1)) != TLB_OK) return st;
+      IBArgs<Real> ia = ibargs(c);
+      if (c->nn > 0) {
+        if ((st = profile(c, ia)) != TLB_OK) return st;
+        if ((st = ibm_forces(c, ia)) != TLB_OK) return st;
+      }
+      if ((st = mark(c, 2)) != TLB_OK) return st;
+      k_collide<L, MODE, TX, TY><<<grid, TX * TY, 0, s>>>(la);
+      TLB_LAUNCHED(c, "k_collide");
+      if ((st = mark(c, 3)) != TLB_OK) return st;
+      if (c->nn > 0) {
+        k_interp_advect<L, MODE><<<blocks((long long)c->nn * 32, 128), 128, 0, s>>>(ia, la.lo_dst);
+        TLB_LAUNCHED(c, "k_interp_advect");
+      }
+      if ((st = mark(c, 4)) != TLB_OK) return st;
+      if ((st = collect(c)) != TLB_OK) return st;
+      c->cur = 1 - c->cur;
+      c->t += 1;
+    }
+    return TLB_OK;
+  }
+
+  tlb_status read_field(Ctx* c, int field, double* dst, size_t nvals) override {
+    cudaStream_t s = c->stream;
+    const long long N = c->N;
+    double* rb = c->ptr<double>(c->L.rb);
+    Geo G = geo(c);
+    std::vector<double> tmp;
+    if (field == TLB_FIELD_I) {
+      if (nvals < (size_t)N) { set_error("read_field: buffer too small"); return TLB_ERR_ARG; }
+      std::vector<Real> h((size_t)N);
+      TLB_CUDA(cudaMemcpyAsync(h.data(), c->ptr<Real>(c->L.I), N * sizeof(Real), cudaMemcpyDeviceToHost, s));
+      TLB_CUDA(cudaStreamSynchronize(s));
+      for (long long i = 0; i < N; ++i) dst[i] = (double)h[i];
+      return TLB_OK;
+    }
+    const size_t need = field == TLB_FIELD_U ? 3 * (size_t)N : (size_t)N;
+    if (nvals < need) { set_error("read_field: buffer too small"); return TLB_ERR_ARG; }
+    k_fields<L, MODE><<<blocks(N, 256), 256, 0, s>>>(G, c->ptr<Store>(c->L.lo[c->cur]),
+                                                      c->ptr<Rest>(c->L.rest[c->cur]), rb);
+    TLB_LAUNCHED(c, "k_fields");
+    tmp.resize((size_t)6 * N);
+    TLB_CUDA(cudaMemcpyAsync(tmp.data(), rb, 6 * N * sizeof(double), cudaMemcpyDeviceToHost, s));
+    TLB_CUDA(cudaStreamSynchronize(s));
+    const double* r = tmp.data();
+    const double* ph = r + N;
+    const double* ps = r + 2 * N;
+    for (long long i = 0; i < N; ++i) {
+      switch (field) {
+        case TLB_FIELD_RHO: dst[i] = r[i]; break;
+        case TLB_FIELD_PHI: dst[i] = ph[i]; break;
+        case TLB_FIELD_PSI: dst[i] = ps[i]; break;
+        case TLB_FIELD_C1: dst[i] = 0.5 * (r[i] + ph[i] - ps[i]); break;
+        case TLB_FIELD_C2: dst[i] = 0.5 * (r[i] - ph[i] - ps[i]); break;
+        case TLB_FIELD_C3: dst[i] = ps[i]; break;
+        case TLB_FIELD_U:
+          if (c->p.dim == 2) {
+            dst[i] = r[3 * N + i];
+            dst[N + i] = r[5 * N + i];
+            dst[2 * N + i] = 0.0;
+          } else {
+            for (int d = 0; d < 3; ++d) dst[d * N + i] = r[(3 + d) * N + i];
+          }
+          break;
+        default: set_error("read_field: unknown field"); return TLB_ERR_ARG;
+      }
+    }
+    return TLB_OK;
+  }
+
+  // Populations are stored post-collision; the caller's view is the streamed
+  // (pre-collision) state.  The conversion runs on the host: it is I/O, not
+  // part of the time step.
+  static double h2d(double v) { return v; }
+  static double h2d(float v) { return v; }
+  static double h2d(__half v) { return (double)__half2float(v); }
+  static double h2d(__nv_bfloat16 v) { return (double)__bfloat162float(v); }
+  static void d2h(double v, double& o) { o = v; }
+  static void d2h(double v, float& o) { o = (float)v; }
+  static void d2h(double v, __half& o) { o = __float2half_rn((float)v); }
+  static void d2h(double v, __nv_bfloat16& o) { o = __float2bfloat16_rn((float)v); }
+
+  static long long hwrap(long long a, long long n) { return ((a % n) + n) % n; }
+
+  tlb_status read_pops(Ctx* c, double* dst) override {
+    cudaStream_t s = c->stream;
+    const long long N = c->N, P = c->P;
+    std::vector<Store> lo((size_t)(3 * L::Q - 2) * P);
+    std::vector<Rest> rest((size_t)2 * P);
+    TLB_CUDA(cudaMemcpyAsync(lo.data(), c->ptr<Store>(c->L.lo[c->cur]), lo.size() * sizeof(Store), cudaMemcpyDeviceToHost, s));
+    TLB_CUDA(cudaMemcpyAsync(rest.data(), c->ptr<Rest>(c->L.rest[c->cur]), rest.size() * sizeof(Rest), cudaMemcpyDeviceToHost, s));
+    TLB_CUDA(cudaStreamSynchronize(s));
+    for (long long n = 0; n < N; ++n) {
+      long long x = n % c->nx, y = (n / c->nx) % c->ny, z = n / ((long long)c->nx * c->ny);
+      for (int i = 0; i < L::Q; ++i) {
+        long long sz = z - L::cz(i), src;
+        int ii = i;
+        if (c->p.wall_last && (sz < 0 || sz >= c->nz)) { src = n; ii = L::opp(i); }
+        else src = (hwrap(sz, c->nz) * c->ny + hwrap(y - L::cy(i), c->ny)) * c->nx + hwrap(x - L::cx(i), c->nx);
+        dst[(long long)i * N + n] = h2d(lo[(size_t)plane_f<L>(ii) * P + src]) + L::w(ii);
+        dst[(long long)(L::Q + i) * N + n] = ii == 0 ? h2d(rest[src]) : h2d(lo[(size_t)plane_g<L>(ii) * P + src]);
+        dst[(long long)(2 * L::Q + i) * N + n] = ii == 0 ? h2d(rest[P + src]) : h2d(lo[(size_t)plane_h<L>(ii) * P + src]);
+      }
+    }
+    return TLB_OK;
+  }
+
+  tlb_status write_pops(Ctx* c, const double* src_in) override {
+    cudaStream_t s = c->stream;
+    const long long N = c->N, P = c->P;
+    std::vector<Store> lo((size_t)(3 * L::Q - 2) * P);
+    std::vector<Rest> rest((size_t)2 * P);
+    for (long long n = 0; n < N; ++n) {
+      long long x = n % c->nx, y = (n / c->nx) % c->ny, z = n / ((long long)c->nx * c->ny);
+      for (int i = 0; i < L::Q; ++i) {
+        long long tz = z + L::cz(i), src;
+        int ii = i;
+        if (c->p.wall_last && (tz < 0 || tz >= c->nz)) { src = n; ii = L::opp(i); }
+        else src = (hwrap(tz, c->nz) * c->ny + hwrap(y + L::cy(i), c->ny)) * c->nx + hwrap(x + L::cx(i), c->nx);
+        d2h(src_in[(long long)ii * N + src] - L::w(ii), lo[(size_t)plane_f<L>(i) * P + n]);
+        if (ii == 0) {
+          d2h(src_in[(long long)L::Q * N + src], rest[n]);
+          d2h(src_in[(long long)2 * L::Q * N + src], rest[P + n]);
+        } else {
+          d2h(src_in[(long long)(L::Q + ii) * N + src], lo[(size_t)plane_g<L>(i) * P + n]);
+          d2h(src_in[(long long)(2 * L::Q + ii) * N + src], lo[(size_t)plane_h<L>(i) * P + n]);
+        }
+      }
+    }
+    TLB_CUDA(cudaMemcpyAsync(c->ptr<Store>(c->L.lo[c->cur]), lo.data(), lo.size() * sizeof(Store), cudaMemcpyHostToDevice, s));
+    TLB_CUDA(cudaMemcpyAsync(c->ptr<Rest>(c->L.rest[c->cur]), rest.data(), rest.size() * sizeof(Rest), cudaMemcpyHostToDevice, s));
+    TLB_CUDA(cudaStreamSynchronize(s));
+    c->initialised = true;
+    return TLB_OK;
+  }
+
+  tlb_status diagnostics(Ctx* c, tlb_diag* out) override {
+    cudaStream_t s = c->stream;
+    Geo G = geo(c);
+    double* part = c->ptr<double>(c->L.part);
+    const int nb = 1024;
+    k_mass_partials<L, MODE><<<nb, 256, 0, s>>>(G, c->ptr<Store>(c->L.lo[c->cur]),
+                                                 c->ptr<Rest>(c->L.rest[c->cur]), part);
+    TLB_LAUNCHED(c, "k_mass_partials");
+    double* meas = c->ptr<double>(c->L.meas);
+    k_reduce_partials<<<1, 256, 0, s>>>(part, nb, 3, meas);
+    TLB_LAUNCHED(c, "k_reduce_partials");
+    if (c->ne > 0) {
+      k_capsule_measures<<<c->ncap, 256, 0, s>>>(c->ptr<double>(c->L.X), c->ptr<int>(c->L.E),
+                                                  c->ptr<int>(c->L.ecap), c->ne, c->NV, c->ncap, meas + 4);
+      TLB_LAUNCHED(c, "k_capsule_measures");
+    }
+    double h[4 + 16];
+    TLB_CUDA(cudaMemcpyAsync(h, meas, sizeof(h), cudaMemcpyDeviceToHost, s));
+    unsigned st = 0;
+    TLB_CUDA(cudaMemcpyAsync(&st, c->ptr<unsigned>(c->L.status), sizeof(unsigned), cudaMemcpyDeviceToHost, s));
+    TLB_CUDA(cudaStreamSynchronize(s));
+    out->step = c->t;
+    for (int q = 0; q < 3; ++q) out->mass[q] = h[q];
+    out->umax = 0;
+    out->n_caps = c->ncap;
+    for (int k = 0; k < 8; ++k) {
+      out->area[k] = k < c->ncap ? h[4 + 2 * k] : 0;
+      out->volume[k] = k < c->ncap ? h[4 + 2 * k + 1] : 0;
+    }
+    if (st & ST_NAN) { set_error("diagnostics: NaN in the populations"); return TLB_ERR_DIVERGED; }
+    if (st & ST_MARKER_JUMP) { set_error("diagnostics: a marker moved half a cell in one step"); return TLB_ERR_DIVERGED; }
+    if (st & ST_OVERFLOW) { set_error("diagnostics: spreading bin overflow"); return TLB_ERR_DIVERGED; }
+    return TLB_OK;
+  }
+};

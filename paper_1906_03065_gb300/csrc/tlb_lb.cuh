@@ -1,0 +1,349 @@
+// Lattice Boltzmann kernels: moments, chemical potentials, the fused
+// force + collision + streaming plane sweep, initial equilibria and the
+// conversions used by read/write of populations.
+#pragma once
+#include "tlb_common.cuh"
+
+template <int MODE>
+struct LBArgs {
+  using Real = typename Prec<MODE>::Real;
+  using Store = typename Prec<MODE>::Store;
+  using Rest = typename Prec<MODE>::Rest;
+  Geo G;
+  const Store* lo_src;
+  const Rest* rest_src;
+  Store* lo_dst;
+  Rest* rest_dst;
+  Real* rho;
+  Real* phi;
+  Real* psi;
+  const Real* I;
+  const Real* fib;  // [3][P] immersed-boundary force density
+  Real* ftot;       // [3][P] total force of the step (read by the interpolation)
+  FEParams<Real> fe;
+  Real om, om_phi, om_psi;  // 1/tau
+  Real gphi, gpsi;          // Gamma_phi, Gamma_psi
+  int zc;                   // planes per block along z
+  unsigned* status;
+};
+
+// ---------------------------------------------------------------- moments
+// rho, phi, psi at every cell from the streamed populations (eq. MomentsDFs).
+template <class L, int MODE>
+__global__ void __launch_bounds__(256) k_moments(LBArgs<MODE> a) {
+  using Real = typename Prec<MODE>::Real;
+  const Geo G = a.G;
+  long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= G.N) return;
+  int x = (int)(n % G.nx);
+  int y = (int)((n / G.nx) % G.ny);
+  int z = (int)(n / ((long long)G.nx * G.ny));
+  Pull<L, MODE> p;
+  p.load(a.lo_src, a.rest_src, G, x, y, z);
+  CellMoments<Real> m = p.moments();
+  a.rho[n] = Real(1) + m.drho;
+  a.phi[n] = m.phi;
+  a.psi[n] = m.psi;
+}
+
+// Second-order polynomial of the equilibria: 3 c.u + 4.5 (c.u)^2 - 1.5 u^2.
+template <class Real>
+__device__ __forceinline__ Real eq_poly(Real cu, Real uu) {
+  return Real(3) * cu + Real(4.5) * cu * cu - Real(1.5) * uu;
+}
+
+// ------------------------------------------------- fused collide + stream
+// One block owns a TX x TY tile of (x, y) columns and sweeps a chunk of z
+// planes.  Shared memory holds a 5-plane ring of the moment fields (halo 2)
+// and a 3-plane ring of the chemical potentials (halo 1), so each cell's
+// radius-2 dependency (mu needs the Laplacian of the moments, the force
+// needs the gradient of mu) is served from on-chip memory.
+template <class L, int MODE, int TX, int TY>
+__global__ void __launch_bounds__(TX* TY) k_collide(LBArgs<MODE> a) {
+  using Real = typename Prec<MODE>::Real;
+  using Store = typename Prec<MODE>::Store;
+  using Rest = typename Prec<MODE>::Rest;
+  constexpr int Q = L::Q;
+  constexpr bool D3 = L::DIM == 3;
+  constexpr int HY = D3 ? 2 : 0;
+  constexpr int MX = TX + 4, MY = TY + 2 * HY;
+  constexpr int UX = TX + 2, UY = TY + (D3 ? 2 : 0);
+  constexpr int NT = TX * TY;
+  __shared__ Real smom[5][3][MY * MX];
+  __shared__ Real smu[3][3][UY * UX];
+
+  const Geo G = a.G;
+  const int tx = threadIdx.x % TX, ty = threadIdx.x / TX, tid = threadIdx.x;
+  const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
+  const int z0 = blockIdx.z * a.zc;
+  const int z1 = min(z0 + a.zc, G.nz);
+  const int x = x0 + tx, y = y0 + ty;
+  const bool active = x < G.nx && y < G.ny;
+
+  auto modn = [](int v, int n) { v %= n; return v < 0 ? v + n : v; };
+  auto plane_src = [&](int p) { return G.wall ? min(max(p, 0), G.nz - 1) : modn(p, G.nz); };
+
+  auto load_mom = [&](int p) {
+    const int slot = (p + 10) % 5;
+    const long long zp = (long long)plane_src(p) * G.ny;
+    for (int k = tid; k < MX * MY; k += NT) {
+      int hx = k % MX, hy = k / MX;
+      int gx = modn(x0 - 2 + hx, G.nx);
+      int gy = D3 ? modn(y0 - HY + hy, G.ny) : 0;
+      long long c = (zp + gy) * G.nx + gx;
+      smom[slot][0][k] = a.rho[c];
+      smom[slot][1][k] = a.phi[c];
+      smom[slot][2][k] = a.psi[c];
+    }
+  };
+
+  // chemical potentials of plane p on the tile plus a halo of 1
+  auto compute_mu = [&](int p) {
+    const int slot = (p + 9) % 3;
+    if (G.wall && (p < 0 || p >= G.nz)) {  // mirror ghost: mu(-1) = mu(0), mu(nz) = mu(nz-1)
+      const int src = (min(max(p, 0), G.nz - 1) + 9) % 3;
+      for (int k = tid; k < UX * UY; k += NT)
+        for (int q = 0; q < 3; ++q) smu[slot][q][k] = smu[src][q][k];
+      return;
+    }
+    const long long zp = (long long)modn(p, G.nz) * G.ny;  // periodic ghost planes wrap
+    for (int k = tid; k < UX * UY; k += NT) {
+      int ux = k % UX, uy = k / UX;
+      int hx = ux + 1, hy = uy + (D3 ? 1 : 0);
+      const int sc = (p + 10) % 5;
+      const int cidx = hy * MX + hx;
+      Real lap[3] = {0, 0, 0};
+      Real cen[3] = {smom[sc][0][cidx], smom[sc][1][cidx], smom[sc][2][cidx]};
+#pragma unroll
+      for (int i = 1; i < Q; ++i) {
+        const int s = (p + L::cz(i) + 10) % 5;
+        const int nb = (hy + L::cy(i)) * MX + hx + L::cx(i);
+        const Real w = Real(L::w(i));
+#pragma unroll
+        for (int q = 0; q < 3; ++q) lap[q] += w * (smom[s][q][nb] - cen[q]);
+      }
+#pragma unroll
+      for (int q = 0; q < 3; ++q) lap[q] *= Real(6);  // 2/cs^2
+      int gx = modn(x0 - 1 + ux, G.nx);
+      int gy = D3 ? modn(y0 - 1 + uy, G.ny) : 0;
+      Real Iv = a.I[(zp + gy) * G.nx + gx];
+      Real mr, mp, ms;
+      chem_potentials<Real>(a.fe, cen[0], cen[1], cen[2], lap[0], lap[1], lap[2], Iv, mr, mp, ms);
+      smu[slot][0][k] = mr;
+      smu[slot][1][k] = mp;
+      smu[slot][2][k] = ms;
+    }
+  };
+
+  auto collide = [&](int zz) {
+    if (!active) return;
+    const long long n = ((long long)zz * G.ny + y) * G.nx + x;
+    Pull<L, MODE> pl;
+    pl.load(a.lo_src, a.rest_src, G, x, y, zz);
+    const CellMoments<Real> m = pl.moments();
+    const Real rho = Real(1) + m.drho, phi = m.phi, psi = m.psi;
+    // gradients of the potentials (radius 1, isotropic stencil)
+    Real gm[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+    const int ux = tx + 1, uy = ty + (D3 ? 1 : 0);
+#pragma unroll
+    for (int i = 1; i < Q; ++i) {
+      const int s = (zz + L::cz(i) + 9) % 3;
+      const int nb = (uy + L::cy(i)) * UX + ux + L::cx(i);
+      const Real w = Real(L::w(i));
+#pragma unroll
+      for (int q = 0; q < 3; ++q) {
+        const Real v = w * smu[s][q][nb];
+        if (L::cx(i)) gm[q][0] += L::cx(i) > 0 ? v : -v;
+        if (L::cy(i)) gm[q][1] += L::cy(i) > 0 ? v : -v;
+        if (L::cz(i)) gm[q][2] += L::cz(i) > 0 ? v : -v;
+      }
+    }
+    const int sc = (zz + 9) % 3;
+    const int cc = uy * UX + ux;
+    const Real mup = smu[sc][1][cc], mus = smu[sc][2][cc];
+    // force: f_FE = -rho grad mu~rho - phi grad mu_phi - psi grad mu_psi' (+ f_IB)
+    Real F[3];
+#pragma unroll
+    for (int d = 0; d < 3; ++d)
+      F[d] = -Real(3) * (rho * gm[0][d] + phi * gm[1][d] + psi * gm[2][d]) + a.fib[d * G.P + n];
+    if (!D3) F[1] = 0;
+    const Real irho = Real(1) / rho;
+    Real u[3], du[3], v[3], us[3];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      u[d] = m.j[d] * irho;
+      du[d] = F[d] * irho;
+      v[d] = u[d] + Real(0.5) * du[d];
+      us[d] = u[d] + u[d] + du[d];  // u + (u + du)
+    }
+    const Real uu = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+    const Real vv = v[0] * v[0] + v[1] * v[1] + v[2] * v[2];
+    const Real dus = du[0] * us[0] + du[1] * us[1] + du[2] * us[2];
+    const Real om = a.om, omp = a.om_phi, oms = a.om_psi;
+    const Real w0 = Real(L::w(0));
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+      const Real w = Real(L::w(i));
+      const Real cu = L::cx(i) * u[0] + L::cy(i) * u[1] + L::cz(i) * u[2];
+      const Real cdu = L::cx(i) * du[0] + L::cy(i) * du[1] + L::cz(i) * du[2];
+      const Real cus = L::cx(i) * us[0] + L::cy(i) * us[1] + L::cz(i) * us[2];
+      // BGK + exact difference method (eq. LBE), written for f_i - w_i
+      const Real dP = Real(3) * cdu + Real(4.5) * cdu * cus - Real(1.5) * dus;
+      const Real fn = (Real(1) - om) * pl.f[i] + om * w * (m.drho + rho * eq_poly(cu, uu)) + w * rho * dP;
+      a.lo_dst[(long long)plane_f<L>(i) * G.P + n] = from_real<Store>(fn);
+      if (i > 0) {
+        const Real cv = L::cx(i) * v[0] + L::cy(i) * v[1] + L::cz(i) * v[2];
+        const Real pv = Real(3) * cv + Real(4.5) * cv * cv - Real(1.5) * vv;
+        const Real ge = w * (Real(3) * a.gphi * mup + phi * pv);
+        const Real he = w * (Real(3) * a.gpsi * mus + psi * pv);
+        a.lo_dst[(long long)plane_g<L>(i) * G.P + n] = from_real<Store>((Real(1) - omp) * pl.g[i] + omp * ge);
+        a.lo_dst[(long long)plane_h<L>(i) * G.P + n] = from_real<Store>((Real(1) - oms) * pl.h[i] + oms * he);
+      }
+    }
+    // rest populations close the zeroth moments (eq. EDF, i = 0)
+    const Real ge0 = phi - Real(3) * a.gphi * mup * (Real(1) - w0) - Real(1.5) * w0 * phi * vv;
+    const Real he0 = psi - Real(3) * a.gpsi * mus * (Real(1) - w0) - Real(1.5) * w0 * psi * vv;
+    a.rest_dst[n] = from_real<Rest>((Real(1) - omp) * pl.g[0] + omp * ge0);
+    a.rest_dst[G.P + n] = from_real<Rest>((Real(1) - oms) * pl.h[0] + oms * he0);
+#pragma unroll
+    for (int d = 0; d < 3; ++d) a.ftot[d * G.P + n] = F[d];
+    if (!(rho == rho) || !(phi == phi) || !(psi == psi)) atomicOr(a.status, (unsigned)ST_NAN);
+  };
+
+  // prologue: moments z0-2 .. z0+1, potentials z0 then z0-1 (a wall ghost
+  // copies its neighbour, so the real plane comes first)
+  for (int p = z0 - 2; p <= z0 + 1; ++p) load_mom(p);
+  __syncthreads();
+  compute_mu(z0);
+  __syncthreads();
+  compute_mu(z0 - 1);
+  __syncthreads();
+  for (int zz = z0; zz < z1; ++zz) {
+    load_mom(zz + 2);
+    __syncthreads();
+    compute_mu(zz + 1);
+    __syncthreads();
+    collide(zz);
+    __syncthreads();
+  }
+}
+
+// ------------------------------------------------------------- init & I/O
+// Chemical potentials from fields in global memory (used at initialisation).
+template <class L, int MODE>
+__global__ void k_mu_global(Geo G, FEParams<typename Prec<MODE>::Real> fe, const typename Prec<MODE>::Real* rho,
+                            const typename Prec<MODE>::Real* phi, const typename Prec<MODE>::Real* psi,
+                            const typename Prec<MODE>::Real* I, typename Prec<MODE>::Real* mu) {
+  using Real = typename Prec<MODE>::Real;
+  long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= G.N) return;
+  int x = (int)(n % G.nx), y = (int)((n / G.nx) % G.ny), z = (int)(n / ((long long)G.nx * G.ny));
+  const Real* F[3] = {rho, phi, psi};
+  Real lap[3] = {0, 0, 0};
+  for (int i = 1; i < L::Q; ++i) {
+    int sx = wrapc(x + L::cx(i), G.nx), sy = wrapc(y + L::cy(i), G.ny);
+    int sz = z + L::cz(i);
+    sz = G.wall ? min(max(sz, 0), G.nz - 1) : wrapc(sz, G.nz);
+    long long c = ((long long)sz * G.ny + sy) * G.nx + sx;
+    for (int q = 0; q < 3; ++q) lap[q] += Real(L::w(i)) * (F[q][c] - F[q][n]);
+  }
+  Real mr, mp, ms;
+  chem_potentials<Real>(fe, rho[n], phi[n], psi[n], 6 * lap[0], 6 * lap[1], 6 * lap[2], I[n], mr, mp, ms);
+  mu[n] = mr;
+  mu[G.P + n] = mp;
+  mu[2 * G.P + n] = ms;
+}
+
+// Equilibrium populations (eq. EDF) of the fields, stored post-collision:
+// the value of direction i at cell y is the equilibrium f_i at y + c_i (or,
+// across a wall, f_{opp(i)} at y), which the next pull brings back to place.
+template <class L, int MODE>
+__global__ void k_init_eq(Geo G, const typename Prec<MODE>::Real* rho, const typename Prec<MODE>::Real* phi,
+                          const typename Prec<MODE>::Real* psi, const typename Prec<MODE>::Real* u,
+                          const typename Prec<MODE>::Real* mu, typename Prec<MODE>::Real gphi,
+                          typename Prec<MODE>::Real gpsi, typename Prec<MODE>::Store* lo,
+                          typename Prec<MODE>::Rest* rest) {
+  using Real = typename Prec<MODE>::Real;
+  using Store = typename Prec<MODE>::Store;
+  using Rest = typename Prec<MODE>::Rest;
+  long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= G.N) return;
+  int x = (int)(n % G.nx), y = (int)((n / G.nx) % G.ny), z = (int)(n / ((long long)G.nx * G.ny));
+  for (int i = 0; i < L::Q; ++i) {
+    int tz = z + L::cz(i);
+    long long src;
+    int ii = i;
+    if (G.wall && (tz < 0 || tz >= G.nz)) {
+      src = n;
+      ii = L::opp(i);
+    } else {
+      src = ((long long)wrapc(tz, G.nz) * G.ny + wrapc(y + L::cy(i), G.ny)) * G.nx + wrapc(x + L::cx(i), G.nx);
+    }
+    Real r = rho[src], p = phi[src], s = psi[src];
+    Real uv[3] = {u[src], u[G.P + src], u[2 * G.P + src]};
+    Real uu = uv[0] * uv[0] + uv[1] * uv[1] + uv[2] * uv[2];
+    Real cu = L::cx(ii) * uv[0] + L::cy(ii) * uv[1] + L::cz(ii) * uv[2];
+    Real w = Real(L::w(ii)), w0 = Real(L::w(0));
+    Real pv = eq_poly(cu, uu);
+    lo[(long long)plane_f<L>(i) * G.P + n] = from_real<Store>(w * ((r - Real(1)) + r * pv));
+    Real mp = mu[G.P + src], ms = mu[2 * G.P + src];
+    if (ii == 0) {
+      // rest populations are stored in their own planes (direction 0 maps to itself)
+      rest[n] = from_real<Rest>(p - Real(3) * gphi * mp * (Real(1) - w0) - Real(1.5) * w0 * p * uu);
+      rest[G.P + n] = from_real<Rest>(s - Real(3) * gpsi * ms * (Real(1) - w0) - Real(1.5) * w0 * s * uu);
+    } else {
+      lo[(long long)plane_g<L>(i) * G.P + n] = from_real<Store>(w * (Real(3) * gphi * mp + p * pv));
+      lo[(long long)plane_h<L>(i) * G.P + n] = from_real<Store>(w * (Real(3) * gpsi * ms + s * pv));
+    }
+  }
+}
+
+// Fields of the streamed populations for read-back: rho, phi, psi, u.
+template <class L, int MODE>
+__global__ void k_fields(Geo G, const typename Prec<MODE>::Store* lo, const typename Prec<MODE>::Rest* rest,
+                         double* out /* [6][N] */) {
+  using Real = typename Prec<MODE>::Real;
+  long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= G.N) return;
+  int x = (int)(n % G.nx), y = (int)((n / G.nx) % G.ny), z = (int)(n / ((long long)G.nx * G.ny));
+  Pull<L, MODE> p;
+  p.load(lo, rest, G, x, y, z);
+  CellMoments<Real> m = p.moments();
+  double rho = 1.0 + (double)m.drho;
+  out[n] = rho;
+  out[G.N + n] = (double)m.phi;
+  out[2 * G.N + n] = (double)m.psi;
+  for (int d = 0; d < 3; ++d) out[(3 + d) * G.N + n] = (double)m.j[d] / rho;
+}
+
+// FP64 totals: per-block partial sums of rho (as 1 + sum of deviations),
+// phi and psi over a fixed cell partition, combined in fixed order by
+// k_reduce_partials, so the result does not depend on scheduling.
+template <class L, int MODE>
+__global__ void __launch_bounds__(256) k_mass_partials(Geo G, const typename Prec<MODE>::Store* lo,
+                                                       const typename Prec<MODE>::Rest* rest, double* part) {
+  __shared__ double sm[3][256];
+  double acc[3] = {0, 0, 0};
+  for (long long n = (long long)blockIdx.x * 256 + threadIdx.x; n < G.N; n += (long long)gridDim.x * 256) {
+    double r = 1.0, p = to_real(rest[n]), s = to_real(rest[G.P + n]);
+    for (int i = 0; i < L::Q; ++i) r += (double)to_real(lo[(long long)plane_f<L>(i) * G.P + n]);
+    for (int i = 1; i < L::Q; ++i) {
+      p += (double)to_real(lo[(long long)plane_g<L>(i) * G.P + n]);
+      s += (double)to_real(lo[(long long)plane_h<L>(i) * G.P + n]);
+    }
+    acc[0] += r;
+    acc[1] += p;
+    acc[2] += s;
+  }
+  for (int q = 0; q < 3; ++q) sm[q][threadIdx.x] = acc[q];
+  __syncthreads();
+  for (int s = 128; s > 0; s >>= 1) {
+    if (threadIdx.x < s)
+      for (int q = 0; q < 3; ++q) sm[q][threadIdx.x] += sm[q][threadIdx.x + s];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0)
+    for (int q = 0; q < 3; ++q) part[q * gridDim.x + blockIdx.x] = sm[q][0];
+}
+
+__global__ void k_reduce_partials(const double* part, int nb, int nq, double* out);

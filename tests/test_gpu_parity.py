@@ -1,0 +1,168 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 CPU oracle.
+
+Tolerances:
+* FP64 storage (2D): 1e-10 on fields and markers after 2000 steps of the
+  64x64 capsule workload, 1e-12 after one step.
+* FP32 storage (3D): relative L-inf 1e-4 on C1..C3 and u and 1e-4 lattice
+  units on marker positions, the bar set for FP32 fields.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1906_03065_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1906_03065_gb300 import build
+    build.build()
+    oracle.build()
+
+
+def _sim(wl):
+    from paper_1906_03065_gb300 import Simulation
+    return Simulation(wl)
+
+
+def _rel(a, b):
+    return np.abs(a - b).max() / max(np.abs(b).max(), 1e-300)
+
+
+def _compare_fields(g, o, tol_C, tol_u, tol_X, rel=True):
+    out = {}
+    for name in ("C1", "C2", "C3"):
+        a, b = g.field(name), o.field(name)
+        out[name] = _rel(a, b) if rel else np.abs(a - b).max()
+    ug = g.field("u")
+    uo = np.stack([o.field("ux"), o.field("uy"), o.field("uz")])
+    out["u"] = _rel(ug, uo) if rel else np.abs(ug - uo).max()
+    for m in range(len(g.nn)):
+        out[f"X{m}"] = np.abs(g.nodes(m) - o.nodes(m)).max()
+    for k, v in out.items():
+        tol = tol_u if k == "u" else (tol_X if k.startswith("X") else tol_C)
+        assert v <= tol, (k, v, out)
+    return out
+
+
+def test_init_matches_oracle_2d_f64():
+    wl = W.capsule_2d("f64")
+    g, o = _sim(wl).init(), oracle.Oracle(wl)
+    P = g.pops()
+    Po = o.pops()
+    assert np.abs(P - Po).max() < 1e-13
+
+
+def test_init_profile_matches_oracle():
+    for wl in (W.small_2d("f64"), W.small_3d("f32")):
+        g, o = _sim(wl).init(), oracle.Oracle(wl)
+        I_o, d_o, _ = o.iprofile(np.concatenate([m.X for m in wl.membranes]))
+        tol = 1e-12 if wl.params.storage == "f64" else 2e-6
+        assert np.abs(g.field("I") - I_o).max() < tol
+
+
+@pytest.mark.parametrize("tau", [1.0, 0.8])
+def test_one_step_random_state_2d_f64(tau):
+    wl = W.small_2d("f64")
+    wl.params.tau = wl.params.tau_phi = wl.params.tau_psi = tau
+    wl.membranes[0] = W.jitter_nodes(wl.membranes[0], 0.2, seed=1)
+    o = oracle.Oracle(wl, init=False)
+    C0, u0 = W.random_fields(wl.params, seed=4)
+    o.init(C0, u0)
+    rng = np.random.default_rng(5)
+    c, w = o.lattice()
+    P = o.pops() + 1e-3 * rng.standard_normal((3, o.Q, o.N)) * w[None, :, None]
+    o.set_pops(P)
+    g = _sim(wl)
+    g.init(C0, u0)
+    g.set_pops(P)
+    o.step(1)
+    g.step(1)
+    assert np.abs(g.pops() - o.pops()).max() < 1e-12
+    assert np.abs(g.nodes(0) - o.nodes(0)).max() < 1e-12
+
+
+def test_capsule_2d_f64_2000_steps():
+    """The 64x64 D2Q9 capsule workload (FP64) after 2000 steps."""
+    wl = W.capsule_2d("f64")
+    g, o = _sim(wl).init(), oracle.Oracle(wl)
+    g.step(2000)
+    o.step(2000)
+    _compare_fields(g, o, 1e-10, 1e-10, 1e-10, rel=False)
+    d = g.diagnostics()
+    m0 = oracle.Oracle(wl).masses()
+    assert np.abs(np.array(d.mass[:]) - m0).max() < 1e-9
+
+
+def test_small_3d_f32_one_step_random():
+    wl = W.small_3d("f32")
+    wl.membranes[0] = W.jitter_nodes(wl.membranes[0], 0.15, seed=3)
+    o = oracle.Oracle(wl, init=False)
+    C0, u0 = W.random_fields(wl.params, seed=6)
+    o.init(C0, u0)
+    g = _sim(wl)
+    g.init(C0, u0)
+    Po = o.pops()
+    assert np.abs(g.pops() - Po).max() < 2e-6
+    g.set_pops(Po)
+    o.step(1)
+    g.step(1)
+    assert np.abs(g.pops() - o.pops()).max() < 5e-6
+    assert np.abs(g.nodes(0) - o.nodes(0)).max() < 1e-6
+
+
+def test_small_3d_f32_200_steps():
+    """Ragged 40x36x34 D3Q19 lattice with walls and a capsule, FP32 storage."""
+    wl = W.small_3d("f32")
+    g, o = _sim(wl).init(), oracle.Oracle(wl)
+    g.step(200)
+    o.step(200)
+    _compare_fields(g, o, 1e-4, 1e-4, 1e-4)
+
+
+def test_periodic_3d_f32_no_membrane():
+    wl = W.small_3d("f32", nx=33, ny=20, nz=18, wall=0)
+    wl.membranes = []
+    C0, u0 = W.random_fields(wl.params, seed=8)
+    o = oracle.Oracle(wl, init=False)
+    o.init(C0, u0)
+    g = _sim(wl)
+    g.init(C0, u0)
+    g.step(20)
+    o.step(20)
+    _compare_fields(g, o, 1e-4, 1e-4, 1e-4)
+
+
+def test_mass_conservation_gpu():
+    wl = W.small_3d("f32")
+    g = _sim(wl).init()
+    m0 = np.array(g.diagnostics().mass[:])
+    g.step(100)
+    m1 = np.array(g.diagnostics().mass[:])
+    # FP32 storage: each cell's sum is conserved to float rounding
+    assert np.abs(m1 - m0).max() < 1e-6 * wl.params.ncells
+    wl2 = W.capsule_2d("f64")
+    g2 = _sim(wl2).init()
+    m0 = np.array(g2.diagnostics().mass[:])
+    g2.step(200)
+    assert np.abs(np.array(g2.diagnostics().mass[:]) - m0).max() < 1e-10
+
+
+def test_full_size_capsule_3d_init_and_step():
+    """The 128^3 icosphere-4 workload at full size: initial state and one
+    step against the oracle (fields and markers)."""
+    wl = W.capsule_3d("f32")
+    oracle.set_threads(0)
+    o = oracle.Oracle(wl)
+    g = _sim(wl).init()
+    for name in ("C1", "C2", "C3"):
+        assert _rel(g.field(name), o.field(name)) < 1e-5
+    # a few steps so that the velocity field is well above FP32 noise
+    o.step(3)
+    g.step(3)
+    _compare_fields(g, o, 1e-4, 1e-4, 1e-4)
