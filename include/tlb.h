@@ -164,6 +164,21 @@ tlb_status tlb_write_populations(void* ctx, const double* src, size_t n_values);
 /* FP64 diagnostics of the current state (synchronises the stream). */
 tlb_status tlb_diagnostics(void* ctx, tlb_diag* out);
 
+/* The same diagnostics, computed with no device memory from the caller or
+ * the arena: the reduction scratch is a fixed array inside the library
+ * (about 26 KB on every GPU that loads it, kept until exit).  For callers
+ * that cannot supply device memory at the point of the call, e.g. code in a
+ * real-time loop where cudaMalloc (which synchronises the device) is not
+ * allowed, or whose device memory belongs to another runtime.  The paper has
+ * no counterpart; this is an operational variant of tlb_diagnostics.
+ * - The first call on a device looks up the array's device address with
+ *   that device current; make that first call before any stream capture.
+ * - All calls share the one array: calls that overlap on the GPU (other
+ *   streams, other contexts on the same device) race.  Serialise them.
+ * - Rejects contexts with more than 8 capsules (TLB_ERR_ARG).
+ * - Calls no cudaMalloc/cudaFree or any allocating routine. */
+tlb_status tlb_diagnostics_static(void* ctx, tlb_diag* out);
+
 /* Per-phase device time of n_steps steps, measured with CUDA events on the
  * context stream around each phase (synchronises the stream).  Phases:
  * moments (streamed-population moments), ibm (profile I, membrane and

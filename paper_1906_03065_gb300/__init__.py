@@ -73,6 +73,8 @@ def lib():
         L.tlb_read_populations.argtypes = [vp, dp, sz]
         L.tlb_write_populations.argtypes = [vp, dp, sz]
         L.tlb_diagnostics.argtypes = [vp, C.POINTER(Diag)]
+        L.tlb_diagnostics_static.argtypes = [vp, C.POINTER(Diag)]
+        L.tlb_diagnostics_static.restype = C.c_int
         L.tlb_profile_steps.argtypes = [vp, C.c_long, C.POINTER(Profile)]
         L.tlb_profile_steps.restype = C.c_int
         L.tlb_last_launch_count.argtypes = [vp]
@@ -216,4 +218,11 @@ class Simulation:
     def diagnostics(self) -> Diag:
         d = Diag()
         _check(lib().tlb_diagnostics(self.h, C.byref(d)))
+        return d
+
+    def diagnostics_static(self) -> Diag:
+        """Diagnostics with the library's fixed scratch array (no device
+        memory from the caller; see tlb_diagnostics_static in tlb.h)."""
+        d = Diag()
+        _check(lib().tlb_diagnostics_static(self.h, C.byref(d)))
         return d
