@@ -267,6 +267,7 @@ static void plan(const tlb_params* p, const std::vector<HostMem>& mems, Ctx& c) 
   take(L.blist, 27 * nn * 4);
   take(L.bact, nb * 4);
   take(L.ctr, 4 * 4);
+  take(L.bflag, nb);
   take(L.status, 64);
   take(L.part, 3 * 1024 * 8);
   take(L.meas, 32 * 8);
@@ -319,6 +320,12 @@ tlb_status tlb_create(const tlb_params* params, const tlb_membrane_desc* mems, i
     default: set_error("unsupported dim/storage"); delete c; return TLB_ERR_ARG;
   }
   cudaStream_t st = c->stream;
+  {
+    tlb_status r0 = cuda_check(cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking), "side stream");
+    if (r0 == TLB_OK) r0 = cuda_check(cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming), "event");
+    if (r0 == TLB_OK) r0 = cuda_check(cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming), "event");
+    if (r0 != TLB_OK) { delete c; return r0; }
+  }
   // zero everything, then set the non-zero initial values
   tlb_status r = cuda_check(cudaMemsetAsync(c->base, 0, c->L.total, st), "memset arena");
   if (r != TLB_OK) { delete c; return r; }
@@ -503,6 +510,7 @@ tlb_status tlb_write_nodes(void* ctx, int capsule, const double* src, size_t n_v
   }
   TLB_CUDA(cudaMemcpyAsync(c->ptr<double>(c->L.X) + 3 * off, h.data(), 3 * nn * 8, cudaMemcpyHostToDevice, c->stream));
   TLB_CUDA(cudaStreamSynchronize(c->stream));
+  c->box_stale = true;
   return TLB_OK;
 }
 

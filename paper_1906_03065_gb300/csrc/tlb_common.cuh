@@ -104,6 +104,40 @@ struct CellMoments {
   Real phi, psi;
 };
 
+// Source of the populations arriving at cell (x, y, z): direction i comes
+// from x - c_i (periodic wrap), or, across a wall, from the cell itself in
+// direction opp(i) (halfway bounce-back).  The wrapped neighbour rows are
+// computed once per cell, so each pulled population costs one add.
+template <class L>
+struct Nbr {
+  long long self;
+  long long row[3][3];  // [dz + 1][dy + 1]: (z + dz, y + dy) row start
+  int xs[3];            // x - 1, x, x + 1 (wrapped)
+  bool wlo, whi;        // cell touches the bottom / top wall
+
+  __device__ __forceinline__ Nbr(const Geo& G, int x, int y, int z) {
+    self = ((long long)z * G.ny + y) * G.nx + x;
+    xs[0] = x == 0 ? G.nx - 1 : x - 1;
+    xs[1] = x;
+    xs[2] = x == G.nx - 1 ? 0 : x + 1;
+    int ys[3] = {y == 0 ? G.ny - 1 : y - 1, y, y == G.ny - 1 ? 0 : y + 1};
+    int zs[3] = {z == 0 ? G.nz - 1 : z - 1, z, z == G.nz - 1 ? 0 : z + 1};
+    wlo = G.wall && z == 0;
+    whi = G.wall && z == G.nz - 1;
+#pragma unroll
+    for (int dz = 0; dz < 3; ++dz)
+#pragma unroll
+      for (int dy = 0; dy < 3; ++dy) row[dz][dy] = ((long long)zs[dz] * G.ny + ys[dy]) * G.nx;
+  }
+  // bounce-back applies to direction i at this cell
+  __device__ __forceinline__ bool bounce(int i) const {
+    return (L::cz(i) > 0 && wlo) || (L::cz(i) < 0 && whi);
+  }
+  __device__ __forceinline__ long long src(int i) const {
+    return bounce(i) ? self : row[1 - L::cz(i)][1 - L::cy(i)] + xs[1 - L::cx(i)];
+  }
+};
+
 // Pull of the populations arriving at cell (x, y, z): f_i(x) = f*_i(x - c_i);
 // across a wall, halfway bounce-back returns f*_{opp(i)}(x).  Both the moment
 // kernel and the collision kernel use this routine so they agree bit for bit.
@@ -116,27 +150,21 @@ struct Pull {
 
   __device__ __forceinline__ void load(const Store* __restrict__ lo, const Rest* __restrict__ rest,
                                        const Geo& G, int x, int y, int z) {
-    const long long self = ((long long)z * G.ny + y) * G.nx + x;
+    const Nbr<L> nb(G, x, y, z);
 #pragma unroll
     for (int i = 0; i < L::Q; ++i) {
-      int sx = wrapc(x - L::cx(i), G.nx);
-      int sy = wrapc(y - L::cy(i), G.ny);
-      int szr = z - L::cz(i);
-      long long src;
-      int ii = i;
-      if (G.wall && (szr < 0 || szr >= G.nz)) {
-        src = self;
-        ii = L::opp(i);
+      const bool bb = nb.bounce(i);
+      const long long src = nb.src(i);
+      const int pf = bb ? plane_f<L>(L::opp(i)) : plane_f<L>(i);
+      f[i] = to_real(__ldg(lo + (long long)pf * G.P + src));
+      if (i == 0) {
+        g[0] = to_real(__ldg(rest + src));
+        h[0] = to_real(__ldg(rest + G.P + src));
       } else {
-        src = ((long long)wrapc(szr, G.nz) * G.ny + sy) * G.nx + sx;
-      }
-      f[i] = to_real(__ldg(lo + (long long)plane_f<L>(ii) * G.P + src));
-      if (ii == 0) {
-        g[i] = to_real(__ldg(rest + src));
-        h[i] = to_real(__ldg(rest + G.P + src));
-      } else {
-        g[i] = to_real(__ldg(lo + (long long)plane_g<L>(ii) * G.P + src));
-        h[i] = to_real(__ldg(lo + (long long)plane_h<L>(ii) * G.P + src));
+        const int pg = bb ? plane_g<L>(L::opp(i)) : plane_g<L>(i);
+        const int ph = bb ? plane_h<L>(L::opp(i)) : plane_h<L>(i);
+        g[i] = to_real(__ldg(lo + (long long)pg * G.P + src));
+        h[i] = to_real(__ldg(lo + (long long)ph * G.P + src));
       }
     }
   }

@@ -45,7 +45,7 @@ struct Layout {
   // membranes
   Region X, E, ecap, ncap, cap_par, ds0, rprev, rnext, A0, G0i, inc_off, inc, adj, edges;
   Region en, vn, esum, F, box;
-  Region bcnt, bprev, bcur, boff, blist, bact, ctr;
+  Region bcnt, bprev, bcur, boff, blist, bact, ctr, bflag;
   // misc
   Region status, part, meas;
   size_t total = 0;
@@ -68,9 +68,12 @@ struct Ctx {
   char* base = nullptr;
   size_t bytes = 0;
   cudaStream_t stream = nullptr;
+  cudaStream_t side = nullptr;  // membrane work that overlaps the moments
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   int cur = 0;  // population buffer holding the current state
   long t = 0;
   bool initialised = false;
+  bool box_stale = false;  // markers were overwritten: recompute the marker box
   long launches = 0;
   // membranes
   std::vector<HostMem> mems;
@@ -82,6 +85,13 @@ struct Ctx {
   ImplBase* impl = nullptr;
 
   template <class T> T* ptr(const Region& r) const { return reinterpret_cast<T*>(base + r.off); }
+
+  ~Ctx() {
+    if (side) cudaStreamSynchronize(side);
+    if (ev_fork) cudaEventDestroy(ev_fork);
+    if (ev_join) cudaEventDestroy(ev_join);
+    if (side) cudaStreamDestroy(side);
+  }
 };
 
 void set_error(const std::string& msg);

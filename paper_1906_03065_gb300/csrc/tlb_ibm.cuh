@@ -42,7 +42,7 @@ struct IBArgs {
   int* own;
   Real* I;
   Real* dsel;
-  const Real* psi;
+  const Real* psi;       // psi(t) (moment field)
   Real* fib;             // [3][P]
   const Real* ftot;      // [3][P]
   int* bcnt;             // bricks: count, previous count, cursor, offset
@@ -51,6 +51,7 @@ struct IBArgs {
   int* boff;
   int* blist;
   int* bact;             // active bricks (compacted list)
+  unsigned char* bflag;  // per brick: markers spread into it this step
   int* ctr;              // [0] active bricks, [1] list slots claimed
   int nbx, nby, nbz, nbricks;
   Real alpha, dc, kc;
@@ -143,41 +144,43 @@ __device__ __forceinline__ V3<Real> elem_closest(const IBArgs<Real>& a, int e, d
 }
 
 // ------------------------------------------------------------ geometry pass
-// Unit outward element normals.  2D segments in the internal (x, z) plane:
-// tangent t = (tx, 0, tz), outward normal (tz, 0, -tx) for a counter-clockwise ring.
+// Face normal of element e, computed from the marker positions.
 template <class Real>
-__global__ void k_elem_normals(IBArgs<Real> a) {
-  int e = blockIdx.x * blockDim.x + threadIdx.x;
-  if (e >= a.ne) return;
-  V3<Real> n;
+__device__ __forceinline__ V3<Real> face_normal(const IBArgs<Real>& a, int e) {
   if (a.NV == 2) {
     int p = a.E[2 * e], q = a.E[2 * e + 1];
     Real tx = (Real)(a.X[3 * q] - a.X[3 * p]), tz = (Real)(a.X[3 * q + 2] - a.X[3 * p + 2]);
     Real l = sqrt(tx * tx + tz * tz);
-    n = mk<Real>(tz / l, Real(0), -tx / l);
-  } else {
-    int p = a.E[3 * e], q = a.E[3 * e + 1], r = a.E[3 * e + 2];
-    V3<Real> b = node_rel<Real>(a.X, q, a.X[3 * p], a.X[3 * p + 1], a.X[3 * p + 2]);
-    V3<Real> c = node_rel<Real>(a.X, r, a.X[3 * p], a.X[3 * p + 1], a.X[3 * p + 2]);
-    V3<Real> cr = cross(b, c);
-    Real l = sqrt(dot(cr, cr));
-    n = (Real(1) / l) * cr;
+    return mk<Real>(tz / l, Real(0), -tx / l);
   }
-  a.en[3 * e] = n.x;
-  a.en[3 * e + 1] = n.y;
-  a.en[3 * e + 2] = n.z;
+  int p = a.E[3 * e], q = a.E[3 * e + 1], r = a.E[3 * e + 2];
+  V3<Real> b = node_rel<Real>(a.X, q, a.X[3 * p], a.X[3 * p + 1], a.X[3 * p + 2]);
+  V3<Real> c = node_rel<Real>(a.X, r, a.X[3 * p], a.X[3 * p + 1], a.X[3 * p + 2]);
+  V3<Real> cr = cross(b, c);
+  return (Real(1) / sqrt(dot(cr, cr))) * cr;
 }
 
-// Vertex pseudo-normals: angle-weighted sum of the incident face normals
-// (Baerentzen and Aanaes 2005); in 2D the sum of the two segment normals.
+// One launch for the geometry of the step: threads [0, ne) store the unit
+// outward face normals; threads [ne, ne + nn) store the vertex
+// pseudo-normals, the angle-weighted sum of the incident face normals
+// (Baerentzen and Aanaes 2005; in 2D the sum of the two segment normals),
+// computing those normals themselves.
 template <class Real>
-__global__ void k_vertex_normals(IBArgs<Real> a) {
-  int k = blockIdx.x * blockDim.x + threadIdx.x;
+__global__ void k_geometry(IBArgs<Real> a) {
+  int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < a.ne) {
+    V3<Real> n = face_normal(a, t);
+    a.en[3 * t] = n.x;
+    a.en[3 * t + 1] = n.y;
+    a.en[3 * t + 2] = n.z;
+    return;
+  }
+  int k = t - a.ne;
   if (k >= a.nn) return;
   V3<Real> s = mk<Real>(0, 0, 0);
   for (int j = a.inc_off[k]; j < a.inc_off[k + 1]; ++j) {
     int e = a.inc[j];
-    V3<Real> n = mk<Real>(a.en[3 * e], a.en[3 * e + 1], a.en[3 * e + 2]);
+    V3<Real> n = face_normal(a, e);
     Real wgt = 1;
     if (a.NV == 3) {
       int q0 = a.E[3 * e], q1 = a.E[3 * e + 1], q2 = a.E[3 * e + 2];
@@ -195,39 +198,34 @@ __global__ void k_vertex_normals(IBArgs<Real> a) {
   a.vn[3 * k + 2] = s.z;
 }
 
-// Bounding box of all markers, widened by dc + 2 cells (unwrapped; walls clamp z).
+// Marker bounding box.  The advection kernel accumulates floor(min X) and
+// -ceil(max X) per axis with integer atomicMin into box[0..5] (reset to a
+// large value after use); k_box does the same from scratch at set-up.
 template <class Real>
 __global__ void k_box(IBArgs<Real> a) {
-  __shared__ double lo[3][256], hi[3][256];
-  double l[3] = {1e300, 1e300, 1e300}, h[3] = {-1e300, -1e300, -1e300};
-  for (int k = threadIdx.x; k < a.nn; k += blockDim.x)
-    for (int d = 0; d < 3; ++d) {
-      l[d] = fmin(l[d], a.X[3 * k + d]);
-      h[d] = fmax(h[d], a.X[3 * k + d]);
-    }
-  for (int d = 0; d < 3; ++d) { lo[d][threadIdx.x] = l[d]; hi[d][threadIdx.x] = h[d]; }
-  __syncthreads();
-  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
-    if (threadIdx.x < s)
-      for (int d = 0; d < 3; ++d) {
-        lo[d][threadIdx.x] = fmin(lo[d][threadIdx.x], lo[d][threadIdx.x + s]);
-        hi[d][threadIdx.x] = fmax(hi[d][threadIdx.x], hi[d][threadIdx.x + s]);
-      }
-    __syncthreads();
+  int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= a.nn) return;
+  for (int d = 0; d < 3; ++d) {
+    double v = fmax(-1e8, fmin(1e8, a.X[3 * k + d]));
+    atomicMin(a.box + d, (int)floor(v));
+    atomicMin(a.box + 3 + d, -(int)ceil(v));
   }
-  if (threadIdx.x == 0) {
-    const int n[3] = {a.G.nx, a.G.ny, a.G.nz};
-    const int m = (int)ceil((double)a.dc) + 2;
-    for (int d = 0; d < 3; ++d) {
-      double fl = fmax(-1e8, fmin(1e8, lo[d][0])), fh = fmax(-1e8, fmin(1e8, hi[d][0]));
-      int bl = (int)floor(fl) - m, bh = (int)ceil(fh) + m;
-      if (d == 1 && a.dim == 2) { bl = 0; bh = 0; }
-      if (d == 2 && a.G.wall) { bl = max(bl, 0); bh = min(bh, n[2] - 1); }
-      if (bh - bl + 1 > n[d]) bh = bl + n[d] - 1;
-      if (bh < bl) bh = bl;
-      a.box[d] = bl;
-      a.box[3 + d] = bh;
-    }
+}
+
+// The box of cells the profile visits: marker box widened by dc + 2 cells
+// (unwrapped; walls clamp z; at most one period along every axis).
+template <class Real>
+__device__ __forceinline__ void profile_box(const IBArgs<Real>& a, int* lo, int* hi) {
+  const int n[3] = {a.G.nx, a.G.ny, a.G.nz};
+  const int m = (int)ceil((double)a.dc) + 2;
+  for (int d = 0; d < 3; ++d) {
+    int bl = a.box[d] - m, bh = -a.box[3 + d] + m;
+    if (d == 1 && a.dim == 2) { bl = 0; bh = 0; }
+    if (d == 2 && a.G.wall) { bl = max(bl, 0); bh = min(bh, n[2] - 1); }
+    if (bh - bl + 1 > n[d]) bh = bl + n[d] - 1;
+    if (bh < bl) bh = bl;
+    lo[d] = bl;
+    hi[d] = bh;
   }
 }
 
@@ -288,16 +286,20 @@ __device__ __forceinline__ int feature_info(const IBArgs<Real>& a, int f, int* c
   return *nT;
 }
 
-// One warp per feature.  Geometry is in Real relative to an integer origin
-// (the lattice cell below the first corner), so the FP32 build does its
-// sweep in single precision without losing accuracy; slice boxes are widened
-// by 1e-3 cells to stay conservative under rounding.
+// One warp per feature, one lane per slice.  Geometry is in Real relative to
+// an integer origin (the lattice cell below the first corner), so the FP32
+// build does its sweep in single precision without losing accuracy; slice
+// boxes are widened by 1e-3 cells to stay conservative under rounding.
+// A feature offers only its lowest-index face: if the nearest point P of a
+// cell lies on the feature, every face containing the feature is at exactly
+// |x - P|, so that face carries the key the tie rule selects; faces offered
+// for cells whose nearest point lies elsewhere are at their exact (larger or
+// equal) distance and cannot win wrongly.
 template <class Real>
 __global__ void __launch_bounds__(SCATTER_WARPS * 32) k_dist_scatter(IBArgs<Real> a) {
-  __shared__ Real sV[SCATTER_WARPS][MAXG][3][3];  // vertices of the feature's faces
-  __shared__ Real sG[SCATTER_WARPS][MAXG][3];     // cone generators
-  __shared__ Real sB[SCATTER_WARPS][3][3];        // feature corners
-  __shared__ int sT[SCATTER_WARPS][MAXG];
+  __shared__ Real sV[SCATTER_WARPS][3][3];     // vertices of the offered face
+  __shared__ Real sG[SCATTER_WARPS][MAXG][3];  // cone generators
+  __shared__ Real sB[SCATTER_WARPS][3][3];     // feature corners
   const int nfeat = a.ne + (a.NV == 3 ? a.nedge : 0) + a.nn;
   const int w = threadIdx.x >> 5;
   const int f = blockIdx.x * SCATTER_WARPS + w;
@@ -305,21 +307,19 @@ __global__ void __launch_bounds__(SCATTER_WARPS * 32) k_dist_scatter(IBArgs<Real
   if (f >= nfeat) return;
   int corners[3], tri[MAXG], nB, nT;
   const int nG = feature_info(a, f, corners, &nB, tri, &nT);
+  int tmin = tri[0];
+  for (int j = 1; j < nT; ++j) tmin = min(tmin, tri[j]);
   int o[3];
   for (int d = 0; d < 3; ++d) o[d] = (int)floor(fmax(-1e8, fmin(1e8, a.X[3 * corners[0] + d])));
   if (a.dim == 2) o[1] = 0;
-  // stage the feature in shared memory (positions relative to o)
-  for (int idx = lane; idx < nT * 9; idx += 32) {
-    int j = idx / 9, q = (idx / 3) % 3, d = idx % 3;
-    if (q < a.NV) sV[w][j][q][d] = (Real)(a.X[3 * a.E[a.NV * tri[j] + q] + d] - (double)o[d]);
+  if (lane < 9) {
+    int q = lane / 3, d = lane % 3;
+    if (q < a.NV) sV[w][q][d] = (Real)(a.X[3 * a.E[a.NV * tmin + q] + d] - (double)o[d]);
+    if (q < nB) sB[w][q][d] = (Real)(a.X[3 * corners[q] + d] - (double)o[d]);
   }
   for (int idx = lane; idx < nG * 3; idx += 32) sG[w][idx / 3][idx % 3] = a.en[3 * tri[idx / 3] + idx % 3];
-  for (int idx = lane; idx < nB * 3; idx += 32)
-    sB[w][idx / 3][idx % 3] = (Real)(a.X[3 * corners[idx / 3] + idx % 3] - (double)o[idx % 3]);
-  if (lane < nT) sT[w][lane] = tri[lane];
   __syncwarp();
   const Real dc = a.dc;
-  // slice axis: largest component of the generator sum, all generators of one sign
   Real S[3] = {0, 0, 0};
   bool finite = true;
   for (int j = 0; j < nG; ++j)
@@ -333,6 +333,7 @@ __global__ void __launch_bounds__(SCATTER_WARPS * 32) k_dist_scatter(IBArgs<Real
     if (lane == 0) atomicOr(a.status, (unsigned)ST_NAN);
     return;
   }
+  // slice axis: largest component of the generator sum, all generators of one sign
   int k = 0;
   if (a.dim == 3) {
     if (fabs(S[1]) > fabs(S[k])) k = 1;
@@ -350,7 +351,10 @@ __global__ void __launch_bounds__(SCATTER_WARPS * 32) k_dist_scatter(IBArgs<Real
   const Real eps = Real(1e-3);
   const int c0 = (int)ceil(bmin - dc - eps), c1 = (int)floor(bmax + dc + eps);
   const bool wide = gmin < Real(0.25);  // a generator nearly parallel to the slices
-  for (int c = c0; c <= c1; ++c) {
+  const V3<Real> v0 = mk<Real>(sV[w][0][0], sV[w][0][1], sV[w][0][2]);
+  const V3<Real> v1 = mk<Real>(sV[w][1][0], sV[w][1][1], sV[w][1][2]);
+  const V3<Real> v2 = a.NV == 3 ? mk<Real>(sV[w][2][0], sV[w][2][1], sV[w][2][2]) : v1;
+  for (int c = c0 + lane; c <= c1; c += 32) {
     Real lo0 = 1e30f, hi0 = -1e30f, lo1 = 1e30f, hi1 = -1e30f;
     for (int q = 0; q < nB; ++q) {
       if (!wide) {
@@ -371,38 +375,28 @@ __global__ void __launch_bounds__(SCATTER_WARPS * 32) k_dist_scatter(IBArgs<Real
     const int wa = a1 - a0 + 1, wb = b1 - b0 + 1;
     if (wa <= 0 || wb <= 0) continue;
     if (wa > 1024 || wb > 1024) {  // bounded work even for a badly deformed mesh
-      if (lane == 0) atomicOr(a.status, (unsigned)ST_OVERFLOW);
+      atomicOr(a.status, (unsigned)ST_OVERFLOW);
       continue;
     }
-    for (int idx = lane; idx < wa * wb; idx += 32) {
-      int r[3];
-      r[k] = c;
-      r[oa] = a0 + idx % wa;
-      if (a.dim == 3) r[ob] = b0 + idx / wa; else r[1] = 0;
-      int pc[3] = {o[0] + r[0], o[1] + r[1], o[2] + r[2]};
-      long long cell = cell_of(a, pc);
-      if (cell < 0) continue;
-      const Real xr = (Real)r[0], yr = (Real)r[1], zr = (Real)r[2];
-      unsigned long long best = KEY_NONE;
-      for (int j = 0; j < nT; ++j) {
+    for (int ib = b0; ib <= b1; ++ib)
+      for (int ia = a0; ia <= a1; ++ia) {
+        int r[3];
+        r[k] = c;
+        r[oa] = ia;
+        if (a.dim == 3) r[ob] = ib; else r[1] = 0;
+        int pc[3] = {o[0] + r[0], o[1] + r[1], o[2] + r[2]};
+        long long cell = cell_of(a, pc);
+        if (cell < 0) continue;
+        const V3<Real> x = mk<Real>((Real)r[0], (Real)r[1], (Real)r[2]);
         Real beta[3];
         int feat;
-        V3<Real> p0 = mk<Real>(sV[w][j][0][0] - xr, sV[w][j][0][1] - yr, sV[w][j][0][2] - zr);
-        V3<Real> p1 = mk<Real>(sV[w][j][1][0] - xr, sV[w][j][1][1] - yr, sV[w][j][1][2] - zr);
-        V3<Real> P;
-        if (a.NV == 2) {
-          P = closest_on_seg(p0, p1, beta, &feat);
-        } else {
-          V3<Real> p2 = mk<Real>(sV[w][j][2][0] - xr, sV[w][j][2][1] - yr, sV[w][j][2][2] - zr);
-          P = closest_on_tri(p0, p1, p2, beta, &feat);
-        }
+        V3<Real> P = a.NV == 2 ? closest_on_seg(v0 - x, v1 - x, beta, &feat)
+                               : closest_on_tri(v0 - x, v1 - x, v2 - x, beta, &feat);
         Real d = sqrt(dot(P, P));
         if (!(d < dc)) continue;
-        unsigned long long key = ((unsigned long long)(d * Real(17179869184.0)) << 24) | (unsigned long long)sT[w][j];
-        best = key < best ? key : best;
+        unsigned long long key = ((unsigned long long)(d * Real(17179869184.0)) << 24) | (unsigned long long)tmin;
+        if (key < a.key[cell]) atomicMin(a.key + cell, key);
       }
-      if (best != KEY_NONE && best < a.key[cell]) atomicMin(a.key + cell, best);
-    }
   }
 }
 
@@ -440,8 +434,10 @@ __device__ __forceinline__ Real feature_sign(const IBArgs<Real>& a, int e, int f
 // the column fill; keys are cleared for the next step.
 template <class Real>
 __global__ void k_band(IBArgs<Real> a) {
-  const int bx0 = a.box[0], by0 = a.box[1], bz0 = a.box[2];
-  const int wx = a.box[3] - bx0 + 1, wy = a.box[4] - by0 + 1, wz = a.box[5] - bz0 + 1;
+  int blo[3], bhi[3];
+  profile_box(a, blo, bhi);
+  const int bx0 = blo[0], by0 = blo[1], bz0 = blo[2];
+  const int wx = bhi[0] - bx0 + 1, wy = bhi[1] - by0 + 1, wz = bhi[2] - bz0 + 1;
   const long long total = (long long)wx * wy * wz;
   const Real al = a.alpha;
   const long long stride = (long long)gridDim.x * blockDim.x;
@@ -512,8 +508,10 @@ __global__ void k_band(IBArgs<Real> a) {
 // outside every capsule): d = +dc inside, -dc outside.
 template <class Real>
 __global__ void k_fill(IBArgs<Real> a) {
-  const int bx0 = a.box[0], by0 = a.box[1], bz0 = a.box[2];
-  const int wx = a.box[3] - bx0 + 1, wy = a.box[4] - by0 + 1, wz = a.box[5] - bz0 + 1;
+  int blo[3], bhi[3];
+  profile_box(a, blo, bhi);
+  const int bx0 = blo[0], by0 = blo[1], bz0 = blo[2];
+  const int wx = bhi[0] - bx0 + 1, wy = bhi[1] - by0 + 1, wz = bhi[2] - bz0 + 1;
   const int col = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (col >= wx * wy) return;
@@ -643,10 +641,10 @@ __device__ __forceinline__ D3<Real> helfrich_dual(const IBArgs<Real>& a, int v, 
   return (kb * Real(0.125)) * (ddot(K, K) / A);
 }
 
-// Node forces, one warp per marker: elastic (2D stretching + bending; 3D
+// Elastic node forces, one warp per marker (2D stretching + bending; 3D
 // Skalak + Helfrich, differentiated with forward-mode duals with respect to
-// the marker) plus the coupling contributions gathered from the incident
-// elements.  Lane sums are combined by a fixed shuffle tree.
+// the marker).  Lane sums are combined by a fixed shuffle tree.  They depend
+// on the marker positions only; the coupling force joins them in k_spread.
 template <class Real>
 __global__ void k_node_forces(IBArgs<Real> a) {
   const int k = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -739,19 +737,25 @@ __global__ void k_node_forces(IBArgs<Real> a) {
   for (int d = 0; d < 3; ++d)
     for (int o = 16; o > 0; o >>= 1) F[d] += __shfl_xor_sync(0xffffffffu, F[d], o);
   if (lane == 0) {
-    // coupling force gathered from the incident elements
-    double cpl[3] = {0, 0, 0};
-    for (int jj = a.inc_off[k]; jj < a.inc_off[k + 1]; ++jj) {
-      int e = a.inc[jj];
-      int slot = 0;
-      for (int q = 0; q < a.NV; ++q)
-        if (a.E[a.NV * e + q] == k) slot = q;
-      for (int d = 0; d < 3; ++d) cpl[d] += (double)(long long)a.esum[(a.NV * e + slot) * 3 + d];
-    }
-    for (int d = 0; d < 3; ++d) F[d] += (Real)(cpl[d] / CPL_SCALE);
     if (a.dim == 2) F[1] = 0;
     for (int d = 0; d < 3; ++d) a.F[3 * k + d] = F[d];
   }
+}
+
+// Coupling force on marker k, gathered from the fixed-point sums of its
+// incident elements (integer totals, so the result is order independent).
+template <class Real>
+__device__ __forceinline__ void coupling_of(const IBArgs<Real>& a, int k, Real* out) {
+  long long cpl[3] = {0, 0, 0};
+  for (int jj = a.inc_off[k]; jj < a.inc_off[k + 1]; ++jj) {
+    int e = a.inc[jj];
+    int slot = 0;
+    for (int q = 0; q < a.NV; ++q)
+      if (a.E[a.NV * e + q] == k) slot = q;
+    for (int d = 0; d < 3; ++d) cpl[d] += (long long)a.esum[(a.NV * e + slot) * 3 + d];
+  }
+  for (int d = 0; d < 3; ++d) out[d] = (Real)((double)cpl[d] / CPL_SCALE);
+  if (a.dim == 2) out[1] = 0;
 }
 
 // ------------------------------------------------------------ spreading
@@ -809,6 +813,7 @@ __global__ void k_brick_compact(IBArgs<Real> a) {
   int b = blockIdx.x * blockDim.x + threadIdx.x;
   if (b >= a.nbricks) return;
   int c = a.bcnt[b];
+  a.bflag[b] = c > 0;
   if (c == 0 && a.bprev[b] == 0) return;
   int i = atomicAdd(a.ctr, 1);
   a.bact[i] = b;
@@ -823,6 +828,10 @@ __global__ void k_brick_fill(IBArgs<Real> a) {
   int m = node_bricks(a, l, b);
   for (int j = 0; j < m; ++j) {
     int s = atomicAdd(a.bcur + b[j], 1);
+    if (s >= a.bcnt[b[j]]) {  // count and fill disagree: flag, never write past the range
+      atomicOr(a.status, (unsigned)ST_OVERFLOW);
+      continue;
+    }
     a.blist[a.boff[b[j]] + s] = l;
   }
 }
@@ -836,10 +845,11 @@ __global__ void k_spread(IBArgs<Real> a) {
   __shared__ int list[512], sorted[512];
   __shared__ Real sX[512][3];
   __shared__ Real sF[512][3];
-  const int nact = a.ctr[0];
+  const int nact = min(a.ctr[0], a.nbricks);
   const int BY = a.dim == 3 ? BRICK : 1;
   for (int ib = blockIdx.x; ib < nact; ib += gridDim.x) {
     const int b = a.bact[ib];
+    if (b < 0 || b >= a.nbricks) continue;
     const int cnt = a.bcnt[b];
     const int off = a.boff[b];
     const int m = min(cnt, 512);
@@ -865,7 +875,9 @@ __global__ void k_spread(IBArgs<Real> a) {
       sX[j][0] = (Real)rx;
       sX[j][1] = (Real)ry;
       sX[j][2] = (Real)rz;
-      for (int d = 0; d < 3; ++d) sF[j][d] = a.F[3 * l + d];
+      Real cp[3];
+      coupling_of(a, l, cp);  // F_mem = F_s + F_b + F_c (eq. MembraneForces)
+      for (int d = 0; d < 3; ++d) sF[j][d] = a.F[3 * l + d] + cp[d];
     }
     __syncthreads();
     const int lx = threadIdx.x % BRICK, ly = (threadIdx.x / BRICK) % BY, lz = threadIdx.x / (BRICK * BY);
@@ -916,16 +928,13 @@ __global__ void k_interp_advect(IBArgs<typename Prec<MODE>::Real> a, const typen
     if (w == Real(0)) continue;
     if (G.wall && (pz < 0 || pz >= G.nz)) continue;
     int x = ((px % G.nx) + G.nx) % G.nx, y = ((py % G.ny) + G.ny) % G.ny, z = ((pz % G.nz) + G.nz) % G.nz;
-    long long self = ((long long)z * G.ny + y) * G.nx + x;
+    const Nbr<L> nb(G, x, y, z);
+    const long long self = nb.self;
     Real r = 0, j[3] = {0, 0, 0};
 #pragma unroll
     for (int i = 0; i < L::Q; ++i) {
-      int sx = wrapc(x - L::cx(i), G.nx), sy = wrapc(y - L::cy(i), G.ny), szr = z - L::cz(i);
-      long long src;
-      int ii = i;
-      if (G.wall && (szr < 0 || szr >= G.nz)) { src = self; ii = L::opp(i); }
-      else src = ((long long)wrapc(szr, G.nz) * G.ny + sy) * G.nx + sx;
-      Real fi = to_real(lo[(long long)plane_f<L>(ii) * G.P + src]);
+      const int pf = nb.bounce(i) ? plane_f<L>(L::opp(i)) : plane_f<L>(i);
+      Real fi = to_real(lo[(long long)pf * G.P + nb.src(i)]);
       r += fi;
       if (L::cx(i)) j[0] += L::cx(i) > 0 ? fi : -fi;
       if (L::cy(i)) j[1] += L::cy(i) > 0 ? fi : -fi;
@@ -940,9 +949,13 @@ __global__ void k_interp_advect(IBArgs<typename Prec<MODE>::Real> a, const typen
     if (a.dim == 2) U[1] = 0;
     if (!(fabs((double)U[0]) < 0.5 && fabs((double)U[1]) < 0.5 && fabs((double)U[2]) < 0.5))
       atomicOr(a.status, (unsigned)ST_MARKER_JUMP);
-    a.X[3 * l] = X0 + (double)U[0];
-    a.X[3 * l + 1] = X1 + (double)U[1];
-    a.X[3 * l + 2] = X2 + (double)U[2];
+    const double Xn[3] = {X0 + (double)U[0], X1 + (double)U[1], X2 + (double)U[2]};
+    for (int d = 0; d < 3; ++d) {
+      a.X[3 * l + d] = Xn[d];
+      double v = fmax(-1e8, fmin(1e8, Xn[d]));
+      atomicMin(a.box + d, (int)floor(v));
+      atomicMin(a.box + 3 + d, -(int)ceil(v));
+    }
   }
 }
 

@@ -15,7 +15,7 @@ struct Impl : ImplBase {
   using Store = typename Prec<MODE>::Store;
   using Rest = typename Prec<MODE>::Rest;
   static constexpr int TX = 32;
-  static constexpr int TY = L::DIM == 3 ? 4 : 1;
+  static constexpr int TY = L::DIM == 3 ? 8 : 1;
 
   static Geo geo(const Ctx* c) {
     Geo g;
@@ -41,6 +41,9 @@ struct Impl : ImplBase {
     a.I = c->ptr<Real>(c->L.I);
     a.fib = c->ptr<Real>(c->L.fib);
     a.ftot = c->ptr<Real>(c->L.ftot);
+    a.bflag = c->ptr<unsigned char>(c->L.bflag);
+    a.nbx = c->nbx;
+    a.nby = c->nby;
     a.fe.k1 = (Real)c->p.kappa[0];
     a.fe.k2 = (Real)c->p.kappa[1];
     a.fe.k3 = (Real)c->p.kappa[2];
@@ -94,6 +97,7 @@ struct Impl : ImplBase {
     a.psi = c->ptr<Real>(c->L.psi);
     a.fib = c->ptr<Real>(c->L.fib);
     a.ftot = c->ptr<Real>(c->L.ftot);
+    a.bflag = c->ptr<unsigned char>(c->L.bflag);
     a.bcnt = c->ptr<int>(c->L.bcnt);
     a.bprev = c->ptr<int>(c->L.bprev);
     a.bcur = c->ptr<int>(c->L.bcur);
@@ -114,29 +118,28 @@ struct Impl : ImplBase {
 
   static unsigned blocks(long long n, int t) { return (unsigned)((n + t - 1) / t); }
 
-  // membrane profile I of the current marker positions and the coupling
-  // contributions of the band cells
-  static tlb_status profile(Ctx* c, IBArgs<Real>& a) {
-    cudaStream_t s = c->stream;
+  // Work of a step that depends on the marker positions X(t) only (element
+  // and vertex normals and the distance scatter here; elastic forces and the
+  // brick binning in ibm_bins).  It runs on the side stream while the
+  // moments of the step are computed.
+  static tlb_status ibm_positions(Ctx* c, IBArgs<Real>& a, cudaStream_t s, bool fresh_box) {
     TLB_CUDA(cudaMemsetAsync(a.esum, 0, c->L.esum.bytes, s));
-    k_box<Real><<<1, 256, 0, s>>>(a);
-    TLB_LAUNCHED(c, "k_box");
-    k_elem_normals<Real><<<blocks(c->ne, 128), 128, 0, s>>>(a);
-    TLB_LAUNCHED(c, "k_elem_normals");
-    k_vertex_normals<Real><<<blocks(c->nn, 128), 128, 0, s>>>(a);
-    TLB_LAUNCHED(c, "k_vertex_normals");
+    if (fresh_box) {  // set-up or overwritten markers: box of the current markers
+      TLB_CUDA(cudaMemsetAsync(a.box, 0x7F, 6 * sizeof(int), s));
+      k_box<Real><<<blocks(c->nn, 128), 128, 0, s>>>(a);
+      TLB_LAUNCHED(c, "k_box");
+    }
+    k_geometry<Real><<<blocks((long long)c->ne + c->nn, 128), 128, 0, s>>>(a);
+    TLB_LAUNCHED(c, "k_geometry");
     const long long nfeat = (long long)c->ne + c->nedge + c->nn;
     k_dist_scatter<Real><<<blocks(nfeat, SCATTER_WARPS), SCATTER_WARPS * 32, 0, s>>>(a);
     TLB_LAUNCHED(c, "k_dist_scatter");
-    k_band<Real><<<8 * 152, 256, 0, s>>>(a);
-    TLB_LAUNCHED(c, "k_band");
-    k_fill<Real><<<blocks((long long)c->nx * c->ny * 32, 256), 256, 0, s>>>(a);
-    TLB_LAUNCHED(c, "k_fill");
     return TLB_OK;
   }
 
-  static tlb_status ibm_forces(Ctx* c, IBArgs<Real>& a) {
-    cudaStream_t s = c->stream;
+  // Elastic forces and the binning of markers into spreading bricks (the
+  // bins are consumed and reset by k_spread of the same step).
+  static tlb_status ibm_bins(Ctx* c, IBArgs<Real>& a, cudaStream_t s) {
     k_node_forces<Real><<<blocks((long long)c->nn * 32, 128), 128, 0, s>>>(a);
     TLB_LAUNCHED(c, "k_node_forces");
     TLB_CUDA(cudaMemsetAsync(a.ctr, 0, 2 * sizeof(int), s));
@@ -146,7 +149,22 @@ struct Impl : ImplBase {
     TLB_LAUNCHED(c, "k_brick_compact");
     k_brick_fill<Real><<<blocks(c->nn, 128), 128, 0, s>>>(a);
     TLB_LAUNCHED(c, "k_brick_fill");
-    k_spread<Real><<<2 * 152, 64, 0, s>>>(a);
+    return TLB_OK;
+  }
+
+  // Profile I of the band and the rest of the box, and the coupling sums
+  // (needs psi(t)); then the box accumulator is reset for the advection.
+  static tlb_status ibm_band(Ctx* c, IBArgs<Real>& a, cudaStream_t s) {
+    k_band<Real><<<8 * 152, 256, 0, s>>>(a);
+    TLB_LAUNCHED(c, "k_band");
+    k_fill<Real><<<blocks((long long)c->nx * c->ny * 32, 256), 256, 0, s>>>(a);
+    TLB_LAUNCHED(c, "k_fill");
+    TLB_CUDA(cudaMemsetAsync(a.box, 0x7F, 6 * sizeof(int), s));
+    return TLB_OK;
+  }
+
+  static tlb_status ibm_spread(Ctx* c, IBArgs<Real>& a, cudaStream_t s) {
+    k_spread<Real><<<min(c->nbricks, 8 * 152), 64, 0, s>>>(a);
     TLB_LAUNCHED(c, "k_spread");
     return TLB_OK;
   }
@@ -157,8 +175,10 @@ struct Impl : ImplBase {
     IBArgs<Real> ia = ibargs(c);
     // membrane profile I(X0) (I_out everywhere when there are no membranes)
     if (c->nn > 0) {
-      tlb_status st = profile(c, ia);
+      tlb_status st = ibm_positions(c, ia, s, true);
+      if (st == TLB_OK) st = ibm_band(c, ia, s);
       if (st != TLB_OK) return st;
+      c->box_stale = true;  // the first step recomputes the box of X0
     }
     std::vector<Real> h((size_t)3 * P, Real(0));
     Real* rho = c->ptr<Real>(c->L.rho);
@@ -251,14 +271,23 @@ struct Impl : ImplBase {
     tlb_status st;
     for (long k = 0; k < n; ++k) {
       LBArgs<MODE> la = lbargs(c, c->cur);
+      IBArgs<Real> ia = ibargs(c);
       if ((st = mark(c, 0)) != TLB_OK) return st;
+      if (c->nn > 0) {  // fork: position-only membrane work on the side stream
+        TLB_CUDA(cudaEventRecord(c->ev_fork, s));
+        TLB_CUDA(cudaStreamWaitEvent(c->side, c->ev_fork, 0));
+        if ((st = ibm_positions(c, ia, c->side, c->box_stale)) != TLB_OK) return st;
+        if ((st = ibm_bins(c, ia, c->side)) != TLB_OK) return st;
+        c->box_stale = false;
+        TLB_CUDA(cudaEventRecord(c->ev_join, c->side));
+      }
       k_moments<L, MODE><<<blocks(N, 256), 256, 0, s>>>(la);
       TLB_LAUNCHED(c, "k_moments");
       if ((st = mark(c, 1)) != TLB_OK) return st;
-      IBArgs<Real> ia = ibargs(c);
-      if (c->nn > 0) {
-        if ((st = profile(c, ia)) != TLB_OK) return st;
-        if ((st = ibm_forces(c, ia)) != TLB_OK) return st;
+      if (c->nn > 0) {  // join
+        TLB_CUDA(cudaStreamWaitEvent(s, c->ev_join, 0));
+        if ((st = ibm_band(c, ia, s)) != TLB_OK) return st;
+        if ((st = ibm_spread(c, ia, s)) != TLB_OK) return st;
       }
       if ((st = mark(c, 2)) != TLB_OK) return st;
       k_collide<L, MODE, TX, TY><<<grid, TX * TY, 0, s>>>(la);

@@ -20,6 +20,8 @@ struct LBArgs {
   const Real* I;
   const Real* fib;  // [3][P] immersed-boundary force density
   Real* ftot;       // [3][P] total force of the step (read by the interpolation)
+  const unsigned char* bflag;  // per 4x4x4 brick: markers spread force into it
+  int nbx, nby;                // brick grid (x, y)
   FEParams<Real> fe;
   Real om, om_phi, om_psi;  // 1/tau
   Real gphi, gpsi;          // Gamma_phi, Gamma_psi
@@ -54,10 +56,11 @@ __device__ __forceinline__ Real eq_poly(Real cu, Real uu) {
 
 // ------------------------------------------------- fused collide + stream
 // One block owns a TX x TY tile of (x, y) columns and sweeps a chunk of z
-// planes.  Shared memory holds a 5-plane ring of the moment fields (halo 2)
-// and a 3-plane ring of the chemical potentials (halo 1), so each cell's
-// radius-2 dependency (mu needs the Laplacian of the moments, the force
-// needs the gradient of mu) is served from on-chip memory.
+// planes.  Shared memory holds a 5-plane ring of the moment fields (halo 2,
+// written by k_moments; halo reads are served by L2) and a 3-plane ring of
+// the chemical potentials (halo 1), so each cell's radius-2 dependency (mu
+// needs the Laplacian of the moments, the force needs the gradient of mu) is
+// served on chip.
 template <class L, int MODE, int TX, int TY>
 __global__ void __launch_bounds__(TX* TY) k_collide(LBArgs<MODE> a) {
   using Real = typename Prec<MODE>::Real;
@@ -161,11 +164,15 @@ __global__ void __launch_bounds__(TX* TY) k_collide(LBArgs<MODE> a) {
     const int sc = (zz + 9) % 3;
     const int cc = uy * UX + ux;
     const Real mup = smu[sc][1][cc], mus = smu[sc][2][cc];
-    // force: f_FE = -rho grad mu~rho - phi grad mu_phi - psi grad mu_psi' (+ f_IB)
+    // force: f_FE = -rho grad mu~rho - phi grad mu_phi - psi grad mu_psi' (+ f_IB
+    // inside the bricks the markers spread into)
+    const bool ib = a.bflag[((zz >> 2) * a.nby + (y >> 2)) * a.nbx + (x >> 2)] != 0;
     Real F[3];
 #pragma unroll
-    for (int d = 0; d < 3; ++d)
-      F[d] = -Real(3) * (rho * gm[0][d] + phi * gm[1][d] + psi * gm[2][d]) + a.fib[d * G.P + n];
+    for (int d = 0; d < 3; ++d) {
+      F[d] = -Real(3) * (rho * gm[0][d] + phi * gm[1][d] + psi * gm[2][d]);
+      if (ib) F[d] += a.fib[d * G.P + n];
+    }
     if (!D3) F[1] = 0;
     const Real irho = Real(1) / rho;
     Real u[3], du[3], v[3], us[3];
@@ -205,8 +212,9 @@ __global__ void __launch_bounds__(TX* TY) k_collide(LBArgs<MODE> a) {
     const Real he0 = psi - Real(3) * a.gpsi * mus * (Real(1) - w0) - Real(1.5) * w0 * psi * vv;
     a.rest_dst[n] = from_real<Rest>((Real(1) - omp) * pl.g[0] + omp * ge0);
     a.rest_dst[G.P + n] = from_real<Rest>((Real(1) - oms) * pl.h[0] + oms * he0);
+    if (ib)
 #pragma unroll
-    for (int d = 0; d < 3; ++d) a.ftot[d * G.P + n] = F[d];
+      for (int d = 0; d < 3; ++d) a.ftot[d * G.P + n] = F[d];
     if (!(rho == rho) || !(phi == phi) || !(psi == psi)) atomicOr(a.status, (unsigned)ST_NAN);
   };
 
