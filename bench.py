@@ -158,6 +158,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-lowprec", action="store_true")
     args = ap.parse_args()
 
     from paper_1906_03065_gb300 import workloads as W
@@ -184,6 +185,7 @@ def main():
 
     sim = T.Simulation(wl, device=dev)
     sim.init()
+    tile_variant, z_chunk = sim.autotune()
     N = wl.params.ncells
     stream = sim.stream
     vis = os.environ.get("CUDA_VISIBLE_DEVICES")
@@ -246,6 +248,34 @@ def main():
     h2d = (Ch.nbytes + Uh.nbytes) / Ke
     d2h = (c3.nbytes + X.nbytes) / Ke
 
+    # the same workload with 16-bit population storage (FP32 arithmetic)
+    lowprec = {}
+    if rank == 0 and not args.no_lowprec:
+        del sim
+        torch.cuda.empty_cache()
+        for fmt, bpc in (("f16", 252), ("bf16", 252)):
+            wl16 = W.capsule_3d(fmt)
+            s16 = T.Simulation(wl16, device=dev)
+            s16.init()
+            s16.autotune()
+            n16 = max(20, min(args.steps, 500))
+            s16.step(args.warmup)
+            torch.cuda.synchronize(dev)
+            a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a0.record(s16.stream)
+            s16.step(n16)
+            a1.record(s16.stream)
+            torch.cuda.synchronize(dev)
+            ms16 = a0.elapsed_time(a1)
+            p16 = s16.profile(nprof)
+            tc16 = p16.ms_collide / nprof / 1e3
+            ach = bpc * N / tc16 / 1e9
+            lowprec[fmt] = {"value": N * n16 / (ms16 / 1e3) / 1e6, "unit": "MLUPS", "steps": n16,
+                            "collide_achieved_gbs": ach, "collide_frac": ach / peak,
+                            "bytes_per_cell": bpc}
+            del s16
+            torch.cuda.empty_cache()
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         import oracle
@@ -265,10 +295,12 @@ def main():
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": wl.name, "cells": N, "markers": int(wl.membranes[0].X.shape[0]),
                        "storage": "f32", "l2": "state 1.1 GB > L2, no flush needed",
-                       "parallelism": "replicas" if world > 1 else "single"},
+                       "parallelism": "replicas" if world > 1 else "single",
+                       "collide_tile_variant": tile_variant, "collide_z_chunk": z_chunk},
             "roofline": roofline, "cpu_baseline": cpu, "clocks": clocks,
             "e2e": {"value": e2e_v, "unit": "MLUPS", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "gpu_launches": launches,
+            "lowprec_storage": lowprec,
         }))
     if dist:
         dist.destroy_process_group()

@@ -42,7 +42,7 @@ class _Params(C.Structure):
                 ("kappa1", C.c_double), ("kappa2", C.c_double), ("kappa3", C.c_double),
                 ("kappa_c", C.c_double), ("dc", C.c_double),
                 ("u0x", C.c_double), ("u0y", C.c_double), ("u0z", C.c_double),
-                ("interface_pos", C.c_double)]
+                ("interface_pos", C.c_double), ("storage", C.c_int), ("pad2", C.c_int)]
 
 
 def lib():
@@ -70,6 +70,8 @@ def lib():
         L.or_get_nodes.argtypes = [C.c_void_p, C.c_int, dp]
         L.or_set_nodes.argtypes = [C.c_void_p, C.c_int, dp]
         L.or_get_field.argtypes = [C.c_void_p, C.c_int, dp]
+        L.or_round.argtypes = [C.c_double, C.c_int, C.c_int, C.c_double]
+        L.or_round.restype = C.c_double
         L.or_peskin.argtypes = [C.c_double]
         L.or_peskin.restype = C.c_double
         L.or_mem_energy.argtypes = [C.c_void_p, C.c_int, C.c_int, dp]
@@ -91,6 +93,8 @@ def _dp(a: np.ndarray):
     return a.ctypes.data_as(C.POINTER(C.c_double))
 
 
+STORAGE_CODE = {"f64": 0, "f32": 1, "f16": 2, "bf16": 3}
+
 FIELDS = {"rho": 0, "phi": 1, "psi": 2, "ux": 3, "uy": 4, "uz": 5, "C1": 6, "C2": 7,
           "C3": 8, "I": 9, "Fx": 10, "Fy": 11, "Fz": 12, "fibx": 13, "fiby": 14,
           "fibz": 15, "mu_rho": 16, "mu_phi": 17, "mu_psi": 18}
@@ -103,7 +107,7 @@ def set_threads(n: int = 0) -> int:
 class Oracle:
     """One oracle simulation.  ``wl`` is a ``workloads.Workload``."""
 
-    def __init__(self, wl, init: bool = True, Cf=None, u=None):
+    def __init__(self, wl, init: bool = True, Cf=None, u=None, emulate_storage: bool = False):
         from paper_1906_03065_gb300.workloads import MEM_RING2D
         L = lib()
         p = wl.params
@@ -111,7 +115,8 @@ class Oracle:
         cp = _Params(p.dim, p.nx, p.ny, p.nz if p.dim == 3 else 1, p.wall_last, 0,
                      p.tau, p.tau_phi, p.tau_psi, p.gamma_phi, p.gamma_psi, p.alpha,
                      p.kappa1, p.kappa2, p.kappa3, p.kappa_c, p.dc,
-                     p.u0[0], p.u0[1], p.u0[2], p.interface_pos)
+                     p.u0[0], p.u0[1], p.u0[2], p.interface_pos,
+                     STORAGE_CODE[p.storage] if emulate_storage else 0, 0)
         self._cp = cp
         self.h = L.or_create(C.byref(cp))
         self.N = p.nx * p.ny * (p.nz if p.dim == 3 else 1)
@@ -241,6 +246,13 @@ class Oracle:
         U = np.zeros_like(X)
         lib().or_interp(self.h, X.shape[0], _dp(X), _dp(field3), _dp(U))
         return U
+
+
+def round_to_format(x: float, fmt: str) -> float:
+    """Round x to binary16 / bfloat16 / binary32 (ties to even)."""
+    p, emin, maxv = {"f16": (11, -14, 65504.0), "bf16": (8, -126, 3.3895313892515355e38),
+                     "f32": (24, -126, 3.4028234663852886e38)}[fmt]
+    return lib().or_round(float(x), p, emin, maxv)
 
 
 def peskin(r: float) -> float:

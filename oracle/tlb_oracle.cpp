@@ -107,6 +107,8 @@ typedef struct {
   double tau, tau_phi, tau_psi, gamma_phi, gamma_psi, alpha;
   double kappa1, kappa2, kappa3, kappa_c, dc;
   double u0x, u0y, u0z, interface_pos;
+  int storage, pad2;  // population storage emulated after every step:
+                      // 0 none (FP64), 1 binary32, 2 binary16, 3 bfloat16
 } or_params;
 
 }  // extern "C"
@@ -869,6 +871,51 @@ void interp(const Sim& s, const double* X, int nn, const std::vector<double>& v,
   }
 }
 
+// ------------------------------------------------- storage rounding
+// Round x to the nearest number with `p` significant bits (ties to even),
+// subnormals below 2^emin on the fixed grid of spacing 2^(emin - p + 1),
+// overflow past the largest finite value to infinity: the IEEE 754
+// binary16 (p = 11, emin = -14, max 65504), bfloat16 (p = 8, emin = -126)
+// and binary32 (p = 24, emin = -126) formats written from their definition.
+double round_to_format(double x, int p, int emin, double maxv) {
+  if (x == 0.0 || !std::isfinite(x)) return x;
+  int e;
+  std::frexp(x, &e);  // |x| = m 2^e, m in [0.5, 1)
+  int ex = e - 1;     // |x| in [2^ex, 2^(ex+1))
+  if (ex < emin) ex = emin;
+  double q = std::ldexp(1.0, ex - (p - 1));     // spacing of the grid at |x|
+  double r = std::nearbyint(x / q) * q;          // default rounding: ties to even
+  if (std::fabs(r) > maxv) return x > 0 ? INFINITY : -INFINITY;
+  return r;
+}
+
+// Storage emulation: the stored quantities are f_i - w_i, g_i and h_i for
+// i != 0 in the storage format, and g_0, h_0 (they carry phi and psi) in
+// binary32 when the storage format is 16 bits wide.
+void emulate_storage(Sim& s) {
+  const int st = s.p.storage;
+  if (st == 0) return;
+  int p = 24, emin = -126;
+  double maxv = 3.4028234663852886e38;
+  if (st == 2) { p = 11; emin = -14; maxv = 65504.0; }
+  if (st == 3) { p = 8; emin = -126; maxv = 3.3895313892515355e38; }
+  const int Q = s.L.Q;
+  const long N = s.N;
+#pragma omp parallel for
+  for (long c = 0; c < N; ++c)
+    for (int i = 0; i < Q; ++i) {
+      long k = (long)i * N + c;
+      s.f[k] = round_to_format(s.f[k] - s.L.w[i], p, emin, maxv) + s.L.w[i];
+      if (i == 0) {
+        s.g[k] = round_to_format(s.g[k], 24, -126, 3.4028234663852886e38);
+        s.h[k] = round_to_format(s.h[k], 24, -126, 3.4028234663852886e38);
+      } else {
+        s.g[k] = round_to_format(s.g[k], p, emin, maxv);
+        s.h[k] = round_to_format(s.h[k], p, emin, maxv);
+      }
+    }
+}
+
 // ------------------------------------------------------------ the step
 void moments(Sim& s) {
   const int Q = s.L.Q;
@@ -1019,6 +1066,7 @@ void do_step(Sim& s) {
     for (int l = 0; l < m.nn; ++l)
       for (int k = 0; k < s.dim; ++k) m.X[3 * l + k] += U[3 * l + k];
   }
+  emulate_storage(s);
   s.t += 1;
 }
 
@@ -1076,6 +1124,7 @@ void do_init(Sim& s, const double* C, const double* u) {
     }
   }
   s.F.assign(3 * N, 0.0);
+  emulate_storage(s);
   s.t = 0;
 }
 
@@ -1204,6 +1253,7 @@ void or_get_field(void* h, int which, double* out) {
 
 // ------------------------------------------------ pieces exposed for pins
 double or_peskin(double r) { return peskin(r); }
+double or_round(double x, int p, int emin, double maxv) { return round_to_format(x, p, emin, maxv); }
 
 // which: 0 stretching (2D) / Skalak (3D); 1 bending (2D) / Helfrich (3D)
 double or_mem_energy(void* h, int m, int which, const double* X) {

@@ -77,6 +77,8 @@ def lib():
         L.tlb_diagnostics_static.restype = C.c_int
         L.tlb_profile_steps.argtypes = [vp, C.c_long, C.POINTER(Profile)]
         L.tlb_profile_steps.restype = C.c_int
+        L.tlb_autotune.argtypes = [vp, C.POINTER(C.c_int), C.POINTER(C.c_int)]
+        L.tlb_autotune.restype = C.c_int
         L.tlb_last_launch_count.argtypes = [vp]
         L.tlb_last_launch_count.restype = C.c_long
         L.tlb_destroy.argtypes = [vp]
@@ -182,6 +184,12 @@ class Simulation:
 
     def step(self, n: int = 1):
         _check(lib().tlb_step(self.h, int(n)))
+
+    def autotune(self):
+        """Pick the collide tile shape and z chunk by timing; returns them."""
+        v, z = C.c_int(0), C.c_int(0)
+        _check(lib().tlb_autotune(self.h, C.byref(v), C.byref(z)))
+        return v.value, z.value
 
     def launches(self) -> int:
         return lib().tlb_last_launch_count(self.h)

@@ -104,7 +104,15 @@ static tlb_status check_params(const tlb_params* p, const tlb_membrane_desc* mem
   if (p->dim == 3 && p->storage == TLB_F64) { set_error("3D lattices support F32/F16/BF16 storage"); return TLB_ERR_ARG; }
   int nz = p->dim == 3 ? p->nz : 1;
   if (p->nx < 4 || p->ny < 4 || (p->dim == 3 && nz < 4)) { set_error("lattice sides must be >= 4"); return TLB_ERR_ARG; }
-  if ((long long)p->nx * p->ny * nz > (1ll << 31)) { set_error("lattice too large"); return TLB_ERR_ARG; }
+  {
+    // population offsets (3Q planes of the padded cell count) are 32-bit
+    const long long cells = (long long)p->nx * p->ny * nz;
+    const long long planes = p->dim == 3 ? 3 * 19 : 3 * 9;
+    if ((cells + 64) * planes >= (1ll << 31)) {
+      set_error("lattice too large: 3Q x cells must stay below 2^31");
+      return TLB_ERR_ARG;
+    }
+  }
   if (!(p->tau > 0.5 && p->tau_phi > 0.5 && p->tau_psi > 0.5)) { set_error("relaxation times must exceed 1/2"); return TLB_ERR_ARG; }
   if (!(p->alpha > 0) || !(p->dc > 0) || p->dc > 60) { set_error("alpha > 0 and 0 < dc <= 60 required"); return TLB_ERR_ARG; }
   if (n_mem < 0 || n_mem > 8) { set_error("at most 8 membranes"); return TLB_ERR_ARG; }
@@ -258,7 +266,7 @@ static void plan(const tlb_params* p, const std::vector<HostMem>& mems, Ctx& c) 
   take(L.vn, 3 * nn * R);
   take(L.esum, 3 * NV * ne * 8);
   take(L.F, 3 * nn * R);
-  take(L.box, 6 * 4);
+  take(L.box, 12 * 4);
   const size_t nb = c.nbricks;
   take(L.bcnt, nb * 4);
   take(L.bprev, nb * 4);
@@ -321,9 +329,14 @@ tlb_status tlb_create(const tlb_params* params, const tlb_membrane_desc* mems, i
   }
   cudaStream_t st = c->stream;
   {
-    tlb_status r0 = cuda_check(cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking), "side stream");
+    // the membrane work is short and latency bound: give its stream the
+    // highest priority so its blocks go first when the collide frees SMs
+    int lo_prio = 0, hi_prio = 0;
+    cudaDeviceGetStreamPriorityRange(&lo_prio, &hi_prio);
+    tlb_status r0 = cuda_check(cudaStreamCreateWithPriority(&c->side, cudaStreamNonBlocking, hi_prio), "side stream");
     if (r0 == TLB_OK) r0 = cuda_check(cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming), "event");
     if (r0 == TLB_OK) r0 = cuda_check(cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming), "event");
+    if (r0 == TLB_OK) r0 = cuda_check(cudaEventCreateWithFlags(&c->ev_mom, cudaEventDisableTiming), "event");
     if (r0 != TLB_OK) { delete c; return r0; }
   }
   // zero everything, then set the non-zero initial values
@@ -554,6 +567,13 @@ tlb_status tlb_profile_steps(void* ctx, long n_steps, tlb_profile* out) {
   out->ms_interp = c->prof_ms[3];
   out->launches_per_step = n_steps > 0 ? c->launches / n_steps : 0;
   return TLB_OK;
+}
+
+tlb_status tlb_autotune(void* ctx, int* tile_variant, int* z_chunk) {
+  Ctx* c = (Ctx*)ctx;
+  if (!c) { set_error("ctx is NULL"); return TLB_ERR_ARG; }
+  if (!c->initialised) { set_error("tlb_autotune before tlb_init_fields"); return TLB_ERR_STATE; }
+  return c->impl->autotune(c, tile_variant, z_chunk);
 }
 
 long tlb_last_launch_count(void* ctx) {

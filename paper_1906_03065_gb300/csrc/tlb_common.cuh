@@ -86,6 +86,7 @@ struct Geo {
   int wall;        // walls at both ends of z
   long long N;     // cells
   long long P;     // plane stride of population / field arrays (>= N, padded)
+  int P32;         // P as int: every population offset (3Q planes) fits 31 bits
 };
 
 TLB_HD int wrapc(int a, int n) { return a < 0 ? a + n : (a >= n ? a - n : a); }
@@ -110,13 +111,13 @@ struct CellMoments {
 // computed once per cell, so each pulled population costs one add.
 template <class L>
 struct Nbr {
-  long long self;
-  long long row[3][3];  // [dz + 1][dy + 1]: (z + dz, y + dy) row start
-  int xs[3];            // x - 1, x, x + 1 (wrapped)
-  bool wlo, whi;        // cell touches the bottom / top wall
+  int self;
+  int row[3][3];  // [dz + 1][dy + 1]: (z + dz, y + dy) row start
+  int xs[3];      // x - 1, x, x + 1 (wrapped)
+  bool wlo, whi;  // cell touches the bottom / top wall
 
   __device__ __forceinline__ Nbr(const Geo& G, int x, int y, int z) {
-    self = ((long long)z * G.ny + y) * G.nx + x;
+    self = (z * G.ny + y) * G.nx + x;
     xs[0] = x == 0 ? G.nx - 1 : x - 1;
     xs[1] = x;
     xs[2] = x == G.nx - 1 ? 0 : x + 1;
@@ -127,14 +128,19 @@ struct Nbr {
 #pragma unroll
     for (int dz = 0; dz < 3; ++dz)
 #pragma unroll
-      for (int dy = 0; dy < 3; ++dy) row[dz][dy] = ((long long)zs[dz] * G.ny + ys[dy]) * G.nx;
+      for (int dy = 0; dy < 3; ++dy) row[dz][dy] = (zs[dz] * G.ny + ys[dy]) * G.nx;
   }
   // bounce-back applies to direction i at this cell
   __device__ __forceinline__ bool bounce(int i) const {
     return (L::cz(i) > 0 && wlo) || (L::cz(i) < 0 && whi);
   }
-  __device__ __forceinline__ long long src(int i) const {
+  __device__ __forceinline__ int src(int i) const {
     return bounce(i) ? self : row[1 - L::cz(i)][1 - L::cy(i)] + xs[1 - L::cx(i)];
+  }
+  // offset of the population of direction i arriving here, in a plane array
+  // whose plane for direction i (no bounce) or opp(i) (bounce) is given
+  __device__ __forceinline__ int off(int i, int plane_i, int plane_opp, int P32) const {
+    return (bounce(i) ? plane_opp : plane_i) * P32 + src(i);
   }
 };
 
@@ -153,18 +159,13 @@ struct Pull {
     const Nbr<L> nb(G, x, y, z);
 #pragma unroll
     for (int i = 0; i < L::Q; ++i) {
-      const bool bb = nb.bounce(i);
-      const long long src = nb.src(i);
-      const int pf = bb ? plane_f<L>(L::opp(i)) : plane_f<L>(i);
-      f[i] = to_real(__ldg(lo + (long long)pf * G.P + src));
+      f[i] = to_real(__ldg(lo + nb.off(i, plane_f<L>(i), plane_f<L>(L::opp(i)), G.P32)));
       if (i == 0) {
-        g[0] = to_real(__ldg(rest + src));
-        h[0] = to_real(__ldg(rest + G.P + src));
+        g[0] = to_real(__ldg(rest + nb.self));
+        h[0] = to_real(__ldg(rest + G.P32 + nb.self));
       } else {
-        const int pg = bb ? plane_g<L>(L::opp(i)) : plane_g<L>(i);
-        const int ph = bb ? plane_h<L>(L::opp(i)) : plane_h<L>(i);
-        g[i] = to_real(__ldg(lo + (long long)pg * G.P + src));
-        h[i] = to_real(__ldg(lo + (long long)ph * G.P + src));
+        g[i] = to_real(__ldg(lo + nb.off(i, plane_g<L>(i), plane_g<L>(L::opp(i)), G.P32)));
+        h[i] = to_real(__ldg(lo + nb.off(i, plane_h<L>(i), plane_h<L>(L::opp(i)), G.P32)));
       }
     }
   }
@@ -190,6 +191,37 @@ struct Pull {
     return m;
   }
 };
+
+// Cells the membrane work of a step touches: the marker box of the step
+// (cur[0..2] = floor(min X), cur[3..5] = -ceil(max X)) widened by `margin`
+// cells, unwrapped; walls clamp z; at most one period per axis.
+__device__ __forceinline__ void marker_box(const int* cur, int margin, const Geo& G, bool d2, int* lo, int* hi) {
+  const int n[3] = {G.nx, G.ny, G.nz};
+  for (int d = 0; d < 3; ++d) {
+    int bl = cur[d] - margin, bh = -cur[3 + d] + margin;
+    if (d == 1 && d2) { bl = 0; bh = 0; }
+    if (d == 2 && G.wall) { bl = max(bl, 0); bh = min(bh, n[2] - 1); }
+    if (bh - bl + 1 > n[d]) bh = bl + n[d] - 1;
+    if (bh < bl) bh = bl;
+    lo[d] = bl;
+    hi[d] = bh;
+  }
+}
+
+// Does the cell range [a0, a1] (per axis, a0 >= -2, a1 < n + 2) meet the box,
+// counting the periodic images of the box along periodic axes?
+__device__ __forceinline__ bool range_meets_box(const int* a0, const int* a1, const int* lo, const int* hi,
+                                                const Geo& G) {
+  const int n[3] = {G.nx, G.ny, G.nz};
+  for (int d = 0; d < 3; ++d) {
+    bool hit = false;
+    const bool per = !(d == 2 && G.wall);
+    for (int k = per ? -1 : 0; k <= (per ? 1 : 0); ++k)
+      hit |= !(hi[d] + k * n[d] < a0[d] || lo[d] + k * n[d] > a1[d]);
+    if (!hit) return false;
+  }
+  return true;
+}
 
 // Chemical potentials of App. A (eq. AppA) without the ideal-gas part of
 // mu_rho; mu_psi' adds kappa_c (psi - I) (Sec. 3.1).

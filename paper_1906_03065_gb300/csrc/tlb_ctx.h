@@ -20,6 +20,7 @@ struct ImplBase {
   virtual tlb_status read_pops(Ctx* c, double* dst) = 0;
   virtual tlb_status write_pops(Ctx* c, const double* src) = 0;
   virtual tlb_status diagnostics(Ctx* c, tlb_diag* out) = 0;
+  virtual tlb_status autotune(Ctx* c, int* variant, int* zc) = 0;
 };
 
 // CUDA events bracketing the phases of a step when profiling.
@@ -69,7 +70,7 @@ struct Ctx {
   size_t bytes = 0;
   cudaStream_t stream = nullptr;
   cudaStream_t side = nullptr;  // membrane work that overlaps the moments
-  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_mom = nullptr;
   int cur = 0;  // population buffer holding the current state
   long t = 0;
   bool initialised = false;
@@ -80,6 +81,7 @@ struct Ctx {
   int nn = 0, ne = 0, NV = 0, ncap = 0, nedge = 0;
   int nbx = 0, nby = 0, nbz = 0, nbricks = 0;
   int tiles_zc = 16;
+  int tile_variant = 0;  // collide tile shape (see Impl::collide)
   PhaseEvents* prof = nullptr;  // non-null while tlb_profile_steps runs
   double prof_ms[4] = {0, 0, 0, 0};
   ImplBase* impl = nullptr;
@@ -90,6 +92,7 @@ struct Ctx {
     if (side) cudaStreamSynchronize(side);
     if (ev_fork) cudaEventDestroy(ev_fork);
     if (ev_join) cudaEventDestroy(ev_join);
+    if (ev_mom) cudaEventDestroy(ev_mom);
     if (side) cudaStreamDestroy(side);
   }
 };

@@ -37,7 +37,8 @@ struct IBArgs {
   Real* vn;              // [nn][3] angle-weighted vertex pseudo-normal
   unsigned long long* esum;  // [ne][NV][3] coupling contributions, fixed point (CPL_SCALE)
   Real* F;               // [nn][3] node force
-  int* box;              // [6] lo xyz, hi xyz (unwrapped, inclusive)
+  int* box;              // [6] marker box accumulator: floor(min X), -ceil(max X)
+  const int* boxc;       // [6] the step's marker box (snapshot of the accumulator)
   unsigned long long* key;
   int* own;
   Real* I;
@@ -212,21 +213,11 @@ __global__ void k_box(IBArgs<Real> a) {
   }
 }
 
-// The box of cells the profile visits: marker box widened by dc + 2 cells
-// (unwrapped; walls clamp z; at most one period along every axis).
+// The box of cells the profile visits: the step's marker box widened by
+// dc + 2 cells (unwrapped; walls clamp z; at most one period per axis).
 template <class Real>
 __device__ __forceinline__ void profile_box(const IBArgs<Real>& a, int* lo, int* hi) {
-  const int n[3] = {a.G.nx, a.G.ny, a.G.nz};
-  const int m = (int)ceil((double)a.dc) + 2;
-  for (int d = 0; d < 3; ++d) {
-    int bl = a.box[d] - m, bh = -a.box[3 + d] + m;
-    if (d == 1 && a.dim == 2) { bl = 0; bh = 0; }
-    if (d == 2 && a.G.wall) { bl = max(bl, 0); bh = min(bh, n[2] - 1); }
-    if (bh - bl + 1 > n[d]) bh = bl + n[d] - 1;
-    if (bh < bl) bh = bl;
-    lo[d] = bl;
-    hi[d] = bh;
-  }
+  marker_box(a.boxc, (int)ceil((double)a.dc) + 2, a.G, a.dim == 2, lo, hi);
 }
 
 template <class Real>
@@ -933,8 +924,7 @@ __global__ void k_interp_advect(IBArgs<typename Prec<MODE>::Real> a, const typen
     Real r = 0, j[3] = {0, 0, 0};
 #pragma unroll
     for (int i = 0; i < L::Q; ++i) {
-      const int pf = nb.bounce(i) ? plane_f<L>(L::opp(i)) : plane_f<L>(i);
-      Real fi = to_real(lo[(long long)pf * G.P + nb.src(i)]);
+      Real fi = to_real(lo[nb.off(i, plane_f<L>(i), plane_f<L>(L::opp(i)), G.P32)]);
       r += fi;
       if (L::cx(i)) j[0] += L::cx(i) > 0 ? fi : -fi;
       if (L::cy(i)) j[1] += L::cy(i) > 0 ? fi : -fi;

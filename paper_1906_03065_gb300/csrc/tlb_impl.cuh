@@ -14,8 +14,12 @@ struct Impl : ImplBase {
   using Real = typename Prec<MODE>::Real;
   using Store = typename Prec<MODE>::Store;
   using Rest = typename Prec<MODE>::Rest;
-  static constexpr int TX = 32;
-  static constexpr int TY = L::DIM == 3 ? 8 : 1;
+  // tile shapes of the collide plane sweep (variant index = c->tile_variant)
+  static constexpr int NVAR = 3;
+  static constexpr int TXS[NVAR] = {32, 32, 64};
+  static constexpr int TYS3[NVAR] = {4, 8, 4};
+  static constexpr int TYS2[NVAR] = {1, 1, 1};
+  static constexpr int TXS2[NVAR] = {32, 64, 128};
 
   static Geo geo(const Ctx* c) {
     Geo g;
@@ -25,6 +29,7 @@ struct Impl : ImplBase {
     g.wall = c->p.wall_last;
     g.N = c->N;
     g.P = c->P;
+    g.P32 = (int)c->P;
     return g;
   }
 
@@ -44,6 +49,9 @@ struct Impl : ImplBase {
     a.bflag = c->ptr<unsigned char>(c->L.bflag);
     a.nbx = c->nbx;
     a.nby = c->nby;
+    a.region = 0;
+    a.boxc = c->ptr<int>(c->L.box) + 6;
+    a.box_margin = max((int)ceil(c->p.dc) + 2, 8);  // covers whole spreading bricks
     a.fe.k1 = (Real)c->p.kappa[0];
     a.fe.k2 = (Real)c->p.kappa[1];
     a.fe.k3 = (Real)c->p.kappa[2];
@@ -90,6 +98,7 @@ struct Impl : ImplBase {
     a.esum = c->ptr<unsigned long long>(c->L.esum);
     a.F = c->ptr<Real>(c->L.F);
     a.box = c->ptr<int>(c->L.box);
+    a.boxc = c->ptr<int>(c->L.box) + 6;
     a.key = c->ptr<unsigned long long>(c->L.key);
     a.own = c->ptr<int>(c->L.own);
     a.I = c->ptr<Real>(c->L.I);
@@ -122,18 +131,27 @@ struct Impl : ImplBase {
   // and vertex normals and the distance scatter here; elastic forces and the
   // brick binning in ibm_bins).  It runs on the side stream while the
   // moments of the step are computed.
-  static tlb_status ibm_positions(Ctx* c, IBArgs<Real>& a, cudaStream_t s, bool fresh_box) {
+  static tlb_status ibm_positions(Ctx* c, IBArgs<Real>& a, cudaStream_t s) {
     TLB_CUDA(cudaMemsetAsync(a.esum, 0, c->L.esum.bytes, s));
-    if (fresh_box) {  // set-up or overwritten markers: box of the current markers
-      TLB_CUDA(cudaMemsetAsync(a.box, 0x7F, 6 * sizeof(int), s));
-      k_box<Real><<<blocks(c->nn, 128), 128, 0, s>>>(a);
-      TLB_LAUNCHED(c, "k_box");
-    }
     k_geometry<Real><<<blocks((long long)c->ne + c->nn, 128), 128, 0, s>>>(a);
     TLB_LAUNCHED(c, "k_geometry");
     const long long nfeat = (long long)c->ne + c->nedge + c->nn;
     k_dist_scatter<Real><<<blocks(nfeat, SCATTER_WARPS), SCATTER_WARPS * 32, 0, s>>>(a);
     TLB_LAUNCHED(c, "k_dist_scatter");
+    return TLB_OK;
+  }
+
+  // The step's marker box: recompute the accumulator if the markers were
+  // overwritten, copy it to the snapshot every kernel of the step reads, and
+  // reset it for the advection of this step.
+  static tlb_status snapshot_box(Ctx* c, IBArgs<Real>& a, cudaStream_t s, bool fresh) {
+    if (fresh) {
+      TLB_CUDA(cudaMemsetAsync(a.box, 0x7F, 6 * sizeof(int), s));
+      k_box<Real><<<blocks(c->nn, 128), 128, 0, s>>>(a);
+      TLB_LAUNCHED(c, "k_box");
+    }
+    TLB_CUDA(cudaMemcpyAsync((void*)a.boxc, a.box, 6 * sizeof(int), cudaMemcpyDeviceToDevice, s));
+    TLB_CUDA(cudaMemsetAsync(a.box, 0x7F, 6 * sizeof(int), s));
     return TLB_OK;
   }
 
@@ -153,13 +171,12 @@ struct Impl : ImplBase {
   }
 
   // Profile I of the band and the rest of the box, and the coupling sums
-  // (needs psi(t)); then the box accumulator is reset for the advection.
+  // (needs psi(t)).
   static tlb_status ibm_band(Ctx* c, IBArgs<Real>& a, cudaStream_t s) {
     k_band<Real><<<8 * 152, 256, 0, s>>>(a);
     TLB_LAUNCHED(c, "k_band");
     k_fill<Real><<<blocks((long long)c->nx * c->ny * 32, 256), 256, 0, s>>>(a);
     TLB_LAUNCHED(c, "k_fill");
-    TLB_CUDA(cudaMemsetAsync(a.box, 0x7F, 6 * sizeof(int), s));
     return TLB_OK;
   }
 
@@ -175,7 +192,8 @@ struct Impl : ImplBase {
     IBArgs<Real> ia = ibargs(c);
     // membrane profile I(X0) (I_out everywhere when there are no membranes)
     if (c->nn > 0) {
-      tlb_status st = ibm_positions(c, ia, s, true);
+      tlb_status st = snapshot_box(c, ia, s, true);
+      if (st == TLB_OK) st = ibm_positions(c, ia, s);
       if (st == TLB_OK) st = ibm_band(c, ia, s);
       if (st != TLB_OK) return st;
       c->box_stale = true;  // the first step recomputes the box of X0
@@ -248,6 +266,73 @@ struct Impl : ImplBase {
     return TLB_OK;
   }
 
+  template <int TXv, int TYv>
+  static tlb_status collide_tile(Ctx* c, LBArgs<MODE>& la, cudaStream_t s) {
+    dim3 grid(blocks(c->nx, TXv), blocks(c->ny, TYv), blocks(c->nz, c->tiles_zc));
+    k_collide<L, MODE, TXv, TYv><<<grid, TXv * TYv, 0, s>>>(la);
+    TLB_LAUNCHED(c, "k_collide");
+    return TLB_OK;
+  }
+
+  static tlb_status collide(Ctx* c, LBArgs<MODE>& la, cudaStream_t s) {
+    if constexpr (L::DIM == 3) {
+      switch (c->tile_variant) {
+        case 1: return collide_tile<32, 8>(c, la, s);
+        case 2: return collide_tile<64, 4>(c, la, s);
+        default: return collide_tile<32, 4>(c, la, s);
+      }
+    } else {
+      switch (c->tile_variant) {
+        case 1: return collide_tile<64, 1>(c, la, s);
+        case 2: return collide_tile<128, 1>(c, la, s);
+        default: return collide_tile<32, 1>(c, la, s);
+      }
+    }
+  }
+
+  // Choose the collide tile shape and z chunk by timing the kernel on the
+  // current state (it only reads the current buffer, so repeats are harmless).
+  tlb_status autotune(Ctx* c, int* variant, int* zc) override {
+    cudaStream_t s = c->stream;
+    LBArgs<MODE> la = lbargs(c, c->cur);
+    k_moments<L, MODE><<<blocks(c->N, 256), 256, 0, s>>>(la);
+    TLB_LAUNCHED(c, "k_moments");
+    cudaEvent_t e0, e1;
+    TLB_CUDA(cudaEventCreate(&e0));
+    TLB_CUDA(cudaEventCreate(&e1));
+    float best = 1e30f;
+    int bv = c->tile_variant, bz = c->tiles_zc;
+    const int zcs[6] = {4, 8, 12, 16, 32, 64};
+    for (int v = 0; v < NVAR; ++v)
+      for (int zi = 0; zi < 6; ++zi) {
+        if (zcs[zi] > c->nz && zi > 0 && zcs[zi - 1] >= c->nz) continue;
+        c->tile_variant = v;
+        c->tiles_zc = min(zcs[zi], c->nz);
+        la.zc = c->tiles_zc;
+        tlb_status st = collide(c, la, s);  // warm
+        float tmin = 1e30f;
+        for (int r = 0; r < 3 && st == TLB_OK; ++r) {
+          cudaEventRecord(e0, s);
+          st = collide(c, la, s);
+          cudaEventRecord(e1, s);
+          cudaEventSynchronize(e1);
+          float ms = 0;
+          cudaEventElapsedTime(&ms, e0, e1);
+          tmin = fminf(tmin, ms);
+        }
+        if (st != TLB_OK) { cudaEventDestroy(e0); cudaEventDestroy(e1); return st; }
+        if (tmin < best) { best = tmin; bv = v; bz = c->tiles_zc; }
+      }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    c->tile_variant = bv;
+    c->tiles_zc = bz;
+    if (variant) *variant = bv;
+    if (zc) *zc = bz;
+    TLB_CUDA(cudaStreamSynchronize(s));
+    return TLB_OK;
+  }
+
   static tlb_status mark(Ctx* c, int k) {
     if (c->prof) TLB_CUDA(cudaEventRecord(c->prof->ev[k], c->stream));
     return TLB_OK;
@@ -267,31 +352,48 @@ struct Impl : ImplBase {
   tlb_status step(Ctx* c, long n) override {
     cudaStream_t s = c->stream;
     const long long N = c->N;
-    dim3 grid(blocks(c->nx, TX), blocks(c->ny, TY), blocks(c->nz, c->tiles_zc));
     tlb_status st;
     for (long k = 0; k < n; ++k) {
       LBArgs<MODE> la = lbargs(c, c->cur);
       IBArgs<Real> ia = ibargs(c);
+      if (c->nn > 0 && (st = snapshot_box(c, ia, s, c->box_stale)) != TLB_OK) return st;
+      c->box_stale = false;
       if ((st = mark(c, 0)) != TLB_OK) return st;
+      const bool overlap = c->nn > 0 && !c->prof;
       if (c->nn > 0) {  // fork: position-only membrane work on the side stream
         TLB_CUDA(cudaEventRecord(c->ev_fork, s));
         TLB_CUDA(cudaStreamWaitEvent(c->side, c->ev_fork, 0));
-        if ((st = ibm_positions(c, ia, c->side, c->box_stale)) != TLB_OK) return st;
+        if ((st = ibm_positions(c, ia, c->side)) != TLB_OK) return st;
         if ((st = ibm_bins(c, ia, c->side)) != TLB_OK) return st;
-        c->box_stale = false;
-        TLB_CUDA(cudaEventRecord(c->ev_join, c->side));
       }
       k_moments<L, MODE><<<blocks(N, 256), 256, 0, s>>>(la);
       TLB_LAUNCHED(c, "k_moments");
       if ((st = mark(c, 1)) != TLB_OK) return st;
-      if (c->nn > 0) {  // join
+      if (overlap) {
+        // the profile, coupling sums and spreading need psi(t): they follow
+        // the moments on the side stream while the tiles away from the
+        // membrane are collided on the main stream
+        TLB_CUDA(cudaEventRecord(c->ev_mom, s));
+        TLB_CUDA(cudaStreamWaitEvent(c->side, c->ev_mom, 0));
+        if ((st = ibm_band(c, ia, c->side)) != TLB_OK) return st;
+        if ((st = ibm_spread(c, ia, c->side)) != TLB_OK) return st;
+        TLB_CUDA(cudaEventRecord(c->ev_join, c->side));
+        la.region = 1;
+        if ((st = collide(c, la, s)) != TLB_OK) return st;
+        if ((st = mark(c, 2)) != TLB_OK) return st;
         TLB_CUDA(cudaStreamWaitEvent(s, c->ev_join, 0));
-        if ((st = ibm_band(c, ia, s)) != TLB_OK) return st;
-        if ((st = ibm_spread(c, ia, s)) != TLB_OK) return st;
+        la.region = 2;
+        if ((st = collide(c, la, s)) != TLB_OK) return st;
+      } else {
+        if (c->nn > 0) {  // serial order (used when timing the phases)
+          TLB_CUDA(cudaEventRecord(c->ev_join, c->side));
+          TLB_CUDA(cudaStreamWaitEvent(s, c->ev_join, 0));
+          if ((st = ibm_band(c, ia, s)) != TLB_OK) return st;
+          if ((st = ibm_spread(c, ia, s)) != TLB_OK) return st;
+        }
+        if ((st = mark(c, 2)) != TLB_OK) return st;
+        if ((st = collide(c, la, s)) != TLB_OK) return st;
       }
-      if ((st = mark(c, 2)) != TLB_OK) return st;
-      k_collide<L, MODE, TX, TY><<<grid, TX * TY, 0, s>>>(la);
-      TLB_LAUNCHED(c, "k_collide");
       if ((st = mark(c, 3)) != TLB_OK) return st;
       if (c->nn > 0) {
         k_interp_advect<L, MODE><<<blocks((long long)c->nn * 32, 128), 128, 0, s>>>(ia, la.lo_dst);

@@ -22,6 +22,10 @@ struct LBArgs {
   Real* ftot;       // [3][P] total force of the step (read by the interpolation)
   const unsigned char* bflag;  // per 4x4x4 brick: markers spread force into it
   int nbx, nby;                // brick grid (x, y)
+  int region;                  // 0: every tile; 1: tiles away from the membrane
+                               // box; 2: tiles that meet it
+  const int* boxc;             // the step's marker box
+  int box_margin;              // cells the membrane work reaches beyond it
   FEParams<Real> fe;
   Real om, om_phi, om_psi;  // 1/tau
   Real gphi, gpsi;          // Gamma_phi, Gamma_psi
@@ -62,7 +66,7 @@ __device__ __forceinline__ Real eq_poly(Real cu, Real uu) {
 // needs the Laplacian of the moments, the force needs the gradient of mu) is
 // served on chip.
 template <class L, int MODE, int TX, int TY>
-__global__ void __launch_bounds__(TX* TY) k_collide(LBArgs<MODE> a) {
+__global__ void __launch_bounds__(TX* TY, 640 / (TX * TY)) k_collide(LBArgs<MODE> a) {
   using Real = typename Prec<MODE>::Real;
   using Store = typename Prec<MODE>::Store;
   using Rest = typename Prec<MODE>::Rest;
@@ -82,6 +86,18 @@ __global__ void __launch_bounds__(TX* TY) k_collide(LBArgs<MODE> a) {
   const int z1 = min(z0 + a.zc, G.nz);
   const int x = x0 + tx, y = y0 + ty;
   const bool active = x < G.nx && y < G.ny;
+
+  // Split launch: tiles whose cells, potentials and force stencils (halo 2)
+  // stay outside the membrane box do not read anything the membrane work of
+  // the step writes, so they run while that work is in flight.
+  if (a.region != 0) {
+    int lo[3], hi[3];
+    marker_box(a.boxc, a.box_margin, G, !D3, lo, hi);
+    const int r0[3] = {x0 - 2, D3 ? y0 - 2 : 0, z0 - 2};
+    const int r1[3] = {x0 + TX + 1, D3 ? y0 + TY + 1 : 0, z1 + 1};
+    const bool near = range_meets_box(r0, r1, lo, hi, G);
+    if ((a.region == 1) == near) return;
+  }
 
   auto modn = [](int v, int n) { v %= n; return v < 0 ? v + n : v; };
   auto plane_src = [&](int p) { return G.wall ? min(max(p, 0), G.nz - 1) : modn(p, G.nz); };
@@ -138,24 +154,28 @@ __global__ void __launch_bounds__(TX* TY) k_collide(LBArgs<MODE> a) {
     }
   };
 
+  // Collision of one cell.  rho, phi, psi come from the moment ring (k_moments
+  // summed them in the same order as Pull::moments); the three population
+  // sets are pulled, collided and stored one after another, so only one set
+  // is live in registers at a time.
   auto collide = [&](int zz) {
     if (!active) return;
-    const long long n = ((long long)zz * G.ny + y) * G.nx + x;
-    Pull<L, MODE> pl;
-    pl.load(a.lo_src, a.rest_src, G, x, y, zz);
-    const CellMoments<Real> m = pl.moments();
-    const Real rho = Real(1) + m.drho, phi = m.phi, psi = m.psi;
+    const Nbr<L> nb(G, x, y, zz);
+    const int n = nb.self;
+    const int sm5 = (zz + 10) % 5;
+    const int mc = (ty + HY) * MX + tx + 2;
+    const Real rho = smom[sm5][0][mc], phi = smom[sm5][1][mc], psi = smom[sm5][2][mc];
     // gradients of the potentials (radius 1, isotropic stencil)
     Real gm[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
     const int ux = tx + 1, uy = ty + (D3 ? 1 : 0);
 #pragma unroll
     for (int i = 1; i < Q; ++i) {
       const int s = (zz + L::cz(i) + 9) % 3;
-      const int nb = (uy + L::cy(i)) * UX + ux + L::cx(i);
+      const int nbi = (uy + L::cy(i)) * UX + ux + L::cx(i);
       const Real w = Real(L::w(i));
 #pragma unroll
       for (int q = 0; q < 3; ++q) {
-        const Real v = w * smu[s][q][nb];
+        const Real v = w * smu[s][q][nbi];
         if (L::cx(i)) gm[q][0] += L::cx(i) > 0 ? v : -v;
         if (L::cy(i)) gm[q][1] += L::cy(i) > 0 ? v : -v;
         if (L::cz(i)) gm[q][2] += L::cz(i) > 0 ? v : -v;
@@ -166,19 +186,34 @@ __global__ void __launch_bounds__(TX* TY) k_collide(LBArgs<MODE> a) {
     const Real mup = smu[sc][1][cc], mus = smu[sc][2][cc];
     // force: f_FE = -rho grad mu~rho - phi grad mu_phi - psi grad mu_psi' (+ f_IB
     // inside the bricks the markers spread into)
-    const bool ib = a.bflag[((zz >> 2) * a.nby + (y >> 2)) * a.nbx + (x >> 2)] != 0;
+    const bool ib = a.region != 1 && a.bflag[((zz >> 2) * a.nby + (y >> 2)) * a.nbx + (x >> 2)] != 0;
     Real F[3];
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
       F[d] = -Real(3) * (rho * gm[0][d] + phi * gm[1][d] + psi * gm[2][d]);
-      if (ib) F[d] += a.fib[d * G.P + n];
+      if (ib) F[d] += a.fib[d * G.P32 + n];
     }
     if (!D3) F[1] = 0;
+    // f: pull, first moment, BGK + exact difference method (eq. LBE) for f_i - w_i
+    Real fv[Q];
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+      fv[i] = to_real(__ldg(a.lo_src + nb.off(i, plane_f<L>(i), plane_f<L>(L::opp(i)), G.P32)));
+    }
+    Real drho = 0, jx = 0, jy = 0, jz = 0;
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+      drho += fv[i];
+      if (L::cx(i)) jx += L::cx(i) > 0 ? fv[i] : -fv[i];
+      if (L::cy(i)) jy += L::cy(i) > 0 ? fv[i] : -fv[i];
+      if (L::cz(i)) jz += L::cz(i) > 0 ? fv[i] : -fv[i];
+    }
     const Real irho = Real(1) / rho;
+    const Real j[3] = {jx, jy, jz};
     Real u[3], du[3], v[3], us[3];
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
-      u[d] = m.j[d] * irho;
+      u[d] = j[d] * irho;
       du[d] = F[d] * irho;
       v[d] = u[d] + Real(0.5) * du[d];
       us[d] = u[d] + u[d] + du[d];  // u + (u + du)
@@ -186,35 +221,51 @@ __global__ void __launch_bounds__(TX* TY) k_collide(LBArgs<MODE> a) {
     const Real uu = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
     const Real vv = v[0] * v[0] + v[1] * v[1] + v[2] * v[2];
     const Real dus = du[0] * us[0] + du[1] * us[1] + du[2] * us[2];
-    const Real om = a.om, omp = a.om_phi, oms = a.om_psi;
-    const Real w0 = Real(L::w(0));
+    const Real om = a.om;
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
       const Real w = Real(L::w(i));
       const Real cu = L::cx(i) * u[0] + L::cy(i) * u[1] + L::cz(i) * u[2];
       const Real cdu = L::cx(i) * du[0] + L::cy(i) * du[1] + L::cz(i) * du[2];
       const Real cus = L::cx(i) * us[0] + L::cy(i) * us[1] + L::cz(i) * us[2];
-      // BGK + exact difference method (eq. LBE), written for f_i - w_i
       const Real dP = Real(3) * cdu + Real(4.5) * cdu * cus - Real(1.5) * dus;
-      const Real fn = (Real(1) - om) * pl.f[i] + om * w * (m.drho + rho * eq_poly(cu, uu)) + w * rho * dP;
-      a.lo_dst[(long long)plane_f<L>(i) * G.P + n] = from_real<Store>(fn);
-      if (i > 0) {
+      const Real fn = (Real(1) - om) * fv[i] + om * w * (drho + rho * eq_poly(cu, uu)) + w * rho * dP;
+      a.lo_dst[plane_f<L>(i) * G.P32 + n] = from_real<Store>(fn);
+    }
+    // g and h: BGK towards the order-parameter equilibria at v (eq. EDF); the
+    // rest population closes the zeroth moment
+    const Real w0 = Real(L::w(0));
+#pragma unroll
+    for (int set = 0; set < 2; ++set) {
+      const Real om_s = set == 0 ? a.om_phi : a.om_psi;
+      const Real Gm = set == 0 ? a.gphi * mup : a.gpsi * mus;
+      const Real ord = set == 0 ? phi : psi;
+      Real gv[Q];
+#pragma unroll
+      for (int i = 0; i < Q; ++i) {
+        if (i == 0) {
+          gv[0] = to_real(__ldg(a.rest_src + (set == 0 ? 0 : G.P32) + n));
+        } else {
+          const int o = set == 0 ? nb.off(i, plane_g<L>(i), plane_g<L>(L::opp(i)), G.P32)
+                                 : nb.off(i, plane_h<L>(i), plane_h<L>(L::opp(i)), G.P32);
+          gv[i] = to_real(__ldg(a.lo_src + o));
+        }
+      }
+#pragma unroll
+      for (int i = 1; i < Q; ++i) {
+        const Real w = Real(L::w(i));
         const Real cv = L::cx(i) * v[0] + L::cy(i) * v[1] + L::cz(i) * v[2];
         const Real pv = Real(3) * cv + Real(4.5) * cv * cv - Real(1.5) * vv;
-        const Real ge = w * (Real(3) * a.gphi * mup + phi * pv);
-        const Real he = w * (Real(3) * a.gpsi * mus + psi * pv);
-        a.lo_dst[(long long)plane_g<L>(i) * G.P + n] = from_real<Store>((Real(1) - omp) * pl.g[i] + omp * ge);
-        a.lo_dst[(long long)plane_h<L>(i) * G.P + n] = from_real<Store>((Real(1) - oms) * pl.h[i] + oms * he);
+        const Real ge = w * (Real(3) * Gm + ord * pv);
+        const int pp = set == 0 ? plane_g<L>(i) : plane_h<L>(i);
+        a.lo_dst[pp * G.P32 + n] = from_real<Store>((Real(1) - om_s) * gv[i] + om_s * ge);
       }
+      const Real ge0 = ord - Real(3) * Gm * (Real(1) - w0) - Real(1.5) * w0 * ord * vv;
+      a.rest_dst[(set == 0 ? 0 : G.P32) + n] = from_real<Rest>((Real(1) - om_s) * gv[0] + om_s * ge0);
     }
-    // rest populations close the zeroth moments (eq. EDF, i = 0)
-    const Real ge0 = phi - Real(3) * a.gphi * mup * (Real(1) - w0) - Real(1.5) * w0 * phi * vv;
-    const Real he0 = psi - Real(3) * a.gpsi * mus * (Real(1) - w0) - Real(1.5) * w0 * psi * vv;
-    a.rest_dst[n] = from_real<Rest>((Real(1) - omp) * pl.g[0] + omp * ge0);
-    a.rest_dst[G.P + n] = from_real<Rest>((Real(1) - oms) * pl.h[0] + oms * he0);
     if (ib)
 #pragma unroll
-      for (int d = 0; d < 3; ++d) a.ftot[d * G.P + n] = F[d];
+      for (int d = 0; d < 3; ++d) a.ftot[d * G.P32 + n] = F[d];
     if (!(rho == rho) || !(phi == phi) || !(psi == psi)) atomicOr(a.status, (unsigned)ST_NAN);
   };
 

@@ -55,6 +55,7 @@ static tlb_status run_static(Ctx* c, double* scratch, tlb_diag* out) {
   G.wall = c->p.wall_last;
   G.N = c->N;
   G.P = c->P;
+  G.P32 = (int)c->P;
   double* part = scratch;
   double* meas = scratch + 3 * TLB_STATIC_BLOCKS;
   // every partial slot, total and measure is overwritten below; nothing in
