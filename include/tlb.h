@@ -179,6 +179,18 @@ tlb_status tlb_diagnostics(void* ctx, tlb_diag* out);
  * - Calls no cudaMalloc/cudaFree or any allocating routine. */
 tlb_status tlb_diagnostics_static(void* ctx, tlb_diag* out);
 
+/* Equilibrium residual in FP64 (synchronises the stream).  out[0] and
+ * out[1]: the largest change of phi and of psi at any cell; out[2]: the
+ * largest change of any coordinate of any membrane marker; each since the
+ * reference state, which is the state at the previous tlb_residual call (or
+ * at tlb_init_fields).  out[3] = max(out[0..2]) / (steps since the
+ * reference), 0 if no step was taken.  The current state becomes the new
+ * reference.  A NaN reads as +inf, so a diverged run never looks converged.
+ * The paper says only that runs were continued until equilibrium was
+ * reached (Sec. 4) and gives no criterion; this residual, taken every K
+ * steps and compared with a tolerance, is the library's reading of it. */
+tlb_status tlb_residual(void* ctx, double out[4]);
+
 /* Per-phase device time of n_steps steps, measured with CUDA events on the
  * context stream around each phase (synchronises the stream).  Phases:
  * moments (streamed-population moments), ibm (profile I, membrane and
@@ -204,6 +216,84 @@ long tlb_last_launch_count(void* ctx);
 
 /* Release the context (the arena stays owned by the caller). */
 void tlb_destroy(void* ctx);
+
+/* ---------------------------------------------------------------- batches
+ * A batch advances many independent lattices together -- a parameter sweep
+ * whose instances differ in size, parameters and membranes but share dim
+ * and storage.  Each of the six phases of a step is one persistent kernel
+ * launch over the work of every active instance, and two steps are
+ * captured in one CUDA graph, so the launch count does not grow with the
+ * number of instances.  Every instance is an ordinary context living in a
+ * sub-arena of the batch arena, advanced by the same kernel bodies as
+ * tlb_step: the state is the one tlb_step gives it alone (identical bits in
+ * FP64; in FP32 the membrane kernels may round differently in the last
+ * place, because the compiler may fuse multiply-adds differently inside the
+ * batched kernels).  Not in the paper: it is
+ * the sweep over capsule and fluid parameters of its Sec. 4 run as one
+ * job. */
+typedef struct {
+  tlb_params params;
+  const tlb_membrane_desc* mems; /* host, borrowed for the call */
+  int n_mem;
+} tlb_instance_desc;
+
+/* Arena bytes of a batch of n_inst instances (each instance's
+ * tlb_state_bytes, 256-byte aligned, plus about 2.1 KB of tables per
+ * instance).  TLB_ERR_ARG if n_inst is not in 1..4096, an instance is
+ * invalid (message names it) or dim/storage differ between instances. */
+tlb_status tlb_batch_state_bytes(const tlb_instance_desc* inst, int n_inst, size_t* bytes);
+
+/* Create the batch in `arena` (device, 256-byte aligned, at least
+ * tlb_batch_state_bytes; owned by the caller until tlb_batch_destroy).
+ * Every instance is created as by tlb_create on the given stream and is
+ * active.  Instances must then be initialised (tlb_init_fields on the
+ * handles of tlb_batch_instance).  Allocates no device memory. */
+tlb_status tlb_batch_create(const tlb_instance_desc* inst, int n_inst, void* arena, size_t bytes,
+                            void* cuda_stream, void** batch_out);
+
+/* Context of instance i (borrowed: valid until tlb_batch_destroy; never
+ * pass it to tlb_destroy).  Every single-context call works on it;
+ * tlb_step on it advances that instance alone. */
+tlb_status tlb_batch_instance(void* batch, int i, void** ctx_out);
+
+/* Select the instances the batch calls advance: flags[i] != 0 (n_inst
+ * entries, host).  All instances are active after tlb_batch_create. */
+tlb_status tlb_batch_set_active(void* batch, const int* flags);
+
+/* Advance every active instance n_steps steps (enqueued on the stream; the
+ * host synchronises only while uploading the argument tables).
+ * TLB_ERR_STATE if an active instance is not initialised. */
+tlb_status tlb_batch_step(void* batch, long n_steps);
+
+/* Run to equilibrium: advance the active instances in chunks of
+ * check_every steps; after each chunk take every active instance's
+ * residual (tlb_residual's out[3]) in one launch and deactivate the
+ * instances at or below tol.  Returns when no instance is active or after
+ * max_steps steps.  steps_done[i] = the step count t of instance i and
+ * residual[i] = its last residual (NaN if it was inactive throughout); both
+ * n_inst entries on the host, or NULL.  Synchronises the stream. */
+tlb_status tlb_batch_run(void* batch, long max_steps, long check_every, double tol, long* steps_done,
+                         double* residual);
+
+/* Collide tile shape and z chunk of the batch, chosen by timing the batched
+ * collide on the current state (not advanced); as tlb_autotune. */
+tlb_status tlb_batch_autotune(void* batch, int* tile_variant, int* z_chunk);
+
+/* Device time of each phase of n_steps batched steps (direct launches,
+ * CUDA events around each phase; the state advances as by tlb_batch_step).
+ * ms_per_phase[0..5] (host) receives the totals in ms of: moments with the
+ * marker geometry and brick counts; elastic forces, distance scatter and
+ * brick compaction; profile band and brick lists; spreading and profile
+ * fill; collide; interpolation and advection.  Synchronises the stream. */
+tlb_status tlb_batch_profile_steps(void* batch, long n_steps, double* ms_per_phase);
+
+/* Kernel launches made by the last tlb_batch_step or tlb_batch_run (each
+ * kernel of a graph launch counted). */
+long tlb_batch_launch_count(void* batch);
+
+/* Destroy the batch and its instance contexts (the arena stays the
+ * caller's). */
+void tlb_batch_destroy(void* batch);
 
 /* Message of the last failed call on this thread ("" if none). */
 const char* tlb_last_error(void);

@@ -166,6 +166,7 @@ class Oracle:
             self._u_arr = np.ascontiguousarray(u, dtype=np.float64)
             uptr = _dp(self._u_arr)
         lib().or_init(self.h, cptr, uptr)
+        self._res_ref = self._res_state()
 
     def step(self, n: int = 1):
         lib().or_step(self.h, int(n))
@@ -196,6 +197,27 @@ class Oracle:
         out = np.zeros(self.N)
         lib().or_get_field(self.h, FIELDS[name], _dp(out))
         return out
+
+    # equilibrium residual --------------------------------------------------
+    def _res_state(self):
+        X = [self.nodes(m) for m in range(len(self.nn))]
+        X = np.concatenate(X) if X else np.zeros((0, 3))
+        return self.t, self.field("phi"), self.field("psi"), X
+
+    def residual(self) -> np.ndarray:
+        """Convergence residual of an equilibrium run (the paper gives no
+        criterion, Sec. 4; this is the reading used throughout): the largest
+        change of phi and of psi over the cells and of any marker coordinate
+        since the reference state (the previous call, or init), and the
+        largest of the three divided by the steps in between.  The current
+        state becomes the reference.  Returns [dphi, dpsi, dX, r]."""
+        t0, phi0, psi0, X0 = self._res_ref
+        t, phi, psi, X = cur = self._res_state()
+        d = np.array([np.max(np.abs(phi - phi0)), np.max(np.abs(psi - psi0)),
+                      np.max(np.abs(X - X0)) if X.size else 0.0])
+        self._res_ref = cur
+        r = d.max() / (t - t0) if t > t0 else 0.0
+        return np.array([d[0], d[1], d[2], r])
 
     def masses(self) -> np.ndarray:
         out = np.zeros(3)

@@ -45,6 +45,10 @@ class _Mem(C.Structure):
                 ("skalak_G", C.c_double), ("skalak_C", C.c_double)]
 
 
+class _Inst(C.Structure):
+    _fields_ = [("params", _Params), ("mems", C.POINTER(_Mem)), ("n_mem", C.c_int)]
+
+
 class Diag(C.Structure):
     _fields_ = [("step", C.c_long), ("mass", C.c_double * 3), ("umax", C.c_double),
                 ("n_caps", C.c_int), ("area", C.c_double * 8), ("volume", C.c_double * 8)]
@@ -81,6 +85,24 @@ def lib():
         L.tlb_autotune.restype = C.c_int
         L.tlb_last_launch_count.argtypes = [vp]
         L.tlb_last_launch_count.restype = C.c_long
+        L.tlb_residual.argtypes = [vp, dp]
+        L.tlb_residual.restype = C.c_int
+        ip, lp = C.POINTER(C.c_int), C.POINTER(C.c_long)
+        L.tlb_batch_state_bytes.argtypes = [C.POINTER(_Inst), C.c_int, C.POINTER(sz)]
+        L.tlb_batch_create.argtypes = [C.POINTER(_Inst), C.c_int, vp, sz, vp, C.POINTER(vp)]
+        L.tlb_batch_instance.argtypes = [vp, C.c_int, C.POINTER(vp)]
+        L.tlb_batch_set_active.argtypes = [vp, ip]
+        L.tlb_batch_step.argtypes = [vp, C.c_long]
+        L.tlb_batch_run.argtypes = [vp, C.c_long, C.c_long, C.c_double, lp, dp]
+        L.tlb_batch_autotune.argtypes = [vp, ip, ip]
+        for n in ("tlb_batch_state_bytes", "tlb_batch_create", "tlb_batch_instance", "tlb_batch_set_active",
+                  "tlb_batch_step", "tlb_batch_run", "tlb_batch_autotune"):
+            getattr(L, n).restype = C.c_int
+        L.tlb_batch_profile_steps.argtypes = [vp, C.c_long, dp]
+        L.tlb_batch_profile_steps.restype = C.c_int
+        L.tlb_batch_launch_count.argtypes = [vp]
+        L.tlb_batch_launch_count.restype = C.c_long
+        L.tlb_batch_destroy.argtypes = [vp]
         L.tlb_destroy.argtypes = [vp]
         L.tlb_last_error.restype = C.c_char_p
         for n in ("tlb_state_bytes", "tlb_create", "tlb_init_fields", "tlb_step", "tlb_read_field",
@@ -117,6 +139,23 @@ def make_params(p) -> _Params:
     return cp
 
 
+def _marshal_membranes(wl, keep):
+    """tlb_membrane_desc array of a workload; arrays it points to go to ``keep``."""
+    mems = (_Mem * max(1, len(wl.membranes)))()
+    for i, m in enumerate(wl.membranes):
+        X = np.ascontiguousarray(m.X, dtype=np.float64)
+        E = np.ascontiguousarray(m.elems if m.elems is not None else np.zeros((1, 3)), dtype=np.int32)
+        keep += [X, E]
+        mems[i].kind = m.kind
+        mems[i].n_nodes = X.shape[0]
+        mems[i].n_elems = E.shape[0] if m.kind == 1 else 0
+        mems[i].X0 = _dp(X)
+        mems[i].elems = E.ctypes.data_as(C.POINTER(C.c_int)) if m.kind == 1 else None
+        mems[i].ks, mems[i].kb = m.ks, m.kb
+        mems[i].skalak_G, mems[i].skalak_C = m.G, m.C
+    return mems
+
+
 class Simulation:
     """One lattice with its membranes on the current CUDA device.
 
@@ -124,29 +163,25 @@ class Simulation:
     ``device``; the stream is torch's current stream unless given.
     """
 
-    def __init__(self, wl, device="cuda:0", stream=None):
-        import torch
-        L = lib()
+    def __init__(self, wl, device="cuda:0", stream=None, _handle=None, _owner=None):
         self.wl = wl
         p = wl.params
         self.p = p
-        self._cp = make_params(p)
-        self._keep = []
-        mems = (_Mem * max(1, len(wl.membranes)))()
-        for i, m in enumerate(wl.membranes):
-            X = np.ascontiguousarray(m.X, dtype=np.float64)
-            E = np.ascontiguousarray(m.elems if m.elems is not None else np.zeros((1, 3)), dtype=np.int32)
-            self._keep += [X, E]
-            mems[i].kind = m.kind
-            mems[i].n_nodes = X.shape[0]
-            mems[i].n_elems = E.shape[0] if m.kind == 1 else 0
-            mems[i].X0 = _dp(X)
-            mems[i].elems = E.ctypes.data_as(C.POINTER(C.c_int)) if m.kind == 1 else None
-            mems[i].ks, mems[i].kb = m.ks, m.kb
-            mems[i].skalak_G, mems[i].skalak_C = m.G, m.C
-        self._mems = mems
         self.n_mem = len(wl.membranes)
         self.nn = [m.X.shape[0] for m in wl.membranes]
+        self.N = p.nx * p.ny * (p.nz if p.dim == 3 else 1)
+        self.Q = 19 if p.dim == 3 else 9
+        if _handle is not None:  # instance of a Batch: borrowed handle
+            self.h = _handle
+            self._owner = _owner
+            return
+        self._owner = None
+        import torch
+        L = lib()
+        self._cp = make_params(p)
+        self._keep = []
+        mems = _marshal_membranes(wl, self._keep)
+        self._mems = mems
         nbytes = C.c_size_t(0)
         _check(L.tlb_state_bytes(C.byref(self._cp), mems, self.n_mem, C.byref(nbytes)))
         self.nbytes = nbytes.value
@@ -160,12 +195,10 @@ class Simulation:
             _check(L.tlb_create(C.byref(self._cp), mems, self.n_mem, C.c_void_p(aligned),
                                 C.c_size_t(self.nbytes), C.c_void_p(self.stream.cuda_stream), C.byref(h)))
         self.h = h
-        self.N = p.nx * p.ny * (p.nz if p.dim == 3 else 1)
-        self.Q = 19 if p.dim == 3 else 9
 
     def __del__(self):
         try:
-            if getattr(self, "h", None) is not None and self.h.value:
+            if getattr(self, "_owner", None) is None and getattr(self, "h", None) is not None and self.h.value:
                 lib().tlb_destroy(self.h)
                 self.h = None
         except Exception:
@@ -228,9 +261,108 @@ class Simulation:
         _check(lib().tlb_diagnostics(self.h, C.byref(d)))
         return d
 
+    def residual(self) -> np.ndarray:
+        """[max |d phi|, max |d psi|, max |d X|, residual] since the last call
+        (or init); see tlb_residual."""
+        out = np.zeros(4)
+        _check(lib().tlb_residual(self.h, _dp(out)))
+        return out
+
     def diagnostics_static(self) -> Diag:
         """Diagnostics with the library's fixed scratch array (no device
         memory from the caller; see tlb_diagnostics_static in tlb.h)."""
         d = Diag()
         _check(lib().tlb_diagnostics_static(self.h, C.byref(d)))
         return d
+
+
+class Batch:
+    """Independent lattices of one dim and storage stepped together (one
+    persistent launch per phase, graph-captured).  ``wls`` is a list of
+    ``workloads.Workload``; ``batch[i]`` is instance i as a Simulation whose
+    handle the batch owns."""
+
+    def __init__(self, wls, device="cuda:0", stream=None):
+        import torch
+        L = lib()
+        self.wls = list(wls)
+        n = len(self.wls)
+        self._keep = []
+        descs = (_Inst * n)()
+        for i, wl in enumerate(self.wls):
+            descs[i].params = make_params(wl.params)
+            mems = _marshal_membranes(wl, self._keep)
+            self._keep.append(mems)
+            descs[i].mems = C.cast(mems, C.POINTER(_Mem))
+            descs[i].n_mem = len(wl.membranes)
+        self._descs = descs
+        nbytes = C.c_size_t(0)
+        _check(L.tlb_batch_state_bytes(descs, n, C.byref(nbytes)))
+        self.nbytes = nbytes.value
+        self.device = torch.device(device)
+        with torch.cuda.device(self.device):
+            self.arena = torch.empty(self.nbytes + 256, dtype=torch.uint8, device=self.device)
+            self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+            aligned = (self.arena.data_ptr() + 255) // 256 * 256
+            h = C.c_void_p()
+            _check(L.tlb_batch_create(descs, n, C.c_void_p(aligned), C.c_size_t(self.nbytes),
+                                      C.c_void_p(self.stream.cuda_stream), C.byref(h)))
+        self.h = h
+        self._handles = []
+        for i in range(n):
+            ih = C.c_void_p()
+            _check(L.tlb_batch_instance(self.h, i, C.byref(ih)))
+            self._handles.append(ih)
+        self.cells = sum(wl.params.ncells for wl in self.wls)
+
+    def __len__(self):
+        return len(self.wls)
+
+    def __getitem__(self, i) -> Simulation:
+        """Instance i (the view keeps the batch alive)."""
+        return Simulation(self.wls[i], _handle=self._handles[i], _owner=self)
+
+    def __del__(self):
+        try:
+            if getattr(self, "h", None) is not None and self.h.value:
+                lib().tlb_batch_destroy(self.h)
+                self.h = None
+        except Exception:
+            pass
+
+    def init(self):
+        """Default initial state of every instance (as Simulation.init())."""
+        for i in range(len(self)):
+            self[i].init()
+        return self
+
+    def set_active(self, flags):
+        f = np.ascontiguousarray(np.asarray(flags, dtype=np.int32))
+        _check(lib().tlb_batch_set_active(self.h, f.ctypes.data_as(C.POINTER(C.c_int))))
+
+    def step(self, n: int = 1):
+        _check(lib().tlb_batch_step(self.h, int(n)))
+
+    def run(self, max_steps: int, check_every: int = 100, tol: float = 1e-8):
+        """Run to residual; returns (steps_done, residual) per instance."""
+        steps = np.zeros(len(self), dtype=np.int64)
+        res = np.zeros(len(self))
+        _check(lib().tlb_batch_run(self.h, int(max_steps), int(check_every), float(tol),
+                                   steps.ctypes.data_as(C.POINTER(C.c_long)), _dp(res)))
+        return steps, res
+
+    def autotune(self):
+        v, z = C.c_int(0), C.c_int(0)
+        _check(lib().tlb_batch_autotune(self.h, C.byref(v), C.byref(z)))
+        return v.value, z.value
+
+    def launches(self) -> int:
+        return lib().tlb_batch_launch_count(self.h)
+
+    PHASES = ("moments_geometry", "forces_scatter", "band", "spread_fill", "collide", "interp")
+
+    def profile(self, n: int) -> dict:
+        """Device ms per step of each phase over n steps (tlb_batch_profile_steps)."""
+        ms = np.zeros(6)
+        _check(lib().tlb_batch_profile_steps(self.h, int(n), _dp(ms)))
+        return {k: v / max(n, 1) for k, v in zip(self.PHASES, ms)}

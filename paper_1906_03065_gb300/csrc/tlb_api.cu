@@ -279,6 +279,9 @@ static void plan(const tlb_params* p, const std::vector<HostMem>& mems, Ctx& c) 
   take(L.status, 64);
   take(L.part, 3 * 1024 * 8);
   take(L.meas, 32 * 8);
+  take(L.snap, 2 * P * 8);
+  take(L.xsnap, 3 * nn * 8);
+  take(L.res, 4 * 8);
   L.total = off;
 }
 
@@ -545,6 +548,32 @@ tlb_status tlb_diagnostics(void* ctx, tlb_diag* out) {
   Ctx* c = (Ctx*)ctx;
   if (!c || !out) { set_error("ctx/out is NULL"); return TLB_ERR_ARG; }
   return c->impl->diagnostics(c, out);
+}
+
+// Residual values from the maxima the residual kernel folded into res[0..2].
+static void residual_values(const unsigned long long* bits, long dt, double* out) {
+  double m = 0;
+  for (int q = 0; q < 3; ++q) {
+    double v;
+    memcpy(&v, &bits[q], sizeof(double));
+    out[q] = v;
+    m = std::max(m, v);
+  }
+  out[3] = dt > 0 ? m / (double)dt : 0.0;
+}
+
+tlb_status tlb_residual(void* ctx, double* out) {
+  Ctx* c = (Ctx*)ctx;
+  if (!c || !out) { set_error("ctx/out is NULL"); return TLB_ERR_ARG; }
+  if (!c->initialised) { set_error("tlb_residual before tlb_init_fields"); return TLB_ERR_STATE; }
+  tlb_status s = c->impl->residual_launch(c);
+  if (s != TLB_OK) return s;
+  unsigned long long h[4];
+  TLB_CUDA(cudaMemcpyAsync(h, c->ptr<unsigned long long>(c->L.res), sizeof(h), cudaMemcpyDeviceToHost, c->stream));
+  TLB_CUDA(cudaStreamSynchronize(c->stream));
+  residual_values(h, c->t - c->t_snap, out);
+  c->t_snap = c->t;
+  return TLB_OK;
 }
 
 tlb_status tlb_profile_steps(void* ctx, long n_steps, tlb_profile* out) {

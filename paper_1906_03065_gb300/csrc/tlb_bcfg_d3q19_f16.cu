@@ -1,0 +1,9 @@
+// Instantiation of the batched driver for one velocity set and storage precision.
+#include "tlb_batch.cuh"
+
+static_assert(sizeof(BArgs<TLB_F16>) <= Batch::ARGS_BYTES, "instance argument record too large");
+
+BatchBase* make_batch_impl_d3q19_f16() {
+  static BatchImpl<D3Q19, TLB_F16> impl;
+  return &impl;
+}

@@ -89,6 +89,17 @@ struct Geo {
   int P32;         // P as int: every population offset (3Q planes) fits 31 bits
 };
 
+// Block coordinates of a launch.  Kernel bodies take them as an argument, so
+// one body runs either as its own grid (the hardware block index) or as one
+// virtual block of a batched persistent launch over many lattices.
+struct Blk {
+  int x, y, z;     // block index
+  int gx, gy, gz;  // grid size in blocks
+};
+__device__ __forceinline__ Blk hw_blk() {
+  return {(int)blockIdx.x, (int)blockIdx.y, (int)blockIdx.z, (int)gridDim.x, (int)gridDim.y, (int)gridDim.z};
+}
+
 TLB_HD int wrapc(int a, int n) { return a < 0 ? a + n : (a >= n ? a - n : a); }
 
 // Population layout: `lo` holds 3Q-2 planes of Store -- f_0..f_{Q-1} stored

@@ -21,6 +21,8 @@ struct ImplBase {
   virtual tlb_status write_pops(Ctx* c, const double* src) = 0;
   virtual tlb_status diagnostics(Ctx* c, tlb_diag* out) = 0;
   virtual tlb_status autotune(Ctx* c, int* variant, int* zc) = 0;
+  // launches the residual kernel into c->L.res (zeroed first); no sync
+  virtual tlb_status residual_launch(Ctx* c) = 0;
 };
 
 // CUDA events bracketing the phases of a step when profiling.
@@ -49,6 +51,8 @@ struct Layout {
   Region bcnt, bprev, bcur, boff, blist, bact, ctr, bflag;
   // misc
   Region status, part, meas;
+  // equilibrium residual: reference phi, psi and marker positions, maxima
+  Region snap, xsnap, res;
   size_t total = 0;
 };
 
@@ -73,6 +77,7 @@ struct Ctx {
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_mom = nullptr;
   int cur = 0;  // population buffer holding the current state
   long t = 0;
+  long t_snap = 0;  // step of the residual's reference state
   bool initialised = false;
   bool box_stale = false;  // markers were overwritten: recompute the marker box
   long launches = 0;
@@ -97,6 +102,54 @@ struct Ctx {
   }
 };
 
+struct Batch;
+
+struct BatchBase {
+  virtual ~BatchBase() {}
+  virtual tlb_status step(Batch* b, long n) = 0;
+  // launches the residual of every active instance into its slot of b->res
+  // (zeroed first); no sync
+  virtual tlb_status residual(Batch* b) = 0;
+  virtual tlb_status autotune(Batch* b, int* variant, int* zc) = 0;
+  // n steps with direct launches, device time of each of the six phases
+  // summed into ms[0..5]; synchronises
+  virtual tlb_status profile(Batch* b, long n, double* ms) = 0;
+};
+
+// A batch of independent contexts of one lattice type and storage, stepped
+// together (see tlb_batch.cuh).  The instances live in sub-arenas of the
+// batch arena, followed by the batch's own tables.
+struct Batch {
+  static constexpr int NPH = 7;      // six phases of a step + the residual
+  static constexpr int MAXOPS = 4;   // kernel bodies per phase
+  static constexpr size_t ARGS_BYTES = 1024;  // bound on one instance's argument record
+  std::vector<Ctx*> inst;
+  std::vector<int> act;  // active instances, ascending
+  int dim = 0, storage = 0;
+  cudaStream_t stream = nullptr;
+  cudaStream_t cap = nullptr;  // capture stream of the step graph
+  char* base = nullptr;
+  size_t bytes = 0;
+  Region targs[2], vg, res;
+  std::vector<int> band_blocks, spread_blocks;  // virtual grids of the box-sized ops
+  int ph_ent[NPH] = {0}, ph_total[NPH] = {0}, ph_grid[NPH] = {0};
+  cudaGraphExec_t graph = nullptr;
+  bool graph_dirty = true;
+  long graph_launches = 0;  // kernels in one launch of the step graph
+  int tile_variant = 0, zc = 16;
+  long launches = 0;
+  BatchBase* impl = nullptr;
+
+  template <class T> T* ptr(const Region& r) const { return reinterpret_cast<T*>(base + r.off); }
+
+  ~Batch() {
+    if (stream) cudaStreamSynchronize(stream);
+    if (graph) cudaGraphExecDestroy(graph);
+    if (cap) cudaStreamDestroy(cap);
+    for (Ctx* c : inst) delete c;
+  }
+};
+
 void set_error(const std::string& msg);
 tlb_status cuda_check(cudaError_t e, const char* what);
 #define TLB_CUDA(call)                                              \
@@ -116,3 +169,8 @@ ImplBase* make_impl_d2q9_f32();
 ImplBase* make_impl_d3q19_f32();
 ImplBase* make_impl_d3q19_f16();
 ImplBase* make_impl_d3q19_bf16();
+BatchBase* make_batch_impl_d2q9_f64();
+BatchBase* make_batch_impl_d2q9_f32();
+BatchBase* make_batch_impl_d3q19_f32();
+BatchBase* make_batch_impl_d3q19_f16();
+BatchBase* make_batch_impl_d3q19_bf16();

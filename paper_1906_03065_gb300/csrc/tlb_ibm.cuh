@@ -167,8 +167,8 @@ __device__ __forceinline__ V3<Real> face_normal(const IBArgs<Real>& a, int e) {
 // (Baerentzen and Aanaes 2005; in 2D the sum of the two segment normals),
 // computing those normals themselves.
 template <class Real>
-__global__ void k_geometry(IBArgs<Real> a) {
-  int t = blockIdx.x * blockDim.x + threadIdx.x;
+__device__ __forceinline__ void geometry_body(const IBArgs<Real>& a, const Blk& blk) {
+  int t = blk.x * blockDim.x + threadIdx.x;
   if (t < a.ne) {
     V3<Real> n = face_normal(a, t);
     a.en[3 * t] = n.x;
@@ -198,19 +198,27 @@ __global__ void k_geometry(IBArgs<Real> a) {
   a.vn[3 * k + 1] = s.y;
   a.vn[3 * k + 2] = s.z;
 }
+template <class Real>
+__global__ void k_geometry(const __grid_constant__ IBArgs<Real> a) {
+  geometry_body(a, hw_blk());
+}
 
 // Marker bounding box.  The advection kernel accumulates floor(min X) and
 // -ceil(max X) per axis with integer atomicMin into box[0..5] (reset to a
 // large value after use); k_box does the same from scratch at set-up.
 template <class Real>
-__global__ void k_box(IBArgs<Real> a) {
-  int k = blockIdx.x * blockDim.x + threadIdx.x;
+__device__ __forceinline__ void box_body(const IBArgs<Real>& a, const Blk& blk) {
+  int k = blk.x * blockDim.x + threadIdx.x;
   if (k >= a.nn) return;
   for (int d = 0; d < 3; ++d) {
     double v = fmax(-1e8, fmin(1e8, a.X[3 * k + d]));
     atomicMin(a.box + d, (int)floor(v));
     atomicMin(a.box + 3 + d, -(int)ceil(v));
   }
+}
+template <class Real>
+__global__ void k_box(const __grid_constant__ IBArgs<Real> a) {
+  box_body(a, hw_blk());
 }
 
 // The box of cells the profile visits: the step's marker box widened by
@@ -287,13 +295,13 @@ __device__ __forceinline__ int feature_info(const IBArgs<Real>& a, int f, int* c
 // for cells whose nearest point lies elsewhere are at their exact (larger or
 // equal) distance and cannot win wrongly.
 template <class Real>
-__global__ void __launch_bounds__(SCATTER_WARPS * 32) k_dist_scatter(IBArgs<Real> a) {
+__device__ __forceinline__ void dist_scatter_body(const IBArgs<Real>& a, const Blk& blk) {
   __shared__ Real sV[SCATTER_WARPS][3][3];     // vertices of the offered face
   __shared__ Real sG[SCATTER_WARPS][MAXG][3];  // cone generators
   __shared__ Real sB[SCATTER_WARPS][3][3];     // feature corners
   const int nfeat = a.ne + (a.NV == 3 ? a.nedge : 0) + a.nn;
   const int w = threadIdx.x >> 5;
-  const int f = blockIdx.x * SCATTER_WARPS + w;
+  const int f = blk.x * SCATTER_WARPS + w;
   const int lane = threadIdx.x & 31;
   if (f >= nfeat) return;
   int corners[3], tri[MAXG], nB, nT;
@@ -390,6 +398,10 @@ __global__ void __launch_bounds__(SCATTER_WARPS * 32) k_dist_scatter(IBArgs<Real
       }
   }
 }
+template <class Real>
+__global__ void __launch_bounds__(SCATTER_WARPS * 32) k_dist_scatter(const __grid_constant__ IBArgs<Real> a) {
+  dist_scatter_body(a, hw_blk());
+}
 
 // Sign of x - P relative to the membrane at the closest feature (interior:
 // element normal; edge: sum of the two adjacent normals; vertex: vertex
@@ -424,15 +436,16 @@ __device__ __forceinline__ Real feature_sign(const IBArgs<Real>& a, int e, int f
 // are combined before one atomic).  Cells without a key are marked -1 for
 // the column fill; keys are cleared for the next step.
 template <class Real>
-__global__ void k_band(IBArgs<Real> a) {
+__device__ __forceinline__ void band_body(const IBArgs<Real>& a, const Blk& blk) {
   int blo[3], bhi[3];
   profile_box(a, blo, bhi);
   const int bx0 = blo[0], by0 = blo[1], bz0 = blo[2];
   const int wx = bhi[0] - bx0 + 1, wy = bhi[1] - by0 + 1, wz = bhi[2] - bz0 + 1;
   const long long total = (long long)wx * wy * wz;
+  const bool full[3] = {wx == a.G.nx, a.dim == 3 && wy == a.G.ny, !a.G.wall && wz == a.G.nz};
   const Real al = a.alpha;
-  const long long stride = (long long)gridDim.x * blockDim.x;
-  for (long long t0 = (long long)blockIdx.x * blockDim.x; t0 < total; t0 += stride) {
+  const long long stride = (long long)blk.gx * blockDim.x;
+  for (long long t0 = (long long)blk.x * blockDim.x; t0 < total; t0 += stride) {
     const long long t = t0 + threadIdx.x;
     int e = -1;
     Real acc[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
@@ -448,7 +461,19 @@ __global__ void k_band(IBArgs<Real> a) {
           a.key[c] = KEY_NONE;
           Real beta[3];
           int feat;
-          V3<Real> P = elem_closest(a, e, (double)pc[0], (double)pc[1], (double)pc[2], beta, &feat);
+          // Along an axis where the box spans a whole period a band cell may
+          // sit one period away from the element that keyed it: measure from
+          // the image of the cell nearest to the element (unique, as
+          // periodic sides are at least 2 dc + 8).  A box narrower than the
+          // period holds every band cell at that image already.
+          int px = pc[0], py = pc[1], pz = pc[2];
+          if (full[0] | full[1] | full[2]) {
+            const double* x0 = a.X + 3 * a.E[a.NV * e];
+            if (full[0]) px += a.G.nx * __float2int_rn((float)(x0[0] - px) / (float)a.G.nx);
+            if (full[1]) py += a.G.ny * __float2int_rn((float)(x0[1] - py) / (float)a.G.ny);
+            if (full[2]) pz += a.G.nz * __float2int_rn((float)(x0[2] - pz) / (float)a.G.nz);
+          }
+          V3<Real> P = elem_closest(a, e, (double)px, (double)py, (double)pz, beta, &feat);
           V3<Real> xmP = mk<Real>(-P.x, -P.y, -P.z);
           Real dist = sqrt(dot(xmP, xmP));
           Real s = feature_sign(a, e, feat, xmP);
@@ -491,6 +516,10 @@ __global__ void k_band(IBArgs<Real> a) {
     }
   }
 }
+template <class Real>
+__global__ void k_band(const __grid_constant__ IBArgs<Real> a) {
+  band_body(a, hw_blk());
+}
 
 // Cells of the box farther than dc from the membrane: one warp per column
 // along z, 32 cells at a time.  A cell outside the band takes the side of
@@ -498,12 +527,12 @@ __global__ void k_band(IBArgs<Real> a) {
 // cells that are both farther than dc from it; the bottom of the box is
 // outside every capsule): d = +dc inside, -dc outside.
 template <class Real>
-__global__ void k_fill(IBArgs<Real> a) {
+__device__ __forceinline__ void fill_body(const IBArgs<Real>& a, const Blk& blk) {
   int blo[3], bhi[3];
   profile_box(a, blo, bhi);
   const int bx0 = blo[0], by0 = blo[1], bz0 = blo[2];
   const int wx = bhi[0] - bx0 + 1, wy = bhi[1] - by0 + 1, wz = bhi[2] - bz0 + 1;
-  const int col = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int col = (blk.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (col >= wx * wy) return;
   const Real dc = a.dc, al = a.alpha;
@@ -536,6 +565,10 @@ __global__ void k_fill(IBArgs<Real> a) {
     bool top = upto ? ((sm >> (31 - __clz(upto))) & 1u) : inside;
     inside = __shfl_sync(0xffffffffu, top, 0);
   }
+}
+template <class Real>
+__global__ void k_fill(const __grid_constant__ IBArgs<Real> a) {
+  fill_body(a, hw_blk());
 }
 
 // ------------------------------------------------------------ elastic forces
@@ -637,8 +670,8 @@ __device__ __forceinline__ D3<Real> helfrich_dual(const IBArgs<Real>& a, int v, 
 // the marker).  Lane sums are combined by a fixed shuffle tree.  They depend
 // on the marker positions only; the coupling force joins them in k_spread.
 template <class Real>
-__global__ void k_node_forces(IBArgs<Real> a) {
-  const int k = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+__device__ __forceinline__ void node_forces_body(const IBArgs<Real>& a, const Blk& blk) {
+  const int k = (blk.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (k >= a.nn) return;
   Real F[3] = {0, 0, 0};
@@ -732,6 +765,10 @@ __global__ void k_node_forces(IBArgs<Real> a) {
     for (int d = 0; d < 3; ++d) a.F[3 * k + d] = F[d];
   }
 }
+template <class Real>
+__global__ void k_node_forces(const __grid_constant__ IBArgs<Real> a) {
+  node_forces_body(a, hw_blk());
+}
 
 // Coupling force on marker k, gathered from the fixed-point sums of its
 // incident elements (integer totals, so the result is order independent).
@@ -789,19 +826,23 @@ __device__ __forceinline__ int node_bricks(const IBArgs<Real>& a, int l, int* ou
 }
 
 template <class Real>
-__global__ void k_brick_count(IBArgs<Real> a) {
-  int l = blockIdx.x * blockDim.x + threadIdx.x;
+__device__ __forceinline__ void brick_count_body(const IBArgs<Real>& a, const Blk& blk) {
+  int l = blk.x * blockDim.x + threadIdx.x;
   if (l >= a.nn) return;
   int b[64];
   int m = node_bricks(a, l, b);
   for (int j = 0; j < m; ++j) atomicAdd(a.bcnt + b[j], 1);
 }
+template <class Real>
+__global__ void k_brick_count(const __grid_constant__ IBArgs<Real> a) {
+  brick_count_body(a, hw_blk());
+}
 
 // Bricks holding markers now or in the previous step join the active list;
 // each claims a contiguous slot range for its marker list.
 template <class Real>
-__global__ void k_brick_compact(IBArgs<Real> a) {
-  int b = blockIdx.x * blockDim.x + threadIdx.x;
+__device__ __forceinline__ void brick_compact_body(const IBArgs<Real>& a, const Blk& blk) {
+  int b = blk.x * blockDim.x + threadIdx.x;
   if (b >= a.nbricks) return;
   int c = a.bcnt[b];
   a.bflag[b] = c > 0;
@@ -810,10 +851,14 @@ __global__ void k_brick_compact(IBArgs<Real> a) {
   a.bact[i] = b;
   a.boff[b] = atomicAdd(a.ctr + 1, c);
 }
+template <class Real>
+__global__ void k_brick_compact(const __grid_constant__ IBArgs<Real> a) {
+  brick_compact_body(a, hw_blk());
+}
 
 template <class Real>
-__global__ void k_brick_fill(IBArgs<Real> a) {
-  int l = blockIdx.x * blockDim.x + threadIdx.x;
+__device__ __forceinline__ void brick_fill_body(const IBArgs<Real>& a, const Blk& blk) {
+  int l = blk.x * blockDim.x + threadIdx.x;
   if (l >= a.nn) return;
   int b[64];
   int m = node_bricks(a, l, b);
@@ -826,19 +871,23 @@ __global__ void k_brick_fill(IBArgs<Real> a) {
     a.blist[a.boff[b[j]] + s] = l;
   }
 }
+template <class Real>
+__global__ void k_brick_fill(const __grid_constant__ IBArgs<Real> a) {
+  brick_fill_body(a, hw_blk());
+}
 
 // Each cell of an active brick sums F_l delta_h(x - X_l) over the brick's
 // markers in ascending marker order (the list is sorted first, so the result
 // does not depend on the order of the atomic slot claims).  Bricks that held
 // markers in the previous step are visited too, so their cells return to zero.
 template <class Real>
-__global__ void k_spread(IBArgs<Real> a) {
+__device__ __forceinline__ void spread_body(const IBArgs<Real>& a, const Blk& blk) {
   __shared__ int list[512], sorted[512];
   __shared__ Real sX[512][3];
   __shared__ Real sF[512][3];
   const int nact = min(a.ctr[0], a.nbricks);
   const int BY = a.dim == 3 ? BRICK : 1;
-  for (int ib = blockIdx.x; ib < nact; ib += gridDim.x) {
+  for (int ib = blk.x; ib < nact; ib += blk.gx) {
     const int b = a.bact[ib];
     if (b < 0 || b >= a.nbricks) continue;
     const int cnt = a.bcnt[b];
@@ -895,15 +944,20 @@ __global__ void k_spread(IBArgs<Real> a) {
     __syncthreads();
   }
 }
+template <class Real>
+__global__ void k_spread(const __grid_constant__ IBArgs<Real> a) {
+  spread_body(a, hw_blk());
+}
 
 // ------------------------------------------------------------ interpolation
 // One warp per marker: v(t+1) = (j' + F/2)/rho' on the 4^d support cells
 // from the streamed populations and the force of the step, weighted by
 // delta_h, reduced over the warp; then X += U (explicit Euler).
 template <class L, int MODE>
-__global__ void k_interp_advect(IBArgs<typename Prec<MODE>::Real> a, const typename Prec<MODE>::Store* lo) {
+__device__ __forceinline__ void interp_advect_body(const IBArgs<typename Prec<MODE>::Real>& a,
+                                                   const typename Prec<MODE>::Store* lo, const Blk& blk) {
   using Real = typename Prec<MODE>::Real;
-  int l = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  int l = (blk.x * blockDim.x + threadIdx.x) >> 5;
   int lane = threadIdx.x & 31;
   if (l >= a.nn) return;
   const Geo G = a.G;
@@ -947,6 +1001,11 @@ __global__ void k_interp_advect(IBArgs<typename Prec<MODE>::Real> a, const typen
       atomicMin(a.box + 3 + d, -(int)ceil(v));
     }
   }
+}
+template <class L, int MODE>
+__global__ void k_interp_advect(const __grid_constant__ IBArgs<typename Prec<MODE>::Real> a,
+                                const typename Prec<MODE>::Store* lo) {
+  interp_advect_body<L, MODE>(a, lo, hw_blk());
 }
 
 // FP64 capsule measures: 2D enclosed area (shoelace in the internal x-z

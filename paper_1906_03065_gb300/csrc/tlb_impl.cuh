@@ -260,9 +260,28 @@ struct Impl : ImplBase {
                                                        c->ptr<Rest>(c->L.rest[c->cur]));
     TLB_LAUNCHED(c, "k_init_eq");
     TLB_CUDA(cudaMemsetAsync(c->ptr<char>(c->L.ftot), 0, c->L.ftot.bytes, s));
+    // the initial state is the first reference of the equilibrium residual
+    tlb_status rs = residual_launch(c);
+    if (rs != TLB_OK) return rs;
     TLB_CUDA(cudaStreamSynchronize(s));
     c->t = 0;
+    c->t_snap = 0;
     c->initialised = true;
+    return TLB_OK;
+  }
+
+  static ResPtrs resptrs(Ctx* c, unsigned long long* res) {
+    return {c->ptr<double>(c->L.snap), c->ptr<double>(c->L.xsnap), res};
+  }
+
+  tlb_status residual_launch(Ctx* c) override {
+    cudaStream_t s = c->stream;
+    TLB_CUDA(cudaMemsetAsync(c->ptr<char>(c->L.res), 0, c->L.res.bytes, s));
+    const unsigned nb = blocks(c->N, 256) + blocks(c->nn, 256);
+    k_residual<L, MODE><<<nb, 256, 0, s>>>(geo(c), c->ptr<Store>(c->L.lo[c->cur]), c->ptr<Rest>(c->L.rest[c->cur]),
+                                           c->ptr<double>(c->L.X), c->nn,
+                                           resptrs(c, c->ptr<unsigned long long>(c->L.res)));
+    TLB_LAUNCHED(c, "k_residual");
     return TLB_OK;
   }
 

@@ -36,10 +36,10 @@ struct LBArgs {
 // ---------------------------------------------------------------- moments
 // rho, phi, psi at every cell from the streamed populations (eq. MomentsDFs).
 template <class L, int MODE>
-__global__ void __launch_bounds__(256) k_moments(LBArgs<MODE> a) {
+__device__ __forceinline__ void moments_body(const LBArgs<MODE>& a, const Blk& blk) {
   using Real = typename Prec<MODE>::Real;
   const Geo G = a.G;
-  long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  long long n = (long long)blk.x * blockDim.x + threadIdx.x;
   if (n >= G.N) return;
   int x = (int)(n % G.nx);
   int y = (int)((n / G.nx) % G.ny);
@@ -50,6 +50,10 @@ __global__ void __launch_bounds__(256) k_moments(LBArgs<MODE> a) {
   a.rho[n] = Real(1) + m.drho;
   a.phi[n] = m.phi;
   a.psi[n] = m.psi;
+}
+template <class L, int MODE>
+__global__ void __launch_bounds__(256) k_moments(const __grid_constant__ LBArgs<MODE> a) {
+  moments_body<L, MODE>(a, hw_blk());
 }
 
 // Second-order polynomial of the equilibria: 3 c.u + 4.5 (c.u)^2 - 1.5 u^2.
@@ -66,7 +70,7 @@ __device__ __forceinline__ Real eq_poly(Real cu, Real uu) {
 // needs the Laplacian of the moments, the force needs the gradient of mu) is
 // served on chip.
 template <class L, int MODE, int TX, int TY>
-__global__ void __launch_bounds__(TX* TY, 640 / (TX * TY)) k_collide(LBArgs<MODE> a) {
+__device__ __forceinline__ void collide_body(const LBArgs<MODE>& a, const Blk& blk) {
   using Real = typename Prec<MODE>::Real;
   using Store = typename Prec<MODE>::Store;
   using Rest = typename Prec<MODE>::Rest;
@@ -81,8 +85,8 @@ __global__ void __launch_bounds__(TX* TY, 640 / (TX * TY)) k_collide(LBArgs<MODE
 
   const Geo G = a.G;
   const int tx = threadIdx.x % TX, ty = threadIdx.x / TX, tid = threadIdx.x;
-  const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
-  const int z0 = blockIdx.z * a.zc;
+  const int x0 = blk.x * TX, y0 = blk.y * TY;
+  const int z0 = blk.z * a.zc;
   const int z1 = min(z0 + a.zc, G.nz);
   const int x = x0 + tx, y = y0 + ty;
   const bool active = x < G.nx && y < G.ny;
@@ -286,6 +290,10 @@ __global__ void __launch_bounds__(TX* TY, 640 / (TX * TY)) k_collide(LBArgs<MODE
     __syncthreads();
   }
 }
+template <class L, int MODE, int TX, int TY>
+__global__ void __launch_bounds__(TX* TY, 640 / (TX * TY)) k_collide(const __grid_constant__ LBArgs<MODE> a) {
+  collide_body<L, MODE, TX, TY>(a, hw_blk());
+}
 
 // ------------------------------------------------------------- init & I/O
 // Chemical potentials from fields in global memory (used at initialisation).
@@ -373,6 +381,67 @@ __global__ void k_fields(Geo G, const typename Prec<MODE>::Store* lo, const type
   out[G.N + n] = (double)m.phi;
   out[2 * G.N + n] = (double)m.psi;
   for (int d = 0; d < 3; ++d) out[(3 + d) * G.N + n] = (double)m.j[d] / rho;
+}
+
+// ------------------------------------------------------------ residual
+// Reference state of the equilibrium residual and the slots its maxima are
+// folded into.
+struct ResPtrs {
+  double* snap;             // [2][P] phi, psi at the reference step
+  double* xsnap;            // [nn][3] marker positions at the reference step
+  unsigned long long* res;  // [3] max |change| of phi, psi, X (bit patterns)
+};
+
+// Largest change since the reference step of phi and psi (FP64 sums of the
+// streamed populations) over the cells, then of the marker positions over
+// the markers (virtual blocks past the cells); the reference is replaced by
+// the current values.  Maxima of non-negative doubles are order independent:
+// they are folded with integer atomicMax on the bit patterns, NaN mapped to
+// +inf so that a diverged run never reads as converged.
+template <class L, int MODE>
+__device__ __forceinline__ void residual_body(const Geo& G, const typename Prec<MODE>::Store* lo,
+                                              const typename Prec<MODE>::Rest* rest, const double* X, int nn,
+                                              const ResPtrs& r, const Blk& blk) {
+  const long long ncb = (G.N + blockDim.x - 1) / blockDim.x;
+  double m[3] = {0, 0, 0};
+  if (blk.x < ncb) {
+    const long long n = (long long)blk.x * blockDim.x + threadIdx.x;
+    if (n < G.N) {
+      const int x = (int)(n % G.nx), y = (int)((n / G.nx) % G.ny), z = (int)(n / ((long long)G.nx * G.ny));
+      Pull<L, MODE> p;
+      p.load(lo, rest, G, x, y, z);
+      double ph = 0, ps = 0;
+#pragma unroll
+      for (int i = 0; i < L::Q; ++i) {
+        ph += (double)p.g[i];
+        ps += (double)p.h[i];
+      }
+      m[0] = fabs(ph - r.snap[n]);
+      m[1] = fabs(ps - r.snap[G.P + n]);
+      r.snap[n] = ph;
+      r.snap[G.P + n] = ps;
+    }
+  } else {
+    const long long l = (long long)(blk.x - ncb) * blockDim.x + threadIdx.x;
+    if (l < nn)
+      for (int d = 0; d < 3; ++d) {
+        m[2] = fmax(m[2], fabs(X[3 * l + d] - r.xsnap[3 * l + d]));
+        if (!(X[3 * l + d] == X[3 * l + d])) m[2] = __longlong_as_double(0x7FF0000000000000ll);
+        r.xsnap[3 * l + d] = X[3 * l + d];
+      }
+  }
+  for (int q = 0; q < 3; ++q) {
+    double v = m[q];
+    if (!(v == v)) v = __longlong_as_double(0x7FF0000000000000ll);
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    if ((threadIdx.x & 31) == 0 && v > 0) atomicMax(r.res + q, (unsigned long long)__double_as_longlong(v));
+  }
+}
+
+template <class L, int MODE>
+__global__ void k_residual(Geo G, const typename Prec<MODE>::Store* lo, const typename Prec<MODE>::Rest* rest,
+                           const double* X, int nn, ResPtrs r) {
+  residual_body<L, MODE>(G, lo, rest, X, nn, r, hw_blk());
 }
 
 // FP64 totals: per-block partial sums of rho (as 1 + sum of deviations),

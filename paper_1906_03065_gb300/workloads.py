@@ -17,6 +17,9 @@ Workload recipes (lattice units, dx = dt = 1, Sec. 3.1 of the paper):
 * ``bridge_3d``   -- D3Q19 192x128x128: two capsules 48 apart along x with a
   C1 cylinder between them in C2 (the 3D analogue of the paper's capillary
   bridge, Sec. 4.2).
+* ``sweep_3d``    -- 64 independent cubic lattices of edge 48..96, each a
+  capsule on an interface with seeded fluid and membrane parameters (the
+  parameter sweeps behind the paper's Sec. 4 figures, run as one batch).
 """
 from __future__ import annotations
 
@@ -203,6 +206,55 @@ def small_3d(storage: str = "f32", nx: int = 40, ny: int = 36, nz: int = 34,
     m = icosphere(level, radius, centre)
     m.G, m.C, m.kb = 0.01, 1.0, 0.005
     return Workload(f"small_3d_{nx}x{ny}x{nz}", p, [m], steps=200)
+
+
+def sweep_3d(n_inst: int = 64, seed: int = 1, storage: str = "f16",
+             edges=(48, 64, 80, 96)) -> List[Workload]:
+    """Parameter sweep of independent cubic 3D lattices, drawn in order from
+    numpy's PCG64 with ``seed``: edge ~ U{edges}; capsule radius R = edge *
+    U[0.15, 0.25] on an icosphere of level 3 if R < 15 else 4; kappa_1,
+    kappa_2, kappa_3 ~ U[0.005, 0.03] each; Skalak G ~ U[0.002, 0.05].  Every
+    instance has the layout of ``capsule_3d`` (walls at the two ends of z, a
+    flat C1/C2 interface at mid-height and the capsule centred on it) with
+    C = 1, kb = 0.005, alpha = 2, kappa_c = 0.01, dc = 16, tau = Gamma = 1."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(n_inst):
+        n = int(rng.choice(np.asarray(edges)))
+        R = float(n * rng.uniform(0.15, 0.25))
+        level = 3 if R < 15 else 4
+        k1, k2, k3 = (float(v) for v in rng.uniform(0.005, 0.03, 3))
+        G = float(rng.uniform(0.002, 0.05))
+        c = n / 2.0
+        p = Params(dim=3, nx=n, ny=n, nz=n, wall_last=1, storage=storage, alpha=2.0,
+                   kappa1=k1, kappa2=k2, kappa3=k3, kappa_c=0.01, dc=16.0, interface_pos=c)
+        m = icosphere(level, R, (c, c, c))
+        m.G, m.C, m.kb = G, 1.0, 0.005
+        out.append(Workload(f"sweep{i}_{n}^3_R{R:.1f}_ico{level}", p, [m], steps=20000))
+    return out
+
+
+def small_sweep_3d(n_inst: int = 4, seed: int = 7, storage: str = "f32") -> List[Workload]:
+    """Small uneven 3D instances for parity of the batched path: x, y ~
+    U{24..36}, z ~ U{22..30} (walls in z), capsule R = min(size) * U[0.15,
+    0.22] on an icosphere of level 2 centred (off the grid) on the interface
+    at mid-height, kappa_i ~ U[0.005, 0.03], G ~ U[0.002, 0.05], alpha = 1,
+    dc = 8."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(n_inst):
+        nx, ny = (int(v) for v in rng.integers(24, 37, 2))
+        nz = int(rng.integers(22, 31))
+        R = float(min(nx, ny, nz) * rng.uniform(0.15, 0.22))
+        k1, k2, k3 = (float(v) for v in rng.uniform(0.005, 0.03, 3))
+        G = float(rng.uniform(0.002, 0.05))
+        ctr = (nx / 2.0 + 0.3, ny / 2.0 - 0.2, nz / 2.0 + 0.1)
+        p = Params(dim=3, nx=nx, ny=ny, nz=nz, wall_last=1, storage=storage, alpha=1.0,
+                   kappa1=k1, kappa2=k2, kappa3=k3, kappa_c=0.01, dc=8.0, interface_pos=nz / 2.0)
+        m = icosphere(2, R, ctr)
+        m.G, m.C, m.kb = G, 1.0, 0.005
+        out.append(Workload(f"small_sweep{i}_{nx}x{ny}x{nz}", p, [m], steps=200))
+    return out
 
 
 def jitter_nodes(m: Membrane, amp: float, seed: int) -> Membrane:

@@ -125,6 +125,27 @@ def test_small_3d_f32_200_steps():
     _compare_fields(g, o, 1e-4, 1e-4, 1e-4)
 
 
+def test_small_3d_f32_band_wider_than_period():
+    """Periodic sides of 25 cells around a capsule of radius 4.8 with dc = 8:
+    the band (capsule +- dc) is wider than the period, so the profile box
+    spans a whole period and every band cell must be measured from its image
+    nearest to the membrane (eq. Iprofile with periodic boundaries).  Also a
+    periodic z (no walls)."""
+    wl = W.small_sweep_3d(1, seed=11, storage="f32")[0]
+    assert wl.params.nx == 25 and wl.params.ny == 25
+    g, o = _sim(wl).init(), oracle.Oracle(wl)
+    assert np.abs(g.field("I") - o.field("I")).max() < 2e-6
+    g.step(100)
+    o.step(100)
+    _compare_fields(g, o, 1e-4, 1e-4, 1e-4)
+    wl.params.wall_last = 0
+    g, o = _sim(wl).init(), oracle.Oracle(wl)
+    assert np.abs(g.field("I") - o.field("I")).max() < 2e-6
+    g.step(50)
+    o.step(50)
+    _compare_fields(g, o, 1e-4, 1e-4, 1e-4)
+
+
 def test_periodic_3d_f32_no_membrane():
     wl = W.small_3d("f32", nx=33, ny=20, nz=18, wall=0)
     wl.membranes = []
