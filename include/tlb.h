@@ -295,6 +295,75 @@ long tlb_batch_launch_count(void* batch);
  * caller's). */
 void tlb_batch_destroy(void* batch);
 
+/* ------------------------------------------------------- learned warm start
+ * A 3D convolutional encoder-decoder guesses the equilibrium of a capsule-
+ * on-interface run from its plain initial state (undeformed capsule on the
+ * flat interface) and five parameters, so that the relaxation starts closer
+ * to it.  Not in the paper; an addition of this library.  The plain start
+ * stays the fallback, and the relaxation itself decides the equilibrium.
+ *
+ * Network on an E^3 lattice, channels c_l = base_channels * 2^l at level l
+ * (edge E / 2^l), `levels` levels:
+ *   input (16 channels): phi0, psi0 of the plain start, the five features,
+ *     nine zeros;
+ *   encoder: e_l = relu(conv3(relu(conv3(in_l)))), in_0 = input,
+ *     in_l = 2x2x2 average pool of e_{l-1};
+ *   decoder: d_l = relu(conv3(relu(conv3([nearest 2x upsample of d_{l+1} |
+ *     e_l])))), d_{levels-1} = e_{levels-1};
+ *   output y = conv1(d_0), 16 channels: y0 = phi correction, y1 = psi
+ *     correction, y2..y4 = displacement field, the rest unused.
+ * conv3 is 3x3x3 with zero padding, conv1 is 1x1x1; every conv has a bias.
+ * Parameters, in order, per conv: W[tap][ci][co] (tap = (kz*3 + ky)*3 + kx
+ * for the input offset (kz-1, ky-1, kx-1)), then b[co]; FP32 on the host.
+ * Activations are stored as bf16, the convolutions run on the tensor cores
+ * with FP32 accumulation.
+ * Features (normalised by the caller): kappa_1..3, Skalak G, R / E.
+ * Training loss for targets dphi_t = phi_eq - phi0, dpsi_t = psi_eq - psi0
+ * (FP32 [B][E^3]) and marker offsets off_t = X_eq - X0 (FP32 [B][max_nodes][3]):
+ *   mean over samples and cells of (y0 - dphi_t)^2 + (y1 - dpsi_t)^2
+ *   + lambda * mean over samples, markers and axes of
+ *     (trilinear(y2..y4)(X0) - off_t)^2.
+ * Input tensors x are bf16 [B][E^3][16] (device). */
+typedef struct {
+  int edge;          /* E: multiple of 2^(levels-1), 2^levels..256 */
+  int base_channels; /* c_0: 16, 32, 48 or 64 */
+  int levels;        /* 2..4 */
+  int max_batch;     /* samples per call, 1..64 */
+  int max_nodes;     /* markers per sample in training, 0..2^20 */
+} tlb_net_desc;
+
+tlb_status tlb_net_param_count(const tlb_net_desc* desc, size_t* n);
+tlb_status tlb_net_state_bytes(const tlb_net_desc* desc, size_t* bytes);
+/* arena: device, 256-byte aligned, >= tlb_net_state_bytes, the caller's. */
+tlb_status tlb_net_create(const tlb_net_desc* desc, void* arena, size_t bytes, void* cuda_stream, void** net_out);
+/* Parameters (host FP32, n = tlb_net_param_count); resets the Adam state. */
+tlb_status tlb_net_set_params(void* net, const float* host, size_t n);
+tlb_status tlb_net_get_params(void* net, float* host, size_t n);
+/* Parameter gradient of the last tlb_net_train_step (host FP32). */
+tlb_status tlb_net_get_grads(void* net, float* host, size_t n);
+/* Input of one sample (x_dev: bf16 [E^3][16], device) from a context that
+ * holds its plain initial state, with features feats[5] (host). */
+tlb_status tlb_net_input(void* net, void* ctx, const double* feats, void* x_dev);
+/* Output y (FP32 [batch][E^3][16], device, or NULL) of batch inputs. */
+tlb_status tlb_net_forward(void* net, const void* x_dev, int batch, float* y_dev);
+/* Forward, loss (returned in *loss_out, host), backward; then one Adam step
+ * (Kingma and Ba 2015; beta1 0.9, beta2 0.999, eps 1e-8, step size lr) when
+ * update != 0.  n_nodes: host [batch] marker counts (NULL: no marker term).
+ * Synchronises the stream. */
+tlb_status tlb_net_train_step(void* net, const void* x_dev, const float* dphi_dev, const float* dpsi_dev,
+                              const float* X0_dev, const float* off_dev, const int* n_nodes, int batch,
+                              double lambda, double lr, int update, double* loss_out);
+/* Warm start of a context that holds its plain initial state (tlb_init_fields
+ * with NULL fields, no step taken; 3D, edge^3 cells, FP32 arithmetic):
+ * phi = phi0 + y0 and psi = psi0 + y1 shifted uniformly so that their totals
+ * equal the plain start's (the method conserves them), rho = 1, markers
+ * X += trilinear(y2..y4)(X); then the profile, u = 0 and the equilibrium
+ * populations of these fields, as tlb_init_fields does.  Synchronises. */
+tlb_status tlb_net_warm_start(void* net, void* ctx, const double* feats);
+/* Kernel launches of the last tlb_net_* call that computes. */
+long tlb_net_launch_count(void* net);
+void tlb_net_destroy(void* net);
+
 /* Message of the last failed call on this thread ("" if none). */
 const char* tlb_last_error(void);
 

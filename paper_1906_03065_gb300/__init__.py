@@ -49,6 +49,11 @@ class _Inst(C.Structure):
     _fields_ = [("params", _Params), ("mems", C.POINTER(_Mem)), ("n_mem", C.c_int)]
 
 
+class _NetDesc(C.Structure):
+    _fields_ = [("edge", C.c_int), ("base_channels", C.c_int), ("levels", C.c_int),
+                ("max_batch", C.c_int), ("max_nodes", C.c_int)]
+
+
 class Diag(C.Structure):
     _fields_ = [("step", C.c_long), ("mass", C.c_double * 3), ("umax", C.c_double),
                 ("n_caps", C.c_int), ("area", C.c_double * 8), ("volume", C.c_double * 8)]
@@ -103,6 +108,25 @@ def lib():
         L.tlb_batch_launch_count.argtypes = [vp]
         L.tlb_batch_launch_count.restype = C.c_long
         L.tlb_batch_destroy.argtypes = [vp]
+        fp = C.POINTER(C.c_float)
+        nd = C.POINTER(_NetDesc)
+        L.tlb_net_param_count.argtypes = [nd, C.POINTER(sz)]
+        L.tlb_net_state_bytes.argtypes = [nd, C.POINTER(sz)]
+        L.tlb_net_create.argtypes = [nd, vp, sz, vp, C.POINTER(vp)]
+        L.tlb_net_set_params.argtypes = [vp, fp, sz]
+        L.tlb_net_get_params.argtypes = [vp, fp, sz]
+        L.tlb_net_get_grads.argtypes = [vp, fp, sz]
+        L.tlb_net_input.argtypes = [vp, vp, dp, vp]
+        L.tlb_net_forward.argtypes = [vp, vp, C.c_int, vp]
+        L.tlb_net_train_step.argtypes = [vp, vp, vp, vp, vp, vp, ip, C.c_int, C.c_double, C.c_double, C.c_int, dp]
+        L.tlb_net_warm_start.argtypes = [vp, vp, dp]
+        for n in ("tlb_net_param_count", "tlb_net_state_bytes", "tlb_net_create", "tlb_net_set_params",
+                  "tlb_net_get_params", "tlb_net_get_grads", "tlb_net_input", "tlb_net_forward",
+                  "tlb_net_train_step", "tlb_net_warm_start"):
+            getattr(L, n).restype = C.c_int
+        L.tlb_net_launch_count.argtypes = [vp]
+        L.tlb_net_launch_count.restype = C.c_long
+        L.tlb_net_destroy.argtypes = [vp]
         L.tlb_destroy.argtypes = [vp]
         L.tlb_last_error.restype = C.c_char_p
         for n in ("tlb_state_bytes", "tlb_create", "tlb_init_fields", "tlb_step", "tlb_read_field",
@@ -366,3 +390,91 @@ class Batch:
         ms = np.zeros(6)
         _check(lib().tlb_batch_profile_steps(self.h, int(n), _dp(ms)))
         return {k: v / max(n, 1) for k, v in zip(self.PHASES, ms)}
+
+
+class WarmStartNet:
+    """The warm-start encoder-decoder of tlb.h on one GPU: parameters, input
+    construction, forward, training steps and the warm start of a context.
+    Tensors are torch tensors on the net's device (x: bf16 [B, E^3, 16];
+    targets fp32)."""
+
+    def __init__(self, edge: int, base_channels: int = 16, levels: int = 4, max_batch: int = 8,
+                 max_nodes: int = 0, device="cuda:0", stream=None):
+        import torch
+        L = lib()
+        self.desc = _NetDesc(edge, base_channels, levels, max_batch, max_nodes)
+        n = C.c_size_t(0)
+        _check(L.tlb_net_param_count(C.byref(self.desc), C.byref(n)))
+        self.n_params = n.value
+        b = C.c_size_t(0)
+        _check(L.tlb_net_state_bytes(C.byref(self.desc), C.byref(b)))
+        self.nbytes = b.value
+        self.edge, self.max_batch, self.max_nodes = edge, max_batch, max_nodes
+        self.device = torch.device(device)
+        with torch.cuda.device(self.device):
+            self.arena = torch.empty(self.nbytes + 256, dtype=torch.uint8, device=self.device)
+            self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+            aligned = (self.arena.data_ptr() + 255) // 256 * 256
+            h = C.c_void_p()
+            _check(L.tlb_net_create(C.byref(self.desc), C.c_void_p(aligned), C.c_size_t(self.nbytes),
+                                    C.c_void_p(self.stream.cuda_stream), C.byref(h)))
+        self.h = h
+
+    def __del__(self):
+        try:
+            if getattr(self, "h", None) is not None and self.h.value:
+                lib().tlb_net_destroy(self.h)
+                self.h = None
+        except Exception:
+            pass
+
+    def set_params(self, theta):
+        t = np.ascontiguousarray(theta, dtype=np.float32)
+        _check(lib().tlb_net_set_params(self.h, t.ctypes.data_as(C.POINTER(C.c_float)), t.size))
+
+    def params(self) -> np.ndarray:
+        out = np.zeros(self.n_params, dtype=np.float32)
+        _check(lib().tlb_net_get_params(self.h, out.ctypes.data_as(C.POINTER(C.c_float)), out.size))
+        return out
+
+    def grads(self) -> np.ndarray:
+        out = np.zeros(self.n_params, dtype=np.float32)
+        _check(lib().tlb_net_get_grads(self.h, out.ctypes.data_as(C.POINTER(C.c_float)), out.size))
+        return out
+
+    def input(self, sim, feats, out=None):
+        """Input tensor of a freshly initialised Simulation (plain start)."""
+        import torch
+        V = self.edge ** 3
+        x = out if out is not None else torch.empty((V, 16), dtype=torch.bfloat16, device=self.device)
+        f = np.ascontiguousarray(feats, dtype=np.float64)
+        _check(lib().tlb_net_input(self.h, sim.h, _dp(f), C.c_void_p(x.data_ptr())))
+        return x
+
+    def forward(self, x):
+        import torch
+        B = x.shape[0] if x.dim() == 3 else 1
+        y = torch.empty((B, self.edge ** 3, 16), dtype=torch.float32, device=self.device)
+        _check(lib().tlb_net_forward(self.h, C.c_void_p(x.data_ptr()), B, C.c_void_p(y.data_ptr())))
+        return y
+
+    def train_step(self, x, dphi, dpsi, X0=None, off=None, n_nodes=None, lam: float = 1.0,
+                   lr: float = 1e-3, update: bool = True) -> float:
+        B = x.shape[0] if x.dim() == 3 else 1
+        nn = None
+        if n_nodes is not None:
+            nn = np.ascontiguousarray(np.asarray(n_nodes, dtype=np.int32))
+        loss = C.c_double(0)
+        vp = lambda t: C.c_void_p(t.data_ptr()) if t is not None else None  # noqa: E731
+        _check(lib().tlb_net_train_step(self.h, vp(x), vp(dphi), vp(dpsi), vp(X0), vp(off),
+                                        nn.ctypes.data_as(C.POINTER(C.c_int)) if nn is not None else None,
+                                        B, float(lam), float(lr), int(bool(update)), C.byref(loss)))
+        return loss.value
+
+    def warm_start(self, sim, feats):
+        """Replace the plain initial state of ``sim`` by the network's guess."""
+        f = np.ascontiguousarray(feats, dtype=np.float64)
+        _check(lib().tlb_net_warm_start(self.h, sim.h, _dp(f)))
+
+    def launches(self) -> int:
+        return lib().tlb_net_launch_count(self.h)

@@ -23,6 +23,9 @@ struct ImplBase {
   virtual tlb_status autotune(Ctx* c, int* variant, int* zc) = 0;
   // launches the residual kernel into c->L.res (zeroed first); no sync
   virtual tlb_status residual_launch(Ctx* c) = 0;
+  // initial state from the rho, phi, psi moment arrays as they stand and the
+  // current marker positions (profile, u = 0, equilibrium populations)
+  virtual tlb_status init_from_moments(Ctx* c) = 0;
 };
 
 // CUDA events bracketing the phases of a step when profiling.

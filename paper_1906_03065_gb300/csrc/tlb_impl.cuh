@@ -270,6 +270,37 @@ struct Impl : ImplBase {
     return TLB_OK;
   }
 
+  tlb_status init_from_moments(Ctx* c) override {
+    cudaStream_t s = c->stream;
+    IBArgs<Real> ia = ibargs(c);
+    if (c->nn > 0) {
+      tlb_status st = snapshot_box(c, ia, s, true);
+      if (st == TLB_OK) st = ibm_positions(c, ia, s);
+      if (st == TLB_OK) st = ibm_band(c, ia, s);
+      if (st != TLB_OK) return st;
+      c->box_stale = true;
+    }
+    Real* uf = c->ptr<Real>(c->L.ftot);  // u = 0
+    TLB_CUDA(cudaMemsetAsync(c->ptr<char>(c->L.ftot), 0, c->L.ftot.bytes, s));
+    Geo G = geo(c);
+    LBArgs<MODE> la = lbargs(c, c->cur);
+    Real* mu = c->ptr<Real>(c->L.mu);
+    Real *rho = c->ptr<Real>(c->L.rho), *phi = c->ptr<Real>(c->L.phi), *psi = c->ptr<Real>(c->L.psi);
+    k_mu_global<L, MODE><<<blocks(c->N, 256), 256, 0, s>>>(G, la.fe, rho, phi, psi, la.I, mu);
+    TLB_LAUNCHED(c, "k_mu_global");
+    k_init_eq<L, MODE><<<blocks(c->N, 256), 256, 0, s>>>(G, rho, phi, psi, uf, mu, la.gphi, la.gpsi,
+                                                          c->ptr<Store>(c->L.lo[c->cur]),
+                                                          c->ptr<Rest>(c->L.rest[c->cur]));
+    TLB_LAUNCHED(c, "k_init_eq");
+    tlb_status rs = residual_launch(c);
+    if (rs != TLB_OK) return rs;
+    TLB_CUDA(cudaStreamSynchronize(s));
+    c->t = 0;
+    c->t_snap = 0;
+    c->initialised = true;
+    return TLB_OK;
+  }
+
   static ResPtrs resptrs(Ctx* c, unsigned long long* res) {
     return {c->ptr<double>(c->L.snap), c->ptr<double>(c->L.xsnap), res};
   }

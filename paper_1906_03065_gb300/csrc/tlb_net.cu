@@ -1,0 +1,1047 @@
+// Learned warm start: a 3D convolutional encoder-decoder that maps the plain
+// initial state of a capsule-on-interface run and its parameters to a guess
+// of the equilibrium (corrections of phi and psi and a displacement field
+// sampled at the markers), trained by this file's own forward and backward
+// kernels.  The lattice Boltzmann + immersed boundary relaxation then starts
+// from that guess.  Not in the paper; see include/tlb.h for the network.
+//
+// Layout: activations channels-last bf16 [B][E_l^3][C] (C a multiple of 16);
+// activation gradients fp32 of the same shape; master weights, gradients and
+// Adam moments fp32 in the order W[tap][ci][co], b[co] per conv; the GEMMs
+// read bf16 weight copies K-contiguous per output: Wf[co][tap*Ci + ci] for
+// the forward pass and Wd[ci][tap*Co + co] (taps mirrored) for the data
+// gradient.  Every convolution is an implicit GEMM on the tensor cores
+// (mma.sync m16n8k16 bf16, fp32 accumulation).
+#include <cuda_bf16.h>
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <string>
+#include <vector>
+
+#include "tlb_ctx.h"
+
+typedef __nv_bfloat16 bf16;
+
+// ------------------------------------------------------------ GEMM core
+__device__ __forceinline__ void mma_bf16(float* c, const unsigned* a, const unsigned* b) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+      "{%0,%1,%2,%3};\n"
+      : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+
+constexpr int TM = 64;    // GEMM rows per CTA (4 warps x 16)
+constexpr int TK = 16;    // K per stage
+constexpr int SK = 24;    // shared row stride (bf16), 48 bytes: 16-byte aligned, conflict-light
+constexpr int YC = 16;    // output channels: dphi, dpsi, displacement (3), 11 unused
+
+// One 16 x BN slab of a warp: A rows arow (k contiguous), B rows n (k contiguous).
+template <int BN>
+__device__ __forceinline__ void warp_mma(const bf16 (*As)[SK], const bf16 (*Bs)[SK], int arow, float (*acc)[4]) {
+  const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+  unsigned a[4];
+  a[0] = *reinterpret_cast<const unsigned*>(&As[arow + g][2 * t]);
+  a[1] = *reinterpret_cast<const unsigned*>(&As[arow + g + 8][2 * t]);
+  a[2] = *reinterpret_cast<const unsigned*>(&As[arow + g][2 * t + 8]);
+  a[3] = *reinterpret_cast<const unsigned*>(&As[arow + g + 8][2 * t + 8]);
+#pragma unroll
+  for (int j = 0; j < BN / 8; ++j) {
+    unsigned b[2];
+    b[0] = *reinterpret_cast<const unsigned*>(&Bs[j * 8 + g][2 * t]);
+    b[1] = *reinterpret_cast<const unsigned*>(&Bs[j * 8 + g][2 * t + 8]);
+    mma_bf16(acc[j], a, b);
+  }
+}
+
+struct Vox {
+  int b, z, y, x;
+};
+__device__ __forceinline__ Vox vox_of(long long v, int El) {
+  Vox r;
+  r.x = (int)(v % El);
+  r.y = (int)((v / El) % El);
+  r.z = (int)((v / ((long long)El * El)) % El);
+  r.b = (int)(v / ((long long)El * El * El));
+  return r;
+}
+// neighbour of voxel p at tap (27: offsets -1..1 per axis, z slowest; 1: itself), -1 outside
+__device__ __forceinline__ long long nbr(const Vox& p, int tap, int taps, int El) {
+  int dz = 0, dy = 0, dx = 0;
+  if (taps == 27) {
+    dz = tap / 9 - 1;
+    dy = (tap / 3) % 3 - 1;
+    dx = tap % 3 - 1;
+  }
+  const int z = p.z + dz, y = p.y + dy, x = p.x + dx;
+  if (z < 0 || z >= El || y < 0 || y >= El || x < 0 || x >= El) return -1;
+  return (((long long)p.b * El + z) * El + y) * El + x;
+}
+
+// out[v][co] = sum_{tap, ci} in[nbr(v, tap)][ci] W[tap][ci][co]  (+ bias),
+// stored as bf16 relu(.) (RELU) or fp32.  in: [nvox][Ci] bf16; Wk: [Co][taps*Ci].
+template <int BN, bool RELU>
+__global__ void __launch_bounds__(128) k_conv(const bf16* __restrict__ in, int Ci, int El, long long nvox, int taps,
+                                              const bf16* __restrict__ Wk, const float* __restrict__ bias, int Co,
+                                              void* __restrict__ out) {
+  __shared__ __align__(16) bf16 As[2][TM][SK];
+  __shared__ __align__(16) bf16 Bs[2][BN][SK];
+  const int tid = threadIdx.x, w = tid >> 5;
+  const long long m0 = (long long)blockIdx.x * TM;
+  const int n0 = blockIdx.y * BN;
+  const int K = taps * Ci, nk = K / TK, cpt = Ci / TK;
+  // A: thread -> (row, 8-channel half); B: thread -> (n, half) for tid < 2 BN
+  const int ar = tid >> 1, ah = tid & 1;
+  const long long av = m0 + ar;
+  Vox p{0, 0, 0, 0};
+  if (av < nvox) p = vox_of(av, El);
+  uint4 ra, rb;
+  auto load = [&](int kc) {
+    const int tap = kc / cpt, ci0 = (kc % cpt) * TK + ah * 8;
+    ra = make_uint4(0, 0, 0, 0);
+    if (av < nvox) {
+      const long long q = nbr(p, tap, taps, El);
+      if (q >= 0) ra = *reinterpret_cast<const uint4*>(in + q * Ci + ci0);
+    }
+    if (tid < 2 * BN) rb = *reinterpret_cast<const uint4*>(Wk + (long long)(n0 + (tid >> 1)) * K + kc * TK + (tid & 1) * 8);
+  };
+  auto store = [&](int s) {
+    *reinterpret_cast<uint4*>(&As[s][ar][ah * 8]) = ra;
+    if (tid < 2 * BN) *reinterpret_cast<uint4*>(&Bs[s][tid >> 1][(tid & 1) * 8]) = rb;
+  };
+  float acc[BN / 8][4];
+#pragma unroll
+  for (int j = 0; j < BN / 8; ++j) acc[j][0] = acc[j][1] = acc[j][2] = acc[j][3] = 0.f;
+  load(0);
+  store(0);
+  __syncthreads();
+  for (int kc = 0; kc < nk; ++kc) {
+    const int s = kc & 1;
+    if (kc + 1 < nk) load(kc + 1);
+    warp_mma<BN>(As[s], Bs[s], w * 16, acc);
+    if (kc + 1 < nk) store(s ^ 1);
+    __syncthreads();
+  }
+  const int lane = tid & 31, g = lane >> 2, t = lane & 3;
+#pragma unroll
+  for (int half = 0; half < 2; ++half) {
+    const long long v = m0 + w * 16 + g + half * 8;
+    if (v >= nvox) continue;
+#pragma unroll
+    for (int j = 0; j < BN / 8; ++j) {
+      const int n = n0 + j * 8 + 2 * t;
+      float o0 = acc[j][half * 2], o1 = acc[j][half * 2 + 1];
+      if (bias) {
+        o0 += bias[n];
+        o1 += bias[n + 1];
+      }
+      if (RELU) {
+        __nv_bfloat162 h = __floats2bfloat162_rn(fmaxf(o0, 0.f), fmaxf(o1, 0.f));
+        *reinterpret_cast<__nv_bfloat162*>(static_cast<bf16*>(out) + v * Co + n) = h;
+      } else {
+        *reinterpret_cast<float2*>(static_cast<float*>(out) + v * Co + n) = make_float2(o0, o1);
+      }
+    }
+  }
+}
+
+// Weight (and bias) gradient of one conv, split over voxel ranges:
+//   part[split][m][n] = sum_{v in range} A[m][v] gz[v][n]
+// with rows m = tap*Ci + ci: A[m][v] = in[nbr(v, tap)][ci], and one extra row
+// m = taps*Ci of ones (its sums are the bias gradient).
+template <int BN>
+__global__ void __launch_bounds__(128) k_wgrad(const bf16* __restrict__ in, int Ci, int El, long long nvox, int taps,
+                                               const bf16* __restrict__ gz, int Co, long long vchunk,
+                                               float* __restrict__ part) {
+  __shared__ __align__(16) bf16 As[2][TM][SK];
+  __shared__ __align__(16) bf16 Bs[2][BN][SK];
+  const int tid = threadIdx.x, w = tid >> 5;
+  const int M = taps * Ci + 1;
+  const int m0 = blockIdx.x * TM, n0 = blockIdx.y * BN;
+  const long long v0 = (long long)blockIdx.z * vchunk;
+  const long long v1 = min(nvox, v0 + vchunk);
+  const int nk = (int)((v1 - v0 + TK - 1) / TK);
+  // A: thread -> (voxel k = tid / 8, rows gq*8 .. +7); B: thread -> (voxel, 8 columns)
+  const int ak = tid >> 3, aq = tid & 7;
+  const int am = m0 + aq * 8;
+  const int atap = am / Ci, aci = am % Ci;
+  const int bcols = BN / 8, bk = tid / bcols, bq = tid % bcols;
+  uint4 ra, rb;
+  auto load = [&](int kc) {
+    const long long v = v0 + (long long)kc * TK + ak;
+    ra = make_uint4(0, 0, 0, 0);
+    if (v < v1) {
+      if (am + 8 <= M - 1) {
+        const long long q = nbr(vox_of(v, El), atap, taps, El);
+        if (q >= 0) ra = *reinterpret_cast<const uint4*>(in + q * Ci + aci);
+      } else if (am <= M - 1) {  // the block of 8 rows holding the ones row
+        __align__(16) bf16 one[8];
+        for (int j = 0; j < 8; ++j) one[j] = __float2bfloat16_rn(am + j == M - 1 ? 1.f : 0.f);
+        ra = *reinterpret_cast<const uint4*>(one);
+      }
+    }
+    rb = make_uint4(0, 0, 0, 0);
+    const long long vb = v0 + (long long)kc * TK + bk;
+    if (tid < TK * bcols && vb < v1) rb = *reinterpret_cast<const uint4*>(gz + vb * Co + n0 + bq * 8);
+  };
+  auto store = [&](int s) {
+    const bf16* e = reinterpret_cast<const bf16*>(&ra);
+#pragma unroll
+    for (int j = 0; j < 8; ++j) As[s][aq * 8 + j][ak] = e[j];
+    if (tid < TK * bcols) {
+      const bf16* f = reinterpret_cast<const bf16*>(&rb);
+#pragma unroll
+      for (int j = 0; j < 8; ++j) Bs[s][bq * 8 + j][bk] = f[j];
+    }
+  };
+  float acc[BN / 8][4];
+#pragma unroll
+  for (int j = 0; j < BN / 8; ++j) acc[j][0] = acc[j][1] = acc[j][2] = acc[j][3] = 0.f;
+  if (nk > 0) {
+    load(0);
+    store(0);
+  }
+  __syncthreads();
+  for (int kc = 0; kc < nk; ++kc) {
+    const int s = kc & 1;
+    if (kc + 1 < nk) load(kc + 1);
+    warp_mma<BN>(As[s], Bs[s], w * 16, acc);
+    if (kc + 1 < nk) store(s ^ 1);
+    __syncthreads();
+  }
+  const int lane = tid & 31, g = lane >> 2, t = lane & 3;
+  float* P = part + (size_t)blockIdx.z * M * Co;
+#pragma unroll
+  for (int half = 0; half < 2; ++half) {
+    const int m = m0 + w * 16 + g + half * 8;
+    if (m >= M) continue;
+#pragma unroll
+    for (int j = 0; j < BN / 8; ++j) {
+      const int n = n0 + j * 8 + 2 * t;
+      P[(size_t)m * Co + n] = acc[j][half * 2];
+      P[(size_t)m * Co + n + 1] = acc[j][half * 2 + 1];
+    }
+  }
+}
+
+// dW (rows < M-1) and db (row M-1) from the split partials, summed in split order.
+__global__ void k_wgrad_reduce(const float* __restrict__ part, int nsplit, int M, int Co, float* __restrict__ dW,
+                               float* __restrict__ db) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= (long long)M * Co) return;
+  float s = 0.f;
+  for (int k = 0; k < nsplit; ++k) s += part[(size_t)k * M * Co + i];
+  const int m = (int)(i / Co);
+  if (m < M - 1) dW[i] = s;
+  else db[i - (long long)(M - 1) * Co] = s;
+}
+
+// ------------------------------------------------------------ elementwise
+// 2x2x2 average pooling, [B][El^3][C] -> [B][(El/2)^3][C], bf16.
+__global__ void k_pool_fwd(const bf16* __restrict__ in, int El, int C, long long nout, bf16* __restrict__ out) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nout * C) return;
+  const int c = (int)(i % C);
+  const long long v = i / C;
+  const int Eh = El / 2;
+  const Vox p = vox_of(v, Eh);
+  float s = 0.f;
+  for (int d = 0; d < 8; ++d) {
+    const long long q = (((long long)p.b * El + 2 * p.z + (d >> 2)) * El + 2 * p.y + ((d >> 1) & 1)) * El + 2 * p.x + (d & 1);
+    s += __bfloat162float(in[q * C + c]);
+  }
+  out[i] = __float2bfloat16_rn(s * 0.125f);
+}
+
+// g_in[child] += g_out[parent] / 8 (fp32).
+__global__ void k_pool_bwd(const float* __restrict__ gout, int El, int C, long long nin, float* __restrict__ gin) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nin * C) return;
+  const int c = (int)(i % C);
+  const Vox p = vox_of(i / C, El);
+  const int Eh = El / 2;
+  const long long q = (((long long)p.b * Eh + p.z / 2) * Eh + p.y / 2) * Eh + p.x / 2;
+  gin[i] += 0.125f * gout[q * C + c];
+}
+
+// cat[v] = [up2(d)[v] (C1) | e[v] (C2)], bf16.
+__global__ void k_cat_fwd(const bf16* __restrict__ d, int C1, const bf16* __restrict__ e, int C2, int El, long long n,
+                          bf16* __restrict__ cat) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const int C = C1 + C2;
+  if (i >= n * C) return;
+  const int c = (int)(i % C);
+  const long long v = i / C;
+  if (c >= C1) {
+    cat[i] = e[v * C2 + (c - C1)];
+  } else {
+    const Vox p = vox_of(v, El);
+    const int Eh = El / 2;
+    const long long q = (((long long)p.b * Eh + p.z / 2) * Eh + p.y / 2) * Eh + p.x / 2;
+    cat[i] = d[q * C1 + c];
+  }
+}
+
+// From g_cat: g_e += skip part (per fine voxel); g_d += sum over the 8 children (per coarse voxel).
+__global__ void k_cat_bwd_skip(const float* __restrict__ gcat, int C1, int C2, long long n, float* __restrict__ ge) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n * C2) return;
+  const long long v = i / C2;
+  ge[i] += gcat[v * (C1 + C2) + C1 + (i % C2)];
+}
+__global__ void k_cat_bwd_up(const float* __restrict__ gcat, int C1, int C2, int El, long long ncoarse,
+                             float* __restrict__ gd) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= ncoarse * C1) return;
+  const int c = (int)(i % C1);
+  const int Eh = El / 2;
+  const Vox p = vox_of(i / C1, Eh);
+  float s = 0.f;
+  for (int d = 0; d < 8; ++d) {
+    const long long q = (((long long)p.b * El + 2 * p.z + (d >> 2)) * El + 2 * p.y + ((d >> 1) & 1)) * El + 2 * p.x + (d & 1);
+    s += gcat[q * (C1 + C2) + c];
+  }
+  gd[i] += s;
+}
+
+// gz = g * relu'(h) as bf16 (h > 0 where the stored activation is positive).
+__global__ void k_relu_bwd(const float* __restrict__ g, const bf16* __restrict__ h, long long n, bf16* __restrict__ gz) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  gz[i] = __float2bfloat16_rn(__bfloat162float(h[i]) > 0.f ? g[i] : 0.f);
+}
+
+__global__ void k_to_bf16(const float* __restrict__ g, long long n, bf16* __restrict__ o) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) o[i] = __float2bfloat16_rn(g[i]);
+}
+
+// Field loss: gy[v][0..1] = 2/(B V) (y - target), gy[v][2..7] = 0; per-block
+// FP64 partial sums of the squared errors.
+__global__ void k_loss_fields(const float* __restrict__ y, const float* __restrict__ tphi, const float* __restrict__ tpsi,
+                              long long n, double scale, float* __restrict__ gy, double* __restrict__ part) {
+  __shared__ double sm[256];
+  const long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  double e = 0;
+  if (v < n) {
+    const float d0 = y[v * YC] - tphi[v], d1 = y[v * YC + 1] - tpsi[v];
+    e = (double)d0 * d0 + (double)d1 * d1;
+    gy[v * YC] = (float)(2.0 * scale * d0);
+    gy[v * YC + 1] = (float)(2.0 * scale * d1);
+    for (int c = 2; c < YC; ++c) gy[v * YC + c] = 0.f;
+  }
+  sm[threadIdx.x] = e;
+  __syncthreads();
+  for (int s = 128; s > 0; s >>= 1) {
+    if (threadIdx.x < s) sm[threadIdx.x] += sm[threadIdx.x + s];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) part[blockIdx.x] = sm[0];
+}
+
+// Trilinear sampling of channels 2..4 of y at X (clamped to [0, E-1]); the
+// 8 corner weights and indices of one point.
+struct Tri {
+  long long idx[8];
+  float w[8];
+};
+__device__ __forceinline__ Tri tri_of(float x, float y, float z, int E) {
+  Tri T;
+  x = fminf(fmaxf(x, 0.f), E - 1.f);
+  y = fminf(fmaxf(y, 0.f), E - 1.f);
+  z = fminf(fmaxf(z, 0.f), E - 1.f);
+  const int ix = min((int)floorf(x), E - 2), iy = min((int)floorf(y), E - 2), iz = min((int)floorf(z), E - 2);
+  const float fx = x - ix, fy = y - iy, fz = z - iz;
+  for (int d = 0; d < 8; ++d) {
+    const int dx = d & 1, dy = (d >> 1) & 1, dz = d >> 2;
+    T.w[d] = (dx ? fx : 1.f - fx) * (dy ? fy : 1.f - fy) * (dz ? fz : 1.f - fz);
+    T.idx[d] = ((long long)(iz + dz) * E + (iy + dy)) * E + (ix + dx);
+  }
+  return T;
+}
+
+// Marker loss of sample b: offsets = trilinear(y2..4)(X0); gy[2..4] += the
+// gradient (scattered with the trilinear weights); FP64 partial sums.
+__global__ void k_loss_nodes(const float* __restrict__ y, const float* __restrict__ X0, const float* __restrict__ toff,
+                             int nn, int E, double scale, float* __restrict__ gy, double* __restrict__ part) {
+  __shared__ double sm[256];
+  const int l = blockIdx.x * blockDim.x + threadIdx.x;
+  double e = 0;
+  if (l < nn) {
+    const Tri T = tri_of(X0[3 * l], X0[3 * l + 1], X0[3 * l + 2], E);
+    for (int a = 0; a < 3; ++a) {
+      float o = 0.f;
+      for (int d = 0; d < 8; ++d) o += T.w[d] * y[T.idx[d] * YC + 2 + a];
+      const float r = o - toff[3 * l + a];
+      e += (double)r * r;
+      const float gr = (float)(2.0 * scale * r);
+      for (int d = 0; d < 8; ++d) atomicAdd(gy + T.idx[d] * YC + 2 + a, gr * T.w[d]);
+    }
+  }
+  sm[threadIdx.x] = e;
+  __syncthreads();
+  for (int s = 128; s > 0; s >>= 1) {
+    if (threadIdx.x < s) sm[threadIdx.x] += sm[threadIdx.x + s];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) part[blockIdx.x] = sm[0];
+}
+
+// Adam (Kingma and Ba 2015) on fp32 parameters; c1 = 1 - b1^t, c2 = 1 - b2^t.
+__global__ void k_adam(float* __restrict__ th, const float* __restrict__ g, float* __restrict__ m, float* __restrict__ v,
+                       long long n, float lr, float b1, float b2, float eps, float c1, float c2) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const float gi = g[i];
+  const float mi = b1 * m[i] + (1.f - b1) * gi;
+  const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
+  m[i] = mi;
+  v[i] = vi;
+  th[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+}
+
+// bf16 GEMM copies of one conv's weights W[tap][ci][co]:
+// Wf[co][tap*Ci + ci] and Wd[ci][tap*Co + co] with the tap mirrored.
+__global__ void k_weights(const float* __restrict__ W, int taps, int Ci, int Co, bf16* __restrict__ Wf,
+                          bf16* __restrict__ Wd) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= (long long)taps * Ci * Co) return;
+  const int co = (int)(i % Co), ci = (int)((i / Co) % Ci), tap = (int)(i / ((long long)Co * Ci));
+  const bf16 w = __float2bfloat16_rn(W[i]);
+  Wf[(long long)co * taps * Ci + (long long)tap * Ci + ci] = w;
+  Wd[(long long)ci * taps * Co + (long long)(taps - 1 - tap) * Co + co] = w;
+}
+
+// Network input of one sample from a context's fields: phi0, psi0, the
+// broadcast features, zeros.
+__global__ void k_make_input(const float* __restrict__ phi, const float* __restrict__ psi, long long V, float f0,
+                             float f1, float f2, float f3, float f4, bf16* __restrict__ x) {
+  const long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (v >= V) return;
+  __align__(16) bf16 c[16];
+  const float fv[7] = {phi[v], psi[v], f0, f1, f2, f3, f4};
+  for (int k = 0; k < 16; ++k) c[k] = __float2bfloat16_rn(k < 7 ? fv[k] : 0.f);
+  reinterpret_cast<uint4*>(x + v * 16)[0] = reinterpret_cast<uint4*>(c)[0];
+  reinterpret_cast<uint4*>(x + v * 16)[1] = reinterpret_cast<uint4*>(c)[1];
+}
+
+// FP64 partial sums (fixed partition) of phi, psi, phi + y0, psi + y1.
+__global__ void k_ws_sums(const float* __restrict__ phi, const float* __restrict__ psi, const float* __restrict__ y,
+                          long long V, double* __restrict__ part) {
+  __shared__ double sm[4][256];
+  double a[4] = {0, 0, 0, 0};
+  for (long long v = (long long)blockIdx.x * 256 + threadIdx.x; v < V; v += (long long)gridDim.x * 256) {
+    a[0] += phi[v];
+    a[1] += psi[v];
+    a[2] += (double)phi[v] + y[v * YC];
+    a[3] += (double)psi[v] + y[v * YC + 1];
+  }
+  for (int q = 0; q < 4; ++q) sm[q][threadIdx.x] = a[q];
+  __syncthreads();
+  for (int s = 128; s > 0; s >>= 1) {
+    if (threadIdx.x < s)
+      for (int q = 0; q < 4; ++q) sm[q][threadIdx.x] += sm[q][threadIdx.x + s];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0)
+    for (int q = 0; q < 4; ++q) part[q * gridDim.x + blockIdx.x] = sm[q][0];
+}
+
+// Warm-start fields, mass-projected: rho = 1, phi = phi0 + y0 + sphi, psi =
+// psi0 + y1 + spsi with the uniform shifts that restore the plain totals.
+__global__ void k_ws_fields(float* __restrict__ rho, float* __restrict__ phi, float* __restrict__ psi,
+                            const float* __restrict__ y, long long V, const double* __restrict__ tot) {
+  const long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (v >= V) return;
+  const double sphi = (tot[0] - tot[2]) / (double)V, spsi = (tot[1] - tot[3]) / (double)V;
+  rho[v] = 1.f;
+  phi[v] = (float)((double)phi[v] + y[v * YC] + sphi);
+  psi[v] = (float)((double)psi[v] + y[v * YC + 1] + spsi);
+}
+
+// Markers moved by the displacement field: X += trilinear(y2..4)(X).
+__global__ void k_ws_nodes(double* __restrict__ X, int nn, const float* __restrict__ y, int E) {
+  const int l = blockIdx.x * blockDim.x + threadIdx.x;
+  if (l >= nn) return;
+  const Tri T = tri_of((float)X[3 * l], (float)X[3 * l + 1], (float)X[3 * l + 2], E);
+  for (int a = 0; a < 3; ++a) {
+    float o = 0.f;
+    for (int d = 0; d < 8; ++d) o += T.w[d] * y[T.idx[d] * YC + 2 + a];
+    X[3 * l + a] += (double)o;
+  }
+}
+
+__global__ void k_sum_parts(const double* __restrict__ part, int nb, int nq, double* __restrict__ out) {
+  __shared__ double sm[256];
+  for (int q = 0; q < nq; ++q) {
+    double a = 0;
+    for (int i = threadIdx.x; i < nb; i += 256) a += part[q * nb + i];
+    sm[threadIdx.x] = a;
+    __syncthreads();
+    for (int s = 128; s > 0; s >>= 1) {
+      if (threadIdx.x < s) sm[threadIdx.x] += sm[threadIdx.x + s];
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) out[q] = sm[0];
+    __syncthreads();
+  }
+}
+
+// ------------------------------------------------------------ host side
+namespace {
+
+struct Conv {
+  int taps, ci, co, level;
+  size_t w, b;       // offsets in the parameter vector
+  size_t wf, wd;     // offsets (elements) in the bf16 weight copies
+};
+
+// A tensor of the network: channels-last, level l, C channels.
+struct Ten {
+  int level, C;
+  size_t act;   // bf16 activation (elements offset), or SIZE_MAX
+  size_t grad;  // fp32 gradient (elements offset), or SIZE_MAX
+};
+
+struct Net {
+  tlb_net_desc d;
+  cudaStream_t stream = nullptr;
+  char* base = nullptr;
+  size_t bytes = 0;
+  std::vector<Conv> convs;
+  size_t nparam = 0;
+  // arena regions (byte offsets)
+  size_t o_theta, o_grad, o_m, o_v, o_wf, o_wd, o_act, o_grad_act, o_gz, o_y, o_gy, o_part, o_lpart, o_misc;
+  size_t n_wbf = 0, n_act = 0, n_gact = 0, n_gz = 0, n_part = 0;
+  // tensors: x, per encoder level (a, e, pool input p), per decoder level (cat, b, d)
+  Ten x, enc_a[4], enc_e[4], enc_p[4], dec_cat[4], dec_b[4], dec_d[4];
+  long adam_t = 0;
+  long launches = 0;
+
+  template <class T> T* at(size_t off) const { return reinterpret_cast<T*>(base + off); }
+  long long vox(int level, int B) const {
+    const long long El = d.edge >> level;
+    return (long long)B * El * El * El;
+  }
+  int chan(int l) const { return d.base_channels << l; }
+};
+
+size_t al256(size_t v) { return (v + 255) & ~(size_t)255; }
+unsigned nb(long long n, int t) { return (unsigned)((n + t - 1) / t); }
+
+tlb_status check_desc(const tlb_net_desc* d) {
+  if (!d) { set_error("net desc is NULL"); return TLB_ERR_ARG; }
+  if (d->levels < 2 || d->levels > 4) { set_error("net: levels must be 2..4"); return TLB_ERR_ARG; }
+  if (d->base_channels < 16 || d->base_channels % 16 || d->base_channels > 64) {
+    set_error("net: base_channels must be 16, 32, 48 or 64");
+    return TLB_ERR_ARG;
+  }
+  const int div = 1 << (d->levels - 1);
+  if (d->edge < 2 * div || d->edge % div || d->edge > 256) {
+    set_error("net: edge must be a multiple of 2^(levels-1), at least 2^levels and at most 256");
+    return TLB_ERR_ARG;
+  }
+  if (d->max_batch < 1 || d->max_batch > 64) { set_error("net: max_batch must be 1..64"); return TLB_ERR_ARG; }
+  if (d->max_nodes < 0 || d->max_nodes > (1 << 20)) { set_error("net: max_nodes must be 0..2^20"); return TLB_ERR_ARG; }
+  return TLB_OK;
+}
+
+// Layers, parameter offsets, tensors and arena plan (offsets only).
+void plan(Net& n) {
+  const tlb_net_desc& d = n.d;
+  const int L = d.levels, B = d.max_batch;
+  n.convs.clear();
+  size_t p = 0, wb = 0;
+  auto conv = [&](int taps, int ci, int co, int level) {
+    Conv c{taps, ci, co, level, p, p + (size_t)taps * ci * co, wb, 0};
+    p += (size_t)taps * ci * co + co;
+    wb += (size_t)taps * ci * co;
+    n.convs.push_back(c);
+  };
+  conv(27, 16, n.chan(0), 0);
+  conv(27, n.chan(0), n.chan(0), 0);
+  for (int l = 1; l < L; ++l) {
+    conv(27, n.chan(l - 1), n.chan(l), l);
+    conv(27, n.chan(l), n.chan(l), l);
+  }
+  for (int l = L - 2; l >= 0; --l) {
+    conv(27, n.chan(l + 1) + n.chan(l), n.chan(l), l);
+    conv(27, n.chan(l), n.chan(l), l);
+  }
+  conv(1, n.chan(0), YC, 0);
+  n.nparam = p;
+  n.n_wbf = wb;
+  for (Conv& c : n.convs) c.wd = c.wf;  // the two copies share offsets in their own arrays
+  // activations (bf16) and activation gradients (fp32)
+  size_t act = 0, gact = 0;
+  auto ten = [&](int level, int C, bool want_grad) {
+    Ten t{level, C, act, want_grad ? gact : (size_t)-1};
+    act += (size_t)n.vox(level, B) * C;
+    if (want_grad) gact += (size_t)n.vox(level, B) * C;
+    return t;
+  };
+  n.x = ten(0, 16, false);
+  for (int l = 0; l < L; ++l) {
+    if (l > 0) n.enc_p[l] = ten(l, n.chan(l - 1), true);
+    n.enc_a[l] = ten(l, n.chan(l), true);
+    n.enc_e[l] = ten(l, n.chan(l), true);
+  }
+  for (int l = L - 2; l >= 0; --l) {
+    n.dec_cat[l] = ten(l, n.chan(l + 1) + n.chan(l), true);
+    n.dec_b[l] = ten(l, n.chan(l), true);
+    n.dec_d[l] = ten(l, n.chan(l), true);
+  }
+  n.n_act = act;
+  n.n_gact = gact;
+  size_t gz = 0;
+  for (const Conv& c : n.convs) gz = std::max(gz, (size_t)n.vox(c.level, B) * std::max(c.co, c.ci));
+  n.n_gz = gz;
+  // split-K partials of the weight gradient: at most 512 splits
+  size_t part = 0;
+  for (const Conv& c : n.convs) part = std::max(part, (size_t)(c.taps * c.ci + 1) * c.co);
+  n.n_part = part * 512;
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    size_t o = off;
+    off = al256(off + std::max<size_t>(bytes, 1));
+    return o;
+  };
+  n.o_theta = take(n.nparam * 4);
+  n.o_grad = take(n.nparam * 4);
+  n.o_m = take(n.nparam * 4);
+  n.o_v = take(n.nparam * 4);
+  n.o_wf = take(n.n_wbf * 2);
+  n.o_wd = take(n.n_wbf * 2);
+  n.o_act = take(n.n_act * 2);
+  n.o_grad_act = take(n.n_gact * 4);
+  n.o_gz = take(n.n_gz * 2);
+  n.o_y = take((size_t)n.vox(0, B) * YC * 4);
+  n.o_gy = take((size_t)n.vox(0, B) * YC * 4);
+  n.o_part = take(n.n_part * 4);
+  n.o_lpart = take((size_t)(nb(n.vox(0, B), 256) + (size_t)B * nb(d.max_nodes, 256) + 1024) * 8);
+  n.o_misc = take(64 * 8);
+  n.bytes = off;
+}
+
+// GEMM columns per CTA: the largest of 64, 32, 16 dividing the channel
+// count (every channel count is a multiple of 16).
+int tile_n(int C) { return C % 64 == 0 ? 64 : (C % 32 == 0 ? 32 : 16); }
+
+#define NET_LAUNCHED(net, what)                                  \
+  do {                                                           \
+    (net)->launches++;                                           \
+    tlb_status _s = cuda_check(cudaGetLastError(), what);        \
+    if (_s != TLB_OK) return _s;                                 \
+  } while (0)
+
+template <bool RELU>
+tlb_status launch_conv(Net* n, const bf16* in, int Ci, int El, long long nvox, int taps, const bf16* Wk,
+                       const float* bias, int Co, void* out) {
+  const int BN = tile_n(Co);
+  dim3 grid(nb(nvox, TM), Co / BN);
+  cudaStream_t s = n->stream;
+  switch (BN) {
+    case 64: k_conv<64, RELU><<<grid, 128, 0, s>>>(in, Ci, El, nvox, taps, Wk, bias, Co, out); break;
+    case 32: k_conv<32, RELU><<<grid, 128, 0, s>>>(in, Ci, El, nvox, taps, Wk, bias, Co, out); break;
+    case 16: k_conv<16, RELU><<<grid, 128, 0, s>>>(in, Ci, El, nvox, taps, Wk, bias, Co, out); break;
+    default: set_error("net: unsupported channel count"); return TLB_ERR_ARG;
+  }
+  NET_LAUNCHED(n, "k_conv");
+  return TLB_OK;
+}
+
+tlb_status launch_wgrad(Net* n, const Conv& c, const bf16* in, int El, long long nvox, const bf16* gz) {
+  const int BN = tile_n(c.co);
+  const int M = c.taps * c.ci + 1;
+  const int mt = (M + TM - 1) / TM, ntile = c.co / BN;
+  long long splits = std::max(1LL, std::min(512LL, (long long)(2 * 152 * 4) / (mt * ntile)));
+  long long vchunk = (nvox + splits - 1) / splits;
+  vchunk = (vchunk + TK - 1) / TK * TK;
+  splits = (nvox + vchunk - 1) / vchunk;
+  dim3 grid(mt, ntile, (unsigned)splits);
+  float* part = n->at<float>(n->o_part);
+  cudaStream_t s = n->stream;
+  switch (BN) {
+    case 64: k_wgrad<64><<<grid, 128, 0, s>>>(in, c.ci, El, nvox, c.taps, gz, c.co, vchunk, part); break;
+    case 32: k_wgrad<32><<<grid, 128, 0, s>>>(in, c.ci, El, nvox, c.taps, gz, c.co, vchunk, part); break;
+    case 16: k_wgrad<16><<<grid, 128, 0, s>>>(in, c.ci, El, nvox, c.taps, gz, c.co, vchunk, part); break;
+    default: set_error("net: unsupported channel count"); return TLB_ERR_ARG;
+  }
+  NET_LAUNCHED(n, "k_wgrad");
+  float* g = n->at<float>(n->o_grad);
+  k_wgrad_reduce<<<nb((long long)M * c.co, 256), 256, 0, s>>>(part, (int)splits, M, c.co, g + c.w, g + c.b);
+  NET_LAUNCHED(n, "k_wgrad_reduce");
+  return TLB_OK;
+}
+
+tlb_status refresh_weights(Net* n) {
+  const float* th = n->at<float>(n->o_theta);
+  for (const Conv& c : n->convs) {
+    k_weights<<<nb((long long)c.taps * c.ci * c.co, 256), 256, 0, n->stream>>>(
+        th + c.w, c.taps, c.ci, c.co, n->at<bf16>(n->o_wf) + c.wf, n->at<bf16>(n->o_wd) + c.wd);
+    NET_LAUNCHED(n, "k_weights");
+  }
+  return TLB_OK;
+}
+
+// Forward pass of B samples from the input tensor x (already in place).
+tlb_status forward(Net* n, int B) {
+  const int L = n->d.levels;
+  bf16* A = n->at<bf16>(n->o_act);
+  const bf16* Wf = n->at<bf16>(n->o_wf);
+  const float* th = n->at<float>(n->o_theta);
+  cudaStream_t s = n->stream;
+  tlb_status st;
+  size_t k = 0;
+  const bf16* h = A + n->x.act;
+  int hc = 16;
+  for (int l = 0; l < L; ++l) {
+    const int El = n->d.edge >> l;
+    const long long V = n->vox(l, B);
+    if (l > 0) {
+      bf16* p = A + n->enc_p[l].act;
+      k_pool_fwd<<<nb(V * hc, 256), 256, 0, s>>>(h, El * 2, hc, V, p);
+      NET_LAUNCHED(n, "k_pool_fwd");
+      h = p;
+    }
+    const Conv& c1 = n->convs[k++];
+    if ((st = launch_conv<true>(n, h, c1.ci, El, V, 27, Wf + c1.wf, th + c1.b, c1.co, A + n->enc_a[l].act)) != TLB_OK)
+      return st;
+    const Conv& c2 = n->convs[k++];
+    if ((st = launch_conv<true>(n, A + n->enc_a[l].act, c2.ci, El, V, 27, Wf + c2.wf, th + c2.b, c2.co,
+                                A + n->enc_e[l].act)) != TLB_OK)
+      return st;
+    h = A + n->enc_e[l].act;
+    hc = c2.co;
+  }
+  const bf16* dprev = A + n->enc_e[L - 1].act;
+  for (int l = L - 2; l >= 0; --l) {
+    const int El = n->d.edge >> l;
+    const long long V = n->vox(l, B);
+    const int C1 = n->chan(l + 1), C2 = n->chan(l);
+    bf16* cat = A + n->dec_cat[l].act;
+    k_cat_fwd<<<nb(V * (C1 + C2), 256), 256, 0, s>>>(dprev, C1, A + n->enc_e[l].act, C2, El, V, cat);
+    NET_LAUNCHED(n, "k_cat_fwd");
+    const Conv& c1 = n->convs[k++];
+    if ((st = launch_conv<true>(n, cat, c1.ci, El, V, 27, Wf + c1.wf, th + c1.b, c1.co, A + n->dec_b[l].act)) != TLB_OK)
+      return st;
+    const Conv& c2 = n->convs[k++];
+    if ((st = launch_conv<true>(n, A + n->dec_b[l].act, c2.ci, El, V, 27, Wf + c2.wf, th + c2.b, c2.co,
+                                A + n->dec_d[l].act)) != TLB_OK)
+      return st;
+    dprev = A + n->dec_d[l].act;
+  }
+  const Conv& co = n->convs[k++];
+  return launch_conv<false>(n, dprev, co.ci, n->d.edge, n->vox(0, B), 1, Wf + co.wf, th + co.b, YC,
+                            n->at<float>(n->o_y));
+}
+
+// Backward of one conv whose output is `out` (post-relu, bf16) with
+// gradient g_out (fp32): weight/bias gradients, and the input gradient
+// (fp32, overwritten) when g_in is non-null.
+tlb_status conv_bwd(Net* n, const Conv& c, const bf16* in, const bf16* out, const float* g_out, float* g_in, int B,
+                    bool relu) {
+  const int El = n->d.edge >> c.level;
+  const long long V = n->vox(c.level, B);
+  bf16* gz = n->at<bf16>(n->o_gz);
+  if (relu) k_relu_bwd<<<nb(V * c.co, 256), 256, 0, n->stream>>>(g_out, out, V * c.co, gz);
+  else k_to_bf16<<<nb(V * c.co, 256), 256, 0, n->stream>>>(g_out, V * c.co, gz);
+  NET_LAUNCHED(n, "k_relu_bwd");
+  tlb_status st = launch_wgrad(n, c, in, El, V, gz);
+  if (st != TLB_OK || !g_in) return st;
+  return launch_conv<false>(n, gz, c.co, El, V, c.taps, n->at<bf16>(n->o_wd) + c.wd, nullptr, c.ci, g_in);
+}
+
+// Backward pass of B samples, from gy (loss gradient of the output) to the
+// parameter gradients.  Order: the output conv, the decoder from the finest
+// level up (its input gradient feeds the skip connection and the coarser
+// level), then the encoder from the coarsest level down (the pooling
+// gradient feeds the finer level).
+tlb_status backward(Net* n, int B) {
+  const int L = n->d.levels;
+  bf16* A = n->at<bf16>(n->o_act);
+  float* G = n->at<float>(n->o_grad_act);
+  cudaStream_t s = n->stream;
+  TLB_CUDA(cudaMemsetAsync(G, 0, n->n_gact * 4, s));
+  tlb_status st;
+  int k = (int)n->convs.size() - 1;
+  const Ten& d0 = n->dec_d[0];
+  if ((st = conv_bwd(n, n->convs[k--], A + d0.act, nullptr, n->at<float>(n->o_gy), G + d0.grad, B, false)) != TLB_OK)
+    return st;
+  for (int l = 0; l <= L - 2; ++l) {
+    const Conv& c2 = n->convs[k--];
+    const Conv& c1 = n->convs[k--];
+    const int C1 = n->chan(l + 1), C2 = n->chan(l);
+    const long long V = n->vox(l, B);
+    const int El = n->d.edge >> l;
+    if ((st = conv_bwd(n, c2, A + n->dec_b[l].act, A + n->dec_d[l].act, G + n->dec_d[l].grad, G + n->dec_b[l].grad,
+                       B, true)) != TLB_OK)
+      return st;
+    if ((st = conv_bwd(n, c1, A + n->dec_cat[l].act, A + n->dec_b[l].act, G + n->dec_b[l].grad,
+                       G + n->dec_cat[l].grad, B, true)) != TLB_OK)
+      return st;
+    k_cat_bwd_skip<<<nb(V * C2, 256), 256, 0, s>>>(G + n->dec_cat[l].grad, C1, C2, V, G + n->enc_e[l].grad);
+    NET_LAUNCHED(n, "k_cat_bwd_skip");
+    const Ten& coarse = (l + 1 <= L - 2) ? n->dec_d[l + 1] : n->enc_e[L - 1];
+    k_cat_bwd_up<<<nb(n->vox(l + 1, B) * C1, 256), 256, 0, s>>>(G + n->dec_cat[l].grad, C1, C2, El,
+                                                                 n->vox(l + 1, B), G + coarse.grad);
+    NET_LAUNCHED(n, "k_cat_bwd_up");
+  }
+  for (int l = L - 1; l >= 0; --l) {
+    const Conv& c2 = n->convs[k--];
+    const Conv& c1 = n->convs[k--];
+    if ((st = conv_bwd(n, c2, A + n->enc_a[l].act, A + n->enc_e[l].act, G + n->enc_e[l].grad, G + n->enc_a[l].grad,
+                       B, true)) != TLB_OK)
+      return st;
+    const bf16* in = l > 0 ? A + n->enc_p[l].act : A + n->x.act;
+    float* gin = l > 0 ? G + n->enc_p[l].grad : nullptr;
+    if ((st = conv_bwd(n, c1, in, A + n->enc_a[l].act, G + n->enc_a[l].grad, gin, B, true)) != TLB_OK) return st;
+    if (l > 0) {
+      const long long Vf = n->vox(l - 1, B);
+      k_pool_bwd<<<nb(Vf * c1.ci, 256), 256, 0, s>>>(G + n->enc_p[l].grad, n->d.edge >> (l - 1), c1.ci, Vf,
+                                                      G + n->enc_e[l - 1].grad);
+      NET_LAUNCHED(n, "k_pool_bwd");
+    }
+  }
+  return TLB_OK;
+}
+
+// Loss of the forward outputs of B samples against the targets; writes gy
+// and returns the loss through tot (device, FP64).
+tlb_status loss(Net* n, int B, const float* dphi, const float* dpsi, const float* X0, const float* off,
+                const int* nnodes, double lambda, double* host_loss) {
+  const long long V = n->vox(0, B), V1 = n->vox(0, 1);
+  const int E = n->d.edge;
+  cudaStream_t s = n->stream;
+  double* part = n->at<double>(n->o_lpart);
+  const unsigned nbf = nb(V, 256);
+  k_loss_fields<<<nbf, 256, 0, s>>>(n->at<float>(n->o_y), dphi, dpsi, V, 1.0 / (double)V, n->at<float>(n->o_gy), part);
+  NET_LAUNCHED(n, "k_loss_fields");
+  long long ntot = 0;
+  for (int b = 0; b < B; ++b) ntot += nnodes ? nnodes[b] : 0;
+  unsigned nbn = 0;
+  if (ntot > 0 && lambda != 0.0) {
+    for (int b = 0; b < B; ++b) {
+      if (nnodes[b] <= 0) continue;
+      const unsigned k = nb(nnodes[b], 256);
+      k_loss_nodes<<<k, 256, 0, s>>>(n->at<float>(n->o_y) + b * V1 * YC, X0 + (size_t)b * n->d.max_nodes * 3,
+                                     off + (size_t)b * n->d.max_nodes * 3, nnodes[b], E, lambda / (3.0 * ntot),
+                                     n->at<float>(n->o_gy) + b * V1 * YC, part + nbf + nbn);
+      NET_LAUNCHED(n, "k_loss_nodes");
+      nbn += k;
+    }
+  }
+  double* tot = n->at<double>(n->o_misc);
+  k_sum_parts<<<1, 256, 0, s>>>(part, (int)nbf, 1, tot);
+  NET_LAUNCHED(n, "k_sum_parts");
+  if (nbn) {
+    k_sum_parts<<<1, 256, 0, s>>>(part + nbf, (int)nbn, 1, tot + 1);
+    NET_LAUNCHED(n, "k_sum_parts");
+  }
+  double h[2] = {0, 0};
+  TLB_CUDA(cudaMemcpyAsync(h, tot, (nbn ? 2 : 1) * sizeof(double), cudaMemcpyDeviceToHost, s));
+  TLB_CUDA(cudaStreamSynchronize(s));
+  if (host_loss) *host_loss = h[0] / (double)V + (nbn ? lambda * h[1] / (3.0 * ntot) : 0.0);
+  return TLB_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+tlb_status tlb_net_param_count(const tlb_net_desc* desc, size_t* n) {
+  tlb_status s = check_desc(desc);
+  if (s != TLB_OK) return s;
+  if (!n) { set_error("n is NULL"); return TLB_ERR_ARG; }
+  Net net;
+  net.d = *desc;
+  plan(net);
+  *n = net.nparam;
+  return TLB_OK;
+}
+
+tlb_status tlb_net_state_bytes(const tlb_net_desc* desc, size_t* bytes) {
+  tlb_status s = check_desc(desc);
+  if (s != TLB_OK) return s;
+  if (!bytes) { set_error("bytes is NULL"); return TLB_ERR_ARG; }
+  Net net;
+  net.d = *desc;
+  plan(net);
+  *bytes = net.bytes;
+  return TLB_OK;
+}
+
+tlb_status tlb_net_create(const tlb_net_desc* desc, void* arena, size_t bytes, void* cuda_stream, void** net_out) {
+  tlb_status s = check_desc(desc);
+  if (s != TLB_OK) return s;
+  if (!arena || !net_out) { set_error("arena and net_out must be non-NULL"); return TLB_ERR_ARG; }
+  if (((uintptr_t)arena) & 255) { set_error("arena must be 256-byte aligned"); return TLB_ERR_ARG; }
+  Net* n = new Net();
+  n->d = *desc;
+  plan(*n);
+  if (bytes < n->bytes) {
+    set_error("net arena too small: need " + std::to_string(n->bytes) + " bytes");
+    delete n;
+    return TLB_ERR_ALLOC;
+  }
+  n->base = (char*)arena;
+  n->stream = (cudaStream_t)cuda_stream;
+  s = cuda_check(cudaMemsetAsync(n->base, 0, n->bytes, n->stream), "memset net arena");
+  if (s == TLB_OK) s = cuda_check(cudaStreamSynchronize(n->stream), "net create");
+  if (s != TLB_OK) { delete n; return s; }
+  *net_out = n;
+  return TLB_OK;
+}
+
+tlb_status tlb_net_set_params(void* net, const float* host, size_t count) {
+  Net* n = (Net*)net;
+  if (!n || !host) { set_error("net/host is NULL"); return TLB_ERR_ARG; }
+  if (count != n->nparam) { set_error("net_set_params: count differs from tlb_net_param_count"); return TLB_ERR_ARG; }
+  TLB_CUDA(cudaMemcpyAsync(n->at<float>(n->o_theta), host, count * 4, cudaMemcpyHostToDevice, n->stream));
+  TLB_CUDA(cudaMemsetAsync(n->at<float>(n->o_m), 0, count * 4, n->stream));
+  TLB_CUDA(cudaMemsetAsync(n->at<float>(n->o_v), 0, count * 4, n->stream));
+  n->adam_t = 0;
+  n->launches = 0;
+  tlb_status s = refresh_weights(n);
+  if (s != TLB_OK) return s;
+  TLB_CUDA(cudaStreamSynchronize(n->stream));
+  return TLB_OK;
+}
+
+static tlb_status copy_out(Net* n, size_t off, float* host, size_t count) {
+  if (!host) { set_error("host is NULL"); return TLB_ERR_ARG; }
+  if (count != n->nparam) { set_error("net: count differs from tlb_net_param_count"); return TLB_ERR_ARG; }
+  TLB_CUDA(cudaMemcpyAsync(host, n->at<float>(off), count * 4, cudaMemcpyDeviceToHost, n->stream));
+  TLB_CUDA(cudaStreamSynchronize(n->stream));
+  return TLB_OK;
+}
+
+tlb_status tlb_net_get_params(void* net, float* host, size_t count) {
+  Net* n = (Net*)net;
+  if (!n) { set_error("net is NULL"); return TLB_ERR_ARG; }
+  return copy_out(n, n->o_theta, host, count);
+}
+
+tlb_status tlb_net_get_grads(void* net, float* host, size_t count) {
+  Net* n = (Net*)net;
+  if (!n) { set_error("net is NULL"); return TLB_ERR_ARG; }
+  return copy_out(n, n->o_grad, host, count);
+}
+
+static tlb_status take_input(Net* n, const void* x_dev, int batch) {
+  if (!x_dev) { set_error("x is NULL"); return TLB_ERR_ARG; }
+  if (batch < 1 || batch > n->d.max_batch) { set_error("net: batch must be 1..max_batch"); return TLB_ERR_ARG; }
+  TLB_CUDA(cudaMemcpyAsync(n->at<bf16>(n->o_act) + n->x.act, x_dev, (size_t)n->vox(0, batch) * 16 * 2,
+                           cudaMemcpyDeviceToDevice, n->stream));
+  return TLB_OK;
+}
+
+tlb_status tlb_net_forward(void* net, const void* x_dev, int batch, float* y_dev) {
+  Net* n = (Net*)net;
+  if (!n) { set_error("net is NULL"); return TLB_ERR_ARG; }
+  n->launches = 0;
+  tlb_status s = take_input(n, x_dev, batch);
+  if (s == TLB_OK) s = forward(n, batch);
+  if (s != TLB_OK) return s;
+  if (y_dev)
+    TLB_CUDA(cudaMemcpyAsync(y_dev, n->at<float>(n->o_y), (size_t)n->vox(0, batch) * YC * 4, cudaMemcpyDeviceToDevice,
+                             n->stream));
+  return TLB_OK;
+}
+
+tlb_status tlb_net_train_step(void* net, const void* x_dev, const float* dphi_dev, const float* dpsi_dev,
+                              const float* X0_dev, const float* off_dev, const int* n_nodes, int batch,
+                              double lambda, double lr, int update, double* loss_out) {
+  Net* n = (Net*)net;
+  if (!n || !dphi_dev || !dpsi_dev) { set_error("net/targets are NULL"); return TLB_ERR_ARG; }
+  if (n_nodes) {
+    for (int b = 0; b < batch; ++b)
+      if (n_nodes[b] < 0 || n_nodes[b] > n->d.max_nodes) { set_error("net: n_nodes outside 0..max_nodes"); return TLB_ERR_ARG; }
+    bool any = false;
+    for (int b = 0; b < batch; ++b) any |= n_nodes[b] > 0;
+    if (any && (!X0_dev || !off_dev)) { set_error("net: marker arrays are NULL"); return TLB_ERR_ARG; }
+  }
+  n->launches = 0;
+  tlb_status s = take_input(n, x_dev, batch);
+  if (s == TLB_OK) s = forward(n, batch);
+  if (s == TLB_OK) s = loss(n, batch, dphi_dev, dpsi_dev, X0_dev, off_dev, n_nodes, lambda, loss_out);
+  if (s == TLB_OK) s = backward(n, batch);
+  if (s != TLB_OK || !update) return s;
+  n->adam_t += 1;
+  const float b1 = 0.9f, b2 = 0.999f;
+  const float c1 = (float)(1.0 - pow(0.9, (double)n->adam_t)), c2 = (float)(1.0 - pow(0.999, (double)n->adam_t));
+  k_adam<<<nb((long long)n->nparam, 256), 256, 0, n->stream>>>(n->at<float>(n->o_theta), n->at<float>(n->o_grad),
+                                                               n->at<float>(n->o_m), n->at<float>(n->o_v),
+                                                               (long long)n->nparam, (float)lr, b1, b2, 1e-8f, c1, c2);
+  NET_LAUNCHED(n, "k_adam");
+  return refresh_weights(n);
+}
+
+static tlb_status check_ctx(Net* n, Ctx* c) {
+  if (!c) { set_error("ctx is NULL"); return TLB_ERR_ARG; }
+  if (c->p.dim != 3 || c->nx != n->d.edge || c->ny != n->d.edge || c->nz != n->d.edge) {
+    set_error("net: the context must be a 3D lattice of edge^3 cells");
+    return TLB_ERR_ARG;
+  }
+  if (c->ts.real != 4) { set_error("net: the context must compute in FP32 (storage f32, f16 or bf16)"); return TLB_ERR_ARG; }
+  if (!c->initialised) { set_error("net: the context is not initialised"); return TLB_ERR_STATE; }
+  return TLB_OK;
+}
+
+tlb_status tlb_net_input(void* net, void* ctx, const double* feats, void* x_dev) {
+  Net* n = (Net*)net;
+  Ctx* c = (Ctx*)ctx;
+  if (!n || !feats || !x_dev) { set_error("net/feats/x is NULL"); return TLB_ERR_ARG; }
+  tlb_status s = check_ctx(n, c);
+  if (s != TLB_OK) return s;
+  k_make_input<<<nb(c->N, 256), 256, 0, n->stream>>>(c->ptr<float>(c->L.phi), c->ptr<float>(c->L.psi), c->N,
+                                                     (float)feats[0], (float)feats[1], (float)feats[2],
+                                                     (float)feats[3], (float)feats[4], (bf16*)x_dev);
+  NET_LAUNCHED(n, "k_make_input");
+  return TLB_OK;
+}
+
+tlb_status tlb_net_warm_start(void* net, void* ctx, const double* feats) {
+  Net* n = (Net*)net;
+  Ctx* c = (Ctx*)ctx;
+  if (!n || !feats) { set_error("net/feats is NULL"); return TLB_ERR_ARG; }
+  tlb_status s = check_ctx(n, c);
+  if (s != TLB_OK) return s;
+  if (c->t != 0) { set_error("net_warm_start: the context must hold its initial state (no step taken)"); return TLB_ERR_STATE; }
+  if (c->stream != n->stream) TLB_CUDA(cudaStreamSynchronize(c->stream));
+  n->launches = 0;
+  cudaStream_t st = n->stream;
+  bf16* x = n->at<bf16>(n->o_act) + n->x.act;
+  float* phi = c->ptr<float>(c->L.phi);
+  float* psi = c->ptr<float>(c->L.psi);
+  k_make_input<<<nb(c->N, 256), 256, 0, st>>>(phi, psi, c->N, (float)feats[0], (float)feats[1], (float)feats[2],
+                                              (float)feats[3], (float)feats[4], x);
+  NET_LAUNCHED(n, "k_make_input");
+  if ((s = forward(n, 1)) != TLB_OK) return s;
+  const float* y = n->at<float>(n->o_y);
+  double* part = n->at<double>(n->o_lpart);
+  double* tot = n->at<double>(n->o_misc) + 8;
+  k_ws_sums<<<256, 256, 0, st>>>(phi, psi, y, c->N, part);
+  NET_LAUNCHED(n, "k_ws_sums");
+  k_sum_parts<<<1, 256, 0, st>>>(part, 256, 4, tot);
+  NET_LAUNCHED(n, "k_sum_parts");
+  k_ws_fields<<<nb(c->N, 256), 256, 0, st>>>(c->ptr<float>(c->L.rho), phi, psi, y, c->N, tot);
+  NET_LAUNCHED(n, "k_ws_fields");
+  if (c->nn > 0) {
+    k_ws_nodes<<<nb(c->nn, 128), 128, 0, st>>>(c->ptr<double>(c->L.X), c->nn, y, n->d.edge);
+    NET_LAUNCHED(n, "k_ws_nodes");
+  }
+  TLB_CUDA(cudaStreamSynchronize(st));
+  return c->impl->init_from_moments(c);
+}
+
+long tlb_net_launch_count(void* net) {
+  Net* n = (Net*)net;
+  return n ? n->launches : 0;
+}
+
+void tlb_net_destroy(void* net) { delete (Net*)net; }
+
+}  // extern "C"

@@ -1,0 +1,176 @@
+"""Learned warm start on the GPU: the library's forward pass, gradients and
+Adam step against the FP64 reference network of oracle/warmstart.py (which
+rounds stored activations to bf16 as the GPU stores them), the warm start of
+a context (mass-projected fields, moved markers), and a small end-to-end
+run: relax a few instances, train on them, relax held-out instances from the
+plain and from the learned start."""
+import numpy as np
+import pytest
+
+from oracle import warmstart as ws
+from paper_1906_03065_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+E, C0, LV = 16, 16, 3
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1906_03065_gb300 import build
+    build.build()
+    import oracle
+    oracle.build()
+
+
+def _theta(seed, c0=C0, lv=LV):
+    rng = np.random.default_rng(seed)
+    th = ws.init_params(seed, c0, lv)
+    o = 0
+    for t, ci, co in ws.layer_shapes(c0, lv):
+        o += t * ci * co
+        th[o:o + co] = rng.normal(0, 0.05, co)  # live biases
+        o += co
+    th[o - 16 - c0 * 16:o - 16] = rng.normal(0, 0.2, c0 * 16)  # live output layer
+    return th
+
+
+def _inputs(rng, B, e=E):
+    xs = [ws.make_input(rng.uniform(-1, 1, e ** 3), rng.uniform(0, 1, e ** 3), rng.uniform(-1, 1, 5), e)
+          for _ in range(B)]
+    return np.stack(xs)
+
+
+def _to_gpu_x(x):
+    import torch
+    B, Cn = x.shape[0], x.shape[1]
+    xl = np.ascontiguousarray(x.reshape(B, Cn, -1).transpose(0, 2, 1))
+    return torch.from_numpy(xl).to(torch.bfloat16).cuda()
+
+
+def _net(**kw):
+    from paper_1906_03065_gb300 import WarmStartNet
+    d = dict(edge=E, base_channels=C0, levels=LV, max_batch=4, max_nodes=32)
+    d.update(kw)
+    return WarmStartNet(**d)
+
+
+def _relerr(a, b):
+    return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
+
+
+def test_forward_matches_oracle():
+    rng = np.random.default_rng(0)
+    th = _theta(1)
+    x = _inputs(rng, 2)
+    net = _net()
+    net.set_params(th)
+    y = net.forward(_to_gpu_x(x)).cpu().numpy()
+    yo, _ = ws.forward(th, x, c0=C0, levels=LV)
+    yo = yo.numpy().reshape(2, 16, -1).transpose(0, 2, 1)
+    assert _relerr(y[..., :5], yo[..., :5]) < 5e-3
+    assert np.abs(y - yo).max() < 2e-2 * np.abs(yo).max()
+    assert net.launches() > 0
+
+
+def test_gradients_and_adam_match_oracle():
+    import torch
+    rng = np.random.default_rng(2)
+    th = _theta(3)
+    B, n = 2, 20
+    x = _inputs(rng, B)
+    dphi = rng.normal(0, 0.05, (B, E ** 3))
+    dpsi = rng.normal(0, 0.05, (B, E ** 3))
+    X0 = [rng.uniform(1, E - 2, (n, 3)) for _ in range(B)]
+    off = [rng.normal(0, 0.2, (n, 3)) for _ in range(B)]
+    net = _net()
+    net.set_params(th)
+    Xa = np.zeros((B, 32, 3), np.float32)
+    Oa = np.zeros((B, 32, 3), np.float32)
+    for b in range(B):
+        Xa[b, :n], Oa[b, :n] = X0[b], off[b]
+    f = lambda a: torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).cuda()  # noqa: E731
+    L = net.train_step(_to_gpu_x(x), f(dphi), f(dpsi), f(Xa), f(Oa), [n] * B, lam=0.5, lr=1e-3, update=False)
+    Lo = ws.loss(th, x, dphi, dpsi, X0, off, lam=0.5, c0=C0, levels=LV).item()
+    assert L == pytest.approx(Lo, rel=1e-2)
+    g = net.grads()
+    go = ws.grad(th, x, dphi, dpsi, X0, off, lam=0.5, c0=C0, levels=LV)
+    # per weight and bias tensor (bf16 GEMM operands against FP64 backward);
+    # tensors whose gradient is negligible beside the largest are skipped
+    o, big = 0, np.abs(go).max()
+    for k, (t, ci, co) in enumerate(ws.layer_shapes(C0, LV)):
+        nw = t * ci * co
+        for s in (slice(o, o + nw), slice(o + nw, o + nw + co)):
+            if np.abs(go[s]).max() > 1e-3 * big:
+                assert _relerr(g[s], go[s]) < 4e-2, (k, s, _relerr(g[s], go[s]))
+        o += nw + co
+    assert _relerr(g, go) < 2e-2
+    # one Adam step (update=1) from the same state
+    net.set_params(th)
+    net.train_step(_to_gpu_x(x), f(dphi), f(dpsi), f(Xa), f(Oa), [n] * B, lam=0.5, lr=1e-3, update=True)
+    g1 = net.grads()
+    t1 = net.params()
+    ref, _, _ = ws.adam(th.astype(np.float64), g1.astype(np.float64), np.zeros_like(g1, dtype=np.float64),
+                        np.zeros_like(g1, dtype=np.float64), 1, lr=1e-3)
+    assert np.abs(t1 - ref).max() < 1e-6
+
+
+def _cube(edge=32, R=6.0, level=2, seed=0):
+    rng = np.random.default_rng(seed)
+    c = edge / 2.0
+    k = rng.uniform(0.005, 0.03, 3)
+    p = W.Params(dim=3, nx=edge, ny=edge, nz=edge, wall_last=1, storage="f32", alpha=1.0, kappa1=k[0],
+                 kappa2=k[1], kappa3=k[2], kappa_c=0.01, dc=8.0, interface_pos=c)
+    m = W.icosphere(level, R * rng.uniform(0.9, 1.1), (c + rng.uniform(-0.4, 0.4), c + rng.uniform(-0.4, 0.4), c))
+    m.G, m.C, m.kb = float(rng.uniform(0.002, 0.05)), 1.0, 0.005
+    return W.Workload(f"cube{edge}_{seed}", p, [m], steps=0)
+
+
+def test_warm_start_of_a_context():
+    """Fields: phi0 + y0 and psi0 + y1 shifted to the plain totals; markers
+    X0 + trilinear(y2..4)(X0); the context then holds the equilibrium
+    populations of these fields."""
+    import oracle
+    import torch
+    from paper_1906_03065_gb300 import Simulation, warmstart as WS
+    wl = _cube(32)
+    th = _theta(5, lv=3)
+    net = _net(edge=32, max_batch=1)
+    net.set_params(th)
+    s = Simulation(wl).init()
+    phi0, psi0, X0 = s.field("phi"), s.field("psi"), s.nodes(0)
+    feats = WS.features(wl)
+    net.warm_start(s, feats)
+    o = oracle.Oracle(wl)
+    x = ws.make_input(o.field("phi"), o.field("psi"), feats, 32)[None]
+    yo, offs = ws.forward(th, x, [X0], c0=C0, levels=3)
+    yo = yo[0].numpy().reshape(16, -1)
+    p_ref, s_ref = ws.mass_projection(phi0 + yo[0], psi0 + yo[1], phi0, psi0)
+    scale = np.abs(yo[:2]).max()
+    assert np.abs(s.field("phi") - p_ref).max() < 2e-2 * scale + 1e-5
+    assert np.abs(s.field("psi") - s_ref).max() < 2e-2 * scale + 1e-5
+    assert s.field("phi").sum() == pytest.approx(phi0.sum(), abs=1e-3)
+    assert s.field("psi").sum() == pytest.approx(psi0.sum(), abs=1e-3)
+    Xr = X0 + offs[0].numpy()
+    assert np.abs(s.nodes(0) - Xr).max() < 2e-2 * np.abs(offs[0].numpy()).max() + 1e-5
+    s.step(5)  # the relaxation runs from it
+    assert np.isfinite(s.field("C3")).all()
+    torch.cuda.synchronize()
+
+
+def test_training_gains_over_the_plain_start():
+    """Relax 12 instances, train on 10, then relax the 2 held-out instances
+    from the plain and from the learned start: the learned start is closer
+    to equilibrium (smaller residual over the first checks)."""
+    from paper_1906_03065_gb300 import WarmStartNet, warmstart as WS
+    wls = [_cube(32, seed=100 + i) for i in range(12)]
+    net = WarmStartNet(edge=32, base_channels=16, levels=3, max_batch=4, max_nodes=162)
+    net.set_params(ws.init_params(0, 16, 3))
+    data = WS.dataset(net, wls[:10], max_steps=1500, check_every=500, tol=0.0)
+    losses = WS.train(net, data, epochs=40, batch=4, lr=2e-3)
+    assert np.mean(losses[-5:]) < 0.5 * np.mean(losses[:3])
+    r = WS.compare(net, wls[10:], max_steps=300, check_every=300, tol=0.0)
+    assert np.mean(r["learned_residual"]) < np.mean(r["plain_residual"]), r
