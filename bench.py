@@ -160,6 +160,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-lowprec", action="store_true")
     ap.add_argument("--no-sweep", action="store_true")
+    ap.add_argument("--no-net", action="store_true")
+    ap.add_argument("--warmstart", action="store_true",
+                    help="also run the time-to-equilibrium experiment of the learned warm start (minutes)")
     args = ap.parse_args()
 
     from paper_1906_03065_gb300 import workloads as W
@@ -322,6 +325,56 @@ def main():
         del views, bt
         torch.cuda.empty_cache()
 
+    # warm-start network: its convolutions are the build's only dense
+    # contraction (tensor cores); algorithmic FLOPs per sample / event time
+    net_line = {}
+    if rank == 0 and not args.no_net:
+        from paper_1906_03065_gb300 import WarmStartNet, warmstart as WSm
+        E, B = 48, 8
+        net = WarmStartNet(E, 16, 4, max_batch=B, max_nodes=642, device=dev)
+        net.set_params(WSm.init_params(net, 0))
+        c = [16 << l for l in range(4)]
+        shapes = [(27, 16, c[0], 0), (27, c[0], c[0], 0)]
+        for l in range(1, 4):
+            shapes += [(27, c[l - 1], c[l], l), (27, c[l], c[l], l)]
+        for l in range(2, -1, -1):
+            shapes += [(27, c[l + 1] + c[l], c[l], l), (27, c[l], c[l], l)]
+        shapes.append((1, c[0], 16, 0))
+        fl = [2.0 * (E >> lv) ** 3 * t * ci * co for t, ci, co, lv in shapes]
+        f_fwd = sum(fl)
+        f_train = 3 * f_fwd - fl[0]  # forward, weight gradients, data gradients but the input's
+        x = torch.zeros((B, E ** 3, 16), dtype=torch.bfloat16, device=dev)
+        tg = torch.zeros((B, E ** 3), dtype=torch.float32, device=dev)
+        a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        net.forward(x)
+        net.train_step(x, tg, tg, lr=0.0)
+        torch.cuda.synchronize(dev)
+        reps = 10
+        a0.record(net.stream)
+        for _ in range(reps):
+            net.forward(x)
+        a1.record(net.stream)
+        torch.cuda.synchronize(dev)
+        ms_f = a0.elapsed_time(a1) / reps
+        a0.record(net.stream)
+        for _ in range(reps):
+            net.train_step(x, tg, tg, lr=0.0)
+        a1.record(net.stream)
+        torch.cuda.synchronize(dev)
+        ms_t = a0.elapsed_time(a1) / reps
+        bf = peaks["bf16_tflops"] if peaks else 1900.0
+        net_line = {"edge": E, "batch": B, "params": net.n_params, "kernel": "k_conv/k_wgrad (mma.sync bf16)",
+                    "forward_ms": ms_f, "train_step_ms": ms_t,
+                    "forward_tflops": B * f_fwd / (ms_f / 1e3) / 1e12,
+                    "train_tflops": B * f_train / (ms_t / 1e3) / 1e12, "peak_bf16_tflops": bf,
+                    "forward_frac": B * f_fwd / (ms_f / 1e3) / 1e12 / bf,
+                    "train_frac": B * f_train / (ms_t / 1e3) / 1e12 / bf,
+                    "peak_source": "measured" if peaks else "fallback"}
+        if args.warmstart:
+            net_line["experiment"] = WSm.experiment(device=dev, log=lambda m: print(m, file=sys.stderr, flush=True))
+        del net, x
+        torch.cuda.empty_cache()
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         import oracle
@@ -348,6 +401,7 @@ def main():
             "gpu_launches": launches,
             "lowprec_storage": lowprec,
             "batched_sweep": sweep,
+            "warm_start_net": net_line,
         }))
     if dist:
         dist.destroy_process_group()

@@ -310,17 +310,19 @@ void tlb_batch_destroy(void* batch);
  *     in_l = 2x2x2 average pool of e_{l-1};
  *   decoder: d_l = relu(conv3(relu(conv3([nearest 2x upsample of d_{l+1} |
  *     e_l])))), d_{levels-1} = e_{levels-1};
- *   output y = conv1(d_0), 16 channels: y0 = phi correction, y1 = psi
- *     correction, y2..y4 = displacement field, the rest unused.
+ *   output y = conv1(d_0), 16 channels: y0 = correction of the phase
+ *     indicator s = phi / (1 - psi) of the C1/C2 fluid, y2..y4 = displacement
+ *     field, the rest (y1 included) unused by the warm start.
  * conv3 is 3x3x3 with zero padding, conv1 is 1x1x1; every conv has a bias.
  * Parameters, in order, per conv: W[tap][ci][co] (tap = (kz*3 + ky)*3 + kx
  * for the input offset (kz-1, ky-1, kx-1)), then b[co]; FP32 on the host.
  * Activations are stored as bf16, the convolutions run on the tensor cores
  * with FP32 accumulation.
  * Features (normalised by the caller): kappa_1..3, Skalak G, R / E.
- * Training loss for targets dphi_t = phi_eq - phi0, dpsi_t = psi_eq - psi0
- * (FP32 [B][E^3]) and marker offsets off_t = X_eq - X0 (FP32 [B][max_nodes][3]):
- *   mean over samples and cells of (y0 - dphi_t)^2 + (y1 - dpsi_t)^2
+ * Training loss for targets t0, t1 of y0, y1 (FP32 [B][E^3]; for the warm
+ * start t0 = s_eq - s0 outside the capsule, 0 inside, and t1 = 0) and marker
+ * offsets off_t = X_eq - X0 (FP32 [B][max_nodes][3]):
+ *   mean over samples and cells of (y0 - t0)^2 + (y1 - t1)^2
  *   + lambda * mean over samples, markers and axes of
  *     (trilinear(y2..y4)(X0) - off_t)^2.
  * Input tensors x are bf16 [B][E^3][16] (device). */
@@ -350,15 +352,22 @@ tlb_status tlb_net_forward(void* net, const void* x_dev, int batch, float* y_dev
  * (Kingma and Ba 2015; beta1 0.9, beta2 0.999, eps 1e-8, step size lr) when
  * update != 0.  n_nodes: host [batch] marker counts (NULL: no marker term).
  * Synchronises the stream. */
-tlb_status tlb_net_train_step(void* net, const void* x_dev, const float* dphi_dev, const float* dpsi_dev,
+tlb_status tlb_net_train_step(void* net, const void* x_dev, const float* t0_dev, const float* t1_dev,
                               const float* X0_dev, const float* off_dev, const int* n_nodes, int batch,
                               double lambda, double lr, int update, double* loss_out);
 /* Warm start of a context that holds its plain initial state (tlb_init_fields
- * with NULL fields, no step taken; 3D, edge^3 cells, FP32 arithmetic):
- * phi = phi0 + y0 and psi = psi0 + y1 shifted uniformly so that their totals
- * equal the plain start's (the method conserves them), rho = 1, markers
- * X += trilinear(y2..y4)(X); then the profile, u = 0 and the equilibrium
- * populations of these fields, as tlb_init_fields does.  Synchronises. */
+ * with NULL fields, no step taken; 3D, edge^3 cells, FP32 arithmetic, one
+ * capsule):
+ *  - markers: D = trilinear(y2..y4)(X0); X = X0 + T + ((D - T).n) n with T
+ *    the mean of D and n the unit vertex pseudo-normals (no tangential
+ *    shear of the reference mesh);
+ *  - psi = I(X) + c_psi: the profile of the moved markers, as the plain
+ *    start takes psi = I(X0);
+ *  - phi = (1 - psi)(s0 + y0 + c_phi) with s0 = phi0 / (1 - psi0);
+ *  - rho = 1, u = 0; c_psi and c_phi are the uniform shifts that restore
+ *    the plain totals of psi and phi (the method conserves them);
+ * then the equilibrium populations of these fields, as tlb_init_fields.
+ * Synchronises. */
 tlb_status tlb_net_warm_start(void* net, void* ctx, const double* feats);
 /* Kernel launches of the last tlb_net_* call that computes. */
 long tlb_net_launch_count(void* net);

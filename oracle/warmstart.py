@@ -229,3 +229,43 @@ def mass_projection(phi, psi, phi_ref, psi_ref):
     the equilibrium has the plain start's totals."""
     n = phi.size
     return phi + (phi_ref.sum() - phi.sum()) / n, psi + (psi_ref.sum() - psi.sum()) / n
+
+
+def vertex_normals(X: np.ndarray, F: np.ndarray) -> np.ndarray:
+    """Unit angle-weighted pseudo-normals of a closed triangle mesh
+    (Baerentzen and Aanaes 2005): per vertex the sum over its faces of the
+    face's unit normal times the face angle at the vertex, normalised."""
+    N = np.zeros_like(X)
+    for f in F:
+        p = X[f]
+        fn = np.cross(p[1] - p[0], p[2] - p[0])
+        fn /= np.linalg.norm(fn)
+        for k in range(3):
+            a, b = p[(k + 1) % 3] - p[k], p[(k + 2) % 3] - p[k]
+            ang = np.arccos(np.clip(a @ b / (np.linalg.norm(a) * np.linalg.norm(b)), -1.0, 1.0))
+            N[f[k]] += ang * fn
+    return N / np.linalg.norm(N, axis=1, keepdims=True)
+
+
+def warm_start_markers(y, X0, normals):
+    """Markers of the warm start: D = trilinear(y2..4)(X0); X0 + T + ((D - T).n) n
+    with T the mean of D over the markers and n the unit vertex normals."""
+    D = trilinear(torch.as_tensor(np.asarray(y, dtype=np.float64))[2:5],
+                  torch.as_tensor(np.asarray(X0, dtype=np.float64))).numpy()
+    T = D.mean(axis=0)
+    r = np.einsum("ij,ij->i", D - T, normals)
+    return X0 + T + r[:, None] * normals
+
+
+def warm_start_fields(y0, phi0, psi0, I_new):
+    """Fields of the warm start from the output y0 (the change of the phase
+    indicator s = phi / (1 - psi)), the plain start and the profile I_new of
+    the moved markers: psi = I_new + c_psi and phi = (1 - psi)(s0 + y0 +
+    c_phi), the uniform shifts c_psi, c_phi restoring the plain totals of psi
+    and phi (the method conserves both)."""
+    w0 = 1.0 - psi0
+    s0 = np.where(w0 > 1e-6, phi0 / np.where(w0 > 1e-6, w0, 1.0), 0.0)
+    psi = I_new + (psi0.sum() - I_new.sum()) / psi0.size
+    w = 1.0 - psi
+    c = (phi0.sum() - (w * (s0 + y0)).sum()) / w.sum()
+    return (1.0 - psi) * (s0 + y0 + c), psi

@@ -26,6 +26,8 @@ struct ImplBase {
   // initial state from the rho, phi, psi moment arrays as they stand and the
   // current marker positions (profile, u = 0, equilibrium populations)
   virtual tlb_status init_from_moments(Ctx* c) = 0;
+  // profile I (with owners and distances) of the current marker positions
+  virtual tlb_status profile_now(Ctx* c) = 0;
 };
 
 // CUDA events bracketing the phases of a step when profiling.

@@ -270,16 +270,21 @@ struct Impl : ImplBase {
     return TLB_OK;
   }
 
-  tlb_status init_from_moments(Ctx* c) override {
+  tlb_status profile_now(Ctx* c) override {
+    if (c->nn == 0) return TLB_OK;
     cudaStream_t s = c->stream;
     IBArgs<Real> ia = ibargs(c);
-    if (c->nn > 0) {
-      tlb_status st = snapshot_box(c, ia, s, true);
-      if (st == TLB_OK) st = ibm_positions(c, ia, s);
-      if (st == TLB_OK) st = ibm_band(c, ia, s);
-      if (st != TLB_OK) return st;
-      c->box_stale = true;
-    }
+    tlb_status st = snapshot_box(c, ia, s, true);
+    if (st == TLB_OK) st = ibm_positions(c, ia, s);
+    if (st == TLB_OK) st = ibm_band(c, ia, s);
+    c->box_stale = true;  // the next step recomputes the box of these markers
+    return st;
+  }
+
+  tlb_status init_from_moments(Ctx* c) override {
+    cudaStream_t s = c->stream;
+    tlb_status pst = profile_now(c);
+    if (pst != TLB_OK) return pst;
     Real* uf = c->ptr<Real>(c->L.ftot);  // u = 0
     TLB_CUDA(cudaMemsetAsync(c->ptr<char>(c->L.ftot), 0, c->L.ftot.bytes, s));
     Geo G = geo(c);

@@ -427,50 +427,120 @@ __global__ void k_make_input(const float* __restrict__ phi, const float* __restr
   reinterpret_cast<uint4*>(x + v * 16)[1] = reinterpret_cast<uint4*>(c)[1];
 }
 
-// FP64 partial sums (fixed partition) of phi, psi, phi + y0, psi + y1.
-__global__ void k_ws_sums(const float* __restrict__ phi, const float* __restrict__ psi, const float* __restrict__ y,
-                          long long V, double* __restrict__ part) {
-  __shared__ double sm[4][256];
-  double a[4] = {0, 0, 0, 0};
-  for (long long v = (long long)blockIdx.x * 256 + threadIdx.x; v < V; v += (long long)gridDim.x * 256) {
-    a[0] += phi[v];
-    a[1] += psi[v];
-    a[2] += (double)phi[v] + y[v * YC];
-    a[3] += (double)psi[v] + y[v * YC + 1];
+// ---- warm start of a context (see tlb_net_warm_start)
+// Displacement of every marker: D_l = trilinear(y2..4)(X0_l) into D [nn][3],
+// with FP64 partial sums of D for the mean translation.
+__global__ void k_ws_disp(const double* __restrict__ X, int nn, const float* __restrict__ y, int E, float* __restrict__ D,
+                          double* __restrict__ part) {
+  __shared__ double sm[3][128];
+  const int l = blockIdx.x * 128 + threadIdx.x;
+  double a[3] = {0, 0, 0};
+  if (l < nn) {
+    const Tri T = tri_of((float)X[3 * l], (float)X[3 * l + 1], (float)X[3 * l + 2], E);
+    for (int q = 0; q < 3; ++q) {
+      float o = 0.f;
+      for (int d = 0; d < 8; ++d) o += T.w[d] * y[T.idx[d] * YC + 2 + q];
+      D[3 * l + q] = o;
+      a[q] = o;
+    }
   }
-  for (int q = 0; q < 4; ++q) sm[q][threadIdx.x] = a[q];
+  for (int q = 0; q < 3; ++q) sm[q][threadIdx.x] = a[q];
   __syncthreads();
-  for (int s = 128; s > 0; s >>= 1) {
+  for (int s = 64; s > 0; s >>= 1) {
     if (threadIdx.x < s)
-      for (int q = 0; q < 4; ++q) sm[q][threadIdx.x] += sm[q][threadIdx.x + s];
+      for (int q = 0; q < 3; ++q) sm[q][threadIdx.x] += sm[q][threadIdx.x + s];
     __syncthreads();
   }
   if (threadIdx.x == 0)
-    for (int q = 0; q < 4; ++q) part[q * gridDim.x + blockIdx.x] = sm[q][0];
+    for (int q = 0; q < 3; ++q) part[q * gridDim.x + blockIdx.x] = sm[q][0];
 }
 
-// Warm-start fields, mass-projected: rho = 1, phi = phi0 + y0 + sphi, psi =
-// psi0 + y1 + spsi with the uniform shifts that restore the plain totals.
-__global__ void k_ws_fields(float* __restrict__ rho, float* __restrict__ phi, float* __restrict__ psi,
-                            const float* __restrict__ y, long long V, const double* __restrict__ tot) {
-  const long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (v >= V) return;
-  const double sphi = (tot[0] - tot[2]) / (double)V, spsi = (tot[1] - tot[3]) / (double)V;
-  rho[v] = 1.f;
-  phi[v] = (float)((double)phi[v] + y[v * YC] + sphi);
-  psi[v] = (float)((double)psi[v] + y[v * YC + 1] + spsi);
-}
-
-// Markers moved by the displacement field: X += trilinear(y2..4)(X).
-__global__ void k_ws_nodes(double* __restrict__ X, int nn, const float* __restrict__ y, int E) {
+// X_l += T + ((D_l - T) . n_l) n_l: the mean translation T = tot / nn and the
+// normal part of the rest, n_l the unit vertex pseudo-normal.
+__global__ void k_ws_move(double* __restrict__ X, int nn, const float* __restrict__ D, const float* __restrict__ vn,
+                          const double* __restrict__ tot) {
   const int l = blockIdx.x * blockDim.x + threadIdx.x;
   if (l >= nn) return;
-  const Tri T = tri_of((float)X[3 * l], (float)X[3 * l + 1], (float)X[3 * l + 2], E);
-  for (int a = 0; a < 3; ++a) {
-    float o = 0.f;
-    for (int d = 0; d < 8; ++d) o += T.w[d] * y[T.idx[d] * YC + 2 + a];
-    X[3 * l + a] += (double)o;
+  double T[3], n[3], r = 0, len = 0;
+  for (int q = 0; q < 3; ++q) {
+    T[q] = tot[q] / nn;
+    n[q] = vn[3 * l + q];
+    len += n[q] * n[q];
   }
+  len = sqrt(len);
+  for (int q = 0; q < 3; ++q) {
+    n[q] = len > 0 ? n[q] / len : 0.0;
+    r += ((double)D[3 * l + q] - T[q]) * n[q];
+  }
+  for (int q = 0; q < 3; ++q) X[3 * l + q] += T[q] + r * n[q];
+}
+
+// Plain-start phase indicator of the C1/C2 fluid: s0 = phi0 / (1 - psi0)
+// (the plain start has phi0 = (1 - psi0)(2 s - 1)), 0 where 1 - psi0 < 1e-6.
+__device__ __forceinline__ double s0_of(float phi0, float psi0) {
+  const double w = 1.0 - (double)psi0;
+  return w > 1e-6 ? (double)phi0 / w : 0.0;
+}
+
+// FP64 partial sums of pass 1: phi0, psi0, I.
+__global__ void k_ws_sums1(const float* __restrict__ phi, const float* __restrict__ psi, const float* __restrict__ I,
+                           long long V, double* __restrict__ part) {
+  __shared__ double sm[3][256];
+  double a[3] = {0, 0, 0};
+  for (long long v = (long long)blockIdx.x * 256 + threadIdx.x; v < V; v += (long long)gridDim.x * 256) {
+    a[0] += phi[v];
+    a[1] += psi[v];
+    a[2] += I[v];
+  }
+  for (int q = 0; q < 3; ++q) sm[q][threadIdx.x] = a[q];
+  __syncthreads();
+  for (int s = 128; s > 0; s >>= 1) {
+    if (threadIdx.x < s)
+      for (int q = 0; q < 3; ++q) sm[q][threadIdx.x] += sm[q][threadIdx.x + s];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0)
+    for (int q = 0; q < 3; ++q) part[q * gridDim.x + blockIdx.x] = sm[q][0];
+}
+
+// Pass 2, with psi = I + cpsi (cpsi = (sum psi0 - sum I) / V from tot[0..2]):
+// sums of (1 - psi) and (1 - psi)(s0 + y0).
+__global__ void k_ws_sums2(const float* __restrict__ phi, const float* __restrict__ psi, const float* __restrict__ I,
+                           const float* __restrict__ y, long long V, const double* __restrict__ tot,
+                           double* __restrict__ part) {
+  __shared__ double sm[2][256];
+  const double cpsi = (tot[1] - tot[2]) / (double)V;
+  double a[2] = {0, 0};
+  for (long long v = (long long)blockIdx.x * 256 + threadIdx.x; v < V; v += (long long)gridDim.x * 256) {
+    const double w = 1.0 - ((double)I[v] + cpsi);
+    a[0] += w;
+    a[1] += w * (s0_of(phi[v], psi[v]) + y[v * YC]);
+  }
+  for (int q = 0; q < 2; ++q) sm[q][threadIdx.x] = a[q];
+  __syncthreads();
+  for (int s = 128; s > 0; s >>= 1) {
+    if (threadIdx.x < s)
+      for (int q = 0; q < 2; ++q) sm[q][threadIdx.x] += sm[q][threadIdx.x + s];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0)
+    for (int q = 0; q < 2; ++q) part[q * gridDim.x + blockIdx.x] = sm[q][0];
+}
+
+// Fields of the warm start: rho = 1, psi = I + cpsi, phi = (1 - psi)(s0 + y0
+// + cphi) with cphi = (sum phi0 - tot2[1]) / tot2[0] restoring the phi total.
+__global__ void k_ws_fields(float* __restrict__ rho, float* __restrict__ phi, float* __restrict__ psi,
+                            const float* __restrict__ I, const float* __restrict__ y, long long V,
+                            const double* __restrict__ tot, const double* __restrict__ tot2) {
+  const long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (v >= V) return;
+  const double cpsi = (tot[1] - tot[2]) / (double)V;
+  const double cphi = (tot[0] - tot2[1]) / tot2[0];
+  const double ps = (double)I[v] + cpsi;
+  const double s = s0_of(phi[v], psi[v]) + y[v * YC] + cphi;
+  rho[v] = 1.f;
+  phi[v] = (float)((1.0 - ps) * s);
+  psi[v] = (float)ps;
 }
 
 __global__ void k_sum_parts(const double* __restrict__ part, int nb, int nq, double* __restrict__ out) {
@@ -1010,29 +1080,50 @@ tlb_status tlb_net_warm_start(void* net, void* ctx, const double* feats) {
   tlb_status s = check_ctx(n, c);
   if (s != TLB_OK) return s;
   if (c->t != 0) { set_error("net_warm_start: the context must hold its initial state (no step taken)"); return TLB_ERR_STATE; }
-  if (c->stream != n->stream) TLB_CUDA(cudaStreamSynchronize(c->stream));
+  if (c->ncap != 1) { set_error("net_warm_start: the context must hold exactly one capsule"); return TLB_ERR_ARG; }
+  // scratch: marker displacements in the output-gradient buffer, 3 sums per
+  // 128-marker block in the loss partials
+  if (3ll * c->nn > n->vox(0, n->d.max_batch) * YC || 3ll * nb(c->nn, 128) > 1024) {
+    set_error("net_warm_start: too many markers for this net's scratch");
+    return TLB_ERR_ARG;
+  }
+  TLB_CUDA(cudaStreamSynchronize(c->stream));
   n->launches = 0;
   cudaStream_t st = n->stream;
   bf16* x = n->at<bf16>(n->o_act) + n->x.act;
   float* phi = c->ptr<float>(c->L.phi);
   float* psi = c->ptr<float>(c->L.psi);
+  float* I = c->ptr<float>(c->L.I);
   k_make_input<<<nb(c->N, 256), 256, 0, st>>>(phi, psi, c->N, (float)feats[0], (float)feats[1], (float)feats[2],
                                               (float)feats[3], (float)feats[4], x);
   NET_LAUNCHED(n, "k_make_input");
   if ((s = forward(n, 1)) != TLB_OK) return s;
   const float* y = n->at<float>(n->o_y);
   double* part = n->at<double>(n->o_lpart);
-  double* tot = n->at<double>(n->o_misc) + 8;
-  k_ws_sums<<<256, 256, 0, st>>>(phi, psi, y, c->N, part);
-  NET_LAUNCHED(n, "k_ws_sums");
-  k_sum_parts<<<1, 256, 0, st>>>(part, 256, 4, tot);
+  double* tot = n->at<double>(n->o_misc) + 8;  // [0..2] pass 1, [4..5] pass 2, [8..10] translation
+  // markers: mean translation plus the normal part of the predicted displacement
+  float* D = n->at<float>(n->o_gy);
+  const unsigned bn = nb(c->nn, 128);
+  k_ws_disp<<<bn, 128, 0, st>>>(c->ptr<double>(c->L.X), c->nn, y, n->d.edge, D, part);
+  NET_LAUNCHED(n, "k_ws_disp");
+  k_sum_parts<<<1, 256, 0, st>>>(part, (int)bn, 3, tot + 8);
   NET_LAUNCHED(n, "k_sum_parts");
-  k_ws_fields<<<nb(c->N, 256), 256, 0, st>>>(c->ptr<float>(c->L.rho), phi, psi, y, c->N, tot);
+  k_ws_move<<<bn, 128, 0, st>>>(c->ptr<double>(c->L.X), c->nn, D, c->ptr<float>(c->L.vn), tot + 8);
+  NET_LAUNCHED(n, "k_ws_move");
+  TLB_CUDA(cudaStreamSynchronize(st));
+  // psi follows the moved membrane: its profile I, shifted to the plain total
+  if ((s = c->impl->profile_now(c)) != TLB_OK) return s;
+  TLB_CUDA(cudaStreamSynchronize(c->stream));
+  k_ws_sums1<<<256, 256, 0, st>>>(phi, psi, I, c->N, part);
+  NET_LAUNCHED(n, "k_ws_sums1");
+  k_sum_parts<<<1, 256, 0, st>>>(part, 256, 3, tot);
+  NET_LAUNCHED(n, "k_sum_parts");
+  k_ws_sums2<<<256, 256, 0, st>>>(phi, psi, I, y, c->N, tot, part);
+  NET_LAUNCHED(n, "k_ws_sums2");
+  k_sum_parts<<<1, 256, 0, st>>>(part, 256, 2, tot + 4);
+  NET_LAUNCHED(n, "k_sum_parts");
+  k_ws_fields<<<nb(c->N, 256), 256, 0, st>>>(c->ptr<float>(c->L.rho), phi, psi, I, y, c->N, tot, tot + 4);
   NET_LAUNCHED(n, "k_ws_fields");
-  if (c->nn > 0) {
-    k_ws_nodes<<<nb(c->nn, 128), 128, 0, st>>>(c->ptr<double>(c->L.X), c->nn, y, n->d.edge);
-    NET_LAUNCHED(n, "k_ws_nodes");
-  }
   TLB_CUDA(cudaStreamSynchronize(st));
   return c->impl->init_from_moments(c);
 }

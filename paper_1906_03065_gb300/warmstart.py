@@ -26,6 +26,45 @@ def features(wl) -> np.ndarray:
                      (m.G - 0.026) / 0.024, (R / p.nx - 0.2) / 0.05])
 
 
+def indicator(phi, psi):
+    """Phase indicator of the C1/C2 fluid, s = phi / (1 - psi) (C1 - C2 over
+    C1 + C2 when rho = 1); 0 where 1 - psi < 1e-6."""
+    w = 1.0 - psi
+    return np.where(w > 1e-6, phi / np.where(w > 1e-6, w, 1.0), 0.0)
+
+
+def indicator_target(phi0, psi0, phi, psi, cut: float = 0.05):
+    """Training target of output y0: s(equilibrium) - s(plain start), where
+    the equilibrium has at least ``cut`` of non-C3 fluid (0 inside the
+    capsule, where s is undefined), clipped to [-1.5, 1.5]."""
+    s0 = indicator(phi0, psi0)
+    s = np.clip(indicator(phi, psi), -1.5, 1.5)
+    return np.where(1.0 - psi >= cut, s - s0, 0.0).astype(np.float32)
+
+
+def init_params(net: WarmStartNet, seed: int) -> np.ndarray:
+    """He-normal weights (standard deviation sqrt(2 / fan_in), fan_in = taps
+    * input channels) from numpy's PCG64 with ``seed``, zero biases and a zero
+    output layer, so that the untrained network returns the plain start.
+    Layer shapes follow the network of tlb.h."""
+    d = net.desc
+    c = [d.base_channels << l for l in range(d.levels)]
+    shapes = [(27, 16, c[0]), (27, c[0], c[0])]
+    for l in range(1, d.levels):
+        shapes += [(27, c[l - 1], c[l]), (27, c[l], c[l])]
+    for l in range(d.levels - 2, -1, -1):
+        shapes += [(27, c[l + 1] + c[l], c[l]), (27, c[l], c[l])]
+    shapes.append((1, c[0], 16))
+    rng = np.random.default_rng(seed)
+    out = []
+    for k, (t, ci, co) in enumerate(shapes):
+        w = np.zeros(t * ci * co) if k == len(shapes) - 1 else rng.normal(0.0, np.sqrt(2.0 / (t * ci)), t * ci * co)
+        out += [w, np.zeros(co)]
+    theta = np.concatenate(out).astype(np.float32)
+    assert theta.size == net.n_params
+    return theta
+
+
 def instances(n: int, seed: int, edge: int = 48, storage: str = "f32"):
     """``n`` sweep instances of one lattice edge (workloads.sweep_3d with a
     single edge, so every sample has the network's lattice)."""
@@ -34,10 +73,11 @@ def instances(n: int, seed: int, edge: int = 48, storage: str = "f32"):
 
 def dataset(net: WarmStartNet, wls, max_steps: int, check_every: int = 200, tol: float = 1e-7):
     """Training tensors (on the net's device) of the instances ``wls``: the
-    inputs of their plain starts, and the equilibrium minus the plain start
-    (fields and marker offsets) after relaxing them together as a batch to
-    the residual ``tol`` (or ``max_steps``).  Returns a dict with x, dphi,
-    dpsi, X0, off, n_nodes, steps, residual."""
+    inputs of their plain starts and the targets of the outputs after relaxing
+    them together as a batch to the residual ``tol`` (or ``max_steps``): the
+    change of the phase indicator (``indicator_target``) for y0, zero for y1,
+    and the marker offsets.  Returns a dict with x, dphi (y0 targets), dpsi
+    (y1 targets), X0, off, n_nodes, steps, residual."""
     import torch
     n, V = len(wls), net.edge ** 3
     b = Batch(wls, device=net.device).init()
@@ -59,8 +99,8 @@ def dataset(net: WarmStartNet, wls, max_steps: int, check_every: int = 200, tol:
     nn = []
     for i in range(n):
         s = b[i]
-        dphi[i] = s.field("phi") - phi0[i]
-        dpsi[i] = s.field("psi") - psi0[i]
+        dphi[i] = indicator_target(phi0[i], psi0[i], s.field("phi"), s.field("psi"))
+        dpsi[i] = 0.0  # psi is not predicted: the warm start takes the profile of the moved markers
         Xe = s.nodes(0)
         k = min(len(Xe), mn)
         Xa[i, :k] = X0[i][:k]
@@ -99,21 +139,110 @@ def train(net: WarmStartNet, data, epochs: int, batch: int = 4, lr: float = 1e-3
     return losses
 
 
-def compare(net: WarmStartNet, wls, max_steps: int, check_every: int = 200, tol: float = 1e-7):
-    """Relaxation of every instance from its plain start and from the learned
-    start, side by side in one batch (instances 0..n-1 plain, n..2n-1
-    learned).  Returns steps and final residual of each, and the wall time of
-    the warm-start calls (s)."""
+def histories(b, max_steps: int, check_every: int, stop_tol: float):
+    """Residual of every instance of batch ``b`` after each chunk of
+    ``check_every`` steps (no instance retires) until every instance has
+    reached ``stop_tol`` once or ``max_steps`` steps; returns [checks][n]."""
+    out = []
+    reached = np.zeros(len(b), dtype=bool)
+    done = 0
+    while done < max_steps and not reached.all():
+        _, r = b.run(check_every, check_every, 0.0)
+        out.append(r.copy())
+        reached |= r <= stop_tol
+        done += check_every
+    return np.array(out)
+
+
+def first_crossing(hist, tol: float, check_every: int):
+    """Steps at which each instance's residual first drops to ``tol`` (NaN if
+    it never does)."""
+    out = np.full(hist.shape[1], np.nan)
+    for i in range(hist.shape[1]):
+        k = np.nonzero(hist[:, i] <= tol)[0]
+        if k.size:
+            out[i] = (k[0] + 1) * check_every
+    return out
+
+
+def compare(net: WarmStartNet, wls, wls_learned=None, max_steps: int = 8000, check_every: int = 250,
+            tols=(1e-4, 5e-5)):
+    """Relaxation of the instances from their plain start and from the
+    learned start (instances ``wls_learned``, default the same), each set as
+    one batch.  Returns the residual histories, the first-crossing steps of
+    every tolerance, the wall time of each relaxation and of the warm-start
+    calls."""
     import time
     import torch
-    n = len(wls)
-    b = Batch(list(wls) + list(wls), device=net.device).init()
-    torch.cuda.synchronize(net.device)
+    out = {}
+    for name, ws_, learned in (("plain", wls, False), ("learned", wls_learned or wls, True)):
+        b = Batch(ws_, device=net.device).init()
+        torch.cuda.synchronize(net.device)
+        t0 = time.perf_counter()
+        if learned:
+            for i, wl in enumerate(ws_):
+                net.warm_start(b[i], features(wl))
+        torch.cuda.synchronize(net.device)
+        t_ws = time.perf_counter() - t0
+        h = histories(b, max_steps, check_every, min(tols))
+        torch.cuda.synchronize(net.device)
+        out[name] = {"history": h, "wall_s": time.perf_counter() - t0, "warm_start_s": t_ws,
+                     "first": {t: first_crossing(h, t, check_every) for t in tols}}
+        del b
+        torch.cuda.empty_cache()
+    for t in tols:
+        p, l = out["plain"]["first"][t], out["learned"]["first"][t]
+        ok = np.isfinite(p) & np.isfinite(l)
+        out[f"ratio_{t:g}"] = {"both": int(ok.sum()), "plain_median": float(np.nanmedian(p)) if np.isfinite(p).any() else None,
+                               "learned_median": float(np.nanmedian(l)) if np.isfinite(l).any() else None,
+                               "median": float(np.median(p[ok] / l[ok])) if ok.any() else None,
+                               "geomean": float(np.exp(np.mean(np.log(p[ok] / l[ok])))) if ok.any() else None}
+    return out
+
+
+def experiment(edge: int = 48, n_train: int = 128, n_test: int = 32, relax_steps: int = 15000,
+               target_tol: float = 2e-5, max_steps: int = 8000, check_every: int = 250, tols=(1e-4, 5e-5),
+               epochs: int = 150, batch: int = 8, lr: float = 1e-3, lam: float = 1.0, seed: int = 0,
+               device="cuda:0", log=print):
+    """Time to equilibrium from the plain and from the learned start.
+
+    Training instances: sweep seeds 1000.., relaxed in FP32 to the residual
+    ``target_tol`` (or ``relax_steps``); held-out instances: seeds 5000...
+    The held-out instances relax from the plain start in FP32 and from the
+    learned start in FP16 storage; reported are the first steps at which the
+    residual drops to each tolerance, and the wall times.  Returns a dict."""
+    import time
+    import torch
+    out = {"edge": edge, "n_train": n_train, "n_test": n_test, "target_tol": target_tol}
+    net = WarmStartNet(edge, 16, 4, max_batch=batch, max_nodes=642, device=device)
+    net.set_params(init_params(net, seed))
     t0 = time.perf_counter()
-    for i, wl in enumerate(wls):
-        net.warm_start(b[n + i], features(wl))
-    torch.cuda.synchronize(net.device)
-    t_ws = time.perf_counter() - t0
-    steps, res = b.run(max_steps, check_every, tol)
-    return {"plain_steps": steps[:n], "learned_steps": steps[n:], "plain_residual": res[:n],
-            "learned_residual": res[n:], "warm_start_s": t_ws, "batch": b}
+    parts = []
+    for k in range(0, n_train, 64):
+        wls = [instances(1, seed=1000 + k + j, edge=edge)[0] for j in range(min(64, n_train - k))]
+        parts.append(dataset(net, wls, relax_steps, check_every=1000, tol=target_tol))
+        log(f"relaxed {k + len(wls)} training instances, median steps {np.median(parts[-1]['steps']):.0f}")
+    data = {key: (torch.cat([p[key] for p in parts]) if torch.is_tensor(parts[0][key])
+                  else np.concatenate([p[key] for p in parts])) for key in parts[0]}
+    out["data_s"] = time.perf_counter() - t0
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    losses = train(net, data, epochs, batch=batch, lr=lr, lam=lam, seed=seed)
+    torch.cuda.synchronize()
+    out["train_s"] = time.perf_counter() - t0
+    out["train_steps"] = len(losses)
+    out["loss_first"], out["loss_last"] = float(np.mean(losses[:5])), float(np.mean(losses[-20:]))
+    log(f"trained {len(losses)} steps in {out['train_s']:.1f} s, loss {out['loss_first']:.3e} -> {out['loss_last']:.3e}")
+    del data, parts
+    torch.cuda.empty_cache()
+    test = [instances(1, seed=5000 + j, edge=edge)[0] for j in range(n_test)]
+    test16 = [instances(1, seed=5000 + j, edge=edge, storage="f16")[0] for j in range(n_test)]
+    r = compare(net, test, test16, max_steps, check_every, tols)
+    for k in ("plain", "learned"):
+        out[k] = {"wall_s": r[k]["wall_s"], "warm_start_s": r[k]["warm_start_s"],
+                  "first": {f"{t:g}": [None if not np.isfinite(v) else int(v) for v in r[k]["first"][t]] for t in tols}}
+    for t in tols:
+        out[f"ratio_{t:g}"] = r[f"ratio_{t:g}"]
+        log(f"tol {t:g}: {r[f'ratio_{t:g}']}")
+    out["params"] = net.params()
+    return out

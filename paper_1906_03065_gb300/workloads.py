@@ -216,7 +216,9 @@ def sweep_3d(n_inst: int = 64, seed: int = 1, storage: str = "f16",
     kappa_2, kappa_3 ~ U[0.005, 0.03] each; Skalak G ~ U[0.002, 0.05].  Every
     instance has the layout of ``capsule_3d`` (walls at the two ends of z, a
     flat C1/C2 interface at mid-height and the capsule centred on it) with
-    C = 1, kb = 0.005, alpha = 2, kappa_c = 0.01, dc = 16, tau = Gamma = 1."""
+    C = 1, kb = 0.005, alpha = 2, kappa_c = 0.01, dc = 16, tau = 1 and
+    Gamma_phi = Gamma_psi = 0.5 (mobility 0.25): with Gamma = 1 and alpha = 2
+    the order-parameter update diverges for kappa_i above about 0.025."""
     rng = np.random.default_rng(seed)
     out = []
     for i in range(n_inst):
@@ -226,8 +228,8 @@ def sweep_3d(n_inst: int = 64, seed: int = 1, storage: str = "f16",
         k1, k2, k3 = (float(v) for v in rng.uniform(0.005, 0.03, 3))
         G = float(rng.uniform(0.002, 0.05))
         c = n / 2.0
-        p = Params(dim=3, nx=n, ny=n, nz=n, wall_last=1, storage=storage, alpha=2.0,
-                   kappa1=k1, kappa2=k2, kappa3=k3, kappa_c=0.01, dc=16.0, interface_pos=c)
+        p = Params(dim=3, nx=n, ny=n, nz=n, wall_last=1, storage=storage, alpha=2.0, gamma_phi=0.5,
+                   gamma_psi=0.5, kappa1=k1, kappa2=k2, kappa3=k3, kappa_c=0.01, dc=16.0, interface_pos=c)
         m = icosphere(level, R, (c, c, c))
         m.G, m.C, m.kb = G, 1.0, 0.005
         out.append(Workload(f"sweep{i}_{n}^3_R{R:.1f}_ico{level}", p, [m], steps=20000))

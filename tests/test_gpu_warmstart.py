@@ -130,11 +130,12 @@ def _cube(edge=32, R=6.0, level=2, seed=0):
 
 
 def test_warm_start_of_a_context():
-    """Fields: phi0 + y0 and psi0 + y1 shifted to the plain totals; markers
-    X0 + trilinear(y2..4)(X0); the context then holds the equilibrium
-    populations of these fields."""
+    """Markers move by the mean predicted displacement plus its normal part;
+    psi becomes the profile of the moved markers and phi = (1 - psi)(s0 + y0),
+    both shifted to the plain totals; the context then holds the equilibrium
+    populations of these fields (compared with the FP64 reference of the
+    same composition, oracle.warmstart)."""
     import oracle
-    import torch
     from paper_1906_03065_gb300 import Simulation, warmstart as WS
     wl = _cube(32)
     th = _theta(5, lv=3)
@@ -146,19 +147,23 @@ def test_warm_start_of_a_context():
     net.warm_start(s, feats)
     o = oracle.Oracle(wl)
     x = ws.make_input(o.field("phi"), o.field("psi"), feats, 32)[None]
-    yo, offs = ws.forward(th, x, [X0], c0=C0, levels=3)
-    yo = yo[0].numpy().reshape(16, -1)
-    p_ref, s_ref = ws.mass_projection(phi0 + yo[0], psi0 + yo[1], phi0, psi0)
-    scale = np.abs(yo[:2]).max()
-    assert np.abs(s.field("phi") - p_ref).max() < 2e-2 * scale + 1e-5
-    assert np.abs(s.field("psi") - s_ref).max() < 2e-2 * scale + 1e-5
-    assert s.field("phi").sum() == pytest.approx(phi0.sum(), abs=1e-3)
-    assert s.field("psi").sum() == pytest.approx(psi0.sum(), abs=1e-3)
-    Xr = X0 + offs[0].numpy()
-    assert np.abs(s.nodes(0) - Xr).max() < 2e-2 * np.abs(offs[0].numpy()).max() + 1e-5
+    yo, _ = ws.forward(th, x, c0=C0, levels=3)
+    yo = yo[0].numpy()
+    Xr = ws.warm_start_markers(yo, X0, ws.vertex_normals(X0, wl.membranes[0].elems))
+    D = np.abs(Xr - X0).max()
+    assert D > 0.05  # the test moves the markers
+    assert np.abs(s.nodes(0) - Xr).max() < 5e-3 * D + 1e-5
+    I_new, _, _ = o.iprofile(Xr)
+    p_ref, s_ref = ws.warm_start_fields(yo[0].reshape(-1), phi0, psi0, I_new)
+    # the bf16 forward pass agrees with the FP64 reference to 2% of max |y|
+    # (test_forward_matches_oracle); phi carries that error times |s0 + y0|
+    tol = 2e-3 + 2e-2 * np.abs(yo[0]).max()
+    assert np.abs(s.field("psi") - s_ref).max() < tol
+    assert np.abs(s.field("phi") - p_ref).max() < tol
+    assert s.field("phi").sum() == pytest.approx(phi0.sum(), abs=1e-2)
+    assert s.field("psi").sum() == pytest.approx(psi0.sum(), abs=1e-2)
     s.step(5)  # the relaxation runs from it
     assert np.isfinite(s.field("C3")).all()
-    torch.cuda.synchronize()
 
 
 def test_training_gains_over_the_plain_start():
@@ -172,5 +177,6 @@ def test_training_gains_over_the_plain_start():
     data = WS.dataset(net, wls[:10], max_steps=1500, check_every=500, tol=0.0)
     losses = WS.train(net, data, epochs=40, batch=4, lr=2e-3)
     assert np.mean(losses[-5:]) < 0.5 * np.mean(losses[:3])
-    r = WS.compare(net, wls[10:], max_steps=300, check_every=300, tol=0.0)
-    assert np.mean(r["learned_residual"]) < np.mean(r["plain_residual"]), r
+    r = WS.compare(net, wls[10:], max_steps=300, check_every=300, tols=(1e-12,))
+    plain, learned = r["plain"]["history"][0], r["learned"]["history"][0]
+    assert np.mean(learned) < np.mean(plain), (plain, learned)

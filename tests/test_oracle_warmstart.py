@@ -109,3 +109,26 @@ def test_untrained_output_layer_returns_plain_start():
     x, X0 = _sample(rng)
     y, offs = ws.forward(theta, x, X0, c0=C0, levels=LV)
     assert float(torch.abs(y).max()) == 0.0 and all(float(torch.abs(o).max()) == 0.0 for o in offs)
+
+
+def test_warm_start_composition_pins():
+    """The reference warm start conserves the phi and psi totals, returns the
+    plain start for a zero output, and moves markers by a uniform
+    displacement field exactly (translation only)."""
+    from paper_1906_03065_gb300 import workloads as W
+    rng = np.random.default_rng(9)
+    m = W.icosphere(2, 5.0, (8.1, 7.9, 8.2))
+    n = ws.vertex_normals(m.X, m.elems)
+    radial = (m.X - m.X.mean(0)) / np.linalg.norm(m.X - m.X.mean(0), axis=1, keepdims=True)
+    assert np.abs(n - radial).max() < 0.05  # sphere: close to radial
+    y = np.zeros((16, E * 2, E * 2, E * 2))
+    assert np.abs(ws.warm_start_markers(y, m.X, n) - m.X).max() == 0.0
+    y[2], y[3], y[4] = 0.3, -0.2, 0.7
+    assert np.abs(ws.warm_start_markers(y, m.X, n) - (m.X + [0.3, -0.2, 0.7])).max() < 1e-12
+    psi0 = rng.uniform(0, 1, 300)
+    phi0 = (1 - psi0) * rng.uniform(-1, 1, 300)
+    phi, psi = ws.warm_start_fields(np.zeros(300), phi0, psi0, psi0)
+    assert np.allclose(phi, phi0, atol=1e-12) and np.allclose(psi, psi0, atol=1e-12)
+    I_new = np.clip(psi0 + rng.normal(0, 0.05, 300), 0, 1)
+    phi, psi = ws.warm_start_fields(rng.normal(0, 0.1, 300), phi0, psi0, I_new)
+    assert phi.sum() == pytest.approx(phi0.sum(), abs=1e-10) and psi.sum() == pytest.approx(psi0.sum(), abs=1e-10)
