@@ -38,22 +38,26 @@ def _peaks():
         return None
 
 
-def _src_hash():
+# sources each profiled kernel is compiled from
+KERNEL_SOURCES = {"k_collide": ("tlb_lb.cuh", "tlb_common.cuh")}
+
+
+def _src_hash(kernel: str = "k_collide"):
     h = hashlib.sha256()
     d = os.path.join(ROOT, "paper_1906_03065_gb300", "csrc")
-    for f in sorted(os.listdir(d)):
+    for f in KERNEL_SOURCES[kernel]:
         h.update(open(os.path.join(d, f), "rb").read())
     return h.hexdigest()[:16]
 
 
 def _traffic(kernel: str):
     """DRAM bytes per launch from a committed ncu summary, if it was taken
-    on the current kernel sources."""
+    on the current sources of the kernel."""
     p = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         t = json.load(open(p))
         e = t[kernel]
-        if e.get("source_sha") != _src_hash():
+        if e.get("source_sha") != _src_hash(kernel):
             return None
         return e["dram_bytes_per_launch"]
     except Exception:
