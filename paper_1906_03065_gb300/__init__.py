@@ -90,6 +90,8 @@ def lib():
         L.tlb_autotune.restype = C.c_int
         L.tlb_last_launch_count.argtypes = [vp]
         L.tlb_last_launch_count.restype = C.c_long
+        L.tlb_set_tile.argtypes = [vp, C.c_int, C.c_int]
+        L.tlb_set_tile.restype = C.c_int
         L.tlb_residual.argtypes = [vp, dp]
         L.tlb_residual.restype = C.c_int
         ip, lp = C.POINTER(C.c_int), C.POINTER(C.c_long)
@@ -247,6 +249,9 @@ class Simulation:
         v, z = C.c_int(0), C.c_int(0)
         _check(lib().tlb_autotune(self.h, C.byref(v), C.byref(z)))
         return v.value, z.value
+
+    def set_tile(self, variant: int, z_chunk: int):
+        _check(lib().tlb_set_tile(self.h, int(variant), int(z_chunk)))
 
     def launches(self) -> int:
         return lib().tlb_last_launch_count(self.h)

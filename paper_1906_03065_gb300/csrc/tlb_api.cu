@@ -605,6 +605,18 @@ tlb_status tlb_autotune(void* ctx, int* tile_variant, int* z_chunk) {
   return c->impl->autotune(c, tile_variant, z_chunk);
 }
 
+tlb_status tlb_set_tile(void* ctx, int tile_variant, int z_chunk) {
+  Ctx* c = (Ctx*)ctx;
+  if (!c) { set_error("ctx is NULL"); return TLB_ERR_ARG; }
+  if (tile_variant < 0 || tile_variant > 5 || z_chunk < 1 || z_chunk > c->nz) {
+    set_error("set_tile: tile_variant must be 0..5 and z_chunk 1..nz");
+    return TLB_ERR_ARG;
+  }
+  c->tile_variant = tile_variant;
+  c->tiles_zc = z_chunk;
+  return TLB_OK;
+}
+
 long tlb_last_launch_count(void* ctx) {
   Ctx* c = (Ctx*)ctx;
   return c ? c->launches : 0;

@@ -14,8 +14,9 @@ struct Impl : ImplBase {
   using Real = typename Prec<MODE>::Real;
   using Store = typename Prec<MODE>::Store;
   using Rest = typename Prec<MODE>::Rest;
-  // tile shapes of the collide plane sweep (variant index = c->tile_variant)
-  static constexpr int NVAR = 3;
+  // tile shapes of the collide plane sweep (variant index = c->tile_variant;
+  // variants 3..5 are 0..2 with the next population set prefetched)
+  static constexpr int NVAR = 6;
   static constexpr int TXS[NVAR] = {32, 32, 64};
   static constexpr int TYS3[NVAR] = {4, 8, 4};
   static constexpr int TYS2[NVAR] = {1, 1, 1};
@@ -321,10 +322,10 @@ struct Impl : ImplBase {
     return TLB_OK;
   }
 
-  template <int TXv, int TYv>
+  template <int TXv, int TYv, bool PF>
   static tlb_status collide_tile(Ctx* c, LBArgs<MODE>& la, cudaStream_t s) {
     dim3 grid(blocks(c->nx, TXv), blocks(c->ny, TYv), blocks(c->nz, c->tiles_zc));
-    k_collide<L, MODE, TXv, TYv><<<grid, TXv * TYv, 0, s>>>(la);
+    k_collide<L, MODE, TXv, TYv, PF><<<grid, TXv * TYv, 0, s>>>(la);
     TLB_LAUNCHED(c, "k_collide");
     return TLB_OK;
   }
@@ -332,15 +333,21 @@ struct Impl : ImplBase {
   static tlb_status collide(Ctx* c, LBArgs<MODE>& la, cudaStream_t s) {
     if constexpr (L::DIM == 3) {
       switch (c->tile_variant) {
-        case 1: return collide_tile<32, 8>(c, la, s);
-        case 2: return collide_tile<64, 4>(c, la, s);
-        default: return collide_tile<32, 4>(c, la, s);
+        case 1: return collide_tile<32, 8, false>(c, la, s);
+        case 2: return collide_tile<64, 4, false>(c, la, s);
+        case 3: return collide_tile<32, 4, true>(c, la, s);
+        case 4: return collide_tile<32, 8, true>(c, la, s);
+        case 5: return collide_tile<64, 4, true>(c, la, s);
+        default: return collide_tile<32, 4, false>(c, la, s);
       }
     } else {
       switch (c->tile_variant) {
-        case 1: return collide_tile<64, 1>(c, la, s);
-        case 2: return collide_tile<128, 1>(c, la, s);
-        default: return collide_tile<32, 1>(c, la, s);
+        case 1: return collide_tile<64, 1, false>(c, la, s);
+        case 2: return collide_tile<128, 1, false>(c, la, s);
+        case 3: return collide_tile<32, 1, true>(c, la, s);
+        case 4: return collide_tile<64, 1, true>(c, la, s);
+        case 5: return collide_tile<128, 1, true>(c, la, s);
+        default: return collide_tile<32, 1, false>(c, la, s);
       }
     }
   }

@@ -69,7 +69,7 @@ __device__ __forceinline__ Real eq_poly(Real cu, Real uu) {
 // the chemical potentials (halo 1), so each cell's radius-2 dependency (mu
 // needs the Laplacian of the moments, the force needs the gradient of mu) is
 // served on chip.
-template <class L, int MODE, int TX, int TY>
+template <class L, int MODE, int TX, int TY, bool PF>
 __device__ __forceinline__ void collide_body(const LBArgs<MODE>& a, const Blk& blk) {
   using Real = typename Prec<MODE>::Real;
   using Store = typename Prec<MODE>::Store;
@@ -198,12 +198,28 @@ __device__ __forceinline__ void collide_body(const LBArgs<MODE>& a, const Blk& b
       if (ib) F[d] += a.fib[d * G.P32 + n];
     }
     if (!D3) F[1] = 0;
+    // pull of the order-parameter set `set` (0: g, 1: h) into v
+    auto load_set = [&](int set, Real* v) {
+#pragma unroll
+      for (int i = 0; i < Q; ++i) {
+        if (i == 0) {
+          v[0] = to_real(__ldg(a.rest_src + (set == 0 ? 0 : G.P32) + n));
+        } else {
+          const int o = set == 0 ? nb.off(i, plane_g<L>(i), plane_g<L>(L::opp(i)), G.P32)
+                                 : nb.off(i, plane_h<L>(i), plane_h<L>(L::opp(i)), G.P32);
+          v[i] = to_real(__ldg(a.lo_src + o));
+        }
+      }
+    };
     // f: pull, first moment, BGK + exact difference method (eq. LBE) for f_i - w_i
     Real fv[Q];
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
       fv[i] = to_real(__ldg(a.lo_src + nb.off(i, plane_f<L>(i), plane_f<L>(L::opp(i)), G.P32)));
     }
+    // with PF the next set's loads are in flight while this one is computed
+    Real nextv[Q];
+    if constexpr (PF) load_set(0, nextv);
     Real drho = 0, jx = 0, jy = 0, jz = 0;
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
@@ -245,15 +261,12 @@ __device__ __forceinline__ void collide_body(const LBArgs<MODE>& a, const Blk& b
       const Real Gm = set == 0 ? a.gphi * mup : a.gpsi * mus;
       const Real ord = set == 0 ? phi : psi;
       Real gv[Q];
+      if constexpr (PF) {
 #pragma unroll
-      for (int i = 0; i < Q; ++i) {
-        if (i == 0) {
-          gv[0] = to_real(__ldg(a.rest_src + (set == 0 ? 0 : G.P32) + n));
-        } else {
-          const int o = set == 0 ? nb.off(i, plane_g<L>(i), plane_g<L>(L::opp(i)), G.P32)
-                                 : nb.off(i, plane_h<L>(i), plane_h<L>(L::opp(i)), G.P32);
-          gv[i] = to_real(__ldg(a.lo_src + o));
-        }
+        for (int i = 0; i < Q; ++i) gv[i] = nextv[i];
+        if (set == 0) load_set(1, nextv);
+      } else {
+        load_set(set, gv);
       }
 #pragma unroll
       for (int i = 1; i < Q; ++i) {
@@ -290,9 +303,14 @@ __device__ __forceinline__ void collide_body(const LBArgs<MODE>& a, const Blk& b
     __syncthreads();
   }
 }
-template <class L, int MODE, int TX, int TY>
-__global__ void __launch_bounds__(TX* TY, 640 / (TX * TY)) k_collide(const __grid_constant__ LBArgs<MODE> a) {
-  collide_body<L, MODE, TX, TY>(a, hw_blk());
+// Resident threads per SM the collide is compiled for: 640 (96 registers)
+// or, with the next population set prefetched, 512 (128 registers).
+template <bool PF> constexpr int collide_threads() { return PF ? 512 : 640; }
+
+template <class L, int MODE, int TX, int TY, bool PF>
+__global__ void __launch_bounds__(TX* TY, collide_threads<PF>() / (TX * TY))
+    k_collide(const __grid_constant__ LBArgs<MODE> a) {
+  collide_body<L, MODE, TX, TY, PF>(a, hw_blk());
 }
 
 // ------------------------------------------------------------- init & I/O
