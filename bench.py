@@ -130,6 +130,20 @@ def _dist():
     return rank, world, local
 
 
+def replica_throughput(ms_local: float, cells: int, steps: int, dist=None, device=None):
+    """Whole-job throughput of independent replicas (one lattice per rank):
+    the slowest rank's time (all_reduce MAX) and all ranks' cell updates over
+    it, in MLUPS.  Returns (ms, MLUPS)."""
+    import torch
+    t = torch.tensor([float(ms_local)], dtype=torch.float64, device=device)
+    world = 1
+    if dist is not None and dist.is_initialized():
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        world = dist.get_world_size()
+    ms = float(t.item())
+    return ms, world * cells * steps / (ms / 1e3) / 1e6
+
+
 def run_reference(args, wl):
     rank, world, _ = _dist()
     if rank != 0:
@@ -215,14 +229,9 @@ def main():
         launches = sim.launches()
         if dist:
             dist.barrier()
-    ms = e0.elapsed_time(e1)
-    ms_t = torch.tensor([ms], device=dev)
-    if dist:
-        dist.all_reduce(ms_t, op=dist.ReduceOp.MAX)
-    ms_max = float(ms_t.item())
+    ms_max, value = replica_throughput(e0.elapsed_time(e1), N, args.steps, dist, dev)
     clocks = clk.summary(tw0 - 0.05, tw1 + 0.05) or clk.summary()
     clk.stop()
-    value = world * N * args.steps / (ms_max / 1e3) / 1e6
 
     # per-phase device time (CUDA events on the library stream) for the roofline
     nprof = max(20, min(200, args.steps))
