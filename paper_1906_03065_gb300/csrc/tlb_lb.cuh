@@ -103,7 +103,17 @@ __device__ __forceinline__ void collide_body(const LBArgs<MODE>& a, const Blk& b
     if ((a.region == 1) == near) return;
   }
 
-  auto modn = [](int v, int n) { v %= n; return v < 0 ? v + n : v; };
+  // wrap of a halo index: within two cells of the range except for tiles
+  // wider than the lattice, which take the division
+  auto modn = [](int v, int n) {
+    if (v < 0) v += n;
+    if (v >= n) v -= n;
+    if (v < 0 || v >= n) {
+      v %= n;
+      if (v < 0) v += n;
+    }
+    return v;
+  };
   auto plane_src = [&](int p) { return G.wall ? min(max(p, 0), G.nz - 1) : modn(p, G.nz); };
 
   auto load_mom = [&](int p) {
