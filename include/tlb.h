@@ -87,7 +87,15 @@ typedef struct {
   double interface_pos;             /* default init: flat C1/C2 interface at
                                        this coordinate of the last axis (C1
                                        above); < 0: no interface (all C2)    */
+  int forcing;                      /* force in the f collision:
+                                       TLB_FORCE_EDM (exact difference method,
+                                       eq. LBE; the paper's) or TLB_FORCE_GUO
+                                       (Guo, Zheng and Shi 2002: BGK towards
+                                       f^eq(rho, v), v = (j + F/2)/rho, plus
+                                       (1 - 1/(2 tau)) w_i [3 (c_i - v) +
+                                       9 (c_i.v) c_i] . F)                    */
 } tlb_params;
+enum { TLB_FORCE_EDM = 0, TLB_FORCE_GUO = 1 };
 
 typedef struct {
   int kind;           /* TLB_MEM_RING2D | TLB_MEM_TRI3D                        */

@@ -42,7 +42,7 @@ class _Params(C.Structure):
                 ("kappa1", C.c_double), ("kappa2", C.c_double), ("kappa3", C.c_double),
                 ("kappa_c", C.c_double), ("dc", C.c_double),
                 ("u0x", C.c_double), ("u0y", C.c_double), ("u0z", C.c_double),
-                ("interface_pos", C.c_double), ("storage", C.c_int), ("pad2", C.c_int)]
+                ("interface_pos", C.c_double), ("storage", C.c_int), ("forcing", C.c_int)]
 
 
 def lib():
@@ -95,6 +95,7 @@ def _dp(a: np.ndarray):
 
 STORAGE_CODE = {"f64": 0, "f32": 1, "f16": 2, "bf16": 3}
 
+FORCING_CODE = {"edm": 0, "guo": 1}
 FIELDS = {"rho": 0, "phi": 1, "psi": 2, "ux": 3, "uy": 4, "uz": 5, "C1": 6, "C2": 7,
           "C3": 8, "I": 9, "Fx": 10, "Fy": 11, "Fz": 12, "fibx": 13, "fiby": 14,
           "fibz": 15, "mu_rho": 16, "mu_phi": 17, "mu_psi": 18}
@@ -116,7 +117,8 @@ class Oracle:
                      p.tau, p.tau_phi, p.tau_psi, p.gamma_phi, p.gamma_psi, p.alpha,
                      p.kappa1, p.kappa2, p.kappa3, p.kappa_c, p.dc,
                      p.u0[0], p.u0[1], p.u0[2], p.interface_pos,
-                     STORAGE_CODE[p.storage] if emulate_storage else 0, 0)
+                     STORAGE_CODE[p.storage] if emulate_storage else 0,
+                     FORCING_CODE[getattr(p, "forcing", "edm")])
         self._cp = cp
         self.h = L.or_create(C.byref(cp))
         self.N = p.nx * p.ny * (p.nz if p.dim == 3 else 1)

@@ -107,8 +107,9 @@ typedef struct {
   double tau, tau_phi, tau_psi, gamma_phi, gamma_psi, alpha;
   double kappa1, kappa2, kappa3, kappa_c, dc;
   double u0x, u0y, u0z, interface_pos;
-  int storage, pad2;  // population storage emulated after every step:
+  int storage;        // population storage emulated after every step:
                       // 0 none (FP64), 1 binary32, 2 binary16, 3 bfloat16
+  int forcing;        // 0: exact difference method (eq. LBE); 1: Guo forcing
 } or_params;
 
 }  // extern "C"
@@ -988,7 +989,8 @@ void do_step(Sim& s) {
     for (int k = 0; k < s.dim; ++k)
       s.F[3 * c + k] = -s.rho[c] * gr[k] - s.phi[c] * gp[k] - s.psi[c] * gs[k] + s.fib[3 * c + k];
   }
-  // (7) collision (eq. LBE): BGK + exact difference method for f; BGK for g, h
+  // (7) collision (eq. LBE): BGK + exact difference method for f (or Guo
+  //     forcing when selected); BGK for g, h
   std::vector<double> fp(Q * N), gp(Q * N), hp(Q * N);
 #pragma omp parallel for
   for (long c = 0; c < N; ++c) {
@@ -1003,10 +1005,20 @@ void do_step(Sim& s) {
     double ge[19], he[19];
     oeq(L, s.phi[c], s.p.gamma_phi, s.muphi[c], v, ge);
     oeq(L, s.psi[c], s.p.gamma_psi, s.mupsi[c], v, he);
+    const double* Fc = &s.F[3 * c];
+    const double vF = v[0] * Fc[0] + v[1] * Fc[1] + v[2] * Fc[2];
     for (int i = 0; i < Q; ++i) {
       long k = (long)i * N + c;
-      double fe = feq(L, i, r, u);
-      fp[k] = s.f[k] - (s.f[k] - fe) / s.p.tau + feq(L, i, r, ud) - fe;
+      if (s.p.forcing == 1) {
+        // Guo, Zheng and Shi (2002): BGK towards f^eq(rho, v), v = (j + F/2)/rho,
+        // plus the source (1 - 1/(2 tau)) w_i [(c_i - v)/cs^2 + (c_i.v) c_i/cs^4] . F
+        const double cv = cdot(L, i, v), cF = cdot(L, i, Fc);
+        const double Si = (1.0 - 0.5 / s.p.tau) * L.w[i] * ((cF - vF) / CS2 + cv * cF / (CS2 * CS2));
+        fp[k] = s.f[k] - (s.f[k] - feq(L, i, r, v)) / s.p.tau + Si;
+      } else {
+        double fe = feq(L, i, r, u);
+        fp[k] = s.f[k] - (s.f[k] - fe) / s.p.tau + feq(L, i, r, ud) - fe;
+      }
       gp[k] = s.g[k] - (s.g[k] - ge[i]) / s.p.tau_phi;
       hp[k] = s.h[k] - (s.h[k] - he[i]) / s.p.tau_psi;
     }

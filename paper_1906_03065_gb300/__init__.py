@@ -35,7 +35,7 @@ class _Params(C.Structure):
                 ("tau", C.c_double), ("tau_phi", C.c_double), ("tau_psi", C.c_double),
                 ("gamma_phi", C.c_double), ("gamma_psi", C.c_double), ("alpha", C.c_double),
                 ("kappa", C.c_double * 3), ("kappa_c", C.c_double), ("dc", C.c_double),
-                ("u0", C.c_double * 3), ("interface_pos", C.c_double)]
+                ("u0", C.c_double * 3), ("interface_pos", C.c_double), ("forcing", C.c_int)]
 
 
 class _Mem(C.Structure):
@@ -162,6 +162,7 @@ def make_params(p) -> _Params:
     for k in range(3):
         cp.u0[k] = p.u0[k]
     cp.interface_pos = p.interface_pos
+    cp.forcing = {"edm": 0, "guo": 1}[getattr(p, "forcing", "edm")]
     return cp
 
 

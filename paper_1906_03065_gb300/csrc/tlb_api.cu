@@ -115,6 +115,7 @@ static tlb_status check_params(const tlb_params* p, const tlb_membrane_desc* mem
   }
   if (!(p->tau > 0.5 && p->tau_phi > 0.5 && p->tau_psi > 0.5)) { set_error("relaxation times must exceed 1/2"); return TLB_ERR_ARG; }
   if (!(p->alpha > 0) || !(p->dc > 0) || p->dc > 60) { set_error("alpha > 0 and 0 < dc <= 60 required"); return TLB_ERR_ARG; }
+  if (p->forcing != TLB_FORCE_EDM && p->forcing != TLB_FORCE_GUO) { set_error("unknown forcing"); return TLB_ERR_ARG; }
   if (n_mem < 0 || n_mem > 8) { set_error("at most 8 membranes"); return TLB_ERR_ARG; }
   for (int m = 0; m < n_mem; ++m) {
     const tlb_membrane_desc& d = mems[m];

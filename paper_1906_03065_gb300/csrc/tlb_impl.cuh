@@ -64,6 +64,7 @@ struct Impl : ImplBase {
     a.gphi = (Real)c->p.gamma_phi;
     a.gpsi = (Real)c->p.gamma_psi;
     a.zc = c->tiles_zc;
+    a.forcing = c->p.forcing;
     a.status = c->ptr<unsigned>(c->L.status);
     return a;
   }

@@ -30,6 +30,7 @@ struct LBArgs {
   Real om, om_phi, om_psi;  // 1/tau
   Real gphi, gpsi;          // Gamma_phi, Gamma_psi
   int zc;                   // planes per block along z
+  int forcing;              // TLB_FORCE_EDM or TLB_FORCE_GUO
   unsigned* status;
 };
 
@@ -252,15 +253,30 @@ __device__ __forceinline__ void collide_body(const LBArgs<MODE>& a, const Blk& b
     const Real vv = v[0] * v[0] + v[1] * v[1] + v[2] * v[2];
     const Real dus = du[0] * us[0] + du[1] * us[1] + du[2] * us[2];
     const Real om = a.om;
+    if (a.forcing == TLB_FORCE_GUO) {
+      // Guo forcing: BGK towards f^eq(rho, v) plus (1 - om/2) w_i [3 (c_i - v) + 9 (c_i.v) c_i] . F
+      const Real vF = v[0] * F[0] + v[1] * F[1] + v[2] * F[2];
+      const Real sc = Real(1) - Real(0.5) * om;
 #pragma unroll
-    for (int i = 0; i < Q; ++i) {
-      const Real w = Real(L::w(i));
-      const Real cu = L::cx(i) * u[0] + L::cy(i) * u[1] + L::cz(i) * u[2];
-      const Real cdu = L::cx(i) * du[0] + L::cy(i) * du[1] + L::cz(i) * du[2];
-      const Real cus = L::cx(i) * us[0] + L::cy(i) * us[1] + L::cz(i) * us[2];
-      const Real dP = Real(3) * cdu + Real(4.5) * cdu * cus - Real(1.5) * dus;
-      const Real fn = (Real(1) - om) * fv[i] + om * w * (drho + rho * eq_poly(cu, uu)) + w * rho * dP;
-      a.lo_dst[plane_f<L>(i) * G.P32 + n] = from_real<Store>(fn);
+      for (int i = 0; i < Q; ++i) {
+        const Real w = Real(L::w(i));
+        const Real cv = L::cx(i) * v[0] + L::cy(i) * v[1] + L::cz(i) * v[2];
+        const Real cF = L::cx(i) * F[0] + L::cy(i) * F[1] + L::cz(i) * F[2];
+        const Real fn = (Real(1) - om) * fv[i] + om * w * (drho + rho * eq_poly(cv, vv)) +
+                        sc * w * (Real(3) * (cF - vF) + Real(9) * cv * cF);
+        a.lo_dst[plane_f<L>(i) * G.P32 + n] = from_real<Store>(fn);
+      }
+    } else {
+#pragma unroll
+      for (int i = 0; i < Q; ++i) {
+        const Real w = Real(L::w(i));
+        const Real cu = L::cx(i) * u[0] + L::cy(i) * u[1] + L::cz(i) * u[2];
+        const Real cdu = L::cx(i) * du[0] + L::cy(i) * du[1] + L::cz(i) * du[2];
+        const Real cus = L::cx(i) * us[0] + L::cy(i) * us[1] + L::cz(i) * us[2];
+        const Real dP = Real(3) * cdu + Real(4.5) * cdu * cus - Real(1.5) * dus;
+        const Real fn = (Real(1) - om) * fv[i] + om * w * (drho + rho * eq_poly(cu, uu)) + w * rho * dP;
+        a.lo_dst[plane_f<L>(i) * G.P32 + n] = from_real<Store>(fn);
+      }
     }
     // g and h: BGK towards the order-parameter equilibria at v (eq. EDF); the
     // rest population closes the zeroth moment

@@ -55,6 +55,7 @@ class Params:
     dc: float = 8.0             # clamp distance of the membrane profile
     u0: tuple = (0.0, 0.0, 0.0)
     interface_pos: float = 32.0  # flat C1/C2 interface along the last axis
+    forcing: str = "edm"        # "edm": exact difference method (the paper); "guo": Guo forcing
 
     @property
     def ncells(self) -> int:

@@ -66,10 +66,11 @@ def test_init_profile_matches_oracle():
         assert np.abs(g.field("I") - I_o).max() < tol
 
 
-@pytest.mark.parametrize("tau", [1.0, 0.8])
-def test_one_step_random_state_2d_f64(tau):
+@pytest.mark.parametrize("tau,forcing", [(1.0, "edm"), (0.8, "edm"), (0.8, "guo")])
+def test_one_step_random_state_2d_f64(tau, forcing):
     wl = W.small_2d("f64")
     wl.params.tau = wl.params.tau_phi = wl.params.tau_psi = tau
+    wl.params.forcing = forcing
     wl.membranes[0] = W.jitter_nodes(wl.membranes[0], 0.2, seed=1)
     o = oracle.Oracle(wl, init=False)
     C0, u0 = W.random_fields(wl.params, seed=4)
@@ -116,9 +117,11 @@ def test_small_3d_f32_one_step_random():
     assert np.abs(g.nodes(0) - o.nodes(0)).max() < 1e-6
 
 
-def test_small_3d_f32_200_steps():
+@pytest.mark.parametrize("forcing", ["edm", "guo"])
+def test_small_3d_f32_200_steps(forcing):
     """Ragged 40x36x34 D3Q19 lattice with walls and a capsule, FP32 storage."""
     wl = W.small_3d("f32")
+    wl.params.forcing = forcing
     g, o = _sim(wl).init(), oracle.Oracle(wl)
     g.step(200)
     o.step(200)

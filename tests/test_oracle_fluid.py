@@ -154,6 +154,47 @@ def test_collision_moments(dim, tau):
         assert np.abs(Gp - ref).max() < 1e-13
 
 
+@pytest.mark.parametrize("dim,tau", [(2, 1.0), (2, 0.8), (3, 0.7)])
+def test_guo_forcing_collision_moments(dim, tau):
+    """Guo forcing (Guo, Zheng and Shi 2002): mass is conserved, momentum
+    changes by exactly F, and the second moment relaxes towards the
+    equilibrium at v = (j + F/2)/rho with the source's (1 - 1/(2 tau))
+    (v F + F v) -- the published moments of the scheme."""
+    if dim == 2:
+        wl = W.small_2d(nx=24, ny=22, nodes=30, radius=5.0, centre=(11.5, 10.7))
+    else:
+        wl = W.small_3d(nx=14, ny=13, nz=12, level=1, radius=3.5, centre=(7.1, 6.4, 5.8), wall=0)
+    p = wl.params
+    p.tau = p.tau_phi = p.tau_psi = tau
+    p.forcing = "guo"
+    o = oracle.Oracle(wl, init=False)
+    C0, u0 = W.random_fields(p, seed=3)
+    o.init(C0, u0)
+    rng = np.random.default_rng(11)
+    P = o.pops()
+    c, w = o.lattice()
+    P = P + 1e-3 * rng.standard_normal(P.shape) * w[None, :, None]
+    o.set_pops(P)
+    rho = P[0].sum(0)
+    j = np.einsum("ia,in->an", c, P[0])
+    Pi = np.einsum("ia,ib,in->abn", c, c, P[0])
+    o.step(1)
+    S = _unstream(o.pops().reshape(3, len(c), -1)[0], c, o.shape)
+    F = np.stack([o.field("Fx"), o.field("Fy"), o.field("Fz")])
+    assert np.abs(F).max() > 1e-6  # the forces are not trivial
+    assert np.abs(S.sum(0) - rho).max() < 1e-13
+    assert np.abs(np.einsum("ia,in->an", c, S) - (j + F)).max() < 1e-13
+    v = (j + 0.5 * F) / rho
+    d = np.eye(3)
+    eq = rho * CS2 * d[:, :, None] + rho * v[:, None] * v[None, :]
+    src = (1 - 0.5 / tau) * (v[:, None] * F[None, :] + F[:, None] * v[None, :])
+    ref = (1 - 1 / tau) * Pi + eq / tau + src
+    M2 = np.einsum("ia,ib,in->abn", c, c, S)
+    if dim == 2:
+        M2, ref = M2[:2, :2], ref[:2, :2]
+    assert np.abs(M2 - ref).max() < 1e-13
+
+
 def test_mass_conservation_with_capsule_and_walls():
     wl = W.small_3d(nx=20, ny=18, nz=16, level=2, radius=5.0, centre=(10.2, 9.1, 8.3))
     o = oracle.Oracle(wl)
