@@ -263,6 +263,8 @@ static void plan(const tlb_params* p, const std::vector<HostMem>& mems, Ctx& c) 
   take(L.inc, NV * ne * 4);
   take(L.adj, 3 * ne * 4);
   take(L.edges, 4 * (size_t)c.nedge * 4);
+  take(L.ring_off, (nn + 1) * 4);
+  take(L.ring, NV * ne * 4);
   take(L.en, 3 * ne * R);
   take(L.vn, 3 * nn * R);
   take(L.esum, 3 * NV * ne * 8);
@@ -431,6 +433,26 @@ tlb_status tlb_create(const tlb_params* params, const tlb_membrane_desc* mems, i
       inc_off[v + 1] = inc_off[v] + (int)inc[v].size();
       incl.insert(incl.end(), inc[v].begin(), inc[v].end());
     }
+    // distinct 1-ring neighbours of every node, in the order of its incident
+    // elements (ascending) and of their vertices
+    std::vector<int> ring_off(c->nn + 1, 0), ring;
+    int max_inc = 0, max_ring = 0;
+    for (int v = 0; v < c->nn; ++v) {
+      const size_t r0 = ring.size();
+      for (int e : inc[v])
+        for (int q = 0; q < c->NV; ++q) {
+          const int u = E[(size_t)c->NV * e + q];
+          if (u != v && std::find(ring.begin() + r0, ring.end(), u) == ring.end()) ring.push_back(u);
+        }
+      ring_off[v + 1] = (int)ring.size();
+      max_inc = std::max(max_inc, (int)inc[v].size());
+      max_ring = std::max(max_ring, (int)(ring.size() - r0));
+    }
+    if (c->NV == 3 && (max_inc > 16 || max_ring > 15)) {
+      set_error("membrane: a node has more than 16 incident triangles or 15 neighbours");
+      delete c;
+      return TLB_ERR_ARG;
+    }
     auto up = [&](const Region& reg, const void* src, size_t n) {
       return cuda_check(cudaMemcpyAsync(c->base + reg.off, src, n, cudaMemcpyHostToDevice, st), "upload");
     };
@@ -448,6 +470,8 @@ tlb_status tlb_create(const tlb_params* params, const tlb_membrane_desc* mems, i
     u = u != TLB_OK ? u : up(c->L.inc_off, inc_off.data(), inc_off.size() * 4);
     u = u != TLB_OK ? u : up(c->L.inc, incl.data(), incl.size() * 4);
     u = u != TLB_OK ? u : up(c->L.adj, adj.data(), adj.size() * 4);
+    u = u != TLB_OK ? u : up(c->L.ring_off, ring_off.data(), ring_off.size() * 4);
+    if (!ring.empty()) u = u != TLB_OK ? u : up(c->L.ring, ring.data(), ring.size() * 4);
     if ((int)edges.size() != 4 * c->nedge) {
       set_error("membrane is not a closed surface (every edge must belong to two triangles)");
       delete c;

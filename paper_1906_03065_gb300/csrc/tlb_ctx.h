@@ -51,7 +51,7 @@ struct Layout {
   Region lo[2], rest[2];
   Region rho, phi, psi, I, dsel, own, key, fib, ftot, mu, rb;
   // membranes
-  Region X, E, ecap, ncap, cap_par, ds0, rprev, rnext, A0, G0i, inc_off, inc, adj, edges;
+  Region X, E, ecap, ncap, cap_par, ds0, rprev, rnext, A0, G0i, inc_off, inc, adj, edges, ring_off, ring;
   Region en, vn, esum, F, box;
   Region bcnt, bprev, bcur, boff, blist, bact, ctr, bflag;
   // misc

@@ -30,6 +30,8 @@ struct IBArgs {
   const int* inc_off;    // node -> incident elements (CSR, ascending)
   const int* inc;
   const int* adj;        // 3D: triangle across edge q (q: vertex q -> q+1)
+  const int* ring_off;   // node -> distinct 1-ring neighbours (CSR, in the order
+  const int* ring;       // of the incident elements and their vertices)
   int nedge;             // 3D: unique edges
   const int* edges;      // 3D: [nedge][4] vertex a, vertex b, face left, face right
   // per-step work
@@ -732,26 +734,8 @@ __device__ __forceinline__ void node_forces_body(const IBArgs<Real>& a, const Bl
     // (lane-17)-th distinct 1-ring neighbour of k, enumerated in the order
     // of the incident triangles and their vertices
     if (lane >= 16) {
-      int want = lane - 16, v = -1;
-      if (want == 0) v = k;
-      else {
-        int cnt = 0;
-        for (int jj = i0; jj < i0 + ninc && v < 0; ++jj) {
-          int t = a.inc[jj];
-          for (int q = 0; q < 3 && v < 0; ++q) {
-            int u = a.E[3 * t + q];
-            if (u == k) continue;
-            bool seen = false;
-            for (int ii = i0; ii < jj && !seen; ++ii) {
-              int t2 = a.inc[ii];
-              seen = a.E[3 * t2] == u || a.E[3 * t2 + 1] == u || a.E[3 * t2 + 2] == u;
-            }
-            for (int q2 = 0; q2 < q && !seen; ++q2) seen = a.E[3 * t + q2] == u;
-            if (seen) continue;
-            if (++cnt == want) v = u;
-          }
-        }
-      }
+      const int want = lane - 16, r0 = a.ring_off[k], deg = a.ring_off[k + 1] - r0;
+      const int v = want == 0 ? k : (want - 1 < deg ? a.ring[r0 + want - 1] : -1);
       if (v >= 0) {
         D3<Real> h = helfrich_dual(a, v, k);
         F[0] -= h.d0; F[1] -= h.d1; F[2] -= h.d2;

@@ -93,6 +93,8 @@ struct Impl : ImplBase {
     a.inc_off = c->ptr<int>(c->L.inc_off);
     a.inc = c->ptr<int>(c->L.inc);
     a.adj = c->ptr<int>(c->L.adj);
+    a.ring_off = c->ptr<int>(c->L.ring_off);
+    a.ring = c->ptr<int>(c->L.ring);
     a.nedge = c->nedge;
     a.edges = c->ptr<int>(c->L.edges);
     a.en = c->ptr<Real>(c->L.en);
