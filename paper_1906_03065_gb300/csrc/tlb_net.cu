@@ -147,6 +147,111 @@ __global__ void __launch_bounds__(128) k_conv(const bf16* __restrict__ in, int C
   }
 }
 
+// 3x3x3 convolution on bricks: a CTA computes an 8x4x4 brick of output
+// voxels (128 GEMM rows, 4 warps x 2 m16 tiles) for BN output channels.  Per
+// chunk of 16 input channels it stages the brick's input with a halo of 1
+// (10x6x6 voxels, zero outside the volume) and the chunk's weights of all 27
+// taps in shared memory once, then runs the 27 taps as shifted views of the
+// staged input.  Rows are 48 bytes apart, so the fragment loads of 8
+// consecutive rows hit distinct banks.
+constexpr int BRX = 8, BRY = 4, BRZ = 4, HX = BRX + 2, HY = BRY + 2, HZ = BRZ + 2, HV = HX * HY * HZ;
+
+template <int BN>
+constexpr int conv3_smem() { return (HV + 27 * BN) * SK * 2; }
+
+template <int BN, bool RELU>
+__global__ void __launch_bounds__(128) k_conv3(const bf16* __restrict__ in, int Ci, int El, int nbatch,
+                                               const bf16* __restrict__ Wk, const float* __restrict__ bias, int Co,
+                                               void* __restrict__ out) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  bf16 (*Xs)[SK] = reinterpret_cast<bf16 (*)[SK]>(smem);
+  bf16 (*Ws)[SK] = reinterpret_cast<bf16 (*)[SK]>(smem + HV * SK * 2);
+  const int bpx = (El + BRX - 1) / BRX, bpy = (El + BRY - 1) / BRY, bpz = (El + BRZ - 1) / BRZ;
+  int bid = blockIdx.x;
+  const int bx = bid % bpx;
+  bid /= bpx;
+  const int by = bid % bpy;
+  bid /= bpy;
+  const int bz = bid % bpz;
+  const int b = bid / bpz;
+  if (b >= nbatch) return;
+  const int x0 = bx * BRX, y0 = by * BRY, z0 = bz * BRZ, n0 = blockIdx.y * BN;
+  const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31, g = lane >> 2, t = lane & 3;
+  const int K = 27 * Ci;
+  float acc[2][BN / 8][4];
+#pragma unroll
+  for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+    for (int j = 0; j < BN / 8; ++j) acc[mt][j][0] = acc[mt][j][1] = acc[mt][j][2] = acc[mt][j][3] = 0.f;
+  // input-tile voxel of GEMM row r at tap offset (0..2 per axis)
+  auto tile_vox = [](int r, int dz, int dy, int dx) {
+    return ((r / (BRX * BRY) + dz) * HY + (r / BRX) % BRY + dy) * HX + r % BRX + dx;
+  };
+  for (int ci0 = 0; ci0 < Ci; ci0 += 16) {
+    for (int i = tid; i < HV * 2; i += 128) {
+      const int v = i >> 1, h = i & 1;
+      const int X = x0 - 1 + v % HX, Y = y0 - 1 + (v / HX) % HY, Z = z0 - 1 + v / (HX * HY);
+      uint4 val = make_uint4(0, 0, 0, 0);
+      if (X >= 0 && X < El && Y >= 0 && Y < El && Z >= 0 && Z < El)
+        val = *reinterpret_cast<const uint4*>(in + ((((long long)b * El + Z) * El + Y) * El + X) * Ci + ci0 + h * 8);
+      *reinterpret_cast<uint4*>(&Xs[v][h * 8]) = val;
+    }
+    for (int i = tid; i < 27 * BN * 2; i += 128) {
+      const int row = i >> 1, h = i & 1, tap = row / BN, n = row % BN;
+      *reinterpret_cast<uint4*>(&Ws[row][h * 8]) =
+          *reinterpret_cast<const uint4*>(Wk + (long long)(n0 + n) * K + tap * Ci + ci0 + h * 8);
+    }
+    __syncthreads();
+#pragma unroll 1
+    for (int tap = 0; tap < 27; ++tap) {
+      const int dz = tap / 9, dy = (tap / 3) % 3, dx = tap % 3;
+      unsigned a[2][4];
+#pragma unroll
+      for (int mt = 0; mt < 2; ++mt) {
+        const int r0 = (w * 2 + mt) * 16 + g;
+        const int v0 = tile_vox(r0, dz, dy, dx), v1 = tile_vox(r0 + 8, dz, dy, dx);
+        a[mt][0] = *reinterpret_cast<const unsigned*>(&Xs[v0][2 * t]);
+        a[mt][1] = *reinterpret_cast<const unsigned*>(&Xs[v1][2 * t]);
+        a[mt][2] = *reinterpret_cast<const unsigned*>(&Xs[v0][2 * t + 8]);
+        a[mt][3] = *reinterpret_cast<const unsigned*>(&Xs[v1][2 * t + 8]);
+      }
+#pragma unroll
+      for (int j = 0; j < BN / 8; ++j) {
+        unsigned bb[2];
+        bb[0] = *reinterpret_cast<const unsigned*>(&Ws[tap * BN + j * 8 + g][2 * t]);
+        bb[1] = *reinterpret_cast<const unsigned*>(&Ws[tap * BN + j * 8 + g][2 * t + 8]);
+        mma_bf16(acc[0][j], a[0], bb);
+        mma_bf16(acc[1][j], a[1], bb);
+      }
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+    for (int half = 0; half < 2; ++half) {
+      const int r = (w * 2 + mt) * 16 + g + half * 8;
+      const int X = x0 + r % BRX, Y = y0 + (r / BRX) % BRY, Z = z0 + r / (BRX * BRY);
+      if (X >= El || Y >= El || Z >= El) continue;
+      const long long v = (((long long)b * El + Z) * El + Y) * El + X;
+#pragma unroll
+      for (int j = 0; j < BN / 8; ++j) {
+        const int n = n0 + j * 8 + 2 * t;
+        float o0 = acc[mt][j][half * 2], o1 = acc[mt][j][half * 2 + 1];
+        if (bias) {
+          o0 += bias[n];
+          o1 += bias[n + 1];
+        }
+        if (RELU) {
+          __nv_bfloat162 hv = __floats2bfloat162_rn(fmaxf(o0, 0.f), fmaxf(o1, 0.f));
+          *reinterpret_cast<__nv_bfloat162*>(static_cast<bf16*>(out) + v * Co + n) = hv;
+        } else {
+          *reinterpret_cast<float2*>(static_cast<float*>(out) + v * Co + n) = make_float2(o0, o1);
+        }
+      }
+    }
+}
+
 // Weight (and bias) gradient of one conv, split over voxel ranges:
 //   part[split][m][n] = sum_{v in range} A[m][v] gz[v][n]
 // with rows m = tap*Ci + ci: A[m][v] = in[nbr(v, tap)][ci], and one extra row
@@ -706,9 +811,25 @@ int tile_n(int C) { return C % 64 == 0 ? 64 : (C % 32 == 0 ? 32 : 16); }
     if (_s != TLB_OK) return _s;                                 \
   } while (0)
 
+template <int BN, bool RELU>
+tlb_status launch_conv3_t(Net* n, const bf16* in, int Ci, int El, int B, const bf16* Wk, const float* bias, int Co,
+                          void* out) {
+  const long long bricks = (long long)((El + BRX - 1) / BRX) * ((El + BRY - 1) / BRY) * ((El + BRZ - 1) / BRZ) * B;
+  constexpr int sm = conv3_smem<BN>();
+  TLB_CUDA(cudaFuncSetAttribute(k_conv3<BN, RELU>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
+  k_conv3<BN, RELU><<<dim3((unsigned)bricks, Co / BN), 128, sm, n->stream>>>(in, Ci, El, B, Wk, bias, Co, out);
+  NET_LAUNCHED(n, "k_conv3");
+  return TLB_OK;
+}
+
 template <bool RELU>
 tlb_status launch_conv(Net* n, const bf16* in, int Ci, int El, long long nvox, int taps, const bf16* Wk,
                        const float* bias, int Co, void* out) {
+  if (taps == 27) {  // brick-tiled direct convolution; columns per CTA: 32 or 16
+    const int B = (int)(nvox / ((long long)El * El * El));
+    if (Co % 32 == 0) return launch_conv3_t<32, RELU>(n, in, Ci, El, B, Wk, bias, Co, out);
+    return launch_conv3_t<16, RELU>(n, in, Ci, El, B, Wk, bias, Co, out);
+  }
   const int BN = tile_n(Co);
   dim3 grid(nb(nvox, TM), Co / BN);
   cudaStream_t s = n->stream;
