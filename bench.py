@@ -376,7 +376,7 @@ def main():
         torch.cuda.synchronize(dev)
         ms_t = a0.elapsed_time(a1) / reps
         bf = peaks["bf16_tflops"] if peaks else 1900.0
-        net_line = {"edge": E, "batch": B, "params": net.n_params, "kernel": "k_conv/k_wgrad (mma.sync bf16)",
+        net_line = {"edge": E, "batch": B, "params": net.n_params, "kernel": "k_conv3/k_wgrad3 (mma.sync bf16, brick-tiled)",
                     "forward_ms": ms_f, "train_step_ms": ms_t,
                     "forward_tflops": B * f_fwd / (ms_f / 1e3) / 1e12,
                     "train_tflops": B * f_train / (ms_t / 1e3) / 1e12, "peak_bf16_tflops": bf,

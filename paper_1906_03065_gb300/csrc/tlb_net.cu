@@ -252,6 +252,137 @@ __global__ void __launch_bounds__(128) k_conv3(const bf16* __restrict__ in, int 
     }
 }
 
+// Shared-memory 8x8 b16 matrices, transposed on load (ldmatrix .trans): lane
+// l gives the row address of matrix l / 8; each row holds 8 consecutive b16.
+__device__ __forceinline__ void ldsm_x4_t(unsigned* r, const void* p) {
+  const unsigned a = (unsigned)__cvta_generic_to_shared(p);
+  asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0,%1,%2,%3}, [%4];\n"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+               : "r"(a));
+}
+__device__ __forceinline__ void ldsm_x2_t(unsigned* r, const void* p) {
+  const unsigned a = (unsigned)__cvta_generic_to_shared(p);
+  asm volatile("ldmatrix.sync.aligned.m8n8.x2.trans.shared.b16 {%0,%1}, [%2];\n" : "=r"(r[0]), "=r"(r[1]) : "r"(a));
+}
+
+// Weight gradient of a 3x3x3 conv on bricks: dW[tap][ci][co] = sum over
+// voxels v of in[v + offset(tap)][ci] gz[v][co], a GEMM with rows (ci), columns
+// (co) and the voxels as K.  A CTA owns 16 input channels (blockIdx.z), BN
+// output channels (blockIdx.y) and the bricks blockIdx.x, blockIdx.x +
+// gridDim.x, ...; per brick it stages the input with its halo and gz in
+// shared memory and warp w accumulates the taps w, w + 4, ... over the
+// brick's 128 voxels.  Operands are read transposed from the channels-last
+// rows with ldmatrix.  Writes part[blockIdx.x][tap][ci][co] (fixed order of
+// bricks per CTA, so the sums are deterministic).
+template <int BN>
+constexpr int gs_stride() { return BN + 8; }
+template <int BN>
+constexpr int wgrad3_smem() { return HV * SK * 2 + 128 * gs_stride<BN>() * 2; }
+
+template <int BN>
+__global__ void __launch_bounds__(128) k_wgrad3(const bf16* __restrict__ in, int Ci, int El, int nbatch,
+                                                const bf16* __restrict__ gz, int Co, float* __restrict__ part) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  constexpr int GS = gs_stride<BN>();
+  bf16 (*Xs)[SK] = reinterpret_cast<bf16 (*)[SK]>(smem);
+  bf16 (*Gs)[GS] = reinterpret_cast<bf16 (*)[GS]>(smem + HV * SK * 2);
+  const int bpx = (El + BRX - 1) / BRX, bpy = (El + BRY - 1) / BRY, bpz = (El + BRZ - 1) / BRZ;
+  const int nbr = bpx * bpy * bpz * nbatch;
+  const int n0 = blockIdx.y * BN, ci0 = blockIdx.z * 16;
+  const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31, g = lane >> 2, t = lane & 3;
+  constexpr int NTW = 7;  // taps per warp: w, w + 4, ... below 27
+  float acc[NTW][BN / 8][4];
+#pragma unroll
+  for (int s = 0; s < NTW; ++s)
+#pragma unroll
+    for (int j = 0; j < BN / 8; ++j) acc[s][j][0] = acc[s][j][1] = acc[s][j][2] = acc[s][j][3] = 0.f;
+  // ldmatrix row of this lane: voxel kk of a 16-voxel k-step, column half
+  const int lrow = (lane & 7) + ((lane >> 4) << 3), lcol = ((lane >> 3) & 1) * 8;
+  for (int bb = blockIdx.x; bb < nbr; bb += gridDim.x) {
+    int bid = bb;
+    const int bx = bid % bpx;
+    bid /= bpx;
+    const int by = bid % bpy;
+    bid /= bpy;
+    const int bz = bid % bpz;
+    const int b = bid / bpz;
+    const int x0 = bx * BRX, y0 = by * BRY, z0 = bz * BRZ;
+    for (int i = tid; i < HV * 2; i += 128) {
+      const int v = i >> 1, h = i & 1;
+      const int X = x0 - 1 + v % HX, Y = y0 - 1 + (v / HX) % HY, Z = z0 - 1 + v / (HX * HY);
+      uint4 val = make_uint4(0, 0, 0, 0);
+      if (X >= 0 && X < El && Y >= 0 && Y < El && Z >= 0 && Z < El)
+        val = *reinterpret_cast<const uint4*>(in + ((((long long)b * El + Z) * El + Y) * El + X) * Ci + ci0 + h * 8);
+      *reinterpret_cast<uint4*>(&Xs[v][h * 8]) = val;
+    }
+    for (int i = tid; i < 128 * (BN / 8); i += 128) {
+      const int r = i / (BN / 8), q = i % (BN / 8);
+      const int X = x0 + r % BRX, Y = y0 + (r / BRX) % BRY, Z = z0 + r / (BRX * BRY);
+      uint4 val = make_uint4(0, 0, 0, 0);
+      if (X < El && Y < El && Z < El)
+        val = *reinterpret_cast<const uint4*>(gz + ((((long long)b * El + Z) * El + Y) * El + X) * Co + n0 + q * 8);
+      *reinterpret_cast<uint4*>(&Gs[r][q * 8]) = val;
+    }
+    __syncthreads();
+#pragma unroll 1
+    for (int k0 = 0; k0 < 128; k0 += 16) {
+      unsigned bf[BN / 8][2];
+#pragma unroll
+      for (int j = 0; j < BN / 8; ++j) ldsm_x2_t(bf[j], &Gs[k0 + (lane & 15)][j * 8]);
+      const int kk = k0 + lrow;
+      const int lz = kk / (BRX * BRY), ly = (kk / BRX) % BRY, lx = kk % BRX;
+#pragma unroll
+      for (int s = 0; s < NTW; ++s) {
+        const int tap = w + 4 * s;
+        if (tap < 27) {
+          const int dz = tap / 9, dy = (tap / 3) % 3, dx = tap % 3;
+          unsigned af[4];
+          ldsm_x4_t(af, &Xs[((lz + dz) * HY + ly + dy) * HX + lx + dx][lcol]);
+#pragma unroll
+          for (int j = 0; j < BN / 8; ++j) mma_bf16(acc[s][j], af, bf[j]);
+        }
+      }
+    }
+    __syncthreads();
+  }
+  float* P = part + (size_t)blockIdx.x * 27 * Ci * Co;
+#pragma unroll
+  for (int s = 0; s < NTW; ++s) {
+    const int tap = w + 4 * s;
+    if (tap >= 27) continue;
+#pragma unroll
+    for (int j = 0; j < BN / 8; ++j) {
+      const int n = n0 + j * 8 + 2 * t;
+#pragma unroll
+      for (int half = 0; half < 2; ++half) {
+        const int ci = ci0 + g + half * 8;
+        float* dst = P + ((size_t)tap * Ci + ci) * Co + n;
+        dst[0] = acc[s][j][half * 2];
+        dst[1] = acc[s][j][half * 2 + 1];
+      }
+    }
+  }
+}
+
+// out[i] = sum over k < nsplit of part[k * n + i], in split order (i < n).
+__global__ void k_sum_splits(const float* __restrict__ part, int nsplit, long long n, float* __restrict__ out) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  float s = 0.f;
+  for (int k = 0; k < nsplit; ++k) s += part[(size_t)k * n + i];
+  out[i] = s;
+}
+
+// Column sums of gz (the bias gradient), per-block partials over fixed voxel ranges.
+__global__ void k_colsum(const bf16* __restrict__ gz, long long V, int Co, long long chunk, float* __restrict__ part) {
+  const long long v0 = (long long)blockIdx.x * chunk, v1 = min(V, v0 + chunk);
+  for (int co = threadIdx.x; co < Co; co += blockDim.x) {
+    float s = 0.f;
+    for (long long v = v0; v < v1; ++v) s += __bfloat162float(gz[v * Co + co]);
+    part[(size_t)blockIdx.x * Co + co] = s;
+  }
+}
+
 // Weight (and bias) gradient of one conv, split over voxel ranges:
 //   part[split][m][n] = sum_{v in range} A[m][v] gz[v][n]
 // with rows m = tap*Ci + ci: A[m][v] = in[nbr(v, tap)][ci], and one extra row
@@ -843,7 +974,38 @@ tlb_status launch_conv(Net* n, const bf16* in, int Ci, int El, long long nvox, i
   return TLB_OK;
 }
 
+template <int BN>
+tlb_status launch_wgrad3_t(Net* n, const Conv& c, const bf16* in, int El, int B, const bf16* gz) {
+  const int nbr = ((El + BRX - 1) / BRX) * ((El + BRY - 1) / BRY) * ((El + BRZ - 1) / BRZ) * B;
+  const int tiles = (c.co / BN) * (c.ci / 16);
+  const int nsplit = std::max(1, std::min(nbr, std::min(512, (2 * 152 * 4 + tiles - 1) / tiles)));
+  constexpr int sm = wgrad3_smem<BN>();
+  float* part = n->at<float>(n->o_part);
+  TLB_CUDA(cudaFuncSetAttribute(k_wgrad3<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
+  k_wgrad3<BN><<<dim3(nsplit, c.co / BN, c.ci / 16), 128, sm, n->stream>>>(in, c.ci, El, B, gz, c.co, part);
+  NET_LAUNCHED(n, "k_wgrad3");
+  float* g = n->at<float>(n->o_grad);
+  // weight gradient: sums over the CTAs' partials [27 * Ci][Co]
+  const long long nw = 27ll * c.ci * c.co;
+  k_sum_splits<<<nb(nw, 256), 256, 0, n->stream>>>(part, nsplit, nw, g + c.w);
+  NET_LAUNCHED(n, "k_sum_splits");
+  // bias gradient: column sums of gz over fixed voxel ranges, then over the ranges
+  const long long V = (long long)B * El * El * El;
+  const int nbs = (int)std::min<long long>(512, (V + 255) / 256);
+  const long long chunk = (V + nbs - 1) / nbs;
+  k_colsum<<<nbs, 128, 0, n->stream>>>(gz, V, c.co, chunk, part);
+  NET_LAUNCHED(n, "k_colsum");
+  k_sum_splits<<<nb(c.co, 256), 256, 0, n->stream>>>(part, nbs, c.co, g + c.b);
+  NET_LAUNCHED(n, "k_sum_splits");
+  return TLB_OK;
+}
+
 tlb_status launch_wgrad(Net* n, const Conv& c, const bf16* in, int El, long long nvox, const bf16* gz) {
+  if (c.taps == 27) {
+    const int B = (int)(nvox / ((long long)El * El * El));
+    if (c.co % 32 == 0) return launch_wgrad3_t<32>(n, c, in, El, B, gz);
+    return launch_wgrad3_t<16>(n, c, in, El, B, gz);
+  }
   const int BN = tile_n(c.co);
   const int M = c.taps * c.ci + 1;
   const int mt = (M + TM - 1) / TM, ntile = c.co / BN;
