@@ -199,6 +199,26 @@ tlb_status tlb_diagnostics_static(void* ctx, tlb_diag* out);
  * steps and compared with a tolerance, is the library's reading of it. */
 tlb_status tlb_residual(void* ctx, double out[4]);
 
+/* Run to equilibrium: tlb_step in chunks of check_every steps, tlb_residual
+ * after each chunk, until the residual (out[3]) is at or below tol or
+ * max_steps steps were taken.  *steps_done = the step count t at return,
+ * *residual = the last residual (NaN if max_steps is 0); either may be NULL.
+ * Synchronises the stream. */
+tlb_status tlb_run(void* ctx, long max_steps, long check_every, double tol, long* steps_done, double* residual);
+
+/* Checkpoint of the state of a context into host memory, and its restore.
+ * The blob holds what a continued run reads (the current populations, the
+ * profile I, the markers, the residual's reference state, the step count),
+ * so that a context restored from it continues bit for bit as the saved one
+ * would have.  tlb_save with host_blob NULL writes the size needed to *bytes;
+ * otherwise *bytes is the blob's capacity on entry and its size on return.
+ * tlb_load needs a context created with the same parameters and membranes
+ * (TLB_ERR_ARG otherwise, or for a truncated or foreign blob); it need not be
+ * initialised.  Both synchronise the stream.  Not in the paper: the
+ * checkpoint/resume of a long relaxation run. */
+tlb_status tlb_save(void* ctx, void* host_blob, size_t* bytes);
+tlb_status tlb_load(void* ctx, const void* host_blob, size_t bytes);
+
 /* Per-phase device time of n_steps steps, measured with CUDA events on the
  * context stream around each phase (synchronises the stream).  Phases:
  * moments (streamed-population moments), ibm (profile I, membrane and

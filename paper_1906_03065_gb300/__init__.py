@@ -90,6 +90,11 @@ def lib():
         L.tlb_autotune.restype = C.c_int
         L.tlb_last_launch_count.argtypes = [vp]
         L.tlb_last_launch_count.restype = C.c_long
+        L.tlb_run.argtypes = [vp, C.c_long, C.c_long, C.c_double, C.POINTER(C.c_long), dp]
+        L.tlb_save.argtypes = [vp, vp, C.POINTER(sz)]
+        L.tlb_load.argtypes = [vp, vp, sz]
+        for n in ("tlb_run", "tlb_save", "tlb_load"):
+            getattr(L, n).restype = C.c_int
         L.tlb_set_tile.argtypes = [vp, C.c_int, C.c_int]
         L.tlb_set_tile.restype = C.c_int
         L.tlb_residual.argtypes = [vp, dp]
@@ -250,6 +255,26 @@ class Simulation:
         v, z = C.c_int(0), C.c_int(0)
         _check(lib().tlb_autotune(self.h, C.byref(v), C.byref(z)))
         return v.value, z.value
+
+    def run(self, max_steps: int, check_every: int = 100, tol: float = 1e-8):
+        """Step until the residual reaches ``tol`` (checked every
+        ``check_every`` steps) or ``max_steps``; returns (t, residual)."""
+        t, r = C.c_long(0), C.c_double(0)
+        _check(lib().tlb_run(self.h, int(max_steps), int(check_every), float(tol), C.byref(t), C.byref(r)))
+        return t.value, r.value
+
+    def save(self) -> np.ndarray:
+        """Checkpoint (host bytes) from which ``load`` resumes exactly."""
+        n = C.c_size_t(0)
+        _check(lib().tlb_save(self.h, None, C.byref(n)))
+        blob = np.empty(n.value, dtype=np.uint8)
+        _check(lib().tlb_save(self.h, C.c_void_p(blob.ctypes.data), C.byref(n)))
+        return blob
+
+    def load(self, blob):
+        b = np.ascontiguousarray(blob, dtype=np.uint8)
+        _check(lib().tlb_load(self.h, C.c_void_p(b.ctypes.data), b.size))
+        return self
 
     def set_tile(self, variant: int, z_chunk: int):
         _check(lib().tlb_set_tile(self.h, int(variant), int(z_chunk)))
