@@ -340,6 +340,9 @@ tlb_status tlb_create(const tlb_params* params, const tlb_membrane_desc* mems, i
     int lo_prio = 0, hi_prio = 0;
     cudaDeviceGetStreamPriorityRange(&lo_prio, &hi_prio);
     tlb_status r0 = cuda_check(cudaStreamCreateWithPriority(&c->side, cudaStreamNonBlocking, hi_prio), "side stream");
+    if (r0 == TLB_OK)
+      r0 = cuda_check(cudaStreamCreateWithPriority(&c->side2, cudaStreamNonBlocking, hi_prio), "side stream");
+    if (r0 == TLB_OK) r0 = cuda_check(cudaEventCreateWithFlags(&c->ev_bins, cudaEventDisableTiming), "event");
     if (r0 == TLB_OK) r0 = cuda_check(cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming), "event");
     if (r0 == TLB_OK) r0 = cuda_check(cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming), "event");
     if (r0 == TLB_OK) r0 = cuda_check(cudaEventCreateWithFlags(&c->ev_mom, cudaEventDisableTiming), "event");

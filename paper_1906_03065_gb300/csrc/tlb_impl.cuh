@@ -425,11 +425,13 @@ struct Impl : ImplBase {
       c->box_stale = false;
       if ((st = mark(c, 0)) != TLB_OK) return st;
       const bool overlap = c->nn > 0 && !c->prof;
-      if (c->nn > 0) {  // fork: position-only membrane work on the side stream
+      if (c->nn > 0) {  // fork: position-only membrane work on the two side streams
         TLB_CUDA(cudaEventRecord(c->ev_fork, s));
         TLB_CUDA(cudaStreamWaitEvent(c->side, c->ev_fork, 0));
+        TLB_CUDA(cudaStreamWaitEvent(c->side2, c->ev_fork, 0));
         if ((st = ibm_positions(c, ia, c->side)) != TLB_OK) return st;
-        if ((st = ibm_bins(c, ia, c->side)) != TLB_OK) return st;
+        if ((st = ibm_bins(c, ia, c->side2)) != TLB_OK) return st;
+        TLB_CUDA(cudaEventRecord(c->ev_bins, c->side2));
       }
       k_moments<L, MODE><<<blocks(N, 256), 256, 0, s>>>(la);
       TLB_LAUNCHED(c, "k_moments");
@@ -441,6 +443,7 @@ struct Impl : ImplBase {
         TLB_CUDA(cudaEventRecord(c->ev_mom, s));
         TLB_CUDA(cudaStreamWaitEvent(c->side, c->ev_mom, 0));
         if ((st = ibm_band(c, ia, c->side)) != TLB_OK) return st;
+        TLB_CUDA(cudaStreamWaitEvent(c->side, c->ev_bins, 0));  // forces and bricks
         if ((st = ibm_spread(c, ia, c->side)) != TLB_OK) return st;
         TLB_CUDA(cudaEventRecord(c->ev_join, c->side));
         la.region = 1;
@@ -453,6 +456,7 @@ struct Impl : ImplBase {
         if (c->nn > 0) {  // serial order (used when timing the phases)
           TLB_CUDA(cudaEventRecord(c->ev_join, c->side));
           TLB_CUDA(cudaStreamWaitEvent(s, c->ev_join, 0));
+          TLB_CUDA(cudaStreamWaitEvent(s, c->ev_bins, 0));
           if ((st = ibm_band(c, ia, s)) != TLB_OK) return st;
           if ((st = ibm_spread(c, ia, s)) != TLB_OK) return st;
         }
