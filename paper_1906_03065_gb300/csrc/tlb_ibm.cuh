@@ -355,49 +355,78 @@ __device__ __forceinline__ void dist_scatter_body(const IBArgs<Real>& a, const B
   const V3<Real> v0 = mk<Real>(sV[w][0][0], sV[w][0][1], sV[w][0][2]);
   const V3<Real> v1 = mk<Real>(sV[w][1][0], sV[w][1][1], sV[w][1][2]);
   const V3<Real> v2 = a.NV == 3 ? mk<Real>(sV[w][2][0], sV[w][2][1], sV[w][2][2]) : v1;
-  for (int c = c0 + lane; c <= c1; c += 32) {
-    Real lo0 = 1e30f, hi0 = -1e30f, lo1 = 1e30f, hi1 = -1e30f;
-    for (int q = 0; q < nB; ++q) {
-      if (!wide) {
-        for (int j = 0; j < nG; ++j) {
-          Real t = ((Real)c - sB[w][q][k]) / sG[w][j][k];
-          Real pa = sB[w][q][oa] + t * sG[w][j][oa], pb = sB[w][q][ob] + t * sG[w][j][ob];
-          lo0 = fmin(lo0, pa); hi0 = fmax(hi0, pa);
-          lo1 = fmin(lo1, pb); hi1 = fmax(hi1, pb);
+  // Up to 32 slices at a time: every lane sizes one slice's rectangle, a
+  // warp prefix sum lays the rectangles' cells end to end, and the lanes take
+  // the cells round-robin (slices near the feature are small, far ones in a
+  // widening cone large: per-slice loops would leave most lanes idle).
+  for (int base = c0; base <= c1; base += 32) {
+    const int c = base + lane;
+    int a0 = 0, b0 = 0, wa = 1, cnt = 0;
+    if (c <= c1) {
+      Real lo0 = 1e30f, hi0 = -1e30f, lo1 = 1e30f, hi1 = -1e30f;
+      for (int q = 0; q < nB; ++q) {
+        if (!wide) {
+          for (int j = 0; j < nG; ++j) {
+            Real t = ((Real)c - sB[w][q][k]) / sG[w][j][k];
+            Real pa = sB[w][q][oa] + t * sG[w][j][oa], pb = sB[w][q][ob] + t * sG[w][j][ob];
+            lo0 = fmin(lo0, pa); hi0 = fmax(hi0, pa);
+            lo1 = fmin(lo1, pb); hi1 = fmax(hi1, pb);
+          }
+        } else {  // conservative: the feature's box widened by dc
+          lo0 = fmin(lo0, sB[w][q][oa] - dc); hi0 = fmax(hi0, sB[w][q][oa] + dc);
+          lo1 = fmin(lo1, sB[w][q][ob] - dc); hi1 = fmax(hi1, sB[w][q][ob] + dc);
         }
-      } else {  // conservative: the feature's box widened by dc
-        lo0 = fmin(lo0, sB[w][q][oa] - dc); hi0 = fmax(hi0, sB[w][q][oa] + dc);
-        lo1 = fmin(lo1, sB[w][q][ob] - dc); hi1 = fmax(hi1, sB[w][q][ob] + dc);
       }
-    }
-    const int a0 = (int)ceil(lo0 - eps), a1 = (int)floor(hi0 + eps);
-    int b0 = 0, b1 = 0;
-    if (a.dim == 3) { b0 = (int)ceil(lo1 - eps); b1 = (int)floor(hi1 + eps); }
-    const int wa = a1 - a0 + 1, wb = b1 - b0 + 1;
-    if (wa <= 0 || wb <= 0) continue;
-    if (wa > 1024 || wb > 1024) {  // bounded work even for a badly deformed mesh
-      atomicOr(a.status, (unsigned)ST_OVERFLOW);
-      continue;
-    }
-    for (int ib = b0; ib <= b1; ++ib)
-      for (int ia = a0; ia <= a1; ++ia) {
-        int r[3];
-        r[k] = c;
-        r[oa] = ia;
-        if (a.dim == 3) r[ob] = ib; else r[1] = 0;
-        int pc[3] = {o[0] + r[0], o[1] + r[1], o[2] + r[2]};
-        long long cell = cell_of(a, pc);
-        if (cell < 0) continue;
-        const V3<Real> x = mk<Real>((Real)r[0], (Real)r[1], (Real)r[2]);
-        Real beta[3];
-        int feat;
-        V3<Real> P = a.NV == 2 ? closest_on_seg(v0 - x, v1 - x, beta, &feat)
-                               : closest_on_tri(v0 - x, v1 - x, v2 - x, beta, &feat);
-        Real d = sqrt(dot(P, P));
-        if (!(d < dc)) continue;
-        unsigned long long key = ((unsigned long long)(d * Real(17179869184.0)) << 24) | (unsigned long long)tmin;
-        if (key < a.key[cell]) atomicMin(a.key + cell, key);
+      a0 = (int)ceil(lo0 - eps);
+      const int a1 = (int)floor(hi0 + eps);
+      int b1 = 0;
+      if (a.dim == 3) { b0 = (int)ceil(lo1 - eps); b1 = (int)floor(hi1 + eps); }
+      const int wb = b1 - b0 + 1;
+      wa = a1 - a0 + 1;
+      if (wa > 0 && wb > 0) {
+        if (wa > 1024 || wb > 1024) atomicOr(a.status, (unsigned)ST_OVERFLOW);  // bounded work, flagged
+        else cnt = wa * wb;
       }
+      if (cnt == 0) wa = 1;
+    }
+    int incl = cnt;
+#pragma unroll
+    for (int sh = 1; sh < 32; sh <<= 1) {
+      const int v = __shfl_up_sync(0xffffffffu, incl, sh);
+      if (lane >= sh) incl += v;
+    }
+    const int total = __shfl_sync(0xffffffffu, incl, 31);
+    for (int i0 = 0; i0 < total; i0 += 32) {
+      const int i = i0 + lane;
+      // slice of cell i: the first lane whose inclusive prefix exceeds i
+      int L = 0;
+#pragma unroll
+      for (int step = 16; step >= 1; step >>= 1) {
+        const int v = __shfl_sync(0xffffffffu, incl, L + step - 1);
+        if (v <= i) L += step;
+      }
+      const int inclL = __shfl_sync(0xffffffffu, incl, L), cntL = __shfl_sync(0xffffffffu, cnt, L);
+      const int a0L = __shfl_sync(0xffffffffu, a0, L), b0L = __shfl_sync(0xffffffffu, b0, L);
+      const int waL = __shfl_sync(0xffffffffu, wa, L);
+      if (i >= total) continue;
+      const int jj = i - (inclL - cntL);
+      int r[3];
+      r[k] = base + L;
+      r[oa] = a0L + jj % waL;
+      if (a.dim == 3) r[ob] = b0L + jj / waL; else r[1] = 0;
+      int pc[3] = {o[0] + r[0], o[1] + r[1], o[2] + r[2]};
+      long long cell = cell_of(a, pc);
+      if (cell < 0) continue;
+      const V3<Real> x = mk<Real>((Real)r[0], (Real)r[1], (Real)r[2]);
+      Real beta[3];
+      int feat;
+      V3<Real> P = a.NV == 2 ? closest_on_seg(v0 - x, v1 - x, beta, &feat)
+                             : closest_on_tri(v0 - x, v1 - x, v2 - x, beta, &feat);
+      Real d = sqrt(dot(P, P));
+      if (!(d < dc)) continue;
+      unsigned long long key = ((unsigned long long)(d * Real(17179869184.0)) << 24) | (unsigned long long)tmin;
+      if (key < a.key[cell]) atomicMin(a.key + cell, key);
+    }
   }
 }
 template <class Real>
