@@ -267,6 +267,8 @@ static void plan(const tlb_params* p, const std::vector<HostMem>& mems, Ctx& c) 
   take(L.ring, NV * ne * 4);
   take(L.en, 3 * ne * R);
   take(L.vn, 3 * nn * R);
+  take(L.erel, 3 * NV * ne * R);
+  take(L.eorg, 3 * ne * 4);
   take(L.esum, 3 * NV * ne * 8);
   take(L.F, 3 * nn * R);
   take(L.box, 12 * 4);

@@ -37,6 +37,8 @@ struct IBArgs {
   // per-step work
   Real* en;              // [ne][3] unit outward normal
   Real* vn;              // [nn][3] angle-weighted vertex pseudo-normal
+  Real* erel;            // [ne][NV][3] vertices relative to the element's origin
+  int* eorg;             // [ne][3] element origin: floor of its first vertex
   unsigned long long* esum;  // [ne][NV][3] coupling contributions, fixed point (CPL_SCALE)
   Real* F;               // [nn][3] node force
   int* box;              // [6] marker box accumulator: floor(min X), -ceil(max X)
@@ -131,18 +133,19 @@ __device__ __forceinline__ V3<Real> closest_on_tri(V3<Real> a, V3<Real> b, V3<Re
   return a + v * ab + w * ac;
 }
 
-// Closest point of cell (cx, cy, cz) (unwrapped) on element e.
+// Closest point of cell p (unwrapped) on element e, relative to the cell:
+// the vertices come from the step's element-relative copy (erel, eorg), so
+// that a cell needs no double-precision arithmetic (in FP64 this is the
+// same single rounding of X - p as a direct difference).
 template <class Real>
-__device__ __forceinline__ V3<Real> elem_closest(const IBArgs<Real>& a, int e, double cx, double cy, double cz,
-                                                 Real* beta, int* feat) {
-  if (a.NV == 2) {
-    V3<Real> p0 = node_rel<Real>(a.X, a.E[2 * e], cx, cy, cz);
-    V3<Real> p1 = node_rel<Real>(a.X, a.E[2 * e + 1], cx, cy, cz);
-    return closest_on_seg(p0, p1, beta, feat);
-  }
-  V3<Real> p0 = node_rel<Real>(a.X, a.E[3 * e], cx, cy, cz);
-  V3<Real> p1 = node_rel<Real>(a.X, a.E[3 * e + 1], cx, cy, cz);
-  V3<Real> p2 = node_rel<Real>(a.X, a.E[3 * e + 2], cx, cy, cz);
+__device__ __forceinline__ V3<Real> elem_closest(const IBArgs<Real>& a, int e, const int* p, Real* beta, int* feat) {
+  const Real* r = a.erel + 3 * a.NV * e;
+  const int* o = a.eorg + 3 * e;
+  const Real sx = (Real)(o[0] - p[0]), sy = (Real)(o[1] - p[1]), sz = (Real)(o[2] - p[2]);
+  V3<Real> p0 = mk<Real>(r[0] + sx, r[1] + sy, r[2] + sz);
+  V3<Real> p1 = mk<Real>(r[3] + sx, r[4] + sy, r[5] + sz);
+  if (a.NV == 2) return closest_on_seg(p0, p1, beta, feat);
+  V3<Real> p2 = mk<Real>(r[6] + sx, r[7] + sy, r[8] + sz);
   return closest_on_tri(p0, p1, p2, beta, feat);
 }
 
@@ -176,6 +179,12 @@ __device__ __forceinline__ void geometry_body(const IBArgs<Real>& a, const Blk& 
     a.en[3 * t] = n.x;
     a.en[3 * t + 1] = n.y;
     a.en[3 * t + 2] = n.z;
+    const int* Et = a.E + a.NV * t;
+    for (int d = 0; d < 3; ++d) {
+      const int o = (int)floor(fmax(-1e8, fmin(1e8, a.X[3 * Et[0] + d])));
+      a.eorg[3 * t + d] = o;
+      for (int q = 0; q < a.NV; ++q) a.erel[3 * (a.NV * t + q) + d] = (Real)(a.X[3 * Et[q] + d] - (double)o);
+    }
     return;
   }
   int k = t - a.ne;
@@ -230,13 +239,62 @@ __device__ __forceinline__ void profile_box(const IBArgs<Real>& a, int* lo, int*
   marker_box(a.boxc, (int)ceil((double)a.dc) + 2, a.G, a.dim == 2, lo, hi);
 }
 
+// Wrap a coordinate into [0, n): a compare and add within one period of the
+// range, the division beyond it.
+__device__ __forceinline__ int wrap_coord(int v, int n) {
+  if (v < 0) v += n;
+  else if (v >= n) v -= n;
+  if ((unsigned)v >= (unsigned)n) {
+    v %= n;
+    if (v < 0) v += n;
+  }
+  return v;
+}
+
 template <class Real>
 __device__ __forceinline__ long long cell_of(const IBArgs<Real>& a, const int* pc) {
   if (a.G.wall && (pc[2] < 0 || pc[2] >= a.G.nz)) return -1;
-  int x = ((pc[0] % a.G.nx) + a.G.nx) % a.G.nx;
-  int y = ((pc[1] % a.G.ny) + a.G.ny) % a.G.ny;
-  int z = ((pc[2] % a.G.nz) + a.G.nz) % a.G.nz;
+  const int x = wrap_coord(pc[0], a.G.nx), y = wrap_coord(pc[1], a.G.ny), z = wrap_coord(pc[2], a.G.nz);
   return ((long long)z * a.G.ny + y) * a.G.nx + x;
+}
+
+// Fixed-point conversions from the bits of an FP32 value, equal to the
+// conversions of the exactly scaled number (v * 2^s) that the FP64 path
+// makes, without FP64 arithmetic (a slow pipe on this GPU).
+// floor(v 2^s) for finite v >= 0, v 2^s < 2^63:
+__device__ __forceinline__ unsigned long long scaled_floor_u64(float v, int s) {
+  const unsigned b = __float_as_uint(v);
+  int e = (int)((b >> 23) & 0xFFu);
+  unsigned long long m = b & 0x7FFFFFu;
+  if (e) m |= 0x800000u;
+  else e = 1;
+  const int sh = e - 150 + s;  // v = m 2^(e - 150)
+  return sh >= 0 ? m << sh : (sh > -24 ? m >> -sh : 0ull);
+}
+// rint(v 2^s), ties to even; saturates at +-2^62:
+__device__ __forceinline__ long long scaled_rint_s64(float v, int s) {
+  const unsigned b = __float_as_uint(v);
+  int e = (int)((b >> 23) & 0xFFu);
+  unsigned long long m = b & 0x7FFFFFu;
+  if (e) m |= 0x800000u;
+  else e = 1;
+  const int sh = e - 150 + s;
+  unsigned long long r;
+  if (sh >= 0) {
+    r = sh <= 38 ? m << sh : (1ull << 62);
+  } else if (sh >= -24) {
+    const int k = -sh;
+    const unsigned long long q = m >> k, rem = m - (q << k), half = 1ull << (k - 1);
+    r = q + ((rem > half || (rem == half && (q & 1ull))) ? 1ull : 0ull);
+  } else {
+    r = 0;
+  }
+  return (b >> 31) ? -(long long)r : (long long)r;
+}
+// distance part of a scatter key: the distance on a grid of 2^-34
+__device__ __forceinline__ unsigned long long dist_code(float d) { return scaled_floor_u64(d, 34); }
+__device__ __forceinline__ unsigned long long dist_code(double d) {
+  return (unsigned long long)(d * 17179869184.0);
 }
 
 // ------------------------------------------------------------ distance scatter
@@ -313,6 +371,8 @@ __device__ __forceinline__ void dist_scatter_body(const IBArgs<Real>& a, const B
   int o[3];
   for (int d = 0; d < 3; ++d) o[d] = (int)floor(fmax(-1e8, fmin(1e8, a.X[3 * corners[0] + d])));
   if (a.dim == 2) o[1] = 0;
+  // the origin's cell wrapped into the lattice (offers index cells from it)
+  const int ow[3] = {wrap_coord(o[0], a.G.nx), wrap_coord(o[1], a.G.ny), a.G.wall ? o[2] : wrap_coord(o[2], a.G.nz)};
   if (lane < 9) {
     int q = lane / 3, d = lane % 3;
     if (q < a.NV) sV[w][q][d] = (Real)(a.X[3 * a.E[a.NV * tmin + q] + d] - (double)o[d]);
@@ -362,6 +422,7 @@ __device__ __forceinline__ void dist_scatter_body(const IBArgs<Real>& a, const B
   for (int base = c0; base <= c1; base += 32) {
     const int c = base + lane;
     int a0 = 0, b0 = 0, wa = 1, cnt = 0;
+    float rwa = 1.0f;
     if (c <= c1) {
       Real lo0 = 1e30f, hi0 = -1e30f, lo1 = 1e30f, hi1 = -1e30f;
       for (int q = 0; q < nB; ++q) {
@@ -388,6 +449,7 @@ __device__ __forceinline__ void dist_scatter_body(const IBArgs<Real>& a, const B
         else cnt = wa * wb;
       }
       if (cnt == 0) wa = 1;
+      rwa = 1.0f / (float)wa;
     }
     int incl = cnt;
 #pragma unroll
@@ -408,13 +470,18 @@ __device__ __forceinline__ void dist_scatter_body(const IBArgs<Real>& a, const B
       const int inclL = __shfl_sync(0xffffffffu, incl, L), cntL = __shfl_sync(0xffffffffu, cnt, L);
       const int a0L = __shfl_sync(0xffffffffu, a0, L), b0L = __shfl_sync(0xffffffffu, b0, L);
       const int waL = __shfl_sync(0xffffffffu, wa, L);
+      const float rwaL = __shfl_sync(0xffffffffu, rwa, L);
       if (i >= total) continue;
       const int jj = i - (inclL - cntL);
+      // jj / waL: jj < 2^20 and waL <= 1024 keep the product within 2^-13 of
+      // the true (jj + 1/2) / waL, whose fraction is at least 2^-11 from an
+      // integer, so the truncation is exact
+      const int qb = (int)(((float)jj + 0.5f) * rwaL);
       int r[3];
       r[k] = base + L;
-      r[oa] = a0L + jj % waL;
-      if (a.dim == 3) r[ob] = b0L + jj / waL; else r[1] = 0;
-      int pc[3] = {o[0] + r[0], o[1] + r[1], o[2] + r[2]};
+      r[oa] = a0L + (jj - qb * waL);
+      if (a.dim == 3) r[ob] = b0L + qb; else r[1] = 0;
+      int pc[3] = {ow[0] + r[0], ow[1] + r[1], ow[2] + r[2]};
       long long cell = cell_of(a, pc);
       if (cell < 0) continue;
       const V3<Real> x = mk<Real>((Real)r[0], (Real)r[1], (Real)r[2]);
@@ -424,7 +491,7 @@ __device__ __forceinline__ void dist_scatter_body(const IBArgs<Real>& a, const B
                              : closest_on_tri(v0 - x, v1 - x, v2 - x, beta, &feat);
       Real d = sqrt(dot(P, P));
       if (!(d < dc)) continue;
-      unsigned long long key = ((unsigned long long)(d * Real(17179869184.0)) << 24) | (unsigned long long)tmin;
+      unsigned long long key = (dist_code(d) << 24) | (unsigned long long)tmin;
       if (key < a.key[cell]) atomicMin(a.key + cell, key);
     }
   }
@@ -457,6 +524,8 @@ __device__ __forceinline__ Real feature_sign(const IBArgs<Real>& a, int e, int f
 // Fixed-point scale of the coupling sums: integer additions make the
 // per-element totals independent of the order of the contributions.
 #define CPL_SCALE 1125899906842624.0  // 2^50
+__device__ __forceinline__ long long cpl_fixed(float v) { return scaled_rint_s64(v, 50); }
+__device__ __forceinline__ long long cpl_fixed(double v) { return llrint(v * CPL_SCALE); }
 
 // Band cells of the marker box (one thread per cell, x fastest): signed
 // distance from the nearest element, I = (1 + tanh(d/(2 alpha)))/2 (eq.
@@ -475,14 +544,30 @@ __device__ __forceinline__ void band_body(const IBArgs<Real>& a, const Blk& blk)
   const long long total = (long long)wx * wy * wz;
   const bool full[3] = {wx == a.G.nx, a.dim == 3 && wy == a.G.ny, !a.G.wall && wz == a.G.nz};
   const Real al = a.alpha;
+  // the box origin wrapped into the lattice: cells are indexed from it, the
+  // geometry uses the unwrapped coordinates
+  const int ox = wrap_coord(bx0, a.G.nx), oy = wrap_coord(by0, a.G.ny), oz = a.G.wall ? bz0 : wrap_coord(bz0, a.G.nz);
+  const bool narrow = total <= 0xFFFFFFFFll;
   const long long stride = (long long)blk.gx * blockDim.x;
   for (long long t0 = (long long)blk.x * blockDim.x; t0 < total; t0 += stride) {
     const long long t = t0 + threadIdx.x;
     int e = -1;
     Real acc[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
     if (t < total) {
-      int pc[3] = {bx0 + (int)(t % wx), by0 + (int)((t / wx) % wy), bz0 + (int)(t / ((long long)wx * wy))};
-      long long c = cell_of(a, pc);
+      int ix, iy, iz;
+      if (narrow) {  // 32-bit division
+        const unsigned tt = (unsigned)t, row = tt / (unsigned)wx, zz = row / (unsigned)wy;
+        ix = (int)(tt - row * (unsigned)wx);
+        iy = (int)(row - zz * (unsigned)wy);
+        iz = (int)zz;
+      } else {
+        ix = (int)(t % wx);
+        iy = (int)((t / wx) % wy);
+        iz = (int)(t / ((long long)wx * wy));
+      }
+      const int pc[3] = {bx0 + ix, by0 + iy, bz0 + iz};
+      const int pw[3] = {ox + ix, oy + iy, oz + iz};
+      long long c = cell_of(a, pw);
       if (c >= 0) {
         unsigned long long key = a.key[c];
         if (key == KEY_NONE) {
@@ -497,14 +582,16 @@ __device__ __forceinline__ void band_body(const IBArgs<Real>& a, const Blk& blk)
           // the image of the cell nearest to the element (unique, as
           // periodic sides are at least 2 dc + 8).  A box narrower than the
           // period holds every band cell at that image already.
-          int px = pc[0], py = pc[1], pz = pc[2];
+          // (the element origin, floor of its first vertex, is within a cell
+          // of it: the nearest image is the same)
+          int pi[3] = {pc[0], pc[1], pc[2]};
           if (full[0] | full[1] | full[2]) {
-            const double* x0 = a.X + 3 * a.E[a.NV * e];
-            if (full[0]) px += a.G.nx * __float2int_rn((float)(x0[0] - px) / (float)a.G.nx);
-            if (full[1]) py += a.G.ny * __float2int_rn((float)(x0[1] - py) / (float)a.G.ny);
-            if (full[2]) pz += a.G.nz * __float2int_rn((float)(x0[2] - pz) / (float)a.G.nz);
+            const int* eo = a.eorg + 3 * e;
+            if (full[0]) pi[0] += a.G.nx * __float2int_rn((float)(eo[0] - pi[0]) / (float)a.G.nx);
+            if (full[1]) pi[1] += a.G.ny * __float2int_rn((float)(eo[1] - pi[1]) / (float)a.G.ny);
+            if (full[2]) pi[2] += a.G.nz * __float2int_rn((float)(eo[2] - pi[2]) / (float)a.G.nz);
           }
-          V3<Real> P = elem_closest(a, e, (double)px, (double)py, (double)pz, beta, &feat);
+          V3<Real> P = elem_closest(a, e, pi, beta, &feat);
           V3<Real> xmP = mk<Real>(-P.x, -P.y, -P.z);
           Real dist = sqrt(dot(xmP, xmP));
           Real s = feature_sign(a, e, feat, xmP);
@@ -518,7 +605,8 @@ __device__ __forceinline__ void band_body(const IBArgs<Real>& a, const Blk& blk)
           V3<Real> dir;
           if (dist > Real(1e-12)) dir = (-s / dist) * xmP;
           else dir = mk<Real>(a.en[3 * e], a.en[3 * e + 1], a.en[3 * e + 2]);
-          for (int q = 0; q < a.NV; ++q) {
+#pragma unroll
+          for (int q = 0; q < 3; ++q) {  // beta[2] = 0 for segments
             acc[q][0] = coef * beta[q] * dir.x;
             acc[q][1] = coef * beta[q] * dir.y;
             acc[q][2] = coef * beta[q] * dir.z;
@@ -532,18 +620,23 @@ __device__ __forceinline__ void band_body(const IBArgs<Real>& a, const Blk& blk)
       const unsigned grp = __match_any_sync(active, e);
       const int leader = __ffs(grp) - 1;
       const int lane = threadIdx.x & 31;
-      for (int q = 0; q < a.NV; ++q)
-        for (int d = 0; d < 3; ++d) {
-          long long v = llrint((double)acc[q][d] * CPL_SCALE);
-          // sum over the group in lane order
-          long long s = 0;
-          for (unsigned m = grp; m; m &= m - 1) {
-            int src = __ffs(m) - 1;
-            long long w = __shfl_sync(grp, v, src);
-            s += w;
-          }
-          if (lane == leader && s != 0) atomicAdd(a.esum + (a.NV * e + q) * 3 + d, (unsigned long long)s);
-        }
+      long long v[9], sum[9];
+#pragma unroll
+      for (int i = 0; i < 9; ++i) {
+        v[i] = cpl_fixed(acc[i / 3][i % 3]);
+        sum[i] = 0;
+      }
+      // sum over the group (integers: any order gives the same total)
+      for (unsigned m = grp; m; m &= m - 1) {
+        const int src = __ffs(m) - 1;
+#pragma unroll
+        for (int i = 0; i < 9; ++i) sum[i] += __shfl_sync(grp, v[i], src);
+      }
+      if (lane == leader) {
+#pragma unroll
+        for (int i = 0; i < 9; ++i)
+          if (i < 3 * a.NV && sum[i] != 0) atomicAdd(a.esum + 3 * a.NV * e + i, (unsigned long long)sum[i]);
+      }
     }
   }
 }

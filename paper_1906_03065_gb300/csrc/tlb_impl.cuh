@@ -99,6 +99,8 @@ struct Impl : ImplBase {
     a.edges = c->ptr<int>(c->L.edges);
     a.en = c->ptr<Real>(c->L.en);
     a.vn = c->ptr<Real>(c->L.vn);
+    a.erel = c->ptr<Real>(c->L.erel);
+    a.eorg = c->ptr<int>(c->L.eorg);
     a.esum = c->ptr<unsigned long long>(c->L.esum);
     a.F = c->ptr<Real>(c->L.F);
     a.box = c->ptr<int>(c->L.box);
