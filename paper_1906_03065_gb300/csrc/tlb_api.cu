@@ -269,6 +269,10 @@ static void plan(const tlb_params* p, const std::vector<HostMem>& mems, Ctx& c) 
   take(L.vn, 3 * nn * R);
   take(L.erel, 3 * NV * ne * R);
   take(L.eorg, 3 * ne * 4);
+  take(L.xo, 3 * nn * 4);
+  take(L.xr, 3 * nn * R);
+  take(L.skc, 5 * ne * R);
+  take(L.capr, 4 * std::max(1, c.ncap) * R);
   take(L.esum, 3 * NV * ne * 8);
   take(L.F, 3 * nn * R);
   take(L.box, 12 * 4);
@@ -472,6 +476,24 @@ tlb_status tlb_create(const tlb_params* params, const tlb_membrane_desc* mems, i
     u = u != TLB_OK ? u : up(c->L.rnext, rnext.data(), rnext.size() * 4);
     u = u != TLB_OK ? u : up(c->L.A0, A0.data(), A0.size() * 8);
     u = u != TLB_OK ? u : up(c->L.G0i, G0i.data(), G0i.size() * 8);
+    // the elastic constants in the working precision (FP32 kernels read
+    // them without FP64 conversions)
+    {
+      std::vector<double> skc(5 * (size_t)c->ne, 0.0);
+      if (c->NV == 3)
+        for (int t = 0; t < c->ne; ++t) {
+          const double* Gi = &G0i[3 * (size_t)t];
+          const double k[5] = {Gi[0], 2.0 * Gi[1], Gi[2], Gi[0] * Gi[2] - Gi[1] * Gi[1], A0[t]};
+          for (int j = 0; j < 5; ++j) skc[5 * (size_t)t + j] = k[j];
+        }
+      auto up_real = [&](const Region& reg, const std::vector<double>& v) {
+        if (c->ts.real == 8) return up(reg, v.data(), v.size() * 8);
+        std::vector<float> f(v.begin(), v.end());
+        return up(reg, f.data(), f.size() * 4);
+      };
+      u = u != TLB_OK ? u : up_real(c->L.skc, skc);
+      u = u != TLB_OK ? u : up_real(c->L.capr, cap_par);
+    }
     u = u != TLB_OK ? u : up(c->L.inc_off, inc_off.data(), inc_off.size() * 4);
     u = u != TLB_OK ? u : up(c->L.inc, incl.data(), incl.size() * 4);
     u = u != TLB_OK ? u : up(c->L.adj, adj.data(), adj.size() * 4);

@@ -4,6 +4,8 @@
 // Spreading with eq. DiscreteDirac), interpolation and advection (eqs.
 // Interpolation, UpdatedXl).
 #pragma once
+#include <type_traits>
+
 #include "tlb_common.cuh"
 
 constexpr unsigned long long KEY_NONE = ~0ull;
@@ -15,6 +17,8 @@ struct IBArgs {
   int dim, NV;  // dim 2: segments (NV = 2); dim 3: triangles (NV = 3)
   int nn, ne;
   double* X;             // [nn][3] unwrapped positions
+  int* xo;               // [nn][3] floor(X) (kept by the box and advection kernels)
+  Real* xr;              // [nn][3] X - xo
   const int* E;          // [ne][NV]
   const int* ecap;       // element -> capsule
   const int* ncap;       // node -> capsule
@@ -27,6 +31,9 @@ struct IBArgs {
   const int* rnext;      // 2D: next node on the ring
   const double* A0;      // 3D: reference area per triangle
   const double* G0i;     // 3D: inverse reference metric per triangle (3)
+  const Real* skc;       // 3D: per triangle G0i[0], 2 G0i[1], G0i[2], det G0i, A0 (working precision)
+  const Real* capr;      // per capsule ks, kb, G, C (working precision), [4][ncaps]
+  int ncaps;
   const int* inc_off;    // node -> incident elements (CSR, ascending)
   const int* inc;
   const int* adj;        // 3D: triangle across edge q (q: vertex q -> q+1)
@@ -74,9 +81,37 @@ template <class T> TLB_HD V3<T> cross(V3<T> a, V3<T> b) {
   return {a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x};
 }
 
+// Marker coordinates in the working precision.  FP32 builds them from the
+// split X = xo + xr (integer cell, fraction) so that the per-step kernels
+// issue no FP64 instructions (a slow pipe on this GPU); FP64 subtracts the
+// positions directly.
+// X_j - X_k along axis d:
 template <class Real>
-__device__ __forceinline__ V3<Real> node_rel(const double* X, int k, double ox, double oy, double oz) {
-  return mk<Real>((Real)(X[3 * k] - ox), (Real)(X[3 * k + 1] - oy), (Real)(X[3 * k + 2] - oz));
+__device__ __forceinline__ Real node_dx(const IBArgs<Real>& a, int j, int k, int d) {
+  if constexpr (std::is_same<Real, float>::value)
+    return (float)(a.xo[3 * j + d] - a.xo[3 * k + d]) + (a.xr[3 * j + d] - a.xr[3 * k + d]);
+  else
+    return a.X[3 * j + d] - a.X[3 * k + d];
+}
+template <class Real>
+__device__ __forceinline__ V3<Real> node_dv(const IBArgs<Real>& a, int j, int k) {
+  return mk<Real>(node_dx(a, j, k, 0), node_dx(a, j, k, 1), node_dx(a, j, k, 2));
+}
+// X_l - o along axis d for an integer o:
+template <class Real>
+__device__ __forceinline__ Real node_off(const IBArgs<Real>& a, int l, int d, int o) {
+  if constexpr (std::is_same<Real, float>::value)
+    return (float)(a.xo[3 * l + d] - o) + a.xr[3 * l + d];
+  else
+    return a.X[3 * l + d] - (double)o;
+}
+// the split of one coordinate (clamped like the marker box)
+template <class Real>
+__device__ __forceinline__ void split_coord(double x, int* xo, Real* xr) {
+  const double v = fmax(-1e8, fmin(1e8, x));
+  const double f = floor(v);
+  *xo = (int)f;
+  *xr = (Real)(v - f);
 }
 
 // Closest point of the origin on segment (a, b) or triangle (a, b, c)
@@ -155,13 +190,13 @@ template <class Real>
 __device__ __forceinline__ V3<Real> face_normal(const IBArgs<Real>& a, int e) {
   if (a.NV == 2) {
     int p = a.E[2 * e], q = a.E[2 * e + 1];
-    Real tx = (Real)(a.X[3 * q] - a.X[3 * p]), tz = (Real)(a.X[3 * q + 2] - a.X[3 * p + 2]);
+    Real tx = node_dx(a, q, p, 0), tz = node_dx(a, q, p, 2);
     Real l = sqrt(tx * tx + tz * tz);
     return mk<Real>(tz / l, Real(0), -tx / l);
   }
   int p = a.E[3 * e], q = a.E[3 * e + 1], r = a.E[3 * e + 2];
-  V3<Real> b = node_rel<Real>(a.X, q, a.X[3 * p], a.X[3 * p + 1], a.X[3 * p + 2]);
-  V3<Real> c = node_rel<Real>(a.X, r, a.X[3 * p], a.X[3 * p + 1], a.X[3 * p + 2]);
+  V3<Real> b = node_dv(a, q, p);
+  V3<Real> c = node_dv(a, r, p);
   V3<Real> cr = cross(b, c);
   return (Real(1) / sqrt(dot(cr, cr))) * cr;
 }
@@ -181,9 +216,9 @@ __device__ __forceinline__ void geometry_body(const IBArgs<Real>& a, const Blk& 
     a.en[3 * t + 2] = n.z;
     const int* Et = a.E + a.NV * t;
     for (int d = 0; d < 3; ++d) {
-      const int o = (int)floor(fmax(-1e8, fmin(1e8, a.X[3 * Et[0] + d])));
+      const int o = a.xo[3 * Et[0] + d];
       a.eorg[3 * t + d] = o;
-      for (int q = 0; q < a.NV; ++q) a.erel[3 * (a.NV * t + q) + d] = (Real)(a.X[3 * Et[q] + d] - (double)o);
+      for (int q = 0; q < a.NV; ++q) a.erel[3 * (a.NV * t + q) + d] = node_off(a, Et[q], d, o);
     }
     return;
   }
@@ -198,8 +233,8 @@ __device__ __forceinline__ void geometry_body(const IBArgs<Real>& a, const Blk& 
       int q0 = a.E[3 * e], q1 = a.E[3 * e + 1], q2 = a.E[3 * e + 2];
       int u = q0 == k ? q1 : (q1 == k ? q2 : q0);
       int v = q0 == k ? q2 : (q1 == k ? q0 : q1);
-      V3<Real> eu = node_rel<Real>(a.X, u, a.X[3 * k], a.X[3 * k + 1], a.X[3 * k + 2]);
-      V3<Real> ev = node_rel<Real>(a.X, v, a.X[3 * k], a.X[3 * k + 1], a.X[3 * k + 2]);
+      V3<Real> eu = node_dv(a, u, k);
+      V3<Real> ev = node_dv(a, v, k);
       Real c = dot(eu, ev) / sqrt(dot(eu, eu) * dot(ev, ev));
       wgt = acos(fmin(Real(1), fmax(Real(-1), c)));
     }
@@ -216,7 +251,8 @@ __global__ void k_geometry(const __grid_constant__ IBArgs<Real> a) {
 
 // Marker bounding box.  The advection kernel accumulates floor(min X) and
 // -ceil(max X) per axis with integer atomicMin into box[0..5] (reset to a
-// large value after use); k_box does the same from scratch at set-up.
+// large value after use); k_box does the same from scratch at set-up, and
+// both store the split X = xo + xr of the positions.
 template <class Real>
 __device__ __forceinline__ void box_body(const IBArgs<Real>& a, const Blk& blk) {
   int k = blk.x * blockDim.x + threadIdx.x;
@@ -225,6 +261,7 @@ __device__ __forceinline__ void box_body(const IBArgs<Real>& a, const Blk& blk) 
     double v = fmax(-1e8, fmin(1e8, a.X[3 * k + d]));
     atomicMin(a.box + d, (int)floor(v));
     atomicMin(a.box + 3 + d, -(int)ceil(v));
+    split_coord(a.X[3 * k + d], a.xo + 3 * k + d, a.xr + 3 * k + d);
   }
 }
 template <class Real>
@@ -236,7 +273,7 @@ __global__ void k_box(const __grid_constant__ IBArgs<Real> a) {
 // dc + 2 cells (unwrapped; walls clamp z; at most one period per axis).
 template <class Real>
 __device__ __forceinline__ void profile_box(const IBArgs<Real>& a, int* lo, int* hi) {
-  marker_box(a.boxc, (int)ceil((double)a.dc) + 2, a.G, a.dim == 2, lo, hi);
+  marker_box(a.boxc, (int)ceil(a.dc) + 2, a.G, a.dim == 2, lo, hi);
 }
 
 // Wrap a coordinate into [0, n): a compare and add within one period of the
@@ -369,14 +406,14 @@ __device__ __forceinline__ void dist_scatter_body(const IBArgs<Real>& a, const B
   int tmin = tri[0];
   for (int j = 1; j < nT; ++j) tmin = min(tmin, tri[j]);
   int o[3];
-  for (int d = 0; d < 3; ++d) o[d] = (int)floor(fmax(-1e8, fmin(1e8, a.X[3 * corners[0] + d])));
+  for (int d = 0; d < 3; ++d) o[d] = a.xo[3 * corners[0] + d];
   if (a.dim == 2) o[1] = 0;
   // the origin's cell wrapped into the lattice (offers index cells from it)
   const int ow[3] = {wrap_coord(o[0], a.G.nx), wrap_coord(o[1], a.G.ny), a.G.wall ? o[2] : wrap_coord(o[2], a.G.nz)};
   if (lane < 9) {
     int q = lane / 3, d = lane % 3;
-    if (q < a.NV) sV[w][q][d] = (Real)(a.X[3 * a.E[a.NV * tmin + q] + d] - (double)o[d]);
-    if (q < nB) sB[w][q][d] = (Real)(a.X[3 * corners[q] + d] - (double)o[d]);
+    if (q < a.NV) sV[w][q][d] = node_off(a, a.E[a.NV * tmin + q], d, o[d]);
+    if (q < nB) sB[w][q][d] = node_off(a, corners[q], d, o[d]);
   }
   for (int idx = lane; idx < nG * 3; idx += 32) sG[w][idx / 3][idx % 3] = a.en[3 * tri[idx / 3] + idx % 3];
   __syncwarp();
@@ -662,32 +699,44 @@ __device__ __forceinline__ void fill_body(const IBArgs<Real>& a, const Blk& blk)
   const Real dc = a.dc, al = a.alpha;
   const Real Iin = Real(0.5) * (Real(1) + tanh(dc / (Real(2) * al)));
   const Real Iout = Real(0.5) * (Real(1) + tanh(-dc / (Real(2) * al)));
-  int pc[3] = {bx0 + col % wx, by0 + col / wx, 0};
+  const Geo& G = a.G;
+  const long long colc = (long long)wrap_coord(by0 + col / wx, G.ny) * G.nx + wrap_coord(bx0 + col % wx, G.nx);
+  const long long plane = (long long)G.nx * G.ny;
   bool inside = false;  // status carried from the chunk below
-  for (int z0 = 0; z0 < wz; z0 += 32) {
-    const int z = z0 + lane;
-    long long c = -1;
-    bool band = false, sgn = false;
-    if (z < wz) {
-      pc[2] = bz0 + z;
-      c = cell_of(a, pc);
-      if (c >= 0) {
-        band = a.own[c] >= 0;
-        if (band) sgn = a.dsel[c] > Real(0);
+  for (int z0 = 0; z0 < wz; z0 += 128) {
+    // the loads of up to four chunks of 32 cells first (dsel is read for
+    // every cell, used for band cells only), then the scans
+    long long cq[4];
+    int ownq[4];
+    Real dq[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int z = z0 + 32 * q + lane, pz = bz0 + z;
+      cq[q] = -1;
+      ownq[q] = -1;
+      dq[q] = 0;
+      if (z < wz && (!G.wall || (pz >= 0 && pz < G.nz))) {
+        cq[q] = (long long)(G.wall ? pz : wrap_coord(pz, G.nz)) * plane + colc;
+        ownq[q] = a.own[cq[q]];
+        dq[q] = a.dsel[cq[q]];
       }
     }
-    const unsigned bm = __ballot_sync(0xffffffffu, band);
-    const unsigned sm = __ballot_sync(0xffffffffu, band && sgn);
-    const unsigned below = bm & ((1u << lane) - 1u);
-    bool my = below ? ((sm >> (31 - __clz(below))) & 1u) : inside;
-    if (c >= 0 && !band) {
-      a.dsel[c] = my ? dc : -dc;
-      a.I[c] = my ? Iin : Iout;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      if (z0 + 32 * q >= wz) break;
+      const long long c = cq[q];
+      const bool band = c >= 0 && ownq[q] >= 0, sgn = band && dq[q] > Real(0);
+      const unsigned bm = __ballot_sync(0xffffffffu, band);
+      const unsigned sm = __ballot_sync(0xffffffffu, sgn);
+      const unsigned below = bm & ((1u << lane) - 1u);
+      const bool my = below ? ((sm >> (31 - __clz(below))) & 1u) : inside;
+      if (c >= 0 && !band) {
+        a.dsel[c] = my ? dc : -dc;
+        a.I[c] = my ? Iin : Iout;
+      }
+      // carry: the status at the top band cell of the chunk
+      inside = bm ? ((sm >> (31 - __clz(bm))) & 1u) : inside;
     }
-    // carry: status at the top lane of the chunk
-    const unsigned upto = bm;  // all band lanes in the chunk
-    bool top = upto ? ((sm >> (31 - __clz(upto))) & 1u) : inside;
-    inside = __shfl_sync(0xffffffffu, top, 0);
   }
 }
 template <class Real>
@@ -731,9 +780,9 @@ template <class T> TLB_HD DV<T> dcross(DV<T> a, DV<T> b) {
 template <class Real>
 __device__ __forceinline__ DV<Real> dnode(const IBArgs<Real>& a, int j, int k) {
   DV<Real> r;
-  r.x = dc<Real>((Real)(a.X[3 * j] - a.X[3 * k]));
-  r.y = dc<Real>((Real)(a.X[3 * j + 1] - a.X[3 * k + 1]));
-  r.z = dc<Real>((Real)(a.X[3 * j + 2] - a.X[3 * k + 2]));
+  r.x = dc<Real>(node_dx(a, j, k, 0));
+  r.y = dc<Real>(node_dx(a, j, k, 1));
+  r.z = dc<Real>(node_dx(a, j, k, 2));
   if (j == k) { r.x.d0 = 1; r.y.d1 = 1; r.z.d2 = 1; }
   return r;
 }
@@ -746,14 +795,14 @@ __device__ __forceinline__ D3<Real> skalak_dual(const IBArgs<Real>& a, int t, in
   DV<Real> xp = dnode(a, p, k), xq = dnode(a, q, k), xr = dnode(a, r, k);
   DV<Real> e1 = dsub(xq, xp), e2 = dsub(xr, xp);
   D3<Real> g11 = ddot(e1, e1), g12 = ddot(e1, e2), g22 = ddot(e2, e2);
-  const double* Gi = a.G0i + 3 * t;
-  D3<Real> tr = (Real)Gi[0] * g11 + (Real)(2.0 * Gi[1]) * g12 + (Real)Gi[2] * g22;
-  D3<Real> det = (Real)(Gi[0] * Gi[2] - Gi[1] * Gi[1]) * (g11 * g22 - g12 * g12);
+  const Real* K = a.skc + 5 * t;
+  D3<Real> tr = K[0] * g11 + K[1] * g12 + K[2] * g22;
+  D3<Real> det = K[3] * (g11 * g22 - g12 * g12);
   D3<Real> I1 = tr - dc<Real>(2), I2 = det - dc<Real>(1);
   int cap = a.ecap[t];
-  Real G = (Real)a.sG[cap], C = (Real)a.sC[cap];
+  Real G = a.capr[2 * a.ncaps + cap], C = a.capr[3 * a.ncaps + cap];
   D3<Real> w = (G * Real(0.25)) * (I1 * I1 + Real(2) * I1 - Real(2) * I2 + C * (I2 * I2));
-  return (Real)a.A0[t] * w;
+  return K[4] * w;
 }
 
 // Helfrich energy of vertex v: kb |sum_T (cot_k (x_v - x_j) + cot_j (x_v - x_k))|^2 / (8 A_v)
@@ -785,7 +834,7 @@ __device__ __forceinline__ D3<Real> helfrich_dual(const IBArgs<Real>& a, int v, 
     else if (dj < 0 || dk < 0) A = A + Real(0.25) * area;
     else A = A + Real(0.125) * (ddot(vj, vj) * cotk + ddot(vk, vk) * cotj);
   }
-  Real kb = (Real)a.kb[a.ncap[v]];
+  Real kb = a.capr[a.ncaps + a.ncap[v]];
   return (kb * Real(0.125)) * (ddot(K, K) / A);
 }
 
@@ -804,11 +853,11 @@ __device__ __forceinline__ void node_forces_body(const IBArgs<Real>& a, const Bl
       // 2D ring: segment l joins node l -> next(l) (eq. DiscreteSE), bending
       // at nodes prev, k, next (eqs. DiscreteBE, DiscreteTheta, DiscreteArcLength).
       const int cap = a.ncap[k];
-      const Real ks = (Real)a.ks[cap], kb = (Real)a.kb[cap];
+      const Real ks = a.capr[cap], kb = a.capr[a.ncaps + cap];
       for (int side = 0; side < 2; ++side) {
         int e = a.inc[a.inc_off[k] + side];
         int p = a.E[2 * e], q = a.E[2 * e + 1];
-        Real tx = (Real)(a.X[3 * q] - a.X[3 * p]), tz = (Real)(a.X[3 * q + 2] - a.X[3 * p + 2]);
+        Real tx = node_dx(a, q, p, 0), tz = node_dx(a, q, p, 2);
         Real L = sqrt(tx * tx + tz * tz);
         Real T = ks * (L / (Real)a.ds0[e] - Real(1)) / L;
         Real sgn = (p == k) ? Real(1) : Real(-1);  // -dE/dX_p = +T t ; -dE/dX_q = -T t
@@ -818,8 +867,8 @@ __device__ __forceinline__ void node_forces_body(const IBArgs<Real>& a, const Bl
       int ms[3] = {a.rprev[k], k, a.rnext[k]};
       for (int mi = 0; mi < 3; ++mi) {
         int m = ms[mi], mp = a.rnext[m], mq = a.rprev[m];
-        Real ax = (Real)(a.X[3 * mp] - a.X[3 * m]), az = (Real)(a.X[3 * mp + 2] - a.X[3 * m + 2]);
-        Real bx = (Real)(a.X[3 * m] - a.X[3 * mq]), bz = (Real)(a.X[3 * m + 2] - a.X[3 * mq + 2]);
+        Real ax = node_dx(a, mp, m, 0), az = node_dx(a, mp, m, 2);
+        Real bx = node_dx(a, m, mq, 0), bz = node_dx(a, m, mq, 2);
         Real la = sqrt(ax * ax + az * az), lb = sqrt(bx * bx + bz * bz);
         Real ab = ax * bx + az * bz;
         Real cr = ax * bz - az * bx;
@@ -888,7 +937,12 @@ __device__ __forceinline__ void coupling_of(const IBArgs<Real>& a, int k, Real* 
       if (a.E[a.NV * e + q] == k) slot = q;
     for (int d = 0; d < 3; ++d) cpl[d] += (long long)a.esum[(a.NV * e + slot) * 3 + d];
   }
-  for (int d = 0; d < 3; ++d) out[d] = (Real)((double)cpl[d] / CPL_SCALE);
+  for (int d = 0; d < 3; ++d) {
+    if constexpr (std::is_same<Real, float>::value)  // one rounding either way
+      out[d] = __ll2float_rn(cpl[d]) * 0x1p-50f;
+    else
+      out[d] = (Real)((double)cpl[d] / CPL_SCALE);
+  }
   if (a.dim == 2) out[1] = 0;
 }
 
@@ -917,13 +971,11 @@ __device__ __forceinline__ int axis_bricks(int base, int n, int* out) {
 template <class Real>
 __device__ __forceinline__ int node_bricks(const IBArgs<Real>& a, int l, int* out) {
   int bx[4], by[4], bz[4];
-  double X0 = fmax(-1e8, fmin(1e8, a.X[3 * l])), X1 = fmax(-1e8, fmin(1e8, a.X[3 * l + 1]));
-  double X2 = fmax(-1e8, fmin(1e8, a.X[3 * l + 2]));
-  int nxb = axis_bricks((int)floor(X0) - 1, a.G.nx, bx);
+  int nxb = axis_bricks(a.xo[3 * l] - 1, a.G.nx, bx);
   int nyb = 1;
   by[0] = 0;
-  if (a.dim == 3) nyb = axis_bricks((int)floor(X1) - 1, a.G.ny, by);
-  int nzb = axis_bricks((int)floor(X2) - 1, a.G.nz, bz);
+  if (a.dim == 3) nyb = axis_bricks(a.xo[3 * l + 1] - 1, a.G.ny, by);
+  int nzb = axis_bricks(a.xo[3 * l + 2] - 1, a.G.nz, bz);
   int m = 0;
   for (int i = 0; i < nxb; ++i)
     for (int j = 0; j < nyb; ++j)
@@ -1014,13 +1066,21 @@ __device__ __forceinline__ void spread_body(const IBArgs<Real>& a, const Blk& bl
     // marker positions relative to the brick corner, nearest periodic image
     for (int j = threadIdx.x; j < m; j += blockDim.x) {
       int l = sorted[j];
-      double rx = a.X[3 * l] - ox, ry = a.X[3 * l + 1] - oy, rz = a.X[3 * l + 2] - oz;
-      rx -= a.G.nx * floor(rx / a.G.nx + 0.5);
-      if (a.dim == 3) ry -= a.G.ny * floor(ry / a.G.ny + 0.5); else ry = 0;
-      if (!a.G.wall) rz -= a.G.nz * floor(rz / a.G.nz + 0.5);
-      sX[j][0] = (Real)rx;
-      sX[j][1] = (Real)ry;
-      sX[j][2] = (Real)rz;
+      if constexpr (std::is_same<Real, float>::value) {
+        // integer part wrapped to [-n/2, n/2) (the image nearest the brick)
+        auto img = [](int k, int n) { return wrap_coord(k + n / 2, n) - n / 2; };
+        sX[j][0] = (float)img(a.xo[3 * l] - ox, a.G.nx) + a.xr[3 * l];
+        sX[j][1] = a.dim == 3 ? (float)img(a.xo[3 * l + 1] - oy, a.G.ny) + a.xr[3 * l + 1] : 0.0f;
+        sX[j][2] = (float)(a.G.wall ? a.xo[3 * l + 2] - oz : img(a.xo[3 * l + 2] - oz, a.G.nz)) + a.xr[3 * l + 2];
+      } else {
+        double rx = a.X[3 * l] - ox, ry = a.X[3 * l + 1] - oy, rz = a.X[3 * l + 2] - oz;
+        rx -= a.G.nx * floor(rx / a.G.nx + 0.5);
+        if (a.dim == 3) ry -= a.G.ny * floor(ry / a.G.ny + 0.5); else ry = 0;
+        if (!a.G.wall) rz -= a.G.nz * floor(rz / a.G.nz + 0.5);
+        sX[j][0] = (Real)rx;
+        sX[j][1] = (Real)ry;
+        sX[j][2] = (Real)rz;
+      }
       Real cp[3];
       coupling_of(a, l, cp);  // F_mem = F_s + F_b + F_c (eq. MembraneForces)
       for (int d = 0; d < 3; ++d) sF[j][d] = a.F[3 * l + d] + cp[d];
@@ -1067,18 +1127,17 @@ __device__ __forceinline__ void interp_advect_body(const IBArgs<typename Prec<MO
   int lane = threadIdx.x & 31;
   if (l >= a.nn) return;
   const Geo G = a.G;
-  const double X0 = a.X[3 * l], X1 = a.X[3 * l + 1], X2 = a.X[3 * l + 2];
-  const int b0 = (int)floor(X0) - 1, b1 = (int)floor(X1) - 1, b2 = (int)floor(X2) - 1;
+  const int b0 = a.xo[3 * l] - 1, b1 = a.xo[3 * l + 1] - 1, b2 = a.xo[3 * l + 2] - 1;
   const int ncell = a.dim == 3 ? 64 : 16;
   Real U[3] = {0, 0, 0};
   for (int s = lane; s < ncell; s += 32) {
     int ox = s % 4, oy = a.dim == 3 ? (s / 4) % 4 : 0, oz = a.dim == 3 ? s / 16 : s / 4;
     int px = b0 + ox, py = a.dim == 3 ? b1 + oy : 0, pz = b2 + oz;
-    Real w = peskin((Real)(px - X0)) * peskin((Real)(pz - X2));
-    if (a.dim == 3) w *= peskin((Real)(py - X1));
+    Real w = peskin(-node_off(a, l, 0, px)) * peskin(-node_off(a, l, 2, pz));
+    if (a.dim == 3) w *= peskin(-node_off(a, l, 1, py));
     if (w == Real(0)) continue;
     if (G.wall && (pz < 0 || pz >= G.nz)) continue;
-    int x = ((px % G.nx) + G.nx) % G.nx, y = ((py % G.ny) + G.ny) % G.ny, z = ((pz % G.nz) + G.nz) % G.nz;
+    int x = wrap_coord(px, G.nx), y = wrap_coord(py, G.ny), z = wrap_coord(pz, G.nz);
     const Nbr<L> nb(G, x, y, z);
     const long long self = nb.self;
     Real r = 0, j[3] = {0, 0, 0};
@@ -1097,14 +1156,15 @@ __device__ __forceinline__ void interp_advect_body(const IBArgs<typename Prec<MO
     for (int o = 16; o > 0; o >>= 1) U[d] += __shfl_xor_sync(0xffffffffu, U[d], o);
   if (lane == 0) {
     if (a.dim == 2) U[1] = 0;
-    if (!(fabs((double)U[0]) < 0.5 && fabs((double)U[1]) < 0.5 && fabs((double)U[2]) < 0.5))
+    if (!(fabs(U[0]) < Real(0.5) && fabs(U[1]) < Real(0.5) && fabs(U[2]) < Real(0.5)))
       atomicOr(a.status, (unsigned)ST_MARKER_JUMP);
-    const double Xn[3] = {X0 + (double)U[0], X1 + (double)U[1], X2 + (double)U[2]};
     for (int d = 0; d < 3; ++d) {
-      a.X[3 * l + d] = Xn[d];
-      double v = fmax(-1e8, fmin(1e8, Xn[d]));
+      const double Xn = a.X[3 * l + d] + (double)U[d];
+      a.X[3 * l + d] = Xn;
+      double v = fmax(-1e8, fmin(1e8, Xn));
       atomicMin(a.box + d, (int)floor(v));
       atomicMin(a.box + 3 + d, -(int)ceil(v));
+      split_coord(Xn, a.xo + 3 * l + d, a.xr + 3 * l + d);
     }
   }
 }

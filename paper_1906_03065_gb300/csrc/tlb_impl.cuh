@@ -101,6 +101,11 @@ struct Impl : ImplBase {
     a.vn = c->ptr<Real>(c->L.vn);
     a.erel = c->ptr<Real>(c->L.erel);
     a.eorg = c->ptr<int>(c->L.eorg);
+    a.xo = c->ptr<int>(c->L.xo);
+    a.xr = c->ptr<Real>(c->L.xr);
+    a.skc = c->ptr<Real>(c->L.skc);
+    a.capr = c->ptr<Real>(c->L.capr);
+    a.ncaps = c->ncap;
     a.esum = c->ptr<unsigned long long>(c->L.esum);
     a.F = c->ptr<Real>(c->L.F);
     a.box = c->ptr<int>(c->L.box);
