@@ -334,6 +334,55 @@ __device__ __forceinline__ unsigned long long dist_code(double d) {
   return (unsigned long long)(d * 17179869184.0);
 }
 
+// Correctly rounded reciprocal (the value of 1 / x, without the division).
+__device__ __forceinline__ float rcp_rn(float x) { return __frcp_rn(x); }
+__device__ __forceinline__ double rcp_rn(double x) { return __drcp_rn(x); }
+
+// Squared distance from a point to a triangle (or a segment), without
+// branches: the projection onto the plane when it falls inside the
+// triangle, else the nearest of the three clamped edge projections.  The
+// per-face quantities are set up once; a point costs about fifty
+// arithmetic instructions and no divergence (the Voronoi-region walk of
+// closest_on_tri, which also returns the feature, serves the band).
+template <class Real>
+struct FaceDist {
+  V3<Real> A, B, ab, ac, bc;
+  Real d00, d01, d11, i00, i11, ibc, iden;
+  bool tri;
+  __device__ __forceinline__ FaceDist(V3<Real> a, V3<Real> b, V3<Real> c, bool is_tri) : A(a), B(b), tri(is_tri) {
+    ab = b - a;
+    ac = c - a;
+    bc = c - b;
+    d00 = dot(ab, ab);
+    d01 = dot(ab, ac);
+    d11 = dot(ac, ac);
+    const Real dbc = dot(bc, bc), den = d00 * d11 - d01 * d01;
+    i00 = d00 > Real(0) ? rcp_rn(d00) : Real(0);  // degenerate edge: its first end
+    i11 = d11 > Real(0) ? rcp_rn(d11) : Real(0);
+    ibc = dbc > Real(0) ? rcp_rn(dbc) : Real(0);
+    iden = den > Real(0) ? rcp_rn(den) : Real(0);  // degenerate face: edges only
+  }
+  __device__ __forceinline__ Real dist2(V3<Real> x) const {
+    const V3<Real> ap = x - A;
+    const Real d20 = dot(ap, ab);
+    const Real t0 = fmin(Real(1), fmax(Real(0), d20 * i00));
+    const V3<Real> e0 = ap - t0 * ab;
+    Real best = dot(e0, e0);
+    if (!tri) return best;
+    const Real d21 = dot(ap, ac);
+    const Real t1 = fmin(Real(1), fmax(Real(0), d21 * i11));
+    const V3<Real> e1 = ap - t1 * ac;
+    const V3<Real> bp = x - B;
+    const Real t2 = fmin(Real(1), fmax(Real(0), dot(bp, bc) * ibc));
+    const V3<Real> e2 = bp - t2 * bc;
+    best = fmin(best, fmin(dot(e1, e1), dot(e2, e2)));
+    const Real v = (d11 * d20 - d01 * d21) * iden, w = (d00 * d21 - d01 * d20) * iden;
+    const V3<Real> q = ap - v * ab - w * ac;
+    const bool inside = iden > Real(0) && v >= Real(0) && w >= Real(0) && v + w <= Real(1);
+    return inside ? dot(q, q) : best;
+  }
+};
+
 // ------------------------------------------------------------ distance scatter
 // Every cell within dc of the membrane must receive the key (distance,
 // element) of its nearest element; keys are combined with atomicMin.  The
@@ -355,33 +404,6 @@ constexpr int SCATTER_WARPS = 4;
 
 // Feature f: its corners, cone generators (unit normals) and the faces
 // containing it.  Returns the number of generators.
-template <class Real>
-__device__ __forceinline__ int feature_info(const IBArgs<Real>& a, int f, int* corners, int* nB, int* tri, int* nT) {
-  const int NV = a.NV;
-  *nT = 0;
-  if (f < a.ne) {  // face (3D) or segment (2D)
-    for (int q = 0; q < NV; ++q) corners[q] = a.E[NV * f + q];
-    *nB = NV;
-    tri[(*nT)++] = f;
-    return 1;
-  }
-  f -= a.ne;
-  if (NV == 3 && f < a.nedge) {  // edge
-    const int* ed = a.edges + 4 * f;
-    corners[0] = ed[0];
-    corners[1] = ed[1];
-    *nB = 2;
-    tri[(*nT)++] = ed[2];
-    tri[(*nT)++] = ed[3];
-    return 2;
-  }
-  if (NV == 3) f -= a.nedge;
-  corners[0] = f;  // vertex
-  *nB = 1;
-  for (int j = a.inc_off[f]; j < a.inc_off[f + 1] && *nT < MAXG; ++j) tri[(*nT)++] = a.inc[j];
-  return *nT;
-}
-
 // One warp per feature, one lane per slice.  Geometry is in Real relative to
 // an integer origin (the lattice cell below the first corner), so the FP32
 // build does its sweep in single precision without losing accuracy; slice
@@ -396,42 +418,76 @@ __device__ __forceinline__ void dist_scatter_body(const IBArgs<Real>& a, const B
   __shared__ Real sV[SCATTER_WARPS][3][3];     // vertices of the offered face
   __shared__ Real sG[SCATTER_WARPS][MAXG][3];  // cone generators
   __shared__ Real sB[SCATTER_WARPS][3][3];     // feature corners
+  __shared__ Real sGi[SCATTER_WARPS][MAXG];    // 1 / (generator component along the slice axis)
   const int nfeat = a.ne + (a.NV == 3 ? a.nedge : 0) + a.nn;
   const int w = threadIdx.x >> 5;
   const int f = blk.x * SCATTER_WARPS + w;
   const int lane = threadIdx.x & 31;
   if (f >= nfeat) return;
-  int corners[3], tri[MAXG], nB, nT;
-  const int nG = feature_info(a, f, corners, &nB, tri, &nT);
-  int tmin = tri[0];
-  for (int j = 1; j < nT; ++j) tmin = min(tmin, tri[j]);
+  // The feature's corners (the same loads in every lane) and its cone
+  // generators, the normals of the faces containing it: lane j holds face j.
+  int corners[3] = {0, 0, 0}, nB, nG, trj = -1;
+  if (f < a.ne) {  // face (3D) or segment (2D)
+    nB = a.NV;
+    nG = 1;
+    for (int q = 0; q < a.NV; ++q) corners[q] = a.E[a.NV * f + q];
+    if (lane == 0) trj = f;
+  } else if (a.NV == 3 && f < a.ne + a.nedge) {  // edge
+    const int* ed = a.edges + 4 * (f - a.ne);
+    corners[0] = ed[0];
+    corners[1] = ed[1];
+    nB = 2;
+    nG = 2;
+    if (lane < 2) trj = ed[2 + lane];
+  } else {  // vertex
+    const int v = f - a.ne - (a.NV == 3 ? a.nedge : 0);
+    corners[0] = v;
+    nB = 1;
+    const int i0 = a.inc_off[v];
+    nG = min(a.inc_off[v + 1] - i0, MAXG);
+    if (lane < nG) trj = a.inc[i0 + lane];
+  }
+  if (nG <= 0) return;  // a vertex of no face offers nothing
+  const int tmin = (int)__reduce_min_sync(0xffffffffu, lane < nG ? (unsigned)trj : 0xffffffffu);
   int o[3];
   for (int d = 0; d < 3; ++d) o[d] = a.xo[3 * corners[0] + d];
   if (a.dim == 2) o[1] = 0;
   // the origin's cell wrapped into the lattice (offers index cells from it)
   const int ow[3] = {wrap_coord(o[0], a.G.nx), wrap_coord(o[1], a.G.ny), a.G.wall ? o[2] : wrap_coord(o[2], a.G.nz)};
+  bool fin = true;
   if (lane < 9) {
     int q = lane / 3, d = lane % 3;
     if (q < a.NV) sV[w][q][d] = node_off(a, a.E[a.NV * tmin + q], d, o[d]);
-    if (q < nB) sB[w][q][d] = node_off(a, corners[q], d, o[d]);
-  }
-  for (int idx = lane; idx < nG * 3; idx += 32) sG[w][idx / 3][idx % 3] = a.en[3 * tri[idx / 3] + idx % 3];
-  __syncwarp();
-  const Real dc = a.dc;
-  Real S[3] = {0, 0, 0};
-  bool finite = true;
-  for (int j = 0; j < nG; ++j)
-    for (int d = 0; d < 3; ++d) {
-      S[d] += sG[w][j][d];
-      finite &= fabs(sG[w][j][d]) <= Real(1.001);
+    if (q < nB) {
+      const Real b = node_off(a, corners[q], d, o[d]);
+      sB[w][q][d] = b;
+      fin = fabs(b) < Real(1e6);  // rejects NaN/Inf
     }
-  for (int q = 0; q < nB; ++q)
-    for (int d = 0; d < 3; ++d) finite &= fabs(sB[w][q][d]) < Real(1e6);  // rejects NaN/Inf
-  if (!finite) {
+  }
+  Real g[3] = {0, 0, 0};
+  if (lane < nG) {
+    for (int d = 0; d < 3; ++d) {
+      g[d] = a.en[3 * trj + d];
+      sG[w][lane][d] = g[d];
+      fin &= fabs(g[d]) <= Real(1.001);
+    }
+  }
+  if (!__all_sync(0xffffffffu, fin)) {
     if (lane == 0) atomicOr(a.status, (unsigned)ST_NAN);
     return;
   }
-  // slice axis: largest component of the generator sum, all generators of one sign
+  __syncwarp();
+  const Real dc = a.dc;
+  // slice axis: largest component of the generator sum, all generators of
+  // one sign (the sum is broadcast from lane 0 so every lane takes the
+  // same axis; any axis gives the same offers' minima)
+  Real S[3] = {g[0], g[1], g[2]};
+#pragma unroll
+  for (int sh = 16; sh > 0; sh >>= 1)
+#pragma unroll
+    for (int d = 0; d < 3; ++d) S[d] += __shfl_xor_sync(0xffffffffu, S[d], sh);
+#pragma unroll
+  for (int d = 0; d < 3; ++d) S[d] = __shfl_sync(0xffffffffu, S[d], 0);
   int k = 0;
   if (a.dim == 3) {
     if (fabs(S[1]) > fabs(S[k])) k = 1;
@@ -439,8 +495,13 @@ __device__ __forceinline__ void dist_scatter_body(const IBArgs<Real>& a, const B
   } else {
     k = fabs(S[2]) > fabs(S[0]) ? 2 : 0;
   }
-  Real gmin = 1e30f;
-  for (int j = 0; j < nG; ++j) gmin = fmin(gmin, sG[w][j][k] * (S[k] >= 0 ? Real(1) : Real(-1)));
+  Real gmin = lane < nG ? g[k] * (S[k] >= 0 ? Real(1) : Real(-1)) : Real(1e30f);
+#pragma unroll
+  for (int sh = 16; sh > 0; sh >>= 1) gmin = fmin(gmin, __shfl_xor_sync(0xffffffffu, gmin, sh));
+  // reciprocals of the generators' slice components (the rectangles are
+  // widened by eps, far above the rounding of a product)
+  if (lane < nG) sGi[w][lane] = rcp_rn(g[k]);
+  __syncwarp();
   int oa, ob;
   if (a.dim == 3) { oa = k == 0 ? 1 : 0; ob = k == 2 ? 1 : 2; }
   else { oa = k == 0 ? 2 : 0; ob = 1; }
@@ -452,43 +513,57 @@ __device__ __forceinline__ void dist_scatter_body(const IBArgs<Real>& a, const B
   const V3<Real> v0 = mk<Real>(sV[w][0][0], sV[w][0][1], sV[w][0][2]);
   const V3<Real> v1 = mk<Real>(sV[w][1][0], sV[w][1][1], sV[w][1][2]);
   const V3<Real> v2 = a.NV == 3 ? mk<Real>(sV[w][2][0], sV[w][2][1], sV[w][2][2]) : v1;
-  // Up to 32 slices at a time: every lane sizes one slice's rectangle, a
-  // warp prefix sum lays the rectangles' cells end to end, and the lanes take
-  // the cells round-robin (slices near the feature are small, far ones in a
-  // widening cone large: per-slice loops would leave most lanes idle).
-  for (int base = c0; base <= c1; base += 32) {
-    const int c = base + lane;
-    int a0 = 0, b0 = 0, wa = 1, cnt = 0;
-    float rwa = 1.0f;
-    if (c <= c1) {
-      Real lo0 = 1e30f, hi0 = -1e30f, lo1 = 1e30f, hi1 = -1e30f;
-      for (int q = 0; q < nB; ++q) {
-        if (!wide) {
-          for (int j = 0; j < nG; ++j) {
-            Real t = ((Real)c - sB[w][q][k]) / sG[w][j][k];
-            Real pa = sB[w][q][oa] + t * sG[w][j][oa], pb = sB[w][q][ob] + t * sG[w][j][ob];
-            lo0 = fmin(lo0, pa); hi0 = fmax(hi0, pa);
-            lo1 = fmin(lo1, pb); hi1 = fmax(hi1, pb);
-          }
-        } else {  // conservative: the feature's box widened by dc
-          lo0 = fmin(lo0, sB[w][q][oa] - dc); hi0 = fmax(hi0, sB[w][q][oa] + dc);
-          lo1 = fmin(lo1, sB[w][q][ob] - dc); hi1 = fmax(hi1, sB[w][q][ob] + dc);
+  const FaceDist<Real> fd(v0, v1, v2, a.NV == 3);
+  const Real dc2 = dc * dc;
+  // Bounding rectangle of the cone's cross-section in slice c: origin (a0,
+  // b0), width wa, cnt cells (0 when empty or flagged as too wide).
+  auto slice_rect = [&](int c, int& a0, int& b0, int& wa, int& cnt) {
+    Real lo0 = 1e30f, hi0 = -1e30f, lo1 = 1e30f, hi1 = -1e30f;
+    for (int q = 0; q < nB; ++q) {
+      if (!wide) {
+        for (int j = 0; j < nG; ++j) {
+          Real t = ((Real)c - sB[w][q][k]) * sGi[w][j];
+          Real pa = sB[w][q][oa] + t * sG[w][j][oa], pb = sB[w][q][ob] + t * sG[w][j][ob];
+          lo0 = fmin(lo0, pa); hi0 = fmax(hi0, pa);
+          lo1 = fmin(lo1, pb); hi1 = fmax(hi1, pb);
         }
+      } else {  // conservative: the feature's box widened by dc
+        lo0 = fmin(lo0, sB[w][q][oa] - dc); hi0 = fmax(hi0, sB[w][q][oa] + dc);
+        lo1 = fmin(lo1, sB[w][q][ob] - dc); hi1 = fmax(hi1, sB[w][q][ob] + dc);
       }
-      a0 = (int)ceil(lo0 - eps);
-      const int a1 = (int)floor(hi0 + eps);
-      int b1 = 0;
-      if (a.dim == 3) { b0 = (int)ceil(lo1 - eps); b1 = (int)floor(hi1 + eps); }
-      const int wb = b1 - b0 + 1;
-      wa = a1 - a0 + 1;
-      if (wa > 0 && wb > 0) {
-        if (wa > 1024 || wb > 1024) atomicOr(a.status, (unsigned)ST_OVERFLOW);  // bounded work, flagged
-        else cnt = wa * wb;
-      }
-      if (cnt == 0) wa = 1;
-      rwa = 1.0f / (float)wa;
     }
-    int incl = cnt;
+    a0 = (int)ceil(lo0 - eps);
+    const int a1 = (int)floor(hi0 + eps);
+    int b1 = 0;
+    b0 = 0;
+    if (a.dim == 3) { b0 = (int)ceil(lo1 - eps); b1 = (int)floor(hi1 + eps); }
+    const int wb = b1 - b0 + 1;
+    wa = a1 - a0 + 1;
+    cnt = 0;
+    if (wa > 0 && wb > 0) {
+      if (wa > 1024 || wb > 1024) atomicOr(a.status, (unsigned)ST_OVERFLOW);  // bounded work, flagged
+      else cnt = wa * wb;
+    }
+    if (cnt == 0) wa = 1;
+  };
+  // Up to 64 slices at a time: every lane sizes the rectangles of two
+  // adjacent slices, a warp prefix sum lays all their cells end to end, and
+  // the lanes take the cells round-robin (slices near the feature are small,
+  // far ones in a widening cone large: per-slice loops would leave most
+  // lanes idle; 2 dc + 1 slices usually fit one pass).
+  for (int base = c0; base <= c1; base += 64) {
+    int a0[2] = {0, 0}, b0[2] = {0, 0}, wa[2] = {1, 1}, cnt[2] = {0, 0};
+    float rwa[2] = {1.0f, 1.0f};
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int c = base + 2 * lane + h;
+      if (c <= c1) {
+        slice_rect(c, a0[h], b0[h], wa[h], cnt[h]);
+        rwa[h] = __frcp_rn((float)wa[h]);
+      }
+    }
+    const int tot = cnt[0] + cnt[1];
+    int incl = tot;
 #pragma unroll
     for (int sh = 1; sh < 32; sh <<= 1) {
       const int v = __shfl_up_sync(0xffffffffu, incl, sh);
@@ -497,44 +572,49 @@ __device__ __forceinline__ void dist_scatter_body(const IBArgs<Real>& a, const B
     const int total = __shfl_sync(0xffffffffu, incl, 31);
     for (int i0 = 0; i0 < total; i0 += 32) {
       const int i = i0 + lane;
-      // slice of cell i: the first lane whose inclusive prefix exceeds i
+      // lane holding cell i: the first lane whose inclusive prefix exceeds i
       int L = 0;
 #pragma unroll
       for (int step = 16; step >= 1; step >>= 1) {
         const int v = __shfl_sync(0xffffffffu, incl, L + step - 1);
         if (v <= i) L += step;
       }
-      const int inclL = __shfl_sync(0xffffffffu, incl, L), cntL = __shfl_sync(0xffffffffu, cnt, L);
-      const int a0L = __shfl_sync(0xffffffffu, a0, L), b0L = __shfl_sync(0xffffffffu, b0, L);
-      const int waL = __shfl_sync(0xffffffffu, wa, L);
-      const float rwaL = __shfl_sync(0xffffffffu, rwa, L);
+      const int inclL = __shfl_sync(0xffffffffu, incl, L), totL = __shfl_sync(0xffffffffu, tot, L);
+      const int cnt0L = __shfl_sync(0xffffffffu, cnt[0], L);
+      int a0L[2], b0L[2], waL[2];
+      float rwaL[2];
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        a0L[h] = __shfl_sync(0xffffffffu, a0[h], L);
+        b0L[h] = __shfl_sync(0xffffffffu, b0[h], L);
+        waL[h] = __shfl_sync(0xffffffffu, wa[h], L);
+        rwaL[h] = __shfl_sync(0xffffffffu, rwa[h], L);
+      }
       if (i >= total) continue;
-      const int jj = i - (inclL - cntL);
-      // jj / waL: jj < 2^20 and waL <= 1024 keep the product within 2^-13 of
-      // the true (jj + 1/2) / waL, whose fraction is at least 2^-11 from an
+      int jj = i - (inclL - totL);
+      const int h = jj >= cnt0L ? 1 : 0;  // the lane's first or second slice
+      if (h) jj -= cnt0L;
+      const int wah = h ? waL[1] : waL[0];
+      // jj / wah: jj < 2^20 and wah <= 1024 keep the product within 2^-13 of
+      // the true (jj + 1/2) / wah, whose fraction is at least 2^-11 from an
       // integer, so the truncation is exact
-      const int qb = (int)(((float)jj + 0.5f) * rwaL);
+      const int qb = (int)(((float)jj + 0.5f) * (h ? rwaL[1] : rwaL[0]));
       int r[3];
-      r[k] = base + L;
-      r[oa] = a0L + (jj - qb * waL);
-      if (a.dim == 3) r[ob] = b0L + qb; else r[1] = 0;
+      r[k] = base + 2 * L + h;
+      r[oa] = (h ? a0L[1] : a0L[0]) + (jj - qb * wah);
+      if (a.dim == 3) r[ob] = (h ? b0L[1] : b0L[0]) + qb; else r[1] = 0;
       int pc[3] = {ow[0] + r[0], ow[1] + r[1], ow[2] + r[2]};
       long long cell = cell_of(a, pc);
       if (cell < 0) continue;
-      const V3<Real> x = mk<Real>((Real)r[0], (Real)r[1], (Real)r[2]);
-      Real beta[3];
-      int feat;
-      V3<Real> P = a.NV == 2 ? closest_on_seg(v0 - x, v1 - x, beta, &feat)
-                             : closest_on_tri(v0 - x, v1 - x, v2 - x, beta, &feat);
-      Real d = sqrt(dot(P, P));
-      if (!(d < dc)) continue;
-      unsigned long long key = (dist_code(d) << 24) | (unsigned long long)tmin;
+      const Real d2 = fd.dist2(mk<Real>((Real)r[0], (Real)r[1], (Real)r[2]));
+      if (!(d2 < dc2)) continue;
+      unsigned long long key = (dist_code(sqrt(d2)) << 24) | (unsigned long long)tmin;
       if (key < a.key[cell]) atomicMin(a.key + cell, key);
     }
   }
 }
 template <class Real>
-__global__ void __launch_bounds__(SCATTER_WARPS * 32) k_dist_scatter(const __grid_constant__ IBArgs<Real> a) {
+__global__ void __launch_bounds__(SCATTER_WARPS * 32, 7) k_dist_scatter(const __grid_constant__ IBArgs<Real> a) {
   dist_scatter_body(a, hw_blk());
 }
 
@@ -1040,9 +1120,10 @@ __global__ void k_brick_fill(const __grid_constant__ IBArgs<Real> a) {
 // markers in the previous step are visited too, so their cells return to zero.
 template <class Real>
 __device__ __forceinline__ void spread_body(const IBArgs<Real>& a, const Blk& blk) {
+  constexpr int CH = 128;  // markers staged at a time
   __shared__ int list[512], sorted[512];
-  __shared__ Real sX[512][3];
-  __shared__ Real sF[512][3];
+  __shared__ Real sW[CH][12];  // per marker: delta_h at the brick's 4 cells along x, y, z
+  __shared__ Real sF[CH][3];
   const int nact = min(a.ctr[0], a.nbricks);
   const int BY = a.dim == 3 ? BRICK : 1;
   for (int ib = blk.x; ib < nact; ib += blk.gx) {
@@ -1063,41 +1144,53 @@ __device__ __forceinline__ void spread_body(const IBArgs<Real>& a, const Blk& bl
     __syncthreads();
     const int bx = b % a.nbx, by = (b / a.nbx) % a.nby, bz = b / (a.nbx * a.nby);
     const int ox = bx * BRICK, oy = by * BRICK, oz = bz * BRICK;
-    // marker positions relative to the brick corner, nearest periodic image
-    for (int j = threadIdx.x; j < m; j += blockDim.x) {
-      int l = sorted[j];
-      if constexpr (std::is_same<Real, float>::value) {
-        // integer part wrapped to [-n/2, n/2) (the image nearest the brick)
-        auto img = [](int k, int n) { return wrap_coord(k + n / 2, n) - n / 2; };
-        sX[j][0] = (float)img(a.xo[3 * l] - ox, a.G.nx) + a.xr[3 * l];
-        sX[j][1] = a.dim == 3 ? (float)img(a.xo[3 * l + 1] - oy, a.G.ny) + a.xr[3 * l + 1] : 0.0f;
-        sX[j][2] = (float)(a.G.wall ? a.xo[3 * l + 2] - oz : img(a.xo[3 * l + 2] - oz, a.G.nz)) + a.xr[3 * l + 2];
-      } else {
-        double rx = a.X[3 * l] - ox, ry = a.X[3 * l + 1] - oy, rz = a.X[3 * l + 2] - oz;
-        rx -= a.G.nx * floor(rx / a.G.nx + 0.5);
-        if (a.dim == 3) ry -= a.G.ny * floor(ry / a.G.ny + 0.5); else ry = 0;
-        if (!a.G.wall) rz -= a.G.nz * floor(rz / a.G.nz + 0.5);
-        sX[j][0] = (Real)rx;
-        sX[j][1] = (Real)ry;
-        sX[j][2] = (Real)rz;
-      }
-      Real cp[3];
-      coupling_of(a, l, cp);  // F_mem = F_s + F_b + F_c (eq. MembraneForces)
-      for (int d = 0; d < 3; ++d) sF[j][d] = a.F[3 * l + d] + cp[d];
-    }
-    __syncthreads();
     const int lx = threadIdx.x % BRICK, ly = (threadIdx.x / BRICK) % BY, lz = threadIdx.x / (BRICK * BY);
     const int cx = ox + lx, cy = oy + ly, cz = oz + lz;
     const bool ok = threadIdx.x < BRICK * BY * BRICK && cx < a.G.nx && cy < a.G.ny && cz < a.G.nz;
-    if (ok) {
-      Real f[3] = {0, 0, 0};
-      for (int j = 0; j < m; ++j) {
-        Real rx = (Real)lx - sX[j][0], ry = (Real)ly - sX[j][1], rz = (Real)lz - sX[j][2];
-        if (!(fabs(rx) < Real(2) && fabs(rz) < Real(2) && (a.dim == 2 || fabs(ry) < Real(2)))) continue;
-        Real wgt = peskin(rx) * peskin(rz);
-        if (a.dim == 3) wgt *= peskin(ry);
-        for (int d = 0; d < 3; ++d) f[d] += wgt * sF[j][d];
+    Real f[3] = {0, 0, 0};
+    for (int j0 = 0; j0 < m; j0 += CH) {
+      const int mc = min(CH, m - j0);
+      // marker positions relative to the brick corner (nearest periodic
+      // image) and the kernel weights of the brick's cells along each axis
+      for (int j = threadIdx.x; j < mc; j += blockDim.x) {
+        int l = sorted[j0 + j];
+        Real r3[3];
+        if constexpr (std::is_same<Real, float>::value) {
+          // integer part wrapped to [-n/2, n/2) (the image nearest the brick)
+          auto img = [](int k, int n) { return wrap_coord(k + n / 2, n) - n / 2; };
+          r3[0] = (float)img(a.xo[3 * l] - ox, a.G.nx) + a.xr[3 * l];
+          r3[1] = a.dim == 3 ? (float)img(a.xo[3 * l + 1] - oy, a.G.ny) + a.xr[3 * l + 1] : 0.0f;
+          r3[2] = (float)(a.G.wall ? a.xo[3 * l + 2] - oz : img(a.xo[3 * l + 2] - oz, a.G.nz)) + a.xr[3 * l + 2];
+        } else {
+          double rx = a.X[3 * l] - ox, ry = a.X[3 * l + 1] - oy, rz = a.X[3 * l + 2] - oz;
+          rx -= a.G.nx * floor(rx / a.G.nx + 0.5);
+          if (a.dim == 3) ry -= a.G.ny * floor(ry / a.G.ny + 0.5); else ry = 0;
+          if (!a.G.wall) rz -= a.G.nz * floor(rz / a.G.nz + 0.5);
+          r3[0] = (Real)rx;
+          r3[1] = (Real)ry;
+          r3[2] = (Real)rz;
+        }
+        // delta_h vanishes outside |r| < 2 (peskin returns 0 there)
+  #pragma unroll
+        for (int d = 0; d < 3; ++d)
+  #pragma unroll
+          for (int o = 0; o < BRICK; ++o) sW[j][4 * d + o] = peskin((Real)o - r3[d]);
+        Real cp[3];
+        coupling_of(a, l, cp);  // F_mem = F_s + F_b + F_c (eq. MembraneForces)
+        for (int d = 0; d < 3; ++d) sF[j][d] = a.F[3 * l + d] + cp[d];
       }
+      __syncthreads();
+      if (ok) {  // summed in marker order across the chunks
+        for (int j = 0; j < mc; ++j) {
+          Real wgt = sW[j][lx] * sW[j][8 + lz];
+          if (a.dim == 3) wgt *= sW[j][4 + ly];
+          if (wgt == Real(0)) continue;  // outside the support
+          for (int d = 0; d < 3; ++d) f[d] += wgt * sF[j][d];
+        }
+      }
+      __syncthreads();
+    }
+    if (ok) {
       long long c = ((long long)cz * a.G.ny + cy) * a.G.nx + cx;
       for (int d = 0; d < 3; ++d) a.fib[d * a.G.P + c] = f[d];
     }
