@@ -1220,18 +1220,35 @@ __device__ __forceinline__ void interp_advect_body(const IBArgs<typename Prec<MO
   int lane = threadIdx.x & 31;
   if (l >= a.nn) return;
   const Geo G = a.G;
-  const int b0 = a.xo[3 * l] - 1, b1 = a.xo[3 * l + 1] - 1, b2 = a.xo[3 * l + 2] - 1;
+  const int bb[3] = {a.xo[3 * l] - 1, a.xo[3 * l + 1] - 1, a.xo[3 * l + 2] - 1};
+  // delta_h along each axis at the 4 support offsets: lane 4 d + o
+  Real wax = 0;
+  if (lane < 12) {
+    const int d = lane >> 2, o = lane & 3;
+    if (d != 1 || a.dim == 3) wax = peskin(-node_off(a, l, d, bb[d] + o));
+  }
   const int ncell = a.dim == 3 ? 64 : 16;
+  // the lane's two support cells: weights and addresses first, so that all
+  // their loads are in flight together (a cell of weight 0 reads cell 0)
+  Real w[2];
+  int cx[2], cy[2], cz[2];
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    const int s = lane + 32 * h;
+    const int ox = s % 4, oy = a.dim == 3 ? (s / 4) % 4 : 0, oz = a.dim == 3 ? s / 16 : (s / 4) % 4;
+    w[h] = __shfl_sync(0xffffffffu, wax, ox) * __shfl_sync(0xffffffffu, wax, 8 + oz);
+    if (a.dim == 3) w[h] *= __shfl_sync(0xffffffffu, wax, 4 + oy);
+    const int px = bb[0] + ox, py = a.dim == 3 ? bb[1] + oy : 0, pz = bb[2] + oz;
+    const bool ok = s < ncell && w[h] != Real(0) && !(G.wall && (pz < 0 || pz >= G.nz));
+    if (!ok) w[h] = 0;
+    cx[h] = ok ? wrap_coord(px, G.nx) : 0;
+    cy[h] = ok ? wrap_coord(py, G.ny) : 0;
+    cz[h] = ok ? wrap_coord(pz, G.nz) : 0;
+  }
   Real U[3] = {0, 0, 0};
-  for (int s = lane; s < ncell; s += 32) {
-    int ox = s % 4, oy = a.dim == 3 ? (s / 4) % 4 : 0, oz = a.dim == 3 ? s / 16 : s / 4;
-    int px = b0 + ox, py = a.dim == 3 ? b1 + oy : 0, pz = b2 + oz;
-    Real w = peskin(-node_off(a, l, 0, px)) * peskin(-node_off(a, l, 2, pz));
-    if (a.dim == 3) w *= peskin(-node_off(a, l, 1, py));
-    if (w == Real(0)) continue;
-    if (G.wall && (pz < 0 || pz >= G.nz)) continue;
-    int x = wrap_coord(px, G.nx), y = wrap_coord(py, G.ny), z = wrap_coord(pz, G.nz);
-    const Nbr<L> nb(G, x, y, z);
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    const Nbr<L> nb(G, cx[h], cy[h], cz[h]);
     const long long self = nb.self;
     Real r = 0, j[3] = {0, 0, 0};
 #pragma unroll
@@ -1242,23 +1259,29 @@ __device__ __forceinline__ void interp_advect_body(const IBArgs<typename Prec<MO
       if (L::cy(i)) j[1] += L::cy(i) > 0 ? fi : -fi;
       if (L::cz(i)) j[2] += L::cz(i) > 0 ? fi : -fi;
     }
+    Real ft[3];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) ft[d] = a.ftot[d * G.P + self];
     Real rho = Real(1) + r;
-    for (int d = 0; d < 3; ++d) U[d] += w * (j[d] + Real(0.5) * a.ftot[d * G.P + self]) / rho;
+    if (w[h] != Real(0))
+      for (int d = 0; d < 3; ++d) U[d] += w[h] * (j[d] + Real(0.5) * ft[d]) / rho;
   }
   for (int d = 0; d < 3; ++d)
     for (int o = 16; o > 0; o >>= 1) U[d] += __shfl_xor_sync(0xffffffffu, U[d], o);
-  if (lane == 0) {
-    if (a.dim == 2) U[1] = 0;
-    if (!(fabs(U[0]) < Real(0.5) && fabs(U[1]) < Real(0.5) && fabs(U[2]) < Real(0.5)))
-      atomicOr(a.status, (unsigned)ST_MARKER_JUMP);
-    for (int d = 0; d < 3; ++d) {
-      const double Xn = a.X[3 * l + d] + (double)U[d];
-      a.X[3 * l + d] = Xn;
-      double v = fmax(-1e8, fmin(1e8, Xn));
-      atomicMin(a.box + d, (int)floor(v));
-      atomicMin(a.box + 3 + d, -(int)ceil(v));
-      split_coord(Xn, a.xo + 3 * l + d, a.xr + 3 * l + d);
-    }
+  // lane 0's totals (each lane's butterfly sums in its own order)
+  for (int d = 0; d < 3; ++d) U[d] = __shfl_sync(0xffffffffu, U[d], 0);
+  if (a.dim == 2) U[1] = 0;
+  if (lane == 0 && !(fabs(U[0]) < Real(0.5) && fabs(U[1]) < Real(0.5) && fabs(U[2]) < Real(0.5)))
+    atomicOr(a.status, (unsigned)ST_MARKER_JUMP);
+  if (lane < 3) {  // lane d advances coordinate d
+    const int d = lane;
+    const Real Ud = d == 0 ? U[0] : (d == 1 ? U[1] : U[2]);
+    const double Xn = a.X[3 * l + d] + (double)Ud;
+    a.X[3 * l + d] = Xn;
+    double v = fmax(-1e8, fmin(1e8, Xn));
+    atomicMin(a.box + d, (int)floor(v));
+    atomicMin(a.box + 3 + d, -(int)ceil(v));
+    split_coord(Xn, a.xo + 3 * l + d, a.xr + 3 * l + d);
   }
 }
 template <class L, int MODE>
