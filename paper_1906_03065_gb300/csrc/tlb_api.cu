@@ -341,9 +341,13 @@ tlb_status tlb_create(const tlb_params* params, const tlb_membrane_desc* mems, i
   }
   cudaStream_t st = c->stream;
   {
-    // the membrane work is short and latency bound: give its stream the
-    // highest priority so its blocks go first when the collide frees SMs
+    // the membrane work is short and latency bound: give its streams the
+    // highest priority so its blocks go first beside the moments kernel
     int lo_prio = 0, hi_prio = 0;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&c->nsm, cudaDevAttrMultiProcessorCount, dev);
+    if (c->nsm <= 0) c->nsm = 1;
     cudaDeviceGetStreamPriorityRange(&lo_prio, &hi_prio);
     tlb_status r0 = cuda_check(cudaStreamCreateWithPriority(&c->side, cudaStreamNonBlocking, hi_prio), "side stream");
     if (r0 == TLB_OK)
@@ -351,7 +355,6 @@ tlb_status tlb_create(const tlb_params* params, const tlb_membrane_desc* mems, i
     if (r0 == TLB_OK) r0 = cuda_check(cudaEventCreateWithFlags(&c->ev_bins, cudaEventDisableTiming), "event");
     if (r0 == TLB_OK) r0 = cuda_check(cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming), "event");
     if (r0 == TLB_OK) r0 = cuda_check(cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming), "event");
-    if (r0 == TLB_OK) r0 = cuda_check(cudaEventCreateWithFlags(&c->ev_mom, cudaEventDisableTiming), "event");
     if (r0 != TLB_OK) { delete c; return r0; }
   }
   // zero everything, then set the non-zero initial values

@@ -349,7 +349,6 @@ struct BatchImpl : BatchBase {
         Ctx* c = b->inst[b->act[j]];
         BA& a = t[j];
         a.lb = I::lbargs(c, c->cur ^ q);
-        a.lb.region = 0;
         a.lb.zc = b->zc;
         a.ib = I::ibargs(c);
         a.rp = I::resptrs(c, b->ptr<unsigned long long>(b->res) + 4 * (size_t)b->act[j]);

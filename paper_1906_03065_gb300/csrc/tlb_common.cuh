@@ -219,21 +219,6 @@ __device__ __forceinline__ void marker_box(const int* cur, int margin, const Geo
   }
 }
 
-// Does the cell range [a0, a1] (per axis, a0 >= -2, a1 < n + 2) meet the box,
-// counting the periodic images of the box along periodic axes?
-__device__ __forceinline__ bool range_meets_box(const int* a0, const int* a1, const int* lo, const int* hi,
-                                                const Geo& G) {
-  const int n[3] = {G.nx, G.ny, G.nz};
-  for (int d = 0; d < 3; ++d) {
-    bool hit = false;
-    const bool per = !(d == 2 && G.wall);
-    for (int k = per ? -1 : 0; k <= (per ? 1 : 0); ++k)
-      hit |= !(hi[d] + k * n[d] < a0[d] || lo[d] + k * n[d] > a1[d]);
-    if (!hit) return false;
-  }
-  return true;
-}
-
 // Chemical potentials of App. A (eq. AppA) without the ideal-gas part of
 // mu_rho; mu_psi' adds kappa_c (psi - I) (Sec. 3.1).
 template <class Real>

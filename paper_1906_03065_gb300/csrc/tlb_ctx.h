@@ -78,10 +78,11 @@ struct Ctx {
   char* base = nullptr;
   size_t bytes = 0;
   cudaStream_t stream = nullptr;
-  cudaStream_t side = nullptr;   // membrane work that overlaps the moments: geometry,
-                                 // distance scatter, then band, fill and spreading
+  cudaStream_t side = nullptr;   // membrane work that overlaps the moments: geometry
+                                 // and the distance scatter
   cudaStream_t side2 = nullptr;  // elastic forces and brick binning, beside `side`
-  cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_mom = nullptr, ev_bins = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_bins = nullptr;
+  int nsm = 1;  // streaming multiprocessors of the device
   int cur = 0;  // population buffer holding the current state
   long t = 0;
   long t_snap = 0;  // step of the residual's reference state
@@ -105,7 +106,6 @@ struct Ctx {
     if (side2) cudaStreamSynchronize(side2);
     if (ev_fork) cudaEventDestroy(ev_fork);
     if (ev_join) cudaEventDestroy(ev_join);
-    if (ev_mom) cudaEventDestroy(ev_mom);
     if (ev_bins) cudaEventDestroy(ev_bins);
     if (side) cudaStreamDestroy(side);
     if (side2) cudaStreamDestroy(side2);

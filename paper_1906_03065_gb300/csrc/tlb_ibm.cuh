@@ -609,13 +609,15 @@ __device__ __forceinline__ void dist_scatter_body(const IBArgs<Real>& a, const B
       const Real d2 = fd.dist2(mk<Real>((Real)r[0], (Real)r[1], (Real)r[2]));
       if (!(d2 < dc2)) continue;
       unsigned long long key = (dist_code(sqrt(d2)) << 24) | (unsigned long long)tmin;
-      if (key < a.key[cell]) atomicMin(a.key + cell, key);
+      atomicMin(a.key + cell, key);  // no return value: a fire-and-forget reduction
     }
   }
 }
+// Persistent over nvb virtual blocks: a grid of a few blocks per SM leaves
+// the moments kernel, which runs beside it, most of each SM.
 template <class Real>
-__global__ void __launch_bounds__(SCATTER_WARPS * 32, 7) k_dist_scatter(const __grid_constant__ IBArgs<Real> a) {
-  dist_scatter_body(a, hw_blk());
+__global__ void __launch_bounds__(SCATTER_WARPS * 32, 7) k_dist_scatter(const __grid_constant__ IBArgs<Real> a, int nvb) {
+  for (int vb = blockIdx.x; vb < nvb; vb += gridDim.x) dist_scatter_body(a, Blk{vb, 0, 0, nvb, 1, 1});
 }
 
 // Sign of x - P relative to the membrane at the closest feature (interior:

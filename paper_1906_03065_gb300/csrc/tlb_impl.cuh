@@ -50,9 +50,6 @@ struct Impl : ImplBase {
     a.bflag = c->ptr<unsigned char>(c->L.bflag);
     a.nbx = c->nbx;
     a.nby = c->nby;
-    a.region = 0;
-    a.boxc = c->ptr<int>(c->L.box) + 6;
-    a.box_margin = max((int)ceil(c->p.dc) + 2, 8);  // covers whole spreading bricks
     a.fe.k1 = (Real)c->p.kappa[0];
     a.fe.k2 = (Real)c->p.kappa[1];
     a.fe.k3 = (Real)c->p.kappa[2];
@@ -147,7 +144,8 @@ struct Impl : ImplBase {
     k_geometry<Real><<<blocks((long long)c->ne + c->nn, 128), 128, 0, s>>>(a);
     TLB_LAUNCHED(c, "k_geometry");
     const long long nfeat = (long long)c->ne + c->nedge + c->nn;
-    k_dist_scatter<Real><<<blocks(nfeat, SCATTER_WARPS), SCATTER_WARPS * 32, 0, s>>>(a);
+    const unsigned nvb = blocks(nfeat, SCATTER_WARPS);
+    k_dist_scatter<Real><<<std::min(nvb, 4u * (unsigned)c->nsm), SCATTER_WARPS * 32, 0, s>>>(a, (int)nvb);
     TLB_LAUNCHED(c, "k_dist_scatter");
     return TLB_OK;
   }
@@ -431,7 +429,6 @@ struct Impl : ImplBase {
       if (c->nn > 0 && (st = snapshot_box(c, ia, s, c->box_stale)) != TLB_OK) return st;
       c->box_stale = false;
       if ((st = mark(c, 0)) != TLB_OK) return st;
-      const bool overlap = c->nn > 0 && !c->prof;
       if (c->nn > 0) {  // fork: position-only membrane work on the two side streams
         TLB_CUDA(cudaEventRecord(c->ev_fork, s));
         TLB_CUDA(cudaStreamWaitEvent(c->side, c->ev_fork, 0));
@@ -443,33 +440,19 @@ struct Impl : ImplBase {
       k_moments<L, MODE><<<blocks(N, 256), 256, 0, s>>>(la);
       TLB_LAUNCHED(c, "k_moments");
       if ((st = mark(c, 1)) != TLB_OK) return st;
-      if (overlap) {
-        // the profile, coupling sums and spreading need psi(t): they follow
-        // the moments on the side stream while the tiles away from the
-        // membrane are collided on the main stream
-        TLB_CUDA(cudaEventRecord(c->ev_mom, s));
-        TLB_CUDA(cudaStreamWaitEvent(c->side, c->ev_mom, 0));
-        if ((st = ibm_band(c, ia, c->side)) != TLB_OK) return st;
-        TLB_CUDA(cudaStreamWaitEvent(c->side, c->ev_bins, 0));  // forces and bricks
-        if ((st = ibm_spread(c, ia, c->side)) != TLB_OK) return st;
+      // the profile, coupling sums and spreading need psi(t) and the
+      // position work: they follow the moments, then the whole lattice is
+      // collided in one launch (splitting it to overlap the membrane work
+      // with the tiles away from the membrane measured slower)
+      if (c->nn > 0) {
         TLB_CUDA(cudaEventRecord(c->ev_join, c->side));
-        la.region = 1;
-        if ((st = collide(c, la, s)) != TLB_OK) return st;
-        if ((st = mark(c, 2)) != TLB_OK) return st;
         TLB_CUDA(cudaStreamWaitEvent(s, c->ev_join, 0));
-        la.region = 2;
-        if ((st = collide(c, la, s)) != TLB_OK) return st;
-      } else {
-        if (c->nn > 0) {  // serial order (used when timing the phases)
-          TLB_CUDA(cudaEventRecord(c->ev_join, c->side));
-          TLB_CUDA(cudaStreamWaitEvent(s, c->ev_join, 0));
-          TLB_CUDA(cudaStreamWaitEvent(s, c->ev_bins, 0));
-          if ((st = ibm_band(c, ia, s)) != TLB_OK) return st;
-          if ((st = ibm_spread(c, ia, s)) != TLB_OK) return st;
-        }
-        if ((st = mark(c, 2)) != TLB_OK) return st;
-        if ((st = collide(c, la, s)) != TLB_OK) return st;
+        TLB_CUDA(cudaStreamWaitEvent(s, c->ev_bins, 0));
+        if ((st = ibm_band(c, ia, s)) != TLB_OK) return st;
+        if ((st = ibm_spread(c, ia, s)) != TLB_OK) return st;
       }
+      if ((st = mark(c, 2)) != TLB_OK) return st;
+      if ((st = collide(c, la, s)) != TLB_OK) return st;
       if ((st = mark(c, 3)) != TLB_OK) return st;
       if (c->nn > 0) {
         k_interp_advect<L, MODE><<<blocks((long long)c->nn * 32, 128), 128, 0, s>>>(ia, la.lo_dst);

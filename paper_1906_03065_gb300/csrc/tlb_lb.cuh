@@ -22,10 +22,6 @@ struct LBArgs {
   Real* ftot;       // [3][P] total force of the step (read by the interpolation)
   const unsigned char* bflag;  // per 4x4x4 brick: markers spread force into it
   int nbx, nby;                // brick grid (x, y)
-  int region;                  // 0: every tile; 1: tiles away from the membrane
-                               // box; 2: tiles that meet it
-  const int* boxc;             // the step's marker box
-  int box_margin;              // cells the membrane work reaches beyond it
   FEParams<Real> fe;
   Real om, om_phi, om_psi;  // 1/tau
   Real gphi, gpsi;          // Gamma_phi, Gamma_psi
@@ -91,18 +87,6 @@ __device__ __forceinline__ void collide_body(const LBArgs<MODE>& a, const Blk& b
   const int z1 = min(z0 + a.zc, G.nz);
   const int x = x0 + tx, y = y0 + ty;
   const bool active = x < G.nx && y < G.ny;
-
-  // Split launch: tiles whose cells, potentials and force stencils (halo 2)
-  // stay outside the membrane box do not read anything the membrane work of
-  // the step writes, so they run while that work is in flight.
-  if (a.region != 0) {
-    int lo[3], hi[3];
-    marker_box(a.boxc, a.box_margin, G, !D3, lo, hi);
-    const int r0[3] = {x0 - 2, D3 ? y0 - 2 : 0, z0 - 2};
-    const int r1[3] = {x0 + TX + 1, D3 ? y0 + TY + 1 : 0, z1 + 1};
-    const bool near = range_meets_box(r0, r1, lo, hi, G);
-    if ((a.region == 1) == near) return;
-  }
 
   // wrap of a halo index: within two cells of the range except for tiles
   // wider than the lattice, which take the division
@@ -201,7 +185,7 @@ __device__ __forceinline__ void collide_body(const LBArgs<MODE>& a, const Blk& b
     const Real mup = smu[sc][1][cc], mus = smu[sc][2][cc];
     // force: f_FE = -rho grad mu~rho - phi grad mu_phi - psi grad mu_psi' (+ f_IB
     // inside the bricks the markers spread into)
-    const bool ib = a.region != 1 && a.bflag[((zz >> 2) * a.nby + (y >> 2)) * a.nbx + (x >> 2)] != 0;
+    const bool ib = a.bflag[((zz >> 2) * a.nby + (y >> 2)) * a.nbx + (x >> 2)] != 0;
     Real F[3];
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
