@@ -253,14 +253,19 @@ def main():
 
     # end to end through the public API with host buffers: upload the initial
     # fields, step, read back the C3 field and the markers
-    Ch = np.ascontiguousarray(np.stack([sim.field("C1"), sim.field("C2"), sim.field("C3")]))
-    Uh = np.ascontiguousarray(sim.field("u"))
+    # (pinned host buffers, as a serving loop would keep them)
+    def pinned(*shape):
+        return torch.empty(shape, dtype=torch.float64, pin_memory=True).numpy()
+    Ch, Uh, c3 = pinned(3, N), pinned(3, N), pinned(N)
+    for k, name in enumerate(("C1", "C2", "C3")):
+        Ch[k] = sim.field(name)
+    Uh[:] = sim.field("u")
     Ke = args.steps
     torch.cuda.synchronize(dev)
     t0 = time.perf_counter()
     sim.init(Ch, Uh)
     sim.step(Ke)
-    c3 = sim.field("C3")
+    sim.field("C3", out=c3)
     X = sim.nodes(0)
     t1 = time.perf_counter()
     e2e_v = world * N * Ke / (t1 - t0) / 1e6

@@ -282,11 +282,16 @@ class Simulation:
     def launches(self) -> int:
         return lib().tlb_last_launch_count(self.h)
 
-    def field(self, name: str) -> np.ndarray:
+    def field(self, name: str, out=None) -> np.ndarray:
+        """A field as doubles (``u``: shape (3, N)); ``out`` may supply the
+        host buffer (e.g. pinned memory) of N (3 N) contiguous doubles."""
         n = self.N * (3 if name == "u" else 1)
-        out = np.zeros(n)
+        if out is None:
+            out = np.empty(n)
+        elif out.dtype != np.float64 or out.size != n or not out.flags.c_contiguous:
+            raise TLBError(f"field: out must hold {n} contiguous doubles")
         _check(lib().tlb_read_field(self.h, FIELD[name], _dp(out), n))
-        return out.reshape(3, self.N) if name == "u" else out
+        return out.reshape(3, self.N) if name == "u" else out.reshape(-1)
 
     def nodes(self, m: int = 0) -> np.ndarray:
         out = np.zeros(3 * self.nn[m])

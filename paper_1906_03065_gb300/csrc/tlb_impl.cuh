@@ -197,7 +197,7 @@ struct Impl : ImplBase {
 
   tlb_status init_fields(Ctx* c, const double* C, const double* u) override {
     cudaStream_t s = c->stream;
-    const long long N = c->N, P = c->P;
+    const long long N = c->N;
     IBArgs<Real> ia = ibargs(c);
     // membrane profile I(X0) (I_out everywhere when there are no membranes)
     if (c->nn > 0) {
@@ -207,58 +207,28 @@ struct Impl : ImplBase {
       if (st != TLB_OK) return st;
       c->box_stale = true;  // the first step recomputes the box of X0
     }
-    std::vector<Real> h((size_t)3 * P, Real(0));
     Real* rho = c->ptr<Real>(c->L.rho);
     Real* phi = c->ptr<Real>(c->L.phi);
     Real* psi = c->ptr<Real>(c->L.psi);
+    Real* uf = c->ptr<Real>(c->L.ftot);  // velocity (free before the first step)
+    // the caller's arrays go to the other population buffer (free until the
+    // first step; at least 48 bytes per cell) and are converted on the device
+    double* scratch = c->ptr<double>(c->L.lo[1 - c->cur]);
+    const double* Cd = nullptr;
+    const double* ud = nullptr;
     if (C) {
-      for (long long n = 0; n < N; ++n) {
-        h[n] = (Real)(C[n] + C[N + n] + C[2 * N + n]);
-        h[P + n] = (Real)(C[n] - C[N + n]);
-        h[2 * P + n] = (Real)C[2 * N + n];
-      }
-    } else {
-      std::vector<Real> I((size_t)N);
-      TLB_CUDA(cudaMemcpyAsync(I.data(), c->ptr<Real>(c->L.I), N * sizeof(Real), cudaMemcpyDeviceToHost, s));
-      TLB_CUDA(cudaStreamSynchronize(s));
-      const double al = c->p.alpha;
-      for (long long n = 0; n < N; ++n) {
-        long long z = n / ((long long)c->nx * c->ny);  // last axis (2D: y)
-        double sv = 0.5 * (1.0 + tanh((z - c->p.interface_pos) / (2.0 * al)));
-        if (c->p.interface_pos < 0) sv = 0.0;
-        double ps = (double)I[n];
-        h[n] = (Real)1.0;
-        h[P + n] = (Real)((1.0 - ps) * (2.0 * sv - 1.0));
-        h[2 * P + n] = (Real)ps;
-      }
+      TLB_CUDA(cudaMemcpyAsync(scratch, C, 3 * N * sizeof(double), cudaMemcpyHostToDevice, s));
+      Cd = scratch;
     }
-    TLB_CUDA(cudaMemcpyAsync(rho, h.data(), N * sizeof(Real), cudaMemcpyHostToDevice, s));
-    TLB_CUDA(cudaMemcpyAsync(phi, h.data() + P, N * sizeof(Real), cudaMemcpyHostToDevice, s));
-    TLB_CUDA(cudaMemcpyAsync(psi, h.data() + 2 * P, N * sizeof(Real), cudaMemcpyHostToDevice, s));
-    TLB_CUDA(cudaStreamSynchronize(s));
-    // velocity field into ftot (free before the first step)
-    std::vector<Real> hu((size_t)3 * P, Real(0));
-    for (long long n = 0; n < N; ++n) {
-      double v[3];
-      if (u) {
-        v[0] = u[n];
-        v[1] = u[N + n];
-        v[2] = u[2 * N + n];
-      } else {
-        v[0] = c->p.u0[0];
-        v[1] = c->p.u0[1];
-        v[2] = c->p.u0[2];
-      }
-      if (c->p.dim == 2) {  // internal (x, 0, y)
-        hu[n] = (Real)v[0];
-        hu[P + n] = 0;
-        hu[2 * P + n] = (Real)v[1];
-      } else {
-        for (int d = 0; d < 3; ++d) hu[d * P + n] = (Real)v[d];
-      }
+    if (u) {
+      TLB_CUDA(cudaMemcpyAsync(scratch + 3 * N, u, 3 * N * sizeof(double), cudaMemcpyHostToDevice, s));
+      ud = scratch + 3 * N;
     }
-    Real* uf = c->ptr<Real>(c->L.ftot);
-    TLB_CUDA(cudaMemcpyAsync(uf, hu.data(), 3 * P * sizeof(Real), cudaMemcpyHostToDevice, s));
+    TLB_CUDA(cudaMemsetAsync(c->ptr<char>(c->L.ftot), 0, c->L.ftot.bytes, s));
+    k_init_fields<Real><<<blocks(N, 256), 256, 0, s>>>(geo(c), c->p.dim, Cd, ud, c->p.u0[0], c->p.u0[1], c->p.u0[2],
+                                                       c->p.alpha, c->p.interface_pos, c->ptr<Real>(c->L.I), rho,
+                                                       phi, psi, uf);
+    TLB_LAUNCHED(c, "k_init_fields");
     Geo G = geo(c);
     LBArgs<MODE> la = lbargs(c, c->cur);
     Real* mu = c->ptr<Real>(c->L.mu);
@@ -470,47 +440,19 @@ struct Impl : ImplBase {
     cudaStream_t s = c->stream;
     const long long N = c->N;
     double* rb = c->ptr<double>(c->L.rb);
-    Geo G = geo(c);
-    std::vector<double> tmp;
-    if (field == TLB_FIELD_I) {
-      if (nvals < (size_t)N) { set_error("read_field: buffer too small"); return TLB_ERR_ARG; }
-      std::vector<Real> h((size_t)N);
-      TLB_CUDA(cudaMemcpyAsync(h.data(), c->ptr<Real>(c->L.I), N * sizeof(Real), cudaMemcpyDeviceToHost, s));
-      TLB_CUDA(cudaStreamSynchronize(s));
-      for (long long i = 0; i < N; ++i) dst[i] = (double)h[i];
-      return TLB_OK;
-    }
     const size_t need = field == TLB_FIELD_U ? 3 * (size_t)N : (size_t)N;
     if (nvals < need) { set_error("read_field: buffer too small"); return TLB_ERR_ARG; }
-    k_fields<L, MODE><<<blocks(N, 256), 256, 0, s>>>(G, c->ptr<Store>(c->L.lo[c->cur]),
-                                                      c->ptr<Rest>(c->L.rest[c->cur]), rb);
-    TLB_LAUNCHED(c, "k_fields");
-    tmp.resize((size_t)6 * N);
-    TLB_CUDA(cudaMemcpyAsync(tmp.data(), rb, 6 * N * sizeof(double), cudaMemcpyDeviceToHost, s));
-    TLB_CUDA(cudaStreamSynchronize(s));
-    const double* r = tmp.data();
-    const double* ph = r + N;
-    const double* ps = r + 2 * N;
-    for (long long i = 0; i < N; ++i) {
-      switch (field) {
-        case TLB_FIELD_RHO: dst[i] = r[i]; break;
-        case TLB_FIELD_PHI: dst[i] = ph[i]; break;
-        case TLB_FIELD_PSI: dst[i] = ps[i]; break;
-        case TLB_FIELD_C1: dst[i] = 0.5 * (r[i] + ph[i] - ps[i]); break;
-        case TLB_FIELD_C2: dst[i] = 0.5 * (r[i] - ph[i] - ps[i]); break;
-        case TLB_FIELD_C3: dst[i] = ps[i]; break;
-        case TLB_FIELD_U:
-          if (c->p.dim == 2) {
-            dst[i] = r[3 * N + i];
-            dst[N + i] = r[5 * N + i];
-            dst[2 * N + i] = 0.0;
-          } else {
-            for (int d = 0; d < 3; ++d) dst[d * N + i] = r[(3 + d) * N + i];
-          }
-          break;
-        default: set_error("read_field: unknown field"); return TLB_ERR_ARG;
-      }
+    // the field is formed on the device, only its values cross to the host
+    if (field == TLB_FIELD_I) {
+      k_to_double<Real><<<blocks(N, 256), 256, 0, s>>>(c->ptr<Real>(c->L.I), N, rb);
+      TLB_LAUNCHED(c, "k_to_double");
+    } else {
+      k_fields<L, MODE><<<blocks(N, 256), 256, 0, s>>>(geo(c), c->ptr<Store>(c->L.lo[c->cur]),
+                                                        c->ptr<Rest>(c->L.rest[c->cur]), field, rb);
+      TLB_LAUNCHED(c, "k_fields");
     }
+    TLB_CUDA(cudaMemcpyAsync(dst, rb, need * sizeof(double), cudaMemcpyDeviceToHost, s));
+    TLB_CUDA(cudaStreamSynchronize(s));
     return TLB_OK;
   }
 

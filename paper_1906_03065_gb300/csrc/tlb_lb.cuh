@@ -394,9 +394,52 @@ __global__ void k_init_eq(Geo G, const typename Prec<MODE>::Real* rho, const typ
 }
 
 // Fields of the streamed populations for read-back: rho, phi, psi, u.
+// Working-precision copy of a field as doubles (read-out).
+template <class Real>
+__global__ void k_to_double(const Real* src, long long n, double* dst) {
+  long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) dst[i] = (double)src[i];
+}
+
+// Initial fields from the caller's compositions C = [3][N] (FP64 sums, then
+// the working precision): rho = C1 + C2 + C3, phi = C1 - C2, psi = C3; or,
+// without C, the default state: rho = 1, psi = I, phi = (1 - I)(2 s - 1)
+// with the flat interface s(z) = (1 + tanh((z - z0)/(2 alpha)))/2 (s = 0
+// when z0 < 0).  The velocity ([3][N], or the uniform u0) goes to uf, 2D
+// fields internally as (x, 0, y).
+template <class Real>
+__global__ void k_init_fields(Geo G, int dim, const double* C, const double* u, double u0x, double u0y,
+                              double u0z, double alpha, double z0, const Real* I, Real* rho, Real* phi,
+                              Real* psi, Real* uf) {
+  const long long N = G.N, P = G.P;
+  long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= N) return;
+  if (C) {
+    rho[n] = (Real)(C[n] + C[N + n] + C[2 * N + n]);
+    phi[n] = (Real)(C[n] - C[N + n]);
+    psi[n] = (Real)C[2 * N + n];
+  } else {
+    const long long z = n / ((long long)G.nx * G.ny);  // last axis (2D: y)
+    double sv = 0.5 * (1.0 + tanh((z - z0) / (2.0 * alpha)));
+    if (z0 < 0) sv = 0.0;
+    const double ps = (double)I[n];
+    rho[n] = (Real)1.0;
+    phi[n] = (Real)((1.0 - ps) * (2.0 * sv - 1.0));
+    psi[n] = (Real)ps;
+  }
+  const double v[3] = {u ? u[n] : u0x, u ? u[N + n] : u0y, u ? u[2 * N + n] : u0z};
+  if (dim == 2) {
+    uf[n] = (Real)v[0];
+    uf[P + n] = 0;
+    uf[2 * P + n] = (Real)v[1];
+  } else {
+    for (int d = 0; d < 3; ++d) uf[d * P + n] = (Real)v[d];
+  }
+}
+
 template <class L, int MODE>
 __global__ void k_fields(Geo G, const typename Prec<MODE>::Store* lo, const typename Prec<MODE>::Rest* rest,
-                         double* out /* [6][N] */) {
+                         int field, double* out /* [N], [3][N] for the velocity */) {
   using Real = typename Prec<MODE>::Real;
   long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (n >= G.N) return;
@@ -404,11 +447,23 @@ __global__ void k_fields(Geo G, const typename Prec<MODE>::Store* lo, const type
   Pull<L, MODE> p;
   p.load(lo, rest, G, x, y, z);
   CellMoments<Real> m = p.moments();
-  double rho = 1.0 + (double)m.drho;
-  out[n] = rho;
-  out[G.N + n] = (double)m.phi;
-  out[2 * G.N + n] = (double)m.psi;
-  for (int d = 0; d < 3; ++d) out[(3 + d) * G.N + n] = (double)m.j[d] / rho;
+  const double rho = 1.0 + (double)m.drho, phi = (double)m.phi, psi = (double)m.psi;
+  switch (field) {
+    case TLB_FIELD_RHO: out[n] = rho; break;
+    case TLB_FIELD_PHI: out[n] = phi; break;
+    case TLB_FIELD_PSI: out[n] = psi; break;
+    case TLB_FIELD_C1: out[n] = 0.5 * (rho + phi - psi); break;
+    case TLB_FIELD_C2: out[n] = 0.5 * (rho - phi - psi); break;
+    case TLB_FIELD_C3: out[n] = psi; break;
+    default:  // velocity; 2D fields are internal (x, 0, y)
+      if (L::DIM == 2) {
+        out[n] = (double)m.j[0] / rho;
+        out[G.N + n] = (double)m.j[2] / rho;
+        out[2 * G.N + n] = 0.0;
+      } else {
+        for (int d = 0; d < 3; ++d) out[d * G.N + n] = (double)m.j[d] / rho;
+      }
+  }
 }
 
 // ------------------------------------------------------------ residual
