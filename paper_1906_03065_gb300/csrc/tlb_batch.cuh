@@ -72,9 +72,9 @@ template <int MODE> struct OpFill {
 template <int MODE> struct OpSpread {
   static __device__ __forceinline__ void run(const BArgs<MODE>& s, const Blk& b) { spread_body(s.ib, b); }
 };
-template <class L, int MODE, int TX, int TY, bool PF> struct OpCollide {
+template <class L, int MODE, int TX, int TY, int FORM> struct OpCollide {
   static __device__ __forceinline__ void run(const BArgs<MODE>& s, const Blk& b) {
-    collide_body<L, MODE, TX, TY, PF>(s.lb, b);
+    collide_body<L, MODE, TX, TY, FORM>(s.lb, b);
   }
 };
 template <class L, int MODE> struct OpInterp {
@@ -173,7 +173,7 @@ struct BatchImpl : BatchBase {
     }
   }
 
-  // tile variants as in Impl::collide (3..5: 0..2 with prefetch)
+  // tile shape of a collide variant (v % 3; the form is v / 3)
   static int tile_x(int v) {
     v %= 3;
     if constexpr (L::DIM == 3) return v == 2 ? 64 : 32;
@@ -241,64 +241,36 @@ struct BatchImpl : BatchBase {
     return TLB_OK;
   }
 
-  template <int TX, int TY, bool PF>
+  template <int TX, int TY, int FORM>
   static int collide_occ() {
     int per_sm = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-        &per_sm, k_phase<TX * TY, collide_threads<PF>() / (TX * TY), BA, OpCollide<L, MODE, TX, TY, PF>>, TX * TY,
-        0);
+        &per_sm, k_phase<TX * TY, collide_threads<FORM>() / (TX * TY), BA, OpCollide<L, MODE, TX, TY, FORM>>,
+        TX * TY, 0);
     return std::max(1, per_sm);
   }
   static int collide_occupancy(int v) {
-    if constexpr (L::DIM == 3) {
-      switch (v) {
-        case 1: return collide_occ<32, 8, false>();
-        case 2: return collide_occ<64, 4, false>();
-        case 3: return collide_occ<32, 4, true>();
-        case 4: return collide_occ<32, 8, true>();
-        case 5: return collide_occ<64, 4, true>();
-        default: return collide_occ<32, 4, false>();
-      }
-    } else {
-      switch (v) {
-        case 1: return collide_occ<64, 1, false>();
-        case 2: return collide_occ<128, 1, false>();
-        case 3: return collide_occ<32, 1, true>();
-        case 4: return collide_occ<64, 1, true>();
-        case 5: return collide_occ<128, 1, true>();
-        default: return collide_occ<32, 1, false>();
-      }
-    }
+    int per_sm = 1;
+    collide_variant<L>(v, [&](auto tx, auto ty, auto fm) {
+      per_sm = collide_occ<decltype(tx)::value, decltype(ty)::value, decltype(fm)::value>();
+      return TLB_OK;
+    });
+    return per_sm;
   }
 
-  template <int TX, int TY, bool PF>
+
+  template <int TX, int TY, int FORM>
   static tlb_status launch_collide_t(Batch* b, const BA* A, const int4* vg, cudaStream_t s) {
     const int n = (int)b->act.size();
-    k_phase<TX * TY, collide_threads<PF>() / (TX * TY), BA, OpCollide<L, MODE, TX, TY, PF>>
+    k_phase<TX * TY, collide_threads<FORM>() / (TX * TY), BA, OpCollide<L, MODE, TX, TY, FORM>>
         <<<b->ph_grid[4], TX * TY, 0, s>>>(A, vg, n, b->ph_ent[4], b->ph_total[4]);
     b->launches++;
     return cuda_check(cudaGetLastError(), "k_phase collide");
   }
   static tlb_status launch_collide(Batch* b, const BA* A, const int4* vg, cudaStream_t s) {
-    if constexpr (L::DIM == 3) {
-      switch (b->tile_variant) {
-        case 1: return launch_collide_t<32, 8, false>(b, A, vg, s);
-        case 2: return launch_collide_t<64, 4, false>(b, A, vg, s);
-        case 3: return launch_collide_t<32, 4, true>(b, A, vg, s);
-        case 4: return launch_collide_t<32, 8, true>(b, A, vg, s);
-        case 5: return launch_collide_t<64, 4, true>(b, A, vg, s);
-        default: return launch_collide_t<32, 4, false>(b, A, vg, s);
-      }
-    } else {
-      switch (b->tile_variant) {
-        case 1: return launch_collide_t<64, 1, false>(b, A, vg, s);
-        case 2: return launch_collide_t<128, 1, false>(b, A, vg, s);
-        case 3: return launch_collide_t<32, 1, true>(b, A, vg, s);
-        case 4: return launch_collide_t<64, 1, true>(b, A, vg, s);
-        case 5: return launch_collide_t<128, 1, true>(b, A, vg, s);
-        default: return launch_collide_t<32, 1, false>(b, A, vg, s);
-      }
-    }
+    return collide_variant<L>(b->tile_variant, [&](auto tx, auto ty, auto fm) {
+      return launch_collide_t<decltype(tx)::value, decltype(ty)::value, decltype(fm)::value>(b, A, vg, s);
+    });
   }
 
   const int4* vg_of(Batch* b, int ph) const {
@@ -493,7 +465,7 @@ struct BatchImpl : BatchBase {
       b->launches++;
       TLB_CUDA(cudaGetLastError());
     }
-    for (int v = 0; v < 6 && st == TLB_OK; ++v)
+    for (int v = 0; v < COLLIDE_NVAR && st == TLB_OK; ++v)
       for (int zi = 0; zi < 6 && st == TLB_OK; ++zi) {
         if (zcs[zi] > nzmax && zi > 0 && zcs[zi - 1] >= nzmax) continue;
         b->tile_variant = v;

@@ -10,6 +10,9 @@
 
 #include "../../include/tlb.h"
 
+// Collide variants: 3 tile shapes x 4 register forms, v = 3 form + tile.
+constexpr int COLLIDE_NVAR = 12;
+
 struct Ctx;
 
 struct ImplBase {
@@ -94,7 +97,7 @@ struct Ctx {
   int nn = 0, ne = 0, NV = 0, ncap = 0, nedge = 0;
   int nbx = 0, nby = 0, nbz = 0, nbricks = 0;
   int tiles_zc = 16;
-  int tile_variant = 0;  // collide tile shape (see Impl::collide)
+  int tile_variant = 0;  // collide tile shape and form (see collide_variant)
   PhaseEvents* prof = nullptr;  // non-null while tlb_profile_steps runs
   double prof_ms[4] = {0, 0, 0, 0};
   ImplBase* impl = nullptr;

@@ -14,13 +14,6 @@ struct Impl : ImplBase {
   using Real = typename Prec<MODE>::Real;
   using Store = typename Prec<MODE>::Store;
   using Rest = typename Prec<MODE>::Rest;
-  // tile shapes of the collide plane sweep (variant index = c->tile_variant;
-  // variants 3..5 are 0..2 with the next population set prefetched)
-  static constexpr int NVAR = 6;
-  static constexpr int TXS[NVAR] = {32, 32, 64};
-  static constexpr int TYS3[NVAR] = {4, 8, 4};
-  static constexpr int TYS2[NVAR] = {1, 1, 1};
-  static constexpr int TXS2[NVAR] = {32, 64, 128};
 
   static Geo geo(const Ctx* c) {
     Geo g;
@@ -179,18 +172,25 @@ struct Impl : ImplBase {
     return TLB_OK;
   }
 
-  // Profile I of the band and the rest of the box, and the coupling sums
-  // (needs psi(t)).
-  static tlb_status ibm_band(Ctx* c, IBArgs<Real>& a, cudaStream_t s) {
-    k_band<Real><<<8 * 152, 256, 0, s>>>(a);
+  // Profile I of the band and the coupling sums (needs psi(t)); the rest of
+  // the box (column fill).
+  static tlb_status launch_band(Ctx* c, IBArgs<Real>& a, cudaStream_t s) {
+    k_band<Real><<<8 * c->nsm, 256, 0, s>>>(a);
     TLB_LAUNCHED(c, "k_band");
+    return TLB_OK;
+  }
+  static tlb_status launch_fill(Ctx* c, IBArgs<Real>& a, cudaStream_t s) {
     k_fill<Real><<<blocks((long long)c->nx * c->ny * 32, 256), 256, 0, s>>>(a);
     TLB_LAUNCHED(c, "k_fill");
     return TLB_OK;
   }
+  static tlb_status ibm_band(Ctx* c, IBArgs<Real>& a, cudaStream_t s) {
+    tlb_status st = launch_band(c, a, s);
+    return st == TLB_OK ? launch_fill(c, a, s) : st;
+  }
 
   static tlb_status ibm_spread(Ctx* c, IBArgs<Real>& a, cudaStream_t s) {
-    k_spread<Real><<<min(c->nbricks, 8 * 152), 64, 0, s>>>(a);
+    k_spread<Real><<<min(c->nbricks, 8 * c->nsm), 64, 0, s>>>(a);
     TLB_LAUNCHED(c, "k_spread");
     return TLB_OK;
   }
@@ -300,34 +300,19 @@ struct Impl : ImplBase {
     return TLB_OK;
   }
 
-  template <int TXv, int TYv, bool PF>
+  template <int TXv, int TYv, int FORM>
   static tlb_status collide_tile(Ctx* c, LBArgs<MODE>& la, cudaStream_t s) {
     dim3 grid(blocks(c->nx, TXv), blocks(c->ny, TYv), blocks(c->nz, c->tiles_zc));
-    k_collide<L, MODE, TXv, TYv, PF><<<grid, TXv * TYv, 0, s>>>(la);
+    k_collide<L, MODE, TXv, TYv, FORM><<<grid, TXv * TYv, 0, s>>>(la);
     TLB_LAUNCHED(c, "k_collide");
     return TLB_OK;
   }
 
+  // the collide in the context's variant (tile shape and form)
   static tlb_status collide(Ctx* c, LBArgs<MODE>& la, cudaStream_t s) {
-    if constexpr (L::DIM == 3) {
-      switch (c->tile_variant) {
-        case 1: return collide_tile<32, 8, false>(c, la, s);
-        case 2: return collide_tile<64, 4, false>(c, la, s);
-        case 3: return collide_tile<32, 4, true>(c, la, s);
-        case 4: return collide_tile<32, 8, true>(c, la, s);
-        case 5: return collide_tile<64, 4, true>(c, la, s);
-        default: return collide_tile<32, 4, false>(c, la, s);
-      }
-    } else {
-      switch (c->tile_variant) {
-        case 1: return collide_tile<64, 1, false>(c, la, s);
-        case 2: return collide_tile<128, 1, false>(c, la, s);
-        case 3: return collide_tile<32, 1, true>(c, la, s);
-        case 4: return collide_tile<64, 1, true>(c, la, s);
-        case 5: return collide_tile<128, 1, true>(c, la, s);
-        default: return collide_tile<32, 1, false>(c, la, s);
-      }
-    }
+    return collide_variant<L>(c->tile_variant, [&](auto tx, auto ty, auto fm) {
+      return collide_tile<decltype(tx)::value, decltype(ty)::value, decltype(fm)::value>(c, la, s);
+    });
   }
 
   // Choose the collide tile shape and z chunk by timing the kernel on the
@@ -343,7 +328,7 @@ struct Impl : ImplBase {
     float best = 1e30f;
     int bv = c->tile_variant, bz = c->tiles_zc;
     const int zcs[6] = {4, 8, 12, 16, 32, 64};
-    for (int v = 0; v < NVAR; ++v)
+    for (int v = 0; v < COLLIDE_NVAR; ++v)
       for (int zi = 0; zi < 6; ++zi) {
         if (zcs[zi] > c->nz && zi > 0 && zcs[zi - 1] >= c->nz) continue;
         c->tile_variant = v;
@@ -412,12 +397,13 @@ struct Impl : ImplBase {
       if ((st = mark(c, 1)) != TLB_OK) return st;
       // the profile, coupling sums and spreading need psi(t) and the
       // position work: they follow the moments, then the whole lattice is
-      // collided in one launch (splitting it to overlap the membrane work
-      // with the tiles away from the membrane measured slower)
+      // collided in one launch
       if (c->nn > 0) {
         TLB_CUDA(cudaEventRecord(c->ev_join, c->side));
         TLB_CUDA(cudaStreamWaitEvent(s, c->ev_join, 0));
         TLB_CUDA(cudaStreamWaitEvent(s, c->ev_bins, 0));
+        // (in order: running the fill beside the spreading, or splitting the
+        // collide to overlap this work, measured slower)
         if ((st = ibm_band(c, ia, s)) != TLB_OK) return st;
         if ((st = ibm_spread(c, ia, s)) != TLB_OK) return st;
       }

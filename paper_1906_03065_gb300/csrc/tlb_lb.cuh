@@ -2,6 +2,8 @@
 // force + collision + streaming plane sweep, initial equilibria and the
 // conversions used by read/write of populations.
 #pragma once
+#include <type_traits>
+
 #include "tlb_common.cuh"
 
 template <int MODE>
@@ -66,8 +68,9 @@ __device__ __forceinline__ Real eq_poly(Real cu, Real uu) {
 // the chemical potentials (halo 1), so each cell's radius-2 dependency (mu
 // needs the Laplacian of the moments, the force needs the gradient of mu) is
 // served on chip.
-template <class L, int MODE, int TX, int TY, bool PF>
+template <class L, int MODE, int TX, int TY, int FORM>
 __device__ __forceinline__ void collide_body(const LBArgs<MODE>& a, const Blk& blk) {
+  constexpr bool PF = FORM == 1;  // the next population set prefetched
   using Real = typename Prec<MODE>::Real;
   using Store = typename Prec<MODE>::Store;
   using Rest = typename Prec<MODE>::Rest;
@@ -315,12 +318,39 @@ __device__ __forceinline__ void collide_body(const LBArgs<MODE>& a, const Blk& b
 }
 // Resident threads per SM the collide is compiled for: 640 (96 registers)
 // or, with the next population set prefetched, 512 (128 registers).
-template <bool PF> constexpr int collide_threads() { return PF ? 512 : 640; }
+// Forms of the collide: threads per SM the register budget is set for
+// (0: 640; 1: 512 with the next set prefetched; 2: 768; 3: 1024).
+template <int FORM> constexpr int collide_threads() {
+  return FORM == 1 ? 512 : (FORM == 2 ? 768 : (FORM == 3 ? 1024 : 640));
+}
 
-template <class L, int MODE, int TX, int TY, bool PF>
-__global__ void __launch_bounds__(TX* TY, collide_threads<PF>() / (TX * TY))
+template <class L, int MODE, int TX, int TY, int FORM>
+__global__ void __launch_bounds__(TX* TY, collide_threads<FORM>() / (TX * TY))
     k_collide(const __grid_constant__ LBArgs<MODE> a) {
-  collide_body<L, MODE, TX, TY, PF>(a, hw_blk());
+  collide_body<L, MODE, TX, TY, FORM>(a, hw_blk());
+}
+
+// Calls fn(tile x, tile y, form) with the variant's compile-time values
+// (3D tiles 32x4, 32x8, 64x4; 2D rows of 32, 64, 128).
+template <int V> using CIdx = std::integral_constant<int, V>;
+template <class L, class Fn>
+__host__ tlb_status collide_variant(int v, Fn&& fn) {
+  constexpr bool D3 = L::DIM == 3;
+  constexpr int X1 = D3 ? 32 : 64, Y1 = D3 ? 8 : 1, X2 = D3 ? 64 : 128, Y0 = D3 ? 4 : 1;
+  switch (v) {
+    case 1: return fn(CIdx<X1>{}, CIdx<Y1>{}, CIdx<0>{});
+    case 2: return fn(CIdx<X2>{}, CIdx<Y0>{}, CIdx<0>{});
+    case 3: return fn(CIdx<32>{}, CIdx<Y0>{}, CIdx<1>{});
+    case 4: return fn(CIdx<X1>{}, CIdx<Y1>{}, CIdx<1>{});
+    case 5: return fn(CIdx<X2>{}, CIdx<Y0>{}, CIdx<1>{});
+    case 6: return fn(CIdx<32>{}, CIdx<Y0>{}, CIdx<2>{});
+    case 7: return fn(CIdx<X1>{}, CIdx<Y1>{}, CIdx<2>{});
+    case 8: return fn(CIdx<X2>{}, CIdx<Y0>{}, CIdx<2>{});
+    case 9: return fn(CIdx<32>{}, CIdx<Y0>{}, CIdx<3>{});
+    case 10: return fn(CIdx<X1>{}, CIdx<Y1>{}, CIdx<3>{});
+    case 11: return fn(CIdx<X2>{}, CIdx<Y0>{}, CIdx<3>{});
+    default: return fn(CIdx<32>{}, CIdx<Y0>{}, CIdx<0>{});
+  }
 }
 
 // ------------------------------------------------------------- init & I/O

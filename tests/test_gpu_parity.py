@@ -194,13 +194,14 @@ def test_full_size_capsule_3d_init_and_step():
 
 @pytest.mark.parametrize("storage", ["f32", "f16"])
 def test_collide_tile_variants_agree(storage):
-    """Every tile shape, z chunk and the prefetching form of the collide give
-    the same state (the per-cell arithmetic does not depend on them)."""
+    """Every tile shape, z chunk and register form of the collide (prefetching,
+    640/768/1024 threads per SM) give the same state (the per-cell
+    arithmetic does not depend on them)."""
     wl = W.small_3d(storage)
     ref = _sim(wl).init()
     ref.step(12)
     P = ref.pops()
-    for v, zc in ((1, 5), (2, 16), (3, 7), (4, 12), (5, 34)):
+    for v, zc in ((1, 5), (2, 16), (3, 7), (4, 12), (5, 34), (6, 9), (7, 12), (8, 3), (9, 12), (10, 6), (11, 20)):
         g = _sim(wl).init()
         g.set_tile(v, zc)
         g.step(12)
