@@ -157,7 +157,7 @@ struct BatchImpl : BatchBase {
       case NODEF: return {mem ? (int)cdiv(32ll * c->nn, NT) : 0, 1, 1};
       case SCAT: {
         const long long nfeat = (long long)c->ne + (c->NV == 3 ? c->nedge : 0) + c->nn;
-        return {mem ? (int)cdiv(nfeat, SCATTER_WARPS) : 0, 1, 1};
+        return {mem ? SCAT_SPLIT * (int)cdiv(nfeat, 32 * scatter_warps<typename Prec<MODE>::Real>()) : 0, 1, 1};
       }
       case BCOMP: return {mem ? (int)cdiv(c->nbricks, NT) : 0, 1, 1};
       case BAND: return {mem ? b->band_blocks[i] : 0, 1, 1};

@@ -349,6 +349,30 @@ struct FaceDist {
   V3<Real> A, B, ab, ac, bc;
   Real d00, d01, d11, i00, i11, ibc, iden;
   bool tri;
+  static constexpr int NC = 22;  // constants kept in shared memory
+  __device__ __forceinline__ FaceDist() {}
+  __device__ __forceinline__ void store(Real* p) const {
+    const Real v[NC] = {A.x,  A.y,  A.z,  B.x,  B.y,  B.z,  ab.x, ab.y, ab.z, ac.x, ac.y,
+                        ac.z, bc.x, bc.y, bc.z, d00,  d01,  d11,  i00,  i11,  ibc,  iden};
+    for (int i = 0; i < NC; ++i) p[i] = v[i];
+  }
+  __device__ __forceinline__ static FaceDist load(const Real* p, bool is_tri) {
+    FaceDist f;
+    f.A = mk<Real>(p[0], p[1], p[2]);
+    f.B = mk<Real>(p[3], p[4], p[5]);
+    f.ab = mk<Real>(p[6], p[7], p[8]);
+    f.ac = mk<Real>(p[9], p[10], p[11]);
+    f.bc = mk<Real>(p[12], p[13], p[14]);
+    f.d00 = p[15];
+    f.d01 = p[16];
+    f.d11 = p[17];
+    f.i00 = p[18];
+    f.i11 = p[19];
+    f.ibc = p[20];
+    f.iden = p[21];
+    f.tri = is_tri;
+    return f;
+  }
   __device__ __forceinline__ FaceDist(V3<Real> a, V3<Real> b, V3<Real> c, bool is_tri) : A(a), B(b), tri(is_tri) {
     ab = b - a;
     ac = c - a;
@@ -400,14 +424,32 @@ struct FaceDist {
 // is enumerated.  Distances are compared on a grid of 2^-34 lattice units,
 // ties going to the lowest element index.
 constexpr int MAXG = 12;  // generators (and faces) per feature
-constexpr int SCATTER_WARPS = 4;
+constexpr int SCAT_W = 4;       // slices per lane per round
+constexpr int SCAT_SPLIT = 4;   // warps sharing one group of 32 features (round r goes to r % SCAT_SPLIT)
+// warps per block (every lane sweeps one feature): FP64 halves them to keep
+// the shared memory under the static limit
+template <class Real> constexpr int scatter_warps() { return sizeof(Real) == 4 ? 4 : 2; }
 
-// Feature f: its corners, cone generators (unit normals) and the faces
-// containing it.  Returns the number of generators.
-// One warp per feature, one lane per slice.  Geometry is in Real relative to
-// an integer origin (the lattice cell below the first corner), so the FP32
-// build does its sweep in single precision without losing accuracy; slice
-// boxes are widened by 1e-3 cells to stay conservative under rounding.
+// Shared memory of one warp: lane l's feature in row l.
+template <class Real>
+struct ScatterWarp {
+  Real cb[32][9];               // corners relative to the feature's origin
+  Real gk[32][MAXG];            // 1 / generator component along the slice axis
+  Real ga[32][MAXG];            // generator components along the two other axes
+  Real gb[32][MAXG];
+  Real fd[32][FaceDist<Real>::NC];  // distance constants of the offered face
+  int4 sl[32][SCAT_W];          // the round's slices: a0, b0, width, cumulative cells
+  int4 ft[32][2];               // origin cell (wrapped) and packed axes; face, first slice
+};
+
+// One lane per feature, geometry in Real relative to an integer origin (the
+// lattice cell below the first corner), so the FP32 build sweeps in single
+// precision without losing accuracy; slice boxes are widened by 1e-3 cells
+// to stay conservative under rounding.  The warp then shares out the cells:
+// per round every lane sizes SCAT_W slices of its feature, a warp prefix sum
+// lays all their cells end to end, and the lanes take them round-robin.
+// SCAT_SPLIT virtual blocks set up the same features and take turns over
+// the rounds (the set-up is short; the rounds are not).
 // A feature offers only its lowest-index face: if the nearest point P of a
 // cell lies on the feature, every face containing the feature is at exactly
 // |x - P|, so that face carries the key the tie rule selects; faces offered
@@ -415,79 +457,64 @@ constexpr int SCATTER_WARPS = 4;
 // equal) distance and cannot win wrongly.
 template <class Real>
 __device__ __forceinline__ void dist_scatter_body(const IBArgs<Real>& a, const Blk& blk) {
-  __shared__ Real sV[SCATTER_WARPS][3][3];     // vertices of the offered face
-  __shared__ Real sG[SCATTER_WARPS][MAXG][3];  // cone generators
-  __shared__ Real sB[SCATTER_WARPS][3][3];     // feature corners
-  __shared__ Real sGi[SCATTER_WARPS][MAXG];    // 1 / (generator component along the slice axis)
+  constexpr int SW = scatter_warps<Real>();
+  __shared__ ScatterWarp<Real> smw[SW];
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (w >= SW) return;
+  ScatterWarp<Real>& sm = smw[w];
   const int nfeat = a.ne + (a.NV == 3 ? a.nedge : 0) + a.nn;
-  const int w = threadIdx.x >> 5;
-  const int f = blk.x * SCATTER_WARPS + w;
-  const int lane = threadIdx.x & 31;
-  if (f >= nfeat) return;
-  // The feature's corners (the same loads in every lane) and its cone
-  // generators, the normals of the faces containing it: lane j holds face j.
-  int corners[3] = {0, 0, 0}, nB, nG, trj = -1;
-  if (f < a.ne) {  // face (3D) or segment (2D)
-    nB = a.NV;
-    nG = 1;
-    for (int q = 0; q < a.NV; ++q) corners[q] = a.E[a.NV * f + q];
-    if (lane == 0) trj = f;
-  } else if (a.NV == 3 && f < a.ne + a.nedge) {  // edge
-    const int* ed = a.edges + 4 * (f - a.ne);
-    corners[0] = ed[0];
-    corners[1] = ed[1];
-    nB = 2;
-    nG = 2;
-    if (lane < 2) trj = ed[2 + lane];
-  } else {  // vertex
-    const int v = f - a.ne - (a.NV == 3 ? a.nedge : 0);
-    corners[0] = v;
-    nB = 1;
-    const int i0 = a.inc_off[v];
-    nG = min(a.inc_off[v + 1] - i0, MAXG);
-    if (lane < nG) trj = a.inc[i0 + lane];
-  }
-  if (nG <= 0) return;  // a vertex of no face offers nothing
-  const int tmin = (int)__reduce_min_sync(0xffffffffu, lane < nG ? (unsigned)trj : 0xffffffffu);
-  int o[3];
-  for (int d = 0; d < 3; ++d) o[d] = a.xo[3 * corners[0] + d];
-  if (a.dim == 2) o[1] = 0;
-  // the origin's cell wrapped into the lattice (offers index cells from it)
-  const int ow[3] = {wrap_coord(o[0], a.G.nx), wrap_coord(o[1], a.G.ny), a.G.wall ? o[2] : wrap_coord(o[2], a.G.nz)};
-  bool fin = true;
-  if (lane < 9) {
-    int q = lane / 3, d = lane % 3;
-    if (q < a.NV) sV[w][q][d] = node_off(a, a.E[a.NV * tmin + q], d, o[d]);
-    if (q < nB) {
-      const Real b = node_off(a, corners[q], d, o[d]);
-      sB[w][q][d] = b;
-      fin = fabs(b) < Real(1e6);  // rejects NaN/Inf
+  const int grp = blk.x / SCAT_SPLIT, phase = blk.x % SCAT_SPLIT;
+  const int f = (grp * SW + w) * 32 + lane;
+  if (__ballot_sync(0xffffffffu, f < nfeat) == 0) return;
+  // ---- the lane's feature: corners, cone generators (the normals of the
+  // faces containing it), slice axis and range, offered face
+  int kind = 0, nB = 0, nG = 0, i0 = 0, corners[3] = {0, 0, 0};
+  if (f < nfeat) {
+    if (f < a.ne) {  // face (3D) or segment (2D)
+      nB = a.NV;
+      nG = 1;
+      for (int q = 0; q < a.NV; ++q) corners[q] = a.E[a.NV * f + q];
+    } else if (a.NV == 3 && f < a.ne + a.nedge) {  // edge
+      kind = 1;
+      const int* ed = a.edges + 4 * (f - a.ne);
+      corners[0] = ed[0];
+      corners[1] = ed[1];
+      nB = 2;
+      nG = 2;
+    } else {  // vertex
+      kind = 2;
+      const int v = f - a.ne - (a.NV == 3 ? a.nedge : 0);
+      corners[0] = v;
+      nB = 1;
+      i0 = a.inc_off[v];
+      nG = min(a.inc_off[v + 1] - i0, MAXG);
     }
   }
-  Real g[3] = {0, 0, 0};
-  if (lane < nG) {
-    for (int d = 0; d < 3; ++d) {
-      g[d] = a.en[3 * trj + d];
-      sG[w][lane][d] = g[d];
-      fin &= fabs(g[d]) <= Real(1.001);
+  auto face_of = [&](int j) { return kind == 0 ? f : (kind == 1 ? a.edges[4 * (f - a.ne) + 2 + j] : a.inc[i0 + j]); };
+  bool ok = nG > 0;
+  int o[3] = {0, 0, 0}, tmin = 0x7fffffff;
+  Real S[3] = {0, 0, 0};
+  if (ok) {
+    for (int d = 0; d < 3; ++d) o[d] = a.xo[3 * corners[0] + d];
+    if (a.dim == 2) o[1] = 0;
+    for (int j = 0; j < nG; ++j) {
+      const int t = face_of(j);
+      tmin = min(tmin, t);
+      for (int d = 0; d < 3; ++d) {
+        const Real g = a.en[3 * t + d];
+        S[d] += g;
+        ok &= fabs(g) <= Real(1.001);
+      }
     }
+    for (int q = 0; q < nB; ++q)
+      for (int d = 0; d < 3; ++d) {
+        const Real b = node_off(a, corners[q], d, o[d]);
+        sm.cb[lane][3 * q + d] = b;
+        ok &= fabs(b) < Real(1e6);  // rejects NaN/Inf
+      }
+    if (!ok) atomicOr(a.status, (unsigned)ST_NAN);
   }
-  if (!__all_sync(0xffffffffu, fin)) {
-    if (lane == 0) atomicOr(a.status, (unsigned)ST_NAN);
-    return;
-  }
-  __syncwarp();
-  const Real dc = a.dc;
-  // slice axis: largest component of the generator sum, all generators of
-  // one sign (the sum is broadcast from lane 0 so every lane takes the
-  // same axis; any axis gives the same offers' minima)
-  Real S[3] = {g[0], g[1], g[2]};
-#pragma unroll
-  for (int sh = 16; sh > 0; sh >>= 1)
-#pragma unroll
-    for (int d = 0; d < 3; ++d) S[d] += __shfl_xor_sync(0xffffffffu, S[d], sh);
-#pragma unroll
-  for (int d = 0; d < 3; ++d) S[d] = __shfl_sync(0xffffffffu, S[d], 0);
+  // slice axis: largest component of the generator sum, all generators of one sign
   int k = 0;
   if (a.dim == 3) {
     if (fabs(S[1]) > fabs(S[k])) k = 1;
@@ -495,41 +522,57 @@ __device__ __forceinline__ void dist_scatter_body(const IBArgs<Real>& a, const B
   } else {
     k = fabs(S[2]) > fabs(S[0]) ? 2 : 0;
   }
-  Real gmin = lane < nG ? g[k] * (S[k] >= 0 ? Real(1) : Real(-1)) : Real(1e30f);
-#pragma unroll
-  for (int sh = 16; sh > 0; sh >>= 1) gmin = fmin(gmin, __shfl_xor_sync(0xffffffffu, gmin, sh));
-  // reciprocals of the generators' slice components (the rectangles are
-  // widened by eps, far above the rounding of a product)
-  if (lane < nG) sGi[w][lane] = rcp_rn(g[k]);
-  __syncwarp();
   int oa, ob;
   if (a.dim == 3) { oa = k == 0 ? 1 : 0; ob = k == 2 ? 1 : 2; }
   else { oa = k == 0 ? 2 : 0; ob = 1; }
-  Real bmin = 1e30f, bmax = -1e30f;
-  for (int q = 0; q < nB; ++q) { bmin = fmin(bmin, sB[w][q][k]); bmax = fmax(bmax, sB[w][q][k]); }
-  const Real eps = Real(1e-3);
-  const int c0 = (int)ceil(bmin - dc - eps), c1 = (int)floor(bmax + dc + eps);
-  const bool wide = gmin < Real(0.25);  // a generator nearly parallel to the slices
-  const V3<Real> v0 = mk<Real>(sV[w][0][0], sV[w][0][1], sV[w][0][2]);
-  const V3<Real> v1 = mk<Real>(sV[w][1][0], sV[w][1][1], sV[w][1][2]);
-  const V3<Real> v2 = a.NV == 3 ? mk<Real>(sV[w][2][0], sV[w][2][1], sV[w][2][2]) : v1;
-  const FaceDist<Real> fd(v0, v1, v2, a.NV == 3);
-  const Real dc2 = dc * dc;
-  // Bounding rectangle of the cone's cross-section in slice c: origin (a0,
-  // b0), width wa, cnt cells (0 when empty or flagged as too wide).
+  const Real dc = a.dc, eps = Real(1e-3);
+  int c0 = 0, nsl = 0;
+  bool wide = false;
+  if (ok) {
+    Real gmin = Real(1e30f);
+    for (int j = 0; j < nG; ++j) {
+      const int t = face_of(j);
+      const Real gkj = a.en[3 * t + k];
+      gmin = fmin(gmin, gkj * (S[k] >= 0 ? Real(1) : Real(-1)));
+      // (the rectangles are widened by eps, far above the rounding of a product)
+      sm.gk[lane][j] = rcp_rn(gkj);
+      sm.ga[lane][j] = a.en[3 * t + oa];
+      sm.gb[lane][j] = a.en[3 * t + ob];
+    }
+    wide = gmin < Real(0.25);  // a generator nearly parallel to the slices
+    Real bmin = 1e30f, bmax = -1e30f;
+    for (int q = 0; q < nB; ++q) {
+      bmin = fmin(bmin, sm.cb[lane][3 * q + k]);
+      bmax = fmax(bmax, sm.cb[lane][3 * q + k]);
+    }
+    c0 = (int)ceil(bmin - dc - eps);
+    nsl = (int)floor(bmax + dc + eps) - c0 + 1;
+    V3<Real> vq[3];
+    for (int q = 0; q < 3; ++q) {
+      const int m = a.E[a.NV * tmin + min(q, a.NV - 1)];
+      vq[q] = mk<Real>(node_off(a, m, 0, o[0]), node_off(a, m, 1, o[1]), node_off(a, m, 2, o[2]));
+    }
+    FaceDist<Real>(vq[0], vq[1], vq[2], a.NV == 3).store(sm.fd[lane]);
+    const int ow[3] = {wrap_coord(o[0], a.G.nx), wrap_coord(o[1], a.G.ny), a.G.wall ? o[2] : wrap_coord(o[2], a.G.nz)};
+    sm.ft[lane][0] = make_int4(ow[0], ow[1], ow[2], k | (oa << 2) | (ob << 4));
+    sm.ft[lane][1] = make_int4(tmin, c0, 0, 0);
+  }
+  // bounding rectangle of the cone's cross-section in slice c: origin (a0,
+  // b0), width wa, cnt cells (0 when empty or flagged as too wide)
   auto slice_rect = [&](int c, int& a0, int& b0, int& wa, int& cnt) {
     Real lo0 = 1e30f, hi0 = -1e30f, lo1 = 1e30f, hi1 = -1e30f;
     for (int q = 0; q < nB; ++q) {
+      const Real bk = sm.cb[lane][3 * q + k], ba = sm.cb[lane][3 * q + oa], bb = sm.cb[lane][3 * q + ob];
       if (!wide) {
         for (int j = 0; j < nG; ++j) {
-          Real t = ((Real)c - sB[w][q][k]) * sGi[w][j];
-          Real pa = sB[w][q][oa] + t * sG[w][j][oa], pb = sB[w][q][ob] + t * sG[w][j][ob];
+          const Real t = ((Real)c - bk) * sm.gk[lane][j];
+          const Real pa = ba + t * sm.ga[lane][j], pb = bb + t * sm.gb[lane][j];
           lo0 = fmin(lo0, pa); hi0 = fmax(hi0, pa);
           lo1 = fmin(lo1, pb); hi1 = fmax(hi1, pb);
         }
       } else {  // conservative: the feature's box widened by dc
-        lo0 = fmin(lo0, sB[w][q][oa] - dc); hi0 = fmax(hi0, sB[w][q][oa] + dc);
-        lo1 = fmin(lo1, sB[w][q][ob] - dc); hi1 = fmax(hi1, sB[w][q][ob] + dc);
+        lo0 = fmin(lo0, ba - dc); hi0 = fmax(hi0, ba + dc);
+        lo1 = fmin(lo1, bb - dc); hi1 = fmax(hi1, bb + dc);
       }
     }
     a0 = (int)ceil(lo0 - eps);
@@ -546,23 +589,18 @@ __device__ __forceinline__ void dist_scatter_body(const IBArgs<Real>& a, const B
     }
     if (cnt == 0) wa = 1;
   };
-  // Up to 64 slices at a time: every lane sizes the rectangles of two
-  // adjacent slices, a warp prefix sum lays all their cells end to end, and
-  // the lanes take the cells round-robin (slices near the feature are small,
-  // far ones in a widening cone large: per-slice loops would leave most
-  // lanes idle; 2 dc + 1 slices usually fit one pass).
-  for (int base = c0; base <= c1; base += 64) {
-    int a0[2] = {0, 0}, b0[2] = {0, 0}, wa[2] = {1, 1}, cnt[2] = {0, 0};
-    float rwa[2] = {1.0f, 1.0f};
+  const int rounds = (int)__reduce_max_sync(0xffffffffu, (unsigned)((nsl + SCAT_W - 1) / SCAT_W));
+  const Real dc2 = dc * dc;
+  for (int r = phase; r < rounds; r += SCAT_SPLIT) {
+    int tot = 0;
 #pragma unroll
-    for (int h = 0; h < 2; ++h) {
-      const int c = base + 2 * lane + h;
-      if (c <= c1) {
-        slice_rect(c, a0[h], b0[h], wa[h], cnt[h]);
-        rwa[h] = __frcp_rn((float)wa[h]);
-      }
+    for (int h = 0; h < SCAT_W; ++h) {
+      const int sidx = r * SCAT_W + h;
+      int a0 = 0, b0 = 0, wa = 1, cnt = 0;
+      if (sidx < nsl) slice_rect(c0 + sidx, a0, b0, wa, cnt);
+      tot += cnt;
+      sm.sl[lane][h] = make_int4(a0, b0, wa, tot);
     }
-    const int tot = cnt[0] + cnt[1];
     int incl = tot;
 #pragma unroll
     for (int sh = 1; sh < 32; sh <<= 1) {
@@ -570,8 +608,9 @@ __device__ __forceinline__ void dist_scatter_body(const IBArgs<Real>& a, const B
       if (lane >= sh) incl += v;
     }
     const int total = __shfl_sync(0xffffffffu, incl, 31);
-    for (int i0 = 0; i0 < total; i0 += 32) {
-      const int i = i0 + lane;
+    __syncwarp();
+    for (int j0 = 0; j0 < total; j0 += 32) {
+      const int i = j0 + lane;
       // lane holding cell i: the first lane whose inclusive prefix exceeds i
       int L = 0;
 #pragma unroll
@@ -579,44 +618,45 @@ __device__ __forceinline__ void dist_scatter_body(const IBArgs<Real>& a, const B
         const int v = __shfl_sync(0xffffffffu, incl, L + step - 1);
         if (v <= i) L += step;
       }
-      const int inclL = __shfl_sync(0xffffffffu, incl, L), totL = __shfl_sync(0xffffffffu, tot, L);
-      const int cnt0L = __shfl_sync(0xffffffffu, cnt[0], L);
-      int a0L[2], b0L[2], waL[2];
-      float rwaL[2];
-#pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        a0L[h] = __shfl_sync(0xffffffffu, a0[h], L);
-        b0L[h] = __shfl_sync(0xffffffffu, b0[h], L);
-        waL[h] = __shfl_sync(0xffffffffu, wa[h], L);
-        rwaL[h] = __shfl_sync(0xffffffffu, rwa[h], L);
-      }
+      const int base = __shfl_sync(0xffffffffu, incl, L) - __shfl_sync(0xffffffffu, tot, L);
       if (i >= total) continue;
-      int jj = i - (inclL - totL);
-      const int h = jj >= cnt0L ? 1 : 0;  // the lane's first or second slice
-      if (h) jj -= cnt0L;
-      const int wah = h ? waL[1] : waL[0];
-      // jj / wah: jj < 2^20 and wah <= 1024 keep the product within 2^-13 of
-      // the true (jj + 1/2) / wah, whose fraction is at least 2^-11 from an
+      int jj = i - base;
+      // its slice: the first whose cumulative count exceeds jj
+      int4 e = sm.sl[L][0];
+      int h = 0, prev = 0;
+#pragma unroll
+      for (int q = 1; q < SCAT_W; ++q) {
+        if (jj >= e.w) {
+          prev = e.w;
+          e = sm.sl[L][q];
+          h = q;
+        }
+      }
+      jj -= prev;
+      // jj / wa: jj < 2^20 and wa <= 1024 keep the product within 2^-13 of the
+      // true (jj + 1/2) / wa, whose fraction is at least 2^-11 from an
       // integer, so the truncation is exact
-      const int qb = (int)(((float)jj + 0.5f) * (h ? rwaL[1] : rwaL[0]));
-      int r[3];
-      r[k] = base + 2 * L + h;
-      r[oa] = (h ? a0L[1] : a0L[0]) + (jj - qb * wah);
-      if (a.dim == 3) r[ob] = (h ? b0L[1] : b0L[0]) + qb; else r[1] = 0;
-      int pc[3] = {ow[0] + r[0], ow[1] + r[1], ow[2] + r[2]};
-      long long cell = cell_of(a, pc);
+      const int qb = (int)(((float)jj + 0.5f) * __frcp_rn((float)e.z));
+      const int4 F0 = sm.ft[L][0], F1 = sm.ft[L][1];
+      const int kk = F0.w & 3, ka = (F0.w >> 2) & 3, kb = (F0.w >> 4) & 3;
+      int rr[3];
+      rr[kk] = F1.y + r * SCAT_W + h;
+      rr[ka] = e.x + (jj - qb * e.z);
+      rr[kb] = a.dim == 3 ? e.y + qb : 0;
+      const int pc[3] = {F0.x + rr[0], F0.y + rr[1], F0.z + rr[2]};
+      const long long cell = cell_of(a, pc);
       if (cell < 0) continue;
-      const Real d2 = fd.dist2(mk<Real>((Real)r[0], (Real)r[1], (Real)r[2]));
+      const Real d2 = FaceDist<Real>::load(sm.fd[L], a.NV == 3).dist2(mk<Real>((Real)rr[0], (Real)rr[1], (Real)rr[2]));
       if (!(d2 < dc2)) continue;
-      unsigned long long key = (dist_code(sqrt(d2)) << 24) | (unsigned long long)tmin;
+      const unsigned long long key = (dist_code(sqrt(d2)) << 24) | (unsigned long long)F1.x;
       atomicMin(a.key + cell, key);  // no return value: a fire-and-forget reduction
     }
+    __syncwarp();  // the next round rewrites the slice table
   }
 }
-// Persistent over nvb virtual blocks: a grid of a few blocks per SM leaves
-// the moments kernel, which runs beside it, most of each SM.
+// Persistent over nvb virtual blocks (grid capped by the caller).
 template <class Real>
-__global__ void __launch_bounds__(SCATTER_WARPS * 32, 7) k_dist_scatter(const __grid_constant__ IBArgs<Real> a, int nvb) {
+__global__ void __launch_bounds__(scatter_warps<Real>() * 32) k_dist_scatter(const __grid_constant__ IBArgs<Real> a, int nvb) {
   for (int vb = blockIdx.x; vb < nvb; vb += gridDim.x) dist_scatter_body(a, Blk{vb, 0, 0, nvb, 1, 1});
 }
 

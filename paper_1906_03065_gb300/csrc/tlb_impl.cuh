@@ -137,8 +137,9 @@ struct Impl : ImplBase {
     k_geometry<Real><<<blocks((long long)c->ne + c->nn, 128), 128, 0, s>>>(a);
     TLB_LAUNCHED(c, "k_geometry");
     const long long nfeat = (long long)c->ne + c->nedge + c->nn;
-    const unsigned nvb = blocks(nfeat, SCATTER_WARPS);
-    k_dist_scatter<Real><<<std::min(nvb, 4u * (unsigned)c->nsm), SCATTER_WARPS * 32, 0, s>>>(a, (int)nvb);
+    constexpr int sw = scatter_warps<Real>();
+    const unsigned nvb = SCAT_SPLIT * blocks(nfeat, 32 * sw);
+    k_dist_scatter<Real><<<std::min(nvb, 4u * (unsigned)c->nsm), 32 * sw, 0, s>>>(a, (int)nvb);
     TLB_LAUNCHED(c, "k_dist_scatter");
     return TLB_OK;
   }
