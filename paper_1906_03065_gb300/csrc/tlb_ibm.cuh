@@ -867,6 +867,8 @@ __global__ void k_fill(const __grid_constant__ IBArgs<Real> a) {
 }
 
 // ------------------------------------------------------------ elastic forces
+constexpr int NODEF_WARPS = 4;  // warps per block of the node-force kernel (at most)
+
 // Forward-mode dual number with derivatives with respect to one node.
 template <class T>
 struct D3 {
@@ -928,44 +930,44 @@ __device__ __forceinline__ D3<Real> skalak_dual(const IBArgs<Real>& a, int t, in
 }
 
 // Helfrich energy of vertex v: kb |sum_T (cot_k (x_v - x_j) + cot_j (x_v - x_k))|^2 / (8 A_v)
-// with A_v the mixed Voronoi area (Meyer et al. 2003).
+// with A_v the mixed Voronoi area (Meyer et al. 2003).  One term: the
+// contributions of face t of v to the sums K and A, differentiated with
+// respect to X_k.
 template <class Real>
-__device__ __forceinline__ D3<Real> helfrich_dual(const IBArgs<Real>& a, int v, int k) {
-  DV<Real> K = {dc<Real>(0), dc<Real>(0), dc<Real>(0)};
-  D3<Real> A = dc<Real>(0);
-  DV<Real> xv = dnode(a, v, k);
-  for (int jj = a.inc_off[v]; jj < a.inc_off[v + 1]; ++jj) {
-    int t = a.inc[jj];
-    int q0 = a.E[3 * t], q1 = a.E[3 * t + 1], q2 = a.E[3 * t + 2];
-    int j = q0 == v ? q1 : (q1 == v ? q2 : q0);
-    int kk = q0 == v ? q2 : (q1 == v ? q0 : q1);
-    DV<Real> xj = dnode(a, j, k), xk = dnode(a, kk, k);
-    DV<Real> vj = dsub(xv, xj), vk = dsub(xv, xk);
-    DV<Real> kj = dsub(xk, xj), jk = dsub(xj, xk);
-    DV<Real> c1 = dcross(vj, kj), c2 = dcross(vk, jk);
-    D3<Real> cotj = ddot(vj, kj) / dsqrt(ddot(c1, c1));
-    D3<Real> cotk = ddot(vk, jk) / dsqrt(ddot(c2, c2));
-    K.x = K.x + cotk * vj.x + cotj * vk.x;
-    K.y = K.y + cotk * vj.y + cotj * vk.y;
-    K.z = K.z + cotk * vj.z + cotj * vk.z;
-    DV<Real> ej = dsub(xj, xv), ek = dsub(xk, xv);
-    DV<Real> cr = dcross(ej, ek);
-    D3<Real> area = Real(0.5) * dsqrt(ddot(cr, cr));
-    Real dv = ddot(ej, ek).v, dj = ddot(vj, kj).v, dk = ddot(vk, jk).v;
-    if (dv < 0) A = A + Real(0.5) * area;
-    else if (dj < 0 || dk < 0) A = A + Real(0.25) * area;
-    else A = A + Real(0.125) * (ddot(vj, vj) * cotk + ddot(vk, vk) * cotj);
-  }
-  Real kb = a.capr[a.ncaps + a.ncap[v]];
-  return (kb * Real(0.125)) * (ddot(K, K) / A);
+__device__ __forceinline__ void helfrich_term(const IBArgs<Real>& a, int v, int t, int k, DV<Real>& Kc, D3<Real>& Ac) {
+  int q0 = a.E[3 * t], q1 = a.E[3 * t + 1], q2 = a.E[3 * t + 2];
+  int j = q0 == v ? q1 : (q1 == v ? q2 : q0);
+  int kk = q0 == v ? q2 : (q1 == v ? q0 : q1);
+  DV<Real> xv = dnode(a, v, k), xj = dnode(a, j, k), xk = dnode(a, kk, k);
+  DV<Real> vj = dsub(xv, xj), vk = dsub(xv, xk);
+  DV<Real> kj = dsub(xk, xj), jk = dsub(xj, xk);
+  DV<Real> c1 = dcross(vj, kj), c2 = dcross(vk, jk);
+  D3<Real> cotj = ddot(vj, kj) / dsqrt(ddot(c1, c1));
+  D3<Real> cotk = ddot(vk, jk) / dsqrt(ddot(c2, c2));
+  Kc.x = cotk * vj.x + cotj * vk.x;
+  Kc.y = cotk * vj.y + cotj * vk.y;
+  Kc.z = cotk * vj.z + cotj * vk.z;
+  DV<Real> ej = dsub(xj, xv), ek = dsub(xk, xv);
+  DV<Real> cr = dcross(ej, ek);
+  D3<Real> area = Real(0.5) * dsqrt(ddot(cr, cr));
+  Real dv = ddot(ej, ek).v, dj = ddot(vj, kj).v, dk = ddot(vk, jk).v;
+  if (dv < 0) Ac = Real(0.5) * area;
+  else if (dj < 0 || dk < 0) Ac = Real(0.25) * area;
+  else Ac = Real(0.125) * (ddot(vj, vj) * cotk + ddot(vk, vk) * cotj);
 }
 
 // Elastic node forces, one warp per marker (2D stretching + bending; 3D
 // Skalak + Helfrich, differentiated with forward-mode duals with respect to
-// the marker).  Lane sums are combined by a fixed shuffle tree.  They depend
-// on the marker positions only; the coupling force joins them in k_spread.
+// the marker).  In 3D lane t takes the Skalak term of incident face t, and
+// the Helfrich terms of the marker and its 1-ring vertices are shared out
+// as (vertex, face) pairs, 32 at a time: each lane stages its pair's
+// contributions to K and A, the lane of each vertex adds them in face order
+// and forms the vertex's energy.  Lane sums are combined by a fixed shuffle
+// tree.  They depend on the marker positions only; the coupling force joins
+// them in k_spread.
 template <class Real>
 __device__ __forceinline__ void node_forces_body(const IBArgs<Real>& a, const Blk& blk) {
+  __shared__ Real hstage[NODEF_WARPS][32 * 16];  // one chunk of Helfrich pairs per warp
   const int k = (blk.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (k >= a.nn) return;
@@ -1018,21 +1020,65 @@ __device__ __forceinline__ void node_forces_body(const IBArgs<Real>& a, const Bl
     }
   } else {
     const int i0 = a.inc_off[k], ninc = a.inc_off[k + 1] - i0;
-    // lanes 0..15: Skalak term of incident triangle `lane`
     if (lane < 16 && lane < ninc) {
       D3<Real> e = skalak_dual(a, a.inc[i0 + lane], k);
       F[0] -= e.d0; F[1] -= e.d1; F[2] -= e.d2;
     }
-    // lanes 16..31: Helfrich term of vertex v = k (lane 16) or of the
-    // (lane-17)-th distinct 1-ring neighbour of k, enumerated in the order
-    // of the incident triangles and their vertices
-    if (lane >= 16) {
-      const int want = lane - 16, r0 = a.ring_off[k], deg = a.ring_off[k + 1] - r0;
-      const int v = want == 0 ? k : (want - 1 < deg ? a.ring[r0 + want - 1] : -1);
-      if (v >= 0) {
-        D3<Real> h = helfrich_dual(a, v, k);
-        F[0] -= h.d0; F[1] -= h.d1; F[2] -= h.d2;
+    // Helfrich vertex slots: 0 the marker, 1.. its distinct 1-ring
+    // neighbours in the order of the incident faces and their vertices
+    const int r0 = a.ring_off[k], nV = min(a.ring_off[k + 1] - r0 + 1, 16);
+    int vs = 0, fs = 0, ds = 0;
+    if (lane < nV) {
+      vs = lane == 0 ? k : a.ring[r0 + lane - 1];
+      fs = a.inc_off[vs];
+      ds = a.inc_off[vs + 1] - fs;
+    }
+    int incl = ds;
+#pragma unroll
+    for (int sh = 1; sh < 32; sh <<= 1) {
+      const int v = __shfl_up_sync(0xffffffffu, incl, sh);
+      if (lane >= sh) incl += v;
+    }
+    const int total = __shfl_sync(0xffffffffu, incl, 31);
+    Real* stg = hstage[threadIdx.x >> 5];
+    DV<Real> K = {dc<Real>(0), dc<Real>(0), dc<Real>(0)};
+    D3<Real> A = dc<Real>(0);
+    for (int p0 = 0; p0 < total; p0 += 32) {
+      const int p = p0 + lane;
+      int S = 0;  // slot of pair p: the first whose inclusive prefix exceeds p
+#pragma unroll
+      for (int step = 16; step >= 1; step >>= 1) {
+        const int v = __shfl_sync(0xffffffffu, incl, S + step - 1);
+        if (v <= p) S += step;
       }
+      const int vS = __shfl_sync(0xffffffffu, vs, S), fS = __shfl_sync(0xffffffffu, fs, S);
+      const int eS = __shfl_sync(0xffffffffu, incl, S) - __shfl_sync(0xffffffffu, ds, S);
+      if (p < total) {
+        DV<Real> Kc;
+        D3<Real> Ac;
+        helfrich_term(a, vS, a.inc[fS + p - eS], k, Kc, Ac);
+        const Real c[16] = {Kc.x.v, Kc.x.d0, Kc.x.d1, Kc.x.d2, Kc.y.v, Kc.y.d0, Kc.y.d1, Kc.y.d2,
+                            Kc.z.v, Kc.z.d0, Kc.z.d1, Kc.z.d2, Ac.v,   Ac.d0,   Ac.d1,   Ac.d2};
+#pragma unroll
+        for (int q = 0; q < 16; ++q) stg[lane * 16 + q] = c[q];
+      }
+      __syncwarp();
+      if (lane < nV) {  // this slot's pairs of the chunk, in face order
+        const int lo = max(incl - ds, p0), hi = min(incl, p0 + 32);
+        for (int q = lo; q < hi; ++q) {
+          const Real* c = stg + (q - p0) * 16;
+          K.x = K.x + D3<Real>{c[0], c[1], c[2], c[3]};
+          K.y = K.y + D3<Real>{c[4], c[5], c[6], c[7]};
+          K.z = K.z + D3<Real>{c[8], c[9], c[10], c[11]};
+          A = A + D3<Real>{c[12], c[13], c[14], c[15]};
+        }
+      }
+      __syncwarp();
+    }
+    if (lane < nV) {
+      const Real kb = a.capr[a.ncaps + a.ncap[vs]];
+      D3<Real> h = (kb * Real(0.125)) * (ddot(K, K) / A);
+      F[0] -= h.d0; F[1] -= h.d1; F[2] -= h.d2;
     }
   }
   for (int d = 0; d < 3; ++d)
