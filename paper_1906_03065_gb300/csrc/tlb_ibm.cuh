@@ -693,7 +693,12 @@ __device__ __forceinline__ long long cpl_fixed(double v) { return llrint(v * CPL
 //   kappa_c (psi - I) sech^2(d/(2 alpha))/(4 alpha) * (-s beta_k (x - P)/|x - P|),
 // summed per element in fixed point (lanes of a warp with the same element
 // are combined before one atomic).  Cells without a key are marked -1 for
-// the column fill; keys are cleared for the next step.
+// the column fill; keys are cleared for the next step.  A cell that was a
+// band cell in the previous step and is not one now lies beyond dc on the
+// side of its last distance (the membrane moves less than half a cell per
+// step and cannot cross a cell farther than dc from it): it takes +-dc and
+// I_in/I_out here, so that between fresh starts the column fill, which
+// would find the same sides, is not needed.
 template <class Real>
 __device__ __forceinline__ void band_body(const IBArgs<Real>& a, const Blk& blk) {
   int blo[3], bhi[3];
@@ -703,6 +708,8 @@ __device__ __forceinline__ void band_body(const IBArgs<Real>& a, const Blk& blk)
   const long long total = (long long)wx * wy * wz;
   const bool full[3] = {wx == a.G.nx, a.dim == 3 && wy == a.G.ny, !a.G.wall && wz == a.G.nz};
   const Real al = a.alpha;
+  const Real Iin = Real(0.5) * (Real(1) + tanh(a.dc / (Real(2) * al)));
+  const Real Iout = Real(0.5) * (Real(1) + tanh(-a.dc / (Real(2) * al)));
   // the box origin wrapped into the lattice: cells are indexed from it, the
   // geometry uses the unwrapped coordinates
   const int ox = wrap_coord(bx0, a.G.nx), oy = wrap_coord(by0, a.G.ny), oz = a.G.wall ? bz0 : wrap_coord(bz0, a.G.nz);
@@ -730,6 +737,11 @@ __device__ __forceinline__ void band_body(const IBArgs<Real>& a, const Blk& blk)
       if (c >= 0) {
         unsigned long long key = a.key[c];
         if (key == KEY_NONE) {
+          if (a.own[c] >= 0) {  // left the band since the previous step
+            const bool in = a.dsel[c] > Real(0);
+            a.dsel[c] = in ? a.dc : -a.dc;
+            a.I[c] = in ? Iin : Iout;
+          }
           a.own[c] = -1;
         } else {
           e = (int)(key & 0xFFFFFF);

@@ -382,7 +382,8 @@ struct Impl : ImplBase {
     for (long k = 0; k < n; ++k) {
       LBArgs<MODE> la = lbargs(c, c->cur);
       IBArgs<Real> ia = ibargs(c);
-      if (c->nn > 0 && (st = snapshot_box(c, ia, s, c->box_stale)) != TLB_OK) return st;
+      const bool fresh = c->box_stale;  // markers set from outside since the last step
+      if (c->nn > 0 && (st = snapshot_box(c, ia, s, fresh)) != TLB_OK) return st;
       c->box_stale = false;
       if ((st = mark(c, 0)) != TLB_OK) return st;
       if (c->nn > 0) {  // fork: position-only membrane work on the two side streams
@@ -405,7 +406,10 @@ struct Impl : ImplBase {
         TLB_CUDA(cudaStreamWaitEvent(s, c->ev_bins, 0));
         // (in order: running the fill beside the spreading, or splitting the
         // collide to overlap this work, measured slower)
-        if ((st = ibm_band(c, ia, s)) != TLB_OK) return st;
+        // (the column fill only after markers were set from outside: between
+        // fresh starts the band keeps the cells beyond dc)
+        if ((st = launch_band(c, ia, s)) != TLB_OK) return st;
+        if (fresh && (st = launch_fill(c, ia, s)) != TLB_OK) return st;
         if ((st = ibm_spread(c, ia, s)) != TLB_OK) return st;
       }
       if ((st = mark(c, 2)) != TLB_OK) return st;
