@@ -269,11 +269,12 @@ static void plan(const tlb_params* p, const std::vector<HostMem>& mems, Ctx& c) 
   take(L.vn, 3 * nn * R);
   take(L.erel, 3 * NV * ne * R);
   take(L.eorg, 3 * ne * 4);
+  take(L.ecst, 16 * ne * R);
   take(L.xo, 3 * nn * 4);
   take(L.xr, 3 * nn * R);
   take(L.skc, 5 * ne * R);
   take(L.capr, 4 * std::max(1, c.ncap) * R);
-  take(L.esum, 3 * NV * ne * 8);
+  take(L.ncpl, 3 * nn * 8);
   take(L.F, 3 * nn * R);
   take(L.box, 12 * 4);
   const size_t nb = c.nbricks;

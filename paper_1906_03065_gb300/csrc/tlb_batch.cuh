@@ -28,9 +28,9 @@ struct BArgs {
 template <int MODE>
 __device__ __forceinline__ void pre_body(const BArgs<MODE>& s, const Blk& blk) {
   const auto& a = s.ib;
-  const long long n = 3ll * a.NV * a.ne;
+  const long long n = 3ll * a.nn;
   for (long long i = (long long)blk.x * blockDim.x + threadIdx.x; i < n; i += (long long)blk.gx * blockDim.x)
-    a.esum[i] = 0;
+    a.ncpl[i] = 0;
   if (blk.x == 0 && threadIdx.x < 6) {
     a.box[6 + threadIdx.x] = a.box[threadIdx.x];
     a.box[threadIdx.x] = 0x7F7F7F7F;
@@ -150,7 +150,7 @@ struct BatchImpl : BatchBase {
     const Ctx* c = b->inst[i];
     const bool mem = c->nn > 0;
     switch (op) {
-      case PRE: return {mem ? (int)std::min<unsigned>(64, std::max(1u, cdiv(3ll * c->NV * c->ne, NT))) : 0, 1, 1};
+      case PRE: return {mem ? (int)std::min<unsigned>(64, std::max(1u, cdiv(3ll * c->nn, NT))) : 0, 1, 1};
       case MOM: return {(int)cdiv(c->N, NT), 1, 1};
       case GEOM: return {mem ? (int)cdiv((long long)c->ne + c->nn, NT) : 0, 1, 1};
       case BCOUNT: return {mem ? (int)cdiv(c->nn, NT) : 0, 1, 1};

@@ -55,7 +55,7 @@ struct Layout {
   Region rho, phi, psi, I, dsel, own, key, fib, ftot, mu, rb;
   // membranes
   Region X, E, ecap, ncap, cap_par, ds0, rprev, rnext, A0, G0i, inc_off, inc, adj, edges, ring_off, ring;
-  Region en, vn, erel, eorg, xo, xr, skc, capr, esum, F, box;
+  Region en, vn, erel, eorg, ecst, xo, xr, skc, capr, ncpl, F, box;
   Region bcnt, bprev, bcur, boff, blist, bact, ctr, bflag;
   // misc
   Region status, part, meas;

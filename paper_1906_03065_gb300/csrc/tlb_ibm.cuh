@@ -46,7 +46,9 @@ struct IBArgs {
   Real* vn;              // [nn][3] angle-weighted vertex pseudo-normal
   Real* erel;            // [ne][NV][3] vertices relative to the element's origin
   int* eorg;             // [ne][3] element origin: floor of its first vertex
-  unsigned long long* esum;  // [ne][NV][3] coupling contributions, fixed point (CPL_SCALE)
+  Real* ecst;            // [ne][16] edge vectors ab, ac, bc, Gram entries d00 d01 d11 and
+                         // the reciprocals of d00, d11, |bc|^2 and the Gram determinant
+  unsigned long long* ncpl;  // [nn][3] coupling force per marker, fixed point (CPL_SCALE)
   Real* F;               // [nn][3] node force
   int* box;              // [6] marker box accumulator: floor(min X), -ceil(max X)
   const int* boxc;       // [6] the step's marker box (snapshot of the accumulator)
@@ -81,6 +83,10 @@ template <class T> TLB_HD V3<T> cross(V3<T> a, V3<T> b) {
   return {a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x};
 }
 
+// Correctly rounded reciprocal (the value of 1 / x, without the division).
+__device__ __forceinline__ float rcp_rn(float x) { return __frcp_rn(x); }
+__device__ __forceinline__ double rcp_rn(double x) { return __drcp_rn(x); }
+
 // Marker coordinates in the working precision.  FP32 builds them from the
 // split X = xo + xr (integer cell, fraction) so that the per-step kernels
 // issue no FP64 instructions (a slow pipe on this GPU); FP64 subtracts the
@@ -114,74 +120,70 @@ __device__ __forceinline__ void split_coord(double x, int* xo, Real* xr) {
   *xr = (Real)(v - f);
 }
 
-// Closest point of the origin on segment (a, b) or triangle (a, b, c)
-// (Voronoi-region classification).  Returns the barycentric weights and
-// the feature: 0 interior, 1..3 edge starting at vertex feat-1, 4..6 vertex feat-4.
-template <class Real>
-__device__ __forceinline__ V3<Real> closest_on_seg(V3<Real> a, V3<Real> b, Real* beta, int* feat) {
-  V3<Real> ab = b - a;
-  Real l2 = dot(ab, ab);
-  Real t = l2 > Real(0) ? -dot(a, ab) / l2 : Real(0);
-  if (t <= Real(0)) { t = 0; *feat = 4; }
-  else if (t >= Real(1)) { t = 1; *feat = 5; }
-  else *feat = 0;
-  beta[0] = Real(1) - t;
-  beta[1] = t;
-  beta[2] = 0;
-  return a + t * ab;
-}
-
-template <class Real>
-__device__ __forceinline__ V3<Real> closest_on_tri(V3<Real> a, V3<Real> b, V3<Real> c, Real* beta, int* feat) {
-  // p = origin
-  V3<Real> ab = b - a, ac = c - a;
-  V3<Real> ap = mk<Real>(-a.x, -a.y, -a.z);
-  Real d1 = dot(ab, ap), d2 = dot(ac, ap);
-  if (d1 <= 0 && d2 <= 0) { beta[0] = 1; beta[1] = 0; beta[2] = 0; *feat = 4; return a; }
-  V3<Real> bp = mk<Real>(-b.x, -b.y, -b.z);
-  Real d3 = dot(ab, bp), d4 = dot(ac, bp);
-  if (d3 >= 0 && d4 <= d3) { beta[0] = 0; beta[1] = 1; beta[2] = 0; *feat = 5; return b; }
-  Real vc = d1 * d4 - d3 * d2;
-  if (vc <= 0 && d1 >= 0 && d3 <= 0) {
-    Real v = d1 / (d1 - d3);
-    beta[0] = 1 - v; beta[1] = v; beta[2] = 0; *feat = 1;
-    return a + v * ab;
-  }
-  V3<Real> cp = mk<Real>(-c.x, -c.y, -c.z);
-  Real d5 = dot(ab, cp), d6 = dot(ac, cp);
-  if (d6 >= 0 && d5 <= d6) { beta[0] = 0; beta[1] = 0; beta[2] = 1; *feat = 6; return c; }
-  Real vb = d5 * d2 - d1 * d6;
-  if (vb <= 0 && d2 >= 0 && d6 <= 0) {
-    Real w = d2 / (d2 - d6);
-    beta[0] = 1 - w; beta[1] = 0; beta[2] = w; *feat = 3;  // edge c -> a
-    return a + w * ac;
-  }
-  Real va = d3 * d6 - d5 * d4;
-  if (va <= 0 && (d4 - d3) >= 0 && (d5 - d6) >= 0) {
-    Real w = (d4 - d3) / ((d4 - d3) + (d5 - d6));
-    beta[0] = 0; beta[1] = 1 - w; beta[2] = w; *feat = 2;  // edge b -> c
-    return b + w * (c - b);
-  }
-  Real den = Real(1) / (va + vb + vc);
-  Real v = vb * den, w = vc * den;
-  beta[0] = 1 - v - w; beta[1] = v; beta[2] = w; *feat = 0;
-  return a + v * ab + w * ac;
-}
-
-// Closest point of cell p (unwrapped) on element e, relative to the cell:
-// the vertices come from the step's element-relative copy (erel, eorg), so
-// that a cell needs no double-precision arithmetic (in FP64 this is the
-// same single rounding of X - p as a direct difference).
+// Closest point of cell p (unwrapped) on element e, relative to the cell,
+// its barycentric weights and feature (0 interior, 1..3 edge starting at
+// vertex feat-1, 4..6 vertex feat-4), without branches: the plane projection when it falls inside the face, else the
+// nearest of the three clamped edge projections (ties to the first edge).
+// The vertices come from the step's element-relative copy (erel, eorg) and
+// the edge constants from ecst, so a cell needs no division and no
+// double-precision arithmetic.
 template <class Real>
 __device__ __forceinline__ V3<Real> elem_closest(const IBArgs<Real>& a, int e, const int* p, Real* beta, int* feat) {
   const Real* r = a.erel + 3 * a.NV * e;
   const int* o = a.eorg + 3 * e;
-  const Real sx = (Real)(o[0] - p[0]), sy = (Real)(o[1] - p[1]), sz = (Real)(o[2] - p[2]);
-  V3<Real> p0 = mk<Real>(r[0] + sx, r[1] + sy, r[2] + sz);
-  V3<Real> p1 = mk<Real>(r[3] + sx, r[4] + sy, r[5] + sz);
-  if (a.NV == 2) return closest_on_seg(p0, p1, beta, feat);
-  V3<Real> p2 = mk<Real>(r[6] + sx, r[7] + sy, r[8] + sz);
-  return closest_on_tri(p0, p1, p2, beta, feat);
+  const Real* k = a.ecst + 16 * e;
+  const V3<Real> A = mk<Real>(r[0] + (Real)(o[0] - p[0]), r[1] + (Real)(o[1] - p[1]), r[2] + (Real)(o[2] - p[2]));
+  const V3<Real> ab = mk<Real>(k[0], k[1], k[2]);
+  const V3<Real> ap = mk<Real>(-A.x, -A.y, -A.z);
+  const Real d20 = dot(ap, ab);
+  const Real t0 = fmin(Real(1), fmax(Real(0), d20 * k[12]));
+  const V3<Real> P0 = A + t0 * ab;
+  const int f0 = t0 <= Real(0) ? 4 : (t0 >= Real(1) ? 5 : 1);
+  if (a.NV == 2) {
+    beta[0] = Real(1) - t0;
+    beta[1] = t0;
+    beta[2] = 0;
+    *feat = f0 == 1 ? 0 : f0;  // a segment's interior is its face
+    return P0;
+  }
+  const V3<Real> ac = mk<Real>(k[3], k[4], k[5]), bc = mk<Real>(k[6], k[7], k[8]);
+  const Real d00 = k[9], d01 = k[10], d11 = k[11];
+  const Real d21 = dot(ap, ac);
+  const Real t1 = fmin(Real(1), fmax(Real(0), d21 * k[13]));
+  const V3<Real> P1 = A + t1 * ac;
+  const V3<Real> Bv = A + ab;
+  const Real t2 = fmin(Real(1), fmax(Real(0), -dot(Bv, bc) * k[14]));
+  const V3<Real> P2 = Bv + t2 * bc;
+  const Real D0 = dot(P0, P0), D1 = dot(P1, P1), D2 = dot(P2, P2);
+  const Real v = (d11 * d20 - d01 * d21) * k[15], w = (d00 * d21 - d01 * d20) * k[15];
+  const bool inside = k[15] > Real(0) && v >= Real(0) && w >= Real(0) && v + w <= Real(1);
+  if (inside) {
+    beta[0] = Real(1) - v - w;
+    beta[1] = v;
+    beta[2] = w;
+    *feat = 0;
+    return A + v * ab + w * ac;
+  }
+  const bool e1 = D1 < D0 && D1 <= D2, e2 = !e1 && D2 < D0;
+  if (e2) {
+    beta[0] = 0;
+    beta[1] = Real(1) - t2;
+    beta[2] = t2;
+    *feat = t2 <= Real(0) ? 5 : (t2 >= Real(1) ? 6 : 2);
+    return P2;
+  }
+  if (e1) {
+    beta[0] = Real(1) - t1;
+    beta[1] = 0;
+    beta[2] = t1;
+    *feat = t1 <= Real(0) ? 4 : (t1 >= Real(1) ? 6 : 3);
+    return P1;
+  }
+  beta[0] = Real(1) - t0;
+  beta[1] = t0;
+  beta[2] = 0;
+  *feat = f0;
+  return P0;
 }
 
 // ------------------------------------------------------------ geometry pass
@@ -215,11 +217,27 @@ __device__ __forceinline__ void geometry_body(const IBArgs<Real>& a, const Blk& 
     a.en[3 * t + 1] = n.y;
     a.en[3 * t + 2] = n.z;
     const int* Et = a.E + a.NV * t;
+    Real rv[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
     for (int d = 0; d < 3; ++d) {
       const int o = a.xo[3 * Et[0] + d];
       a.eorg[3 * t + d] = o;
-      for (int q = 0; q < a.NV; ++q) a.erel[3 * (a.NV * t + q) + d] = node_off(a, Et[q], d, o);
+      for (int q = 0; q < a.NV; ++q) {
+        rv[q][d] = node_off(a, Et[q], d, o);
+        a.erel[3 * (a.NV * t + q) + d] = rv[q][d];
+      }
     }
+    // edge constants of the band's closest-point search (a segment keeps
+    // ac = bc = 0)
+    const V3<Real> A = mk<Real>(rv[0][0], rv[0][1], rv[0][2]), Bv = mk<Real>(rv[1][0], rv[1][1], rv[1][2]);
+    const V3<Real> Cv = a.NV == 3 ? mk<Real>(rv[2][0], rv[2][1], rv[2][2]) : A;
+    const V3<Real> ab = Bv - A, ac = a.NV == 3 ? Cv - A : mk<Real>(0, 0, 0), bc = a.NV == 3 ? Cv - Bv : mk<Real>(0, 0, 0);
+    const Real d00 = dot(ab, ab), d01 = dot(ab, ac), d11 = dot(ac, ac), dbc = dot(bc, bc);
+    const Real den = d00 * d11 - d01 * d01;
+    Real* k = a.ecst + 16 * t;
+    const Real kv[16] = {ab.x, ab.y, ab.z, ac.x, ac.y, ac.z, bc.x, bc.y, bc.z, d00, d01, d11,
+                         d00 > Real(0) ? rcp_rn(d00) : Real(0), d11 > Real(0) ? rcp_rn(d11) : Real(0),
+                         dbc > Real(0) ? rcp_rn(dbc) : Real(0), den > Real(0) ? rcp_rn(den) : Real(0)};
+    for (int q = 0; q < 16; ++q) k[q] = kv[q];
     return;
   }
   int k = t - a.ne;
@@ -334,16 +352,11 @@ __device__ __forceinline__ unsigned long long dist_code(double d) {
   return (unsigned long long)(d * 17179869184.0);
 }
 
-// Correctly rounded reciprocal (the value of 1 / x, without the division).
-__device__ __forceinline__ float rcp_rn(float x) { return __frcp_rn(x); }
-__device__ __forceinline__ double rcp_rn(double x) { return __drcp_rn(x); }
-
 // Squared distance from a point to a triangle (or a segment), without
 // branches: the projection onto the plane when it falls inside the
 // triangle, else the nearest of the three clamped edge projections.  The
 // per-face quantities are set up once; a point costs about fifty
-// arithmetic instructions and no divergence (the Voronoi-region walk of
-// closest_on_tri, which also returns the feature, serves the band).
+// arithmetic instructions and no divergence.
 template <class Real>
 struct FaceDist {
   V3<Real> A, B, ab, ac, bc;
@@ -803,10 +816,15 @@ __device__ __forceinline__ void band_body(const IBArgs<Real>& a, const Blk& blk)
 #pragma unroll
         for (int i = 0; i < 9; ++i) sum[i] += __shfl_sync(grp, v[i], src);
       }
-      if (lane == leader) {
+      if (lane == leader) {  // straight to the element's nodes
 #pragma unroll
-        for (int i = 0; i < 9; ++i)
-          if (i < 3 * a.NV && sum[i] != 0) atomicAdd(a.esum + 3 * a.NV * e + i, (unsigned long long)sum[i]);
+        for (int q = 0; q < 3; ++q) {
+          if (q >= a.NV) break;
+          const int node = a.E[a.NV * e + q];
+#pragma unroll
+          for (int d = 0; d < 3; ++d)
+            if (sum[3 * q + d] != 0) atomicAdd(a.ncpl + 3 * node + d, (unsigned long long)sum[3 * q + d]);
+        }
       }
     }
   }
@@ -1105,18 +1123,12 @@ __global__ void k_node_forces(const __grid_constant__ IBArgs<Real> a) {
   node_forces_body(a, hw_blk());
 }
 
-// Coupling force on marker k, gathered from the fixed-point sums of its
-// incident elements (integer totals, so the result is order independent).
+// Coupling force on marker k from its fixed-point sum (integer totals, so
+// the result does not depend on the order of the contributions).
 template <class Real>
 __device__ __forceinline__ void coupling_of(const IBArgs<Real>& a, int k, Real* out) {
-  long long cpl[3] = {0, 0, 0};
-  for (int jj = a.inc_off[k]; jj < a.inc_off[k + 1]; ++jj) {
-    int e = a.inc[jj];
-    int slot = 0;
-    for (int q = 0; q < a.NV; ++q)
-      if (a.E[a.NV * e + q] == k) slot = q;
-    for (int d = 0; d < 3; ++d) cpl[d] += (long long)a.esum[(a.NV * e + slot) * 3 + d];
-  }
+  long long cpl[3];
+  for (int d = 0; d < 3; ++d) cpl[d] = (long long)a.ncpl[3 * k + d];
   for (int d = 0; d < 3; ++d) {
     if constexpr (std::is_same<Real, float>::value)  // one rounding either way
       out[d] = __ll2float_rn(cpl[d]) * 0x1p-50f;

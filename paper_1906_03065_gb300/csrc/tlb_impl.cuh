@@ -91,12 +91,13 @@ struct Impl : ImplBase {
     a.vn = c->ptr<Real>(c->L.vn);
     a.erel = c->ptr<Real>(c->L.erel);
     a.eorg = c->ptr<int>(c->L.eorg);
+    a.ecst = c->ptr<Real>(c->L.ecst);
     a.xo = c->ptr<int>(c->L.xo);
     a.xr = c->ptr<Real>(c->L.xr);
     a.skc = c->ptr<Real>(c->L.skc);
     a.capr = c->ptr<Real>(c->L.capr);
     a.ncaps = c->ncap;
-    a.esum = c->ptr<unsigned long long>(c->L.esum);
+    a.ncpl = c->ptr<unsigned long long>(c->L.ncpl);
     a.F = c->ptr<Real>(c->L.F);
     a.box = c->ptr<int>(c->L.box);
     a.boxc = c->ptr<int>(c->L.box) + 6;
@@ -133,7 +134,7 @@ struct Impl : ImplBase {
   // brick binning in ibm_bins).  It runs on the side stream while the
   // moments of the step are computed.
   static tlb_status ibm_positions(Ctx* c, IBArgs<Real>& a, cudaStream_t s) {
-    TLB_CUDA(cudaMemsetAsync(a.esum, 0, c->L.esum.bytes, s));
+    TLB_CUDA(cudaMemsetAsync(a.ncpl, 0, c->L.ncpl.bytes, s));
     k_geometry<Real><<<blocks((long long)c->ne + c->nn, 128), 128, 0, s>>>(a);
     TLB_LAUNCHED(c, "k_geometry");
     const long long nfeat = (long long)c->ne + c->nedge + c->nn;
