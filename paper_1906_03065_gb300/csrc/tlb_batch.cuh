@@ -454,7 +454,7 @@ struct BatchImpl : BatchBase {
     int bv = b->tile_variant, bz = b->zc;
     int nzmax = 0;
     for (int i : b->act) nzmax = std::max(nzmax, b->inst[i]->nz);
-    const int zcs[6] = {4, 8, 12, 16, 32, 64};
+    const std::vector<int> zcs = z_chunk_candidates(nzmax);
     tlb_status st = TLB_OK;
     // the moments of the current state feed the collide (only the moments:
     // the first phase of a step would also consume the marker box)
@@ -466,8 +466,7 @@ struct BatchImpl : BatchBase {
       TLB_CUDA(cudaGetLastError());
     }
     for (int v = 0; v < COLLIDE_NVAR && st == TLB_OK; ++v)
-      for (int zi = 0; zi < 6 && st == TLB_OK; ++zi) {
-        if (zcs[zi] > nzmax && zi > 0 && zcs[zi - 1] >= nzmax) continue;
+      for (size_t zi = 0; zi < zcs.size() && st == TLB_OK; ++zi) {
         b->tile_variant = v;
         b->zc = zcs[zi];
         b->graph_dirty = true;
@@ -475,7 +474,7 @@ struct BatchImpl : BatchBase {
         if (st == TLB_OK) st = upload_tables(b);
         if (st == TLB_OK) st = launch_collide(b, b->ptr<BA>(b->targs[0]), vg_of(b, 4), b->stream);
         float tmin = 1e30f;
-        for (int r = 0; r < 3 && st == TLB_OK; ++r) {
+        for (int r = 0; r < 2 && st == TLB_OK; ++r) {
           cudaEventRecord(e0, b->stream);
           st = launch_collide(b, b->ptr<BA>(b->targs[0]), vg_of(b, 4), b->stream);
           cudaEventRecord(e1, b->stream);

@@ -13,6 +13,19 @@
 // Collide variants: 3 tile shapes x 4 register forms, v = 3 form + tile.
 constexpr int COLLIDE_NVAR = 12;
 
+// z-chunk lengths the collide autotuner tries: every distinct ceil(nz / m)
+// of at least 4 planes (each gives another grid, so another fill of the
+// last wave of blocks).
+inline std::vector<int> z_chunk_candidates(int nz) {
+  std::vector<int> v;
+  for (int m = 1;; ++m) {
+    const int zc = (nz + m - 1) / m;
+    if (v.empty() || v.back() != zc) v.push_back(zc);
+    if (zc <= 4) break;
+  }
+  return v;
+}
+
 struct Ctx;
 
 struct ImplBase {

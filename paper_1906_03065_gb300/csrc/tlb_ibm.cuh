@@ -69,6 +69,7 @@ struct IBArgs {
   int* ctr;              // [0] active bricks, [1] list slots claimed
   int nbx, nby, nbz, nbricks;
   Real alpha, dc, kc;
+  Real Iin, Iout;        // I beyond dc inside / outside: (1 +- tanh(dc/(2 alpha)))/2
   unsigned* status;
 };
 
@@ -704,8 +705,9 @@ __device__ __forceinline__ long long cpl_fixed(double v) { return llrint(v * CPL
 // Iprofile), owner element, and the coupling force contributions (eq.
 // DiscreteCF from eq. DiscreteCE): node k of the owner receives
 //   kappa_c (psi - I) sech^2(d/(2 alpha))/(4 alpha) * (-s beta_k (x - P)/|x - P|),
-// summed per element in fixed point (lanes of a warp with the same element
-// are combined before one atomic).  Cells without a key are marked -1 for
+// summed per marker in fixed point (lanes of a warp with the same element
+// are combined before one atomic per node; a reduction per lane measured
+// slower on the contended addresses).  Cells without a key are marked -1 for
 // the column fill; keys are cleared for the next step.  A cell that was a
 // band cell in the previous step and is not one now lies beyond dc on the
 // side of its last distance (the membrane moves less than half a cell per
@@ -720,9 +722,7 @@ __device__ __forceinline__ void band_body(const IBArgs<Real>& a, const Blk& blk)
   const int wx = bhi[0] - bx0 + 1, wy = bhi[1] - by0 + 1, wz = bhi[2] - bz0 + 1;
   const long long total = (long long)wx * wy * wz;
   const bool full[3] = {wx == a.G.nx, a.dim == 3 && wy == a.G.ny, !a.G.wall && wz == a.G.nz};
-  const Real al = a.alpha;
-  const Real Iin = Real(0.5) * (Real(1) + tanh(a.dc / (Real(2) * al)));
-  const Real Iout = Real(0.5) * (Real(1) + tanh(-a.dc / (Real(2) * al)));
+  const Real al = a.alpha, Iin = a.Iin, Iout = a.Iout;
   // the box origin wrapped into the lattice: cells are indexed from it, the
   // geometry uses the unwrapped coordinates
   const int ox = wrap_coord(bx0, a.G.nx), oy = wrap_coord(by0, a.G.ny), oz = a.G.wall ? bz0 : wrap_coord(bz0, a.G.nz);
@@ -848,9 +848,7 @@ __device__ __forceinline__ void fill_body(const IBArgs<Real>& a, const Blk& blk)
   const int col = (blk.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (col >= wx * wy) return;
-  const Real dc = a.dc, al = a.alpha;
-  const Real Iin = Real(0.5) * (Real(1) + tanh(dc / (Real(2) * al)));
-  const Real Iout = Real(0.5) * (Real(1) + tanh(-dc / (Real(2) * al)));
+  const Real dc = a.dc, Iin = a.Iin, Iout = a.Iout;
   const Geo& G = a.G;
   const long long colc = (long long)wrap_coord(by0 + col / wx, G.ny) * G.nx + wrap_coord(bx0 + col % wx, G.nx);
   const long long plane = (long long)G.nx * G.ny;

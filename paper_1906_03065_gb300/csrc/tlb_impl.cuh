@@ -123,6 +123,8 @@ struct Impl : ImplBase {
     a.alpha = (Real)c->p.alpha;
     a.dc = (Real)c->p.dc;
     a.kc = (Real)c->p.kappa_c;
+    a.Iin = (Real)(0.5 * (1.0 + tanh(c->p.dc / (2.0 * c->p.alpha))));
+    a.Iout = (Real)(0.5 * (1.0 + tanh(-c->p.dc / (2.0 * c->p.alpha))));
     a.status = c->ptr<unsigned>(c->L.status);
     return a;
   }
@@ -329,16 +331,15 @@ struct Impl : ImplBase {
     TLB_CUDA(cudaEventCreate(&e1));
     float best = 1e30f;
     int bv = c->tile_variant, bz = c->tiles_zc;
-    const int zcs[6] = {4, 8, 12, 16, 32, 64};
+    const std::vector<int> zcs = z_chunk_candidates(c->nz);
     for (int v = 0; v < COLLIDE_NVAR; ++v)
-      for (int zi = 0; zi < 6; ++zi) {
-        if (zcs[zi] > c->nz && zi > 0 && zcs[zi - 1] >= c->nz) continue;
+      for (const int zcv : zcs) {
         c->tile_variant = v;
-        c->tiles_zc = min(zcs[zi], c->nz);
+        c->tiles_zc = zcv;
         la.zc = c->tiles_zc;
         tlb_status st = collide(c, la, s);  // warm
         float tmin = 1e30f;
-        for (int r = 0; r < 3 && st == TLB_OK; ++r) {
+        for (int r = 0; r < 2 && st == TLB_OK; ++r) {
           cudaEventRecord(e0, s);
           st = collide(c, la, s);
           cudaEventRecord(e1, s);
