@@ -356,6 +356,8 @@ tlb_status tlb_create(const tlb_params* params, const tlb_membrane_desc* mems, i
     if (r0 == TLB_OK) r0 = cuda_check(cudaEventCreateWithFlags(&c->ev_bins, cudaEventDisableTiming), "event");
     if (r0 == TLB_OK) r0 = cuda_check(cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming), "event");
     if (r0 == TLB_OK) r0 = cuda_check(cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming), "event");
+    if (r0 == TLB_OK) r0 = cuda_check(cudaEventCreateWithFlags(&c->ev_coll, cudaEventDisableTiming), "event");
+    if (r0 == TLB_OK) r0 = cuda_check(cudaEventCreateWithFlags(&c->ev_interp, cudaEventDisableTiming), "event");
     if (r0 != TLB_OK) { delete c; return r0; }
   }
   // zero everything, then set the non-zero initial values

@@ -97,7 +97,7 @@ struct Ctx {
   cudaStream_t side = nullptr;   // membrane work that overlaps the moments: geometry
                                  // and the distance scatter
   cudaStream_t side2 = nullptr;  // elastic forces and brick binning, beside `side`
-  cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_bins = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_bins = nullptr, ev_coll = nullptr, ev_interp = nullptr;
   int nsm = 1;  // streaming multiprocessors of the device
   int cur = 0;  // population buffer holding the current state
   long t = 0;
@@ -123,6 +123,8 @@ struct Ctx {
     if (ev_fork) cudaEventDestroy(ev_fork);
     if (ev_join) cudaEventDestroy(ev_join);
     if (ev_bins) cudaEventDestroy(ev_bins);
+    if (ev_coll) cudaEventDestroy(ev_coll);
+    if (ev_interp) cudaEventDestroy(ev_interp);
     if (side) cudaStreamDestroy(side);
     if (side2) cudaStreamDestroy(side2);
   }

@@ -381,17 +381,29 @@ struct Impl : ImplBase {
     cudaStream_t s = c->stream;
     const long long N = c->N;
     tlb_status st;
+    // Pipelined: the interpolation and advection of a step runs on the side
+    // stream beside the next step's moments (which read the populations
+    // only); the next step's marker work waits for it there.  The phase
+    // profile keeps every kernel on the main stream.
+    const bool pipe = c->nn > 0 && !c->prof;
     for (long k = 0; k < n; ++k) {
       LBArgs<MODE> la = lbargs(c, c->cur);
       IBArgs<Real> ia = ibargs(c);
       const bool fresh = c->box_stale;  // markers set from outside since the last step
-      if (c->nn > 0 && (st = snapshot_box(c, ia, s, fresh)) != TLB_OK) return st;
       c->box_stale = false;
       if ((st = mark(c, 0)) != TLB_OK) return st;
       if (c->nn > 0) {  // fork: position-only membrane work on the two side streams
+        // The step's marker box: after markers set from outside it is rebuilt
+        // (with the coordinate split the side streams read) before the fork;
+        // otherwise it is the previous advection's accumulator, copied on the
+        // side stream after that advection.
+        const bool box_on_side = pipe && !fresh;
+        if (!box_on_side && (st = snapshot_box(c, ia, s, fresh)) != TLB_OK) return st;
         TLB_CUDA(cudaEventRecord(c->ev_fork, s));
         TLB_CUDA(cudaStreamWaitEvent(c->side, c->ev_fork, 0));
         TLB_CUDA(cudaStreamWaitEvent(c->side2, c->ev_fork, 0));
+        if (pipe) TLB_CUDA(cudaStreamWaitEvent(c->side2, c->ev_interp, 0));  // the previous advection
+        if (box_on_side && (st = snapshot_box(c, ia, c->side, false)) != TLB_OK) return st;
         if ((st = ibm_positions(c, ia, c->side)) != TLB_OK) return st;
         if ((st = ibm_bins(c, ia, c->side2)) != TLB_OK) return st;
         TLB_CUDA(cudaEventRecord(c->ev_bins, c->side2));
@@ -418,14 +430,22 @@ struct Impl : ImplBase {
       if ((st = collide(c, la, s)) != TLB_OK) return st;
       if ((st = mark(c, 3)) != TLB_OK) return st;
       if (c->nn > 0) {
-        k_interp_advect<L, MODE><<<blocks((long long)c->nn * 32, 128), 128, 0, s>>>(ia, la.lo_dst);
+        cudaStream_t si = s;
+        if (pipe) {
+          TLB_CUDA(cudaEventRecord(c->ev_coll, s));
+          TLB_CUDA(cudaStreamWaitEvent(c->side, c->ev_coll, 0));
+          si = c->side;
+        }
+        k_interp_advect<L, MODE><<<blocks((long long)c->nn * 32, 128), 128, 0, si>>>(ia, la.lo_dst);
         TLB_LAUNCHED(c, "k_interp_advect");
+        if (pipe) TLB_CUDA(cudaEventRecord(c->ev_interp, c->side));
       }
       if ((st = mark(c, 4)) != TLB_OK) return st;
       if ((st = collect(c)) != TLB_OK) return st;
       c->cur = 1 - c->cur;
       c->t += 1;
     }
+    if (pipe && n > 0) TLB_CUDA(cudaStreamWaitEvent(s, c->ev_interp, 0));  // all of it on the caller's stream
     return TLB_OK;
   }
 
