@@ -316,8 +316,6 @@ __device__ __forceinline__ void collide_body(const LBArgs<MODE>& a, const Blk& b
     __syncthreads();
   }
 }
-// Resident threads per SM the collide is compiled for: 640 (96 registers)
-// or, with the next population set prefetched, 512 (128 registers).
 // Forms of the collide: threads per SM the register budget is set for
 // (0: 640; 1: 512 with the next set prefetched; 2: 768; 3: 1024).
 template <int FORM> constexpr int collide_threads() {
