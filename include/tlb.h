@@ -236,12 +236,13 @@ tlb_status tlb_profile_steps(void* ctx, long n_steps, tlb_profile* out);
  * advanced).  Writes the chosen variant v = 3 form + tile (tile 0: 32x4,
  * 1: 32x8, 2: 64x4 in 3D; 0: 32, 1: 64, 2: 128 columns in 2D; form 0:
  * registers for 640 threads per SM, 1: 512 with the next population set
- * prefetched, 2: 768, 3: 1024) and planes per chunk when the pointers are
+ * prefetched, 2: 768, 3: 1024; v = 12: tile 0 at 896) and planes per chunk
+ * when the pointers are
  * non-NULL.  Synchronises the stream.  Not in the paper: an autotuner for
  * this implementation's launch shape. */
 tlb_status tlb_autotune(void* ctx, int* tile_variant, int* z_chunk);
 
-/* Set the collide variant (0..11, as written by tlb_autotune) and the
+/* Set the collide variant (0..12, as written by tlb_autotune) and the
  * planes per z chunk (1..nz) explicitly.  The results do not depend on the
  * choice. */
 tlb_status tlb_set_tile(void* ctx, int tile_variant, int z_chunk);

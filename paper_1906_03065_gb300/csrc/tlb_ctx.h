@@ -10,8 +10,9 @@
 
 #include "../../include/tlb.h"
 
-// Collide variants: 3 tile shapes x 4 register forms, v = 3 form + tile.
-constexpr int COLLIDE_NVAR = 12;
+// Collide variants: 3 tile shapes x 4 register forms, v = 3 form + tile,
+// and the smallest tile in a fifth form (v = 12).
+constexpr int COLLIDE_NVAR = 13;
 
 // z-chunk lengths the collide autotuner tries: every distinct ceil(nz / m)
 // of at least 4 planes (each gives another grid, so another fill of the

@@ -317,9 +317,9 @@ __device__ __forceinline__ void collide_body(const LBArgs<MODE>& a, const Blk& b
   }
 }
 // Forms of the collide: threads per SM the register budget is set for
-// (0: 640; 1: 512 with the next set prefetched; 2: 768; 3: 1024).
+// (0: 640; 1: 512 with the next set prefetched; 2: 768; 3: 1024; 4: 896).
 template <int FORM> constexpr int collide_threads() {
-  return FORM == 1 ? 512 : (FORM == 2 ? 768 : (FORM == 3 ? 1024 : 640));
+  return FORM == 1 ? 512 : (FORM == 2 ? 768 : (FORM == 3 ? 1024 : (FORM == 4 ? 896 : 640)));
 }
 
 template <class L, int MODE, int TX, int TY, int FORM>
@@ -329,7 +329,8 @@ __global__ void __launch_bounds__(TX* TY, collide_threads<FORM>() / (TX * TY))
 }
 
 // Calls fn(tile x, tile y, form) with the variant's compile-time values
-// (3D tiles 32x4, 32x8, 64x4; 2D rows of 32, 64, 128).
+// (3D tiles 32x4, 32x8, 64x4; 2D rows of 32, 64, 128; variant 12 is the
+// smallest tile in form 4).
 template <int V> using CIdx = std::integral_constant<int, V>;
 template <class L, class Fn>
 __host__ tlb_status collide_variant(int v, Fn&& fn) {
@@ -347,6 +348,7 @@ __host__ tlb_status collide_variant(int v, Fn&& fn) {
     case 9: return fn(CIdx<32>{}, CIdx<Y0>{}, CIdx<3>{});
     case 10: return fn(CIdx<X1>{}, CIdx<Y1>{}, CIdx<3>{});
     case 11: return fn(CIdx<X2>{}, CIdx<Y0>{}, CIdx<3>{});
+    case 12: return fn(CIdx<32>{}, CIdx<Y0>{}, CIdx<4>{});  // (the larger tiles at 896 repeat 768)
     default: return fn(CIdx<32>{}, CIdx<Y0>{}, CIdx<0>{});
   }
 }

@@ -201,7 +201,8 @@ def test_collide_tile_variants_agree(storage):
     ref = _sim(wl).init()
     ref.step(12)
     P = ref.pops()
-    for v, zc in ((1, 5), (2, 16), (3, 7), (4, 12), (5, 34), (6, 9), (7, 12), (8, 3), (9, 12), (10, 6), (11, 20)):
+    for v, zc in ((1, 5), (2, 16), (3, 7), (4, 12), (5, 34), (6, 9), (7, 12), (8, 3), (9, 12), (10, 6), (11, 20),
+                  (12, 11)):
         g = _sim(wl).init()
         g.set_tile(v, zc)
         g.step(12)
