@@ -25,6 +25,10 @@
  *  - Calls are ordered on the CUDA stream given to tlb_create().  tlb_step
  *    returns once the work is enqueued; every tlb_read_* and
  *    tlb_diagnostics call synchronises that stream before returning.
+ *    Inside a tlb_step call the membrane work of a step runs partly on two
+ *    internal streams of the context; all of it is joined back into the
+ *    context stream before the call returns, so work the caller enqueues on
+ *    that stream afterwards sees the finished steps.
  *  - Every call returns a tlb_status; on failure tlb_last_error() returns a
  *    message (thread-local).  A context is not thread-safe.
  */
