@@ -42,7 +42,8 @@ class _Params(C.Structure):
                 ("kappa1", C.c_double), ("kappa2", C.c_double), ("kappa3", C.c_double),
                 ("kappa_c", C.c_double), ("dc", C.c_double),
                 ("u0x", C.c_double), ("u0y", C.c_double), ("u0z", C.c_double),
-                ("interface_pos", C.c_double), ("storage", C.c_int), ("forcing", C.c_int)]
+                ("interface_pos", C.c_double), ("storage", C.c_int), ("forcing", C.c_int),
+                ("force_form", C.c_int)]
 
 
 def lib():
@@ -85,6 +86,14 @@ def lib():
         L.or_spread.argtypes = [C.c_void_p, dp, dp, dp]
         L.or_interp.argtypes = [C.c_void_p, C.c_int, dp, dp, dp]
         L.or_masses.argtypes = [C.c_void_p, dp]
+        L.or_grad_field.argtypes = [C.c_void_p, dp, dp]
+        L.or_lap_field.argtypes = [C.c_void_p, dp, dp]
+        L.or_force_fe.argtypes = [C.c_void_p, dp, dp, dp, dp, dp]
+        L.or_bulk_pressure.argtypes = [C.c_void_p, C.c_double, C.c_double, C.c_double]
+        L.or_bulk_pressure.restype = C.c_double
+        L.or_capsule_measures.argtypes = [C.c_void_p, C.c_int, dp, dp]
+        L.or_contact_angle.argtypes = [C.c_void_p, C.c_int, dp, dp, dp]
+        L.or_contact_angle.restype = C.c_int
         _lib = L
     return _lib
 
@@ -96,6 +105,7 @@ def _dp(a: np.ndarray):
 STORAGE_CODE = {"f64": 0, "f32": 1, "f16": 2, "bf16": 3}
 
 FORCING_CODE = {"edm": 0, "guo": 1}
+FORCE_FORM_CODE = {"potential": 0, "pressure_tensor": 1}
 FIELDS = {"rho": 0, "phi": 1, "psi": 2, "ux": 3, "uy": 4, "uz": 5, "C1": 6, "C2": 7,
           "C3": 8, "I": 9, "Fx": 10, "Fy": 11, "Fz": 12, "fibx": 13, "fiby": 14,
           "fibz": 15, "mu_rho": 16, "mu_phi": 17, "mu_psi": 18}
@@ -118,7 +128,8 @@ class Oracle:
                      p.kappa1, p.kappa2, p.kappa3, p.kappa_c, p.dc,
                      p.u0[0], p.u0[1], p.u0[2], p.interface_pos,
                      STORAGE_CODE[p.storage] if emulate_storage else 0,
-                     FORCING_CODE[getattr(p, "forcing", "edm")])
+                     FORCING_CODE[getattr(p, "forcing", "edm")],
+                     FORCE_FORM_CODE[getattr(p, "force_form", "potential")])
         self._cp = cp
         self.h = L.or_create(C.byref(cp))
         self.N = p.nx * p.ny * (p.nz if p.dim == 3 else 1)
@@ -263,6 +274,45 @@ class Oracle:
         out = np.zeros(3 * self.N)
         lib().or_spread(self.h, _dp(Xall), _dp(Fall), _dp(out))
         return out.reshape(3, self.N)
+
+    def grad_field(self, a):
+        """Lattice gradient [3][N] of a scalar field (the step's stencil)."""
+        a = np.ascontiguousarray(a, dtype=np.float64)
+        g = np.zeros(3 * self.N)
+        lib().or_grad_field(self.h, _dp(a), _dp(g))
+        return g.reshape(3, self.N)
+
+    def lap_field(self, a):
+        a = np.ascontiguousarray(a, dtype=np.float64)
+        out = np.zeros(self.N)
+        lib().or_lap_field(self.h, _dp(a), _dp(out))
+        return out
+
+    def force_fe(self, rho, phi, psi, I):
+        """Free-energy force [3][N] of given fields as the step forms it."""
+        arrs = [np.ascontiguousarray(a, dtype=np.float64) for a in (rho, phi, psi, I)]
+        F = np.zeros(3 * self.N)
+        lib().or_force_fe(self.h, *[_dp(a) for a in arrs], _dp(F))
+        return F.reshape(3, self.N)
+
+    def bulk_pressure(self, rho, phi, psi):
+        return lib().or_bulk_pressure(self.h, float(rho), float(phi), float(psi))
+
+    def capsule_measures(self, m: int = 0, X=None):
+        """(area, volume) of membrane m at X (default: current markers)."""
+        X = self.nodes(m) if X is None else np.ascontiguousarray(X, dtype=np.float64)
+        out = np.zeros(2)
+        lib().or_capsule_measures(self.h, m, _dp(X), _dp(out))
+        return out
+
+    def contact_angle(self, m: int = 0, X=None, phi=None):
+        """(mean, min, max) contact angle in degrees of membrane m with the
+        phi = 0 interface, and the number of contact points."""
+        X = self.nodes(m) if X is None else np.ascontiguousarray(X, dtype=np.float64)
+        phi = self.field("phi") if phi is None else np.ascontiguousarray(phi, dtype=np.float64)
+        out = np.full(3, np.nan)
+        n = lib().or_contact_angle(self.h, m, _dp(X), _dp(phi), _dp(out))
+        return out, n
 
     def interp(self, X, field3):
         X = np.ascontiguousarray(X, dtype=np.float64)

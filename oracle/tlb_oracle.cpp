@@ -27,6 +27,15 @@
 //       finite differences of the coupling energy)
 //   Peskin kernel, spreading, interpolation -- pinned (moment identities,
 //       exact transfer of totals and of linear fields)
+//   gradient and Laplacian stencils -- pinned (analytic derivatives of
+//       smooth fields, second-order convergence, mirror ghost at walls)
+//   pressure-tensor force form and bulk pressure of App. A -- pinned
+//       (Gibbs-Duhem relation; equal to the potential form to second order)
+//   interface tensions -- pinned for all three pairs; Neumann-triangle
+//       angles of a relaxed ternary lens
+//   capsule area / volume -- pinned (polygon and icosahedron closed forms,
+//       convergence to the sphere); contact angle -- pinned (sphere or ring
+//       on a flat or tilted interface: arccos(-h/R))
 
 #include <algorithm>
 #include <cmath>
@@ -110,6 +119,9 @@ typedef struct {
   int storage;        // population storage emulated after every step:
                       // 0 none (FP64), 1 binary32, 2 binary16, 3 bfloat16
   int forcing;        // 0: exact difference method (eq. LBE); 1: Guo forcing
+  int force_form;     // 0: potential form of f_FE (eq. ForceFE through eq.
+                      // GradPT); 1: divergence of the explicit pressure
+                      // tensor of App. A
 } or_params;
 
 }  // extern "C"
@@ -951,6 +963,116 @@ void potentials(Sim& s) {
              lap(s, s.psi, c), s.I[c], &s.mur[c], &s.muphi[c], &s.mupsi[c]);
 }
 
+// Bulk pressure p_b of App. A (the ideal-gas part rho cs^2 included).
+// Reading: the printed polynomial does not satisfy the Gibbs-Duhem relation
+// grad p_b = rho grad mu_rho^b + phi grad mu_phi^b + psi grad mu_psi^b of the
+// bulk free energy of eq. LandauFE; it is short by 3 (kappa_1 + kappa_2)
+// psi^2 / 32, which is not a constant.  That term is added here (the last
+// line), so that p_b = rho cs^2 + sum_m C_m dF/dC_m - F_b exactly.
+double bulk_pressure(const or_params& p, double r, double f, double s) {
+  const double k1 = p.kappa1, k2 = p.kappa2, k3 = p.kappa3;
+  const double r2 = r * r, f2 = f * f, s2 = s * s;
+  double pb = r * CS2;
+  pb += (k1 + k2) * (3.0 / 32 * r2 * r2 + 3.0 / 32 * f2 * f2 + 9.0 / 16 * r2 * f2 + 9.0 / 16 * r2 * s2 +
+                     9.0 / 16 * f2 * s2 - 3.0 / 8 * r2 * r * s - 3.0 / 8 * r * s2 * s + 3.0 / 4 * r2 * s -
+                     3.0 / 4 * r * f2 - 3.0 / 4 * r * s2 + 3.0 / 4 * f2 * s - 1.0 / 4 * r2 * r + 1.0 / 8 * r2 +
+                     1.0 / 8 * f2 - 1.0 / 4 * r * s - 9.0 / 8 * r * f2 * s);
+  pb += (k1 - k2) * (3.0 / 8 * r2 * r * f + 3.0 / 8 * r * f2 * f - 3.0 / 8 * f2 * f * s - 3.0 / 8 * f * s2 * s -
+                     1.0 / 4 * f2 * f - 3.0 / 4 * r2 * f - 3.0 / 4 * f * s2 + 1.0 / 4 * r * f - 1.0 / 4 * f * s +
+                     9.0 / 8 * r * f * s2 - 9.0 / 8 * r2 * f * s + 3.0 / 2 * r * f * s);
+  pb += 0.25 * (k1 + k2 - 8.0 * k3) * s2 * s + (k1 + k2 + 16.0 * k3) * (3.0 / 32 * s2 * s2 + 1.0 / 32 * s2);
+  pb += 3.0 / 32 * (k1 + k2) * s2;  // the Gibbs-Duhem term missing from the print
+  return pb;
+}
+
+// Pressure tensor of App. A at every cell, [6][N] in the order xx, yy, zz,
+// xy, xz, yz, from the lattice gradients and Laplacians of rho, phi, psi.
+// Mixing coefficients: k_rr = k_ff = (k1 + k2)/4, k_ss = (k1 + k2 + 4 k3)/4,
+// k_rf = -k_fs = (k1 - k2)/4, k_rs = -(k1 + k2)/4.  Each cross pair (a, b)
+// contributes d_a a d_b b + d_a b d_b a - (grad a . grad b) delta
+// - a lap b delta - b lap a delta (the printed last pair reads psi (d_gg)
+// for psi (d_gg phi), a typo).
+void pressure_tensor(const Sim& s, std::vector<double>& P) {
+  const long N = s.N;
+  const double a2 = s.p.alpha * s.p.alpha;
+  const double k1 = s.p.kappa1, k2 = s.p.kappa2, k3 = s.p.kappa3;
+  // coefficient matrix over (rho, phi, psi)
+  const double K[3][3] = {{(k1 + k2) / 4, (k1 - k2) / 4, -(k1 + k2) / 4},
+                          {(k1 - k2) / 4, (k1 + k2) / 4, -(k1 - k2) / 4},
+                          {-(k1 + k2) / 4, -(k1 - k2) / 4, (k1 + k2 + 4 * k3) / 4}};
+  const int ia[6] = {0, 1, 2, 0, 0, 1}, ib[6] = {0, 1, 2, 1, 2, 2};
+  P.assign(6 * N, 0.0);
+  const std::vector<double>* fld[3] = {&s.rho, &s.phi, &s.psi};
+#pragma omp parallel for
+  for (long c = 0; c < N; ++c) {
+    double g[3][3], L[3], v[3];
+    for (int q = 0; q < 3; ++q) {
+      grad(s, *fld[q], c, g[q]);
+      L[q] = lap(s, *fld[q], c);
+      v[q] = (*fld[q])[c];
+    }
+    double tr = bulk_pressure(s.p, v[0], v[1], v[2]);
+    // isotropic part of the gradient terms: sum_ab K_ab (-(1/2) grad a . grad b - a lap b)
+    for (int a = 0; a < 3; ++a)
+      for (int b = 0; b < 3; ++b) {
+        const double gg = g[a][0] * g[b][0] + g[a][1] * g[b][1] + g[a][2] * g[b][2];
+        tr += a2 * K[a][b] * (-0.5 * gg - v[a] * L[b]);
+      }
+    for (int q = 0; q < 6; ++q) {
+      double t = ia[q] == ib[q] ? tr : 0.0;
+      for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b) t += a2 * K[a][b] * g[a][ia[q]] * g[b][ib[q]];
+      P[(long)q * N + c] = t;
+    }
+  }
+}
+
+// The free-energy force f_FE at every cell, [N][3], from the moment fields
+// and the potentials of the step.
+//  * potential form (the default): -rho grad mu~rho - phi grad mu_phi
+//    - psi grad mu_psi' (eq. ForceFE with eq. GradPT; grad rho cs^2 cancels
+//    rho grad cs^2 ln rho, so both ideal-gas parts are dropped).
+//  * pressure-tensor form: grad(rho cs^2) - div p (App. A)
+//    - psi grad(kappa_c (psi - I)), the first line of eq. ForceFE literally.
+// The two agree in the continuum and differ at second order in the lattice
+// spacing.
+void fe_force(const Sim& s, std::vector<double>& F) {
+  const long N = s.N;
+  F.assign(3 * N, 0.0);
+  if (s.p.force_form == 1) {
+    std::vector<double> P, cpl(N);
+    pressure_tensor(s, P);
+    for (long c = 0; c < N; ++c) cpl[c] = s.p.kappa_c * (s.psi[c] - s.I[c]);
+    std::vector<double> comp[6];
+    for (int q = 0; q < 6; ++q) comp[q].assign(P.begin() + (long)q * N, P.begin() + (long)(q + 1) * N);
+    // row a of the symmetric tensor: (xx, xy, xz), (xy, yy, yz), (xz, yz, zz)
+    const int row[3][3] = {{0, 3, 4}, {3, 1, 5}, {4, 5, 2}};
+#pragma omp parallel for
+    for (long c = 0; c < N; ++c) {
+      double gr[3], gc[3], gp[3];
+      grad(s, s.rho, c, gr);
+      grad(s, cpl, c, gc);
+      for (int a = 0; a < 3; ++a) {
+        double div = 0.0;
+        for (int b = 0; b < 3; ++b) {
+          grad(s, comp[row[a][b]], c, gp);
+          div += gp[b];
+        }
+        if (a < s.dim) F[3 * c + a] = CS2 * gr[a] - div - s.psi[c] * gc[a];
+      }
+    }
+    return;
+  }
+#pragma omp parallel for
+  for (long c = 0; c < N; ++c) {
+    double gr[3], gp[3], gs[3];
+    grad(s, s.mur, c, gr);
+    grad(s, s.muphi, c, gp);
+    grad(s, s.mupsi, c, gs);
+    for (int k = 0; k < s.dim; ++k) F[3 * c + k] = -s.rho[c] * gr[k] - s.phi[c] * gp[k] - s.psi[c] * gs[k];
+  }
+}
+
 std::vector<const double*> node_ptrs(const Sim& s) {
   std::vector<const double*> Xs;
   for (const Membrane& m : s.mem) Xs.push_back(m.X.data());
@@ -977,18 +1099,14 @@ void do_step(Sim& s) {
   coupling_force(s, Xs, s.band, s.psi, s.I, Fm);
   // (5) spreading to the lattice (eq. Spreading)
   spread(s, Xs, Fm, s.fib);
-  // (6) total force: f_FE = -rho grad mu~rho - phi grad mu_phi - psi grad mu_psi'
-  //     (eq. ForceFE with eq. GradPT; the ideal-gas parts cancel) plus f_IB
+  // (6) total force: f_FE (potential form, or the pressure-tensor form when
+  //     selected) plus f_IB
   s.F.assign(3 * N, 0.0);
+  std::vector<double> ffe;
+  fe_force(s, ffe);
 #pragma omp parallel for
-  for (long c = 0; c < N; ++c) {
-    double gr[3], gp[3], gs[3];
-    grad(s, s.mur, c, gr);
-    grad(s, s.muphi, c, gp);
-    grad(s, s.mupsi, c, gs);
-    for (int k = 0; k < s.dim; ++k)
-      s.F[3 * c + k] = -s.rho[c] * gr[k] - s.phi[c] * gp[k] - s.psi[c] * gs[k] + s.fib[3 * c + k];
-  }
+  for (long c = 0; c < N; ++c)
+    for (int k = 0; k < s.dim; ++k) s.F[3 * c + k] = ffe[3 * c + k] + s.fib[3 * c + k];
   // (7) collision (eq. LBE): BGK + exact difference method for f (or Guo
   //     forcing when selected); BGK for g, h
   std::vector<double> fp(Q * N), gp(Q * N), hp(Q * N);
@@ -1364,6 +1482,198 @@ void or_interp(void* h, int nn, const double* X, const double* field, double* U)
   for (long c = 0; c < s->N; ++c)
     for (int k = 0; k < 3; ++k) v[3 * c + k] = field[k * s->N + c];
   interp(*s, X, nn, v, U);
+}
+
+// Lattice gradient ([3][N]) and Laplacian of a given scalar field, the
+// isotropic stencils of the step (periodic, mirror ghost at walls).
+void or_grad_field(void* h, const double* a, double* g) {
+  Sim* s = (Sim*)h;
+  std::vector<double> av(a, a + s->N);
+  for (long c = 0; c < s->N; ++c) {
+    double gg[3];
+    grad(*s, av, c, gg);
+    for (int k = 0; k < 3; ++k) g[k * s->N + c] = gg[k];
+  }
+}
+void or_lap_field(void* h, const double* a, double* out) {
+  Sim* s = (Sim*)h;
+  std::vector<double> av(a, a + s->N);
+  for (long c = 0; c < s->N; ++c) out[c] = lap(*s, av, c);
+}
+
+// Free-energy force f_FE ([3][N]) of given fields, exactly as the step forms
+// it (potential form or pressure-tensor form per the parameters, with
+// mu_psi' from I), without the immersed-boundary part.
+void or_force_fe(void* h, const double* rho, const double* phi, const double* psi, const double* I,
+                 double* F) {
+  Sim* s = (Sim*)h;
+  s->rho.assign(rho, rho + s->N);
+  s->phi.assign(phi, phi + s->N);
+  s->psi.assign(psi, psi + s->N);
+  s->I.assign(I, I + s->N);
+  potentials(*s);
+  std::vector<double> f;
+  fe_force(*s, f);
+  for (long c = 0; c < s->N; ++c)
+    for (int k = 0; k < 3; ++k) F[k * s->N + c] = f[3 * c + k];
+}
+double or_bulk_pressure(void* h, double rho, double phi, double psi) {
+  return bulk_pressure(((Sim*)h)->p, rho, phi, psi);
+}
+
+// Shape measures of membrane m at positions X (unwrapped markers):
+// out[0] = area, out[1] = volume.  2D ring: the enclosed area by the
+// shoelace formula (volume 0).  3D: the sum of the triangle areas, and the
+// enclosed volume by the divergence theorem, sum over triangles of
+// a . (b x c) / 6 (positive for triangles counter-clockwise seen from
+// outside).
+void or_capsule_measures(void* h, int m, const double* X, double* out) {
+  const Membrane& mm = ((Sim*)h)->mem[m];
+  double A = 0.0, V = 0.0;
+  if (mm.kind == 0) {
+    for (int l = 0; l < mm.nn; ++l) {
+      const double* p = &X[3 * l];
+      const double* q = &X[3 * ((l + 1) % mm.nn)];
+      A += 0.5 * (p[0] * q[1] - q[0] * p[1]);
+    }
+  } else {
+    for (int t = 0; t < mm.ne; ++t) {
+      const double* a = &X[3 * mm.E[3 * t]];
+      const double* b = &X[3 * mm.E[3 * t + 1]];
+      const double* c = &X[3 * mm.E[3 * t + 2]];
+      double e1[3] = {b[0] - a[0], b[1] - a[1], b[2] - a[2]};
+      double e2[3] = {c[0] - a[0], c[1] - a[1], c[2] - a[2]};
+      double cr[3] = {e1[1] * e2[2] - e1[2] * e2[1], e1[2] * e2[0] - e1[0] * e2[2], e1[0] * e2[1] - e1[1] * e2[0]};
+      A += 0.5 * n3(cr);
+      double bc[3] = {b[1] * c[2] - b[2] * c[1], b[2] * c[0] - b[0] * c[2], b[0] * c[1] - b[1] * c[0]};
+      V += (a[0] * bc[0] + a[1] * bc[1] + a[2] * bc[2]) / 6.0;
+    }
+  }
+  out[0] = A;
+  out[1] = V;
+}
+
+// Interpolation of a scalar lattice field at one point with the kernel of
+// eq. DiscreteDirac (as eq. Interpolation does for the velocity).
+static double interp_scalar(const Sim& s, const double* P, const std::vector<double>& a) {
+  int base[3] = {0, 0, 0}, span[3] = {1, 1, 1};
+  for (int k = 0; k < s.dim; ++k) { base[k] = (int)std::floor(P[k]) - 1; span[k] = 4; }
+  double acc = 0.0;
+  for (int i0 = 0; i0 < span[0]; ++i0)
+    for (int i1 = 0; i1 < span[1]; ++i1)
+      for (int i2 = 0; i2 < span[2]; ++i2) {
+        int q[3] = {base[0] + i0, base[1] + i1, base[2] + i2};
+        double wgt = 1.0;
+        for (int k = 0; k < s.dim; ++k) wgt *= peskin(q[k] - P[k]);
+        if (wgt == 0.0) continue;
+        bool out = false;
+        for (int k = 0; k < 3; ++k) {
+          if (is_wall_axis(s, k)) { if (q[k] < 0 || q[k] >= s.n[k]) out = true; }
+          else q[k] = wrapi(q[k], s.n[k]);
+        }
+        if (out) continue;
+        acc += wgt * a[cidx(s, q[0], q[1], q[2])];
+      }
+  return acc;
+}
+
+// Contact angle of membrane m (positions X) with the C1/C2 interface
+// phi = C1 - C2 = 0, the equilibrium measure of the capsule at a
+// fluid-fluid interface (Sec. 4.1).  The paper prints no discrete recipe;
+// reading: phi is interpolated to the markers with the kernel of eq.
+// DiscreteDirac; every membrane edge whose end values change sign holds a
+// contact point at the linear zero crossing; there the interface normal is
+// the interpolated lattice gradient of phi (pointing into C1) and the
+// membrane normal is the linear interpolation along the edge of its two
+// end markers' outward normals (a marker's normal: the normalised sum of
+// the area vectors of its triangles in 3D, of the outward normals of its
+// two segments in 2D).  The angle at a contact point is the angle between
+// the two unit normals; the result is their mean in degrees.  out[0] =
+// mean, out[1] = smallest, out[2] = largest angle.  Returns the number of
+// contact points (0: the membrane does not cross the interface; out is
+// then left unchanged).
+int or_contact_angle(void* h, int m, const double* X, const double* phi, double* out) {
+  Sim* s = (Sim*)h;
+  const Membrane& mm = s->mem[m];
+  const long N = s->N;
+  std::vector<double> ph(phi, phi + N), g[3];
+  for (int k = 0; k < 3; ++k) g[k].assign(N, 0.0);
+  for (long c = 0; c < N; ++c) {
+    double gg[3];
+    grad(*s, ph, c, gg);
+    for (int k = 0; k < 3; ++k) g[k][c] = gg[k];
+  }
+  std::vector<double> pn(mm.nn);
+  for (int l = 0; l < mm.nn; ++l) pn[l] = interp_scalar(*s, &X[3 * l], ph);
+  // marker normals and the edges
+  std::vector<double> vn(3 * mm.nn, 0.0);
+  std::vector<int> ea, eb;
+  if (mm.kind == 0) {
+    for (int l = 0; l < mm.nn; ++l) {
+      int l1 = (l + 1) % mm.nn;
+      double tx = X[3 * l1] - X[3 * l], ty = X[3 * l1 + 1] - X[3 * l + 1];
+      double lt = std::sqrt(tx * tx + ty * ty);
+      for (int q : {l, l1}) {
+        vn[3 * q] += ty / lt;
+        vn[3 * q + 1] += -tx / lt;
+      }
+      ea.push_back(l);
+      eb.push_back(l1);
+    }
+  } else {
+    std::vector<std::pair<int, int>> edges;
+    for (int t = 0; t < mm.ne; ++t) {
+      const int* v = &mm.E[3 * t];
+      const double* a = &X[3 * v[0]];
+      const double* b = &X[3 * v[1]];
+      const double* c = &X[3 * v[2]];
+      double e1[3] = {b[0] - a[0], b[1] - a[1], b[2] - a[2]};
+      double e2[3] = {c[0] - a[0], c[1] - a[1], c[2] - a[2]};
+      double cr[3] = {e1[1] * e2[2] - e1[2] * e2[1], e1[2] * e2[0] - e1[0] * e2[2], e1[0] * e2[1] - e1[1] * e2[0]};
+      for (int q = 0; q < 3; ++q) {
+        for (int k = 0; k < 3; ++k) vn[3 * v[q] + k] += cr[k];
+        edges.push_back({std::min(v[q], v[(q + 1) % 3]), std::max(v[q], v[(q + 1) % 3])});
+      }
+    }
+    std::sort(edges.begin(), edges.end());
+    edges.erase(std::unique(edges.begin(), edges.end()), edges.end());
+    for (auto& e : edges) {
+      ea.push_back(e.first);
+      eb.push_back(e.second);
+    }
+  }
+  for (int l = 0; l < mm.nn; ++l) {
+    double len = n3(&vn[3 * l]);
+    for (int k = 0; k < 3; ++k) vn[3 * l + k] /= len;
+  }
+  int cnt = 0;
+  double sum = 0.0, lo = 1e300, hi = -1e300;
+  for (size_t e = 0; e < ea.size(); ++e) {
+    const double fa = pn[ea[e]], fb = pn[eb[e]];
+    if (!(fa * fb < 0.0)) continue;
+    const double t = fa / (fa - fb);
+    double P[3], nm[3], gp[3];
+    for (int k = 0; k < 3; ++k) {
+      P[k] = X[3 * ea[e] + k] + t * (X[3 * eb[e] + k] - X[3 * ea[e] + k]);
+      nm[k] = (1.0 - t) * vn[3 * ea[e] + k] + t * vn[3 * eb[e] + k];
+    }
+    for (int k = 0; k < 3; ++k) gp[k] = interp_scalar(*s, P, g[k]);
+    const double lg = n3(gp), lm = n3(nm);
+    if (!(lg > 0.0) || !(lm > 0.0)) continue;
+    double cs = (gp[0] * nm[0] + gp[1] * nm[1] + gp[2] * nm[2]) / (lg * lm);
+    cs = std::min(1.0, std::max(-1.0, cs));
+    const double ang = std::acos(cs) * 180.0 / M_PI;
+    sum += ang;
+    lo = std::min(lo, ang);
+    hi = std::max(hi, ang);
+    ++cnt;
+  }
+  if (cnt > 0) {
+    out[0] = sum / cnt;
+    out[1] = lo;
+    out[2] = hi;
+  }
+  return cnt;
 }
 
 // FP64 totals of the current populations: sum rho, sum phi, sum psi.  Cell
