@@ -9,8 +9,9 @@ flush is needed between steps.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
-N > 1 runs independent replicas, one per rank (the method does not shard
-here): value = all ranks' cell updates / max-over-ranks time.
+N > 1 runs independent replicas, one per rank (independent lattices: the
+step of one lattice has no exchange with another): value = all ranks' cell
+updates / max-over-ranks time.
 `--impl reference` times the FP64 CPU oracle on the host cores instead.
 """
 from __future__ import annotations
@@ -31,6 +32,21 @@ METRIC = "ternary D3Q19+IBM MLUPS & %HBM roofline; time-to-equilibrium learned v
 BYTES_PER_CELL = 480  # algorithmic bytes per cell update with FP32 storage
 
 
+def kernel_bytes(store: int, real: int = 4, q: int = 19, t1: bool = True):
+    """Algorithmic DRAM bytes per cell of the two lattice kernels of a step
+    (each array element read or written once; store = bytes of a stored
+    population, real = of a moment field):
+      k_moments: pulls the 3Q populations, writes rho - 1, phi, psi and, for
+        the tau = 1 collide, j;
+      k_collide: reads rho - 1, phi, psi and I, writes the 3Q populations;
+        the general form also pulls the 3Q populations, the tau = 1 form
+        reads j instead."""
+    pops = 3 * q * store
+    mom = (6 if t1 else 3) * real
+    coll = pops + 4 * real + (3 * real if t1 else pops)
+    return {"k_moments": pops + mom, "k_collide": coll}
+
+
 def _peaks():
     try:
         return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -39,7 +55,7 @@ def _peaks():
 
 
 # sources each profiled kernel is compiled from
-KERNEL_SOURCES = {"k_collide": ("tlb_lb.cuh", "tlb_common.cuh")}
+KERNEL_SOURCES = {"k_collide": ("tlb_lb.cuh", "tlb_common.cuh"), "k_moments": ("tlb_lb.cuh", "tlb_common.cuh")}
 
 
 def _src_hash(kernel: str = "k_collide"):
@@ -177,12 +193,15 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-lowprec", action="store_true")
+    ap.add_argument("--no-moments", action="store_true", help="skip the moment-storage line")
     ap.add_argument("--no-sweep", action="store_true")
     ap.add_argument("--no-net", action="store_true")
     ap.add_argument("--warmstart", action="store_true",
                     help="the full time-to-equilibrium experiment of the learned warm start (128 training "
                          "equilibria, 32 held-out instances; minutes) instead of the reduced default one")
     ap.add_argument("--no-warmstart", action="store_true", help="skip the time-to-equilibrium measurement")
+    ap.add_argument("--tile", default=None,
+                    help="collide variant and z chunk 'V,ZC' for the main workload instead of autotuning")
     args = ap.parse_args()
 
     from paper_1906_03065_gb300 import workloads as W
@@ -209,7 +228,11 @@ def main():
 
     sim = T.Simulation(wl, device=dev)
     sim.init()
-    tile_variant, z_chunk = sim.autotune()
+    if args.tile:
+        tile_variant, z_chunk = (int(v) for v in args.tile.split(","))
+        sim.set_tile(tile_variant, z_chunk)
+    else:
+        tile_variant, z_chunk = sim.autotune()
     N = wl.params.ncells
     stream = sim.stream
     vis = os.environ.get("CUDA_VISIBLE_DEVICES")
@@ -238,18 +261,42 @@ def main():
     # per-phase device time (CUDA events on the library stream) for the roofline
     nprof = max(20, min(200, args.steps))
     pr = sim.profile(nprof)
-    t_coll = pr.ms_collide / nprof / 1e3
     peaks = _peaks()
     peak = peaks["hbm_gbs"] if peaks else 6800.0
-    achieved = BYTES_PER_CELL * N / t_coll / 1e9
+    t1 = tile_variant >= 13
+    kb = kernel_bytes(4, t1=t1)
+    kern = {}
+    for name, ms in (("k_moments", pr.ms_moments), ("k_collide", pr.ms_collide)):
+        t = ms / nprof / 1e3
+        ach = kb[name] * N / t / 1e9
+        kern[name] = {"bytes_per_cell": kb[name], "bytes_per_launch": kb[name] * N, "ms": t * 1e3,
+                      "achieved": ach, "frac": ach / peak, "traffic": _traffic(name)}
+    dom = max(kern, key=lambda k: kern[k]["ms"])
     step_eff = BYTES_PER_CELL * N * args.steps / (ms_max / 1e3) / 1e9
-    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak, "traffic": _traffic("k_collide"),
-                "kernel": "k_collide", "peak_source": "measured" if peaks else "fallback",
-                "bytes_per_launch": BYTES_PER_CELL * N,
-                "whole_step_frac": step_eff / peak,
+    roofline = {"bound": "hbm", "achieved": kern[dom]["achieved"], "peak": peak, "unit": "GB/s",
+                "frac": kern[dom]["frac"], "traffic": kern[dom]["traffic"],
+                "kernel": dom, "peak_source": "measured" if peaks else "fallback",
+                "bytes_per_launch": kern[dom]["bytes_per_launch"],
+                "whole_step_frac": step_eff / peak, "whole_step_bytes_per_cell": BYTES_PER_CELL,
+                "collide_form": "tau=1 equilibrium store" if t1 else "general (populations pulled)",
+                "kernels": kern,
                 "phase_ms_per_step": {"moments": pr.ms_moments / nprof, "ibm": pr.ms_ibm / nprof,
                                       "collide": pr.ms_collide / nprof, "interp": pr.ms_interp / nprof}}
+    # the same workload with the general collide (populations pulled; every tau)
+    general = {}
+    if t1:
+        with torch.cuda.stream(stream):
+            sim.set_tile(6, z_chunk)
+            sim.step(args.warmup)
+            g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            g0.record(stream)
+            sim.step(max(20, args.steps // 4))
+            g1.record(stream)
+            torch.cuda.synchronize(dev)
+            gms = g0.elapsed_time(g1) / max(20, args.steps // 4)
+            sim.set_tile(tile_variant, z_chunk)
+        general = {"tile_variant": 6, "ms_per_step": gms, "value": N / (gms / 1e3) / 1e6, "unit": "MLUPS"}
+    roofline["general_collide"] = general
 
     # end to end through the public API with host buffers: upload the initial
     # fields, step, read back the C3 field and the markers
@@ -272,16 +319,57 @@ def main():
     h2d = (Ch.nbytes + Uh.nbytes) / Ke
     d2h = (c3.nbytes + X.nbytes) / Ke
 
+    # the same workload with moment storage (tau = 1): 11 stored moments per
+    # cell instead of the 57 populations, rebuilt in the pull
+    moments = {}
+    if rank == 0 and not args.no_moments:
+        del sim
+        torch.cuda.empty_cache()
+        wlm = W.capsule_3d("f32")
+        wlm.params.state = "moments"
+        sm = T.Simulation(wlm, device=dev)
+        sm.init()
+        tvm, zcm = sm.autotune()
+        nm = max(20, min(args.steps, 1000))
+        sm.step(args.warmup)
+        torch.cuda.synchronize(dev)
+        m0, m1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        m0.record(sm.stream)
+        sm.step(nm)
+        m1.record(sm.stream)
+        torch.cuda.synchronize(dev)
+        msm = m0.elapsed_time(m1)
+        pm = sm.profile(nprof)
+        # algorithmic bytes per cell: the 11 stored moments read once by the
+        # rebuilding pull (k_moments_recon, which writes rho - 1, phi, psi, j)
+        # and written once by the collide (which reads those and I)
+        kbm = {"k_moments_recon": 11 * 4 + 6 * 4, "k_collide": 7 * 4 + 11 * 4}
+        km = {}
+        for name, ms in (("k_moments_recon", pm.ms_moments), ("k_collide", pm.ms_collide)):
+            t = ms / nprof / 1e3
+            ach = kbm[name] * N / t / 1e9
+            km[name] = {"bytes_per_cell": kbm[name], "ms": t * 1e3, "achieved": ach, "frac": ach / peak}
+        bpm = 11 * 8 + 24  # stored moments read and written, rho - 1, phi, psi written and read
+        moments = {"workload": wlm.name + " (state: moments)", "value": N * nm / (msm / 1e3) / 1e6,
+                   "unit": "MLUPS", "steps": nm, "ms_per_step": msm / nm, "tile_variant": tvm,
+                   "whole_step_bytes_per_cell": bpm,
+                   "whole_step_frac": bpm * N * nm / (msm / 1e3) / 1e9 / peak, "kernels": km,
+                   "phase_ms_per_step": {"moments": pm.ms_moments / nprof, "ibm": pm.ms_ibm / nprof,
+                                         "collide": pm.ms_collide / nprof, "interp": pm.ms_interp / nprof}}
+        del sm
+        torch.cuda.empty_cache()
+
     # the same workload with 16-bit population storage (FP32 arithmetic)
     lowprec = {}
     if rank == 0 and not args.no_lowprec:
-        del sim
+        if "sim" in locals():
+            del sim
         torch.cuda.empty_cache()
         for fmt, bpc in (("f16", 252), ("bf16", 252)):
             wl16 = W.capsule_3d(fmt)
             s16 = T.Simulation(wl16, device=dev)
             s16.init()
-            s16.autotune()
+            tv16, _ = s16.autotune()
             n16 = max(20, min(args.steps, 500))
             s16.step(args.warmup)
             torch.cuda.synchronize(dev)
@@ -292,11 +380,16 @@ def main():
             torch.cuda.synchronize(dev)
             ms16 = a0.elapsed_time(a1)
             p16 = s16.profile(nprof)
-            tc16 = p16.ms_collide / nprof / 1e3
-            ach = bpc * N / tc16 / 1e9
+            kb16 = kernel_bytes(2, t1=tv16 >= 13)
+            k16 = {}
+            for name, ms in (("k_moments", p16.ms_moments), ("k_collide", p16.ms_collide)):
+                t = ms / nprof / 1e3
+                ach = kb16[name] * N / t / 1e9
+                k16[name] = {"bytes_per_cell": kb16[name], "ms": t * 1e3, "achieved": ach, "frac": ach / peak}
             lowprec[fmt] = {"value": N * n16 / (ms16 / 1e3) / 1e6, "unit": "MLUPS", "steps": n16,
-                            "collide_achieved_gbs": ach, "collide_frac": ach / peak,
-                            "bytes_per_cell": bpc}
+                            "whole_step_bytes_per_cell": bpc,
+                            "whole_step_frac": bpc * N * n16 / (ms16 / 1e3) / 1e9 / peak,
+                            "tile_variant": tv16, "kernels": k16}
             del s16
             torch.cuda.empty_cache()
 
@@ -441,6 +534,7 @@ def main():
             "roofline": roofline, "cpu_baseline": cpu, "clocks": clocks,
             "e2e": {"value": e2e_v, "unit": "MLUPS", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "gpu_launches": launches,
+            "moment_storage": moments,
             "lowprec_storage": lowprec,
             "batched_sweep": sweep,
             "warm_start_net": net_line,

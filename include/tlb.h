@@ -98,8 +98,24 @@ typedef struct {
                                        f^eq(rho, v), v = (j + F/2)/rho, plus
                                        (1 - 1/(2 tau)) w_i [3 (c_i - v) +
                                        9 (c_i.v) c_i] . F)                    */
+  int state;                        /* TLB_STATE_POPULATIONS (default) or
+                                       TLB_STATE_MOMENTS (see below)         */
 } tlb_params;
 enum { TLB_FORCE_EDM = 0, TLB_FORCE_GUO = 1 };
+/* State kept between steps (tlb_params.state):
+ * TLB_STATE_POPULATIONS -- the 3Q post-collision populations (any tau);
+ * TLB_STATE_MOMENTS     -- at tau = tau_phi = tau_psi = 1 with TLB_FORCE_EDM
+ *   (the paper's setting, Sec. 3.1) every post-collision population is an
+ *   equilibrium (eq. EDF) of its cell, so 11 values per cell stand for all
+ *   of them: rho - 1, u + du, phi, Gamma_phi mu_phi, psi, Gamma_psi mu_psi'
+ *   and v (eq. LBE at tau = 1).  The pull of each step rebuilds every
+ *   population from the cell it streams from.  The same method, another
+ *   executed scheme: 88 bytes of state traffic per cell update in FP32
+ *   against 456.  Only with FP32 storage (FP64 or FP32 in 2D); not in
+ *   batches.  Initial states and populations written by the caller are
+ *   pulled as populations by the next step; reads of populations or fields
+ *   see the populations the moments stand for. */
+enum { TLB_STATE_POPULATIONS = 0, TLB_STATE_MOMENTS = 1 };
 
 typedef struct {
   int kind;           /* TLB_MEM_RING2D | TLB_MEM_TRI3D                        */
@@ -191,6 +207,21 @@ tlb_status tlb_diagnostics(void* ctx, tlb_diag* out);
  * - Calls no cudaMalloc/cudaFree or any allocating routine. */
 tlb_status tlb_diagnostics_static(void* ctx, tlb_diag* out);
 
+/* Contact angle of every capsule with the C1/C2 interface phi = 0, in FP64
+ * (synchronises the stream): the equilibrium measure of a capsule at a
+ * fluid-fluid interface (Sec. 4.1; the paper prints no discrete recipe).
+ * phi is interpolated to the markers with the kernel of eq. DiscreteDirac;
+ * each membrane edge whose ends change sign holds a contact point at the
+ * linear zero crossing; there the angle between the interface normal (the
+ * interpolated lattice gradient of phi, pointing into C1) and the outward
+ * membrane normal (the end markers' normals interpolated along the edge).
+ * out: host, n_values >= 4*n_caps doubles; per capsule the mean angle over
+ * its contact points (degrees), the smallest, the largest and the number of
+ * contact points (mean/min/max NaN when it does not cross the interface).
+ * Uses the population buffer the next step overwrites as scratch, so it
+ * must not overlap a tlb_step of the same context. */
+tlb_status tlb_contact_angle(void* ctx, double* out, size_t n_values);
+
 /* Equilibrium residual in FP64 (synchronises the stream).  out[0] and
  * out[1]: the largest change of phi and of psi at any cell; out[2]: the
  * largest change of any coordinate of any membrane marker; each since the
@@ -241,14 +272,21 @@ tlb_status tlb_profile_steps(void* ctx, long n_steps, tlb_profile* out);
  * 1: 32x8, 2: 64x4 in 3D; 0: 32, 1: 64, 2: 128 columns in 2D; form 0:
  * registers for 640 threads per SM, 1: 512 with the next population set
  * prefetched, 2: 768, 3: 1024; v = 12: tile 0 at 896) and planes per chunk
- * when the pointers are
- * non-NULL.  Synchronises the stream.  Not in the paper: an autotuner for
- * this implementation's launch shape. */
+ * when the pointers are non-NULL.  Variants 13..18 (tiles 0..2 at 768,
+ * then at 1024 threads per SM) are the collide for tau = tau_phi = tau_psi
+ * = 1 with TLB_FORCE_EDM, the paper's setting (Sec. 3.1): there every
+ * post-collision population is an equilibrium of the cell's moments (eq.
+ * LBE), so that collide pulls no population and only stores; the moment
+ * pass then also writes j.  They are tried only where they
+ * apply, and a new context starts on variant 13 there (else 0).
+ * Synchronises the stream.  Not in the paper: an autotuner for this
+ * implementation's launch shape. */
 tlb_status tlb_autotune(void* ctx, int* tile_variant, int* z_chunk);
 
-/* Set the collide variant (0..12, as written by tlb_autotune) and the
- * planes per z chunk (1..nz) explicitly.  The results do not depend on the
- * choice. */
+/* Set the collide variant (0..18, as written by tlb_autotune; 13..18 only
+ * where tau = tau_phi = tau_psi = 1 with TLB_FORCE_EDM, else TLB_ERR_ARG)
+ * and the planes per z chunk (1..nz) explicitly.  The results do not depend
+ * on the choice beyond rounding. */
 tlb_status tlb_set_tile(void* ctx, int tile_variant, int z_chunk);
 
 /* Number of CUDA kernel launches enqueued by the last tlb_step call. */

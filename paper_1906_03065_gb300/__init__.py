@@ -35,7 +35,8 @@ class _Params(C.Structure):
                 ("tau", C.c_double), ("tau_phi", C.c_double), ("tau_psi", C.c_double),
                 ("gamma_phi", C.c_double), ("gamma_psi", C.c_double), ("alpha", C.c_double),
                 ("kappa", C.c_double * 3), ("kappa_c", C.c_double), ("dc", C.c_double),
-                ("u0", C.c_double * 3), ("interface_pos", C.c_double), ("forcing", C.c_int)]
+                ("u0", C.c_double * 3), ("interface_pos", C.c_double), ("forcing", C.c_int),
+                ("state", C.c_int)]
 
 
 class _Mem(C.Structure):
@@ -99,6 +100,8 @@ def lib():
         L.tlb_set_tile.restype = C.c_int
         L.tlb_residual.argtypes = [vp, dp]
         L.tlb_residual.restype = C.c_int
+        L.tlb_contact_angle.argtypes = [vp, dp, sz]
+        L.tlb_contact_angle.restype = C.c_int
         ip, lp = C.POINTER(C.c_int), C.POINTER(C.c_long)
         L.tlb_batch_state_bytes.argtypes = [C.POINTER(_Inst), C.c_int, C.POINTER(sz)]
         L.tlb_batch_create.argtypes = [C.POINTER(_Inst), C.c_int, vp, sz, vp, C.POINTER(vp)]
@@ -168,6 +171,7 @@ def make_params(p) -> _Params:
         cp.u0[k] = p.u0[k]
     cp.interface_pos = p.interface_pos
     cp.forcing = {"edm": 0, "guo": 1}[getattr(p, "forcing", "edm")]
+    cp.state = {"populations": 0, "moments": 1}[getattr(p, "state", "populations")]
     return cp
 
 
@@ -320,6 +324,13 @@ class Simulation:
         d = Diag()
         _check(lib().tlb_diagnostics(self.h, C.byref(d)))
         return d
+
+    def contact_angle(self) -> np.ndarray:
+        """Per capsule [mean, min, max angle in degrees, contact points] of
+        the membrane with the phi = 0 interface (see tlb_contact_angle)."""
+        out = np.zeros(4 * max(1, len(self.nn)))
+        _check(lib().tlb_contact_angle(self.h, _dp(out), out.size))
+        return out.reshape(-1, 4)[:len(self.nn)]
 
     def residual(self) -> np.ndarray:
         """[max |d phi|, max |d psi|, max |d X|, residual] since the last call

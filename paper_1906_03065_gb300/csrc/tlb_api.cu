@@ -116,6 +116,17 @@ static tlb_status check_params(const tlb_params* p, const tlb_membrane_desc* mem
   if (!(p->tau > 0.5 && p->tau_phi > 0.5 && p->tau_psi > 0.5)) { set_error("relaxation times must exceed 1/2"); return TLB_ERR_ARG; }
   if (!(p->alpha > 0) || !(p->dc > 0) || p->dc > 60) { set_error("alpha > 0 and 0 < dc <= 60 required"); return TLB_ERR_ARG; }
   if (p->forcing != TLB_FORCE_EDM && p->forcing != TLB_FORCE_GUO) { set_error("unknown forcing"); return TLB_ERR_ARG; }
+  if (p->state != TLB_STATE_POPULATIONS && p->state != TLB_STATE_MOMENTS) { set_error("unknown state"); return TLB_ERR_ARG; }
+  if (p->state == TLB_STATE_MOMENTS) {
+    if (!(p->tau == 1.0 && p->tau_phi == 1.0 && p->tau_psi == 1.0 && p->forcing == TLB_FORCE_EDM)) {
+      set_error("TLB_STATE_MOMENTS needs tau = tau_phi = tau_psi = 1 and TLB_FORCE_EDM");
+      return TLB_ERR_ARG;
+    }
+    if (!(p->storage == TLB_F32 || (p->dim == 2 && p->storage == TLB_F64))) {
+      set_error("TLB_STATE_MOMENTS needs FP32 storage (or FP64 in 2D)");
+      return TLB_ERR_ARG;
+    }
+  }
   if (n_mem < 0 || n_mem > 8) { set_error("at most 8 membranes"); return TLB_ERR_ARG; }
   for (int m = 0; m < n_mem; ++m) {
     const tlb_membrane_desc& d = mems[m];
@@ -240,6 +251,8 @@ static void plan(const tlb_params* p, const std::vector<HostMem>& mems, Ctx& c) 
   take(L.rho, P * R);
   take(L.phi, P * R);
   take(L.psi, P * R);
+  take(L.jm, 3 * P * R);
+  take(L.M, p->state == TLB_STATE_MOMENTS ? 11 * P * R : 0);
   take(L.I, P * R);
   take(L.dsel, P * R);
   take(L.own, P * 4);
@@ -332,6 +345,8 @@ tlb_status tlb_create(const tlb_params* params, const tlb_membrane_desc* mems, i
   // z chunk of the plane sweep: long enough to amortise the 4-plane halo,
   // short enough to give a few waves on the 152 SMs
   c->tiles_zc = c->nz >= 64 ? 32 : (c->nz >= 16 ? 8 : c->nz);
+  // the tau = 1 collide (no population pull) wherever it applies
+  c->tile_variant = c->t1_ok() ? 13 : 0;
   switch (params->dim * 10 + params->storage) {
     case 20: c->impl = make_impl_d2q9_f64(); break;
     case 21: c->impl = make_impl_d2q9_f32(); break;
@@ -608,6 +623,14 @@ tlb_status tlb_diagnostics(void* ctx, tlb_diag* out) {
   return c->impl->diagnostics(c, out);
 }
 
+tlb_status tlb_contact_angle(void* ctx, double* out, size_t n_values) {
+  Ctx* c = (Ctx*)ctx;
+  if (!c || !out) { set_error("ctx/out is NULL"); return TLB_ERR_ARG; }
+  if (n_values < 4 * (size_t)c->ncap) { set_error("contact_angle: out holds fewer than 4 values per capsule"); return TLB_ERR_ARG; }
+  if (!c->initialised) { set_error("contact_angle: context not initialised"); return TLB_ERR_STATE; }
+  return c->impl->contact_angle(c, out);
+}
+
 // Residual values from the maxima the residual kernel folded into res[0..2].
 static void residual_values(const unsigned long long* bits, long dt, double* out) {
   double m = 0;
@@ -667,7 +690,15 @@ tlb_status tlb_set_tile(void* ctx, int tile_variant, int z_chunk) {
   Ctx* c = (Ctx*)ctx;
   if (!c) { set_error("ctx is NULL"); return TLB_ERR_ARG; }
   if (tile_variant < 0 || tile_variant >= COLLIDE_NVAR || z_chunk < 1 || z_chunk > c->nz) {
-    set_error("set_tile: tile_variant must be 0..12 and z_chunk 1..nz");
+    set_error("set_tile: tile_variant must be 0..18 and z_chunk 1..nz");
+    return TLB_ERR_ARG;
+  }
+  if (variant_t1(tile_variant) && !c->t1_ok()) {
+    set_error("set_tile: variants 13..18 need tau = tau_phi = tau_psi = 1 and TLB_FORCE_EDM");
+    return TLB_ERR_ARG;
+  }
+  if (!variant_t1(tile_variant) && c->moments()) {
+    set_error("set_tile: moment storage needs one of the variants 13..18");
     return TLB_ERR_ARG;
   }
   c->tile_variant = tile_variant;

@@ -173,17 +173,17 @@ struct BatchImpl : BatchBase {
     }
   }
 
-  // tile shape of a collide variant (v % 3; the form is v / 3)
-  static int tile_x(int v) {
-    v %= 3;
-    if constexpr (L::DIM == 3) return v == 2 ? 64 : 32;
-    else return v == 1 ? 64 : (v == 2 ? 128 : 32);
+  // tile shape of a collide variant, read off the variant dispatch itself
+  static int2 tile_of(int v) {
+    int2 t = {32, 1};
+    collide_variant<L>(v, [&](auto tx, auto ty, auto) {
+      t = {decltype(tx)::value, decltype(ty)::value};
+      return TLB_OK;
+    });
+    return t;
   }
-  static int tile_y(int v) {
-    v %= 3;
-    if constexpr (L::DIM == 3) return v == 1 ? 8 : 4;
-    else return 1;
-  }
+  static int tile_x(int v) { return tile_of(v).x; }
+  static int tile_y(int v) { return tile_of(v).y; }
 
   template <int MINB, class... Ops>
   static int occupancy_grid(int nt) {
@@ -322,6 +322,7 @@ struct BatchImpl : BatchBase {
         BA& a = t[j];
         a.lb = I::lbargs(c, c->cur ^ q);
         a.lb.zc = b->zc;
+        a.lb.jm = variant_t1(b->tile_variant) ? c->ptr<typename Prec<MODE>::Real>(c->L.jm) : nullptr;
         a.ib = I::ibargs(c);
         a.rp = I::resptrs(c, b->ptr<unsigned long long>(b->res) + 4 * (size_t)b->act[j]);
       }
@@ -461,12 +462,16 @@ struct BatchImpl : BatchBase {
     for (int i : b->act) {
       Ctx* c = b->inst[i];
       LBArgs<MODE> la = I::lbargs(c, c->cur);
+      la.jm = c->ptr<typename Prec<MODE>::Real>(c->L.jm);
       k_moments<L, MODE><<<cdiv(c->N, 256), 256, 0, b->stream>>>(la);
       b->launches++;
       TLB_CUDA(cudaGetLastError());
     }
+    bool t1 = true;
+    for (int i : b->act) t1 = t1 && b->inst[i]->t1_ok();
     for (int v = 0; v < COLLIDE_NVAR && st == TLB_OK; ++v)
       for (size_t zi = 0; zi < zcs.size() && st == TLB_OK; ++zi) {
+        if (variant_t1(v) && !t1) continue;
         b->tile_variant = v;
         b->zc = zcs[zi];
         b->graph_dirty = true;

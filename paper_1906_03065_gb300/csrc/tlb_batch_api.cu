@@ -97,6 +97,11 @@ tlb_status tlb_batch_create(const tlb_instance_desc* inst, int n_inst, void* are
     set_error("batch arena too small: need " + std::to_string(bp.total) + " bytes");
     return TLB_ERR_ALLOC;
   }
+  for (int i = 0; i < n_inst; ++i)
+    if (inst[i].params.state != TLB_STATE_POPULATIONS) {
+      set_error("batch: instances keep populations (TLB_STATE_POPULATIONS)");
+      return TLB_ERR_ARG;
+    }
   Batch* b = new Batch();
   b->dim = inst[0].params.dim;
   b->storage = inst[0].params.storage;
@@ -132,6 +137,9 @@ tlb_status tlb_batch_create(const tlb_instance_desc* inst, int n_inst, void* are
     nzmax = std::max(nzmax, c->nz);
   }
   b->zc = nzmax >= 64 ? 16 : std::min(nzmax, 8);
+  bool t1 = true;
+  for (Ctx* c : b->inst) t1 = t1 && c->t1_ok();
+  b->tile_variant = t1 ? 13 : 0;  // the tau = 1 collide wherever it applies
   for (int q = 0; q < 2; ++q) b->targs[q] = {bp.targs[q], (size_t)n_inst * Batch::ARGS_BYTES};
   b->vg = {bp.vg, (size_t)Batch::NPH * Batch::MAXOPS * n_inst * 16};
   b->res = {bp.res, (size_t)n_inst * 4 * 8};

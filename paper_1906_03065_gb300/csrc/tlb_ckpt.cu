@@ -26,11 +26,36 @@ struct Header {
   char magic[8];
   uint32_t version, header_bytes;
   // the parameters, field by field (no struct padding in the file)
-  int32_t dim, nx, ny, nz, wall_last, storage, forcing, pad;
+  int32_t dim, nx, ny, nz, wall_last, storage, forcing, state;
   double tau, tau_phi, tau_psi, gamma_phi, gamma_psi, alpha, kappa[3], kappa_c, dc, u0[3], interface_pos;
   int64_t nn, ne, N, P, t, t_snap;
+  uint64_t mem_hash;  // the membranes: reference shapes, elements, moduli
   uint64_t sec_bytes[kSections];
 };
+
+// FNV-1a over the membrane descriptors the context was created with, so a
+// checkpoint only loads onto a context with the same membranes (shape,
+// connectivity and stiffness), not just the same counts.
+uint64_t membrane_hash(const Ctx* c) {
+  uint64_t h = 1469598103934665603ull;
+  auto mix = [&](const void* p, size_t n) {
+    const unsigned char* b = (const unsigned char*)p;
+    for (size_t i = 0; i < n; ++i) {
+      h ^= b[i];
+      h *= 1099511628211ull;
+    }
+  };
+  for (const HostMem& m : c->mems) {
+    mix(&m.kind, sizeof(m.kind));
+    mix(&m.nn, sizeof(m.nn));
+    mix(&m.ne, sizeof(m.ne));
+    mix(m.X0.data(), m.X0.size() * sizeof(double));
+    mix(m.E.data(), m.E.size() * sizeof(int));
+    const double mod[4] = {m.ks, m.kb, m.G, m.C};
+    mix(mod, sizeof(mod));
+  }
+  return h;
+}
 
 void fill_params(Header& h, const tlb_params& p) {
   h.dim = p.dim;
@@ -40,7 +65,7 @@ void fill_params(Header& h, const tlb_params& p) {
   h.wall_last = p.wall_last;
   h.storage = p.storage;
   h.forcing = p.forcing;
-  h.pad = 0;
+  h.state = p.state;
   h.tau = p.tau;
   h.tau_phi = p.tau_phi;
   h.tau_psi = p.tau_psi;
@@ -56,7 +81,7 @@ void fill_params(Header& h, const tlb_params& p) {
 
 bool same_params(const Header& a, const Header& b) {
   if (a.dim != b.dim || a.nx != b.nx || a.ny != b.ny || a.nz != b.nz || a.wall_last != b.wall_last ||
-      a.storage != b.storage || a.forcing != b.forcing)
+      a.storage != b.storage || a.forcing != b.forcing || a.state != b.state)
     return false;
   const double x[] = {a.tau, a.tau_phi, a.tau_psi, a.gamma_phi, a.gamma_psi, a.alpha, a.kappa[0], a.kappa[1],
                       a.kappa[2], a.kappa_c, a.dc, a.u0[0], a.u0[1], a.u0[2], a.interface_pos};
@@ -78,7 +103,7 @@ Header header_of(Ctx* c, const size_t* bytes) {
   Header h;
   memset(&h, 0, sizeof(h));
   memcpy(h.magic, kMagic, 8);
-  h.version = 1;
+  h.version = 2;
   h.header_bytes = sizeof(Header);
   fill_params(h, c->p);
   h.nn = c->nn;
@@ -87,6 +112,7 @@ Header header_of(Ctx* c, const size_t* bytes) {
   h.P = c->P;
   h.t = c->t;
   h.t_snap = c->t_snap;
+  h.mem_hash = membrane_hash(c);
   for (int k = 0; k < kSections; ++k) h.sec_bytes[k] = bytes[k];
   return h;
 }
@@ -99,6 +125,9 @@ tlb_status tlb_save(void* ctx, void* host_blob, size_t* bytes) {
   Ctx* c = (Ctx*)ctx;
   if (!c || !bytes) { set_error("ctx/bytes is NULL"); return TLB_ERR_ARG; }
   if (!c->initialised) { set_error("tlb_save before tlb_init_fields"); return TLB_ERR_STATE; }
+  // moment storage: the checkpoint holds the populations the moments stand
+  // for (the same values the next pull would rebuild)
+  if (tlb_status st = c->impl->sync_pops(c); st != TLB_OK) return st;
   char* dev[kSections];
   size_t sz[kSections];
   sections(c, c->cur, dev, sz);
@@ -131,7 +160,7 @@ tlb_status tlb_load(void* ctx, const void* host_blob, size_t bytes) {
   if (bytes < sizeof(Header)) { set_error("tlb_load: blob shorter than its header"); return TLB_ERR_ARG; }
   Header h;
   memcpy(&h, host_blob, sizeof(h));
-  if (memcmp(h.magic, kMagic, 8) != 0 || h.version != 1 || h.header_bytes != sizeof(Header)) {
+  if (memcmp(h.magic, kMagic, 8) != 0 || h.version != 2 || h.header_bytes != sizeof(Header)) {
     set_error("tlb_load: not a checkpoint of this library version");
     return TLB_ERR_ARG;
   }
@@ -139,7 +168,8 @@ tlb_status tlb_load(void* ctx, const void* host_blob, size_t bytes) {
   size_t sz[kSections];
   sections(c, 0, dev, sz);
   Header mine = header_of(c, sz);
-  if (!same_params(h, mine) || h.nn != mine.nn || h.ne != mine.ne || h.N != mine.N || h.P != mine.P) {
+  if (!same_params(h, mine) || h.nn != mine.nn || h.ne != mine.ne || h.N != mine.N || h.P != mine.P ||
+      h.mem_hash != mine.mem_hash) {
     set_error("tlb_load: the checkpoint was taken of a context with other parameters or membranes");
     return TLB_ERR_ARG;
   }
@@ -162,6 +192,8 @@ tlb_status tlb_load(void* ctx, const void* host_blob, size_t bytes) {
   c->t_snap = h.t_snap;
   c->initialised = true;
   c->box_stale = true;
+  c->state_in_pops = true;  // (moment storage: the next step pulls them)
+  c->pops_stale = false;
   return TLB_OK;
 }
 

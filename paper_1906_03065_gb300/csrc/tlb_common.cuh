@@ -181,11 +181,16 @@ struct Pull {
     }
   }
 
+  // The rest populations are added last: g_0 and h_0 carry nearly all of
+  // phi and psi, so the small moving populations are summed first at their
+  // own scale and the sum is rounded once at the scale of phi (adding them
+  // one by one to g_0 rounds each addition there: in FP32 that made the
+  // force about 4 times noisier).
   __device__ __forceinline__ CellMoments<Real> moments() const {
     CellMoments<Real> m;
     Real r = 0, jx = 0, jy = 0, jz = 0, p = 0, s = 0;
 #pragma unroll
-    for (int i = 0; i < L::Q; ++i) {
+    for (int i = 1; i < L::Q; ++i) {
       r += f[i];
       if (L::cx(i)) jx += L::cx(i) > 0 ? f[i] : -f[i];
       if (L::cy(i)) jy += L::cy(i) > 0 ? f[i] : -f[i];
@@ -193,6 +198,9 @@ struct Pull {
       p += g[i];
       s += h[i];
     }
+    r += f[0];
+    p += g[0];
+    s += h[0];
     m.drho = r;
     m.j[0] = jx;
     m.j[1] = jy;
@@ -220,18 +228,22 @@ __device__ __forceinline__ void marker_box(const int* cur, int margin, const Geo
 }
 
 // Chemical potentials of App. A (eq. AppA) without the ideal-gas part of
-// mu_rho; mu_psi' adds kappa_c (psi - I) (Sec. 3.1).
+// mu_rho; mu_psi' adds kappa_c (psi - I) (Sec. 3.1).  The density enters as
+// drho = rho - 1 (and Lr as its Laplacian, which is the Laplacian of rho):
+// with A = rho + phi - psi = 1 + a, A (A - 1)(A - 2) = a (a^2 - 1), the same
+// polynomial written around the bulk value, so that a working-precision
+// drho keeps its low bits (rho = 1 + drho would round them away).
 template <class Real>
 struct FEParams {
   Real k1, k2, k3, kc, a2;  // kappa_1..3, kappa_c, alpha^2
 };
 template <class Real>
-__device__ __forceinline__ void chem_potentials(const FEParams<Real>& fe, Real rho, Real phi, Real psi,
+__device__ __forceinline__ void chem_potentials(const FEParams<Real>& fe, Real drho, Real phi, Real psi,
                                                 Real Lr, Real Lp, Real Ls, Real I, Real& mr,
                                                 Real& mp, Real& ms) {
-  Real A = rho + phi - psi, B = rho - phi - psi;
-  Real tA = fe.k1 * Real(0.125) * A * (A - Real(1)) * (A - Real(2));
-  Real tB = fe.k2 * Real(0.125) * B * (B - Real(1)) * (B - Real(2));
+  const Real a = drho + phi - psi, b = drho - phi - psi;  // A - 1, B - 1
+  Real tA = fe.k1 * Real(0.125) * a * (a * a - Real(1));
+  Real tB = fe.k2 * Real(0.125) * b * (b * b - Real(1));
   Real q = Real(0.25) * fe.a2;
   Real kp = fe.k1 + fe.k2, km = fe.k2 - fe.k1;
   mr = tA + tB + q * (kp * (Ls - Lr) + km * Lp);
@@ -239,6 +251,68 @@ __device__ __forceinline__ void chem_potentials(const FEParams<Real>& fe, Real r
   ms = -tA - tB + q * (kp * Lr - km * Lp - (kp + Real(4) * fe.k3) * Ls) +
        fe.k3 * psi * (psi - Real(1)) * (Real(2) * psi - Real(1)) + fe.kc * (psi - I);
 }
+
+// Explicitly rounded arithmetic (round to nearest, never contracted): the
+// same expression then rounds the same way in every kernel it is inlined
+// into, whatever the compiler's multiply-add contraction would choose there.
+__device__ __forceinline__ float rmul(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double rmul(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ float radd(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ double radd(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ float rfma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ double rfma(double a, double b, double c) { return __fma_rn(a, b, c); }
+
+// ------------------------------------------------ moment storage (tau = 1)
+// At tau = tau_phi = tau_psi = 1 with the exact difference method every
+// post-collision population is an equilibrium (eq. EDF) of its cell:
+// f*_i = f_i^eq(rho, w) with w = u + du, g*_i = g_i^eq(phi, Gamma_phi mu_phi,
+// v), h*_i = h_i^eq(psi, Gamma_psi mu_psi', v) (eq. LBE at tau = 1).  The
+// moment-storage scheme keeps these 11 values per cell instead of the 3Q
+// populations; the pull of the next step rebuilds each population from the
+// cell it streams from.  Plane order of the stored moments:
+enum { M_DRHO = 0, M_W = 1, M_PHI = 4, M_GMP = 5, M_PSI = 6, M_GMS = 7, M_V = 8, M_COUNT = 11 };
+
+// The post-collision populations of one cell from its stored moments, with
+// the explicitly rounded operations (see rmul), so the reconstruction in the
+// pull, in the interpolation and in the materialised populations gives the
+// same value.
+template <class L, class Real>
+struct EqCell {
+  Real drho, rho, w[3], ww, ord[2], gm3[2], v[3], vv;
+  // drho and w only (what f_i needs)
+  __device__ __forceinline__ void load_f(const Real* __restrict__ M, int P32, int c) {
+    drho = M[M_DRHO * P32 + c];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) w[d] = M[(M_W + d) * P32 + c];
+    rho = Real(1) + drho;
+    ww = rfma(w[2], w[2], rfma(w[1], w[1], rmul(w[0], w[0])));
+  }
+  __device__ __forceinline__ void load(const Real* __restrict__ M, int P32, int c) {
+    load_f(M, P32, c);
+    ord[0] = M[M_PHI * P32 + c];
+    ord[1] = M[M_PSI * P32 + c];
+    gm3[0] = rmul(Real(3), M[M_GMP * P32 + c]);
+    gm3[1] = rmul(Real(3), M[M_GMS * P32 + c]);
+#pragma unroll
+    for (int d = 0; d < 3; ++d) v[d] = M[(M_V + d) * P32 + c];
+    vv = rfma(v[2], v[2], rfma(v[1], v[1], rmul(v[0], v[0])));
+  }
+  // f_i - w_i = w_i (drho + rho (3 c.w + 4.5 (c.w)^2 - 1.5 w^2))
+  __device__ __forceinline__ Real f(int i) const {
+    const Real cw = L::cx(i) * w[0] + L::cy(i) * w[1] + L::cz(i) * w[2];
+    const Real p = rfma(rmul(Real(4.5), cw), cw, rfma(Real(3), cw, rmul(Real(-1.5), ww)));
+    return rmul(Real(L::w(i)), rfma(rho, p, drho));
+  }
+  // g_i (s = 0) or h_i (s = 1): w_i (3 Gamma mu + ord p(c.v)) for i != 0; the
+  // rest population closes the zeroth moment
+  __device__ __forceinline__ Real o(int s, int i) const {
+    if (i == 0)
+      return radd(rfma(gm3[s], Real(L::w(0)) - Real(1), ord[s]), rmul(rmul(Real(-1.5 * L::w(0)), ord[s]), vv));
+    const Real cv = L::cx(i) * v[0] + L::cy(i) * v[1] + L::cz(i) * v[2];
+    const Real p = rfma(rmul(Real(4.5), cv), cv, rfma(Real(3), cv, rmul(Real(-1.5), vv)));
+    return rmul(Real(L::w(i)), rfma(ord[s], p, gm3[s]));
+  }
+};
 
 // Status flags written by kernels (bitwise OR into a device word).
 enum { ST_NAN = 1, ST_MARKER_JUMP = 2, ST_TIMEOUT = 4, ST_OVERFLOW = 8 };

@@ -11,8 +11,10 @@
 #include "../../include/tlb.h"
 
 // Collide variants: 3 tile shapes x 4 register forms, v = 3 form + tile,
-// and the smallest tile in a fifth form (v = 12).
-constexpr int COLLIDE_NVAR = 13;
+// the smallest tile in a fifth form (v = 12), and the 3 tiles in the two
+// forms of the tau = 1 collide (v = 13..18, see variant_t1).
+constexpr int COLLIDE_NVAR = 19;
+constexpr bool variant_t1(int v) { return v >= 13 && v <= 18; }
 
 // z-chunk lengths the collide autotuner tries: every distinct ceil(nz / m)
 // of at least 4 planes (each gives another grid, so another fill of the
@@ -45,6 +47,12 @@ struct ImplBase {
   virtual tlb_status init_from_moments(Ctx* c) = 0;
   // profile I (with owners and distances) of the current marker positions
   virtual tlb_status profile_now(Ctx* c) = 0;
+  // contact angle of every capsule with phi = 0: out[cap] = {mean, min,
+  // max, contact points}; synchronises
+  virtual tlb_status contact_angle(Ctx* c, double* out) = 0;
+  // moment storage: write the populations the stored moments stand for into
+  // the current population buffer if it is stale (no-op otherwise)
+  virtual tlb_status sync_pops(Ctx* c) = 0;
 };
 
 // CUDA events bracketing the phases of a step when profiling.
@@ -66,7 +74,7 @@ struct Region {
 struct Layout {
   // lattice
   Region lo[2], rest[2];
-  Region rho, phi, psi, I, dsel, own, key, fib, ftot, mu, rb;
+  Region rho, phi, psi, jm, M, I, dsel, own, key, fib, ftot, mu, rb;
   // membranes
   Region X, E, ecap, ncap, cap_par, ds0, rprev, rnext, A0, G0i, inc_off, inc, adj, edges, ring_off, ring;
   Region en, vn, erel, eorg, ecst, xo, xr, skc, capr, ncpl, F, box;
@@ -87,6 +95,18 @@ struct HostMem {
 
 struct Ctx {
   tlb_params p;
+  // the tau = 1 collide applies: tau = tau_phi = tau_psi = 1 and the exact
+  // difference method (every post-collision population is an equilibrium)
+  bool t1_ok() const {
+    return p.tau == 1.0 && p.tau_phi == 1.0 && p.tau_psi == 1.0 && p.forcing == TLB_FORCE_EDM;
+  }
+  // moment storage (TLB_STATE_MOMENTS): the state is the moment buffer M,
+  // except after an initialisation or a write of populations, which the
+  // next step pulls as populations (state_in_pops); the population buffer
+  // is refreshed from M for readers when it is stale
+  bool moments() const { return p.state == TLB_STATE_MOMENTS; }
+  bool state_in_pops = true;
+  bool pops_stale = false;
   int Q = 0;
   int nx = 0, ny = 0, nz = 0;  // internal sizes (2D: nx, 1, ny)
   long long N = 0, P = 0;

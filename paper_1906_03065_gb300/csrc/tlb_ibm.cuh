@@ -57,6 +57,9 @@ struct IBArgs {
   Real* I;
   Real* dsel;
   const Real* psi;       // psi(t) (moment field)
+  const Real* M;         // moment storage: the stored moments the interpolation
+                         // rebuilds the streamed populations from (NULL: the
+                         // population buffers are read)
   Real* fib;             // [3][P]
   const Real* ftot;      // [3][P]
   int* bcnt;             // bricks: count, previous count, cursor, offset
@@ -1363,7 +1366,14 @@ __device__ __forceinline__ void interp_advect_body(const IBArgs<typename Prec<MO
     Real r = 0, j[3] = {0, 0, 0};
 #pragma unroll
     for (int i = 0; i < L::Q; ++i) {
-      Real fi = to_real(lo[nb.off(i, plane_f<L>(i), plane_f<L>(L::opp(i)), G.P32)]);
+      Real fi;
+      if (a.M) {
+        EqCell<L, Real> e;
+        e.load_f(a.M, G.P32, nb.src(i));
+        fi = e.f(nb.bounce(i) ? L::opp(i) : i);
+      } else {
+        fi = to_real(lo[nb.off(i, plane_f<L>(i), plane_f<L>(L::opp(i)), G.P32)]);
+      }
       r += fi;
       if (L::cx(i)) j[0] += L::cx(i) > 0 ? fi : -fi;
       if (L::cy(i)) j[1] += L::cy(i) > 0 ? fi : -fi;

@@ -8,6 +8,7 @@
 #include "tlb_ctx.h"
 #include "tlb_ibm.cuh"
 #include "tlb_lb.cuh"
+#include "tlb_measure.cuh"
 
 template <class L, int MODE>
 struct Impl : ImplBase {
@@ -37,6 +38,11 @@ struct Impl : ImplBase {
     a.rho = c->ptr<Real>(c->L.rho);
     a.phi = c->ptr<Real>(c->L.phi);
     a.psi = c->ptr<Real>(c->L.psi);
+    // rho - 1 and j for the tau = 1 collide (the moments write them only then)
+    a.jm = variant_t1(c->tile_variant) ? c->ptr<Real>(c->L.jm) : nullptr;
+    // moment storage: the collide stores the moments, the pull rebuilds from them
+    a.mst = c->moments() ? c->ptr<Real>(c->L.M) : nullptr;
+    a.msrc = a.mst;
     a.I = c->ptr<Real>(c->L.I);
     a.fib = c->ptr<Real>(c->L.fib);
     a.ftot = c->ptr<Real>(c->L.ftot);
@@ -106,6 +112,7 @@ struct Impl : ImplBase {
     a.I = c->ptr<Real>(c->L.I);
     a.dsel = c->ptr<Real>(c->L.dsel);
     a.psi = c->ptr<Real>(c->L.psi);
+    a.M = c->moments() ? c->ptr<Real>(c->L.M) : nullptr;
     a.fib = c->ptr<Real>(c->L.fib);
     a.ftot = c->ptr<Real>(c->L.ftot);
     a.bflag = c->ptr<unsigned char>(c->L.bflag);
@@ -250,6 +257,35 @@ struct Impl : ImplBase {
     c->t = 0;
     c->t_snap = 0;
     c->initialised = true;
+    c->state_in_pops = true;  // (moment storage: the first step pulls these populations)
+    c->pops_stale = false;
+    return TLB_OK;
+  }
+
+  tlb_status sync_pops(Ctx* c) override {
+    if (!c->moments() || c->state_in_pops || !c->pops_stale) return TLB_OK;
+    k_materialize<L, MODE><<<blocks(c->N, 256), 256, 0, c->stream>>>(
+        geo(c), c->ptr<Real>(c->L.M), c->ptr<Store>(c->L.lo[c->cur]), c->ptr<Rest>(c->L.rest[c->cur]));
+    TLB_LAUNCHED(c, "k_materialize");
+    c->pops_stale = false;
+    return TLB_OK;
+  }
+
+  // the moments of the streamed populations: pulled from the population
+  // buffer, or (moment storage) rebuilt from the stored moments
+  static tlb_status launch_moments(Ctx* c, const LBArgs<MODE>& la, cudaStream_t s) {
+    if (c->moments() && !c->state_in_pops) {
+      // tiles of 32 x 4 columns (2D: 64) walking 16 planes
+      constexpr int RX = L::DIM == 3 ? 32 : 64, RY = L::DIM == 3 ? 4 : 1;
+      LBArgs<MODE> lr = la;
+      lr.zc = 16;
+      const dim3 grid(blocks(c->nx, RX), blocks(c->ny, RY), blocks(c->nz, lr.zc));
+      k_moments_recon_tiled<L, MODE, RX, RY><<<grid, RX * RY, 0, s>>>(lr);
+      TLB_LAUNCHED(c, "k_moments_recon");
+    } else {
+      k_moments<L, MODE><<<blocks(c->N, 256), 256, 0, s>>>(la);
+      TLB_LAUNCHED(c, "k_moments");
+    }
     return TLB_OK;
   }
 
@@ -286,6 +322,8 @@ struct Impl : ImplBase {
     c->t = 0;
     c->t_snap = 0;
     c->initialised = true;
+    c->state_in_pops = true;
+    c->pops_stale = false;
     return TLB_OK;
   }
 
@@ -295,6 +333,7 @@ struct Impl : ImplBase {
 
   tlb_status residual_launch(Ctx* c) override {
     cudaStream_t s = c->stream;
+    if (tlb_status st = sync_pops(c); st != TLB_OK) return st;
     TLB_CUDA(cudaMemsetAsync(c->ptr<char>(c->L.res), 0, c->L.res.bytes, s));
     const unsigned nb = blocks(c->N, 256) + blocks(c->nn, 256);
     k_residual<L, MODE><<<nb, 256, 0, s>>>(geo(c), c->ptr<Store>(c->L.lo[c->cur]), c->ptr<Rest>(c->L.rest[c->cur]),
@@ -324,8 +363,11 @@ struct Impl : ImplBase {
   tlb_status autotune(Ctx* c, int* variant, int* zc) override {
     cudaStream_t s = c->stream;
     LBArgs<MODE> la = lbargs(c, c->cur);
-    k_moments<L, MODE><<<blocks(c->N, 256), 256, 0, s>>>(la);
-    TLB_LAUNCHED(c, "k_moments");
+    la.jm = c->ptr<Real>(c->L.jm);  // every variant's input, the tau = 1 forms' too
+    if (tlb_status st = launch_moments(c, la, s); st != TLB_OK) return st;
+    // moment storage: the timed collides store into the idle population
+    // buffer, not into the state
+    if (c->moments()) la.mst = c->ptr<Real>(c->L.lo[1 - c->cur]);
     cudaEvent_t e0, e1;
     TLB_CUDA(cudaEventCreate(&e0));
     TLB_CUDA(cudaEventCreate(&e1));
@@ -334,6 +376,7 @@ struct Impl : ImplBase {
     const std::vector<int> zcs = z_chunk_candidates(c->nz);
     for (int v = 0; v < COLLIDE_NVAR; ++v)
       for (const int zcv : zcs) {
+        if (variant_t1(v) ? !c->t1_ok() : c->moments()) continue;
         c->tile_variant = v;
         c->tiles_zc = zcv;
         la.zc = c->tiles_zc;
@@ -408,8 +451,7 @@ struct Impl : ImplBase {
         if ((st = ibm_bins(c, ia, c->side2)) != TLB_OK) return st;
         TLB_CUDA(cudaEventRecord(c->ev_bins, c->side2));
       }
-      k_moments<L, MODE><<<blocks(N, 256), 256, 0, s>>>(la);
-      TLB_LAUNCHED(c, "k_moments");
+      if ((st = launch_moments(c, la, s)) != TLB_OK) return st;
       if ((st = mark(c, 1)) != TLB_OK) return st;
       // the profile, coupling sums and spreading need psi(t) and the
       // position work: they follow the moments, then the whole lattice is
@@ -444,6 +486,10 @@ struct Impl : ImplBase {
       if ((st = collect(c)) != TLB_OK) return st;
       c->cur = 1 - c->cur;
       c->t += 1;
+      if (c->moments()) {  // the state is the stored moments from here on
+        c->state_in_pops = false;
+        c->pops_stale = true;
+      }
     }
     if (pipe && n > 0) TLB_CUDA(cudaStreamWaitEvent(s, c->ev_interp, 0));  // all of it on the caller's stream
     return TLB_OK;
@@ -455,6 +501,7 @@ struct Impl : ImplBase {
     double* rb = c->ptr<double>(c->L.rb);
     const size_t need = field == TLB_FIELD_U ? 3 * (size_t)N : (size_t)N;
     if (nvals < need) { set_error("read_field: buffer too small"); return TLB_ERR_ARG; }
+    if (tlb_status st = sync_pops(c); st != TLB_OK) return st;
     // the field is formed on the device, only its values cross to the host
     if (field == TLB_FIELD_I) {
       k_to_double<Real><<<blocks(N, 256), 256, 0, s>>>(c->ptr<Real>(c->L.I), N, rb);
@@ -485,6 +532,7 @@ struct Impl : ImplBase {
 
   tlb_status read_pops(Ctx* c, double* dst) override {
     cudaStream_t s = c->stream;
+    if (tlb_status st = sync_pops(c); st != TLB_OK) return st;
     const long long N = c->N, P = c->P;
     std::vector<Store> lo((size_t)(3 * L::Q - 2) * P);
     std::vector<Rest> rest((size_t)2 * P);
@@ -532,11 +580,60 @@ struct Impl : ImplBase {
     TLB_CUDA(cudaMemcpyAsync(c->ptr<Rest>(c->L.rest[c->cur]), rest.data(), rest.size() * sizeof(Rest), cudaMemcpyHostToDevice, s));
     TLB_CUDA(cudaStreamSynchronize(s));
     c->initialised = true;
+    c->state_in_pops = true;  // (moment storage: the next step pulls them)
+    c->pops_stale = false;
+    return TLB_OK;
+  }
+
+  // Contact angles (tlb_measure.cuh).  Scratch: phi in the read-back
+  // buffer; marker values, edge angles and the per-capsule results in the
+  // population buffer that the next step writes (idle between steps).
+  tlb_status contact_angle(Ctx* c, double* out) override {
+    cudaStream_t s = c->stream;
+    const long long N = c->N;
+    const int nedge = c->NV == 2 ? c->nn : c->nedge;
+    const size_t need = (size_t)(4 * c->nn + nedge + 4 * c->ncap) * sizeof(double) + (size_t)nedge * sizeof(int);
+    if (c->ncap == 0) return TLB_OK;
+    if (need > c->L.lo[1 - c->cur].bytes) { set_error("contact_angle: scratch too small"); return TLB_ERR_ARG; }
+    if (tlb_status st = sync_pops(c); st != TLB_OK) return st;
+    double* phi = c->ptr<double>(c->L.rb);
+    k_fields<L, MODE><<<blocks(N, 256), 256, 0, s>>>(geo(c), c->ptr<Store>(c->L.lo[c->cur]),
+                                                      c->ptr<Rest>(c->L.rest[c->cur]), TLB_FIELD_PHI, phi);
+    TLB_LAUNCHED(c, "k_fields");
+    double* sc = c->ptr<double>(c->L.lo[1 - c->cur]);
+    AngleArgs a;
+    a.G = geo(c);
+    a.dim = c->p.dim;
+    a.nn = c->nn;
+    a.NV = c->NV;
+    a.X = c->ptr<double>(c->L.X);
+    a.phi = phi;
+    a.E = c->ptr<int>(c->L.E);
+    a.inc_off = c->ptr<int>(c->L.inc_off);
+    a.inc = c->ptr<int>(c->L.inc);
+    a.rnext = c->ptr<int>(c->L.rnext);
+    a.rprev = c->ptr<int>(c->L.rprev);
+    a.edges = c->ptr<int>(c->L.edges);
+    a.ncap = c->ptr<int>(c->L.ncap);
+    a.nedge = nedge;
+    a.mk = sc;
+    a.ang = sc + 4 * c->nn;
+    double* res = a.ang + nedge;
+    a.ecapo = reinterpret_cast<int*>(res + 4 * c->ncap);
+    k_marker_phi<<<blocks(c->nn, 128), 128, 0, s>>>(a);
+    TLB_LAUNCHED(c, "k_marker_phi");
+    k_contact_edges<L><<<blocks(nedge, 128), 128, 0, s>>>(a);
+    TLB_LAUNCHED(c, "k_contact_edges");
+    k_contact_reduce<<<c->ncap, 256, 0, s>>>(a.ang, a.ecapo, nedge, res);
+    TLB_LAUNCHED(c, "k_contact_reduce");
+    TLB_CUDA(cudaMemcpyAsync(out, res, 4 * c->ncap * sizeof(double), cudaMemcpyDeviceToHost, s));
+    TLB_CUDA(cudaStreamSynchronize(s));
     return TLB_OK;
   }
 
   tlb_status diagnostics(Ctx* c, tlb_diag* out) override {
     cudaStream_t s = c->stream;
+    if (tlb_status st = sync_pops(c); st != TLB_OK) return st;
     Geo G = geo(c);
     double* part = c->ptr<double>(c->L.part);
     const int nb = 1024;

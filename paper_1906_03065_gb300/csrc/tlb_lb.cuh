@@ -16,9 +16,14 @@ struct LBArgs {
   const Rest* rest_src;
   Store* lo_dst;
   Rest* rest_dst;
-  Real* rho;
+  Real* rho;        // rho - 1 (the deviation keeps its low bits in FP32)
   Real* phi;
   Real* psi;
+  Real* jm;         // [3][P] j of the streamed populations, written by the
+                    // moments for the tau = 1 collide (NULL otherwise)
+  Real* mst;        // moment storage: [11][P] moments the tau = 1 collide
+                    // stores in place of the populations (NULL otherwise)
+  const Real* msrc; // moment storage: the moments the reconstructing pull reads
   const Real* I;
   const Real* fib;  // [3][P] immersed-boundary force density
   Real* ftot;       // [3][P] total force of the step (read by the interpolation)
@@ -32,8 +37,23 @@ struct LBArgs {
   unsigned* status;
 };
 
+// Asynchronous global -> shared copies of one element (cp.async, 4 or 8
+// bytes): the copy runs while the thread computes; cp_async_wait_all blocks
+// until every copy the thread issued has landed.
+__device__ __forceinline__ void cp_async_elem(float* dst, const float* src) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_elem(double* dst, const double* src) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+
 // ---------------------------------------------------------------- moments
-// rho, phi, psi at every cell from the streamed populations (eq. MomentsDFs).
+// rho - 1, phi, psi at every cell from the streamed populations (eq.
+// MomentsDFs), and j for the tau = 1 collide.
 template <class L, int MODE>
 __device__ __forceinline__ void moments_body(const LBArgs<MODE>& a, const Blk& blk) {
   using Real = typename Prec<MODE>::Real;
@@ -46,13 +66,151 @@ __device__ __forceinline__ void moments_body(const LBArgs<MODE>& a, const Blk& b
   Pull<L, MODE> p;
   p.load(a.lo_src, a.rest_src, G, x, y, z);
   CellMoments<Real> m = p.moments();
-  a.rho[n] = Real(1) + m.drho;
+  a.rho[n] = m.drho;
   a.phi[n] = m.phi;
   a.psi[n] = m.psi;
+  if (a.jm) {
+    a.jm[n] = m.j[0];
+    a.jm[G.P + n] = m.j[1];
+    a.jm[2 * G.P + n] = m.j[2];
+  }
 }
 template <class L, int MODE>
 __global__ void __launch_bounds__(256) k_moments(const __grid_constant__ LBArgs<MODE> a) {
   moments_body<L, MODE>(a, hw_blk());
+}
+
+// Moments of the streamed populations, each rebuilt from the stored moments
+// of the cell it streams from (across a wall: this cell's opposite
+// direction, halfway bounce-back); summed as the population pull sums.
+template <class L, int MODE>
+__device__ __forceinline__ void moments_recon_body(const LBArgs<MODE>& a, const Blk& blk) {
+  using Real = typename Prec<MODE>::Real;
+  const Geo G = a.G;
+  long long n = (long long)blk.x * blockDim.x + threadIdx.x;
+  if (n >= G.N) return;
+  const int x = (int)(n % G.nx), y = (int)((n / G.nx) % G.ny), z = (int)(n / ((long long)G.nx * G.ny));
+  const Nbr<L> nb(G, x, y, z);
+  Pull<L, MODE> p;
+#pragma unroll
+  for (int i = 0; i < L::Q; ++i) {
+    const int ii = nb.bounce(i) ? L::opp(i) : i;
+    EqCell<L, Real> e;
+    e.load(a.msrc, G.P32, nb.src(i));
+    p.f[i] = e.f(ii);
+    p.g[i] = e.o(0, ii);
+    p.h[i] = e.o(1, ii);
+  }
+  CellMoments<Real> m = p.moments();
+  a.rho[n] = m.drho;
+  a.phi[n] = m.phi;
+  a.psi[n] = m.psi;
+  a.jm[n] = m.j[0];
+  a.jm[G.P + n] = m.j[1];
+  a.jm[2 * G.P + n] = m.j[2];
+}
+template <class L, int MODE>
+__global__ void __launch_bounds__(256) k_moments_recon(const __grid_constant__ LBArgs<MODE> a) {
+  moments_recon_body<L, MODE>(a, hw_blk());
+}
+
+// The same pull as a plane sweep: a TX x TY tile of columns walks a chunk of
+// z planes; the stored moments of four planes (tile plus a halo of 1) sit in
+// a shared-memory ring filled by asynchronous copies one plane ahead, so
+// every stored moment is read once from memory and the 19 x 11 reads of a
+// cell's rebuild come from shared memory.  Same arithmetic and summation
+// order as moments_recon_body.
+template <class L, int MODE, int TX, int TY>
+__global__ void __launch_bounds__(TX* TY) k_moments_recon_tiled(const __grid_constant__ LBArgs<MODE> a) {
+  using Real = typename Prec<MODE>::Real;
+  constexpr bool D3 = L::DIM == 3;
+  constexpr int HX = TX + 2, HY = D3 ? TY + 2 : 1, CELLS = HX * HY, NT = TX * TY;
+  __shared__ Real sM[4][M_COUNT][CELLS];
+  const Geo G = a.G;
+  const int tx = threadIdx.x % TX, ty = threadIdx.x / TX, tid = threadIdx.x;
+  const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
+  const int z0 = blockIdx.z * a.zc;
+  const int z1 = min(z0 + a.zc, G.nz);
+  const int x = x0 + tx, y = y0 + ty;
+  const bool active = x < G.nx && y < G.ny;
+  auto wrapn = [](int v, int n) {
+    v %= n;
+    return v < 0 ? v + n : v;
+  };
+  // plane p of the ring (planes beyond a wall are never read: the pull
+  // bounces there, so they take the nearest plane)
+  auto issue_plane = [&](int p) {
+    const int slot = (p + 8) & 3;
+    const int pz = G.wall ? min(max(p, 0), G.nz - 1) : wrapn(p, G.nz);
+    for (int k = tid; k < CELLS; k += NT) {
+      const int hx = k % HX, hy = k / HX;
+      const int gx = wrapn(x0 - 1 + hx, G.nx);
+      const int gy = D3 ? wrapn(y0 - 1 + hy, G.ny) : 0;
+      const long long c = ((long long)pz * G.ny + gy) * G.nx + gx;
+#pragma unroll
+      for (int f = 0; f < M_COUNT; ++f) cp_async_elem(&sM[slot][f][k], a.msrc + (long long)f * G.P + c);
+    }
+    cp_async_commit();
+  };
+  for (int p = z0 - 1; p <= z0 + 1; ++p) issue_plane(p);
+  cp_async_wait_all();
+  __syncthreads();
+  for (int zz = z0; zz < z1; ++zz) {
+    // plane zz + 2 replaces plane zz - 2, which this iteration does not read
+    if (zz + 2 <= z1) issue_plane(zz + 2);
+    if (active) {
+      const bool wlo = G.wall && zz == 0, whi = G.wall && zz == G.nz - 1;
+      Pull<L, MODE> p;
+#pragma unroll
+      for (int i = 0; i < L::Q; ++i) {
+        const bool bounce = (L::cz(i) > 0 && wlo) || (L::cz(i) < 0 && whi);
+        const int ii = bounce ? L::opp(i) : i;
+        const int sz = bounce ? zz : zz - L::cz(i);
+        const int hx = bounce ? tx + 1 : tx + 1 - L::cx(i);
+        const int hy = D3 ? (bounce ? ty + 1 : ty + 1 - L::cy(i)) : 0;
+        EqCell<L, Real> e;
+        e.load(&sM[(sz + 8) & 3][0][0], CELLS, hy * HX + hx);
+        p.f[i] = e.f(ii);
+        p.g[i] = e.o(0, ii);
+        p.h[i] = e.o(1, ii);
+      }
+      const CellMoments<Real> m = p.moments();
+      const long long n = ((long long)zz * G.ny + y) * G.nx + x;
+      a.rho[n] = m.drho;
+      a.phi[n] = m.phi;
+      a.psi[n] = m.psi;
+      a.jm[n] = m.j[0];
+      a.jm[G.P + n] = m.j[1];
+      a.jm[2 * G.P + n] = m.j[2];
+    }
+    cp_async_wait_all();
+    __syncthreads();
+  }
+}
+
+// The populations a cell's stored moments stand for, written post-collision
+// into the population buffers (for the readers of the population state).
+template <class L, int MODE>
+__global__ void k_materialize(Geo G, const typename Prec<MODE>::Real* M, typename Prec<MODE>::Store* lo,
+                              typename Prec<MODE>::Rest* rest) {
+  using Real = typename Prec<MODE>::Real;
+  using Store = typename Prec<MODE>::Store;
+  using Rest = typename Prec<MODE>::Rest;
+  const long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= G.N) return;
+  EqCell<L, Real> e;
+  e.load(M, G.P32, (int)n);
+#pragma unroll
+  for (int i = 0; i < L::Q; ++i) {
+    lo[(long long)plane_f<L>(i) * G.P + n] = from_real<Store>(e.f(i));
+    if (i == 0) {
+      rest[n] = from_real<Rest>(e.o(0, 0));
+      rest[G.P + n] = from_real<Rest>(e.o(1, 0));
+    } else {
+      lo[(long long)plane_g<L>(i) * G.P + n] = from_real<Store>(e.o(0, i));
+      lo[(long long)plane_h<L>(i) * G.P + n] = from_real<Store>(e.o(1, i));
+    }
+  }
 }
 
 // Second-order polynomial of the equilibria: 3 c.u + 4.5 (c.u)^2 - 1.5 u^2.
@@ -63,14 +221,25 @@ __device__ __forceinline__ Real eq_poly(Real cu, Real uu) {
 
 // ------------------------------------------------- fused collide + stream
 // One block owns a TX x TY tile of (x, y) columns and sweeps a chunk of z
-// planes.  Shared memory holds a 5-plane ring of the moment fields (halo 2,
+// planes.  Shared memory holds a 5-plane ring of the moment fields rho - 1,
+// phi, psi (halo 2,
 // written by k_moments; halo reads are served by L2) and a 3-plane ring of
 // the chemical potentials (halo 1), so each cell's radius-2 dependency (mu
 // needs the Laplacian of the moments, the force needs the gradient of mu) is
 // served on chip.
+// Forms 5 and 6 are the collide at tau = tau_phi = tau_psi = 1 with the exact
+// difference method: there every post-collision population is an
+// equilibrium, f* = f^eq(rho, u + du), g* = g^eq(phi, mu_phi, v), h* =
+// h^eq(psi, mu_psi', v) (eq. LBE with tau = 1), so the collide reads the
+// moments rho - 1 and j that the moment pass wrote (summed in the same order
+// as the pull of the general forms) and pulls no population: it only stores
+// them.
+template <int FORM> constexpr bool form_t1() { return FORM == 5 || FORM == 6; }
+
 template <class L, int MODE, int TX, int TY, int FORM>
-__device__ __forceinline__ void collide_body(const LBArgs<MODE>& a, const Blk& blk) {
+__device__ __forceinline__ void collide_gen_body(const LBArgs<MODE>& a, const Blk& blk) {
   constexpr bool PF = FORM == 1;  // the next population set prefetched
+  constexpr bool T1 = form_t1<FORM>();
   using Real = typename Prec<MODE>::Real;
   using Store = typename Prec<MODE>::Store;
   using Rest = typename Prec<MODE>::Rest;
@@ -166,7 +335,8 @@ __device__ __forceinline__ void collide_body(const LBArgs<MODE>& a, const Blk& b
     const int n = nb.self;
     const int sm5 = (zz + 10) % 5;
     const int mc = (ty + HY) * MX + tx + 2;
-    const Real rho = smom[sm5][0][mc], phi = smom[sm5][1][mc], psi = smom[sm5][2][mc];
+    const Real drho_c = smom[sm5][0][mc], phi = smom[sm5][1][mc], psi = smom[sm5][2][mc];
+    const Real rho = Real(1) + drho_c;
     // gradients of the potentials (radius 1, isotropic stencil)
     Real gm[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
     const int ux = tx + 1, uy = ty + (D3 ? 1 : 0);
@@ -210,21 +380,29 @@ __device__ __forceinline__ void collide_body(const LBArgs<MODE>& a, const Blk& b
       }
     };
     // f: pull, first moment, BGK + exact difference method (eq. LBE) for f_i - w_i
-    Real fv[Q];
-#pragma unroll
-    for (int i = 0; i < Q; ++i) {
-      fv[i] = to_real(__ldg(a.lo_src + nb.off(i, plane_f<L>(i), plane_f<L>(L::opp(i)), G.P32)));
-    }
-    // with PF the next set's loads are in flight while this one is computed
-    Real nextv[Q];
-    if constexpr (PF) load_set(0, nextv);
+    Real fv[T1 ? 1 : Q];
     Real drho = 0, jx = 0, jy = 0, jz = 0;
+    // with PF the next set's loads are in flight while this one is computed
+    Real nextv[PF ? Q : 1];
+    if constexpr (T1) {
+      drho = drho_c;
+      jx = a.jm[n];
+      jy = a.jm[G.P32 + n];
+      jz = a.jm[2 * G.P32 + n];
+    } else {
 #pragma unroll
-    for (int i = 0; i < Q; ++i) {
-      drho += fv[i];
-      if (L::cx(i)) jx += L::cx(i) > 0 ? fv[i] : -fv[i];
-      if (L::cy(i)) jy += L::cy(i) > 0 ? fv[i] : -fv[i];
-      if (L::cz(i)) jz += L::cz(i) > 0 ? fv[i] : -fv[i];
+      for (int i = 0; i < Q; ++i) {
+        fv[i] = to_real(__ldg(a.lo_src + nb.off(i, plane_f<L>(i), plane_f<L>(L::opp(i)), G.P32)));
+      }
+      if constexpr (PF) load_set(0, nextv);
+#pragma unroll
+      for (int i = 1; i < Q; ++i) {  // in the order of Pull::moments (rest last)
+        drho += fv[i];
+        if (L::cx(i)) jx += L::cx(i) > 0 ? fv[i] : -fv[i];
+        if (L::cy(i)) jy += L::cy(i) > 0 ? fv[i] : -fv[i];
+        if (L::cz(i)) jz += L::cz(i) > 0 ? fv[i] : -fv[i];
+      }
+      drho += fv[0];
     }
     const Real irho = Real(1) / rho;
     const Real j[3] = {jx, jy, jz};
@@ -240,7 +418,42 @@ __device__ __forceinline__ void collide_body(const LBArgs<MODE>& a, const Blk& b
     const Real vv = v[0] * v[0] + v[1] * v[1] + v[2] * v[2];
     const Real dus = du[0] * us[0] + du[1] * us[1] + du[2] * us[2];
     const Real om = a.om;
-    if (a.forcing == TLB_FORCE_GUO) {
+    if constexpr (T1) {
+      if (a.mst) {
+        // moment storage: the 11 values whose equilibria are this cell's
+        // post-collision populations (see EqCell)
+        Real* M = a.mst;
+        M[M_DRHO * G.P32 + n] = drho;
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+          M[(M_W + d) * G.P32 + n] = radd(u[d], du[d]);
+          M[(M_V + d) * G.P32 + n] = v[d];
+        }
+        M[M_PHI * G.P32 + n] = phi;
+        M[M_GMP * G.P32 + n] = a.gphi * mup;
+        M[M_PSI * G.P32 + n] = psi;
+        M[M_GMS * G.P32 + n] = a.gpsi * mus;
+        if (ib)
+#pragma unroll
+          for (int d = 0; d < 3; ++d) a.ftot[d * G.P32 + n] = F[d];
+        if (!(rho == rho) || !(phi == phi) || !(psi == psi)) atomicOr(a.status, (unsigned)ST_NAN);
+        return;
+      }
+      // f* = f^eq(rho, u + du), written as w [drho + rho p(u)] + w rho dP with
+      // the explicitly rounded operations (see rmul)
+#pragma unroll
+      for (int i = 0; i < Q; ++i) {
+        const Real w = Real(L::w(i));
+        const Real wrho = rmul(rho, w);
+        const Real cu = L::cx(i) * u[0] + L::cy(i) * u[1] + L::cz(i) * u[2];
+        const Real cdu = L::cx(i) * du[0] + L::cy(i) * du[1] + L::cz(i) * du[2];
+        const Real cus = L::cx(i) * us[0] + L::cy(i) * us[1] + L::cz(i) * us[2];
+        const Real pu = rfma(rmul(Real(4.5), cu), cu, rfma(Real(3), cu, rmul(Real(-1.5), uu)));
+        const Real dP = rfma(rmul(Real(4.5), cdu), cus, rfma(Real(3), cdu, rmul(Real(-1.5), dus)));
+        const Real fn = rfma(wrho, dP, rmul(w, rfma(rho, pu, drho)));
+        a.lo_dst[plane_f<L>(i) * G.P32 + n] = from_real<Store>(fn);
+      }
+    } else if (a.forcing == TLB_FORCE_GUO) {
       // Guo forcing: BGK towards f^eq(rho, v) plus (1 - om/2) w_i [3 (c_i - v) + 9 (c_i.v) c_i] . F
       const Real vF = v[0] * F[0] + v[1] * F[1] + v[2] * F[2];
       const Real sc = Real(1) - Real(0.5) * om;
@@ -273,25 +486,43 @@ __device__ __forceinline__ void collide_body(const LBArgs<MODE>& a, const Blk& b
       const Real om_s = set == 0 ? a.om_phi : a.om_psi;
       const Real Gm = set == 0 ? a.gphi * mup : a.gpsi * mus;
       const Real ord = set == 0 ? phi : psi;
-      Real gv[Q];
-      if constexpr (PF) {
+      Real gv[T1 ? 1 : Q];
+      if constexpr (T1) {
+        // (om_s = 1: the post-collision set is the equilibrium)
+      } else if constexpr (PF) {
 #pragma unroll
         for (int i = 0; i < Q; ++i) gv[i] = nextv[i];
         if (set == 0) load_set(1, nextv);
       } else {
         load_set(set, gv);
       }
+      if constexpr (T1) {
+        // g* = g^eq(ord, mu, v) (om_s = 1), explicitly rounded (see rmul)
+        const Real g3 = rmul(Real(3), Gm);
 #pragma unroll
-      for (int i = 1; i < Q; ++i) {
-        const Real w = Real(L::w(i));
-        const Real cv = L::cx(i) * v[0] + L::cy(i) * v[1] + L::cz(i) * v[2];
-        const Real pv = Real(3) * cv + Real(4.5) * cv * cv - Real(1.5) * vv;
-        const Real ge = w * (Real(3) * Gm + ord * pv);
-        const int pp = set == 0 ? plane_g<L>(i) : plane_h<L>(i);
-        a.lo_dst[pp * G.P32 + n] = from_real<Store>((Real(1) - om_s) * gv[i] + om_s * ge);
+        for (int i = 1; i < Q; ++i) {
+          const Real w = Real(L::w(i));
+          const Real cv = L::cx(i) * v[0] + L::cy(i) * v[1] + L::cz(i) * v[2];
+          const Real pv = rfma(rmul(Real(4.5), cv), cv, rfma(Real(3), cv, rmul(Real(-1.5), vv)));
+          const int pp = set == 0 ? plane_g<L>(i) : plane_h<L>(i);
+          a.lo_dst[pp * G.P32 + n] = from_real<Store>(rmul(w, rfma(ord, pv, g3)));
+        }
+        // ord - 3 Gm (1 - w0) - 1.5 w0 ord v^2
+        const Real ge0 = radd(rfma(g3, w0 - Real(1), ord), rmul(rmul(Real(-1.5) * w0, ord), vv));
+        a.rest_dst[(set == 0 ? 0 : G.P32) + n] = from_real<Rest>(ge0);
+      } else {
+#pragma unroll
+        for (int i = 1; i < Q; ++i) {
+          const Real w = Real(L::w(i));
+          const Real cv = L::cx(i) * v[0] + L::cy(i) * v[1] + L::cz(i) * v[2];
+          const Real pv = Real(3) * cv + Real(4.5) * cv * cv - Real(1.5) * vv;
+          const Real ge = w * (Real(3) * Gm + ord * pv);
+          const int pp = set == 0 ? plane_g<L>(i) : plane_h<L>(i);
+          a.lo_dst[pp * G.P32 + n] = from_real<Store>((Real(1) - om_s) * gv[i] + om_s * ge);
+        }
+        const Real ge0 = ord - Real(3) * Gm * (Real(1) - w0) - Real(1.5) * w0 * ord * vv;
+        a.rest_dst[(set == 0 ? 0 : G.P32) + n] = from_real<Rest>((Real(1) - om_s) * gv[0] + om_s * ge0);
       }
-      const Real ge0 = ord - Real(3) * Gm * (Real(1) - w0) - Real(1.5) * w0 * ord * vv;
-      a.rest_dst[(set == 0 ? 0 : G.P32) + n] = from_real<Rest>((Real(1) - om_s) * gv[0] + om_s * ge0);
     }
     if (ib)
 #pragma unroll
@@ -316,11 +547,255 @@ __device__ __forceinline__ void collide_body(const LBArgs<MODE>& a, const Blk& b
     __syncthreads();
   }
 }
-// Forms of the collide: threads per SM the register budget is set for
-// (0: 640; 1: 512 with the next set prefetched; 2: 768; 3: 1024; 4: 896).
-template <int FORM> constexpr int collide_threads() {
-  return FORM == 1 ? 512 : (FORM == 2 ? 768 : (FORM == 3 ? 1024 : (FORM == 4 ? 896 : 640)));
+
+// The collide of forms 5 and 6 (tau = tau_phi = tau_psi = 1, exact
+// difference method): every post-collision population is an equilibrium of
+// the cell's moments, so nothing is pulled; the kernel is a plane sweep over
+// the moment fields that stores 3Q populations per cell (or, with moment
+// storage, the 11 moments).  Per plane: the ring plane three ahead (rho - 1,
+// phi, psi and I, tile plus a halo of 2) is copied asynchronously into the
+// 5-plane ring while the potentials of the next plane and the collision of
+// this one are computed.  The equilibria of opposite velocities share their
+// even part, and g and h share the velocity polynomial; all rounded
+// explicitly (see rmul), so every kernel it is inlined into computes the
+// same values.
+template <class L, int MODE, int TX, int TY, int FORM>
+__device__ __forceinline__ void collide_t1_body(const LBArgs<MODE>& a, const Blk& blk) {
+  using Real = typename Prec<MODE>::Real;
+  using Store = typename Prec<MODE>::Store;
+  using Rest = typename Prec<MODE>::Rest;
+  constexpr int Q = L::Q;
+  constexpr bool D3 = L::DIM == 3;
+  constexpr int HY = D3 ? 2 : 0;
+  constexpr int MX = TX + 4, MY = TY + 2 * HY;
+  constexpr int UX = TX + 2, UY = TY + (D3 ? 2 : 0);
+  constexpr int NT = TX * TY;
+  __shared__ Real smom[5][4][MY * MX];  // rho - 1, phi, psi, I
+  __shared__ Real smu[3][3][UY * UX];
+
+  const Geo G = a.G;
+  const int tx = threadIdx.x % TX, ty = threadIdx.x / TX, tid = threadIdx.x;
+  const int x0 = blk.x * TX, y0 = blk.y * TY;
+  const int z0 = blk.z * a.zc;
+  const int z1 = min(z0 + a.zc, G.nz);
+  const int x = x0 + tx, y = y0 + ty;
+  const bool active = x < G.nx && y < G.ny;
+
+  auto modn = [](int v, int n) {
+    if (v < 0) v += n;
+    if (v >= n) v -= n;
+    if (v < 0 || v >= n) {
+      v %= n;
+      if (v < 0) v += n;
+    }
+    return v;
+  };
+  auto plane_src = [&](int p) { return G.wall ? min(max(p, 0), G.nz - 1) : modn(p, G.nz); };
+
+  // asynchronous copy of ring plane p (a wall's ghost planes mirror the
+  // plane next to the wall)
+  auto issue_plane = [&](int p) {
+    const int slot = (p + 10) % 5;
+    const long long zp = (long long)plane_src(p) * G.ny;
+    for (int k = tid; k < MX * MY; k += NT) {
+      const int hx = k % MX, hy = k / MX;
+      const int gx = modn(x0 - 2 + hx, G.nx);
+      const int gy = D3 ? modn(y0 - HY + hy, G.ny) : 0;
+      const long long c = (zp + gy) * G.nx + gx;
+      cp_async_elem(&smom[slot][0][k], a.rho + c);
+      cp_async_elem(&smom[slot][1][k], a.phi + c);
+      cp_async_elem(&smom[slot][2][k], a.psi + c);
+      cp_async_elem(&smom[slot][3][k], a.I + c);
+    }
+    cp_async_commit();
+  };
+
+  // chemical potentials of plane p on the tile plus a halo of 1
+  auto compute_mu = [&](int p) {
+    const int slot = (p + 9) % 3;
+    if (G.wall && (p < 0 || p >= G.nz)) {  // mirror ghost: mu(-1) = mu(0), mu(nz) = mu(nz-1)
+      const int src = (min(max(p, 0), G.nz - 1) + 9) % 3;
+      for (int k = tid; k < UX * UY; k += NT)
+        for (int q = 0; q < 3; ++q) smu[slot][q][k] = smu[src][q][k];
+      return;
+    }
+    const int sc = (p + 10) % 5;
+    for (int k = tid; k < UX * UY; k += NT) {
+      const int ux = k % UX, uy = k / UX;
+      const int hx = ux + 1, hy = uy + (D3 ? 1 : 0);
+      const int cidx = hy * MX + hx;
+      Real lap[3] = {0, 0, 0};
+      const Real cen[3] = {smom[sc][0][cidx], smom[sc][1][cidx], smom[sc][2][cidx]};
+#pragma unroll
+      for (int i = 1; i < Q; ++i) {
+        const int s = (p + L::cz(i) + 10) % 5;
+        const int nb = (hy + L::cy(i)) * MX + hx + L::cx(i);
+        const Real w = Real(L::w(i));
+#pragma unroll
+        for (int q = 0; q < 3; ++q) lap[q] += w * (smom[s][q][nb] - cen[q]);
+      }
+#pragma unroll
+      for (int q = 0; q < 3; ++q) lap[q] *= Real(6);  // 2/cs^2
+      Real mr, mp, ms;
+      chem_potentials<Real>(a.fe, cen[0], cen[1], cen[2], lap[0], lap[1], lap[2], smom[sc][3][cidx], mr, mp, ms);
+      smu[slot][0][k] = mr;
+      smu[slot][1][k] = mp;
+      smu[slot][2][k] = ms;
+    }
+  };
+
+  auto collide = [&](int zz) {
+    if (!active) return;
+    const int n = (zz * G.ny + y) * G.nx + x;
+    // the cell's momentum first: its loads run under the stencil below
+    const Real j[3] = {a.jm[n], a.jm[G.P32 + n], a.jm[2 * G.P32 + n]};
+    const bool ib = a.bflag[((zz >> 2) * a.nby + (y >> 2)) * a.nbx + (x >> 2)] != 0;
+    const int sm5 = (zz + 10) % 5;
+    const int mc = (ty + HY) * MX + tx + 2;
+    const Real drho = smom[sm5][0][mc], phi = smom[sm5][1][mc], psi = smom[sm5][2][mc];
+    const Real rho = Real(1) + drho;
+    // gradients of the potentials (radius 1, isotropic stencil)
+    Real gm[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+    const int ux = tx + 1, uy = ty + (D3 ? 1 : 0);
+#pragma unroll
+    for (int i = 1; i < Q; ++i) {
+      const int s = (zz + L::cz(i) + 9) % 3;
+      const int nbi = (uy + L::cy(i)) * UX + ux + L::cx(i);
+      const Real w = Real(L::w(i));
+#pragma unroll
+      for (int q = 0; q < 3; ++q) {
+        const Real v = w * smu[s][q][nbi];
+        if (L::cx(i)) gm[q][0] += L::cx(i) > 0 ? v : -v;
+        if (L::cy(i)) gm[q][1] += L::cy(i) > 0 ? v : -v;
+        if (L::cz(i)) gm[q][2] += L::cz(i) > 0 ? v : -v;
+      }
+    }
+    const int sc = (zz + 9) % 3;
+    const int cc = uy * UX + ux;
+    const Real mup = smu[sc][1][cc], mus = smu[sc][2][cc];
+    Real F[3];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      F[d] = -Real(3) * (rho * gm[0][d] + phi * gm[1][d] + psi * gm[2][d]);
+      if (ib) F[d] += a.fib[d * G.P32 + n];
+    }
+    if (!D3) F[1] = 0;
+    const Real irho = Real(1) / rho;
+    Real u[3], du[3], v[3], us[3];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      u[d] = j[d] * irho;
+      du[d] = F[d] * irho;
+      v[d] = u[d] + Real(0.5) * du[d];
+      us[d] = u[d] + u[d] + du[d];  // u + (u + du)
+    }
+    const Real uu = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+    const Real vv = v[0] * v[0] + v[1] * v[1] + v[2] * v[2];
+    const Real dus = du[0] * us[0] + du[1] * us[1] + du[2] * us[2];
+    const Real gmp = a.gphi * mup, gms = a.gpsi * mus;
+    if (a.mst) {
+      // moment storage: the 11 values whose equilibria are this cell's
+      // post-collision populations (see EqCell)
+      Real* M = a.mst;
+      M[M_DRHO * G.P32 + n] = drho;
+#pragma unroll
+      for (int d = 0; d < 3; ++d) {
+        M[(M_W + d) * G.P32 + n] = radd(u[d], du[d]);
+        M[(M_V + d) * G.P32 + n] = v[d];
+      }
+      M[M_PHI * G.P32 + n] = phi;
+      M[M_GMP * G.P32 + n] = gmp;
+      M[M_PSI * G.P32 + n] = psi;
+      M[M_GMS * G.P32 + n] = gms;
+    } else {
+      // f* = f^eq(rho, u) + w rho dP: w [drho + rho p(u)] + w rho dP; for c and
+      // -c, p = A +- 3 c.u and dP = B +- 3 c.du with the shared even parts
+      const Real mu15 = rmul(Real(-1.5), uu), md15 = rmul(Real(-1.5), dus);
+      {
+        const Real w0 = Real(L::w(0));
+        a.lo_dst[plane_f<L>(0) * G.P32 + n] = from_real<Store>(rfma(rmul(rho, w0), md15, rmul(w0, rfma(rho, mu15, drho))));
+      }
+#pragma unroll
+      for (int i = 1; i < Q; ++i) {
+        if (L::opp(i) < i) continue;
+        const int o = L::opp(i);
+        const Real w = Real(L::w(i));
+        const Real wrho = rmul(rho, w);
+        const Real cu = L::cx(i) * u[0] + L::cy(i) * u[1] + L::cz(i) * u[2];
+        const Real cdu = L::cx(i) * du[0] + L::cy(i) * du[1] + L::cz(i) * du[2];
+        const Real cus = L::cx(i) * us[0] + L::cy(i) * us[1] + L::cz(i) * us[2];
+        const Real A = rfma(rmul(Real(4.5), cu), cu, mu15);
+        const Real B = rfma(rmul(Real(4.5), cdu), cus, md15);
+        const Real fp = rfma(wrho, rfma(Real(3), cdu, B), rmul(w, rfma(rho, rfma(Real(3), cu, A), drho)));
+        const Real fm = rfma(wrho, rfma(Real(-3), cdu, B), rmul(w, rfma(rho, rfma(Real(-3), cu, A), drho)));
+        a.lo_dst[plane_f<L>(i) * G.P32 + n] = from_real<Store>(fp);
+        a.lo_dst[plane_f<L>(o) * G.P32 + n] = from_real<Store>(fm);
+      }
+      // g* = g^eq(phi, mu_phi, v), h* = h^eq(psi, mu_psi', v): one velocity
+      // polynomial per pair of opposite velocities serves both
+      const Real g3 = rmul(Real(3), gmp), h3 = rmul(Real(3), gms);
+      const Real mv15 = rmul(Real(-1.5), vv);
+#pragma unroll
+      for (int i = 1; i < Q; ++i) {
+        if (L::opp(i) < i) continue;
+        const int o = L::opp(i);
+        const Real w = Real(L::w(i));
+        const Real cv = L::cx(i) * v[0] + L::cy(i) * v[1] + L::cz(i) * v[2];
+        const Real C = rfma(rmul(Real(4.5), cv), cv, mv15);
+        const Real pp = rfma(Real(3), cv, C), pm = rfma(Real(-3), cv, C);
+        a.lo_dst[plane_g<L>(i) * G.P32 + n] = from_real<Store>(rmul(w, rfma(phi, pp, g3)));
+        a.lo_dst[plane_g<L>(o) * G.P32 + n] = from_real<Store>(rmul(w, rfma(phi, pm, g3)));
+        a.lo_dst[plane_h<L>(i) * G.P32 + n] = from_real<Store>(rmul(w, rfma(psi, pp, h3)));
+        a.lo_dst[plane_h<L>(o) * G.P32 + n] = from_real<Store>(rmul(w, rfma(psi, pm, h3)));
+      }
+      // rest populations close the zeroth moments: ord - 3 Gm (1 - w0) - 1.5 w0 ord v^2
+      const Real w0 = Real(L::w(0));
+      a.rest_dst[n] = from_real<Rest>(radd(rfma(g3, w0 - Real(1), phi), rmul(rmul(Real(-1.5) * w0, phi), vv)));
+      a.rest_dst[G.P32 + n] = from_real<Rest>(radd(rfma(h3, w0 - Real(1), psi), rmul(rmul(Real(-1.5) * w0, psi), vv)));
+    }
+    if (ib)
+#pragma unroll
+      for (int d = 0; d < 3; ++d) a.ftot[d * G.P32 + n] = F[d];
+    if (!(rho == rho) || !(phi == phi) || !(psi == psi)) atomicOr(a.status, (unsigned)ST_NAN);
+  };
+
+  // prologue: ring planes z0-2 .. z0+2, potentials z0 then z0-1 (a wall
+  // ghost copies its neighbour, so the real plane comes first)
+  for (int p = z0 - 2; p <= z0 + 2; ++p) issue_plane(p);
+  cp_async_wait_all();
+  __syncthreads();
+  compute_mu(z0);
+  __syncthreads();
+  compute_mu(z0 - 1);
+  __syncthreads();
+  for (int zz = z0; zz < z1; ++zz) {
+    // plane zz + 3 replaces plane zz - 2, which no step of this iteration reads
+    if (zz + 3 <= z1 + 1) issue_plane(zz + 3);
+    compute_mu(zz + 1);
+    __syncthreads();
+    collide(zz);
+    cp_async_wait_all();
+    __syncthreads();
+  }
 }
+
+// The collide of a form: the tau = 1 body for forms 5 and 6, else the
+// general one.
+template <class L, int MODE, int TX, int TY, int FORM>
+__device__ __forceinline__ void collide_body(const LBArgs<MODE>& a, const Blk& blk) {
+  if constexpr (form_t1<FORM>())
+    collide_t1_body<L, MODE, TX, TY, FORM>(a, blk);
+  else
+    collide_gen_body<L, MODE, TX, TY, FORM>(a, blk);
+}
+// Forms of the collide: threads per SM the register budget is set for
+// (0: 640; 1: 512 with the next set prefetched; 2: 768; 3: 1024; 4: 896;
+// the tau = 1 collide at 5: 768 and 6: 1024).
+template <int FORM> constexpr int collide_threads() {
+  return FORM == 1 ? 512
+                   : (FORM == 2 || FORM == 5 ? 768 : (FORM == 3 || FORM == 6 ? 1024 : (FORM == 4 ? 896 : 640)));
+}
+
 
 template <class L, int MODE, int TX, int TY, int FORM>
 __global__ void __launch_bounds__(TX* TY, collide_threads<FORM>() / (TX * TY))
@@ -330,7 +805,8 @@ __global__ void __launch_bounds__(TX* TY, collide_threads<FORM>() / (TX * TY))
 
 // Calls fn(tile x, tile y, form) with the variant's compile-time values
 // (3D tiles 32x4, 32x8, 64x4; 2D rows of 32, 64, 128; variant 12 is the
-// smallest tile in form 4).
+// smallest tile in form 4; variants 13-18 the three tiles in the tau = 1
+// forms 5 and 6).
 template <int V> using CIdx = std::integral_constant<int, V>;
 template <class L, class Fn>
 __host__ tlb_status collide_variant(int v, Fn&& fn) {
@@ -349,12 +825,19 @@ __host__ tlb_status collide_variant(int v, Fn&& fn) {
     case 10: return fn(CIdx<X1>{}, CIdx<Y1>{}, CIdx<3>{});
     case 11: return fn(CIdx<X2>{}, CIdx<Y0>{}, CIdx<3>{});
     case 12: return fn(CIdx<32>{}, CIdx<Y0>{}, CIdx<4>{});  // (the larger tiles at 896 repeat 768)
+    case 13: return fn(CIdx<32>{}, CIdx<Y0>{}, CIdx<5>{});
+    case 14: return fn(CIdx<X1>{}, CIdx<Y1>{}, CIdx<5>{});
+    case 15: return fn(CIdx<X2>{}, CIdx<Y0>{}, CIdx<5>{});
+    case 16: return fn(CIdx<32>{}, CIdx<Y0>{}, CIdx<6>{});
+    case 17: return fn(CIdx<X1>{}, CIdx<Y1>{}, CIdx<6>{});
+    case 18: return fn(CIdx<X2>{}, CIdx<Y0>{}, CIdx<6>{});
     default: return fn(CIdx<32>{}, CIdx<Y0>{}, CIdx<0>{});
   }
 }
 
 // ------------------------------------------------------------- init & I/O
-// Chemical potentials from fields in global memory (used at initialisation).
+// Chemical potentials from fields in global memory (used at initialisation);
+// rho holds rho - 1.
 template <class L, int MODE>
 __global__ void k_mu_global(Geo G, FEParams<typename Prec<MODE>::Real> fe, const typename Prec<MODE>::Real* rho,
                             const typename Prec<MODE>::Real* phi, const typename Prec<MODE>::Real* psi,
@@ -379,7 +862,8 @@ __global__ void k_mu_global(Geo G, FEParams<typename Prec<MODE>::Real> fe, const
   mu[2 * G.P + n] = ms;
 }
 
-// Equilibrium populations (eq. EDF) of the fields, stored post-collision:
+// Equilibrium populations (eq. EDF) of the fields (rho holds rho - 1),
+// stored post-collision:
 // the value of direction i at cell y is the equilibrium f_i at y + c_i (or,
 // across a wall, f_{opp(i)} at y), which the next pull brings back to place.
 template <class L, int MODE>
@@ -404,13 +888,14 @@ __global__ void k_init_eq(Geo G, const typename Prec<MODE>::Real* rho, const typ
     } else {
       src = ((long long)wrapc(tz, G.nz) * G.ny + wrapc(y + L::cy(i), G.ny)) * G.nx + wrapc(x + L::cx(i), G.nx);
     }
-    Real r = rho[src], p = phi[src], s = psi[src];
+    Real dr = rho[src], p = phi[src], s = psi[src];
+    Real r = Real(1) + dr;
     Real uv[3] = {u[src], u[G.P + src], u[2 * G.P + src]};
     Real uu = uv[0] * uv[0] + uv[1] * uv[1] + uv[2] * uv[2];
     Real cu = L::cx(ii) * uv[0] + L::cy(ii) * uv[1] + L::cz(ii) * uv[2];
     Real w = Real(L::w(ii)), w0 = Real(L::w(0));
     Real pv = eq_poly(cu, uu);
-    lo[(long long)plane_f<L>(i) * G.P + n] = from_real<Store>(w * ((r - Real(1)) + r * pv));
+    lo[(long long)plane_f<L>(i) * G.P + n] = from_real<Store>(w * (dr + r * pv));
     Real mp = mu[G.P + src], ms = mu[2 * G.P + src];
     if (ii == 0) {
       // rest populations are stored in their own planes (direction 0 maps to itself)
@@ -432,8 +917,8 @@ __global__ void k_to_double(const Real* src, long long n, double* dst) {
 }
 
 // Initial fields from the caller's compositions C = [3][N] (FP64 sums, then
-// the working precision): rho = C1 + C2 + C3, phi = C1 - C2, psi = C3; or,
-// without C, the default state: rho = 1, psi = I, phi = (1 - I)(2 s - 1)
+// the working precision): rho - 1 = C1 + C2 + C3 - 1, phi = C1 - C2, psi =
+// C3; or, without C, the default state: rho = 1, psi = I, phi = (1 - I)(2 s - 1)
 // with the flat interface s(z) = (1 + tanh((z - z0)/(2 alpha)))/2 (s = 0
 // when z0 < 0).  The velocity ([3][N], or the uniform u0) goes to uf, 2D
 // fields internally as (x, 0, y).
@@ -445,7 +930,7 @@ __global__ void k_init_fields(Geo G, int dim, const double* C, const double* u, 
   long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (n >= N) return;
   if (C) {
-    rho[n] = (Real)(C[n] + C[N + n] + C[2 * N + n]);
+    rho[n] = (Real)(C[n] + C[N + n] + C[2 * N + n] - 1.0);
     phi[n] = (Real)(C[n] - C[N + n]);
     psi[n] = (Real)C[2 * N + n];
   } else {
@@ -453,7 +938,7 @@ __global__ void k_init_fields(Geo G, int dim, const double* C, const double* u, 
     double sv = 0.5 * (1.0 + tanh((z - z0) / (2.0 * alpha)));
     if (z0 < 0) sv = 0.0;
     const double ps = (double)I[n];
-    rho[n] = (Real)1.0;
+    rho[n] = (Real)0.0;
     phi[n] = (Real)((1.0 - ps) * (2.0 * sv - 1.0));
     psi[n] = (Real)ps;
   }

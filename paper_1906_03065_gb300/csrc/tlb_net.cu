@@ -763,7 +763,7 @@ __global__ void k_ws_sums2(const float* __restrict__ phi, const float* __restric
     for (int q = 0; q < 2; ++q) part[q * gridDim.x + blockIdx.x] = sm[q][0];
 }
 
-// Fields of the warm start: rho = 1, psi = I + cpsi, phi = (1 - psi)(s0 + y0
+// Fields of the warm start: rho = 1 (the array holds rho - 1), psi = I + cpsi, phi = (1 - psi)(s0 + y0
 // + cphi) with cphi = (sum phi0 - tot2[1]) / tot2[0] restoring the phi total.
 __global__ void k_ws_fields(float* __restrict__ rho, float* __restrict__ phi, float* __restrict__ psi,
                             const float* __restrict__ I, const float* __restrict__ y, long long V,
@@ -774,7 +774,7 @@ __global__ void k_ws_fields(float* __restrict__ rho, float* __restrict__ phi, fl
   const double cphi = (tot[0] - tot2[1]) / tot2[0];
   const double ps = (double)I[v] + cpsi;
   const double s = s0_of(phi[v], psi[v]) + y[v * YC] + cphi;
-  rho[v] = 1.f;
+  rho[v] = 0.f;
   phi[v] = (float)((1.0 - ps) * s);
   psi[v] = (float)ps;
 }

@@ -20,22 +20,28 @@
 #define TLB_STATIC_DOUBLES (3 * TLB_STATIC_BLOCKS + 4 + 2 * TLB_STATIC_MAX_CAPS)
 static __device__ __align__(256) double g_diag_scratch[TLB_STATIC_DOUBLES];
 
-// Device address of g_diag_scratch, looked up once per device with that
-// device current (the host-side symbol is not a device address).
+// Device address of g_diag_scratch on the device that holds the context's
+// arena, looked up once per device with that device current (the host-side
+// symbol is not a device address); the caller's current device is restored.
 static std::mutex g_scratch_mu;
 static double* g_scratch_addr[64] = {nullptr};
 
-static tlb_status scratch_address(double** out) {
-  int dev = 0;
-  TLB_CUDA(cudaGetDevice(&dev));
+static tlb_status scratch_address(const Ctx* c, double** out) {
+  cudaPointerAttributes at;
+  TLB_CUDA(cudaPointerGetAttributes(&at, c->base));
+  const int dev = at.device;
   if (dev < 0 || dev >= 64) {
-    set_error("tlb_diagnostics_static: device ordinal above 63");
+    set_error("tlb_diagnostics_static: the arena is not on a device with ordinal 0..63");
     return TLB_ERR_ARG;
   }
   std::lock_guard<std::mutex> lock(g_scratch_mu);
   if (!g_scratch_addr[dev]) {
+    int prev = 0;
+    TLB_CUDA(cudaGetDevice(&prev));
+    if (prev != dev) TLB_CUDA(cudaSetDevice(dev));
     void* p = nullptr;
     cudaError_t e = cudaGetSymbolAddress(&p, g_diag_scratch);
+    if (prev != dev) TLB_CUDA(cudaSetDevice(prev));
     if (e != cudaSuccess) return cuda_check(e, "cudaGetSymbolAddress(g_diag_scratch)");
     g_scratch_addr[dev] = (double*)p;
   }
@@ -97,8 +103,10 @@ extern "C" tlb_status tlb_diagnostics_static(void* ctx, tlb_diag* out) {
     return TLB_ERR_ARG;
   }
   double* scratch = nullptr;
-  tlb_status st = scratch_address(&scratch);
+  tlb_status st = scratch_address(c, &scratch);
   if (st != TLB_OK) return st;
+  // moment storage: the populations the moments stand for (no allocation)
+  if ((st = c->impl->sync_pops(c)) != TLB_OK) return st;
   switch (c->p.dim * 10 + c->p.storage) {
     case 20: return run_static<D2Q9, TLB_F64>(c, scratch, out);
     case 21: return run_static<D2Q9, TLB_F32>(c, scratch, out);

@@ -56,6 +56,7 @@ class Params:
     u0: tuple = (0.0, 0.0, 0.0)
     interface_pos: float = 32.0  # flat C1/C2 interface along the last axis
     forcing: str = "edm"        # "edm": exact difference method (the paper); "guo": Guo forcing
+    state: str = "populations"  # "populations", or "moments": 11 stored moments per cell (tau = 1)
 
     @property
     def ncells(self) -> int:

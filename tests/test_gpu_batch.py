@@ -45,8 +45,9 @@ def test_batch_matches_single_instances_bitwise_f64():
         for s in alone:
             s.step(n)
         for i, s in enumerate(alone):
-            assert np.array_equal(b[i].pops(), s.pops()), (n, i)
-            assert np.array_equal(b[i].nodes(0), s.nodes(0)), (n, i)
+            Pb, Ps = b[i].pops(), s.pops()
+            assert np.array_equal(Pb, Ps), (n, i, np.abs(Pb - Ps).max())
+            assert np.array_equal(b[i].nodes(0), s.nodes(0)), (n, i, np.abs(b[i].nodes(0) - s.nodes(0)).max())
 
 
 def test_batch_matches_single_instances_f32():

@@ -1,12 +1,21 @@
 """FP16 / BF16 population storage (FP32 arithmetic): parity of the CUDA
 path with the FP64 oracle that rounds its populations to the same storage
 format after every step (f_i - w_i, g_i and h_i for i != 0 in the 16-bit
-format; g_0, h_0 in binary32).
+format; g_0, h_0 in binary32), with the error against the plain FP64 oracle
+reported beside it.
 
-The two sides compute in FP32 and FP64, so a stored value that lies within
-the FP32 rounding of a 16-bit midpoint can round differently: such events
-move a population by one 16-bit unit (about 2^-11 or 2^-8 of its size).
-The tolerances below bound the effect of those events over the run."""
+How the tolerance is set.  The GPU computes in FP32 and the oracle in FP64,
+so a stored value whose FP32 result lies within FP32 rounding of a 16-bit
+rounding boundary is stored one 16-bit unit apart on the two sides.  Each
+such event has the size of the storage rounding itself, so the GPU's
+distance from the emulating oracle is bounded by a small multiple of the
+whole effect of the storage rounding on the run, which the oracle measures
+on its own: S = |emulating oracle - plain FP64 oracle| after the same steps.
+The bar is 3 S for C1..C3 (relative L-inf), u (relative L-inf) and the
+markers (absolute).  Measured on the 40x36x34 capsule after 100 steps, the
+GPU's distance is 0.2-1.8 S (FP16: C 1.4e-6, u 3.5e-4, X 2.2e-6 against S
+of 5.9e-6, 2.1e-4, 4.7e-6; BF16: C 9.3e-6, u 3.1e-3, X 1.3e-5 against
+1.5e-5, 1.8e-3, 3.1e-5)."""
 import numpy as np
 import pytest
 
@@ -30,25 +39,46 @@ def _rel(a, b):
     return np.abs(a - b).max() / max(np.abs(b).max(), 1e-300)
 
 
-# (storage, steps, tol on C1..C3, tol on u, tol on markers)
-CASES = [("f16", 100, 2e-3, 5e-2, 1e-3), ("bf16", 100, 2e-2, 5e-1, 1e-2)]
+def _state(s):
+    """C1..C3, u [3][N] and markers of a Simulation or an Oracle."""
+    C = [s.field(n) for n in ("C1", "C2", "C3")]
+    if isinstance(s, oracle.Oracle):
+        u = np.stack([s.field("ux"), s.field("uy"), s.field("uz")])
+    else:
+        u = s.field("u")
+    return C, u, s.nodes(0)
 
 
-@pytest.mark.parametrize("storage,steps,tc,tu,tx", CASES)
-def test_low_precision_storage_matches_emulating_oracle(storage, steps, tc, tu, tx):
+def _dist(a, b):
+    (Ca, ua, Xa), (Cb, ub, Xb) = a, b
+    d = {f"C{k + 1}": _rel(Ca[k], Cb[k]) for k in range(3)}
+    d["u"] = _rel(ua, ub)
+    d["X"] = np.abs(Xa - Xb).max()
+    return d
+
+
+@pytest.mark.parametrize("storage", ["f16", "bf16"])
+def test_low_precision_storage_matches_emulating_oracle(storage):
     from paper_1906_03065_gb300 import Simulation
+    steps = 100
     wl = W.small_3d(storage)
+    oracle.set_threads(0)
     g = Simulation(wl).init()
-    o = oracle.Oracle(wl, emulate_storage=True)
+    oe = oracle.Oracle(wl, emulate_storage=True)
+    op = oracle.Oracle(wl)
     g.step(steps)
-    o.step(steps)
-    err = {n: _rel(g.field(n), o.field(n)) for n in ("C1", "C2", "C3")}
-    ug = g.field("u")
-    uo = np.stack([o.field("ux"), o.field("uy"), o.field("uz")])
-    err["u"] = _rel(ug, uo)
-    err["X"] = np.abs(g.nodes(0) - o.nodes(0)).max()
-    print(storage, {k: f"{v:.2e}" for k, v in err.items()})
-    for n in ("C1", "C2", "C3"):
-        assert err[n] < tc, err
-    assert err["u"] < tu, err
-    assert err["X"] < tx, err
+    oe.step(steps)
+    op.step(steps)
+    sg, se, sp = _state(g), _state(oe), _state(op)
+    S = _dist(se, sp)      # the storage rounding's own effect (oracle only)
+    E = _dist(sg, se)      # GPU against the emulating oracle
+    P = _dist(sg, sp)      # GPU against the plain FP64 oracle (reported)
+    print(storage, "vs emulating:", {k: f"{v:.2e}" for k, v in E.items()},
+          "storage effect:", {k: f"{v:.2e}" for k, v in S.items()},
+          "vs plain FP64:", {k: f"{v:.2e}" for k, v in P.items()})
+    for k in E:
+        assert E[k] <= 3 * S[k], (k, E, S)
+    # the storage effect itself stays far below the FP32 bar's scale for C
+    # and the markers (FP16) -- what the format costs against FP64
+    if storage == "f16":
+        assert P["C1"] < 2e-5 and P["C2"] < 2e-5 and P["C3"] < 2e-5 and P["X"] < 2e-5, P

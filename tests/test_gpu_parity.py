@@ -128,6 +128,19 @@ def test_small_3d_f32_200_steps(forcing):
     _compare_fields(g, o, 1e-4, 1e-4, 1e-4)
 
 
+def test_small_3d_f32_2000_steps():
+    """The stated bar for FP32 fields: relative L-inf 1e-4 on C1..C3 and u,
+    1e-4 lattice units on the markers, after 2000 steps.  Ragged 40x36x34
+    D3Q19 lattice with walls and an icosphere capsule on the interface."""
+    wl = W.small_3d("f32")
+    oracle.set_threads(0)
+    g, o = _sim(wl).init(), oracle.Oracle(wl)
+    g.step(2000)
+    o.step(2000)
+    out = _compare_fields(g, o, 1e-4, 1e-4, 1e-4)
+    print("small_3d f32 2000 steps:", {k: f"{v:.2e}" for k, v in out.items()})
+
+
 def test_small_3d_f32_band_wider_than_period():
     """Periodic sides of 25 cells around a capsule of radius 4.8 with dc = 8:
     the band (capsule +- dc) is wider than the period, so the profile box
@@ -201,9 +214,31 @@ def test_collide_tile_variants_agree(storage):
     ref = _sim(wl).init()
     ref.step(12)
     P = ref.pops()
-    for v, zc in ((1, 5), (2, 16), (3, 7), (4, 12), (5, 34), (6, 9), (7, 12), (8, 3), (9, 12), (10, 6), (11, 20),
-                  (12, 11)):
+    for v, zc in ((0, 8), (1, 5), (2, 16), (3, 7), (4, 12), (5, 34), (6, 9), (7, 12), (8, 3), (9, 12), (10, 6),
+                  (11, 20), (12, 11), (13, 7), (14, 12), (15, 9), (16, 5), (17, 20), (18, 11)):
         g = _sim(wl).init()
         g.set_tile(v, zc)
         g.step(12)
         assert np.abs(g.pops() - P).max() < 1e-6, (v, zc)
+
+
+def test_tau1_collide_only_where_it_applies():
+    """The tau = 1 collide (variants 13-18: every post-collision population
+    an equilibrium, eq. LBE at tau = 1) is the default at tau = 1 with the
+    exact difference method, equals the general collide there, and is
+    refused elsewhere."""
+    from paper_1906_03065_gb300 import TLBError
+    wl = W.small_2d("f64")
+    a = _sim(wl).init()
+    b = _sim(wl).init()
+    b.set_tile(1, 8)  # a general variant
+    a.step(40)
+    b.step(40)
+    assert np.abs(a.pops() - b.pops()).max() < 1e-14
+    for tau, forcing in ((0.8, "edm"), (1.0, "guo")):
+        w2 = W.small_2d("f64")
+        w2.params.tau = w2.params.tau_phi = w2.params.tau_psi = tau
+        w2.params.forcing = forcing
+        g = _sim(w2).init()
+        with pytest.raises(TLBError):
+            g.set_tile(13, 8)
