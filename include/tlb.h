@@ -100,7 +100,18 @@ typedef struct {
                                        9 (c_i.v) c_i] . F)                    */
   int state;                        /* TLB_STATE_POPULATIONS (default) or
                                        TLB_STATE_MOMENTS (see below)         */
+  int force_form;                   /* free-energy force: TLB_FE_POTENTIAL
+                                       (default: -rho grad mu~rho - phi grad
+                                       mu_phi - psi grad mu_psi', eq. ForceFE
+                                       through eq. GradPT) or
+                                       TLB_FE_PRESSURE_TENSOR (grad(rho cs^2)
+                                       - div p - psi grad(kappa_c (psi - I)),
+                                       eq. ForceFE with the explicit tensor
+                                       of App. A, the bulk pressure of eq.
+                                       PressureV2); equal to second order in
+                                       the lattice spacing                  */
 } tlb_params;
+enum { TLB_FE_POTENTIAL = 0, TLB_FE_PRESSURE_TENSOR = 1 };
 enum { TLB_FORCE_EDM = 0, TLB_FORCE_GUO = 1 };
 /* State kept between steps (tlb_params.state):
  * TLB_STATE_POPULATIONS -- the 3Q post-collision populations (any tau);

@@ -247,14 +247,29 @@ def vertex_normals(X: np.ndarray, F: np.ndarray) -> np.ndarray:
     return N / np.linalg.norm(N, axis=1, keepdims=True)
 
 
-def warm_start_markers(y, X0, normals):
+def enclosed_volume(X: np.ndarray, F: np.ndarray) -> float:
+    """Volume of the closed triangle mesh (X, F), counter-clockwise from
+    outside, by the divergence theorem: sum over faces of a . (b x c) / 6."""
+    a, b, c = X[F[:, 0]], X[F[:, 1]], X[F[:, 2]]
+    return float(np.einsum("ij,ij->i", a, np.cross(b, c)).sum() / 6.0)
+
+
+def warm_start_markers(y, X0, normals, F=None):
     """Markers of the warm start: D = trilinear(y2..4)(X0); X0 + T + ((D - T).n) n
-    with T the mean of D over the markers and n the unit vertex normals."""
+    with T the mean of D over the markers and n the unit vertex normals; with
+    the faces F, then scaled about the centroid by (V(X0) / V(X))^(1/3), so
+    that the moved membrane encloses the plain start's volume (the method
+    conserves the fluid inside)."""
     D = trilinear(torch.as_tensor(np.asarray(y, dtype=np.float64))[2:5],
                   torch.as_tensor(np.asarray(X0, dtype=np.float64))).numpy()
     T = D.mean(axis=0)
     r = np.einsum("ij,ij->i", D - T, normals)
-    return X0 + T + r[:, None] * normals
+    X = X0 + T + r[:, None] * normals
+    if F is not None:
+        s = (enclosed_volume(X0, F) / enclosed_volume(X, F)) ** (1.0 / 3.0)
+        c = X.mean(axis=0)
+        X = c + s * (X - c)
+    return X
 
 
 def warm_start_fields(y0, phi0, psi0, I_new):

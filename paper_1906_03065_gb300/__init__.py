@@ -36,7 +36,7 @@ class _Params(C.Structure):
                 ("gamma_phi", C.c_double), ("gamma_psi", C.c_double), ("alpha", C.c_double),
                 ("kappa", C.c_double * 3), ("kappa_c", C.c_double), ("dc", C.c_double),
                 ("u0", C.c_double * 3), ("interface_pos", C.c_double), ("forcing", C.c_int),
-                ("state", C.c_int)]
+                ("state", C.c_int), ("force_form", C.c_int)]
 
 
 class _Mem(C.Structure):
@@ -172,6 +172,7 @@ def make_params(p) -> _Params:
     cp.interface_pos = p.interface_pos
     cp.forcing = {"edm": 0, "guo": 1}[getattr(p, "forcing", "edm")]
     cp.state = {"populations": 0, "moments": 1}[getattr(p, "state", "populations")]
+    cp.force_form = {"potential": 0, "pressure_tensor": 1}[getattr(p, "force_form", "potential")]
     return cp
 
 

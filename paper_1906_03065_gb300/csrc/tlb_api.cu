@@ -117,6 +117,14 @@ static tlb_status check_params(const tlb_params* p, const tlb_membrane_desc* mem
   if (!(p->alpha > 0) || !(p->dc > 0) || p->dc > 60) { set_error("alpha > 0 and 0 < dc <= 60 required"); return TLB_ERR_ARG; }
   if (p->forcing != TLB_FORCE_EDM && p->forcing != TLB_FORCE_GUO) { set_error("unknown forcing"); return TLB_ERR_ARG; }
   if (p->state != TLB_STATE_POPULATIONS && p->state != TLB_STATE_MOMENTS) { set_error("unknown state"); return TLB_ERR_ARG; }
+  if (p->force_form != TLB_FE_POTENTIAL && p->force_form != TLB_FE_PRESSURE_TENSOR) {
+    set_error("unknown force_form");
+    return TLB_ERR_ARG;
+  }
+  if (p->state == TLB_STATE_MOMENTS && p->force_form != TLB_FE_POTENTIAL) {
+    set_error("TLB_STATE_MOMENTS needs the potential force form");
+    return TLB_ERR_ARG;
+  }
   if (p->state == TLB_STATE_MOMENTS) {
     if (!(p->tau == 1.0 && p->tau_phi == 1.0 && p->tau_psi == 1.0 && p->forcing == TLB_FORCE_EDM)) {
       set_error("TLB_STATE_MOMENTS needs tau = tau_phi = tau_psi = 1 and TLB_FORCE_EDM");
@@ -346,7 +354,7 @@ tlb_status tlb_create(const tlb_params* params, const tlb_membrane_desc* mems, i
   // short enough to give a few waves on the 152 SMs
   c->tiles_zc = c->nz >= 64 ? 32 : (c->nz >= 16 ? 8 : c->nz);
   // the tau = 1 collide (no population pull) wherever it applies
-  c->tile_variant = c->t1_ok() ? 13 : 0;
+  c->tile_variant = params->force_form == TLB_FE_PRESSURE_TENSOR ? 19 : (c->t1_ok() ? 13 : 0);
   switch (params->dim * 10 + params->storage) {
     case 20: c->impl = make_impl_d2q9_f64(); break;
     case 21: c->impl = make_impl_d2q9_f32(); break;
@@ -690,15 +698,12 @@ tlb_status tlb_set_tile(void* ctx, int tile_variant, int z_chunk) {
   Ctx* c = (Ctx*)ctx;
   if (!c) { set_error("ctx is NULL"); return TLB_ERR_ARG; }
   if (tile_variant < 0 || tile_variant >= COLLIDE_NVAR || z_chunk < 1 || z_chunk > c->nz) {
-    set_error("set_tile: tile_variant must be 0..18 and z_chunk 1..nz");
+    set_error("set_tile: tile_variant must be 0..21 and z_chunk 1..nz");
     return TLB_ERR_ARG;
   }
-  if (variant_t1(tile_variant) && !c->t1_ok()) {
-    set_error("set_tile: variants 13..18 need tau = tau_phi = tau_psi = 1 and TLB_FORCE_EDM");
-    return TLB_ERR_ARG;
-  }
-  if (!variant_t1(tile_variant) && c->moments()) {
-    set_error("set_tile: moment storage needs one of the variants 13..18");
+  if (!c->variant_ok(tile_variant)) {
+    set_error("set_tile: variants 13..18 need tau = tau_phi = tau_psi = 1, TLB_FORCE_EDM and the potential "
+              "force (and are the only ones with moment storage); 19..21 are those of the pressure-tensor force");
     return TLB_ERR_ARG;
   }
   c->tile_variant = tile_variant;

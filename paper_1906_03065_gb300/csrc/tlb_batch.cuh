@@ -467,11 +467,14 @@ struct BatchImpl : BatchBase {
       b->launches++;
       TLB_CUDA(cudaGetLastError());
     }
-    bool t1 = true;
-    for (int i : b->act) t1 = t1 && b->inst[i]->t1_ok();
+    auto all_ok = [&](int v) {
+      for (int i : b->act)
+        if (!b->inst[i]->variant_ok(v)) return false;
+      return true;
+    };
     for (int v = 0; v < COLLIDE_NVAR && st == TLB_OK; ++v)
       for (size_t zi = 0; zi < zcs.size() && st == TLB_OK; ++zi) {
-        if (variant_t1(v) && !t1) continue;
+        if (!all_ok(v)) continue;
         b->tile_variant = v;
         b->zc = zcs[zi];
         b->graph_dirty = true;

@@ -137,9 +137,22 @@ tlb_status tlb_batch_create(const tlb_instance_desc* inst, int n_inst, void* are
     nzmax = std::max(nzmax, c->nz);
   }
   b->zc = nzmax >= 64 ? 16 : std::min(nzmax, 8);
-  bool t1 = true;
-  for (Ctx* c : b->inst) t1 = t1 && c->t1_ok();
-  b->tile_variant = t1 ? 13 : 0;  // the tau = 1 collide wherever it applies
+  // the tau = 1 collide wherever it applies; one force form per batch
+  b->tile_variant = 0;
+  for (int v : {13, 19, 0}) {
+    bool ok = true;
+    for (Ctx* c : b->inst) ok = ok && c->variant_ok(v);
+    if (ok) {
+      b->tile_variant = v;
+      break;
+    }
+  }
+  for (Ctx* c : b->inst)
+    if (!c->variant_ok(b->tile_variant)) {
+      set_error("batch: instances mix force forms");
+      delete b;
+      return TLB_ERR_ARG;
+    }
   for (int q = 0; q < 2; ++q) b->targs[q] = {bp.targs[q], (size_t)n_inst * Batch::ARGS_BYTES};
   b->vg = {bp.vg, (size_t)Batch::NPH * Batch::MAXOPS * n_inst * 16};
   b->res = {bp.res, (size_t)n_inst * 4 * 8};

@@ -26,7 +26,7 @@ struct Header {
   char magic[8];
   uint32_t version, header_bytes;
   // the parameters, field by field (no struct padding in the file)
-  int32_t dim, nx, ny, nz, wall_last, storage, forcing, state;
+  int32_t dim, nx, ny, nz, wall_last, storage, forcing, state, force_form, pad;
   double tau, tau_phi, tau_psi, gamma_phi, gamma_psi, alpha, kappa[3], kappa_c, dc, u0[3], interface_pos;
   int64_t nn, ne, N, P, t, t_snap;
   uint64_t mem_hash;  // the membranes: reference shapes, elements, moduli
@@ -66,6 +66,8 @@ void fill_params(Header& h, const tlb_params& p) {
   h.storage = p.storage;
   h.forcing = p.forcing;
   h.state = p.state;
+  h.force_form = p.force_form;
+  h.pad = 0;
   h.tau = p.tau;
   h.tau_phi = p.tau_phi;
   h.tau_psi = p.tau_psi;
@@ -81,7 +83,7 @@ void fill_params(Header& h, const tlb_params& p) {
 
 bool same_params(const Header& a, const Header& b) {
   if (a.dim != b.dim || a.nx != b.nx || a.ny != b.ny || a.nz != b.nz || a.wall_last != b.wall_last ||
-      a.storage != b.storage || a.forcing != b.forcing || a.state != b.state)
+      a.storage != b.storage || a.forcing != b.forcing || a.state != b.state || a.force_form != b.force_form)
     return false;
   const double x[] = {a.tau, a.tau_phi, a.tau_psi, a.gamma_phi, a.gamma_psi, a.alpha, a.kappa[0], a.kappa[1],
                       a.kappa[2], a.kappa_c, a.dc, a.u0[0], a.u0[1], a.u0[2], a.interface_pos};

@@ -272,6 +272,13 @@ __device__ __forceinline__ double rfma(double a, double b, double c) { return __
 // cell it streams from.  Plane order of the stored moments:
 enum { M_DRHO = 0, M_W = 1, M_PHI = 4, M_GMP = 5, M_PSI = 6, M_GMS = 7, M_V = 8, M_COUNT = 11 };
 
+// Four values of one cell side by side, so that a shared-memory ring of them
+// is read with one 16-byte load (two in double precision) per cell.
+template <class R>
+struct alignas(4 * sizeof(R)) R4 {
+  R x, y, z, w;
+};
+
 // The post-collision populations of one cell from its stored moments, with
 // the explicitly rounded operations (see rmul), so the reconstruction in the
 // pull, in the interpolation and in the materialised populations gives the
@@ -295,6 +302,24 @@ struct EqCell {
     gm3[1] = rmul(Real(3), M[M_GMS * P32 + c]);
 #pragma unroll
     for (int d = 0; d < 3; ++d) v[d] = M[(M_V + d) * P32 + c];
+    vv = rfma(v[2], v[2], rfma(v[1], v[1], rmul(v[0], v[0])));
+  }
+  // the same from three packed values: (drho, w), (phi, Gamma_phi mu_phi,
+  // psi, Gamma_psi mu_psi'), (v, -)
+  __device__ __forceinline__ void load3(const R4<Real>& A, const R4<Real>& B, const R4<Real>& C) {
+    drho = A.x;
+    w[0] = A.y;
+    w[1] = A.z;
+    w[2] = A.w;
+    rho = Real(1) + drho;
+    ww = rfma(w[2], w[2], rfma(w[1], w[1], rmul(w[0], w[0])));
+    ord[0] = B.x;
+    ord[1] = B.z;
+    gm3[0] = rmul(Real(3), B.y);
+    gm3[1] = rmul(Real(3), B.w);
+    v[0] = C.x;
+    v[1] = C.y;
+    v[2] = C.z;
     vv = rfma(v[2], v[2], rfma(v[1], v[1], rmul(v[0], v[0])));
   }
   // f_i - w_i = w_i (drho + rho (3 c.w + 4.5 (c.w)^2 - 1.5 w^2))

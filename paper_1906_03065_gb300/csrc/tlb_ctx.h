@@ -13,8 +13,10 @@
 // Collide variants: 3 tile shapes x 4 register forms, v = 3 form + tile,
 // the smallest tile in a fifth form (v = 12), and the 3 tiles in the two
 // forms of the tau = 1 collide (v = 13..18, see variant_t1).
-constexpr int COLLIDE_NVAR = 19;
+constexpr int COLLIDE_NVAR = 22;
 constexpr bool variant_t1(int v) { return v >= 13 && v <= 18; }
+// variants 19..21: the general collide with the pressure-tensor force
+constexpr bool variant_pt(int v) { return v >= 19 && v <= 21; }
 
 // z-chunk lengths the collide autotuner tries: every distinct ceil(nz / m)
 // of at least 4 planes (each gives another grid, so another fill of the
@@ -98,7 +100,16 @@ struct Ctx {
   // the tau = 1 collide applies: tau = tau_phi = tau_psi = 1 and the exact
   // difference method (every post-collision population is an equilibrium)
   bool t1_ok() const {
-    return p.tau == 1.0 && p.tau_phi == 1.0 && p.tau_psi == 1.0 && p.forcing == TLB_FORCE_EDM;
+    return p.tau == 1.0 && p.tau_phi == 1.0 && p.tau_psi == 1.0 && p.forcing == TLB_FORCE_EDM &&
+           p.force_form == TLB_FE_POTENTIAL;
+  }
+  // a collide variant this context can run: the pressure-tensor variants for
+  // the pressure-tensor force only, the tau = 1 ones only where they apply,
+  // and with moment storage only the tau = 1 ones
+  bool variant_ok(int v) const {
+    if (variant_pt(v) != (p.force_form == TLB_FE_PRESSURE_TENSOR)) return false;
+    if (variant_t1(v)) return t1_ok();
+    return !moments();
   }
   // moment storage (TLB_STATE_MOMENTS): the state is the moment buffer M,
   // except after an initialisation or a write of populations, which the

@@ -376,7 +376,7 @@ struct Impl : ImplBase {
     const std::vector<int> zcs = z_chunk_candidates(c->nz);
     for (int v = 0; v < COLLIDE_NVAR; ++v)
       for (const int zcv : zcs) {
-        if (variant_t1(v) ? !c->t1_ok() : c->moments()) continue;
+        if (!c->variant_ok(v)) continue;
         c->tile_variant = v;
         c->tiles_zc = zcv;
         la.zc = c->tiles_zc;

@@ -117,15 +117,18 @@ __global__ void __launch_bounds__(256) k_moments_recon(const __grid_constant__ L
 // The same pull as a plane sweep: a TX x TY tile of columns walks a chunk of
 // z planes; the stored moments of four planes (tile plus a halo of 1) sit in
 // a shared-memory ring filled by asynchronous copies one plane ahead, so
-// every stored moment is read once from memory and the 19 x 11 reads of a
-// cell's rebuild come from shared memory.  Same arithmetic and summation
-// order as moments_recon_body.
+// every stored moment is read once from memory and a cell's rebuild reads
+// its 19 sources from shared memory, three 16-byte vectors each.  Same
+// arithmetic and summation order as moments_recon_body.
 template <class L, int MODE, int TX, int TY>
 __global__ void __launch_bounds__(TX* TY) k_moments_recon_tiled(const __grid_constant__ LBArgs<MODE> a) {
   using Real = typename Prec<MODE>::Real;
   constexpr bool D3 = L::DIM == 3;
   constexpr int HX = TX + 2, HY = D3 ? TY + 2 : 1, CELLS = HX * HY, NT = TX * TY;
-  __shared__ Real sM[4][M_COUNT][CELLS];
+  struct Cell {
+    R4<Real> a, b, c;  // (drho, w), (phi, gmp, psi, gms), (v, -)
+  };
+  __shared__ Cell sM[4][CELLS];
   const Geo G = a.G;
   const int tx = threadIdx.x % TX, ty = threadIdx.x / TX, tid = threadIdx.x;
   const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
@@ -147,8 +150,12 @@ __global__ void __launch_bounds__(TX* TY) k_moments_recon_tiled(const __grid_con
       const int gx = wrapn(x0 - 1 + hx, G.nx);
       const int gy = D3 ? wrapn(y0 - 1 + hy, G.ny) : 0;
       const long long c = ((long long)pz * G.ny + gy) * G.nx + gx;
+      Real* d[M_COUNT] = {&sM[slot][k].a.x, &sM[slot][k].a.y, &sM[slot][k].a.z, &sM[slot][k].a.w,
+                          &sM[slot][k].b.x, &sM[slot][k].b.y, &sM[slot][k].b.z, &sM[slot][k].b.w,
+                          &sM[slot][k].c.x, &sM[slot][k].c.y, &sM[slot][k].c.z};
+      // (plane order of the stored moments: drho, w, phi, gmp, psi, gms, v)
 #pragma unroll
-      for (int f = 0; f < M_COUNT; ++f) cp_async_elem(&sM[slot][f][k], a.msrc + (long long)f * G.P + c);
+      for (int f = 0; f < M_COUNT; ++f) cp_async_elem(d[f], a.msrc + (long long)f * G.P + c);
     }
     cp_async_commit();
   };
@@ -169,7 +176,8 @@ __global__ void __launch_bounds__(TX* TY) k_moments_recon_tiled(const __grid_con
         const int hx = bounce ? tx + 1 : tx + 1 - L::cx(i);
         const int hy = D3 ? (bounce ? ty + 1 : ty + 1 - L::cy(i)) : 0;
         EqCell<L, Real> e;
-        e.load(&sM[(sz + 8) & 3][0][0], CELLS, hy * HX + hx);
+        const Cell& src = sM[(sz + 8) & 3][hy * HX + hx];
+        e.load3(src.a, src.b, src.c);
         p.f[i] = e.f(ii);
         p.g[i] = e.o(0, ii);
         p.h[i] = e.o(1, ii);
@@ -227,6 +235,52 @@ __device__ __forceinline__ Real eq_poly(Real cu, Real uu) {
 // the chemical potentials (halo 1), so each cell's radius-2 dependency (mu
 // needs the Laplacian of the moments, the force needs the gradient of mu) is
 // served on chip.
+// Pressure tensor of App. A without its ideal-gas part rho cs^2 delta (the
+// force form grad(rho cs^2) - div p needs only the rest), in the variables
+// rho, phi, psi with the mixing coefficients k_rr = k_ff = (k1 + k2)/4,
+// k_ss = (k1 + k2 + 4 k3)/4, k_rf = -k_fs = (k1 - k2)/4, k_rs = -(k1 + k2)/4:
+//   p'_ab = p'_b delta_ab + alpha^2 sum_mn k_mn [d_a m d_b n - delta_ab
+//           ((1/2) grad m . grad n + m lap n)],
+// with the bulk pressure of eq. PressureV2 (the ideal part dropped),
+// p'_b = rho mu_rho^b + phi mu_phi^b + psi mu_psi^b - f_b and f_b = sum_m
+// kappa_m/2 C_m^2 (1 - C_m)^2 = kappa1/32 (1 - a^2)^2 + kappa2/32 (1 - b^2)^2
+// + kappa3/2 psi^2 (1 - psi)^2 (a = A - 1, b = B - 1 as in chem_potentials).
+// Components xx, yy, zz, xy, xz, yz.  gr: the lattice gradients of rho - 1,
+// phi, psi; lap: their Laplacians.
+template <class Real>
+__device__ __forceinline__ void pressure_tensor(const FEParams<Real>& fe, Real drho, Real phi, Real psi,
+                                                const Real* lap, const Real (*gr)[3], Real* out) {
+  const Real a = drho + phi - psi, b = drho - phi - psi;
+  const Real tA = fe.k1 * Real(0.125) * a * (a * a - Real(1));
+  const Real tB = fe.k2 * Real(0.125) * b * (b * b - Real(1));
+  const Real ta = Real(1) - a * a, tb = Real(1) - b * b, tp = psi * (Real(1) - psi);
+  const Real fb = fe.k1 * Real(1.0 / 32) * ta * ta + fe.k2 * Real(1.0 / 32) * tb * tb + fe.k3 * Real(0.5) * tp * tp;
+  const Real rho = Real(1) + drho;
+  const Real pb = rho * (tA + tB) + phi * (tA - tB) +
+                  psi * (-tA - tB + fe.k3 * psi * (psi - Real(1)) * (Real(2) * psi - Real(1))) - fb;
+  const Real kp = Real(0.25) * (fe.k1 + fe.k2), km = Real(0.25) * (fe.k1 - fe.k2);
+  const Real K[3][3] = {{kp, km, -kp}, {km, kp, -km}, {-kp, -km, kp + fe.k3}};
+  const Real val[3] = {rho, phi, psi};
+  Real tr = pb;
+#pragma unroll
+  for (int m = 0; m < 3; ++m)
+#pragma unroll
+    for (int n = 0; n < 3; ++n) {
+      const Real gg = gr[m][0] * gr[n][0] + gr[m][1] * gr[n][1] + gr[m][2] * gr[n][2];
+      tr -= fe.a2 * K[m][n] * (Real(0.5) * gg + val[m] * lap[n]);
+    }
+  const int ia[6] = {0, 1, 2, 0, 0, 1}, ib[6] = {0, 1, 2, 1, 2, 2};
+#pragma unroll
+  for (int q = 0; q < 6; ++q) {
+    Real t = ia[q] == ib[q] ? tr : Real(0);
+#pragma unroll
+    for (int m = 0; m < 3; ++m)
+#pragma unroll
+      for (int n = 0; n < 3; ++n) t += fe.a2 * K[m][n] * gr[m][ia[q]] * gr[n][ib[q]];
+    out[q] = t;
+  }
+}
+
 // Forms 5 and 6 are the collide at tau = tau_phi = tau_psi = 1 with the exact
 // difference method: there every post-collision population is an
 // equilibrium, f* = f^eq(rho, u + du), g* = g^eq(phi, mu_phi, v), h* =
@@ -240,6 +294,8 @@ template <class L, int MODE, int TX, int TY, int FORM>
 __device__ __forceinline__ void collide_gen_body(const LBArgs<MODE>& a, const Blk& blk) {
   constexpr bool PF = FORM == 1;  // the next population set prefetched
   constexpr bool T1 = form_t1<FORM>();
+  // form 7: the force from the explicit pressure tensor (see pt_of)
+  constexpr bool PT = FORM == 7;
   using Real = typename Prec<MODE>::Real;
   using Store = typename Prec<MODE>::Store;
   using Rest = typename Prec<MODE>::Rest;
@@ -249,8 +305,13 @@ __device__ __forceinline__ void collide_gen_body(const LBArgs<MODE>& a, const Bl
   constexpr int MX = TX + 4, MY = TY + 2 * HY;
   constexpr int UX = TX + 2, UY = TY + (D3 ? 2 : 0);
   constexpr int NT = TX * TY;
+  // per cell of the potentials' ring: mu~rho, mu_phi, mu_psi'; with the
+  // pressure tensor: p_xx p_yy p_zz p_xy p_xz p_yz, kappa_c (psi - I),
+  // mu_phi, mu_psi'
+  constexpr int NMU = PT ? 9 : 3;
+  constexpr int MUP = PT ? 7 : 1, MUS = PT ? 8 : 2;  // slots of mu_phi, mu_psi'
   __shared__ Real smom[5][3][MY * MX];
-  __shared__ Real smu[3][3][UY * UX];
+  __shared__ Real smu[3][NMU][UY * UX];
 
   const Geo G = a.G;
   const int tx = threadIdx.x % TX, ty = threadIdx.x / TX, tid = threadIdx.x;
@@ -293,7 +354,7 @@ __device__ __forceinline__ void collide_gen_body(const LBArgs<MODE>& a, const Bl
     if (G.wall && (p < 0 || p >= G.nz)) {  // mirror ghost: mu(-1) = mu(0), mu(nz) = mu(nz-1)
       const int src = (min(max(p, 0), G.nz - 1) + 9) % 3;
       for (int k = tid; k < UX * UY; k += NT)
-        for (int q = 0; q < 3; ++q) smu[slot][q][k] = smu[src][q][k];
+        for (int q = 0; q < NMU; ++q) smu[slot][q][k] = smu[src][q][k];
       return;
     }
     const long long zp = (long long)modn(p, G.nz) * G.ny;  // periodic ghost planes wrap
@@ -319,9 +380,34 @@ __device__ __forceinline__ void collide_gen_body(const LBArgs<MODE>& a, const Bl
       Real Iv = a.I[(zp + gy) * G.nx + gx];
       Real mr, mp, ms;
       chem_potentials<Real>(a.fe, cen[0], cen[1], cen[2], lap[0], lap[1], lap[2], Iv, mr, mp, ms);
-      smu[slot][0][k] = mr;
-      smu[slot][1][k] = mp;
-      smu[slot][2][k] = ms;
+      if constexpr (PT) {
+        // gradients of rho - 1, phi, psi (radius 1, isotropic stencil)
+        Real gr[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+#pragma unroll
+        for (int i = 1; i < Q; ++i) {
+          const int s = (p + L::cz(i) + 10) % 5;
+          const int nb = (hy + L::cy(i)) * MX + hx + L::cx(i);
+          const Real w = Real(L::w(i)) * Real(3);
+#pragma unroll
+          for (int q = 0; q < 3; ++q) {
+            const Real v = w * smom[s][q][nb];
+            if (L::cx(i)) gr[q][0] += L::cx(i) > 0 ? v : -v;
+            if (L::cy(i)) gr[q][1] += L::cy(i) > 0 ? v : -v;
+            if (L::cz(i)) gr[q][2] += L::cz(i) > 0 ? v : -v;
+          }
+        }
+        Real pt[6];
+        pressure_tensor<Real>(a.fe, cen[0], cen[1], cen[2], lap, gr, pt);
+#pragma unroll
+        for (int q = 0; q < 6; ++q) smu[slot][q][k] = pt[q];
+        smu[slot][6][k] = a.fe.kc * (cen[2] - Iv);
+        smu[slot][MUP][k] = mp;
+        smu[slot][MUS][k] = ms;
+      } else {
+        smu[slot][0][k] = mr;
+        smu[slot][1][k] = mp;
+        smu[slot][2][k] = ms;
+      }
     }
   };
 
@@ -337,8 +423,12 @@ __device__ __forceinline__ void collide_gen_body(const LBArgs<MODE>& a, const Bl
     const int mc = (ty + HY) * MX + tx + 2;
     const Real drho_c = smom[sm5][0][mc], phi = smom[sm5][1][mc], psi = smom[sm5][2][mc];
     const Real rho = Real(1) + drho_c;
-    // gradients of the potentials (radius 1, isotropic stencil)
-    Real gm[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+    // gradients of the potentials' ring entries (radius 1, isotropic
+    // stencil; the 1/cs^2 is applied below)
+    constexpr int NG = PT ? 7 : 3;
+    Real gm[NG][3];
+#pragma unroll
+    for (int q = 0; q < NG; ++q) gm[q][0] = gm[q][1] = gm[q][2] = Real(0);
     const int ux = tx + 1, uy = ty + (D3 ? 1 : 0);
 #pragma unroll
     for (int i = 1; i < Q; ++i) {
@@ -346,7 +436,7 @@ __device__ __forceinline__ void collide_gen_body(const LBArgs<MODE>& a, const Bl
       const int nbi = (uy + L::cy(i)) * UX + ux + L::cx(i);
       const Real w = Real(L::w(i));
 #pragma unroll
-      for (int q = 0; q < 3; ++q) {
+      for (int q = 0; q < NG; ++q) {
         const Real v = w * smu[s][q][nbi];
         if (L::cx(i)) gm[q][0] += L::cx(i) > 0 ? v : -v;
         if (L::cy(i)) gm[q][1] += L::cy(i) > 0 ? v : -v;
@@ -355,14 +445,23 @@ __device__ __forceinline__ void collide_gen_body(const LBArgs<MODE>& a, const Bl
     }
     const int sc = (zz + 9) % 3;
     const int cc = uy * UX + ux;
-    const Real mup = smu[sc][1][cc], mus = smu[sc][2][cc];
-    // force: f_FE = -rho grad mu~rho - phi grad mu_phi - psi grad mu_psi' (+ f_IB
-    // inside the bricks the markers spread into)
+    const Real mup = smu[sc][MUP][cc], mus = smu[sc][MUS][cc];
+    // force (+ f_IB inside the bricks the markers spread into):
+    //  potential form: f_FE = -rho grad mu~rho - phi grad mu_phi - psi grad mu_psi'
+    //  pressure-tensor form: f_FE = -div p' - psi grad(kappa_c (psi - I)), p' the
+    //  tensor of App. A without rho cs^2 (whose divergence cancels grad rho cs^2)
     const bool ib = a.bflag[((zz >> 2) * a.nby + (y >> 2)) * a.nbx + (x >> 2)] != 0;
     Real F[3];
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
-      F[d] = -Real(3) * (rho * gm[0][d] + phi * gm[1][d] + psi * gm[2][d]);
+      if constexpr (PT) {
+        // row d of the symmetric tensor: (xx, xy, xz), (xy, yy, yz), (xz, yz, zz)
+        const int r0 = d == 0 ? 0 : (d == 1 ? 3 : 4), r1 = d == 0 ? 3 : (d == 1 ? 1 : 5),
+                  r2 = d == 0 ? 4 : (d == 1 ? 5 : 2);
+        F[d] = -Real(3) * (gm[r0][0] + gm[r1][1] + gm[r2][2] + psi * gm[6][d]);
+      } else {
+        F[d] = -Real(3) * (rho * gm[0][d] + phi * gm[1][d] + psi * gm[2][d]);
+      }
       if (ib) F[d] += a.fib[d * G.P32 + n];
     }
     if (!D3) F[1] = 0;
@@ -570,8 +669,8 @@ __device__ __forceinline__ void collide_t1_body(const LBArgs<MODE>& a, const Blk
   constexpr int MX = TX + 4, MY = TY + 2 * HY;
   constexpr int UX = TX + 2, UY = TY + (D3 ? 2 : 0);
   constexpr int NT = TX * TY;
-  __shared__ Real smom[5][4][MY * MX];  // rho - 1, phi, psi, I
-  __shared__ Real smu[3][3][UY * UX];
+  __shared__ R4<Real> smom[5][MY * MX];  // (rho - 1, phi, psi, I) per cell
+  __shared__ R4<Real> smu[3][UY * UX];   // (mu~rho, mu_phi, mu_psi', -) per cell
 
   const Geo G = a.G;
   const int tx = threadIdx.x % TX, ty = threadIdx.x / TX, tid = threadIdx.x;
@@ -602,10 +701,10 @@ __device__ __forceinline__ void collide_t1_body(const LBArgs<MODE>& a, const Blk
       const int gx = modn(x0 - 2 + hx, G.nx);
       const int gy = D3 ? modn(y0 - HY + hy, G.ny) : 0;
       const long long c = (zp + gy) * G.nx + gx;
-      cp_async_elem(&smom[slot][0][k], a.rho + c);
-      cp_async_elem(&smom[slot][1][k], a.phi + c);
-      cp_async_elem(&smom[slot][2][k], a.psi + c);
-      cp_async_elem(&smom[slot][3][k], a.I + c);
+      cp_async_elem(&smom[slot][k].x, a.rho + c);
+      cp_async_elem(&smom[slot][k].y, a.phi + c);
+      cp_async_elem(&smom[slot][k].z, a.psi + c);
+      cp_async_elem(&smom[slot][k].w, a.I + c);
     }
     cp_async_commit();
   };
@@ -615,32 +714,28 @@ __device__ __forceinline__ void collide_t1_body(const LBArgs<MODE>& a, const Blk
     const int slot = (p + 9) % 3;
     if (G.wall && (p < 0 || p >= G.nz)) {  // mirror ghost: mu(-1) = mu(0), mu(nz) = mu(nz-1)
       const int src = (min(max(p, 0), G.nz - 1) + 9) % 3;
-      for (int k = tid; k < UX * UY; k += NT)
-        for (int q = 0; q < 3; ++q) smu[slot][q][k] = smu[src][q][k];
+      for (int k = tid; k < UX * UY; k += NT) smu[slot][k] = smu[src][k];
       return;
     }
     const int sc = (p + 10) % 5;
     for (int k = tid; k < UX * UY; k += NT) {
       const int ux = k % UX, uy = k / UX;
       const int hx = ux + 1, hy = uy + (D3 ? 1 : 0);
-      const int cidx = hy * MX + hx;
+      const R4<Real> cen = smom[sc][hy * MX + hx];
       Real lap[3] = {0, 0, 0};
-      const Real cen[3] = {smom[sc][0][cidx], smom[sc][1][cidx], smom[sc][2][cidx]};
 #pragma unroll
       for (int i = 1; i < Q; ++i) {
-        const int s = (p + L::cz(i) + 10) % 5;
-        const int nb = (hy + L::cy(i)) * MX + hx + L::cx(i);
+        const R4<Real> nbv = smom[(p + L::cz(i) + 10) % 5][(hy + L::cy(i)) * MX + hx + L::cx(i)];
         const Real w = Real(L::w(i));
-#pragma unroll
-        for (int q = 0; q < 3; ++q) lap[q] += w * (smom[s][q][nb] - cen[q]);
+        lap[0] += w * (nbv.x - cen.x);
+        lap[1] += w * (nbv.y - cen.y);
+        lap[2] += w * (nbv.z - cen.z);
       }
 #pragma unroll
       for (int q = 0; q < 3; ++q) lap[q] *= Real(6);  // 2/cs^2
       Real mr, mp, ms;
-      chem_potentials<Real>(a.fe, cen[0], cen[1], cen[2], lap[0], lap[1], lap[2], smom[sc][3][cidx], mr, mp, ms);
-      smu[slot][0][k] = mr;
-      smu[slot][1][k] = mp;
-      smu[slot][2][k] = ms;
+      chem_potentials<Real>(a.fe, cen.x, cen.y, cen.z, lap[0], lap[1], lap[2], cen.w, mr, mp, ms);
+      smu[slot][k] = R4<Real>{mr, mp, ms, Real(0)};
     }
   };
 
@@ -650,29 +745,27 @@ __device__ __forceinline__ void collide_t1_body(const LBArgs<MODE>& a, const Blk
     // the cell's momentum first: its loads run under the stencil below
     const Real j[3] = {a.jm[n], a.jm[G.P32 + n], a.jm[2 * G.P32 + n]};
     const bool ib = a.bflag[((zz >> 2) * a.nby + (y >> 2)) * a.nbx + (x >> 2)] != 0;
-    const int sm5 = (zz + 10) % 5;
-    const int mc = (ty + HY) * MX + tx + 2;
-    const Real drho = smom[sm5][0][mc], phi = smom[sm5][1][mc], psi = smom[sm5][2][mc];
+    const R4<Real> mom = smom[(zz + 10) % 5][(ty + HY) * MX + tx + 2];
+    const Real drho = mom.x, phi = mom.y, psi = mom.z;
     const Real rho = Real(1) + drho;
     // gradients of the potentials (radius 1, isotropic stencil)
     Real gm[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
     const int ux = tx + 1, uy = ty + (D3 ? 1 : 0);
 #pragma unroll
     for (int i = 1; i < Q; ++i) {
-      const int s = (zz + L::cz(i) + 9) % 3;
-      const int nbi = (uy + L::cy(i)) * UX + ux + L::cx(i);
+      const R4<Real> m4 = smu[(zz + L::cz(i) + 9) % 3][(uy + L::cy(i)) * UX + ux + L::cx(i)];
       const Real w = Real(L::w(i));
+      const Real mv[3] = {m4.x, m4.y, m4.z};
 #pragma unroll
       for (int q = 0; q < 3; ++q) {
-        const Real v = w * smu[s][q][nbi];
+        const Real v = w * mv[q];
         if (L::cx(i)) gm[q][0] += L::cx(i) > 0 ? v : -v;
         if (L::cy(i)) gm[q][1] += L::cy(i) > 0 ? v : -v;
         if (L::cz(i)) gm[q][2] += L::cz(i) > 0 ? v : -v;
       }
     }
-    const int sc = (zz + 9) % 3;
-    const int cc = uy * UX + ux;
-    const Real mup = smu[sc][1][cc], mus = smu[sc][2][cc];
+    const R4<Real> muc = smu[(zz + 9) % 3][uy * UX + ux];
+    const Real mup = muc.y, mus = muc.z;
     Real F[3];
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
@@ -806,7 +899,8 @@ __global__ void __launch_bounds__(TX* TY, collide_threads<FORM>() / (TX * TY))
 // Calls fn(tile x, tile y, form) with the variant's compile-time values
 // (3D tiles 32x4, 32x8, 64x4; 2D rows of 32, 64, 128; variant 12 is the
 // smallest tile in form 4; variants 13-18 the three tiles in the tau = 1
-// forms 5 and 6).
+// forms 5 and 6; variants 19-21 the three tiles of form 7, the general
+// collide with the pressure-tensor force).
 template <int V> using CIdx = std::integral_constant<int, V>;
 template <class L, class Fn>
 __host__ tlb_status collide_variant(int v, Fn&& fn) {
@@ -831,6 +925,9 @@ __host__ tlb_status collide_variant(int v, Fn&& fn) {
     case 16: return fn(CIdx<32>{}, CIdx<Y0>{}, CIdx<6>{});
     case 17: return fn(CIdx<X1>{}, CIdx<Y1>{}, CIdx<6>{});
     case 18: return fn(CIdx<X2>{}, CIdx<Y0>{}, CIdx<6>{});
+    case 19: return fn(CIdx<32>{}, CIdx<Y0>{}, CIdx<7>{});
+    case 20: return fn(CIdx<X1>{}, CIdx<Y1>{}, CIdx<7>{});
+    case 21: return fn(CIdx<X2>{}, CIdx<Y0>{}, CIdx<7>{});
     default: return fn(CIdx<32>{}, CIdx<Y0>{}, CIdx<0>{});
   }
 }

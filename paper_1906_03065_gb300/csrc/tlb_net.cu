@@ -711,6 +711,39 @@ __global__ void k_ws_move(double* __restrict__ X, int nn, const float* __restric
   for (int q = 0; q < 3; ++q) X[3 * l + q] += T[q] + r * n[q];
 }
 
+// FP64 partial sums of the marker positions (their centroid).
+__global__ void k_ws_centroid(const double* __restrict__ X, int nn, double* __restrict__ part) {
+  __shared__ double sm[3][128];
+  const int l = blockIdx.x * 128 + threadIdx.x;
+  for (int q = 0; q < 3; ++q) sm[q][threadIdx.x] = l < nn ? X[3 * l + q] : 0.0;
+  __syncthreads();
+  for (int s = 64; s > 0; s >>= 1) {
+    if (threadIdx.x < s)
+      for (int q = 0; q < 3; ++q) sm[q][threadIdx.x] += sm[q][threadIdx.x + s];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0)
+    for (int q = 0; q < 3; ++q) part[q * gridDim.x + blockIdx.x] = sm[q][0];
+}
+
+// Volume projection of the moved membrane: X_l = c + s (X_l - c) about the
+// centroid c = tot / nn with s = (V0 / V1)^(1/3), so that the capsule
+// encloses the plain start's volume V0 again (the fluid inside is conserved
+// by the method, so the prediction's shape change must not change it).
+__global__ void k_ws_scale(double* __restrict__ X, int nn, const double* __restrict__ tot,
+                           const double* __restrict__ v0, const double* __restrict__ v1) {
+  const int l = blockIdx.x * blockDim.x + threadIdx.x;
+  if (l >= nn) return;
+  const double s = cbrt(v0[1] / v1[1]);
+  for (int q = 0; q < 3; ++q) {
+    const double c = tot[q] / nn;
+    X[3 * l + q] = c + s * (X[3 * l + q] - c);
+  }
+}
+
+__global__ void k_capsule_measures(const double* X, const int* E, const int* ecap, int ne, int NV, int ncap,
+                                   double* out);
+
 // Plain-start phase indicator of the C1/C2 fluid: s0 = phi0 / (1 - psi0)
 // (the plain start has phi0 = (1 - psi0)(2 s - 1)), 0 where 1 - psi0 < 1e-6.
 __device__ __forceinline__ double s0_of(float phi0, float psi0) {
@@ -1384,15 +1417,29 @@ tlb_status tlb_net_warm_start(void* net, void* ctx, const double* feats) {
   const float* y = n->at<float>(n->o_y);
   double* part = n->at<double>(n->o_lpart);
   double* tot = n->at<double>(n->o_misc) + 8;  // [0..2] pass 1, [4..5] pass 2, [8..10] translation
-  // markers: mean translation plus the normal part of the predicted displacement
+  // markers: mean translation plus the normal part of the predicted
+  // displacement, then scaled about their centroid back to the plain
+  // start's enclosed volume
   float* D = n->at<float>(n->o_gy);
   const unsigned bn = nb(c->nn, 128);
-  k_ws_disp<<<bn, 128, 0, st>>>(c->ptr<double>(c->L.X), c->nn, y, n->d.edge, D, part);
+  double* X = c->ptr<double>(c->L.X);
+  double* vol = n->at<double>(n->o_misc) + 32;  // [0, 1] area, volume before; [2, 3] after; [4..6] centroid sums
+  k_capsule_measures<<<1, 256, 0, st>>>(X, c->ptr<int>(c->L.E), c->ptr<int>(c->L.ecap), c->ne, c->NV, 1, vol);
+  NET_LAUNCHED(n, "k_capsule_measures");
+  k_ws_disp<<<bn, 128, 0, st>>>(X, c->nn, y, n->d.edge, D, part);
   NET_LAUNCHED(n, "k_ws_disp");
   k_sum_parts<<<1, 256, 0, st>>>(part, (int)bn, 3, tot + 8);
   NET_LAUNCHED(n, "k_sum_parts");
-  k_ws_move<<<bn, 128, 0, st>>>(c->ptr<double>(c->L.X), c->nn, D, c->ptr<float>(c->L.vn), tot + 8);
+  k_ws_move<<<bn, 128, 0, st>>>(X, c->nn, D, c->ptr<float>(c->L.vn), tot + 8);
   NET_LAUNCHED(n, "k_ws_move");
+  k_capsule_measures<<<1, 256, 0, st>>>(X, c->ptr<int>(c->L.E), c->ptr<int>(c->L.ecap), c->ne, c->NV, 1, vol + 2);
+  NET_LAUNCHED(n, "k_capsule_measures");
+  k_ws_centroid<<<bn, 128, 0, st>>>(X, c->nn, part);
+  NET_LAUNCHED(n, "k_ws_centroid");
+  k_sum_parts<<<1, 256, 0, st>>>(part, (int)bn, 3, vol + 4);
+  NET_LAUNCHED(n, "k_sum_parts");
+  k_ws_scale<<<bn, 128, 0, st>>>(X, c->nn, vol + 4, vol, vol + 2);
+  NET_LAUNCHED(n, "k_ws_scale");
   TLB_CUDA(cudaStreamSynchronize(st));
   // psi follows the moved membrane: its profile I, shifted to the plain total
   if ((s = c->impl->profile_now(c)) != TLB_OK) return s;

@@ -139,19 +139,29 @@ def train(net: WarmStartNet, data, epochs: int, batch: int = 4, lr: float = 1e-3
     return losses
 
 
+def measures(s) -> np.ndarray:
+    """Equilibrium-quality measures of one instance: the mean contact angle
+    of the capsule with the C1/C2 interface (degrees, FP64 read-out of the
+    library) and the capsule's area and volume (FP64 diagnostics)."""
+    d = s.diagnostics()
+    return np.array([s.contact_angle()[0][0], d.area[0], d.volume[0]])
+
+
 def histories(b, max_steps: int, check_every: int, stop_tol: float):
-    """Residual of every instance of batch ``b`` after each chunk of
-    ``check_every`` steps (no instance retires) until every instance has
-    reached ``stop_tol`` once or ``max_steps`` steps; returns [checks][n]."""
-    out = []
+    """Residual and measures of every instance of batch ``b`` after each
+    chunk of ``check_every`` steps (no instance retires) until every
+    instance has reached ``stop_tol`` once or ``max_steps`` steps.  Returns
+    the residuals [checks][n] and the measures [checks][n][3]."""
+    out, meas = [], []
     reached = np.zeros(len(b), dtype=bool)
     done = 0
     while done < max_steps and not reached.all():
         _, r = b.run(check_every, check_every, 0.0)
         out.append(r.copy())
+        meas.append(np.array([measures(b[i]) for i in range(len(b))]))
         reached |= r <= stop_tol
         done += check_every
-    return np.array(out)
+    return np.array(out), np.array(meas)
 
 
 def first_crossing(hist, tol: float, check_every: int):
@@ -165,13 +175,43 @@ def first_crossing(hist, tol: float, check_every: int):
     return out
 
 
+# the equilibrium gate: contact angle within 0.5 degrees, area and volume
+# within 0.1 % of the reference equilibrium
+GATE = (0.5, 1e-3, 1e-3)
+
+
+def within_gate(m, ref) -> np.ndarray:
+    """Whether measures m (..., 3) lie within GATE of the reference ref."""
+    m, ref = np.asarray(m), np.asarray(ref)
+    return ((np.abs(m[..., 0] - ref[..., 0]) <= GATE[0]) & (np.abs(m[..., 1] / ref[..., 1] - 1) <= GATE[1]) &
+            (np.abs(m[..., 2] / ref[..., 2] - 1) <= GATE[2]))
+
+
+def settled(meas, ref, check_every: int):
+    """Steps from which each instance stays within GATE of its reference for
+    every later check (NaN if the last check is outside)."""
+    ok = within_gate(meas, ref[None])  # [checks][n]
+    out = np.full(ok.shape[1], np.nan)
+    for i in range(ok.shape[1]):
+        if not ok[-1, i]:
+            continue
+        bad = np.nonzero(~ok[:, i])[0]
+        out[i] = ((bad[-1] + 2) if bad.size else 1) * check_every
+    return out
+
+
 def compare(net: WarmStartNet, wls, wls_learned=None, max_steps: int = 8000, check_every: int = 250,
-            tols=(1e-4, 5e-5)):
-    """Relaxation of the instances from their plain start and from the
-    learned start (instances ``wls_learned``, default the same), each set as
-    one batch.  Returns the residual histories, the first-crossing steps of
-    every tolerance, the wall time of each relaxation and of the warm-start
-    calls."""
+            tols=(1e-4, 5e-5), ref_steps: int = None):
+    """Relaxation of the instances from their plain start (FP32, for
+    ``ref_steps`` steps, default max_steps) and from the learned start
+    (instances ``wls_learned``, default the same; ``max_steps`` steps), each
+    set as one batch, with the equilibrium gate: the reference equilibrium of
+    an instance is the plain run's last state.  Reported per tolerance: the
+    first residual crossing, counted only where the learned state there is
+    within GATE of the reference; and the steps from which each run's shape
+    stays within GATE of the reference (time to the equilibrium shape: a run
+    counts once it stays within the gate until its end).  Also the wall time
+    of each relaxation and of the warm-start calls."""
     import time
     import torch
     out = {}
@@ -184,26 +224,56 @@ def compare(net: WarmStartNet, wls, wls_learned=None, max_steps: int = 8000, che
                 net.warm_start(b[i], features(wl))
         torch.cuda.synchronize(net.device)
         t_ws = time.perf_counter() - t0
-        h = histories(b, max_steps, check_every, min(tols))
+        n_steps = (ref_steps or max_steps) if not learned else max_steps
+        h, m = histories(b, n_steps, check_every, 0.0)
         torch.cuda.synchronize(net.device)
-        out[name] = {"history": h, "wall_s": time.perf_counter() - t0, "warm_start_s": t_ws,
+        out[name] = {"history": h, "measures": m, "wall_s": time.perf_counter() - t0, "warm_start_s": t_ws,
                      "first": {t: first_crossing(h, t, check_every) for t in tols}}
         del b
         torch.cuda.empty_cache()
-    for t in tols:
-        p, l = out["plain"]["first"][t], out["learned"]["first"][t]
+    ref = out["plain"]["measures"][-1]  # [n][3]
+    for name in ("plain", "learned"):
+        m = out[name]["measures"]
+        out[name]["shape_steps"] = settled(m, ref, check_every)
+        for t in tols:
+            # measures at the first residual crossing, and the gate there
+            f = out[name]["first"][t]
+            at = np.full((len(f), 3), np.nan)
+            for i, v in enumerate(f):
+                if np.isfinite(v):
+                    at[i] = m[int(v) // check_every - 1, i]
+            out[name].setdefault("gate", {})[t] = within_gate(at, ref)
+            out[name].setdefault("dev", {})[t] = np.stack([np.abs(at[:, 0] - ref[:, 0]),
+                                                           np.abs(at[:, 1] / ref[:, 1] - 1),
+                                                           np.abs(at[:, 2] / ref[:, 2] - 1)], 1)
+
+    def ratios(p, l):
         ok = np.isfinite(p) & np.isfinite(l)
-        out[f"ratio_{t:g}"] = {"both": int(ok.sum()), "plain_median": float(np.nanmedian(p)) if np.isfinite(p).any() else None,
-                               "learned_median": float(np.nanmedian(l)) if np.isfinite(l).any() else None,
-                               "median": float(np.median(p[ok] / l[ok])) if ok.any() else None,
-                               "geomean": float(np.exp(np.mean(np.log(p[ok] / l[ok])))) if ok.any() else None}
+        return {"both": int(ok.sum()),
+                "plain_median": float(np.nanmedian(p)) if np.isfinite(p).any() else None,
+                "learned_median": float(np.nanmedian(l)) if np.isfinite(l).any() else None,
+                "median": float(np.median(p[ok] / l[ok])) if ok.any() else None,
+                "geomean": float(np.exp(np.mean(np.log(p[ok] / l[ok])))) if ok.any() else None}
+
+    for t in tols:
+        p, l = out["plain"]["first"][t], out["learned"]["first"][t].copy()
+        g = out["learned"]["gate"][t]
+        dev = out["learned"]["dev"][t]
+        l[~g] = np.nan  # a learned crossing counts only within the gate
+        r = ratios(p, l)
+        r["gated"] = int(g.sum())
+        r["max_dev_angle_deg"] = float(np.nanmax(dev[:, 0])) if np.isfinite(dev[:, 0]).any() else None
+        r["max_dev_area"] = float(np.nanmax(dev[:, 1])) if np.isfinite(dev[:, 1]).any() else None
+        r["max_dev_volume"] = float(np.nanmax(dev[:, 2])) if np.isfinite(dev[:, 2]).any() else None
+        out[f"ratio_{t:g}"] = r
+    out["ratio_shape"] = ratios(out["plain"]["shape_steps"], out["learned"]["shape_steps"])
     return out
 
 
-def experiment(edge: int = 48, n_train: int = 128, n_test: int = 32, relax_steps: int = 15000,
+def experiment(edge: int = 48, n_train: int = 128, n_test: int = 64, relax_steps: int = 15000,
                target_tol: float = 2e-5, max_steps: int = 8000, check_every: int = 250, tols=(1e-4, 5e-5),
                epochs: int = 150, batch: int = 8, lr: float = 1e-3, lam: float = 1.0, seed: int = 0,
-               device="cuda:0", log=print):
+               ref_steps: int = 20000, device="cuda:0", log=print):
     """Time to equilibrium from the plain and from the learned start.
 
     Training instances: sweep seeds 1000.., relaxed in FP32 to the residual
@@ -237,12 +307,18 @@ def experiment(edge: int = 48, n_train: int = 128, n_test: int = 32, relax_steps
     torch.cuda.empty_cache()
     test = [instances(1, seed=5000 + j, edge=edge)[0] for j in range(n_test)]
     test16 = [instances(1, seed=5000 + j, edge=edge, storage="f16")[0] for j in range(n_test)]
-    r = compare(net, test, test16, max_steps, check_every, tols)
+    r = compare(net, test, test16, max_steps, check_every, tols, ref_steps=ref_steps)
+    fin = lambda a: [None if not np.isfinite(v) else int(v) for v in a]  # noqa: E731
     for k in ("plain", "learned"):
         out[k] = {"wall_s": r[k]["wall_s"], "warm_start_s": r[k]["warm_start_s"],
-                  "first": {f"{t:g}": [None if not np.isfinite(v) else int(v) for v in r[k]["first"][t]] for t in tols}}
+                  "first": {f"{t:g}": fin(r[k]["first"][t]) for t in tols},
+                  "shape_steps": fin(r[k]["shape_steps"])}
     for t in tols:
         out[f"ratio_{t:g}"] = r[f"ratio_{t:g}"]
         log(f"tol {t:g}: {r[f'ratio_{t:g}']}")
+    out["ratio_shape"] = r["ratio_shape"]
+    out["gate"] = {"angle_deg": GATE[0], "area_rel": GATE[1], "volume_rel": GATE[2],
+                   "reference": "the plain FP32 run's last state"}
+    log(f"time to the equilibrium shape: {r['ratio_shape']}")
     out["params"] = net.params()
     return out

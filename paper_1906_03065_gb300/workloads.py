@@ -57,6 +57,7 @@ class Params:
     interface_pos: float = 32.0  # flat C1/C2 interface along the last axis
     forcing: str = "edm"        # "edm": exact difference method (the paper); "guo": Guo forcing
     state: str = "populations"  # "populations", or "moments": 11 stored moments per cell (tau = 1)
+    force_form: str = "potential"  # free-energy force: "potential" or "pressure_tensor" (App. A)
 
     @property
     def ncells(self) -> int:

@@ -76,12 +76,14 @@ def test_measures_after_a_run_match_the_oracle_run():
     assert int(ca3[3]) == c3 and abs(ca3[0] - m3) < 0.05
 
 
-@pytest.mark.parametrize("h", [0.0, 3.0])
+@pytest.mark.parametrize("h", [0.37, 3.0])
 def test_contact_angle_closed_form(h):
     """Fluid started as a flat tanh interface phi = tanh((z - z0)/(2 alpha))
     (C1 above, C2 below, no C3): a sphere centred at z0 + h meets it at
     arccos(-h/R); the oracle's read-out of the same state agrees to FP64
-    rounding of the FP32 fields."""
+    rounding of the FP32 fields.  (h = 0 would put icosphere vertices on the
+    plane itself, where phi = 0 up to rounding and whether an edge holds a
+    contact point is decided by the last bit.)"""
     n, R = 64, 20.0
     wl = W.capsule_3d("f32", n=n, level=4, radius=R)
     wl.membranes[0].X = wl.membranes[0].X + np.array([0.31, -0.17, h])

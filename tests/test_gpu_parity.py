@@ -242,3 +242,44 @@ def test_tau1_collide_only_where_it_applies():
         g = _sim(w2).init()
         with pytest.raises(TLBError):
             g.set_tile(13, 8)
+
+
+def test_pressure_tensor_force_2d_f64_one_step_random():
+    """The pressure-tensor force (grad(rho cs^2) - div p - psi grad(kappa_c
+    (psi - I)), App. A; the GPU forms the bulk pressure by eq. PressureV2,
+    the oracle from the printed polynomial of App. A with its Gibbs-Duhem
+    term) from a perturbed random state, against the oracle's same form."""
+    wl = W.small_2d("f64")
+    wl.params.force_form = "pressure_tensor"
+    wl.membranes[0] = W.jitter_nodes(wl.membranes[0], 0.2, seed=1)
+    o = oracle.Oracle(wl, init=False)
+    C0, u0 = W.random_fields(wl.params, seed=4)
+    o.init(C0, u0)
+    rng = np.random.default_rng(5)
+    c, w = o.lattice()
+    P = o.pops() + 1e-3 * rng.standard_normal((3, o.Q, o.N)) * w[None, :, None]
+    o.set_pops(P)
+    g = _sim(wl)
+    g.init(C0, u0)
+    g.set_pops(P)
+    o.step(1)
+    g.step(1)
+    assert np.abs(g.pops() - o.pops()).max() < 1e-12
+    # not the potential form: the two differ at second order
+    wl2 = W.small_2d("f64")
+    wl2.membranes[0] = W.jitter_nodes(wl2.membranes[0], 0.2, seed=1)
+    g2 = _sim(wl2)
+    g2.init(C0, u0)
+    g2.set_pops(P)
+    g2.step(1)
+    assert np.abs(g2.pops() - g.pops()).max() > 1e-9
+
+
+def test_pressure_tensor_force_3d_f32_200_steps():
+    wl = W.small_3d("f32")
+    wl.params.force_form = "pressure_tensor"
+    oracle.set_threads(0)
+    g, o = _sim(wl).init(), oracle.Oracle(wl)
+    g.step(200)
+    o.step(200)
+    _compare_fields(g, o, 1e-4, 1e-4, 1e-4)

@@ -149,7 +149,10 @@ def test_warm_start_of_a_context():
     x = ws.make_input(o.field("phi"), o.field("psi"), feats, 32)[None]
     yo, _ = ws.forward(th, x, c0=C0, levels=3)
     yo = yo[0].numpy()
-    Xr = ws.warm_start_markers(yo, X0, ws.vertex_normals(X0, wl.membranes[0].elems))
+    F = wl.membranes[0].elems
+    Xr = ws.warm_start_markers(yo, X0, ws.vertex_normals(X0, F), F)
+    # the moved membrane encloses the plain start's volume
+    assert abs(ws.enclosed_volume(s.nodes(0), F) / ws.enclosed_volume(X0, F) - 1) < 1e-9
     D = np.abs(Xr - X0).max()
     assert D > 0.05  # the test moves the markers
     assert np.abs(s.nodes(0) - Xr).max() < 5e-3 * D + 1e-5

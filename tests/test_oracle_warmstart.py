@@ -132,3 +132,25 @@ def test_warm_start_composition_pins():
     I_new = np.clip(psi0 + rng.normal(0, 0.05, 300), 0, 1)
     phi, psi = ws.warm_start_fields(rng.normal(0, 0.1, 300), phi0, psi0, I_new)
     assert phi.sum() == pytest.approx(phi0.sum(), abs=1e-10) and psi.sum() == pytest.approx(psi0.sum(), abs=1e-10)
+
+
+def test_enclosed_volume_and_the_volume_projection():
+    """The reference warm start projects the moved markers back to the plain
+    start's enclosed volume: the divergence-theorem volume of the regular
+    icosahedron has its closed form, and the projection restores it."""
+    import math
+    from paper_1906_03065_gb300 import workloads as Wk
+    R = 5.0
+    m = Wk.icosphere(0, R, (12.0, 11.0, 10.0))
+    a = 4 * R / math.sqrt(10 + 2 * math.sqrt(5))
+    assert abs(ws.enclosed_volume(m.X, m.elems) - 5 / 12 * (3 + math.sqrt(5)) * a ** 3) < 1e-10
+    m3 = Wk.icosphere(2, R, (16.0, 16.0, 16.0))
+    E = 32
+    y = np.zeros((16, E, E, E))
+    y[2:5] = np.random.default_rng(0).normal(0.0, 0.3, (3, E, E, E))  # a non-uniform displacement field
+    nrm = ws.vertex_normals(m3.X, m3.elems)
+    X1 = ws.warm_start_markers(y, m3.X, nrm)
+    X2 = ws.warm_start_markers(y, m3.X, nrm, m3.elems)
+    V0 = ws.enclosed_volume(m3.X, m3.elems)
+    assert abs(ws.enclosed_volume(X1, m3.elems) / V0 - 1) > 1e-4  # the displacement changes it
+    assert abs(ws.enclosed_volume(X2, m3.elems) / V0 - 1) < 1e-12
