@@ -300,7 +300,21 @@ tlb_status tlb_autotune(void* ctx, int* tile_variant, int* z_chunk);
  * on the choice beyond rounding. */
 tlb_status tlb_set_tile(void* ctx, int tile_variant, int z_chunk);
 
-/* Number of CUDA kernel launches enqueued by the last tlb_step call. */
+/* Step graphs on (on != 0) or off (the default).  With graphs on, tlb_step
+ * and tlb_run issue runs of 8 steps as one CUDA graph launch, captured once
+ * per population buffer and collide variant from the same kernels the
+ * direct launches use (the results are identical bit for bit); the first
+ * step after markers were set from outside, the first step after
+ * populations were written with moment storage, the steps of
+ * tlb_profile_steps and a remainder below 8 steps run as direct launches.
+ * Turning graphs off releases the captured graphs.  On the 128^3 capsule
+ * the replay measured slower than direct launches (the captured side-stream
+ * kernels lose their stream priority), hence off by default.  Not in the
+ * paper: a launch mechanism of this implementation. */
+tlb_status tlb_set_graphs(void* ctx, int on);
+
+/* Number of CUDA kernel launches enqueued by the last tlb_step call (a
+ * graph replay counts the kernels it holds). */
 long tlb_last_launch_count(void* ctx);
 
 /* Release the context (the arena stays owned by the caller). */
@@ -406,7 +420,10 @@ void tlb_batch_destroy(void* batch);
  * Parameters, in order, per conv: W[tap][ci][co] (tap = (kz*3 + ky)*3 + kx
  * for the input offset (kz-1, ky-1, kx-1)), then b[co]; FP32 on the host.
  * Activations are stored as bf16, the convolutions run on the tensor cores
- * with FP32 accumulation.
+ * with FP32 accumulation: the 3x3x3 convolutions of the forward pass and of
+ * the input gradient on the fifth-generation tensor cores (tcgen05, the
+ * accumulator in tensor memory; the default) or on the warp-level mma.sync
+ * path, the weight gradients and the 1x1x1 convolution on mma.sync.
  * Features (normalised by the caller): kappa_1..3, Skalak G, R / E.
  * Training loss for targets t0, t1 of y0, y1 (FP32 [B][E^3]; for the warm
  * start t0 = s_eq - s0 outside the capsule, 0 inside, and t1 = 0) and marker
@@ -458,6 +475,16 @@ tlb_status tlb_net_train_step(void* net, const void* x_dev, const float* t0_dev,
  * then the equilibrium populations of these fields, as tlb_init_fields.
  * Synchronises. */
 tlb_status tlb_net_warm_start(void* net, void* ctx, const double* feats);
+/* Choose the tensor-core path of the 3x3x3 convolutions: tcgen05 (on != 0,
+ * the default) or mma.sync.  The two agree up to the order of the FP32
+ * accumulation. */
+tlb_status tlb_net_set_tcgen05(void* net, int on);
+/* Synchronise the net's stream and read (then clear) its status word: bit 0
+ * set when a tcgen05 kernel gave up waiting for the tensor core (its
+ * outputs are then not written); TLB_ERR_CUDA in that case.
+ * tlb_net_train_step with loss_out and tlb_net_warm_start check it
+ * themselves. */
+tlb_status tlb_net_status(void* net, unsigned* status);
 /* Kernel launches of the last tlb_net_* call that computes. */
 long tlb_net_launch_count(void* net);
 void tlb_net_destroy(void* net);

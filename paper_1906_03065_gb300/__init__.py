@@ -98,6 +98,8 @@ def lib():
             getattr(L, n).restype = C.c_int
         L.tlb_set_tile.argtypes = [vp, C.c_int, C.c_int]
         L.tlb_set_tile.restype = C.c_int
+        L.tlb_set_graphs.argtypes = [vp, C.c_int]
+        L.tlb_set_graphs.restype = C.c_int
         L.tlb_residual.argtypes = [vp, dp]
         L.tlb_residual.restype = C.c_int
         L.tlb_contact_angle.argtypes = [vp, dp, sz]
@@ -136,6 +138,10 @@ def lib():
             getattr(L, n).restype = C.c_int
         L.tlb_net_launch_count.argtypes = [vp]
         L.tlb_net_launch_count.restype = C.c_long
+        L.tlb_net_set_tcgen05.argtypes = [vp, C.c_int]
+        L.tlb_net_set_tcgen05.restype = C.c_int
+        L.tlb_net_status.argtypes = [vp, C.POINTER(C.c_uint)]
+        L.tlb_net_status.restype = C.c_int
         L.tlb_net_destroy.argtypes = [vp]
         L.tlb_destroy.argtypes = [vp]
         L.tlb_last_error.restype = C.c_char_p
@@ -283,6 +289,9 @@ class Simulation:
 
     def set_tile(self, variant: int, z_chunk: int):
         _check(lib().tlb_set_tile(self.h, int(variant), int(z_chunk)))
+
+    def set_graphs(self, on: bool):
+        _check(lib().tlb_set_graphs(self.h, int(bool(on))))
 
     def launches(self) -> int:
         return lib().tlb_last_launch_count(self.h)
@@ -523,6 +532,14 @@ class WarmStartNet:
         """Replace the plain initial state of ``sim`` by the network's guess."""
         f = np.ascontiguousarray(feats, dtype=np.float64)
         _check(lib().tlb_net_warm_start(self.h, sim.h, _dp(f)))
+
+    def set_tcgen05(self, on: bool):
+        _check(lib().tlb_net_set_tcgen05(self.h, int(bool(on))))
+
+    def status(self) -> int:
+        st = C.c_uint(0)
+        _check(lib().tlb_net_status(self.h, C.byref(st)))
+        return st.value
 
     def launches(self) -> int:
         return lib().tlb_net_launch_count(self.h)

@@ -18,6 +18,7 @@ void set_error(const std::string& msg) { g_err = msg; }
 tlb_status cuda_check(cudaError_t e, const char* what) {
   if (e == cudaSuccess) return TLB_OK;
   g_err = std::string(what) + ": " + cudaGetErrorString(e);
+  cudaGetLastError();  // reported here: not left for the caller's next CUDA call
   return TLB_ERR_CUDA;
 }
 
@@ -708,6 +709,17 @@ tlb_status tlb_set_tile(void* ctx, int tile_variant, int z_chunk) {
   }
   c->tile_variant = tile_variant;
   c->tiles_zc = z_chunk;
+  return TLB_OK;
+}
+
+tlb_status tlb_set_graphs(void* ctx, int on) {
+  Ctx* c = (Ctx*)ctx;
+  if (!c) { set_error("ctx is NULL"); return TLB_ERR_ARG; }
+  if (!on) {
+    TLB_CUDA(cudaStreamSynchronize(c->stream));
+    c->drop_graphs();
+  }
+  c->graphs = on != 0;
   return TLB_OK;
 }
 

@@ -146,10 +146,36 @@ struct Ctx {
   PhaseEvents* prof = nullptr;  // non-null while tlb_profile_steps runs
   double prof_ms[4] = {0, 0, 0, 0};
   ImplBase* impl = nullptr;
+  // Step graphs: GRAPH_STEPS steps captured from the context's streams and
+  // replayed as one graph launch, one graph per starting population buffer;
+  // a graph holds the collide variant and z chunk it was captured with.
+  static constexpr int GRAPH_STEPS = 8;
+  bool graphs = false;         // replay captured steps where a step qualifies
+  bool capturing = false;      // the steps being issued are captured
+  cudaGraphExec_t gexec[2] = {nullptr, nullptr};
+  // graphs are captured on and replayed from a stream of the context's own
+  // (the caller's stream may be the legacy default stream, which cannot be
+  // captured), ordered after and before the caller's stream by two events
+  cudaStream_t gstream = nullptr;
+  cudaEvent_t ev_gin = nullptr, ev_gout = nullptr;
+  int gsig[2][2] = {{-1, -1}, {-1, -1}};  // (tile_variant, tiles_zc) of each graph
+  long glaunch[2] = {0, 0};    // kernel launches one replay makes
+  void drop_graphs() {
+    for (int k = 0; k < 2; ++k) {
+      if (gexec[k]) cudaGraphExecDestroy(gexec[k]);
+      gexec[k] = nullptr;
+      gsig[k][0] = gsig[k][1] = -1;
+    }
+  }
 
   template <class T> T* ptr(const Region& r) const { return reinterpret_cast<T*>(base + r.off); }
 
   ~Ctx() {
+    if (gstream) cudaStreamSynchronize(gstream);
+    drop_graphs();
+    if (ev_gin) cudaEventDestroy(ev_gin);
+    if (ev_gout) cudaEventDestroy(ev_gout);
+    if (gstream) cudaStreamDestroy(gstream);
     if (side) cudaStreamSynchronize(side);
     if (side2) cudaStreamSynchronize(side2);
     if (ev_fork) cudaEventDestroy(ev_fork);

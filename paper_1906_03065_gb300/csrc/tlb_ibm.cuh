@@ -367,6 +367,7 @@ struct FaceDist {
   Real d00, d01, d11, i00, i11, ibc, iden;
   bool tri;
   static constexpr int NC = 22;  // constants kept in shared memory
+  static constexpr int NCP = 24; // row stride of the shared copy (16-byte rows for FP32)
   __device__ __forceinline__ FaceDist() {}
   __device__ __forceinline__ void store(Real* p) const {
     const Real v[NC] = {A.x,  A.y,  A.z,  B.x,  B.y,  B.z,  ab.x, ab.y, ab.z, ac.x, ac.y,
@@ -374,6 +375,32 @@ struct FaceDist {
     for (int i = 0; i < NC; ++i) p[i] = v[i];
   }
   __device__ __forceinline__ static FaceDist load(const Real* p, bool is_tri) {
+    if constexpr (sizeof(Real) == 4) {  // six 16-byte loads of the padded row
+      float v[NCP];
+#pragma unroll
+      for (int i = 0; i < NCP / 4; ++i) {
+        const float4 q = reinterpret_cast<const float4*>(p)[i];
+        v[4 * i] = q.x;
+        v[4 * i + 1] = q.y;
+        v[4 * i + 2] = q.z;
+        v[4 * i + 3] = q.w;
+      }
+      FaceDist f;
+      f.A = mk<Real>(v[0], v[1], v[2]);
+      f.B = mk<Real>(v[3], v[4], v[5]);
+      f.ab = mk<Real>(v[6], v[7], v[8]);
+      f.ac = mk<Real>(v[9], v[10], v[11]);
+      f.bc = mk<Real>(v[12], v[13], v[14]);
+      f.d00 = v[15];
+      f.d01 = v[16];
+      f.d11 = v[17];
+      f.i00 = v[18];
+      f.i11 = v[19];
+      f.ibc = v[20];
+      f.iden = v[21];
+      f.tri = is_tri;
+      return f;
+    }
     FaceDist f;
     f.A = mk<Real>(p[0], p[1], p[2]);
     f.B = mk<Real>(p[3], p[4], p[5]);
@@ -442,7 +469,7 @@ struct FaceDist {
 // ties going to the lowest element index.
 constexpr int MAXG = 12;  // generators (and faces) per feature
 constexpr int SCAT_W = 4;       // slices per lane per round
-constexpr int SCAT_SPLIT = 4;   // warps sharing one group of 32 features (round r goes to r % SCAT_SPLIT)
+constexpr int SCAT_SPLIT = 8;   // warps sharing one group of 32 features (round r goes to r % SCAT_SPLIT)
 // warps per block (every lane sweeps one feature): FP64 halves them to keep
 // the shared memory under the static limit
 template <class Real> constexpr int scatter_warps() { return sizeof(Real) == 4 ? 4 : 2; }
@@ -454,7 +481,7 @@ struct ScatterWarp {
   Real gk[32][MAXG];            // 1 / generator component along the slice axis
   Real ga[32][MAXG];            // generator components along the two other axes
   Real gb[32][MAXG];
-  Real fd[32][FaceDist<Real>::NC];  // distance constants of the offered face
+  alignas(16) Real fd[32][FaceDist<Real>::NCP];  // distance constants of the offered face
   int4 sl[32][SCAT_W];          // the round's slices: a0, b0, width, cumulative cells
   int4 ft[32][2];               // origin cell (wrapped) and packed axes; face, first slice
 };
@@ -1359,32 +1386,56 @@ __device__ __forceinline__ void interp_advect_body(const IBArgs<typename Prec<MO
     cz[h] = ok ? wrap_coord(pz, G.nz) : 0;
   }
   Real U[3] = {0, 0, 0};
+  if (a.M) {
 #pragma unroll
-  for (int h = 0; h < 2; ++h) {
-    const Nbr<L> nb(G, cx[h], cy[h], cz[h]);
-    const long long self = nb.self;
-    Real r = 0, j[3] = {0, 0, 0};
+    for (int h = 0; h < 2; ++h) {
+      const Nbr<L> nb(G, cx[h], cy[h], cz[h]);
+      const long long self = nb.self;
+      Real r = 0, j[3] = {0, 0, 0};
 #pragma unroll
-    for (int i = 0; i < L::Q; ++i) {
-      Real fi;
-      if (a.M) {
+      for (int i = 0; i < L::Q; ++i) {
         EqCell<L, Real> e;
         e.load_f(a.M, G.P32, nb.src(i));
-        fi = e.f(nb.bounce(i) ? L::opp(i) : i);
-      } else {
-        fi = to_real(lo[nb.off(i, plane_f<L>(i), plane_f<L>(L::opp(i)), G.P32)]);
+        const Real fi = e.f(nb.bounce(i) ? L::opp(i) : i);
+        r += fi;
+        if (L::cx(i)) j[0] += L::cx(i) > 0 ? fi : -fi;
+        if (L::cy(i)) j[1] += L::cy(i) > 0 ? fi : -fi;
+        if (L::cz(i)) j[2] += L::cz(i) > 0 ? fi : -fi;
       }
-      r += fi;
-      if (L::cx(i)) j[0] += L::cx(i) > 0 ? fi : -fi;
-      if (L::cy(i)) j[1] += L::cy(i) > 0 ? fi : -fi;
-      if (L::cz(i)) j[2] += L::cz(i) > 0 ? fi : -fi;
-    }
-    Real ft[3];
+      Real ft[3];
 #pragma unroll
-    for (int d = 0; d < 3; ++d) ft[d] = a.ftot[d * G.P + self];
-    Real rho = Real(1) + r;
-    if (w[h] != Real(0))
-      for (int d = 0; d < 3; ++d) U[d] += w[h] * (j[d] + Real(0.5) * ft[d]) / rho;
+      for (int d = 0; d < 3; ++d) ft[d] = a.ftot[d * G.P + self];
+      Real rho = Real(1) + r;
+      if (w[h] != Real(0))
+        for (int d = 0; d < 3; ++d) U[d] += w[h] * (j[d] + Real(0.5) * ft[d]) / rho;
+    }
+  } else {
+    // the populations of both support cells (and their forces) are all
+    // requested before the first sum, so their latencies overlap
+    Real fv[2][L::Q], ft[2][3];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const Nbr<L> nb(G, cx[h], cy[h], cz[h]);
+#pragma unroll
+      for (int i = 0; i < L::Q; ++i) fv[h][i] = to_real(__ldg(lo + nb.off(i, plane_f<L>(i), plane_f<L>(L::opp(i)), G.P32)));
+#pragma unroll
+      for (int d = 0; d < 3; ++d) ft[h][d] = __ldg(a.ftot + d * G.P + nb.self);
+    }
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      Real r = 0, j[3] = {0, 0, 0};
+#pragma unroll
+      for (int i = 0; i < L::Q; ++i) {
+        const Real fi = fv[h][i];
+        r += fi;
+        if (L::cx(i)) j[0] += L::cx(i) > 0 ? fi : -fi;
+        if (L::cy(i)) j[1] += L::cy(i) > 0 ? fi : -fi;
+        if (L::cz(i)) j[2] += L::cz(i) > 0 ? fi : -fi;
+      }
+      Real rho = Real(1) + r;
+      if (w[h] != Real(0))
+        for (int d = 0; d < 3; ++d) U[d] += w[h] * (j[d] + Real(0.5) * ft[h][d]) / rho;
+    }
   }
   for (int d = 0; d < 3; ++d)
     for (int o = 16; o > 0; o >>= 1) U[d] += __shfl_xor_sync(0xffffffffu, U[d], o);

@@ -420,7 +420,98 @@ struct Impl : ImplBase {
     return TLB_OK;
   }
 
+  // n steps; runs of GRAPH_STEPS steps replay a captured graph where the
+  // step qualifies (see graph_ready)
   tlb_status step(Ctx* c, long n) override {
+    while (n > 0) {
+      if (n >= Ctx::GRAPH_STEPS && graph_ready(c)) {
+        tlb_status st = replay(c);
+        if (st != TLB_OK) return st;
+        n -= Ctx::GRAPH_STEPS;
+        continue;
+      }
+      // direct launches until a step qualifies, the rest at the end
+      const long k = (n >= Ctx::GRAPH_STEPS && c->graphs && !c->prof) ? 1 : n;
+      tlb_status st = step_direct(c, k);
+      if (st != TLB_OK) return st;
+      n -= k;
+    }
+    return TLB_OK;
+  }
+
+  // A step replays from a graph when it launches the same work every time:
+  // no phase profile, no markers set from outside since the last step (their
+  // box is rebuilt first) and, with moment storage, the state in the stored
+  // moments (the first step after populations were written rebuilds them).
+  bool graph_ready(Ctx* c) const {
+    return c->graphs && !c->prof && !c->box_stale && !(c->moments() && c->state_in_pops);
+  }
+
+  // Launch the graph of the current buffer, capturing it first if missing or
+  // captured with another collide variant.  A replay advances the state by
+  // GRAPH_STEPS (an even number: the buffer index comes back).
+  tlb_status replay(Ctx* c) {
+    const int k = c->cur;
+    if (!c->gstream) {
+      TLB_CUDA(cudaStreamCreateWithFlags(&c->gstream, cudaStreamNonBlocking));
+      TLB_CUDA(cudaEventCreateWithFlags(&c->ev_gin, cudaEventDisableTiming));
+      TLB_CUDA(cudaEventCreateWithFlags(&c->ev_gout, cudaEventDisableTiming));
+    }
+    cudaStream_t user = c->stream;
+    TLB_CUDA(cudaEventRecord(c->ev_gin, user));
+    TLB_CUDA(cudaStreamWaitEvent(c->gstream, c->ev_gin, 0));
+    if (!c->gexec[k] || c->gsig[k][0] != c->tile_variant || c->gsig[k][1] != c->tiles_zc) {
+      if (c->gexec[k]) {  // (after its last replay has finished)
+        TLB_CUDA(cudaStreamSynchronize(c->gstream));
+        cudaGraphExecDestroy(c->gexec[k]);
+        c->gexec[k] = nullptr;
+      }
+      // capture without executing: the host-side state is put back after
+      const int cur0 = c->cur;
+      const long t0 = c->t, l0 = c->launches;
+      const bool sp0 = c->state_in_pops, ps0 = c->pops_stale;
+      TLB_CUDA(cudaStreamBeginCapture(c->gstream, cudaStreamCaptureModeThreadLocal));
+      c->capturing = true;
+      c->stream = c->gstream;
+      tlb_status st = step_direct(c, Ctx::GRAPH_STEPS);
+      c->stream = user;
+      c->capturing = false;
+      cudaGraph_t g = nullptr;
+      const cudaError_t ce = cudaStreamEndCapture(c->gstream, &g);
+      c->glaunch[k] = c->launches - l0;
+      c->cur = cur0;
+      c->t = t0;
+      c->launches = l0;
+      c->state_in_pops = sp0;
+      c->pops_stale = ps0;
+      if (st == TLB_OK) st = cuda_check(ce, "step graph capture");
+      if (st == TLB_OK) st = cuda_check(cudaGraphInstantiate(&c->gexec[k], g, 0), "step graph instantiate");
+      if (g) cudaGraphDestroy(g);
+      if (st != TLB_OK) {
+        c->gexec[k] = nullptr;
+        c->graphs = false;  // direct launches from here on
+        cudaEventRecord(c->ev_interp, user);
+        return st;
+      }
+      c->gsig[k][0] = c->tile_variant;
+      c->gsig[k][1] = c->tiles_zc;
+    }
+    TLB_CUDA(cudaGraphLaunch(c->gexec[k], c->gstream));
+    TLB_CUDA(cudaEventRecord(c->ev_gout, c->gstream));
+    TLB_CUDA(cudaStreamWaitEvent(user, c->ev_gout, 0));
+    // the events recorded inside the capture stand for graph nodes: the one
+    // a direct step waits on before recording it is recorded again here
+    TLB_CUDA(cudaEventRecord(c->ev_interp, user));
+    c->launches += c->glaunch[k];
+    c->t += Ctx::GRAPH_STEPS;
+    if (c->moments()) {
+      c->state_in_pops = false;
+      c->pops_stale = true;
+    }
+    return TLB_OK;
+  }
+
+  tlb_status step_direct(Ctx* c, long n) {
     cudaStream_t s = c->stream;
     const long long N = c->N;
     tlb_status st;
@@ -445,7 +536,9 @@ struct Impl : ImplBase {
         TLB_CUDA(cudaEventRecord(c->ev_fork, s));
         TLB_CUDA(cudaStreamWaitEvent(c->side, c->ev_fork, 0));
         TLB_CUDA(cudaStreamWaitEvent(c->side2, c->ev_fork, 0));
-        if (pipe) TLB_CUDA(cudaStreamWaitEvent(c->side2, c->ev_interp, 0));  // the previous advection
+        // the previous advection (a graph's first step follows the whole
+        // previous launch on the caller's stream instead)
+        if (pipe && !(c->capturing && k == 0)) TLB_CUDA(cudaStreamWaitEvent(c->side2, c->ev_interp, 0));
         if (box_on_side && (st = snapshot_box(c, ia, c->side, false)) != TLB_OK) return st;
         if ((st = ibm_positions(c, ia, c->side)) != TLB_OK) return st;
         if ((st = ibm_bins(c, ia, c->side2)) != TLB_OK) return st;

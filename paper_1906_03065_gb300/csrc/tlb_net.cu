@@ -21,6 +21,7 @@
 #include <vector>
 
 #include "tlb_ctx.h"
+#include "tlb_umma.cuh"
 
 typedef __nv_bfloat16 bf16;
 
@@ -250,6 +251,155 @@ __global__ void __launch_bounds__(128) k_conv3(const bf16* __restrict__ in, int 
         }
       }
     }
+}
+
+// 3x3x3 convolution on the fifth-generation tensor cores (tcgen05): a CTA
+// computes ZB planes of 8 (x) x 16 (y) output voxels, one M = 128 GEMM tile
+// per plane (row r: x = r % 8, y = r / 8), for BN output channels, the ZB
+// accumulators side by side in tensor memory.  Per chunk of 16 input
+// channels the input brick with its halo of 1 (10 x 18 x (ZB + 2) voxels,
+// zero outside the volume) and the chunk's weights of all 27 taps are copied
+// into shared memory (cp.async, two stages: the next chunk's copy runs under
+// this chunk's products), laid out as K-major core matrices:
+//   input   A[kh][voxel][8 channels]  (voxel = (z HY + y) HX + x),
+//   weights B[kh][tap BN + n][8 channels].
+// A tap's operand is then a strided view of the staged brick: its 16 row
+// groups of 8 voxels (one y row each) lie HX voxels apart, so one
+// descriptor per tap and plane serves, and one thread issues 27 ZB products
+// of 128 x BN x 16 per chunk.  The epilogue reads each warp's 32 rows back
+// from tensor memory, adds the bias, applies relu and stores channels-last.
+// Waits on the tensor core give up after a bounded number of polls (status
+// bit 1 then) and the tensor memory is freed on every path.
+constexpr int TC_HX = 10, TC_HY = 18;
+template <int BN, int ZB>
+constexpr int tc_stage_bytes() { return 2 * TC_HX * TC_HY * (ZB + 2) * 16 + 2 * 27 * BN * 16; }
+template <int BN, int ZB>
+constexpr int tc_smem() { return 2 * tc_stage_bytes<BN, ZB>() + 32; }
+
+template <int BN, int ZB, bool RELU>
+__global__ void __launch_bounds__(128) k_conv3_tc(const bf16* __restrict__ in, int Ci, int El, int nbatch,
+                                                  const bf16* __restrict__ Wk, const float* __restrict__ bias,
+                                                  int Co, void* __restrict__ out, unsigned* __restrict__ status) {
+  constexpr int HX = TC_HX, HY = TC_HY, HZ = ZB + 2, HV = HX * HY * HZ;
+  constexpr int ABYTES = 2 * HV * 16, STAGE = tc_stage_bytes<BN, ZB>();
+  constexpr int NCOL = umma::tmem_cols(ZB * BN);
+  constexpr unsigned IDESC = umma::idesc_bf16<128, BN>();
+  constexpr long POLL = 1L << 22;
+  extern __shared__ __align__(128) unsigned char smem[];
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smem + 2 * STAGE);
+  unsigned* tslot = reinterpret_cast<unsigned*>(smem + 2 * STAGE + 16);
+  const int bpx = (El + 7) / 8, bpy = (El + 15) / 16, bpz = (El + ZB - 1) / ZB;
+  int bid = blockIdx.x;
+  const int bx = bid % bpx;
+  bid /= bpx;
+  const int by = bid % bpy;
+  bid /= bpy;
+  const int bz = bid % bpz;
+  const int b = bid / bpz;
+  if (b >= nbatch) return;
+  const int x0 = bx * 8, y0 = by * 16, z0 = bz * ZB, n0 = blockIdx.y * BN;
+  const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31;
+  const int K = 27 * Ci, nck = Ci / 16;
+
+  if (w == 0) umma::tmem_alloc(tslot, NCOL);
+  if (tid == 0) {
+    umma::mbar_init(&bar[0], 1);
+    umma::mbar_init(&bar[1], 1);
+  }
+  umma::fence_proxy_async();
+  umma::fence_before_sync();
+  __syncthreads();
+  umma::fence_after_sync();
+  const unsigned tmem = *tslot;
+
+  auto stage = [&](int s, int ck) {
+    unsigned char* As = smem + s * STAGE;
+    unsigned char* Bs = As + ABYTES;
+    const int ci0 = ck * 16;
+    for (int i = tid; i < 2 * HV; i += 128) {
+      const int v = i >> 1, kh = i & 1;
+      const int X = x0 - 1 + v % HX, Y = y0 - 1 + (v / HX) % HY, Z = z0 - 1 + v / (HX * HY);
+      const bool ok = X >= 0 && X < El && Y >= 0 && Y < El && Z >= 0 && Z < El;
+      const bf16* src = ok ? in + ((((long long)b * El + Z) * El + Y) * El + X) * Ci + ci0 + kh * 8 : in;
+      umma::cp16(As + (kh * HV + v) * 16, src, ok);
+    }
+    for (int i = tid; i < 2 * 27 * BN; i += 128) {
+      const int row = i >> 1, kh = i & 1, tap = row / BN, n = row % BN;
+      umma::cp16(Bs + (kh * 27 * BN + row) * 16, Wk + (long long)(n0 + n) * K + tap * Ci + ci0 + kh * 8, true);
+    }
+  };
+
+  bool ok = true;
+  stage(0, 0);
+  umma::cp_commit();
+  for (int ck = 0; ck < nck; ++ck) {
+    const int s = ck & 1;
+    if (ck + 1 < nck) {
+      // the other stage was read by the products of chunk ck - 1
+      if (ck >= 1 && ok) ok = umma::mbar_wait(&bar[s ^ 1], ((ck - 1) >> 1) & 1, POLL);
+      stage(s ^ 1, ck + 1);
+      umma::cp_commit();
+      umma::cp_wait<1>();
+    } else {
+      umma::cp_wait<0>();
+    }
+    umma::fence_proxy_async();
+    __syncthreads();
+    if (tid == 0 && ok) {
+      umma::fence_after_sync();
+      const unsigned As = umma::smem_u32(smem + s * STAGE), Bs = As + ABYTES;
+#pragma unroll 1
+      for (int zp = 0; zp < ZB; ++zp)
+#pragma unroll 1
+        for (int tap = 0; tap < 27; ++tap) {
+          const int dz = tap / 9, dy = (tap / 3) % 3, dx = tap % 3;
+          const uint64_t ad = umma::desc(As + (((zp + dz) * HY + dy) * HX + dx) * 16, HV * 16, HX * 16);
+          const uint64_t bd = umma::desc(Bs + tap * BN * 16, 27 * BN * 16, 128);
+          umma::mma_bf16(tmem + zp * BN, ad, bd, IDESC, ck > 0 || tap > 0);
+        }
+      umma::commit(&bar[s]);
+    }
+  }
+  if (ok) ok = umma::mbar_wait(&bar[(nck - 1) & 1], ((nck - 1) >> 1) & 1, POLL);
+  if (!ok) atomicOr(status, 1u);
+  umma::fence_after_sync();
+  if (__all_sync(0xffffffffu, ok)) {
+    const int r = 32 * w + lane, X = x0 + r % 8, Y = y0 + r / 8;
+    for (int zp = 0; zp < ZB; ++zp) {
+      const int Z = z0 + zp;
+      const bool in_vol = X < El && Y < El && Z < El;
+      const long long v = (((long long)b * El + Z) * El + Y) * El + X;
+#pragma unroll 1
+      for (int j0 = 0; j0 < BN; j0 += 16) {
+        float o[16];
+        umma::ld16(tmem + ((unsigned)(32 * w) << 16) + zp * BN + j0, o);
+        if (!in_vol) continue;
+        const int n = n0 + j0;
+        if (bias)
+#pragma unroll
+          for (int i = 0; i < 16; ++i) o[i] += bias[n + i];
+        if (RELU) {
+          uint4 pk[2];
+          unsigned* u = reinterpret_cast<unsigned*>(pk);
+#pragma unroll
+          for (int i = 0; i < 8; ++i) {
+            __nv_bfloat162 h = __floats2bfloat162_rn(fmaxf(o[2 * i], 0.f), fmaxf(o[2 * i + 1], 0.f));
+            u[i] = *reinterpret_cast<unsigned*>(&h);
+          }
+          uint4* dst = reinterpret_cast<uint4*>(static_cast<bf16*>(out) + v * Co + n);
+          dst[0] = pk[0];
+          dst[1] = pk[1];
+        } else {
+          float4* dst = reinterpret_cast<float4*>(static_cast<float*>(out) + v * Co + n);
+#pragma unroll
+          for (int i = 0; i < 4; ++i) dst[i] = make_float4(o[4 * i], o[4 * i + 1], o[4 * i + 2], o[4 * i + 3]);
+        }
+      }
+    }
+  }
+  umma::fence_before_sync();
+  __syncthreads();
+  if (w == 0) umma::tmem_free(tmem, NCOL);
 }
 
 // Shared-memory 8x8 b16 matrices, transposed on load (ldmatrix .trans): lane
@@ -858,6 +1008,8 @@ struct Net {
   Ten x, enc_a[4], enc_e[4], enc_p[4], dec_cat[4], dec_b[4], dec_d[4];
   long adam_t = 0;
   long launches = 0;
+  bool tc = true;  // 3x3x3 convolutions on tcgen05 (else mma.sync)
+  unsigned* status() const { return reinterpret_cast<unsigned*>(base + o_misc + 64 * 8); }
 
   template <class T> T* at(size_t off) const { return reinterpret_cast<T*>(base + off); }
   long long vox(int level, int B) const {
@@ -960,7 +1112,7 @@ void plan(Net& n) {
   n.o_gy = take((size_t)n.vox(0, B) * YC * 4);
   n.o_part = take(n.n_part * 4);
   n.o_lpart = take((size_t)(nb(n.vox(0, B), 256) + (size_t)B * nb(d.max_nodes, 256) + 1024) * 8);
-  n.o_misc = take(64 * 8);
+  n.o_misc = take(72 * 8);  // FP64 sums; the status word at double 64
   n.bytes = off;
 }
 
@@ -986,9 +1138,27 @@ tlb_status launch_conv3_t(Net* n, const bf16* in, int Ci, int El, int B, const b
   return TLB_OK;
 }
 
+template <int BN, int ZB, bool RELU>
+tlb_status launch_conv3_tc_t(Net* n, const bf16* in, int Ci, int El, int B, const bf16* Wk, const float* bias, int Co,
+                             void* out) {
+  const long long bricks = (long long)((El + 7) / 8) * ((El + 15) / 16) * ((El + ZB - 1) / ZB) * B;
+  constexpr int sm = tc_smem<BN, ZB>();
+  TLB_CUDA(cudaFuncSetAttribute(k_conv3_tc<BN, ZB, RELU>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
+  k_conv3_tc<BN, ZB, RELU><<<dim3((unsigned)bricks, Co / BN), 128, sm, n->stream>>>(in, Ci, El, B, Wk, bias, Co, out,
+                                                                                     n->status());
+  NET_LAUNCHED(n, "k_conv3_tc");
+  return TLB_OK;
+}
+
 template <bool RELU>
 tlb_status launch_conv(Net* n, const bf16* in, int Ci, int El, long long nvox, int taps, const bf16* Wk,
                        const float* bias, int Co, void* out) {
+  if (taps == 27 && n->tc) {  // tensor memory accumulators; columns per CTA: 64, 32 or 16
+    const int B = (int)(nvox / ((long long)El * El * El));
+    if (Co % 64 == 0) return launch_conv3_tc_t<64, 4, RELU>(n, in, Ci, El, B, Wk, bias, Co, out);
+    if (Co % 32 == 0) return launch_conv3_tc_t<32, 4, RELU>(n, in, Ci, El, B, Wk, bias, Co, out);
+    return launch_conv3_tc_t<16, 4, RELU>(n, in, Ci, El, B, Wk, bias, Co, out);
+  }
   if (taps == 27) {  // brick-tiled direct convolution; columns per CTA: 32 or 16
     const int B = (int)(nvox / ((long long)El * El * El));
     if (Co % 32 == 0) return launch_conv3_t<32, RELU>(n, in, Ci, El, B, Wk, bias, Co, out);
@@ -1324,6 +1494,34 @@ static tlb_status take_input(Net* n, const void* x_dev, int batch) {
   return TLB_OK;
 }
 
+// The status word the tensor-core kernels set when a wait gave up: read
+// (synchronising the stream) and cleared.
+static tlb_status read_status(Net* n, unsigned* out) {
+  unsigned h = 0;
+  TLB_CUDA(cudaMemcpyAsync(&h, n->status(), 4, cudaMemcpyDeviceToHost, n->stream));
+  TLB_CUDA(cudaStreamSynchronize(n->stream));
+  if (h) TLB_CUDA(cudaMemsetAsync(n->status(), 0, 4, n->stream));
+  if (out) *out = h;
+  if (h) {
+    set_error("net: a tensor-core wait gave up (status " + std::to_string(h) + ")");
+    return TLB_ERR_CUDA;
+  }
+  return TLB_OK;
+}
+
+tlb_status tlb_net_status(void* net, unsigned* status) {
+  Net* n = (Net*)net;
+  if (!n) { set_error("net is NULL"); return TLB_ERR_ARG; }
+  return read_status(n, status);
+}
+
+tlb_status tlb_net_set_tcgen05(void* net, int on) {
+  Net* n = (Net*)net;
+  if (!n) { set_error("net is NULL"); return TLB_ERR_ARG; }
+  n->tc = on != 0;
+  return TLB_OK;
+}
+
 tlb_status tlb_net_forward(void* net, const void* x_dev, int batch, float* y_dev) {
   Net* n = (Net*)net;
   if (!n) { set_error("net is NULL"); return TLB_ERR_ARG; }
@@ -1362,7 +1560,9 @@ tlb_status tlb_net_train_step(void* net, const void* x_dev, const float* dphi_de
                                                                n->at<float>(n->o_m), n->at<float>(n->o_v),
                                                                (long long)n->nparam, (float)lr, b1, b2, 1e-8f, c1, c2);
   NET_LAUNCHED(n, "k_adam");
-  return refresh_weights(n);
+  s = refresh_weights(n);
+  if (s == TLB_OK && loss_out) s = read_status(n, nullptr);
+  return s;
 }
 
 static tlb_status check_ctx(Net* n, Ctx* c) {
@@ -1455,6 +1655,7 @@ tlb_status tlb_net_warm_start(void* net, void* ctx, const double* feats) {
   k_ws_fields<<<nb(c->N, 256), 256, 0, st>>>(c->ptr<float>(c->L.rho), phi, psi, I, y, c->N, tot, tot + 4);
   NET_LAUNCHED(n, "k_ws_fields");
   TLB_CUDA(cudaStreamSynchronize(st));
+  if ((s = read_status(n, nullptr)) != TLB_OK) return s;
   return c->impl->init_from_moments(c);
 }
 

@@ -76,6 +76,35 @@ def test_forward_matches_oracle():
     assert net.launches() > 0
 
 
+@pytest.mark.parametrize("c0,lv,e", [(16, 3, 16), (48, 2, 24)])
+def test_tcgen05_convolutions_match_the_mma_sync_path(c0, lv, e):
+    """The 3x3x3 convolutions on tcgen05 (tensor-memory accumulators) against
+    the mma.sync path on the same bf16 operands: the two differ only in the
+    order of the FP32 accumulation (and the bf16 roundings that follows).
+    Channel counts 16..192 take every column tile (16, 32, 64); edges 24, 12,
+    16, 8, 4 leave ragged bricks."""
+    import torch
+    rng = np.random.default_rng(5)
+    th = _theta(7, c0, lv)
+    x = _to_gpu_x(_inputs(rng, 2, e))
+    B, n = 2, 10
+    dphi = torch.from_numpy(rng.normal(0, 0.05, (B, e ** 3)).astype(np.float32)).cuda()
+    dpsi = torch.from_numpy(rng.normal(0, 0.05, (B, e ** 3)).astype(np.float32)).cuda()
+    out = []
+    for tc in (False, True):
+        net = _net(edge=e, base_channels=c0, levels=lv, max_batch=2, max_nodes=0)
+        net.set_tcgen05(tc)
+        net.set_params(th)
+        y = net.forward(x).cpu().numpy()
+        L = net.train_step(x, dphi, dpsi, None, None, None, lam=0.0, lr=1e-3, update=False)
+        assert net.status() == 0
+        out.append((y, L, net.grads()))
+    (ya, La, ga), (yb, Lb, gb) = out
+    assert _relerr(yb, ya) < 3e-3
+    assert Lb == pytest.approx(La, rel=1e-3)
+    assert _relerr(gb, ga) < 1e-2
+
+
 def test_gradients_and_adam_match_oracle():
     import torch
     rng = np.random.default_rng(2)
