@@ -529,30 +529,40 @@ def main():
         x = torch.zeros((B, E ** 3, 16), dtype=torch.bfloat16, device=dev)
         tg = torch.zeros((B, E ** 3), dtype=torch.float32, device=dev)
         a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        net.forward(x)
-        net.train_step(x, tg, tg, lr=0.0)
-        torch.cuda.synchronize(dev)
-        reps = 10
-        a0.record(net.stream)
-        for _ in range(reps):
-            net.forward(x)
-        a1.record(net.stream)
-        torch.cuda.synchronize(dev)
-        ms_f = a0.elapsed_time(a1) / reps
-        a0.record(net.stream)
-        for _ in range(reps):
-            net.train_step(x, tg, tg, lr=0.0)
-        a1.record(net.stream)
-        torch.cuda.synchronize(dev)
-        ms_t = a0.elapsed_time(a1) / reps
         bf = peaks["bf16_tflops"] if peaks else 1900.0
-        net_line = {"edge": E, "batch": B, "params": net.n_params, "kernel": "k_conv3/k_wgrad3 (mma.sync bf16, brick-tiled)",
-                    "forward_ms": ms_f, "train_step_ms": ms_t,
+
+        def net_times(mode):
+            net.set_tcgen05(mode)
+            net.forward(x)
+            net.train_step(x, tg, tg, lr=0.0)
+            torch.cuda.synchronize(dev)
+            reps = 10
+            a0.record(net.stream)
+            for _ in range(reps):
+                net.forward(x)
+            a1.record(net.stream)
+            torch.cuda.synchronize(dev)
+            ms_f = a0.elapsed_time(a1) / reps
+            a0.record(net.stream)
+            for _ in range(reps):
+                net.train_step(x, tg, tg, lr=0.0)
+            a1.record(net.stream)
+            torch.cuda.synchronize(dev)
+            ms_t = a0.elapsed_time(a1) / reps
+            assert net.status() == 0
+            return {"forward_ms": ms_f, "train_step_ms": ms_t,
                     "forward_tflops": B * f_fwd / (ms_f / 1e3) / 1e12,
-                    "train_tflops": B * f_train / (ms_t / 1e3) / 1e12, "peak_bf16_tflops": bf,
+                    "train_tflops": B * f_train / (ms_t / 1e3) / 1e12,
                     "forward_frac": B * f_fwd / (ms_f / 1e3) / 1e12 / bf,
-                    "train_frac": B * f_train / (ms_t / 1e3) / 1e12 / bf,
-                    "peak_source": "measured" if peaks else "fallback"}
+                    "train_frac": B * f_train / (ms_t / 1e3) / 1e12 / bf}
+
+        legacy = net_times(0)
+        net_line = {"edge": E, "batch": B, "params": net.n_params,
+                    "kernel": "k_conv3_tma: 3x3x3 convolutions (forward and data gradient) on tcgen05, operands by "
+                              "TMA, accumulators in tensor memory; k_wgrad3 (mma.sync) for the weight gradients",
+                    **net_times(2), "peak_bf16_tflops": bf,
+                    "peak_source": "measured" if peaks else "fallback",
+                    "mma_sync": {"kernel": "k_conv3 / k_wgrad3 (mma.sync bf16, brick-tiled)", **legacy}}
         del net, x
         torch.cuda.empty_cache()
         if not args.no_warmstart:

@@ -422,8 +422,9 @@ void tlb_batch_destroy(void* batch);
  * Activations are stored as bf16, the convolutions run on the tensor cores
  * with FP32 accumulation: the 3x3x3 convolutions of the forward pass and of
  * the input gradient on the fifth-generation tensor cores (tcgen05, the
- * accumulator in tensor memory; the default) or on the warp-level mma.sync
- * path, the weight gradients and the 1x1x1 convolution on mma.sync.
+ * accumulator in tensor memory, the operands loaded by TMA; the default) or
+ * on the warp-level mma.sync path, the weight gradients and the 1x1x1
+ * convolution on mma.sync.
  * Features (normalised by the caller): kappa_1..3, Skalak G, R / E.
  * Training loss for targets t0, t1 of y0, y1 (FP32 [B][E^3]; for the warm
  * start t0 = s_eq - s0 outside the capsule, 0 inside, and t1 = 0) and marker
@@ -467,18 +468,21 @@ tlb_status tlb_net_train_step(void* net, const void* x_dev, const float* t0_dev,
  *  - markers: D = trilinear(y2..y4)(X0); X = X0 + T + ((D - T).n) n with T
  *    the mean of D and n the unit vertex pseudo-normals (no tangential
  *    shear of the reference mesh);
- *  - psi = I(X) + c_psi: the profile of the moved markers, as the plain
- *    start takes psi = I(X0);
- *  - phi = (1 - psi)(s0 + y0 + c_phi) with s0 = phi0 / (1 - psi0);
- *  - rho = 1, u = 0; c_psi and c_phi are the uniform shifts that restore
- *    the plain totals of psi and phi (the method conserves them);
+ *  - psi = I(X) + l_psi 4 I(X)(1 - I(X)): the profile of the moved
+ *    markers, as the plain start takes psi = I(X0);
+ *  - phi = (1 - psi)(s + l_phi (1 - s^2)_+) with s = s0 + y0 and
+ *    s0 = phi0 / (1 - psi0);
+ *  - rho = 1, u = 0; l_psi and l_phi restore the plain totals of psi and
+ *    phi (the method conserves them) by moving the membrane's profile and
+ *    the C1/C2 interface, leaving the bulk values where they are;
  * then the equilibrium populations of these fields, as tlb_init_fields.
  * Synchronises. */
 tlb_status tlb_net_warm_start(void* net, void* ctx, const double* feats);
-/* Choose the tensor-core path of the 3x3x3 convolutions: tcgen05 (on != 0,
- * the default) or mma.sync.  The two agree up to the order of the FP32
- * accumulation. */
-tlb_status tlb_net_set_tcgen05(void* net, int on);
+/* Choose the tensor-core path of the 3x3x3 convolutions: 2 (the default)
+ * tcgen05 in a persistent warp-specialised pipeline whose operands arrive by
+ * TMA, 1 tcgen05 with cp.async operand staging, 0 mma.sync.  They agree up
+ * to the order of the FP32 accumulation.  TLB_ERR_ARG for other values. */
+tlb_status tlb_net_set_tcgen05(void* net, int mode);
 /* Synchronise the net's stream and read (then clear) its status word: bit 0
  * set when a tcgen05 kernel gave up waiting for the tensor core (its
  * outputs are then not written); TLB_ERR_CUDA in that case.

@@ -272,15 +272,28 @@ def warm_start_markers(y, X0, normals, F=None):
     return X
 
 
-def warm_start_fields(y0, phi0, psi0, I_new):
+def warm_start_fields(y0, phi0, psi0, I_new, factors=False):
     """Fields of the warm start from the output y0 (the change of the phase
     indicator s = phi / (1 - psi)), the plain start and the profile I_new of
-    the moved markers: psi = I_new + c_psi and phi = (1 - psi)(s0 + y0 +
-    c_phi), the uniform shifts c_psi, c_phi restoring the plain totals of psi
-    and phi (the method conserves both)."""
+    the moved markers.  The method conserves the totals of psi and phi
+    (Sec. 2, the advection-diffusion equations of C_m are in conservation
+    form); the warm start restores the plain totals by moving the
+    interfaces, not by shifting the bulk values away from the minimisers
+    of the bulk free energy:
+        psi = I_new + l_psi 4 I_new (1 - I_new),
+        phi = (1 - psi)(s + l_phi (1 - s^2)_+),  s = s0 + y0,
+    with l_psi, l_phi the factors that restore the totals (0 when their
+    weights vanish everywhere), returned after the fields when `factors`."""
     w0 = 1.0 - psi0
     s0 = np.where(w0 > 1e-6, phi0 / np.where(w0 > 1e-6, w0, 1.0), 0.0)
-    psi = I_new + (psi0.sum() - I_new.sum()) / psi0.size
+    wpsi = 4.0 * I_new * (1.0 - I_new)
+    l_psi = (psi0.sum() - I_new.sum()) / wpsi.sum() if wpsi.sum() > 1e-12 else 0.0
+    psi = I_new + l_psi * wpsi
+    s = s0 + y0
     w = 1.0 - psi
-    c = (phi0.sum() - (w * (s0 + y0)).sum()) / w.sum()
-    return (1.0 - psi) * (s0 + y0 + c), psi
+    wphi = np.maximum(0.0, 1.0 - s * s)
+    den = (w * wphi).sum()
+    l_phi = (phi0.sum() - (w * s).sum()) / den if den > 1e-12 else 0.0
+    if factors:
+        return w * (s + l_phi * wphi), psi, l_psi, l_phi
+    return w * (s + l_phi * wphi), psi

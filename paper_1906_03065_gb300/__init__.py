@@ -533,8 +533,9 @@ class WarmStartNet:
         f = np.ascontiguousarray(feats, dtype=np.float64)
         _check(lib().tlb_net_warm_start(self.h, sim.h, _dp(f)))
 
-    def set_tcgen05(self, on: bool):
-        _check(lib().tlb_net_set_tcgen05(self.h, int(bool(on))))
+    def set_tcgen05(self, mode: int):
+        """2: tcgen05 fed by TMA (default), 1: tcgen05 with cp.async staging, 0: mma.sync."""
+        _check(lib().tlb_net_set_tcgen05(self.h, int(mode)))
 
     def status(self) -> int:
         st = C.c_uint(0)

@@ -12,6 +12,8 @@
 // the forward pass and Wd[ci][tap*Co + co] (taps mirrored) for the data
 // gradient.  Every convolution is an implicit GEMM on the tensor cores
 // (mma.sync m16n8k16 bf16, fp32 accumulation).
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_bf16.h>
 #include <math.h>
 #include <string.h>
@@ -276,6 +278,27 @@ constexpr int tc_stage_bytes() { return 2 * TC_HX * TC_HY * (ZB + 2) * 16 + 2 * 
 template <int BN, int ZB>
 constexpr int tc_smem() { return 2 * tc_stage_bytes<BN, ZB>() + 32; }
 
+// The 27 ZB products of one chunk of 16 input channels, issued by one
+// thread, tap by tap: plane zp and tap (dz, dy, dx) read the staged brick from voxel
+// ((zp + dz) HY + dy) HX + dx on.  A descriptor's start-address field is its
+// low 14 bits (16-byte units, below 2^14 for any shared address), so each
+// product's descriptors are the chunk's base descriptors plus constants.
+template <int BN, int ZB, int HX, int HY, int HV>
+__device__ __forceinline__ void conv3_products(unsigned As, unsigned Bs, unsigned dtmem, bool acc0) {
+  constexpr unsigned IDESC = umma::idesc_bf16<128, BN>();
+  const uint64_t a0 = umma::desc(As, HV * 16, HX * 16), b0 = umma::desc(Bs, 27 * BN * 16, 128);
+  // consecutive products go to different planes' accumulators, so that
+  // they do not wait on one another
+#pragma unroll
+  for (int tap = 0; tap < 27; ++tap) {
+    const int dz = tap / 9, dy = (tap / 3) % 3, dx = tap % 3;
+    const uint64_t at = a0 + (uint64_t)((dz * HY + dy) * HX + dx), bt = b0 + (uint64_t)(tap * BN);
+#pragma unroll
+    for (int zp = 0; zp < ZB; ++zp)
+      umma::mma_bf16(dtmem + zp * BN, at + (uint64_t)(zp * HY * HX), bt, IDESC, acc0 || tap > 0);
+  }
+}
+
 template <int BN, int ZB, bool RELU>
 __global__ void __launch_bounds__(128) k_conv3_tc(const bf16* __restrict__ in, int Ci, int El, int nbatch,
                                                   const bf16* __restrict__ Wk, const float* __restrict__ bias,
@@ -283,7 +306,6 @@ __global__ void __launch_bounds__(128) k_conv3_tc(const bf16* __restrict__ in, i
   constexpr int HX = TC_HX, HY = TC_HY, HZ = ZB + 2, HV = HX * HY * HZ;
   constexpr int ABYTES = 2 * HV * 16, STAGE = tc_stage_bytes<BN, ZB>();
   constexpr int NCOL = umma::tmem_cols(ZB * BN);
-  constexpr unsigned IDESC = umma::idesc_bf16<128, BN>();
   constexpr long POLL = 1L << 22;
   extern __shared__ __align__(128) unsigned char smem[];
   uint64_t* bar = reinterpret_cast<uint64_t*>(smem + 2 * STAGE);
@@ -348,15 +370,7 @@ __global__ void __launch_bounds__(128) k_conv3_tc(const bf16* __restrict__ in, i
     if (tid == 0 && ok) {
       umma::fence_after_sync();
       const unsigned As = umma::smem_u32(smem + s * STAGE), Bs = As + ABYTES;
-#pragma unroll 1
-      for (int zp = 0; zp < ZB; ++zp)
-#pragma unroll 1
-        for (int tap = 0; tap < 27; ++tap) {
-          const int dz = tap / 9, dy = (tap / 3) % 3, dx = tap % 3;
-          const uint64_t ad = umma::desc(As + (((zp + dz) * HY + dy) * HX + dx) * 16, HV * 16, HX * 16);
-          const uint64_t bd = umma::desc(Bs + tap * BN * 16, 27 * BN * 16, 128);
-          umma::mma_bf16(tmem + zp * BN, ad, bd, IDESC, ck > 0 || tap > 0);
-        }
+      conv3_products<BN, ZB, HX, HY, HV>(As, Bs, tmem, ck > 0);
       umma::commit(&bar[s]);
     }
   }
@@ -400,6 +414,174 @@ __global__ void __launch_bounds__(128) k_conv3_tc(const bf16* __restrict__ in, i
   umma::fence_before_sync();
   __syncthreads();
   if (w == 0) umma::tmem_free(tmem, NCOL);
+}
+
+// The same 3x3x3 convolution as a persistent, warp-specialised tcgen05
+// pipeline fed by the tensor memory accelerator (TMA):
+//  - warp 4 (one thread) loads each chunk of 16 input channels of a work
+//    item (a brick of ZB planes of 8 x 16 output voxels and BN output
+//    channels) with four tiled TMA copies: the input brick with its halo as
+//    two 5D boxes of 8 channels x 10 x 18 x (ZB + 2) voxels (zero outside
+//    the volume) and the weights as two 3D boxes of 8 channels x BN outputs
+//    x 27 taps, landing in exactly the K-major core-matrix layouts of
+//    k_conv3_tc, into one of S shared-memory stages;
+//  - warp 5 (one thread) issues the 27 ZB products of each chunk into one of
+//    two tensor-memory accumulators and frees the stage through an mbarrier
+//    when they complete;
+//  - warps 0..3 drain the other accumulator (bias, relu, channels-last
+//    store) while the next item accumulates.
+// Every wait is bounded (status bit 1 when one gave up; the roles then stop
+// and the tensor memory is freed).
+constexpr int TMA_THREADS = 192;
+// stages: as many as fit in 227 KiB of shared memory, 2 to 4
+template <int BN, int ZB>
+constexpr int tma_stages() {
+  return (232448 - 1280) / tc_stage_bytes<BN, ZB>() >= 4 ? 4 : ((232448 - 1280) / tc_stage_bytes<BN, ZB>() >= 3 ? 3 : 2);
+}
+template <int BN, int ZB>
+constexpr int tma_smem() { return 1024 + tma_stages<BN, ZB>() * tc_stage_bytes<BN, ZB>() + 256; }
+
+template <int BN, int ZB, bool RELU>
+__global__ void __launch_bounds__(TMA_THREADS) k_conv3_tma(const __grid_constant__ CUtensorMap tin,
+                                                           const __grid_constant__ CUtensorMap tw, int Ci, int El,
+                                                           int nbatch, const float* __restrict__ bias, int Co,
+                                                           void* __restrict__ out, unsigned* __restrict__ status) {
+  constexpr int HX = TC_HX, HY = TC_HY, HZ = ZB + 2, HV = HX * HY * HZ;
+  constexpr int ABYTES = 2 * HV * 16, STAGE = tc_stage_bytes<BN, ZB>(), S = tma_stages<BN, ZB>();
+  constexpr int NCOL = umma::tmem_cols(2 * ZB * BN);
+  constexpr long POLL = 1L << 24;
+  extern __shared__ unsigned char smem_raw[];
+  unsigned char* smem = smem_raw + ((1024 - (umma::smem_u32(smem_raw) & 1023)) & 1023);
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + S * STAGE);
+  uint64_t* empty = full + S;
+  uint64_t* acc_full = empty + S;
+  uint64_t* acc_empty = acc_full + 2;
+  unsigned* tslot = reinterpret_cast<unsigned*>(acc_empty + 2);
+  const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31;
+  const int bpx = (El + 7) / 8, bpy = (El + 15) / 16, bpz = (El + ZB - 1) / ZB;
+  const int nbr = bpx * bpy * bpz * nbatch, ntile = Co / BN, items = nbr * ntile, nck = Ci / 16;
+
+  if (w == 5) umma::tmem_alloc(tslot, NCOL);
+  if (tid == 0) {
+    for (int s = 0; s < S; ++s) {
+      umma::mbar_init(&full[s], 1);
+      umma::mbar_init(&empty[s], 1);
+    }
+    for (int a = 0; a < 2; ++a) {
+      umma::mbar_init(&acc_full[a], 1);
+      umma::mbar_init(&acc_empty[a], 128);
+    }
+    umma::mbar_init_fence();
+  }
+  umma::fence_before_sync();
+  __syncthreads();
+  umma::fence_after_sync();
+  const unsigned tmem = *tslot;
+  auto item_coords = [&](int it, int& x0, int& y0, int& z0, int& b, int& n0) {
+    const int t = it % ntile;
+    int r = it / ntile;
+    x0 = (r % bpx) * 8;
+    r /= bpx;
+    y0 = (r % bpy) * 16;
+    r /= bpy;
+    z0 = (r % bpz) * ZB;
+    b = r / bpz;
+    n0 = t * BN;
+  };
+  bool ok = true;
+  if (w == 4) {
+    if (lane == 0) {  // producer
+      long g = 0;
+      for (int it = blockIdx.x; it < items && ok; it += gridDim.x) {
+        int x0, y0, z0, b, n0;
+        item_coords(it, x0, y0, z0, b, n0);
+        for (int ck = 0; ck < nck && ok; ++ck, ++g) {
+          const int s = (int)(g % S);
+          if (g >= S) ok = umma::mbar_poll(&empty[s], (unsigned)((g / S - 1) & 1), POLL);
+          if (!ok) break;
+          unsigned char* As = smem + s * STAGE;
+          unsigned char* Bs = As + ABYTES;
+          umma::mbar_expect_tx(&full[s], (unsigned)STAGE);
+          for (int kh = 0; kh < 2; ++kh) {
+            umma::tma_load_5d(As + kh * HV * 16, &tin, ck * 16 + kh * 8, x0 - 1, y0 - 1, z0 - 1, b, &full[s]);
+            umma::tma_load_3d(Bs + kh * 27 * BN * 16, &tw, ck * 16 + kh * 8, n0, 0, &full[s]);
+          }
+        }
+      }
+    }
+  } else if (w == 5) {
+    if (lane == 0) {  // tensor-core issue
+      long g = 0;
+      int j = 0;
+      for (int it = blockIdx.x; it < items && ok; it += gridDim.x, ++j) {
+        const int acc = j & 1;
+        if (j >= 2) ok = umma::mbar_poll(&acc_empty[acc], (unsigned)((j / 2 - 1) & 1), POLL);
+        if (!ok) break;
+        umma::fence_after_sync();
+        const unsigned dbase = tmem + acc * ZB * BN;
+        for (int ck = 0; ck < nck && ok; ++ck, ++g) {
+          const int s = (int)(g % S);
+          ok = umma::mbar_poll(&full[s], (unsigned)((g / S) & 1), POLL);
+          if (!ok) break;
+          umma::fence_after_sync();
+          const unsigned As = umma::smem_u32(smem + s * STAGE), Bs = As + ABYTES;
+          conv3_products<BN, ZB, HX, HY, HV>(As, Bs, dbase, ck > 0);
+          umma::commit(&empty[s]);
+        }
+        if (ok) umma::commit(&acc_full[acc]);
+      }
+    }
+  } else {  // epilogue: warp w holds accumulator rows 32 w .. 32 w + 31
+    int j = 0;
+    for (int it = blockIdx.x; it < items && ok; it += gridDim.x, ++j) {
+      const int acc = j & 1;
+      ok = umma::mbar_poll(&acc_full[acc], (unsigned)((j / 2) & 1), POLL);
+      ok = __all_sync(0xffffffffu, ok);
+      if (!ok) break;
+      umma::fence_after_sync();
+      int x0, y0, z0, b, n0;
+      item_coords(it, x0, y0, z0, b, n0);
+      const int r = 32 * w + lane, X = x0 + r % 8, Y = y0 + r / 8;
+      for (int zp = 0; zp < ZB; ++zp) {
+        const int Z = z0 + zp;
+        const bool in_vol = X < El && Y < El && Z < El;
+        const long long v = (((long long)b * El + Z) * El + Y) * El + X;
+#pragma unroll 1
+        for (int j0 = 0; j0 < BN; j0 += 16) {
+          float o[16];
+          umma::ld16(tmem + ((unsigned)(32 * w) << 16) + acc * ZB * BN + zp * BN + j0, o);
+          if (!in_vol) continue;
+          const int n = n0 + j0;
+          if (bias)
+#pragma unroll
+            for (int i = 0; i < 16; ++i) o[i] += bias[n + i];
+          if (RELU) {
+            uint4 pk[2];
+            unsigned* u = reinterpret_cast<unsigned*>(pk);
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+              __nv_bfloat162 h = __floats2bfloat162_rn(fmaxf(o[2 * i], 0.f), fmaxf(o[2 * i + 1], 0.f));
+              u[i] = *reinterpret_cast<unsigned*>(&h);
+            }
+            uint4* dst = reinterpret_cast<uint4*>(static_cast<bf16*>(out) + v * Co + n);
+            dst[0] = pk[0];
+            dst[1] = pk[1];
+          } else {
+            float4* dst = reinterpret_cast<float4*>(static_cast<float*>(out) + v * Co + n);
+#pragma unroll
+            for (int i = 0; i < 4; ++i) dst[i] = make_float4(o[4 * i], o[4 * i + 1], o[4 * i + 2], o[4 * i + 3]);
+          }
+        }
+      }
+      umma::fence_before_sync();
+      umma::mbar_arrive(&acc_empty[acc]);
+    }
+  }
+  if (!ok) atomicOr(status, 1u);
+  umma::fence_before_sync();
+  __syncthreads();
+  umma::fence_after_sync();
+  if (w == 5) umma::tmem_free(tmem, NCOL);
 }
 
 // Shared-memory 8x8 b16 matrices, transposed on load (ldmatrix .trans): lane
@@ -514,22 +696,44 @@ __global__ void __launch_bounds__(128) k_wgrad3(const bf16* __restrict__ in, int
   }
 }
 
-// out[i] = sum over k < nsplit of part[k * n + i], in split order (i < n).
+// out[i] = sum over k < nsplit of part[k * n + i] (i < n): eight running
+// sums (split k goes to sum k mod 8, so eight loads are in flight per
+// thread) combined in a fixed tree; the result does not depend on timing.
 __global__ void k_sum_splits(const float* __restrict__ part, int nsplit, long long n, float* __restrict__ out) {
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
-  float s = 0.f;
-  for (int k = 0; k < nsplit; ++k) s += part[(size_t)k * n + i];
-  out[i] = s;
+  float a[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+  int k = 0;
+  for (; k + 8 <= nsplit; k += 8)
+#pragma unroll
+    for (int j = 0; j < 8; ++j) a[j] += part[(size_t)(k + j) * n + i];
+  for (; k < nsplit; ++k) a[k & 7] += part[(size_t)k * n + i];
+  out[i] = ((a[0] + a[1]) + (a[2] + a[3])) + ((a[4] + a[5]) + (a[6] + a[7]));
 }
 
-// Column sums of gz (the bias gradient), per-block partials over fixed voxel ranges.
-__global__ void k_colsum(const bf16* __restrict__ gz, long long V, int Co, long long chunk, float* __restrict__ part) {
+// Column sums of gz (the bias gradient): block b sums voxels [b chunk,
+// (b + 1) chunk); thread (tx, ty) of its TX x TY threads (TX = min(Co, 256))
+// takes channels tx, tx + TX, .. of voxels ty, ty + TY, ..; the TY partial
+// sums of a channel are then added in ty order (fixed, so deterministic).
+__global__ void __launch_bounds__(256) k_colsum(const bf16* __restrict__ gz, long long V, int Co, long long chunk,
+                                                float* __restrict__ part) {
+  __shared__ float sm[256];
+  const int TX = Co < 256 ? Co : 256, TY = 256 / TX;
+  const int tx = threadIdx.x % TX, ty = threadIdx.x / TX;
   const long long v0 = (long long)blockIdx.x * chunk, v1 = min(V, v0 + chunk);
-  for (int co = threadIdx.x; co < Co; co += blockDim.x) {
+  for (int c0 = 0; c0 < Co; c0 += TX) {
     float s = 0.f;
-    for (long long v = v0; v < v1; ++v) s += __bfloat162float(gz[v * Co + co]);
-    part[(size_t)blockIdx.x * Co + co] = s;
+    const bool live = ty < TY && c0 + tx < Co;
+    if (live)
+      for (long long v = v0 + ty; v < v1; v += TY) s += __bfloat162float(gz[v * Co + c0 + tx]);
+    __syncthreads();
+    sm[threadIdx.x] = s;
+    __syncthreads();
+    if (ty == 0 && c0 + tx < Co) {
+      float t = 0.f;
+      for (int k = 0; k < TY; ++k) t += sm[k * TX + tx];
+      part[(size_t)blockIdx.x * Co + c0 + tx] = t;
+    }
   }
 }
 
@@ -655,19 +859,23 @@ __global__ void k_pool_bwd(const float* __restrict__ gout, int El, int C, long l
 // cat[v] = [up2(d)[v] (C1) | e[v] (C2)], bf16.
 __global__ void k_cat_fwd(const bf16* __restrict__ d, int C1, const bf16* __restrict__ e, int C2, int El, long long n,
                           bf16* __restrict__ cat) {
+  // one thread per voxel and group of 8 channels (16 bytes; C1, C2 are
+  // multiples of 16); 32-bit voxel arithmetic (n < 2^31 voxels)
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  const int C = C1 + C2;
-  if (i >= n * C) return;
-  const int c = (int)(i % C);
-  const long long v = i / C;
-  if (c >= C1) {
-    cat[i] = e[v * C2 + (c - C1)];
+  const int G = (C1 + C2) >> 3;
+  if (i >= n * G) return;
+  const int g = (int)(i % G);
+  const unsigned v = (unsigned)(i / G);
+  uint4 val;
+  if (8 * g >= C1) {
+    val = *reinterpret_cast<const uint4*>(e + (long long)v * C2 + (8 * g - C1));
   } else {
-    const Vox p = vox_of(v, El);
-    const int Eh = El / 2;
-    const long long q = (((long long)p.b * Eh + p.z / 2) * Eh + p.y / 2) * Eh + p.x / 2;
-    cat[i] = d[q * C1 + c];
+    const unsigned E = (unsigned)El, Eh = E / 2;
+    const unsigned x = v % E, r = v / E, y = r % E, r2 = r / E, z = r2 % E, b = r2 / E;
+    const unsigned q = ((b * Eh + z / 2) * Eh + y / 2) * Eh + x / 2;
+    val = *reinterpret_cast<const uint4*>(d + (long long)q * C1 + 8 * g);
   }
+  *reinterpret_cast<uint4*>(cat + (long long)v * (C1 + C2) + 8 * g) = val;
 }
 
 // From g_cat: g_e += skip part (per fine voxel); g_d += sum over the 8 children (per coarse voxel).
@@ -693,15 +901,39 @@ __global__ void k_cat_bwd_up(const float* __restrict__ gcat, int C1, int C2, int
 }
 
 // gz = g * relu'(h) as bf16 (h > 0 where the stored activation is positive).
+// gz = bf16(h > 0 ? g : 0) (or bf16(g)), eight elements per thread (n is a
+// multiple of 16: channels come in multiples of 16).
 __global__ void k_relu_bwd(const float* __restrict__ g, const bf16* __restrict__ h, long long n, bf16* __restrict__ gz) {
-  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long i = 8 * ((long long)blockIdx.x * blockDim.x + threadIdx.x);
   if (i >= n) return;
-  gz[i] = __float2bfloat16_rn(__bfloat162float(h[i]) > 0.f ? g[i] : 0.f);
+  const float4 g0 = *reinterpret_cast<const float4*>(g + i), g1 = *reinterpret_cast<const float4*>(g + i + 4);
+  const uint4 hv = *reinterpret_cast<const uint4*>(h + i);
+  const bf16* hb = reinterpret_cast<const bf16*>(&hv);
+  const float gv[8] = {g0.x, g0.y, g0.z, g0.w, g1.x, g1.y, g1.z, g1.w};
+  uint4 o;
+  unsigned* u = reinterpret_cast<unsigned*>(&o);
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    __nv_bfloat162 p = __floats2bfloat162_rn(__bfloat162float(hb[2 * k]) > 0.f ? gv[2 * k] : 0.f,
+                                              __bfloat162float(hb[2 * k + 1]) > 0.f ? gv[2 * k + 1] : 0.f);
+    u[k] = *reinterpret_cast<unsigned*>(&p);
+  }
+  *reinterpret_cast<uint4*>(gz + i) = o;
 }
 
 __global__ void k_to_bf16(const float* __restrict__ g, long long n, bf16* __restrict__ o) {
-  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n) o[i] = __float2bfloat16_rn(g[i]);
+  const long long i = 8 * ((long long)blockIdx.x * blockDim.x + threadIdx.x);
+  if (i >= n) return;
+  const float4 g0 = *reinterpret_cast<const float4*>(g + i), g1 = *reinterpret_cast<const float4*>(g + i + 4);
+  uint4 r;
+  unsigned* u = reinterpret_cast<unsigned*>(&r);
+  const float gv[8] = {g0.x, g0.y, g0.z, g0.w, g1.x, g1.y, g1.z, g1.w};
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    __nv_bfloat162 p = __floats2bfloat162_rn(gv[2 * k], gv[2 * k + 1]);
+    u[k] = *reinterpret_cast<unsigned*>(&p);
+  }
+  *reinterpret_cast<uint4*>(o + i) = r;
 }
 
 // Field loss: gy[v][0..1] = 2/(B V) (y - target), gy[v][2..7] = 0; per-block
@@ -901,64 +1133,75 @@ __device__ __forceinline__ double s0_of(float phi0, float psi0) {
   return w > 1e-6 ? (double)phi0 / w : 0.0;
 }
 
-// FP64 partial sums of pass 1: phi0, psi0, I.
+// The warm start restores the plain totals of psi and phi (the method
+// conserves both) by moving interfaces, not by shifting bulk values: the
+// corrections are weighted by 4 I (1 - I) (nonzero only across the
+// membrane's profile) and by (1 - s^2)_+ (only across the C1/C2 interface),
+// so that the bulk fluids start at their equilibrium compositions.
+__device__ __forceinline__ double ws_wpsi(float I) { return 4.0 * (double)I * (1.0 - (double)I); }
+__device__ __forceinline__ double ws_wphi(double s) { return fmax(0.0, 1.0 - s * s); }
+
+// Block partial sums of nq values per cell, written to part[q][block].
+template <int NQ, class F>
+__device__ __forceinline__ void ws_block_sums(long long V, double* __restrict__ part, F cell) {
+  __shared__ double sm[NQ][256];
+  double a[NQ];
+  for (int q = 0; q < NQ; ++q) a[q] = 0;
+  for (long long v = (long long)blockIdx.x * 256 + threadIdx.x; v < V; v += (long long)gridDim.x * 256) cell(v, a);
+  for (int q = 0; q < NQ; ++q) sm[q][threadIdx.x] = a[q];
+  __syncthreads();
+  for (int s = 128; s > 0; s >>= 1) {
+    if (threadIdx.x < s)
+      for (int q = 0; q < NQ; ++q) sm[q][threadIdx.x] += sm[q][threadIdx.x + s];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0)
+    for (int q = 0; q < NQ; ++q) part[q * gridDim.x + blockIdx.x] = sm[q][0];
+}
+
+// Pass 1: sums of phi0, psi0, I and 4 I (1 - I).
 __global__ void k_ws_sums1(const float* __restrict__ phi, const float* __restrict__ psi, const float* __restrict__ I,
                            long long V, double* __restrict__ part) {
-  __shared__ double sm[3][256];
-  double a[3] = {0, 0, 0};
-  for (long long v = (long long)blockIdx.x * 256 + threadIdx.x; v < V; v += (long long)gridDim.x * 256) {
+  ws_block_sums<4>(V, part, [&](long long v, double* a) {
     a[0] += phi[v];
     a[1] += psi[v];
     a[2] += I[v];
-  }
-  for (int q = 0; q < 3; ++q) sm[q][threadIdx.x] = a[q];
-  __syncthreads();
-  for (int s = 128; s > 0; s >>= 1) {
-    if (threadIdx.x < s)
-      for (int q = 0; q < 3; ++q) sm[q][threadIdx.x] += sm[q][threadIdx.x + s];
-    __syncthreads();
-  }
-  if (threadIdx.x == 0)
-    for (int q = 0; q < 3; ++q) part[q * gridDim.x + blockIdx.x] = sm[q][0];
+    a[3] += ws_wpsi(I[v]);
+  });
 }
 
-// Pass 2, with psi = I + cpsi (cpsi = (sum psi0 - sum I) / V from tot[0..2]):
-// sums of (1 - psi) and (1 - psi)(s0 + y0).
+__device__ __forceinline__ double ws_lpsi(const double* tot) {
+  return tot[3] > 1e-12 ? (tot[1] - tot[2]) / tot[3] : 0.0;
+}
+
+// Pass 2, with psi = I + lpsi 4 I (1 - I) and s = s0 + y0: sums of
+// (1 - psi) s and (1 - psi) (1 - s^2)_+.
 __global__ void k_ws_sums2(const float* __restrict__ phi, const float* __restrict__ psi, const float* __restrict__ I,
                            const float* __restrict__ y, long long V, const double* __restrict__ tot,
                            double* __restrict__ part) {
-  __shared__ double sm[2][256];
-  const double cpsi = (tot[1] - tot[2]) / (double)V;
-  double a[2] = {0, 0};
-  for (long long v = (long long)blockIdx.x * 256 + threadIdx.x; v < V; v += (long long)gridDim.x * 256) {
-    const double w = 1.0 - ((double)I[v] + cpsi);
-    a[0] += w;
-    a[1] += w * (s0_of(phi[v], psi[v]) + y[v * YC]);
-  }
-  for (int q = 0; q < 2; ++q) sm[q][threadIdx.x] = a[q];
-  __syncthreads();
-  for (int s = 128; s > 0; s >>= 1) {
-    if (threadIdx.x < s)
-      for (int q = 0; q < 2; ++q) sm[q][threadIdx.x] += sm[q][threadIdx.x + s];
-    __syncthreads();
-  }
-  if (threadIdx.x == 0)
-    for (int q = 0; q < 2; ++q) part[q * gridDim.x + blockIdx.x] = sm[q][0];
+  const double lpsi = ws_lpsi(tot);
+  ws_block_sums<2>(V, part, [&](long long v, double* a) {
+    const double w = 1.0 - ((double)I[v] + lpsi * ws_wpsi(I[v]));
+    const double sv = s0_of(phi[v], psi[v]) + y[v * YC];
+    a[0] += w * sv;
+    a[1] += w * ws_wphi(sv);
+  });
 }
 
-// Fields of the warm start: rho = 1 (the array holds rho - 1), psi = I + cpsi, phi = (1 - psi)(s0 + y0
-// + cphi) with cphi = (sum phi0 - tot2[1]) / tot2[0] restoring the phi total.
+// Fields of the warm start: rho = 1 (the array holds rho - 1), psi = I +
+// lpsi 4 I (1 - I), phi = (1 - psi)(s + lphi (1 - s^2)_+) with s = s0 + y0
+// and lphi = (sum phi0 - tot2[0]) / tot2[1].
 __global__ void k_ws_fields(float* __restrict__ rho, float* __restrict__ phi, float* __restrict__ psi,
                             const float* __restrict__ I, const float* __restrict__ y, long long V,
                             const double* __restrict__ tot, const double* __restrict__ tot2) {
   const long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (v >= V) return;
-  const double cpsi = (tot[1] - tot[2]) / (double)V;
-  const double cphi = (tot[0] - tot2[1]) / tot2[0];
-  const double ps = (double)I[v] + cpsi;
-  const double s = s0_of(phi[v], psi[v]) + y[v * YC] + cphi;
+  const double lpsi = ws_lpsi(tot);
+  const double lphi = tot2[1] > 1e-12 ? (tot[0] - tot2[0]) / tot2[1] : 0.0;
+  const double ps = (double)I[v] + lpsi * ws_wpsi(I[v]);
+  const double sv = s0_of(phi[v], psi[v]) + y[v * YC];
   rho[v] = 0.f;
-  phi[v] = (float)((1.0 - ps) * s);
+  phi[v] = (float)((1.0 - ps) * (sv + lphi * ws_wphi(sv)));
   psi[v] = (float)ps;
 }
 
@@ -1008,7 +1251,8 @@ struct Net {
   Ten x, enc_a[4], enc_e[4], enc_p[4], dec_cat[4], dec_b[4], dec_d[4];
   long adam_t = 0;
   long launches = 0;
-  bool tc = true;  // 3x3x3 convolutions on tcgen05 (else mma.sync)
+  int tc = 2;      // 3x3x3 convolutions: 0 mma.sync, 1 tcgen05 (cp.async staging), 2 tcgen05 fed by TMA
+  int nsm = 1;     // streaming multiprocessors (persistent grids)
   unsigned* status() const { return reinterpret_cast<unsigned*>(base + o_misc + 64 * 8); }
 
   template <class T> T* at(size_t off) const { return reinterpret_cast<T*>(base + off); }
@@ -1150,9 +1394,72 @@ tlb_status launch_conv3_tc_t(Net* n, const bf16* in, int Ci, int El, int B, cons
   return TLB_OK;
 }
 
+// cuTensorMapEncodeTiled through the runtime's driver entry point (no link
+// against the driver library).
+static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
+    cudaGetLastError();
+  }
+  return fn;
+}
+
+// Tensor maps of a 3x3x3 convolution: the input [B][El^3][Ci] bf16 as 5D
+// (channel, x, y, z, sample) with a box of 8 channels x 10 x 18 x (ZB + 2)
+// voxels, the weights [Co][27 Ci] bf16 as 3D (channel, output, tap) with a
+// box of 8 channels x BN outputs x 27 taps.
+static tlb_status conv3_maps(const bf16* in, int Ci, int El, int B, int ZB, const bf16* Wk, int Co, int BN,
+                             CUtensorMap* tin, CUtensorMap* tw) {
+  PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+  if (!enc) { set_error("net: cuTensorMapEncodeTiled is not available"); return TLB_ERR_CUDA; }
+  const cuuint64_t e = (cuuint64_t)El, ci2 = (cuuint64_t)Ci * 2;
+  const cuuint64_t gdim[5] = {(cuuint64_t)Ci, e, e, e, (cuuint64_t)B};
+  const cuuint64_t gstr[4] = {ci2, ci2 * e, ci2 * e * e, ci2 * e * e * e};
+  const cuuint32_t box[5] = {8, (cuuint32_t)TC_HX, (cuuint32_t)TC_HY, (cuuint32_t)(ZB + 2), 1};
+  const cuuint32_t one[5] = {1, 1, 1, 1, 1};
+  CUresult r = enc(tin, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, (void*)in, gdim, gstr, box, one,
+                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) { set_error("net: input tensor map (" + std::to_string((int)r) + ")"); return TLB_ERR_CUDA; }
+  const cuuint64_t wdim[3] = {(cuuint64_t)Ci, (cuuint64_t)Co, 27};
+  const cuuint64_t wstr[2] = {27 * ci2, ci2};
+  const cuuint32_t wbox[3] = {8, (cuuint32_t)BN, 27};
+  r = enc(tw, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, (void*)Wk, wdim, wstr, wbox, one, CU_TENSOR_MAP_INTERLEAVE_NONE,
+          CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) { set_error("net: weight tensor map (" + std::to_string((int)r) + ")"); return TLB_ERR_CUDA; }
+  return TLB_OK;
+}
+
+template <int BN, int ZB, bool RELU>
+tlb_status launch_conv3_tma_t(Net* n, const bf16* in, int Ci, int El, int B, const bf16* Wk, const float* bias,
+                              int Co, void* out) {
+  CUtensorMap tin, tw;
+  if (tlb_status st = conv3_maps(in, Ci, El, B, ZB, Wk, Co, BN, &tin, &tw); st != TLB_OK) return st;
+  const long long items = (long long)((El + 7) / 8) * ((El + 15) / 16) * ((El + ZB - 1) / ZB) * B * (Co / BN);
+  constexpr int sm = tma_smem<BN, ZB>();
+  TLB_CUDA(cudaFuncSetAttribute(k_conv3_tma<BN, ZB, RELU>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
+  const unsigned grid = (unsigned)std::min<long long>(items, n->nsm);
+  k_conv3_tma<BN, ZB, RELU><<<grid, TMA_THREADS, sm, n->stream>>>(tin, tw, Ci, El, B, bias, Co, out, n->status());
+  NET_LAUNCHED(n, "k_conv3_tma");
+  return TLB_OK;
+}
+
 template <bool RELU>
 tlb_status launch_conv(Net* n, const bf16* in, int Ci, int El, long long nvox, int taps, const bf16* Wk,
                        const float* bias, int Co, void* out) {
+  if (taps == 27 && n->tc == 2) {  // TMA-fed persistent pipeline; columns per tile: 64, 32 or 16
+    const int B = (int)(nvox / ((long long)El * El * El));
+    // (8 planes, i.e. 8 independent accumulators per item, where the
+    // tensor memory holds two sets of them)
+    if (Co % 64 == 0) return launch_conv3_tma_t<64, 4, RELU>(n, in, Ci, El, B, Wk, bias, Co, out);
+    if (Co % 32 == 0) return launch_conv3_tma_t<32, 8, RELU>(n, in, Ci, El, B, Wk, bias, Co, out);
+    return launch_conv3_tma_t<16, 8, RELU>(n, in, Ci, El, B, Wk, bias, Co, out);
+  }
   if (taps == 27 && n->tc) {  // tensor memory accumulators; columns per CTA: 64, 32 or 16
     const int B = (int)(nvox / ((long long)El * El * El));
     if (Co % 64 == 0) return launch_conv3_tc_t<64, 4, RELU>(n, in, Ci, El, B, Wk, bias, Co, out);
@@ -1190,15 +1497,15 @@ tlb_status launch_wgrad3_t(Net* n, const Conv& c, const bf16* in, int El, int B,
   float* g = n->at<float>(n->o_grad);
   // weight gradient: sums over the CTAs' partials [27 * Ci][Co]
   const long long nw = 27ll * c.ci * c.co;
-  k_sum_splits<<<nb(nw, 256), 256, 0, n->stream>>>(part, nsplit, nw, g + c.w);
+  k_sum_splits<<<nb(nw, 64), 64, 0, n->stream>>>(part, nsplit, nw, g + c.w);
   NET_LAUNCHED(n, "k_sum_splits");
   // bias gradient: column sums of gz over fixed voxel ranges, then over the ranges
   const long long V = (long long)B * El * El * El;
   const int nbs = (int)std::min<long long>(512, (V + 255) / 256);
   const long long chunk = (V + nbs - 1) / nbs;
-  k_colsum<<<nbs, 128, 0, n->stream>>>(gz, V, c.co, chunk, part);
+  k_colsum<<<nbs, 256, 0, n->stream>>>(gz, V, c.co, chunk, part);
   NET_LAUNCHED(n, "k_colsum");
-  k_sum_splits<<<nb(c.co, 256), 256, 0, n->stream>>>(part, nbs, c.co, g + c.b);
+  k_sum_splits<<<nb(c.co, 64), 64, 0, n->stream>>>(part, nbs, c.co, g + c.b);
   NET_LAUNCHED(n, "k_sum_splits");
   return TLB_OK;
 }
@@ -1278,7 +1585,7 @@ tlb_status forward(Net* n, int B) {
     const long long V = n->vox(l, B);
     const int C1 = n->chan(l + 1), C2 = n->chan(l);
     bf16* cat = A + n->dec_cat[l].act;
-    k_cat_fwd<<<nb(V * (C1 + C2), 256), 256, 0, s>>>(dprev, C1, A + n->enc_e[l].act, C2, El, V, cat);
+    k_cat_fwd<<<nb(V * ((C1 + C2) / 8), 256), 256, 0, s>>>(dprev, C1, A + n->enc_e[l].act, C2, El, V, cat);
     NET_LAUNCHED(n, "k_cat_fwd");
     const Conv& c1 = n->convs[k++];
     if ((st = launch_conv<true>(n, cat, c1.ci, El, V, 27, Wf + c1.wf, th + c1.b, c1.co, A + n->dec_b[l].act)) != TLB_OK)
@@ -1302,8 +1609,8 @@ tlb_status conv_bwd(Net* n, const Conv& c, const bf16* in, const bf16* out, cons
   const int El = n->d.edge >> c.level;
   const long long V = n->vox(c.level, B);
   bf16* gz = n->at<bf16>(n->o_gz);
-  if (relu) k_relu_bwd<<<nb(V * c.co, 256), 256, 0, n->stream>>>(g_out, out, V * c.co, gz);
-  else k_to_bf16<<<nb(V * c.co, 256), 256, 0, n->stream>>>(g_out, V * c.co, gz);
+  if (relu) k_relu_bwd<<<nb(V * c.co / 8, 256), 256, 0, n->stream>>>(g_out, out, V * c.co, gz);
+  else k_to_bf16<<<nb(V * c.co / 8, 256), 256, 0, n->stream>>>(g_out, V * c.co, gz);
   NET_LAUNCHED(n, "k_relu_bwd");
   tlb_status st = launch_wgrad(n, c, in, El, V, gz);
   if (st != TLB_OK || !g_in) return st;
@@ -1444,6 +1751,12 @@ tlb_status tlb_net_create(const tlb_net_desc* desc, void* arena, size_t bytes, v
   }
   n->base = (char*)arena;
   n->stream = (cudaStream_t)cuda_stream;
+  {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&n->nsm, cudaDevAttrMultiProcessorCount, dev);
+    if (n->nsm <= 0) n->nsm = 1;
+  }
   s = cuda_check(cudaMemsetAsync(n->base, 0, n->bytes, n->stream), "memset net arena");
   if (s == TLB_OK) s = cuda_check(cudaStreamSynchronize(n->stream), "net create");
   if (s != TLB_OK) { delete n; return s; }
@@ -1518,7 +1831,8 @@ tlb_status tlb_net_status(void* net, unsigned* status) {
 tlb_status tlb_net_set_tcgen05(void* net, int on) {
   Net* n = (Net*)net;
   if (!n) { set_error("net is NULL"); return TLB_ERR_ARG; }
-  n->tc = on != 0;
+  if (on < 0 || on > 2) { set_error("net_set_tcgen05: 0, 1 or 2"); return TLB_ERR_ARG; }
+  n->tc = on;
   return TLB_OK;
 }
 
@@ -1616,7 +1930,7 @@ tlb_status tlb_net_warm_start(void* net, void* ctx, const double* feats) {
   if ((s = forward(n, 1)) != TLB_OK) return s;
   const float* y = n->at<float>(n->o_y);
   double* part = n->at<double>(n->o_lpart);
-  double* tot = n->at<double>(n->o_misc) + 8;  // [0..2] pass 1, [4..5] pass 2, [8..10] translation
+  double* tot = n->at<double>(n->o_misc) + 8;  // [0..3] pass 1, [4..5] pass 2, [8..10] translation
   // markers: mean translation plus the normal part of the predicted
   // displacement, then scaled about their centroid back to the plain
   // start's enclosed volume
@@ -1646,7 +1960,7 @@ tlb_status tlb_net_warm_start(void* net, void* ctx, const double* feats) {
   TLB_CUDA(cudaStreamSynchronize(c->stream));
   k_ws_sums1<<<256, 256, 0, st>>>(phi, psi, I, c->N, part);
   NET_LAUNCHED(n, "k_ws_sums1");
-  k_sum_parts<<<1, 256, 0, st>>>(part, 256, 3, tot);
+  k_sum_parts<<<1, 256, 0, st>>>(part, 256, 4, tot);
   NET_LAUNCHED(n, "k_sum_parts");
   k_ws_sums2<<<256, 256, 0, st>>>(phi, psi, I, y, c->N, tot, part);
   NET_LAUNCHED(n, "k_ws_sums2");

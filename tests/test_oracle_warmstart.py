@@ -132,6 +132,20 @@ def test_warm_start_composition_pins():
     I_new = np.clip(psi0 + rng.normal(0, 0.05, 300), 0, 1)
     phi, psi = ws.warm_start_fields(rng.normal(0, 0.1, 300), phi0, psi0, I_new)
     assert phi.sum() == pytest.approx(phi0.sum(), abs=1e-10) and psi.sum() == pytest.approx(psi0.sum(), abs=1e-10)
+    # the totals are restored on the interfaces only: bulk cells (I = 0 or 1,
+    # s = +-1) keep their values
+    I_b = I_new.copy()
+    I_b[:100], I_b[100:150] = 0.0, 1.0
+    w0 = 1 - psi0
+    s0 = phi0 / w0
+    y0 = rng.normal(0, 0.1, 300)
+    y0[150:200] = 1.0 - s0[150:200]
+    y0[200:230] = -1.0 - s0[200:230]
+    phi, psi = ws.warm_start_fields(y0, phi0, psi0, I_b)
+    assert np.all(psi[:100] == 0.0) and np.all(psi[100:150] == 1.0)
+    assert np.allclose(phi[150:200], 1 - psi[150:200], atol=1e-14)
+    assert np.allclose(phi[200:230], -(1 - psi[200:230]), atol=1e-14)
+    assert phi.sum() == pytest.approx(phi0.sum(), abs=1e-10) and psi.sum() == pytest.approx(psi0.sum(), abs=1e-10)
 
 
 def test_enclosed_volume_and_the_volume_projection():
