@@ -696,19 +696,33 @@ __global__ void __launch_bounds__(128) k_wgrad3(const bf16* __restrict__ in, int
   }
 }
 
-// out[i] = sum over k < nsplit of part[k * n + i] (i < n): eight running
-// sums (split k goes to sum k mod 8, so eight loads are in flight per
-// thread) combined in a fixed tree; the result does not depend on timing.
-__global__ void k_sum_splits(const float* __restrict__ part, int nsplit, long long n, float* __restrict__ out) {
+// out[i] = sum over k < nsplit of part[k * n + i] (i < n), in two passes
+// whose grouping is fixed (so the result does not depend on timing): pass 1
+// (k_sum_groups) adds the splits of each group of SPLIT_GROUP into the
+// group's first row, in place; pass 2 (k_sum_splits with step SPLIT_GROUP)
+// adds the groups' rows.  Each thread keeps eight running sums (split k to
+// sum k mod 8) combined in a fixed tree, so eight loads are in flight.
+constexpr int SPLIT_GROUP = 16;
+__device__ __forceinline__ float sum_rows(const float* __restrict__ part, int k0, int k1, int step, long long n,
+                                          long long i) {
+  float a[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+  int k = k0;
+  for (; k + 8 * step <= k1; k += 8 * step)
+#pragma unroll
+    for (int j = 0; j < 8; ++j) a[j] += part[(size_t)(k + j * step) * n + i];
+  for (int j = 0; k < k1; k += step, ++j) a[j & 7] += part[(size_t)k * n + i];
+  return ((a[0] + a[1]) + (a[2] + a[3])) + ((a[4] + a[5]) + (a[6] + a[7]));
+}
+__global__ void k_sum_groups(float* __restrict__ part, int nsplit, long long n) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const int k0 = blockIdx.y * SPLIT_GROUP;
+  if (i >= n || k0 >= nsplit) return;
+  part[(size_t)k0 * n + i] = sum_rows(part, k0, min(nsplit, k0 + SPLIT_GROUP), 1, n, i);
+}
+__global__ void k_sum_splits(const float* __restrict__ part, int nsplit, long long n, int step, float* __restrict__ out) {
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
-  float a[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-  int k = 0;
-  for (; k + 8 <= nsplit; k += 8)
-#pragma unroll
-    for (int j = 0; j < 8; ++j) a[j] += part[(size_t)(k + j) * n + i];
-  for (; k < nsplit; ++k) a[k & 7] += part[(size_t)k * n + i];
-  out[i] = ((a[0] + a[1]) + (a[2] + a[3])) + ((a[4] + a[5]) + (a[6] + a[7]));
+  out[i] = sum_rows(part, 0, nsplit, step, n, i);
 }
 
 // Column sums of gz (the bias gradient): block b sums voxels [b chunk,
@@ -830,30 +844,65 @@ __global__ void k_wgrad_reduce(const float* __restrict__ part, int nsplit, int M
 
 // ------------------------------------------------------------ elementwise
 // 2x2x2 average pooling, [B][El^3][C] -> [B][(El/2)^3][C], bf16.
+// voxel index -> (b, z, y, x) on an El^3 grid, 32-bit (fewer than 2^31 voxels)
+struct Vox32 {
+  unsigned b, z, y, x;
+};
+__device__ __forceinline__ Vox32 vox32(unsigned v, unsigned E) {
+  Vox32 r;
+  r.x = v % E;
+  v /= E;
+  r.y = v % E;
+  v /= E;
+  r.z = v % E;
+  r.b = v / E;
+  return r;
+}
+
+// 2x2x2 average pool, eight channels per thread (C is a multiple of 16).
 __global__ void k_pool_fwd(const bf16* __restrict__ in, int El, int C, long long nout, bf16* __restrict__ out) {
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= nout * C) return;
-  const int c = (int)(i % C);
-  const long long v = i / C;
-  const int Eh = El / 2;
-  const Vox p = vox_of(v, Eh);
-  float s = 0.f;
+  const int G = C >> 3;
+  if (i >= nout * G) return;
+  const int g = (int)(i % G);
+  const unsigned v = (unsigned)(i / G), E = (unsigned)El;
+  const Vox32 p = vox32(v, E / 2);
+  float s[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
   for (int d = 0; d < 8; ++d) {
-    const long long q = (((long long)p.b * El + 2 * p.z + (d >> 2)) * El + 2 * p.y + ((d >> 1) & 1)) * El + 2 * p.x + (d & 1);
-    s += __bfloat162float(in[q * C + c]);
+    const unsigned q = ((p.b * E + 2 * p.z + (d >> 2)) * E + 2 * p.y + ((d >> 1) & 1)) * E + 2 * p.x + (d & 1);
+    const uint4 w = *reinterpret_cast<const uint4*>(in + (long long)q * C + 8 * g);
+    const bf16* h = reinterpret_cast<const bf16*>(&w);
+#pragma unroll
+    for (int k = 0; k < 8; ++k) s[k] += __bfloat162float(h[k]);
   }
-  out[i] = __float2bfloat16_rn(s * 0.125f);
+  uint4 o;
+  unsigned* u = reinterpret_cast<unsigned*>(&o);
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    __nv_bfloat162 b2 = __floats2bfloat162_rn(s[2 * k] * 0.125f, s[2 * k + 1] * 0.125f);
+    u[k] = *reinterpret_cast<unsigned*>(&b2);
+  }
+  *reinterpret_cast<uint4*>(out + (long long)v * C + 8 * g) = o;
 }
 
 // g_in[child] += g_out[parent] / 8 (fp32).
 __global__ void k_pool_bwd(const float* __restrict__ gout, int El, int C, long long nin, float* __restrict__ gin) {
+  // four channels per thread (C is a multiple of 16)
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= nin * C) return;
-  const int c = (int)(i % C);
-  const Vox p = vox_of(i / C, El);
-  const int Eh = El / 2;
-  const long long q = (((long long)p.b * Eh + p.z / 2) * Eh + p.y / 2) * Eh + p.x / 2;
-  gin[i] += 0.125f * gout[q * C + c];
+  const int G = C >> 2;
+  if (i >= nin * G) return;
+  const int g = (int)(i % G);
+  const unsigned v = (unsigned)(i / G), E = (unsigned)El, Eh = E / 2;
+  const Vox32 p = vox32(v, E);
+  const unsigned q = ((p.b * Eh + p.z / 2) * Eh + p.y / 2) * Eh + p.x / 2;
+  const float4 a = *reinterpret_cast<const float4*>(gout + (long long)q * C + 4 * g);
+  float4* dst = reinterpret_cast<float4*>(gin + (long long)v * C + 4 * g);
+  float4 b = *dst;
+  b.x += 0.125f * a.x;
+  b.y += 0.125f * a.y;
+  b.z += 0.125f * a.z;
+  b.w += 0.125f * a.w;
+  *dst = b;
 }
 
 // cat[v] = [up2(d)[v] (C1) | e[v] (C2)], bf16.
@@ -880,24 +929,45 @@ __global__ void k_cat_fwd(const bf16* __restrict__ d, int C1, const bf16* __rest
 
 // From g_cat: g_e += skip part (per fine voxel); g_d += sum over the 8 children (per coarse voxel).
 __global__ void k_cat_bwd_skip(const float* __restrict__ gcat, int C1, int C2, long long n, float* __restrict__ ge) {
+  // four channels per thread (C1, C2 are multiples of 16)
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n * C2) return;
-  const long long v = i / C2;
-  ge[i] += gcat[v * (C1 + C2) + C1 + (i % C2)];
+  const int G = C2 >> 2;
+  if (i >= n * G) return;
+  const int g = (int)(i % G);
+  const long long v = i / G;
+  const float4 a = *reinterpret_cast<const float4*>(gcat + v * (C1 + C2) + C1 + 4 * g);
+  float4* dst = reinterpret_cast<float4*>(ge + v * C2 + 4 * g);
+  float4 b = *dst;
+  b.x += a.x;
+  b.y += a.y;
+  b.z += a.z;
+  b.w += a.w;
+  *dst = b;
 }
 __global__ void k_cat_bwd_up(const float* __restrict__ gcat, int C1, int C2, int El, long long ncoarse,
                              float* __restrict__ gd) {
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= ncoarse * C1) return;
-  const int c = (int)(i % C1);
-  const int Eh = El / 2;
-  const Vox p = vox_of(i / C1, Eh);
-  float s = 0.f;
+  const int G = C1 >> 2;
+  if (i >= ncoarse * G) return;
+  const int g = (int)(i % G);
+  const unsigned v = (unsigned)(i / G), E = (unsigned)El;
+  const Vox32 p = vox32(v, E / 2);
+  float4 s = make_float4(0.f, 0.f, 0.f, 0.f);
   for (int d = 0; d < 8; ++d) {
-    const long long q = (((long long)p.b * El + 2 * p.z + (d >> 2)) * El + 2 * p.y + ((d >> 1) & 1)) * El + 2 * p.x + (d & 1);
-    s += gcat[q * (C1 + C2) + c];
+    const unsigned q = ((p.b * E + 2 * p.z + (d >> 2)) * E + 2 * p.y + ((d >> 1) & 1)) * E + 2 * p.x + (d & 1);
+    const float4 a = *reinterpret_cast<const float4*>(gcat + (long long)q * (C1 + C2) + 4 * g);
+    s.x += a.x;
+    s.y += a.y;
+    s.z += a.z;
+    s.w += a.w;
   }
-  gd[i] += s;
+  float4* dst = reinterpret_cast<float4*>(gd + (long long)v * C1 + 4 * g);
+  float4 b = *dst;
+  b.x += s.x;
+  b.y += s.y;
+  b.z += s.z;
+  b.w += s.w;
+  *dst = b;
 }
 
 // gz = g * relu'(h) as bf16 (h > 0 where the stored activation is positive).
@@ -1484,8 +1554,23 @@ tlb_status launch_conv(Net* n, const bf16* in, int Ci, int El, long long nvox, i
   return TLB_OK;
 }
 
+// out = sum of the nsplit rows of part ([nsplit][n]; overwritten).
+tlb_status sum_splits(Net* n, float* part, int nsplit, long long nn, float* out) {
+  int step = 1;
+  if (nsplit > SPLIT_GROUP) {
+    const unsigned groups = (unsigned)((nsplit + SPLIT_GROUP - 1) / SPLIT_GROUP);
+    k_sum_groups<<<dim3(nb(nn, 128), groups), 128, 0, n->stream>>>(part, nsplit, nn);
+    NET_LAUNCHED(n, "k_sum_groups");
+    step = SPLIT_GROUP;
+  }
+  k_sum_splits<<<nb(nn, 64), 64, 0, n->stream>>>(part, nsplit, nn, step, out);
+  NET_LAUNCHED(n, "k_sum_splits");
+  return TLB_OK;
+}
+
 template <int BN>
 tlb_status launch_wgrad3_t(Net* n, const Conv& c, const bf16* in, int El, int B, const bf16* gz) {
+  tlb_status st;
   const int nbr = ((El + BRX - 1) / BRX) * ((El + BRY - 1) / BRY) * ((El + BRZ - 1) / BRZ) * B;
   const int tiles = (c.co / BN) * (c.ci / 16);
   const int nsplit = std::max(1, std::min(nbr, std::min(512, (2 * 152 * 4 + tiles - 1) / tiles)));
@@ -1497,16 +1582,14 @@ tlb_status launch_wgrad3_t(Net* n, const Conv& c, const bf16* in, int El, int B,
   float* g = n->at<float>(n->o_grad);
   // weight gradient: sums over the CTAs' partials [27 * Ci][Co]
   const long long nw = 27ll * c.ci * c.co;
-  k_sum_splits<<<nb(nw, 64), 64, 0, n->stream>>>(part, nsplit, nw, g + c.w);
-  NET_LAUNCHED(n, "k_sum_splits");
+  if ((st = sum_splits(n, part, nsplit, nw, g + c.w)) != TLB_OK) return st;
   // bias gradient: column sums of gz over fixed voxel ranges, then over the ranges
   const long long V = (long long)B * El * El * El;
   const int nbs = (int)std::min<long long>(512, (V + 255) / 256);
   const long long chunk = (V + nbs - 1) / nbs;
   k_colsum<<<nbs, 256, 0, n->stream>>>(gz, V, c.co, chunk, part);
   NET_LAUNCHED(n, "k_colsum");
-  k_sum_splits<<<nb(c.co, 64), 64, 0, n->stream>>>(part, nbs, c.co, g + c.b);
-  NET_LAUNCHED(n, "k_sum_splits");
+  if ((st = sum_splits(n, part, nbs, c.co, g + c.b)) != TLB_OK) return st;
   return TLB_OK;
 }
 
@@ -1565,7 +1648,7 @@ tlb_status forward(Net* n, int B) {
     const long long V = n->vox(l, B);
     if (l > 0) {
       bf16* p = A + n->enc_p[l].act;
-      k_pool_fwd<<<nb(V * hc, 256), 256, 0, s>>>(h, El * 2, hc, V, p);
+      k_pool_fwd<<<nb(V * hc / 8, 256), 256, 0, s>>>(h, El * 2, hc, V, p);
       NET_LAUNCHED(n, "k_pool_fwd");
       h = p;
     }
@@ -1645,10 +1728,10 @@ tlb_status backward(Net* n, int B) {
     if ((st = conv_bwd(n, c1, A + n->dec_cat[l].act, A + n->dec_b[l].act, G + n->dec_b[l].grad,
                        G + n->dec_cat[l].grad, B, true)) != TLB_OK)
       return st;
-    k_cat_bwd_skip<<<nb(V * C2, 256), 256, 0, s>>>(G + n->dec_cat[l].grad, C1, C2, V, G + n->enc_e[l].grad);
+    k_cat_bwd_skip<<<nb(V * C2 / 4, 256), 256, 0, s>>>(G + n->dec_cat[l].grad, C1, C2, V, G + n->enc_e[l].grad);
     NET_LAUNCHED(n, "k_cat_bwd_skip");
     const Ten& coarse = (l + 1 <= L - 2) ? n->dec_d[l + 1] : n->enc_e[L - 1];
-    k_cat_bwd_up<<<nb(n->vox(l + 1, B) * C1, 256), 256, 0, s>>>(G + n->dec_cat[l].grad, C1, C2, El,
+    k_cat_bwd_up<<<nb(n->vox(l + 1, B) * C1 / 4, 256), 256, 0, s>>>(G + n->dec_cat[l].grad, C1, C2, El,
                                                                  n->vox(l + 1, B), G + coarse.grad);
     NET_LAUNCHED(n, "k_cat_bwd_up");
   }
@@ -1663,7 +1746,7 @@ tlb_status backward(Net* n, int B) {
     if ((st = conv_bwd(n, c1, in, A + n->enc_a[l].act, G + n->enc_a[l].grad, gin, B, true)) != TLB_OK) return st;
     if (l > 0) {
       const long long Vf = n->vox(l - 1, B);
-      k_pool_bwd<<<nb(Vf * c1.ci, 256), 256, 0, s>>>(G + n->enc_p[l].grad, n->d.edge >> (l - 1), c1.ci, Vf,
+      k_pool_bwd<<<nb(Vf * c1.ci / 4, 256), 256, 0, s>>>(G + n->enc_p[l].grad, n->d.edge >> (l - 1), c1.ci, Vf,
                                                       G + n->enc_e[l - 1].grad);
       NET_LAUNCHED(n, "k_pool_bwd");
     }

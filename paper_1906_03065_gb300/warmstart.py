@@ -265,6 +265,15 @@ def compare(net: WarmStartNet, wls, wls_learned=None, max_steps: int = 8000, che
         r["max_dev_angle_deg"] = float(np.nanmax(dev[:, 0])) if np.isfinite(dev[:, 0]).any() else None
         r["max_dev_area"] = float(np.nanmax(dev[:, 1])) if np.isfinite(dev[:, 1]).any() else None
         r["max_dev_volume"] = float(np.nanmax(dev[:, 2])) if np.isfinite(dev[:, 2]).any() else None
+        # the same gate for the plain run at its own crossing: how far the
+        # reference itself still is from the plain state at that time
+        gp, dp = out["plain"]["gate"][t], out["plain"]["dev"][t]
+        r["plain_gated"] = int(gp.sum())
+        for j, k in enumerate(("angle_deg", "area", "volume")):
+            col = dp[:, j]
+            r[f"plain_max_dev_{k}"] = float(np.nanmax(col)) if np.isfinite(col).any() else None
+            r[f"median_dev_{k}"] = float(np.nanmedian(dev[:, j])) if np.isfinite(dev[:, j]).any() else None
+            r[f"plain_median_dev_{k}"] = float(np.nanmedian(col)) if np.isfinite(col).any() else None
         out[f"ratio_{t:g}"] = r
     out["ratio_shape"] = ratios(out["plain"]["shape_steps"], out["learned"]["shape_steps"])
     return out
