@@ -288,14 +288,21 @@ tlb_status tlb_profile_steps(void* ctx, long n_steps, tlb_profile* out);
  * = 1 with TLB_FORCE_EDM, the paper's setting (Sec. 3.1): there every
  * post-collision population is an equilibrium of the cell's moments (eq.
  * LBE), so that collide pulls no population and only stores; the moment
- * pass then also writes j.  They are tried only where they
- * apply, and a new context starts on variant 13 there (else 0).
+ * pass then also writes j.  Variants 22..27 are the same collide with two
+ * x-adjacent cells per thread (tiles 0..2 at 384, then at 512 threads per
+ * SM), every stored value of the pair written by one store; they need an
+ * even nx.  Variants 19..21 are tiles 0..2 of the general collide with the
+ * pressure-tensor force.  They are tried only where they apply, and a new
+ * context starts on variant 13 there (19 with the pressure-tensor force,
+ * else 0).
  * Synchronises the stream.  Not in the paper: an autotuner for this
  * implementation's launch shape. */
 tlb_status tlb_autotune(void* ctx, int* tile_variant, int* z_chunk);
 
-/* Set the collide variant (0..18, as written by tlb_autotune; 13..18 only
- * where tau = tau_phi = tau_psi = 1 with TLB_FORCE_EDM, else TLB_ERR_ARG)
+/* Set the collide variant (0..27, as written by tlb_autotune; 13..18 and
+ * 22..27 only where tau = tau_phi = tau_psi = 1 with TLB_FORCE_EDM and the
+ * potential force, 22..27 only with an even nx, 19..21 only with the
+ * pressure-tensor force, else TLB_ERR_ARG)
  * and the planes per z chunk (1..nz) explicitly.  The results do not depend
  * on the choice beyond rounding. */
 tlb_status tlb_set_tile(void* ctx, int tile_variant, int z_chunk);

@@ -245,8 +245,10 @@ struct BatchImpl : BatchBase {
   static int collide_occ() {
     int per_sm = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-        &per_sm, k_phase<TX * TY, collide_threads<FORM>() / (TX * TY), BA, OpCollide<L, MODE, TX, TY, FORM>>,
-        TX * TY, 0);
+        &per_sm,
+        k_phase<collide_block<FORM, TX, TY>(), collide_threads<FORM>() / collide_block<FORM, TX, TY>(), BA,
+                OpCollide<L, MODE, TX, TY, FORM>>,
+        collide_block<FORM, TX, TY>(), 0);
     return std::max(1, per_sm);
   }
   static int collide_occupancy(int v) {
@@ -262,8 +264,9 @@ struct BatchImpl : BatchBase {
   template <int TX, int TY, int FORM>
   static tlb_status launch_collide_t(Batch* b, const BA* A, const int4* vg, cudaStream_t s) {
     const int n = (int)b->act.size();
-    k_phase<TX * TY, collide_threads<FORM>() / (TX * TY), BA, OpCollide<L, MODE, TX, TY, FORM>>
-        <<<b->ph_grid[4], TX * TY, 0, s>>>(A, vg, n, b->ph_ent[4], b->ph_total[4]);
+    k_phase<collide_block<FORM, TX, TY>(), collide_threads<FORM>() / collide_block<FORM, TX, TY>(), BA,
+            OpCollide<L, MODE, TX, TY, FORM>>
+        <<<b->ph_grid[4], collide_block<FORM, TX, TY>(), 0, s>>>(A, vg, n, b->ph_ent[4], b->ph_total[4]);
     b->launches++;
     return cuda_check(cudaGetLastError(), "k_phase collide");
   }

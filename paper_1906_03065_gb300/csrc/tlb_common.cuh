@@ -80,6 +80,27 @@ template <> __device__ __forceinline__ float from_real<float>(float v) { return 
 template <> __device__ __forceinline__ __half from_real<__half>(float v) { return __float2half_rn(v); }
 template <> __device__ __forceinline__ __nv_bfloat16 from_real<__nv_bfloat16>(float v) { return __float2bfloat16_rn(v); }
 
+// Two consecutive Real values (one 8 or 16-byte load).
+template <class R> struct R2Of;
+template <> struct R2Of<float> { using T = float2; };
+template <> struct R2Of<double> { using T = double2; };
+template <class R> using R2 = typename R2Of<R>::T;
+
+// Two adjacent cells' values stored together (one 4, 8 or 16-byte store;
+// p is aligned to two elements), each rounded as from_real rounds it.
+__device__ __forceinline__ void store_pair(double* p, double a, double b) {
+  *reinterpret_cast<double2*>(p) = make_double2(a, b);
+}
+__device__ __forceinline__ void store_pair(float* p, float a, float b) {
+  *reinterpret_cast<float2*>(p) = make_float2(a, b);
+}
+__device__ __forceinline__ void store_pair(__half* p, float a, float b) {
+  *reinterpret_cast<__half2*>(p) = __floats2half2_rn(a, b);
+}
+__device__ __forceinline__ void store_pair(__nv_bfloat16* p, float a, float b) {
+  *reinterpret_cast<__nv_bfloat162*>(p) = __floats2bfloat162_rn(a, b);
+}
+
 // ------------------------------------------------------------ geometry
 struct Geo {
   int nx, ny, nz;
@@ -88,6 +109,15 @@ struct Geo {
   long long P;     // plane stride of population / field arrays (>= N, padded)
   int P32;         // P as int: every population offset (3Q planes) fits 31 bits
 };
+
+// Cell (x, y, z) of linear index n < N (N < 2^31: every population offset
+// fits 31 bits), by two 32-bit divisions.
+__device__ __forceinline__ void cell_xyz(const Geo& G, long long n, int& x, int& y, int& z) {
+  const unsigned un = (unsigned)n, t = un / (unsigned)G.nx, zz = t / (unsigned)G.ny;
+  x = (int)(un - t * (unsigned)G.nx);
+  y = (int)(t - zz * (unsigned)G.ny);
+  z = (int)zz;
+}
 
 // Block coordinates of a launch.  Kernel bodies take them as an argument, so
 // one body runs either as its own grid (the hardware block index) or as one

@@ -13,8 +13,10 @@
 // Collide variants: 3 tile shapes x 4 register forms, v = 3 form + tile,
 // the smallest tile in a fifth form (v = 12), and the 3 tiles in the two
 // forms of the tau = 1 collide (v = 13..18, see variant_t1).
-constexpr int COLLIDE_NVAR = 22;
-constexpr bool variant_t1(int v) { return v >= 13 && v <= 18; }
+constexpr int COLLIDE_NVAR = 28;
+constexpr bool variant_t1(int v) { return (v >= 13 && v <= 18) || v >= 22; }
+// variants 22..27: the tau = 1 collide with two x-adjacent cells per thread
+constexpr bool variant_pair(int v) { return v >= 22 && v <= 27; }
 // variants 19..21: the general collide with the pressure-tensor force
 constexpr bool variant_pt(int v) { return v >= 19 && v <= 21; }
 
@@ -108,6 +110,7 @@ struct Ctx {
   // and with moment storage only the tau = 1 ones
   bool variant_ok(int v) const {
     if (variant_pt(v) != (p.force_form == TLB_FE_PRESSURE_TENSOR)) return false;
+    if (variant_pair(v) && nx % 2 != 0) return false;  // pairs never straddle a row
     if (variant_t1(v)) return t1_ok();
     return !moments();
   }

@@ -469,7 +469,7 @@ struct FaceDist {
 // ties going to the lowest element index.
 constexpr int MAXG = 12;  // generators (and faces) per feature
 constexpr int SCAT_W = 4;       // slices per lane per round
-constexpr int SCAT_SPLIT = 8;   // warps sharing one group of 32 features (round r goes to r % SCAT_SPLIT)
+constexpr int SCAT_SPLIT = 4;   // warps sharing one group of 32 features (round r goes to r % SCAT_SPLIT)
 // warps per block (every lane sweeps one feature): FP64 halves them to keep
 // the shared memory under the static limit
 template <class Real> constexpr int scatter_warps() { return sizeof(Real) == 4 ? 4 : 2; }

@@ -346,7 +346,7 @@ struct Impl : ImplBase {
   template <int TXv, int TYv, int FORM>
   static tlb_status collide_tile(Ctx* c, LBArgs<MODE>& la, cudaStream_t s) {
     dim3 grid(blocks(c->nx, TXv), blocks(c->ny, TYv), blocks(c->nz, c->tiles_zc));
-    k_collide<L, MODE, TXv, TYv, FORM><<<grid, TXv * TYv, 0, s>>>(la);
+    k_collide<L, MODE, TXv, TYv, FORM><<<grid, collide_block<FORM, TXv, TYv>(), 0, s>>>(la);
     TLB_LAUNCHED(c, "k_collide");
     return TLB_OK;
   }

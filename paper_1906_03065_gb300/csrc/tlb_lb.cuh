@@ -60,9 +60,8 @@ __device__ __forceinline__ void moments_body(const LBArgs<MODE>& a, const Blk& b
   const Geo G = a.G;
   long long n = (long long)blk.x * blockDim.x + threadIdx.x;
   if (n >= G.N) return;
-  int x = (int)(n % G.nx);
-  int y = (int)((n / G.nx) % G.ny);
-  int z = (int)(n / ((long long)G.nx * G.ny));
+  int x, y, z;
+  cell_xyz(G, n, x, y, z);
   Pull<L, MODE> p;
   p.load(a.lo_src, a.rest_src, G, x, y, z);
   CellMoments<Real> m = p.moments();
@@ -89,7 +88,8 @@ __device__ __forceinline__ void moments_recon_body(const LBArgs<MODE>& a, const 
   const Geo G = a.G;
   long long n = (long long)blk.x * blockDim.x + threadIdx.x;
   if (n >= G.N) return;
-  const int x = (int)(n % G.nx), y = (int)((n / G.nx) % G.ny), z = (int)(n / ((long long)G.nx * G.ny));
+  int x, y, z;
+  cell_xyz(G, n, x, y, z);
   const Nbr<L> nb(G, x, y, z);
   Pull<L, MODE> p;
 #pragma unroll
@@ -288,7 +288,9 @@ __device__ __forceinline__ void pressure_tensor(const FEParams<Real>& fe, Real d
 // moments rho - 1 and j that the moment pass wrote (summed in the same order
 // as the pull of the general forms) and pulls no population: it only stores
 // them.
-template <int FORM> constexpr bool form_t1() { return FORM == 5 || FORM == 6; }
+template <int FORM> constexpr bool form_t1() { return FORM == 5 || FORM == 6 || FORM == 8 || FORM == 9; }
+// forms 8 and 9: the tau = 1 collide with two x-adjacent cells per thread
+template <int FORM> constexpr bool form_pair() { return FORM == 8 || FORM == 9; }
 
 template <class L, int MODE, int TX, int TY, int FORM>
 __device__ __forceinline__ void collide_gen_body(const LBArgs<MODE>& a, const Blk& blk) {
@@ -668,12 +670,14 @@ __device__ __forceinline__ void collide_t1_body(const LBArgs<MODE>& a, const Blk
   constexpr int HY = D3 ? 2 : 0;
   constexpr int MX = TX + 4, MY = TY + 2 * HY;
   constexpr int UX = TX + 2, UY = TY + (D3 ? 2 : 0);
-  constexpr int NT = TX * TY;
+  // cells per thread: two x-adjacent cells in the pair forms (8, 9)
+  constexpr int NC = form_pair<FORM>() ? 2 : 1;
+  constexpr int NT = TX / NC * TY;
   __shared__ R4<Real> smom[5][MY * MX];  // (rho - 1, phi, psi, I) per cell
   __shared__ R4<Real> smu[3][UY * UX];   // (mu~rho, mu_phi, mu_psi', -) per cell
 
   const Geo G = a.G;
-  const int tx = threadIdx.x % TX, ty = threadIdx.x / TX, tid = threadIdx.x;
+  const int tid = threadIdx.x, tx = NC * (tid % (TX / NC)), ty = tid / (TX / NC);
   const int x0 = blk.x * TX, y0 = blk.y * TY;
   const int z0 = blk.z * a.zc;
   const int z1 = min(z0 + a.zc, G.nz);
@@ -741,115 +745,173 @@ __device__ __forceinline__ void collide_t1_body(const LBArgs<MODE>& a, const Blk
 
   auto collide = [&](int zz) {
     if (!active) return;
-    const int n = (zz * G.ny + y) * G.nx + x;
-    // the cell's momentum first: its loads run under the stencil below
-    const Real j[3] = {a.jm[n], a.jm[G.P32 + n], a.jm[2 * G.P32 + n]};
-    const bool ib = a.bflag[((zz >> 2) * a.nby + (y >> 2)) * a.nbx + (x >> 2)] != 0;
-    const R4<Real> mom = smom[(zz + 10) % 5][(ty + HY) * MX + tx + 2];
-    const Real drho = mom.x, phi = mom.y, psi = mom.z;
-    const Real rho = Real(1) + drho;
-    // gradients of the potentials (radius 1, isotropic stencil)
-    Real gm[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
-    const int ux = tx + 1, uy = ty + (D3 ? 1 : 0);
+    const int n = (zz * G.ny + y) * G.nx + x;  // the (first) cell
+    // value of cell c: stored together for the two cells of a pair
+    auto put = [&](auto* p, Real v0, Real v1) {
+      using T = typename std::remove_pointer<decltype(p)>::type;
+      if constexpr (NC == 2) store_pair(p, v0, v1);
+      else *p = from_real<T>(v0);
+    };
+    // the cells' momenta first: their loads run under the stencil below
+    Real j[NC][3];
 #pragma unroll
-    for (int i = 1; i < Q; ++i) {
-      const R4<Real> m4 = smu[(zz + L::cz(i) + 9) % 3][(uy + L::cy(i)) * UX + ux + L::cx(i)];
-      const Real w = Real(L::w(i));
-      const Real mv[3] = {m4.x, m4.y, m4.z};
-#pragma unroll
-      for (int q = 0; q < 3; ++q) {
-        const Real v = w * mv[q];
-        if (L::cx(i)) gm[q][0] += L::cx(i) > 0 ? v : -v;
-        if (L::cy(i)) gm[q][1] += L::cy(i) > 0 ? v : -v;
-        if (L::cz(i)) gm[q][2] += L::cz(i) > 0 ? v : -v;
+    for (int d = 0; d < 3; ++d) {
+      if constexpr (NC == 2) {
+        const auto jj = *reinterpret_cast<const R2<Real>*>(a.jm + d * G.P32 + n);
+        j[0][d] = jj.x;
+        j[1][d] = jj.y;
+      } else {
+        j[0][d] = a.jm[d * G.P32 + n];
       }
     }
-    const R4<Real> muc = smu[(zz + 9) % 3][uy * UX + ux];
-    const Real mup = muc.y, mus = muc.z;
-    Real F[3];
+    // (the cells of a pair share their brick: x is even, bricks are 4 wide)
+    const bool ib = a.bflag[((zz >> 2) * a.nby + (y >> 2)) * a.nbx + (x >> 2)] != 0;
+    Real drho[NC], phi[NC], psi[NC], rho[NC], F[NC][3], u[NC][3], du[NC][3], v[NC][3], us[NC][3];
+    Real uu[NC], vv[NC], dus[NC], gmp[NC], gms[NC];
 #pragma unroll
-    for (int d = 0; d < 3; ++d) {
-      F[d] = -Real(3) * (rho * gm[0][d] + phi * gm[1][d] + psi * gm[2][d]);
-      if (ib) F[d] += a.fib[d * G.P32 + n];
-    }
-    if (!D3) F[1] = 0;
-    const Real irho = Real(1) / rho;
-    Real u[3], du[3], v[3], us[3];
+    for (int c = 0; c < NC; ++c) {
+      const int lx = tx + c;  // tile-local x of the cell
+      const R4<Real> mom = smom[(zz + 10) % 5][(ty + HY) * MX + lx + 2];
+      drho[c] = mom.x;
+      phi[c] = mom.y;
+      psi[c] = mom.z;
+      rho[c] = Real(1) + drho[c];
+      // gradients of the potentials (radius 1, isotropic stencil)
+      Real gm[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+      const int ux = lx + 1, uy = ty + (D3 ? 1 : 0);
 #pragma unroll
-    for (int d = 0; d < 3; ++d) {
-      u[d] = j[d] * irho;
-      du[d] = F[d] * irho;
-      v[d] = u[d] + Real(0.5) * du[d];
-      us[d] = u[d] + u[d] + du[d];  // u + (u + du)
+      for (int i = 1; i < Q; ++i) {
+        const R4<Real> m4 = smu[(zz + L::cz(i) + 9) % 3][(uy + L::cy(i)) * UX + ux + L::cx(i)];
+        const Real w = Real(L::w(i));
+        const Real mv[3] = {m4.x, m4.y, m4.z};
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+          const Real vq = w * mv[q];
+          if (L::cx(i)) gm[q][0] += L::cx(i) > 0 ? vq : -vq;
+          if (L::cy(i)) gm[q][1] += L::cy(i) > 0 ? vq : -vq;
+          if (L::cz(i)) gm[q][2] += L::cz(i) > 0 ? vq : -vq;
+        }
+      }
+      const R4<Real> muc = smu[(zz + 9) % 3][uy * UX + ux];
+#pragma unroll
+      for (int d = 0; d < 3; ++d) {
+        F[c][d] = -Real(3) * (rho[c] * gm[0][d] + phi[c] * gm[1][d] + psi[c] * gm[2][d]);
+        if (ib) F[c][d] += a.fib[d * G.P32 + n + c];
+      }
+      if (!D3) F[c][1] = 0;
+      const Real irho = Real(1) / rho[c];
+#pragma unroll
+      for (int d = 0; d < 3; ++d) {
+        u[c][d] = j[c][d] * irho;
+        du[c][d] = F[c][d] * irho;
+        v[c][d] = u[c][d] + Real(0.5) * du[c][d];
+        us[c][d] = u[c][d] + u[c][d] + du[c][d];  // u + (u + du)
+      }
+      uu[c] = u[c][0] * u[c][0] + u[c][1] * u[c][1] + u[c][2] * u[c][2];
+      vv[c] = v[c][0] * v[c][0] + v[c][1] * v[c][1] + v[c][2] * v[c][2];
+      dus[c] = du[c][0] * us[c][0] + du[c][1] * us[c][1] + du[c][2] * us[c][2];
+      gmp[c] = a.gphi * muc.y;
+      gms[c] = a.gpsi * muc.z;
     }
-    const Real uu = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
-    const Real vv = v[0] * v[0] + v[1] * v[1] + v[2] * v[2];
-    const Real dus = du[0] * us[0] + du[1] * us[1] + du[2] * us[2];
-    const Real gmp = a.gphi * mup, gms = a.gpsi * mus;
+    const int c1 = NC - 1;  // the second cell (the first again without pairs)
     if (a.mst) {
       // moment storage: the 11 values whose equilibria are this cell's
       // post-collision populations (see EqCell)
       Real* M = a.mst;
-      M[M_DRHO * G.P32 + n] = drho;
+      put(M + M_DRHO * G.P32 + n, drho[0], drho[c1]);
 #pragma unroll
       for (int d = 0; d < 3; ++d) {
-        M[(M_W + d) * G.P32 + n] = radd(u[d], du[d]);
-        M[(M_V + d) * G.P32 + n] = v[d];
+        put(M + (M_W + d) * G.P32 + n, radd(u[0][d], du[0][d]), radd(u[c1][d], du[c1][d]));
+        put(M + (M_V + d) * G.P32 + n, v[0][d], v[c1][d]);
       }
-      M[M_PHI * G.P32 + n] = phi;
-      M[M_GMP * G.P32 + n] = gmp;
-      M[M_PSI * G.P32 + n] = psi;
-      M[M_GMS * G.P32 + n] = gms;
+      put(M + M_PHI * G.P32 + n, phi[0], phi[c1]);
+      put(M + M_GMP * G.P32 + n, gmp[0], gmp[c1]);
+      put(M + M_PSI * G.P32 + n, psi[0], psi[c1]);
+      put(M + M_GMS * G.P32 + n, gms[0], gms[c1]);
     } else {
       // f* = f^eq(rho, u) + w rho dP: w [drho + rho p(u)] + w rho dP; for c and
       // -c, p = A +- 3 c.u and dP = B +- 3 c.du with the shared even parts
-      const Real mu15 = rmul(Real(-1.5), uu), md15 = rmul(Real(-1.5), dus);
+      Real mu15[NC], md15[NC];
+#pragma unroll
+      for (int c = 0; c < NC; ++c) {
+        mu15[c] = rmul(Real(-1.5), uu[c]);
+        md15[c] = rmul(Real(-1.5), dus[c]);
+      }
       {
         const Real w0 = Real(L::w(0));
-        a.lo_dst[plane_f<L>(0) * G.P32 + n] = from_real<Store>(rfma(rmul(rho, w0), md15, rmul(w0, rfma(rho, mu15, drho))));
+        Real f0[NC];
+#pragma unroll
+        for (int c = 0; c < NC; ++c)
+          f0[c] = rfma(rmul(rho[c], w0), md15[c], rmul(w0, rfma(rho[c], mu15[c], drho[c])));
+        put(a.lo_dst + plane_f<L>(0) * G.P32 + n, f0[0], f0[c1]);
       }
 #pragma unroll
       for (int i = 1; i < Q; ++i) {
         if (L::opp(i) < i) continue;
         const int o = L::opp(i);
         const Real w = Real(L::w(i));
-        const Real wrho = rmul(rho, w);
-        const Real cu = L::cx(i) * u[0] + L::cy(i) * u[1] + L::cz(i) * u[2];
-        const Real cdu = L::cx(i) * du[0] + L::cy(i) * du[1] + L::cz(i) * du[2];
-        const Real cus = L::cx(i) * us[0] + L::cy(i) * us[1] + L::cz(i) * us[2];
-        const Real A = rfma(rmul(Real(4.5), cu), cu, mu15);
-        const Real B = rfma(rmul(Real(4.5), cdu), cus, md15);
-        const Real fp = rfma(wrho, rfma(Real(3), cdu, B), rmul(w, rfma(rho, rfma(Real(3), cu, A), drho)));
-        const Real fm = rfma(wrho, rfma(Real(-3), cdu, B), rmul(w, rfma(rho, rfma(Real(-3), cu, A), drho)));
-        a.lo_dst[plane_f<L>(i) * G.P32 + n] = from_real<Store>(fp);
-        a.lo_dst[plane_f<L>(o) * G.P32 + n] = from_real<Store>(fm);
+        Real fp[NC], fm[NC];
+#pragma unroll
+        for (int c = 0; c < NC; ++c) {
+          const Real wrho = rmul(rho[c], w);
+          const Real cu = L::cx(i) * u[c][0] + L::cy(i) * u[c][1] + L::cz(i) * u[c][2];
+          const Real cdu = L::cx(i) * du[c][0] + L::cy(i) * du[c][1] + L::cz(i) * du[c][2];
+          const Real cus = L::cx(i) * us[c][0] + L::cy(i) * us[c][1] + L::cz(i) * us[c][2];
+          const Real A = rfma(rmul(Real(4.5), cu), cu, mu15[c]);
+          const Real B = rfma(rmul(Real(4.5), cdu), cus, md15[c]);
+          fp[c] = rfma(wrho, rfma(Real(3), cdu, B), rmul(w, rfma(rho[c], rfma(Real(3), cu, A), drho[c])));
+          fm[c] = rfma(wrho, rfma(Real(-3), cdu, B), rmul(w, rfma(rho[c], rfma(Real(-3), cu, A), drho[c])));
+        }
+        put(a.lo_dst + plane_f<L>(i) * G.P32 + n, fp[0], fp[c1]);
+        put(a.lo_dst + plane_f<L>(o) * G.P32 + n, fm[0], fm[c1]);
       }
       // g* = g^eq(phi, mu_phi, v), h* = h^eq(psi, mu_psi', v): one velocity
       // polynomial per pair of opposite velocities serves both
-      const Real g3 = rmul(Real(3), gmp), h3 = rmul(Real(3), gms);
-      const Real mv15 = rmul(Real(-1.5), vv);
+      Real g3[NC], h3[NC], mv15[NC];
+#pragma unroll
+      for (int c = 0; c < NC; ++c) {
+        g3[c] = rmul(Real(3), gmp[c]);
+        h3[c] = rmul(Real(3), gms[c]);
+        mv15[c] = rmul(Real(-1.5), vv[c]);
+      }
 #pragma unroll
       for (int i = 1; i < Q; ++i) {
         if (L::opp(i) < i) continue;
         const int o = L::opp(i);
         const Real w = Real(L::w(i));
-        const Real cv = L::cx(i) * v[0] + L::cy(i) * v[1] + L::cz(i) * v[2];
-        const Real C = rfma(rmul(Real(4.5), cv), cv, mv15);
-        const Real pp = rfma(Real(3), cv, C), pm = rfma(Real(-3), cv, C);
-        a.lo_dst[plane_g<L>(i) * G.P32 + n] = from_real<Store>(rmul(w, rfma(phi, pp, g3)));
-        a.lo_dst[plane_g<L>(o) * G.P32 + n] = from_real<Store>(rmul(w, rfma(phi, pm, g3)));
-        a.lo_dst[plane_h<L>(i) * G.P32 + n] = from_real<Store>(rmul(w, rfma(psi, pp, h3)));
-        a.lo_dst[plane_h<L>(o) * G.P32 + n] = from_real<Store>(rmul(w, rfma(psi, pm, h3)));
+        Real gp[NC], gq[NC], hp[NC], hq[NC];
+#pragma unroll
+        for (int c = 0; c < NC; ++c) {
+          const Real cv = L::cx(i) * v[c][0] + L::cy(i) * v[c][1] + L::cz(i) * v[c][2];
+          const Real C = rfma(rmul(Real(4.5), cv), cv, mv15[c]);
+          const Real pp = rfma(Real(3), cv, C), pm = rfma(Real(-3), cv, C);
+          gp[c] = rmul(w, rfma(phi[c], pp, g3[c]));
+          gq[c] = rmul(w, rfma(phi[c], pm, g3[c]));
+          hp[c] = rmul(w, rfma(psi[c], pp, h3[c]));
+          hq[c] = rmul(w, rfma(psi[c], pm, h3[c]));
+        }
+        put(a.lo_dst + plane_g<L>(i) * G.P32 + n, gp[0], gp[c1]);
+        put(a.lo_dst + plane_g<L>(o) * G.P32 + n, gq[0], gq[c1]);
+        put(a.lo_dst + plane_h<L>(i) * G.P32 + n, hp[0], hp[c1]);
+        put(a.lo_dst + plane_h<L>(o) * G.P32 + n, hq[0], hq[c1]);
       }
       // rest populations close the zeroth moments: ord - 3 Gm (1 - w0) - 1.5 w0 ord v^2
       const Real w0 = Real(L::w(0));
-      a.rest_dst[n] = from_real<Rest>(radd(rfma(g3, w0 - Real(1), phi), rmul(rmul(Real(-1.5) * w0, phi), vv)));
-      a.rest_dst[G.P32 + n] = from_real<Rest>(radd(rfma(h3, w0 - Real(1), psi), rmul(rmul(Real(-1.5) * w0, psi), vv)));
+      Real r0[NC], r1[NC];
+#pragma unroll
+      for (int c = 0; c < NC; ++c) {
+        r0[c] = radd(rfma(g3[c], w0 - Real(1), phi[c]), rmul(rmul(Real(-1.5) * w0, phi[c]), vv[c]));
+        r1[c] = radd(rfma(h3[c], w0 - Real(1), psi[c]), rmul(rmul(Real(-1.5) * w0, psi[c]), vv[c]));
+      }
+      put(a.rest_dst + n, r0[0], r0[c1]);
+      put(a.rest_dst + G.P32 + n, r1[0], r1[c1]);
     }
     if (ib)
 #pragma unroll
-      for (int d = 0; d < 3; ++d) a.ftot[d * G.P32 + n] = F[d];
-    if (!(rho == rho) || !(phi == phi) || !(psi == psi)) atomicOr(a.status, (unsigned)ST_NAN);
+      for (int d = 0; d < 3; ++d) put(a.ftot + d * G.P32 + n, F[0][d], F[c1][d]);
+#pragma unroll
+    for (int c = 0; c < NC; ++c)
+      if (!(rho[c] == rho[c]) || !(phi[c] == phi[c]) || !(psi[c] == psi[c])) atomicOr(a.status, (unsigned)ST_NAN);
   };
 
   // prologue: ring planes z0-2 .. z0+2, potentials z0 then z0-1 (a wall
@@ -886,12 +948,17 @@ __device__ __forceinline__ void collide_body(const LBArgs<MODE>& a, const Blk& b
 // the tau = 1 collide at 5: 768 and 6: 1024).
 template <int FORM> constexpr int collide_threads() {
   return FORM == 1 ? 512
-                   : (FORM == 2 || FORM == 5 ? 768 : (FORM == 3 || FORM == 6 ? 1024 : (FORM == 4 ? 896 : 640)));
+                   : (FORM == 2 || FORM == 5 ? 768
+                                             : (FORM == 3 || FORM == 6 ? 1024
+                                                                       : (FORM == 4 ? 896 : (FORM == 8 ? 384 : (FORM == 9 ? 512 : 640)))));
 }
+// threads of a collide block: one per cell of the TX x TY tile, or one per
+// pair of cells in the pair forms
+template <int FORM, int TX, int TY> constexpr int collide_block() { return form_pair<FORM>() ? TX / 2 * TY : TX * TY; }
 
 
 template <class L, int MODE, int TX, int TY, int FORM>
-__global__ void __launch_bounds__(TX* TY, collide_threads<FORM>() / (TX * TY))
+__global__ void __launch_bounds__(collide_block<FORM, TX, TY>(), collide_threads<FORM>() / collide_block<FORM, TX, TY>())
     k_collide(const __grid_constant__ LBArgs<MODE> a) {
   collide_body<L, MODE, TX, TY, FORM>(a, hw_blk());
 }
@@ -928,6 +995,14 @@ __host__ tlb_status collide_variant(int v, Fn&& fn) {
     case 19: return fn(CIdx<32>{}, CIdx<Y0>{}, CIdx<7>{});
     case 20: return fn(CIdx<X1>{}, CIdx<Y1>{}, CIdx<7>{});
     case 21: return fn(CIdx<X2>{}, CIdx<Y0>{}, CIdx<7>{});
+    // the tau = 1 pair forms: the three tiles with 384 and 512 threads per
+    // SM (two cells per thread)
+    case 22: return fn(CIdx<32>{}, CIdx<Y0>{}, CIdx<8>{});
+    case 23: return fn(CIdx<X1>{}, CIdx<Y1>{}, CIdx<8>{});
+    case 24: return fn(CIdx<X2>{}, CIdx<Y0>{}, CIdx<8>{});
+    case 25: return fn(CIdx<32>{}, CIdx<Y0>{}, CIdx<9>{});
+    case 26: return fn(CIdx<X1>{}, CIdx<Y1>{}, CIdx<9>{});
+    case 27: return fn(CIdx<X2>{}, CIdx<Y0>{}, CIdx<9>{});
     default: return fn(CIdx<32>{}, CIdx<Y0>{}, CIdx<0>{});
   }
 }
@@ -942,7 +1017,8 @@ __global__ void k_mu_global(Geo G, FEParams<typename Prec<MODE>::Real> fe, const
   using Real = typename Prec<MODE>::Real;
   long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (n >= G.N) return;
-  int x = (int)(n % G.nx), y = (int)((n / G.nx) % G.ny), z = (int)(n / ((long long)G.nx * G.ny));
+  int x, y, z;
+  cell_xyz(G, n, x, y, z);
   const Real* F[3] = {rho, phi, psi};
   Real lap[3] = {0, 0, 0};
   for (int i = 1; i < L::Q; ++i) {
@@ -974,7 +1050,8 @@ __global__ void k_init_eq(Geo G, const typename Prec<MODE>::Real* rho, const typ
   using Rest = typename Prec<MODE>::Rest;
   long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (n >= G.N) return;
-  int x = (int)(n % G.nx), y = (int)((n / G.nx) % G.ny), z = (int)(n / ((long long)G.nx * G.ny));
+  int x, y, z;
+  cell_xyz(G, n, x, y, z);
   for (int i = 0; i < L::Q; ++i) {
     int tz = z + L::cz(i);
     long long src;
@@ -1055,7 +1132,8 @@ __global__ void k_fields(Geo G, const typename Prec<MODE>::Store* lo, const type
   using Real = typename Prec<MODE>::Real;
   long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (n >= G.N) return;
-  int x = (int)(n % G.nx), y = (int)((n / G.nx) % G.ny), z = (int)(n / ((long long)G.nx * G.ny));
+  int x, y, z;
+  cell_xyz(G, n, x, y, z);
   Pull<L, MODE> p;
   p.load(lo, rest, G, x, y, z);
   CellMoments<Real> m = p.moments();
@@ -1102,7 +1180,8 @@ __device__ __forceinline__ void residual_body(const Geo& G, const typename Prec<
   if (blk.x < ncb) {
     const long long n = (long long)blk.x * blockDim.x + threadIdx.x;
     if (n < G.N) {
-      const int x = (int)(n % G.nx), y = (int)((n / G.nx) % G.ny), z = (int)(n / ((long long)G.nx * G.ny));
+      int x, y, z;
+      cell_xyz(G, n, x, y, z);
       Pull<L, MODE> p;
       p.load(lo, rest, G, x, y, z);
       double ph = 0, ps = 0;

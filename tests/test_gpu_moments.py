@@ -141,3 +141,18 @@ def test_refused_where_it_does_not_apply():
     from paper_1906_03065_gb300 import Batch
     with pytest.raises(TLBError):
         Batch([_moments(W.small_2d("f64"))])
+
+
+def test_pair_collide_stores_the_same_moments():
+    """With moment storage the tau = 1 collide with two cells per thread
+    (variants 22-27) writes the same 11 moments per cell as the single-cell
+    collide."""
+    wl = _moments(W.small_3d("f32"))
+    a, b = _sim(wl).init(), _sim(wl).init()
+    a.set_tile(14, 8)
+    b.set_tile(23, 8)
+    a.step(20)
+    b.step(20)
+    for n in ("C1", "C2", "C3", "u"):
+        assert np.array_equal(a.field(n), b.field(n)), n
+    assert np.array_equal(a.nodes(0), b.nodes(0))

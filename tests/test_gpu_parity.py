@@ -208,18 +208,36 @@ def test_full_size_capsule_3d_init_and_step():
 @pytest.mark.parametrize("storage", ["f32", "f16"])
 def test_collide_tile_variants_agree(storage):
     """Every tile shape, z chunk and register form of the collide (prefetching,
-    640/768/1024 threads per SM) give the same state (the per-cell
-    arithmetic does not depend on them)."""
+    640/768/1024 threads per SM, one or two cells per thread) give the same
+    state (the per-cell arithmetic does not depend on them)."""
     wl = W.small_3d(storage)
     ref = _sim(wl).init()
     ref.step(12)
     P = ref.pops()
     for v, zc in ((0, 8), (1, 5), (2, 16), (3, 7), (4, 12), (5, 34), (6, 9), (7, 12), (8, 3), (9, 12), (10, 6),
-                  (11, 20), (12, 11), (13, 7), (14, 12), (15, 9), (16, 5), (17, 20), (18, 11)):
+                  (11, 20), (12, 11), (13, 7), (14, 12), (15, 9), (16, 5), (17, 20), (18, 11), (22, 7), (23, 12),
+                  (24, 9), (25, 5), (26, 20), (27, 11)):
         g = _sim(wl).init()
         g.set_tile(v, zc)
         g.step(12)
         assert np.abs(g.pops() - P).max() < 1e-6, (v, zc)
+
+
+def test_pair_variants_need_an_even_row():
+    """The tau = 1 collide with two x-adjacent cells per thread (variants
+    22-27) stores the pair together, so it is refused where nx is odd; with
+    an even nx it is bitwise the single-cell collide, in 2D FP64 too."""
+    from paper_1906_03065_gb300 import TLBError
+    g = _sim(W.small_3d("f32", nx=41)).init()
+    with pytest.raises(TLBError):
+        g.set_tile(22, 8)
+    wl = W.small_2d("f64")
+    a, b = _sim(wl).init(), _sim(wl).init()
+    a.set_tile(13, 8)
+    b.set_tile(25, 8)
+    a.step(30)
+    b.step(30)
+    assert np.array_equal(a.pops(), b.pops())
 
 
 def test_tau1_collide_only_where_it_applies():
