@@ -198,6 +198,7 @@ def main():
                     help="skip the lines of the 2D FP64 capsule, the FP16/BF16 bridge and the sweep to residual")
     ap.add_argument("--no-sweep", action="store_true")
     ap.add_argument("--no-net", action="store_true")
+    ap.add_argument("--no-validation", action="store_true", help="skip the 2D validation sweep of Sec. 4.1")
     ap.add_argument("--warmstart", action="store_true",
                     help="the full time-to-equilibrium experiment of the learned warm start (128 training "
                          "equilibria, 32 held-out instances; minutes) instead of the reduced default one")
@@ -596,6 +597,30 @@ def main():
             net_line["time_to_equilibrium"] = tte
         torch.cuda.empty_cache()
 
+    # the paper's 2D validation sweep (Sec. 4.1, symmetric case): the capsule
+    # (ks = kb = 1e-2) and the pure lens for the 20 values of kappa_3, at the
+    # paper's size (R = 20, 240 x 120), each set relaxed as one FP32 batch
+    validation = {}
+    if rank == 0 and not args.no_validation:
+        from paper_1906_03065_gb300 import validation as V
+        torch.cuda.empty_cache()
+        steps_v = 10000
+        cases = V.symmetric_case()
+        torch.cuda.synchronize(dev)
+        tv = time.perf_counter()
+        rows = V.deformation_sweep(cases, ks_list=(1e-2,), kb_list=(1e-2,), steps=steps_v, lens=True, device=dev)
+        torch.cuda.synchronize(dev)
+        wall_v = time.perf_counter() - tv
+        cells_v = 2 * len(cases) * 240 * 120
+        validation = {"workload": "Sec. 4.1 symmetric case: kappa_1 = kappa_2 = 8e-3, kappa_3 = 5e-4 .. 1e-2 (20 "
+                                  "values), R = 20 on 240 x 120; capsule ks = kb = 1e-2 and the pure lens, FP32, "
+                                  "two batches of 20 lattices",
+                      "steps": steps_v, "wall_s": wall_v, "value": cells_v * steps_v / wall_v / 1e6,
+                      "unit": "MLUPS (cell updates of all lattices / wall time)",
+                      "g12_over_g13": [r["g12/g13"] for r in rows if r["ks"] is not None],
+                      "D_capsule": [r["D"] for r in rows if r["ks"] is not None],
+                      "D_lens": [r["D"] for r in rows if r["ks"] is None]}
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         import oracle
@@ -635,6 +660,7 @@ def main():
             "lowprec_storage": lowprec,
             "batched_sweep": sweep,
             "warm_start_net": net_line,
+            "validation_sweep": validation,
         }))
     if dist:
         dist.destroy_process_group()

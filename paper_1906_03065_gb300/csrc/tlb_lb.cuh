@@ -674,7 +674,7 @@ __device__ __forceinline__ void collide_t1_body(const LBArgs<MODE>& a, const Blk
   constexpr int NC = form_pair<FORM>() ? 2 : 1;
   constexpr int NT = TX / NC * TY;
   __shared__ R4<Real> smom[5][MY * MX];  // (rho - 1, phi, psi, I) per cell
-  __shared__ R4<Real> smu[3][UY * UX];   // (mu~rho, mu_phi, mu_psi', -) per cell
+  __shared__ R4<Real> smu[4][UY * UX];   // (mu~rho, mu_phi, mu_psi', -) per cell
 
   const Geo G = a.G;
   const int tid = threadIdx.x, tx = NC * (tid % (TX / NC)), ty = tid / (TX / NC);
@@ -715,9 +715,9 @@ __device__ __forceinline__ void collide_t1_body(const LBArgs<MODE>& a, const Blk
 
   // chemical potentials of plane p on the tile plus a halo of 1
   auto compute_mu = [&](int p) {
-    const int slot = (p + 9) % 3;
+    const int slot = (p + 8) % 4;
     if (G.wall && (p < 0 || p >= G.nz)) {  // mirror ghost: mu(-1) = mu(0), mu(nz) = mu(nz-1)
-      const int src = (min(max(p, 0), G.nz - 1) + 9) % 3;
+      const int src = (min(max(p, 0), G.nz - 1) + 8) % 4;
       for (int k = tid; k < UX * UY; k += NT) smu[slot][k] = smu[src][k];
       return;
     }
@@ -781,7 +781,7 @@ __device__ __forceinline__ void collide_t1_body(const LBArgs<MODE>& a, const Blk
       const int ux = lx + 1, uy = ty + (D3 ? 1 : 0);
 #pragma unroll
       for (int i = 1; i < Q; ++i) {
-        const R4<Real> m4 = smu[(zz + L::cz(i) + 9) % 3][(uy + L::cy(i)) * UX + ux + L::cx(i)];
+        const R4<Real> m4 = smu[(zz + L::cz(i) + 8) % 4][(uy + L::cy(i)) * UX + ux + L::cx(i)];
         const Real w = Real(L::w(i));
         const Real mv[3] = {m4.x, m4.y, m4.z};
 #pragma unroll
@@ -792,7 +792,7 @@ __device__ __forceinline__ void collide_t1_body(const LBArgs<MODE>& a, const Blk
           if (L::cz(i)) gm[q][2] += L::cz(i) > 0 ? vq : -vq;
         }
       }
-      const R4<Real> muc = smu[(zz + 9) % 3][uy * UX + ux];
+      const R4<Real> muc = smu[(zz + 8) % 4][uy * UX + ux];
 #pragma unroll
       for (int d = 0; d < 3; ++d) {
         F[c][d] = -Real(3) * (rho[c] * gm[0][d] + phi[c] * gm[1][d] + psi[c] * gm[2][d]);
@@ -914,20 +914,28 @@ __device__ __forceinline__ void collide_t1_body(const LBArgs<MODE>& a, const Blk
       if (!(rho[c] == rho[c]) || !(phi[c] == phi[c]) || !(psi[c] == psi[c])) atomicOr(a.status, (unsigned)ST_NAN);
   };
 
-  // prologue: ring planes z0-2 .. z0+2, potentials z0 then z0-1 (a wall
-  // ghost copies its neighbour, so the real plane comes first)
+  // prologue: ring planes z0-2 .. z0+2; potentials z0, then z0-1 and z0+1
+  // (a wall ghost copies its neighbour, so the real plane comes first); then
+  // plane z0+3 into the slot of z0-2
   for (int p = z0 - 2; p <= z0 + 2; ++p) issue_plane(p);
   cp_async_wait_all();
   __syncthreads();
   compute_mu(z0);
   __syncthreads();
   compute_mu(z0 - 1);
+  compute_mu(z0 + 1);
   __syncthreads();
+  if (z0 + 3 <= z1 + 1) issue_plane(z0 + 3);
+  cp_async_wait_all();
+  __syncthreads();
+  // One barrier per plane: the potentials two planes ahead are computed in
+  // the same phase as the collision of this plane (their threads' uneven
+  // shares of the haloed potentials even out against the collisions).
   for (int zz = z0; zz < z1; ++zz) {
-    // plane zz + 3 replaces plane zz - 2, which no step of this iteration reads
-    if (zz + 3 <= z1 + 1) issue_plane(zz + 3);
-    compute_mu(zz + 1);
-    __syncthreads();
+    // plane zz + 4 replaces plane zz - 1 and the potentials of zz + 2 those
+    // of zz - 2: neither is read in this iteration
+    if (zz + 4 <= z1 + 1) issue_plane(zz + 4);
+    if (zz + 2 <= z1) compute_mu(zz + 2);
     collide(zz);
     cp_async_wait_all();
     __syncthreads();

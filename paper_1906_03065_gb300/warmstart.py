@@ -259,8 +259,10 @@ def compare(net: WarmStartNet, wls, wls_learned=None, max_steps: int = 8000, che
         p, l = out["plain"]["first"][t], out["learned"]["first"][t].copy()
         g = out["learned"]["gate"][t]
         dev = out["learned"]["dev"][t]
+        ungated = ratios(p, l.copy())
         l[~g] = np.nan  # a learned crossing counts only within the gate
         r = ratios(p, l)
+        r["ungated"] = ungated  # the residual crossings alone, without the gate
         r["gated"] = int(g.sum())
         r["max_dev_angle_deg"] = float(np.nanmax(dev[:, 0])) if np.isfinite(dev[:, 0]).any() else None
         r["max_dev_area"] = float(np.nanmax(dev[:, 1])) if np.isfinite(dev[:, 1]).any() else None
