@@ -29,19 +29,31 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "ternary D3Q19+IBM MLUPS & %HBM roofline; time-to-equilibrium learned vs plain"
-BYTES_PER_CELL = 480  # algorithmic bytes per cell update with FP32 storage
+
+
+def pop_bytes(store: int, real: int = 4, q: int = 19) -> int:
+    """Bytes of one cell's populations: 3Q - 2 in the storage type, the two
+    rest populations g_0, h_0 in the arithmetic type (they carry phi and psi
+    themselves)."""
+    return (3 * q - 2) * store + 2 * real
+
+
+def step_bytes(store: int, real: int = 4, q: int = 19) -> int:
+    """Algorithmic bytes of a lattice update: every population read once and
+    written once, rho, phi, psi written and read once (480 in FP32)."""
+    return 2 * pop_bytes(store, real, q) + 6 * real
 
 
 def kernel_bytes(store: int, real: int = 4, q: int = 19, t1: bool = True):
     """Algorithmic DRAM bytes per cell of the two lattice kernels of a step
     (each array element read or written once; store = bytes of a stored
     population, real = of a moment field):
-      k_moments: pulls the 3Q populations, writes rho - 1, phi, psi and, for
+      k_moments: pulls the populations, writes rho - 1, phi, psi and, for
         the tau = 1 collide, j;
-      k_collide: reads rho - 1, phi, psi and I, writes the 3Q populations;
-        the general form also pulls the 3Q populations, the tau = 1 form
+      k_collide: reads rho - 1, phi, psi and I, writes the populations;
+        the general form also pulls the populations, the tau = 1 form
         reads j instead."""
-    pops = 3 * q * store
+    pops = pop_bytes(store, real, q)
     mom = (6 if t1 else 3) * real
     coll = pops + 4 * real + (3 * real if t1 else pops)
     return {"k_moments": pops + mom, "k_collide": coll}
@@ -197,6 +209,8 @@ def main():
     ap.add_argument("--no-workloads", action="store_true",
                     help="skip the lines of the 2D FP64 capsule, the FP16/BF16 bridge and the sweep to residual")
     ap.add_argument("--no-sweep", action="store_true")
+    ap.add_argument("--storage", default="f32", choices=["f32", "f16", "bf16"],
+                    help="population storage of the main workload (FP32 arithmetic in every case)")
     ap.add_argument("--no-net", action="store_true")
     ap.add_argument("--no-validation", action="store_true", help="skip the 2D validation sweep of Sec. 4.1")
     ap.add_argument("--warmstart", action="store_true",
@@ -208,7 +222,7 @@ def main():
     args = ap.parse_args()
 
     from paper_1906_03065_gb300 import workloads as W
-    wl = W.capsule_3d("f32")
+    wl = W.capsule_3d(args.storage)
     if args.impl == "reference":
         return run_reference(args, wl)
 
@@ -267,7 +281,7 @@ def main():
     peaks = _peaks()
     peak = peaks["hbm_gbs"] if peaks else 6800.0
     t1 = tile_variant >= 13
-    kb = kernel_bytes(4, t1=t1)
+    kb = kernel_bytes(4 if args.storage == "f32" else 2, t1=t1)
     kern = {}
     for name, ms in (("k_moments", pr.ms_moments), ("k_collide", pr.ms_collide)):
         t = ms / nprof / 1e3
@@ -275,12 +289,13 @@ def main():
         kern[name] = {"bytes_per_cell": kb[name], "bytes_per_launch": kb[name] * N, "ms": t * 1e3,
                       "achieved": ach, "frac": ach / peak, "traffic": _traffic(name)}
     dom = max(kern, key=lambda k: kern[k]["ms"])
-    step_eff = BYTES_PER_CELL * N * args.steps / (ms_max / 1e3) / 1e9
+    sb = step_bytes(4 if args.storage == "f32" else 2)
+    step_eff = sb * N * args.steps / (ms_max / 1e3) / 1e9
     roofline = {"bound": "hbm", "achieved": kern[dom]["achieved"], "peak": peak, "unit": "GB/s",
                 "frac": kern[dom]["frac"], "traffic": kern[dom]["traffic"],
                 "kernel": dom, "peak_source": "measured" if peaks else "fallback",
                 "bytes_per_launch": kern[dom]["bytes_per_launch"],
-                "whole_step_frac": step_eff / peak, "whole_step_bytes_per_cell": BYTES_PER_CELL,
+                "whole_step_frac": step_eff / peak, "whole_step_bytes_per_cell": sb,
                 "collide_form": "tau=1 equilibrium store" if t1 else "general (populations pulled)",
                 "kernels": kern,
                 "phase_ms_per_step": {"moments": pr.ms_moments / nprof, "ibm": pr.ms_ibm / nprof,
@@ -368,7 +383,7 @@ def main():
         if "sim" in locals():
             del sim
         torch.cuda.empty_cache()
-        for fmt, bpc in (("f16", 252), ("bf16", 252)):
+        for fmt, bpc in (("f16", step_bytes(2)), ("bf16", step_bytes(2))):
             wl16 = W.capsule_3d(fmt)
             s16 = T.Simulation(wl16, device=dev)
             s16.init()
@@ -430,11 +445,11 @@ def main():
         b1.record(bt.stream)
         torch.cuda.synchronize(dev)
         mss = b0.elapsed_time(b1)
-        eff = 252 * cells * nsw / (msb / 1e3) / 1e9
+        eff = step_bytes(2) * cells * nsw / (msb / 1e3) / 1e9
         sweep = {"workload": f"sweep_3d: {len(wls)} instances, edges 48-96, FP16 storage, seed 1",
                  "instances": len(wls), "cells": cells, "value": cells * nsw / (msb / 1e3) / 1e6,
                  "unit": "MLUPS", "steps": nsw, "ms_per_step": msb / nsw, "gpu_launches_per_step": lps,
-                 "effective_gbs": eff, "effective_frac": eff / peak, "bytes_per_cell": 252,
+                 "effective_gbs": eff, "effective_frac": eff / peak, "bytes_per_cell": step_bytes(2),
                  "collide_tile_variant": tv, "collide_z_chunk": zc, "phase_ms_per_step": phase_ms,
                  "one_at_a_time": {"value": cells * nsingle / (mss / 1e3) / 1e6, "unit": "MLUPS",
                                    "steps": nsingle, "ms_per_step": mss / nsingle}}
@@ -481,7 +496,7 @@ def main():
             workloads["bridge_3d_" + fmt] = {
                 "workload": wb.name, "storage": fmt, "steps": nb_, "value": wb.params.ncells * nb_ / (msb_ / 1e3) / 1e6,
                 "unit": "MLUPS", "ms_per_step": msb_ / nb_, "tile_variant": tvb,
-                "whole_step_frac": 252 * wb.params.ncells * nb_ / (msb_ / 1e3) / 1e9 / peak,
+                "whole_step_frac": step_bytes(2) * wb.params.ncells * nb_ / (msb_ / 1e3) / 1e9 / peak,
                 "fp64_mass": list(db.mass[:]), "area": list(db.area[:2]), "volume": list(db.volume[:2])}
             del sb
             torch.cuda.empty_cache()
@@ -649,7 +664,7 @@ def main():
             "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": wl.name, "cells": N, "markers": int(wl.membranes[0].X.shape[0]),
-                       "storage": "f32", "l2": "state 1.1 GB > L2, no flush needed",
+                       "storage": args.storage, "l2": "state > 0.6 GB > L2, no flush needed",
                        "parallelism": "replicas" if world > 1 else "single",
                        "collide_tile_variant": tile_variant, "collide_z_chunk": z_chunk},
             "roofline": roofline, "cpu_baseline": cpu, "clocks": clocks,
