@@ -85,7 +85,7 @@ def _traffic(kernel: str):
     try:
         t = json.load(open(p))
         e = t[kernel]
-        if e.get("source_sha") != _src_hash(kernel):
+        if e.get("source_sha") != _src_hash(kernel.split("_f16")[0].split("_bf16")[0]):
             return None
         return e["dram_bytes_per_launch"]
     except Exception:
@@ -287,7 +287,8 @@ def main():
         t = ms / nprof / 1e3
         ach = kb[name] * N / t / 1e9
         kern[name] = {"bytes_per_cell": kb[name], "bytes_per_launch": kb[name] * N, "ms": t * 1e3,
-                      "achieved": ach, "frac": ach / peak, "traffic": _traffic(name)}
+                      "achieved": ach, "frac": ach / peak,
+                      "traffic": _traffic(name if args.storage == "f32" else f"{name}_{args.storage}")}
     dom = max(kern, key=lambda k: kern[k]["ms"])
     sb = step_bytes(4 if args.storage == "f32" else 2)
     step_eff = sb * N * args.steps / (ms_max / 1e3) / 1e9
@@ -403,7 +404,8 @@ def main():
             for name, ms in (("k_moments", p16.ms_moments), ("k_collide", p16.ms_collide)):
                 t = ms / nprof / 1e3
                 ach = kb16[name] * N / t / 1e9
-                k16[name] = {"bytes_per_cell": kb16[name], "ms": t * 1e3, "achieved": ach, "frac": ach / peak}
+                k16[name] = {"bytes_per_cell": kb16[name], "ms": t * 1e3, "achieved": ach, "frac": ach / peak,
+                             "traffic": _traffic(f"{name}_{fmt}")}
             lowprec[fmt] = {"value": N * n16 / (ms16 / 1e3) / 1e6, "unit": "MLUPS", "steps": n16,
                             "whole_step_bytes_per_cell": bpc,
                             "whole_step_frac": bpc * N * n16 / (ms16 / 1e3) / 1e9 / peak,
