@@ -267,7 +267,17 @@ __device__ __forceinline__ void geometry_body(const IBArgs<Real>& a, const Blk& 
   a.vn[3 * k + 2] = s.z;
 }
 template <class Real>
-__global__ void k_geometry(const __grid_constant__ IBArgs<Real> a) {
+__global__ void k_geometry(const __grid_constant__ IBArgs<Real> a, int snap) {
+  // start-of-step bookkeeping of the single-lattice path: clear the
+  // coupling sums and, with snap, take the snapshot of the marker box and
+  // reset its accumulator
+  const long long n3 = 3ll * a.nn;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n3; i += (long long)gridDim.x * blockDim.x)
+    a.ncpl[i] = 0;
+  if (snap && blockIdx.x == 0 && threadIdx.x < 6) {
+    a.box[6 + threadIdx.x] = a.box[threadIdx.x];
+    a.box[threadIdx.x] = 0x7F7F7F7F;
+  }
   geometry_body(a, hw_blk());
 }
 
@@ -1148,6 +1158,7 @@ __device__ __forceinline__ void node_forces_body(const IBArgs<Real>& a, const Bl
 }
 template <class Real>
 __global__ void k_node_forces(const __grid_constant__ IBArgs<Real> a) {
+  if (blockIdx.x == 0 && threadIdx.x < 2) a.ctr[threadIdx.x] = 0;  // the brick compaction's counters
   node_forces_body(a, hw_blk());
 }
 

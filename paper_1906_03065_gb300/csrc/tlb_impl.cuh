@@ -9,6 +9,7 @@
 #include "tlb_ibm.cuh"
 #include "tlb_lb.cuh"
 #include "tlb_measure.cuh"
+#include "tlb_diag.cuh"
 
 template <class L, int MODE>
 struct Impl : ImplBase {
@@ -142,9 +143,10 @@ struct Impl : ImplBase {
   // and vertex normals and the distance scatter here; elastic forces and the
   // brick binning in ibm_bins).  It runs on the side stream while the
   // moments of the step are computed.
-  static tlb_status ibm_positions(Ctx* c, IBArgs<Real>& a, cudaStream_t s) {
-    TLB_CUDA(cudaMemsetAsync(a.ncpl, 0, c->L.ncpl.bytes, s));
-    k_geometry<Real><<<blocks((long long)c->ne + c->nn, 128), 128, 0, s>>>(a);
+  // With snap the geometry kernel also takes the marker box's snapshot (the
+  // advection's accumulator) and resets it.
+  static tlb_status ibm_positions(Ctx* c, IBArgs<Real>& a, cudaStream_t s, bool snap = false) {
+    k_geometry<Real><<<blocks((long long)c->ne + c->nn, 128), 128, 0, s>>>(a, snap ? 1 : 0);
     TLB_LAUNCHED(c, "k_geometry");
     const long long nfeat = (long long)c->ne + c->nedge + c->nn;
     constexpr int sw = scatter_warps<Real>();
@@ -171,9 +173,8 @@ struct Impl : ImplBase {
   // Elastic forces and the binning of markers into spreading bricks (the
   // bins are consumed and reset by k_spread of the same step).
   static tlb_status ibm_bins(Ctx* c, IBArgs<Real>& a, cudaStream_t s) {
-    k_node_forces<Real><<<blocks((long long)c->nn * 32, 128), 128, 0, s>>>(a);
+    k_node_forces<Real><<<blocks((long long)c->nn * 32, 128), 128, 0, s>>>(a);  // (clears ctr)
     TLB_LAUNCHED(c, "k_node_forces");
-    TLB_CUDA(cudaMemsetAsync(a.ctr, 0, 2 * sizeof(int), s));
     k_brick_count<Real><<<blocks(c->nn, 128), 128, 0, s>>>(a);
     TLB_LAUNCHED(c, "k_brick_count");
     k_brick_compact<Real><<<blocks(c->nbricks, 256), 256, 0, s>>>(a);
@@ -539,8 +540,7 @@ struct Impl : ImplBase {
         // the previous advection (a graph's first step follows the whole
         // previous launch on the caller's stream instead)
         if (pipe && !(c->capturing && k == 0)) TLB_CUDA(cudaStreamWaitEvent(c->side2, c->ev_interp, 0));
-        if (box_on_side && (st = snapshot_box(c, ia, c->side, false)) != TLB_OK) return st;
-        if ((st = ibm_positions(c, ia, c->side)) != TLB_OK) return st;
+        if ((st = ibm_positions(c, ia, c->side, box_on_side)) != TLB_OK) return st;
         if ((st = ibm_bins(c, ia, c->side2)) != TLB_OK) return st;
         TLB_CUDA(cudaEventRecord(c->ev_bins, c->side2));
       }
@@ -725,38 +725,7 @@ struct Impl : ImplBase {
   }
 
   tlb_status diagnostics(Ctx* c, tlb_diag* out) override {
-    cudaStream_t s = c->stream;
     if (tlb_status st = sync_pops(c); st != TLB_OK) return st;
-    Geo G = geo(c);
-    double* part = c->ptr<double>(c->L.part);
-    const int nb = 1024;
-    k_mass_partials<L, MODE><<<nb, 256, 0, s>>>(G, c->ptr<Store>(c->L.lo[c->cur]),
-                                                 c->ptr<Rest>(c->L.rest[c->cur]), part);
-    TLB_LAUNCHED(c, "k_mass_partials");
-    double* meas = c->ptr<double>(c->L.meas);
-    k_reduce_partials<<<1, 256, 0, s>>>(part, nb, 3, meas);
-    TLB_LAUNCHED(c, "k_reduce_partials");
-    if (c->ne > 0) {
-      k_capsule_measures<<<c->ncap, 256, 0, s>>>(c->ptr<double>(c->L.X), c->ptr<int>(c->L.E),
-                                                  c->ptr<int>(c->L.ecap), c->ne, c->NV, c->ncap, meas + 4);
-      TLB_LAUNCHED(c, "k_capsule_measures");
-    }
-    double h[4 + 16];
-    TLB_CUDA(cudaMemcpyAsync(h, meas, sizeof(h), cudaMemcpyDeviceToHost, s));
-    unsigned st = 0;
-    TLB_CUDA(cudaMemcpyAsync(&st, c->ptr<unsigned>(c->L.status), sizeof(unsigned), cudaMemcpyDeviceToHost, s));
-    TLB_CUDA(cudaStreamSynchronize(s));
-    out->step = c->t;
-    for (int q = 0; q < 3; ++q) out->mass[q] = h[q];
-    out->umax = 0;
-    out->n_caps = c->ncap;
-    for (int k = 0; k < 8; ++k) {
-      out->area[k] = k < c->ncap ? h[4 + 2 * k] : 0;
-      out->volume[k] = k < c->ncap ? h[4 + 2 * k + 1] : 0;
-    }
-    if (st & ST_NAN) { set_error("diagnostics: NaN in the populations"); return TLB_ERR_DIVERGED; }
-    if (st & ST_MARKER_JUMP) { set_error("diagnostics: a marker moved half a cell in one step"); return TLB_ERR_DIVERGED; }
-    if (st & ST_OVERFLOW) { set_error("diagnostics: spreading bin overflow"); return TLB_ERR_DIVERGED; }
-    return TLB_OK;
+    return fp64_diagnostics<L, MODE>(c, c->ptr<double>(c->L.part), 1024, c->ptr<double>(c->L.meas), out);
   }
 };

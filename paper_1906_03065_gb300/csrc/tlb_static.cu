@@ -11,6 +11,7 @@
 #include "tlb_ctx.h"
 #include "tlb_ibm.cuh"
 #include "tlb_lb.cuh"
+#include "tlb_diag.cuh"
 
 // Partial sums of up to TLB_STATIC_BLOCKS reduction blocks for the three
 // totals, then the totals themselves and two measures per capsule.  Every
@@ -51,48 +52,7 @@ static tlb_status scratch_address(const Ctx* c, double** out) {
 
 template <class L, int MODE>
 static tlb_status run_static(Ctx* c, double* scratch, tlb_diag* out) {
-  using Store = typename Prec<MODE>::Store;
-  using Rest = typename Prec<MODE>::Rest;
-  cudaStream_t s = c->stream;
-  Geo G;
-  G.nx = c->nx;
-  G.ny = c->ny;
-  G.nz = c->nz;
-  G.wall = c->p.wall_last;
-  G.N = c->N;
-  G.P = c->P;
-  G.P32 = (int)c->P;
-  double* part = scratch;
-  double* meas = scratch + 3 * TLB_STATIC_BLOCKS;
-  // every partial slot, total and measure is overwritten below; nothing in
-  // the scratch needs to start at zero
-  k_mass_partials<L, MODE><<<TLB_STATIC_BLOCKS, 256, 0, s>>>(G, c->ptr<Store>(c->L.lo[c->cur]),
-                                                             c->ptr<Rest>(c->L.rest[c->cur]), part);
-  TLB_LAUNCHED(c, "k_mass_partials");
-  k_reduce_partials<<<1, 256, 0, s>>>(part, TLB_STATIC_BLOCKS, 3, meas);
-  TLB_LAUNCHED(c, "k_reduce_partials");
-  if (c->ne > 0) {
-    k_capsule_measures<<<c->ncap, 256, 0, s>>>(c->ptr<double>(c->L.X), c->ptr<int>(c->L.E), c->ptr<int>(c->L.ecap),
-                                               c->ne, c->NV, c->ncap, meas + 4);
-    TLB_LAUNCHED(c, "k_capsule_measures");
-  }
-  double h[4 + 2 * TLB_STATIC_MAX_CAPS];
-  TLB_CUDA(cudaMemcpyAsync(h, meas, sizeof(h), cudaMemcpyDeviceToHost, s));
-  unsigned st = 0;
-  TLB_CUDA(cudaMemcpyAsync(&st, c->ptr<unsigned>(c->L.status), sizeof(unsigned), cudaMemcpyDeviceToHost, s));
-  TLB_CUDA(cudaStreamSynchronize(s));
-  out->step = c->t;
-  for (int q = 0; q < 3; ++q) out->mass[q] = h[q];
-  out->umax = 0;
-  out->n_caps = c->ncap;
-  for (int k = 0; k < 8; ++k) {
-    out->area[k] = k < c->ncap ? h[4 + 2 * k] : 0;
-    out->volume[k] = k < c->ncap ? h[4 + 2 * k + 1] : 0;
-  }
-  if (st & ST_NAN) { set_error("diagnostics: NaN in the populations"); return TLB_ERR_DIVERGED; }
-  if (st & ST_MARKER_JUMP) { set_error("diagnostics: a marker moved half a cell in one step"); return TLB_ERR_DIVERGED; }
-  if (st & ST_OVERFLOW) { set_error("diagnostics: spreading bin overflow"); return TLB_ERR_DIVERGED; }
-  return TLB_OK;
+  return fp64_diagnostics<L, MODE>(c, scratch, TLB_STATIC_BLOCKS, scratch + 3 * TLB_STATIC_BLOCKS, out);
 }
 
 extern "C" tlb_status tlb_diagnostics_static(void* ctx, tlb_diag* out) {

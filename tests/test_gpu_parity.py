@@ -141,6 +141,23 @@ def test_small_3d_f32_2000_steps():
     print("small_3d f32 2000 steps:", {k: f"{v:.2e}" for k, v in out.items()})
 
 
+def test_capsule_3d_reduction_f32():
+    """The benchmark workload's physics at a reduced size, to the FP32 bar:
+    alpha = 2, dc = 16, kappa = (0.01, 0.02, 0.015), walls in z, the Skalak
+    and Helfrich moduli of the 128^3 capsule, an icosphere of level 2 on a
+    40^3 lattice (the smallest periodic side the dc = 16 band allows; the
+    band then covers whole periods).  400 steps: the oracle's profile is a
+    brute-force nearest-element search (0.3-0.6 s per step here), so the
+    2000-step bar is held by test_small_3d_f32_2000_steps."""
+    wl = W.capsule_3d("f32", n=40, level=2, radius=9.0)
+    oracle.set_threads(0)
+    g, o = _sim(wl).init(), oracle.Oracle(wl)
+    g.step(400)
+    o.step(400)
+    out = _compare_fields(g, o, 1e-4, 1e-4, 1e-4)
+    print("capsule_3d 40^3 f32 400 steps:", {k: f"{v:.2e}" for k, v in out.items()})
+
+
 def test_small_3d_f32_band_wider_than_period():
     """Periodic sides of 25 cells around a capsule of radius 4.8 with dc = 8:
     the band (capsule +- dc) is wider than the period, so the profile box

@@ -49,3 +49,17 @@ def test_single_rank_without_process_group():
     import bench
     ms, v = bench.replica_throughput(4.0, 2000, 10)
     assert ms == 4.0 and v == pytest.approx(2000 * 10 / 0.004 / 1e6)
+
+
+def test_algorithmic_bytes_of_the_roofline():
+    """The bench's byte counts: every population read and written once and
+    rho, phi, psi written and read once is 480 B per FP32 cell update (the
+    figure of the lattice update); 16-bit storage keeps the two rest
+    populations in FP32 (118 B of populations, 260 B per update).  The tau
+    = 1 kernels add j (12 B each way)."""
+    import bench
+    assert bench.pop_bytes(4) == 228 and bench.step_bytes(4) == 480
+    assert bench.pop_bytes(2) == 118 and bench.step_bytes(2) == 260
+    assert bench.kernel_bytes(4) == {"k_moments": 252, "k_collide": 256}
+    assert bench.kernel_bytes(4, t1=False) == {"k_moments": 240, "k_collide": 472}
+    assert bench.kernel_bytes(2) == {"k_moments": 142, "k_collide": 146}
