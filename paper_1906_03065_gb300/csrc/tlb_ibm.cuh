@@ -788,6 +788,9 @@ __device__ __forceinline__ void band_body(const IBArgs<Real>& a, const Blk& blk)
       const int pw[3] = {ox + ix, oy + iy, oz + iz};
       long long c = cell_of(a, pw);
       if (c >= 0) {
+        // psi is requested with the key, so its latency overlaps the key's
+        // and the element's (it is needed only for band cells)
+        const Real psic = a.psi[c];
         unsigned long long key = a.key[c];
         if (key == KEY_NONE) {
           if (a.own[c] >= 0) {  // left the band since the previous step
@@ -825,7 +828,7 @@ __device__ __forceinline__ void band_body(const IBArgs<Real>& a, const Blk& blk)
           a.own[c] = e;
           a.I[c] = I;
           Real ch = cosh(d / (Real(2) * al));
-          Real coef = a.kc * (a.psi[c] - I) / (ch * ch) / (Real(4) * al);
+          Real coef = a.kc * (psic - I) / (ch * ch) / (Real(4) * al);
           V3<Real> dir;
           if (dist > Real(1e-12)) dir = (-s / dist) * xmP;
           else dir = mk<Real>(a.en[3 * e], a.en[3 * e + 1], a.en[3 * e + 2]);
