@@ -291,7 +291,9 @@ tlb_status tlb_profile_steps(void* ctx, long n_steps, tlb_profile* out);
  * pass then also writes j.  Variants 22..27 are the same collide with two
  * x-adjacent cells per thread (tiles 0..2 at 384, then at 512 threads per
  * SM), every stored value of the pair written by one store; they need an
- * even nx.  Variants 19..21 are tiles 0..2 of the general collide with the
+ * even nx.  Variants 28..31 are the tau = 1 collide on 32x16 tiles (3D):
+ * one cell per thread at 768 / 1024, two cells per thread (even nx) at 384
+ * / 512 threads per SM.  Variants 19..21 are tiles 0..2 of the general collide with the
  * pressure-tensor force.  They are tried only where they apply, and a new
  * context starts on variant 13 there (19 with the pressure-tensor force,
  * else 0).
@@ -299,9 +301,9 @@ tlb_status tlb_profile_steps(void* ctx, long n_steps, tlb_profile* out);
  * implementation's launch shape. */
 tlb_status tlb_autotune(void* ctx, int* tile_variant, int* z_chunk);
 
-/* Set the collide variant (0..27, as written by tlb_autotune; 13..18 and
- * 22..27 only where tau = tau_phi = tau_psi = 1 with TLB_FORCE_EDM and the
- * potential force, 22..27 only with an even nx, 19..21 only with the
+/* Set the collide variant (0..31, as written by tlb_autotune; 13..18 and
+ * 22..31 only where tau = tau_phi = tau_psi = 1 with TLB_FORCE_EDM and the
+ * potential force, 22..27, 30 and 31 only with an even nx, 19..21 only with the
  * pressure-tensor force, else TLB_ERR_ARG)
  * and the planes per z chunk (1..nz) explicitly.  The results do not depend
  * on the choice beyond rounding. */

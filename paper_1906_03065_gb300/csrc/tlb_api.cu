@@ -699,7 +699,7 @@ tlb_status tlb_set_tile(void* ctx, int tile_variant, int z_chunk) {
   Ctx* c = (Ctx*)ctx;
   if (!c) { set_error("ctx is NULL"); return TLB_ERR_ARG; }
   if (tile_variant < 0 || tile_variant >= COLLIDE_NVAR || z_chunk < 1 || z_chunk > c->nz) {
-    set_error("set_tile: tile_variant must be 0..27 and z_chunk 1..nz");
+    set_error("set_tile: tile_variant must be 0..31 and z_chunk 1..nz");
     return TLB_ERR_ARG;
   }
   if (!c->variant_ok(tile_variant)) {

@@ -13,10 +13,11 @@
 // Collide variants: 3 tile shapes x 4 register forms, v = 3 form + tile,
 // the smallest tile in a fifth form (v = 12), and the 3 tiles in the two
 // forms of the tau = 1 collide (v = 13..18, see variant_t1).
-constexpr int COLLIDE_NVAR = 28;
+constexpr int COLLIDE_NVAR = 32;
 constexpr bool variant_t1(int v) { return (v >= 13 && v <= 18) || v >= 22; }
-// variants 22..27: the tau = 1 collide with two x-adjacent cells per thread
-constexpr bool variant_pair(int v) { return v >= 22 && v <= 27; }
+// variants 22..27 and 30, 31: the tau = 1 collide with two x-adjacent cells
+// per thread; 28..31 are the tau = 1 forms on 32 x 16 tiles
+constexpr bool variant_pair(int v) { return (v >= 22 && v <= 27) || v == 30 || v == 31; }
 // variants 19..21: the general collide with the pressure-tensor force
 constexpr bool variant_pt(int v) { return v >= 19 && v <= 21; }
 

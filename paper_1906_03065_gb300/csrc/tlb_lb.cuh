@@ -1011,6 +1011,12 @@ __host__ tlb_status collide_variant(int v, Fn&& fn) {
     case 25: return fn(CIdx<32>{}, CIdx<Y0>{}, CIdx<9>{});
     case 26: return fn(CIdx<X1>{}, CIdx<Y1>{}, CIdx<9>{});
     case 27: return fn(CIdx<X2>{}, CIdx<Y0>{}, CIdx<9>{});
+    // the tau = 1 forms on 32 x 16 tiles (3D; less halo per cell): one cell
+    // per thread at 768 / 1024 threads per SM, two at 384 / 512
+    case 28: return fn(CIdx<32>{}, CIdx<D3 ? 16 : 1>{}, CIdx<5>{});
+    case 29: return fn(CIdx<32>{}, CIdx<D3 ? 16 : 1>{}, CIdx<6>{});
+    case 30: return fn(CIdx<32>{}, CIdx<D3 ? 16 : 1>{}, CIdx<8>{});
+    case 31: return fn(CIdx<32>{}, CIdx<D3 ? 16 : 1>{}, CIdx<9>{});
     default: return fn(CIdx<32>{}, CIdx<Y0>{}, CIdx<0>{});
   }
 }

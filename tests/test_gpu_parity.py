@@ -233,7 +233,7 @@ def test_collide_tile_variants_agree(storage):
     P = ref.pops()
     for v, zc in ((0, 8), (1, 5), (2, 16), (3, 7), (4, 12), (5, 34), (6, 9), (7, 12), (8, 3), (9, 12), (10, 6),
                   (11, 20), (12, 11), (13, 7), (14, 12), (15, 9), (16, 5), (17, 20), (18, 11), (22, 7), (23, 12),
-                  (24, 9), (25, 5), (26, 20), (27, 11)):
+                  (24, 9), (25, 5), (26, 20), (27, 11), (28, 6), (29, 13), (30, 8), (31, 34)):
         g = _sim(wl).init()
         g.set_tile(v, zc)
         g.step(12)
