@@ -614,9 +614,10 @@ def main():
             net_line["time_to_equilibrium"] = tte
         torch.cuda.empty_cache()
 
-    # the paper's 2D validation sweep (Sec. 4.1, symmetric case): the capsule
-    # (ks = kb = 1e-2) and the pure lens for the 20 values of kappa_3, at the
-    # paper's size (R = 20, 240 x 120), each set relaxed as one FP32 batch
+    # the paper's 2D validation sweeps at the paper's size (R = 20, 240 x 120),
+    # each set relaxed as one FP32 batch: Sec. 4.1, symmetric case (the
+    # capsule with ks = kb = 1e-2 and the pure lens for the 20 values of
+    # kappa_3), and the Sec. 4.2 capillary bridge
     validation = {}
     if rank == 0 and not args.no_validation:
         from paper_1906_03065_gb300 import validation as V
@@ -637,6 +638,20 @@ def main():
                       "g12_over_g13": [r["g12/g13"] for r in rows if r["ks"] is not None],
                       "D_capsule": [r["D"] for r in rows if r["ks"] is not None],
                       "D_lens": [r["D"] for r in rows if r["ks"] is None]}
+        # Sec. 4.2: the capillary bridge, kappa_1 in {1e-3, 3e-3, 9e-3} x ks in
+        # {1e-3, 1e-2, 1e-1}, one batch of 9 lattices of 240 x 120
+        torch.cuda.synchronize(dev)
+        tb = time.perf_counter()
+        steps_b = 20000
+        brows = V.bridge_sweep(steps=steps_b, device=dev)
+        torch.cuda.synchronize(dev)
+        wall_b = time.perf_counter() - tb
+        validation["bridge"] = {"workload": "Sec. 4.2 capillary bridge: kappa_1 in {1e-3, 3e-3, 9e-3} x ks in {1e-3, "
+                                            "1e-2, 1e-1}, R = 20 on 240 x 120, FP32, one batch of 9 lattices",
+                                "steps": steps_b, "wall_s": wall_b,
+                                "value": len(brows) * 240 * 120 * steps_b / wall_b / 1e6,
+                                "unit": "MLUPS (cell updates of all lattices / wall time)",
+                                "rows": [{"kappa1": r["kappa1"], "ks": r["ks"], "Lc_over_Hc": r["aspect"]} for r in brows]}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

@@ -205,3 +205,22 @@ def deformation_sweep(cases, ks_list=(1e-3, 1e-2, 1e-1), kb_list=(1e-4, 1e-2), s
                          "D": lens_deformation(b[i].field("psi"), (wls[i].params.ny, wls[i].params.nx))})
         del b
     return rows
+
+
+def bridge_sweep(kappa1_list=(1e-3, 3e-3, 9e-3), ks_list=(1e-3, 1e-2, 1e-1), steps: int = 20000,
+                 device="cuda:0", storage: str = "f32"):
+    """Sec. 4.2: aspect ratio L_c / H_c of both capsules of the capillary
+    bridge for every (kappa_1, ks), relaxed as one batch.  Returns rows of
+    (kappa_1, ks, [L_c / H_c of capsule 0, of capsule 1])."""
+    from . import Batch
+    cases = [(k1, ks) for k1 in kappa1_list for ks in ks_list]
+    built = [capillary_bridge(k1, ks, storage=storage) for k1, ks in cases]
+    b = Batch([wl for wl, _ in built], device=device)
+    for i, (wl, rect) in enumerate(built):
+        b[i].init(initial_fields(wl, bridge=rect), None)
+    b.run(steps, 1000, 0.0)
+    rows = []
+    for i, (k1, ks) in enumerate(cases):
+        rows.append({"kappa1": k1, "ks": ks, "aspect": [aspect_ratio(b[i].nodes(m)) for m in range(2)]})
+    del b
+    return rows

@@ -89,3 +89,38 @@ def test_softer_capsules_deform_more():
     D_lens = V.lens_deformation(bl[0].field("psi"), (lens.params.ny, lens.params.nx))
     print(f"D for kappa_s 1e-3, 1e-2, 1e-1: {D}; lens (C3 field moments) {D_lens:.4f}")
     assert D[0] > D[1] > D[2] > 0.0
+
+
+def test_capillary_bridge_matches_the_oracle():
+    """Sec. 4.2 set-up (a C2 bridge between two capsules in C1) at half the
+    paper's size, FP64: the GPU run equals the oracle's after 400 steps."""
+    import oracle
+    from paper_1906_03065_gb300 import Simulation
+    oracle.build()
+    oracle.set_threads(0)
+    wl, rect = V.capillary_bridge(3e-3, 1e-2, R=R)
+    C = V.initial_fields(wl, bridge=rect)
+    g = Simulation(wl).init(C, None)
+    o = oracle.Oracle(wl, init=False)
+    o.init(C, None)
+    g.step(400)
+    o.step(400)
+    for m in range(2):
+        assert np.abs(g.nodes(m) - o.nodes(m)).max() < 1e-9
+    for n in ("C1", "C2", "C3"):
+        assert np.abs(g.field(n) - o.field(n)).max() < 1e-10, n
+
+
+def test_bridge_deforms_softer_capsules_more():
+    """Sec. 4.2 at the paper's size, gamma_12 / gamma_13 = 0.8 (kappa_1 =
+    9e-3): the bridge compresses the capsules along the line joining them
+    (L_c / H_c < 1), and a stiffer capsule ends shorter and wider than a soft
+    one (larger L_c / H_c), as the paper reports; the two capsules, mirror
+    images across the bridge, deform alike."""
+    rows = V.bridge_sweep(kappa1_list=(9e-3,), ks_list=(1e-3, 1e-1), steps=20000, device="cuda:0")
+    soft, stiff = rows[0]["aspect"], rows[1]["aspect"]
+    print(f"L_c/H_c: ks 1e-3 {soft}, ks 1e-1 {stiff}")
+    assert soft[0] < 1 and stiff[0] < 1
+    assert stiff[0] > soft[0]
+    for a in (soft, stiff):
+        assert abs(a[0] - a[1]) < 0.02 * abs(a[0])
