@@ -531,25 +531,26 @@ def main():
     net_line = {}
     if rank == 0 and not args.no_net:
         from paper_1906_03065_gb300 import WarmStartNet, warmstart as WSm
-        E, B = 48, 8
-        net = WarmStartNet(E, 16, 4, max_batch=B, max_nodes=642, device=dev)
-        net.set_params(WSm.init_params(net, 0))
-        c = [16 << l for l in range(4)]
-        shapes = [(27, 16, c[0], 0), (27, c[0], c[0], 0)]
-        for l in range(1, 4):
-            shapes += [(27, c[l - 1], c[l], l), (27, c[l], c[l], l)]
-        for l in range(2, -1, -1):
-            shapes += [(27, c[l + 1] + c[l], c[l], l), (27, c[l], c[l], l)]
-        shapes.append((1, c[0], 16, 0))
-        fl = [2.0 * (E >> lv) ** 3 * t * ci * co for t, ci, co, lv in shapes]
-        f_fwd = sum(fl)
-        f_train = 3 * f_fwd - fl[0]  # forward, weight gradients, data gradients but the input's
-        x = torch.zeros((B, E ** 3, 16), dtype=torch.bfloat16, device=dev)
-        tg = torch.zeros((B, E ** 3), dtype=torch.float32, device=dev)
-        a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         bf = peaks["bf16_tflops"] if peaks else 1900.0
 
-        def net_times(mode):
+        def net_flops(E, base):
+            """Algorithmic FLOPs of one sample's forward pass and training step."""
+            c = [base << l for l in range(4)]
+            shapes = [(27, 16, c[0], 0), (27, c[0], c[0], 0)]
+            for l in range(1, 4):
+                shapes += [(27, c[l - 1], c[l], l), (27, c[l], c[l], l)]
+            for l in range(2, -1, -1):
+                shapes += [(27, c[l + 1] + c[l], c[l], l), (27, c[l], c[l], l)]
+            shapes.append((1, c[0], 16, 0))
+            fl = [2.0 * (E >> lv) ** 3 * t * ci * co for t, ci, co, lv in shapes]
+            # forward, weight gradients, data gradients but the input's
+            return sum(fl), 3 * sum(fl) - fl[0]
+
+        def net_times(net, E, B, mode):
+            f_fwd, f_train = net_flops(E, net.desc.base_channels)
+            x = torch.zeros((B, E ** 3, 16), dtype=torch.bfloat16, device=dev)
+            tg = torch.zeros((B, E ** 3), dtype=torch.float32, device=dev)
+            a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             net.set_tcgen05(mode)
             net.forward(x)
             net.train_step(x, tg, tg, lr=0.0)
@@ -574,14 +575,26 @@ def main():
                     "forward_frac": B * f_fwd / (ms_f / 1e3) / 1e12 / bf,
                     "train_frac": B * f_train / (ms_t / 1e3) / 1e12 / bf}
 
-        legacy = net_times(0)
+        E, B = 48, 8
+        net = WarmStartNet(E, 16, 4, max_batch=B, max_nodes=642, device=dev)
+        net.set_params(WSm.init_params(net, 0))
+        legacy = net_times(net, E, B, 0)
         net_line = {"edge": E, "batch": B, "params": net.n_params,
                     "kernel": "k_conv3_tma: 3x3x3 convolutions (forward and data gradient) on tcgen05, operands by "
                               "TMA, accumulators in tensor memory; k_wgrad3 (mma.sync) for the weight gradients",
-                    **net_times(2), "peak_bf16_tflops": bf,
+                    **net_times(net, E, B, 2), "peak_bf16_tflops": bf,
                     "peak_source": "measured" if peaks else "fallback",
                     "mma_sync": {"kernel": "k_conv3 / k_wgrad3 (mma.sync bf16, brick-tiled)", **legacy}}
-        del net, x
+        del net
+        torch.cuda.empty_cache()
+        # the same kernels on the network at the sweep's stated scale: 96^3
+        # input, 32 to 256 channels over the four levels (random weights)
+        E2, B2 = 96, 2
+        net = WarmStartNet(E2, 32, 4, max_batch=B2, max_nodes=2562, device=dev)
+        net.set_params(WSm.init_params(net, 0))
+        net_line["stated_scale"] = {"edge": E2, "batch": B2, "channels": [32, 64, 128, 256],
+                                    "params": net.n_params, **net_times(net, E2, B2, 2)}
+        del net
         torch.cuda.empty_cache()
         if not args.no_warmstart:
             # time to equilibrium: plain FP32 start against the learned start in FP16
