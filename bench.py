@@ -628,31 +628,46 @@ def main():
         torch.cuda.empty_cache()
 
     # the paper's 2D validation sweeps at the paper's size (R = 20, 240 x 120),
-    # each set relaxed as one FP32 batch: Sec. 4.1, symmetric and asymmetric
-    # cases (the capsule with ks = kb = 1e-2 and the pure lens for every
-    # value of kappa_3), and the Sec. 4.2 capillary bridge
+    # in FP32 batches: Sec. 4.1, symmetric and asymmetric cases (the capsule
+    # for every kappa_3 x ks x kb of the paper as one batch, the pure lens for
+    # every kappa_3 as another), the Galilean runs, and the Sec. 4.2
+    # capillary bridge
     validation = {}
     if rank == 0 and not args.no_validation:
         from paper_1906_03065_gb300 import validation as V
         torch.cuda.empty_cache()
         steps_v = 20000
+        ks_v, kb_v = (1e-3, 1e-2, 1e-1), (1e-4, 1e-2)
         for name, cases in (("symmetric", V.symmetric_case()), ("asymmetric", V.asymmetric_case())):
             torch.cuda.synchronize(dev)
             tv = time.perf_counter()
-            rows = V.deformation_sweep(cases, ks_list=(1e-2,), kb_list=(1e-2,), steps=steps_v, lens=True,
-                                       device=dev)
+            rows = V.deformation_sweep(cases, ks_list=ks_v, kb_list=kb_v, steps=steps_v, lens=True, device=dev)
             torch.cuda.synchronize(dev)
             wall_v = time.perf_counter() - tv
-            cells_v = 2 * len(cases) * 240 * 120
+            n_caps = len(cases) * len(ks_v) * len(kb_v)
+            cells_v = (n_caps + len(cases)) * 240 * 120
             validation[name] = {
                 "workload": f"Sec. 4.1 {name} case: kappa = {cases[0][:2]}, kappa_3 = {cases[0][2]:g} .. "
-                            f"{cases[-1][2]:g} ({len(cases)} values), R = 20 on 240 x 120; capsule ks = kb = 1e-2 "
-                            f"and the pure lens, FP32, two batches of {len(cases)} lattices",
+                            f"{cases[-1][2]:g} ({len(cases)} values), R = 20 on 240 x 120, FP32; the capsule for "
+                            f"every kappa_3 x ks in {{1e-3, 1e-2, 1e-1}} x kb in {{1e-4, 1e-2}} (one batch of "
+                            f"{n_caps} lattices) and the pure lens (one batch of {len(cases)})",
                 "steps": steps_v, "wall_s": wall_v, "value": cells_v * steps_v / wall_v / 1e6,
                 "unit": "MLUPS (cell updates of all lattices / wall time)",
-                "g12_over_g13": [r["g12/g13"] for r in rows if r["ks"] is not None],
-                "D_capsule": [r["D"] for r in rows if r["ks"] is not None],
+                "g12_over_g13": [r["g12/g13"] for r in rows if r["ks"] is None],
+                "D_capsule": {f"ks{ks:g}_kb{kb:g}": [r["D"] for r in rows if r["ks"] == ks and r["kb"] == kb]
+                              for ks in ks_v for kb in kb_v},
                 "D_lens": [r["D"] for r in rows if r["ks"] is None]}
+        torch.cuda.synchronize(dev)
+        tg = time.perf_counter()
+        grows = V.galilean_runs(steps=steps_v, device=dev)
+        torch.cuda.synchronize(dev)
+        validation["galilean"] = {
+            "workload": "Sec. 4.1 Galilean runs: kappa = (8e-3, 8e-3, 5e-4), ks = 1e-3, kb = 1e-2, every fluid at "
+                        "U_x0 in {1e-4, 1e-3, 1e-2} beside the stationary run, R = 20 on 240 x 120, FP32, one "
+                        "batch of 4 lattices",
+            "steps": steps_v, "wall_s": time.perf_counter() - tg,
+            "rows": [{"U": r["U"], "drift_x": r["drift"][0], "U_steps": r["U_steps"],
+                      "shape_dev": r["shape_dev"], "D": r["D"], "D_stationary": r["D_stationary"]} for r in grows]}
         # Sec. 4.2: the capillary bridge, kappa_1 in {1e-3, 3e-3, 9e-3} x ks in
         # {1e-3, 1e-2, 1e-1}, one batch of 9 lattices of 240 x 120
         torch.cuda.synchronize(dev)

@@ -179,18 +179,19 @@ def asymmetric_case():
 def deformation_sweep(cases, ks_list=(1e-3, 1e-2, 1e-1), kb_list=(1e-4, 1e-2), steps: int = 40000,
                       lens: bool = True, device="cuda:0", storage: str = "f32"):
     """Taylor deformation of the relaxed capsule for every (kappa, ks, kb),
-    and of the pure lens for every kappa, each set relaxed as one batch.
-    Returns rows of (kappa, ratio g12/g13, g13/g23, ks, kb, D)."""
+    relaxed together as one batch, and of the pure lens for every kappa, as
+    a second batch.  Returns rows of (kappa, ratio g12/g13, g13/g23, ks, kb,
+    D), the capsules in (ks, kb, kappa) order, then the lenses."""
     rows = []
-    for ks in ks_list:
-        for kb in kb_list:
-            wls = [capsule_at_interface(k, ks, kb, storage=storage) for k in cases]
-            b = relax(wls, steps, device=device)
-            for i, k in enumerate(cases):
-                g12, g13, g23 = tensions(k)
-                rows.append({"kappa": k, "g12/g13": g12 / g13, "g13/g23": g13 / g23, "ks": ks, "kb": kb,
-                             "D": taylor_deformation(b[i].nodes(0))})
-            del b
+    combos = [(ks, kb, k) for ks in ks_list for kb in kb_list for k in cases]
+    if combos:
+        wls = [capsule_at_interface(k, ks, kb, storage=storage) for ks, kb, k in combos]
+        b = relax(wls, steps, device=device)
+        for i, (ks, kb, k) in enumerate(combos):
+            g12, g13, g23 = tensions(k)
+            rows.append({"kappa": k, "g12/g13": g12 / g13, "g13/g23": g13 / g23, "ks": ks, "kb": kb,
+                         "D": taylor_deformation(b[i].nodes(0))})
+        del b
     if lens:
         wls = [capsule_at_interface(k, 0.0, 0.0, membrane=False, storage=storage) for k in cases]
         fields = []
@@ -204,6 +205,30 @@ def deformation_sweep(cases, ks_list=(1e-3, 1e-2, 1e-1), kb_list=(1e-4, 1e-2), s
             rows.append({"kappa": k, "g12/g13": g12 / g13, "g13/g23": g13 / g23, "ks": None, "kb": None,
                          "D": lens_deformation(b[i].field("psi"), (wls[i].params.ny, wls[i].params.nx))})
         del b
+    return rows
+
+
+def galilean_runs(kappa=(8e-3, 8e-3, 5e-4), ks: float = 1e-3, kb: float = 1e-2, U_list=(1e-4, 1e-3, 1e-2),
+                  steps: int = 20000, R: float = R_PAPER, device="cuda:0", storage: str = "f32"):
+    """Sec. 4.1, Galilean invariance: the capsule with every fluid started
+    at a uniform U_x0, relaxed beside the stationary run (U = 0) as one
+    batch.  Returns rows of (U, the mean marker displacement from the
+    stationary run, U * steps, the largest distance between corresponding
+    markers of the two shapes with each centroid removed, D of both)."""
+    wls = [capsule_at_interface(kappa, ks, kb, U=U, R=R, storage=storage) for U in (0.0,) + tuple(U_list)]
+    b = relax(wls, steps, device=device)
+    X0 = b[0].nodes(0)
+
+    def centred(X):
+        return X[:, :2] - X[:, :2].mean(axis=0)
+
+    rows = []
+    for i, U in enumerate(U_list, start=1):
+        X = b[i].nodes(0)
+        rows.append({"U": U, "drift": (X[:, :2] - X0[:, :2]).mean(axis=0).tolist(), "U_steps": U * steps,
+                     "shape_dev": float(np.abs(centred(X) - centred(X0)).max()),
+                     "D": taylor_deformation(X), "D_stationary": taylor_deformation(X0)})
+    del b
     return rows
 
 

@@ -124,3 +124,25 @@ def test_bridge_deforms_softer_capsules_more():
     assert stiff[0] > soft[0]
     for a in (soft, stiff):
         assert abs(a[0] - a[1]) < 0.02 * abs(a[0])
+
+
+def test_deformation_sweep_batches_every_combination_as_if_alone():
+    """The Sec. 4.1 sweep relaxes every (kappa, ks, kb) capsule in one batch;
+    each lattice's result is the one it gets relaxed alone, bit for bit (the
+    instances share kernels, not state)."""
+    cases = [SYM, (8e-3, 8e-3, 4e-3)]
+    rows = V.deformation_sweep(cases, ks_list=(1e-3, 1e-1), kb_list=(1e-2,), steps=500, lens=False)
+    assert [(r["ks"], r["kappa"]) for r in rows] == [(ks, k) for ks in (1e-3, 1e-1) for k in cases]
+    for r in rows:
+        b = V.relax([V.capsule_at_interface(r["kappa"], r["ks"], r["kb"], storage="f32")], 500)
+        assert V.taylor_deformation(b[0].nodes(0)) == r["D"]
+
+
+def test_galilean_runs_report_drift_and_shape():
+    """The Galilean rows carry the capsule along at U (drift close to U *
+    steps) with the stationary shape (half the paper's size, 3000 steps)."""
+    rows = V.galilean_runs(U_list=(1e-3, 1e-2), steps=3000, R=R)
+    for r in rows:
+        assert abs(r["drift"][0] - r["U_steps"]) < 0.02 * r["U_steps"] + 0.05, r
+        assert r["shape_dev"] < 0.05 * (r["U"] / 1e-2) + 0.005, r
+        assert abs(r["D"] - r["D_stationary"]) < 2e-3, r
