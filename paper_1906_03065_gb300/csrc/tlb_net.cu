@@ -1006,10 +1006,12 @@ __global__ void k_to_bf16(const float* __restrict__ g, long long n, bf16* __rest
   *reinterpret_cast<uint4*>(o + i) = r;
 }
 
-// Field loss: gy[v][0..1] = 2/(B V) (y - target), gy[v][2..7] = 0; per-block
-// FP64 partial sums of the squared errors.
+// Field loss: gy[v][0..1] = 2/(B V) (y - target), gy[v][2..15] = 0, and the
+// marker loss's fixed-point accumulators of v cleared (gfix, if not NULL);
+// per-block FP64 partial sums of the squared errors.
 __global__ void k_loss_fields(const float* __restrict__ y, const float* __restrict__ tphi, const float* __restrict__ tpsi,
-                              long long n, double scale, float* __restrict__ gy, double* __restrict__ part) {
+                              long long n, double scale, float* __restrict__ gy, long long* __restrict__ gfix,
+                              double* __restrict__ part) {
   __shared__ double sm[256];
   const long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   double e = 0;
@@ -1019,6 +1021,8 @@ __global__ void k_loss_fields(const float* __restrict__ y, const float* __restri
     gy[v * YC] = (float)(2.0 * scale * d0);
     gy[v * YC + 1] = (float)(2.0 * scale * d1);
     for (int c = 2; c < YC; ++c) gy[v * YC + c] = 0.f;
+    if (gfix)
+      for (int a = 0; a < 3; ++a) gfix[3 * v + a] = 0;
   }
   sm[threadIdx.x] = e;
   __syncthreads();
@@ -1050,10 +1054,20 @@ __device__ __forceinline__ Tri tri_of(float x, float y, float z, int E) {
   return T;
 }
 
-// Marker loss of sample b: offsets = trilinear(y2..4)(X0); gy[2..4] += the
-// gradient (scattered with the trilinear weights); FP64 partial sums.
+// The marker loss's gradient is scattered in fixed point (steps of
+// 2^-GFIX_BITS) with integer atomics: the sums do not depend on the order of
+// the additions, so a training step is reproducible bit for bit.  Each
+// contribution is clamped to +-2^GFIX_CLAMP, far above any gradient of this
+// loss (2 lambda / (3 markers) times an offset error), so that the few
+// hundred contributions a voxel can receive stay inside the 2^(63 -
+// GFIX_BITS) range.
+constexpr int GFIX_BITS = 48, GFIX_CLAMP = 8;
+
+// Marker loss of sample b: offsets = trilinear(y2..4)(X0); the gradient is
+// added, scattered with the trilinear weights, into the fixed-point
+// accumulators gfix[v][0..2] of the sample; FP64 partial sums of the loss.
 __global__ void k_loss_nodes(const float* __restrict__ y, const float* __restrict__ X0, const float* __restrict__ toff,
-                             int nn, int E, double scale, float* __restrict__ gy, double* __restrict__ part) {
+                             int nn, int E, double scale, long long* __restrict__ gfix, double* __restrict__ part) {
   __shared__ double sm[256];
   const int l = blockIdx.x * blockDim.x + threadIdx.x;
   double e = 0;
@@ -1065,7 +1079,11 @@ __global__ void k_loss_nodes(const float* __restrict__ y, const float* __restric
       const float r = o - toff[3 * l + a];
       e += (double)r * r;
       const float gr = (float)(2.0 * scale * r);
-      for (int d = 0; d < 8; ++d) atomicAdd(gy + T.idx[d] * YC + 2 + a, gr * T.w[d]);
+      for (int d = 0; d < 8; ++d) {
+        const double c = fmin(fmax((double)(gr * T.w[d]), -(double)(1 << GFIX_CLAMP)), (double)(1 << GFIX_CLAMP));
+        const long long q = __double2ll_rn(c * (double)(1ll << GFIX_BITS));
+        atomicAdd(reinterpret_cast<unsigned long long*>(gfix + 3 * T.idx[d] + a), (unsigned long long)q);
+      }
     }
   }
   sm[threadIdx.x] = e;
@@ -1075,6 +1093,14 @@ __global__ void k_loss_nodes(const float* __restrict__ y, const float* __restric
     __syncthreads();
   }
   if (threadIdx.x == 0) part[blockIdx.x] = sm[0];
+}
+
+// gy[v][2..4] = gfix[v][0..2] 2^-GFIX_BITS (the marker loss's gradient).
+__global__ void k_loss_fold(const long long* __restrict__ gfix, long long n, float* __restrict__ gy) {
+  const long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (v >= n) return;
+  const double s = 1.0 / (double)(1ll << GFIX_BITS);
+  for (int a = 0; a < 3; ++a) gy[v * YC + 2 + a] = (float)((double)gfix[3 * v + a] * s);
 }
 
 // Adam (Kingma and Ba 2015) on fp32 parameters; c1 = 1 - b1^t, c2 = 1 - b2^t.
@@ -1315,7 +1341,7 @@ struct Net {
   std::vector<Conv> convs;
   size_t nparam = 0;
   // arena regions (byte offsets)
-  size_t o_theta, o_grad, o_m, o_v, o_wf, o_wd, o_act, o_grad_act, o_gz, o_y, o_gy, o_part, o_lpart, o_misc;
+  size_t o_theta, o_grad, o_m, o_v, o_wf, o_wd, o_act, o_grad_act, o_gz, o_y, o_gy, o_part, o_gfix, o_lpart, o_misc;
   size_t n_wbf = 0, n_act = 0, n_gact = 0, n_gz = 0, n_part = 0;
   // tensors: x, per encoder level (a, e, pool input p), per decoder level (cat, b, d)
   Ten x, enc_a[4], enc_e[4], enc_p[4], dec_cat[4], dec_b[4], dec_d[4];
@@ -1425,6 +1451,7 @@ void plan(Net& n) {
   n.o_y = take((size_t)n.vox(0, B) * YC * 4);
   n.o_gy = take((size_t)n.vox(0, B) * YC * 4);
   n.o_part = take(n.n_part * 4);
+  n.o_gfix = take(d.max_nodes > 0 ? (size_t)n.vox(0, B) * 3 * 8 : 0);
   n.o_lpart = take((size_t)(nb(n.vox(0, B), 256) + (size_t)B * nb(d.max_nodes, 256) + 1024) * 8);
   n.o_misc = take(72 * 8);  // FP64 sums; the status word at double 64
   n.bytes = off;
@@ -1763,7 +1790,9 @@ tlb_status loss(Net* n, int B, const float* dphi, const float* dpsi, const float
   cudaStream_t s = n->stream;
   double* part = n->at<double>(n->o_lpart);
   const unsigned nbf = nb(V, 256);
-  k_loss_fields<<<nbf, 256, 0, s>>>(n->at<float>(n->o_y), dphi, dpsi, V, 1.0 / (double)V, n->at<float>(n->o_gy), part);
+  long long* gfix = n->d.max_nodes > 0 ? n->at<long long>(n->o_gfix) : nullptr;
+  k_loss_fields<<<nbf, 256, 0, s>>>(n->at<float>(n->o_y), dphi, dpsi, V, 1.0 / (double)V, n->at<float>(n->o_gy), gfix,
+                                    part);
   NET_LAUNCHED(n, "k_loss_fields");
   long long ntot = 0;
   for (int b = 0; b < B; ++b) ntot += nnodes ? nnodes[b] : 0;
@@ -1774,9 +1803,13 @@ tlb_status loss(Net* n, int B, const float* dphi, const float* dpsi, const float
       const unsigned k = nb(nnodes[b], 256);
       k_loss_nodes<<<k, 256, 0, s>>>(n->at<float>(n->o_y) + b * V1 * YC, X0 + (size_t)b * n->d.max_nodes * 3,
                                      off + (size_t)b * n->d.max_nodes * 3, nnodes[b], E, lambda / (3.0 * ntot),
-                                     n->at<float>(n->o_gy) + b * V1 * YC, part + nbf + nbn);
+                                     gfix + b * V1 * 3, part + nbf + nbn);
       NET_LAUNCHED(n, "k_loss_nodes");
       nbn += k;
+    }
+    if (nbn) {
+      k_loss_fold<<<nbf, 256, 0, s>>>(gfix, V, n->at<float>(n->o_gy));
+      NET_LAUNCHED(n, "k_loss_fold");
     }
   }
   double* tot = n->at<double>(n->o_misc);

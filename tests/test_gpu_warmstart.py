@@ -151,6 +151,29 @@ def test_gradients_and_adam_match_oracle():
     assert np.abs(t1 - ref).max() < 1e-6
 
 
+def test_training_steps_are_bitwise_reproducible():
+    """The marker loss scatters its gradient in fixed point, so the same
+    training steps from the same state give the same parameters bit for bit,
+    even with many markers sharing voxels."""
+    import torch
+    rng = np.random.default_rng(4)
+    B, n = 2, 32
+    x = _to_gpu_x(_inputs(rng, B))
+    f = lambda a: torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).cuda()  # noqa: E731
+    dphi, dpsi = f(rng.normal(0, 0.05, (B, E ** 3))), f(rng.normal(0, 0.05, (B, E ** 3)))
+    X0 = f(rng.uniform(7.0, 8.5, (B, n, 3)))  # every marker in the same few voxels
+    off = f(rng.normal(0, 0.2, (B, n, 3)))
+    out = []
+    for _ in range(2):
+        net = _net()
+        net.set_params(_theta(5))
+        for _ in range(3):
+            net.train_step(x, dphi, dpsi, X0, off, [n] * B, lam=1.0, lr=1e-3, update=True)
+        out.append((net.params(), net.grads()))
+    assert np.array_equal(out[0][0], out[1][0])
+    assert np.array_equal(out[0][1], out[1][1])
+
+
 def _cube(edge=32, R=6.0, level=2, seed=0):
     rng = np.random.default_rng(seed)
     c = edge / 2.0
