@@ -467,6 +467,9 @@ tlb_status tlb_net_forward(void* net, const void* x_dev, int batch, float* y_dev
 /* Forward, loss (returned in *loss_out, host), backward; then one Adam step
  * (Kingma and Ba 2015; beta1 0.9, beta2 0.999, eps 1e-8, step size lr) when
  * update != 0.  n_nodes: host [batch] marker counts (NULL: no marker term).
+ * Every sum is order-independent (the marker term's gradient is scattered
+ * in 64-bit fixed point, each contribution clamped to +-2^8), so the same
+ * call from the same state gives the same parameters bit for bit.
  * Synchronises the stream. */
 tlb_status tlb_net_train_step(void* net, const void* x_dev, const float* t0_dev, const float* t1_dev,
                               const float* X0_dev, const float* off_dev, const int* n_nodes, int batch,
