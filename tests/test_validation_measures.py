@@ -54,3 +54,65 @@ def test_initial_fields_sum_to_one_and_carry_the_interfaces():
     assert np.abs(Cb.sum(0) - 1).max() < 1e-12
     C2 = Cb[1].reshape(wlb.params.ny, wlb.params.nx)
     assert C2[60, 120] > 0.95 and C2[5, 5] < 0.01  # (a bridge 2S = 20 wide: tanh edges 10 cells off)
+
+
+class _Inst:
+    def __init__(self, X):
+        self.X = X
+
+    def nodes(self, m):
+        return self.X
+
+
+class _StubBatch(list):
+    """Stands in for a relaxed batch: instance i holds the markers the stub
+    relaxation gave it."""
+
+
+def _stub_relax(shape_of):
+    def relax(wls, steps, fields=None, device=None):
+        return _StubBatch(_Inst(shape_of(wl, steps)) for wl in wls)
+    return relax
+
+
+def test_deformation_sweep_rows_follow_the_batch_order(monkeypatch):
+    """Every (ks, kb, kappa) capsule is one instance of a single batch; row i
+    reports instance i's deformation under its own (kappa, ks, kb)."""
+    cases = [(8e-3, 8e-3, 5e-4), (8e-3, 8e-3, 1e-3), (8e-3, 8e-3, 2e-3)]
+
+    def shape(wl, steps):  # an ellipse whose D encodes the instance's ks and kappa_3
+        m = wl.membranes[0]
+        d = 0.1 * math.log10(1.0 / m.ks) + 10 * wl.params.kappa3
+        return _ellipse(20 * (1 + d), 20 * (1 - d))
+
+    monkeypatch.setattr(V, "relax", _stub_relax(shape))
+    rows = V.deformation_sweep(cases, ks_list=(1e-3, 1e-1), kb_list=(1e-4, 1e-2), steps=10, lens=False)
+    assert [(r["ks"], r["kb"], r["kappa"]) for r in rows] == \
+        [(ks, kb, k) for ks in (1e-3, 1e-1) for kb in (1e-4, 1e-2) for k in cases]
+    for r in rows:
+        want = 0.1 * math.log10(1.0 / r["ks"]) + 10 * r["kappa"][2]
+        assert abs(r["D"] - want) < 1e-6
+        g12, g13, _ = V.tensions(r["kappa"])
+        assert r["g12/g13"] == pytest.approx(g12 / g13)
+
+
+def test_galilean_rows_measure_drift_and_shape(monkeypatch):
+    """The Galilean rows take the mean marker displacement from the
+    stationary run as the drift and compare the shapes with each centroid
+    removed: a run translated by U * steps and uniformly offset by 0.01 in
+    x has drift U * steps + 0.01 and shape deviation 0."""
+    def shape(wl, steps):
+        U = wl.params.u0[0]
+        X = _ellipse(22.0, 18.0)
+        X[:, 0] += U * steps + (0.01 if U else 0.0)
+        return X
+
+    monkeypatch.setattr(V, "relax", _stub_relax(shape))
+    rows = V.galilean_runs(U_list=(1e-4, 1e-2), steps=1000)
+    assert [r["U"] for r in rows] == [1e-4, 1e-2]
+    for r in rows:
+        assert r["drift"][0] == pytest.approx(r["U"] * 1000 + 0.01)
+        assert abs(r["drift"][1]) < 1e-12
+        assert r["shape_dev"] < 1e-9
+        assert r["D"] == pytest.approx(r["D_stationary"])
+        assert r["U_steps"] == pytest.approx(r["U"] * 1000)
